@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Benchmark of the exact ddKS hot path on GB300.
+
+Default workload: exact ddKS, d = 4, NP = NT = 20,000 float32 (P ~ N(0, I4);
+T with corr(x0, x1) = 0.5 and 1% of its rows exact copies of P rows).  One step
+is one ddks_distance call over the device-resident inputs (rank encoding,
+orthant counts, max over origins, result to the host).  The metric is
+origin*point*dim compares per second: N^2 * d per step, N = NP + NT.
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle instead.
+Under torchrun every rank runs its own replica of the workload (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ddks_compares_per_s"
+UNIT = "compares/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["cfg2", "cfg1", "cfg3"], default="cfg2")
+    ap.add_argument("--path", type=int, default=0, help="force a kernel path (0 = auto)")
+    ap.add_argument("--flush-mb", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+WORKLOADS = {
+    "cfg2": ("cfg2_d4_20000x20000_f32_ties", "exact ddKS d=4 NP=NT=20000 f32, corr(x0,x1)=0.5, 1% tied T rows"),
+    "cfg1": ("cfg1_d3_200x200_f32", "exact ddKS d=3 NP=NT=200 f32 gaussian, T shifted by 0.2"),
+    "cfg3": ("cfg3_d12_4096x4096_f64", "exact ddKS d=12 NP=NT=4096 f64 uniform, T coord 5 ~ Beta(2,2)"),
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken while the timed loop runs."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}", "--format=csv,noheader,nounits",
+                 "-lms", "20", "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peak_lane_ops(torch, dev, sm_max_mhz):
+    """Integer issue roofline: SMs x 4 sub-partitions x 32 lanes x max SM clock."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = sm_max_mhz or 2070.0
+    return sms * 128 * mhz * 1e6, sms, mhz
+
+
+def load_traffic(kernel_key):
+    """DRAM bytes per launch of the count kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        rec = json.load(open(p)).get(kernel_key)
+    except (ValueError, OSError):
+        return None
+    if not rec:
+        return None
+    from paper_2106_13706_gb300 import build as bld
+    if rec.get("source_digest") != bld._digest():
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2106_13706_gb300 as pkg
+    from paper_2106_13706_gb300 import build as bld
+    from paper_2106_13706_gb300 import workloads as wl
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    bld.build()
+    key, desc = WORKLOADS[args.workload]
+    P, T = wl.CONFIGS[key]()
+    NP, d = P.shape
+    NT = T.shape[0]
+    N = NP + NT
+    units = float(N) * N * d
+    Pd = torch.from_numpy(P).cuda()
+    Td = torch.from_numpy(T).cuda()
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device="cuda")
+    ctx = pkg.Context(device=local, path=args.path)
+    ctx.set_stage_timing(True)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        ref = ctx.distance(Pd, Td)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.2)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    count_ms = []
+    launches0 = ctx.stats()["kernel_launches"]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        r = ctx.distance(Pd, Td)
+        ev[s][1].record(stream)
+        count_ms.append(ctx.stage_times()[1])
+        if r["num_max"] != ref["num_max"]:
+            raise RuntimeError("result changed between steps")
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    launches = ctx.stats()["kernel_launches"] - launches0
+    sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = units * args.steps * world / (total_ms * 1e-3)
+
+    # end to end through the same C call with pinned host inputs: the H2D copy
+    # of P and T and the D2H copy of the result are inside each timed call
+    e2e = None
+    if not args.no_e2e:
+        Ph = torch.from_numpy(P).pin_memory()
+        Th = torch.from_numpy(T).pin_memory()
+        for _ in range(3):
+            ctx.distance(Ph, Th)
+        torch.cuda.synchronize()
+    if not args.no_e2e:
+        tot = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            r2 = ctx.distance(Ph, Th)
+            tot += time.perf_counter() - a
+        if r2["num_max"] != ref["num_max"]:
+            raise RuntimeError("host-input result differs")
+        e2e = {"value": units * args.steps * world / tot, "unit": UNIT,
+               "h2d_bytes_per_step": int(Ph.numel() * Ph.element_size() + Th.numel() * Th.element_size()),
+               "d2h_bytes_per_step": 3 * 8 + 4}
+
+    clocks = sampler.summary()
+    peak, sms, mhz = peak_lane_ops(torch, local, clocks.get("sm_max_mhz"))
+    cnt = statistics.mean(count_ms) if count_ms else None
+    roof = None
+    if cnt:
+        achieved = units / (cnt * 1e-3)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
+                "frac": achieved / peak, "traffic": load_traffic(f"count_{args.workload}"),
+                "kernel": "orthant count kernel", "kernel_ms": cnt,
+                "peak_basis": f"{sms} SMs x 128 int lanes x {mhz:.0f} MHz (max SM clock)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(P, T, d)
+    ctx.close()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 ranks (f32 input)" if P.dtype == np.float32 else "u32 ranks (f64 input)",
+        "data": "synthetic (seeded numpy PCG64)",
+        "config": {"workload": desc, "N": N, "d": d, "units_per_step": units,
+                   "l2": f"flushed between steps ({args.flush_mb} MB write)", "replicas": world},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks, "num_max": ref["num_max"], "denom": ref["denom"],
+        "wall_s_timed": wall,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(P, T, d, max_origins=None):
+    """The CPU oracle as it stands, all host cores, on the same workload."""
+    from oracle import oracle as orc
+    N = len(P) + len(T)
+    nthr = orc.num_threads()
+    o_end = N if max_origins is None else min(N, max_origins)
+    t0 = time.perf_counter()
+    orc.ddks(P, T, origins=(0, o_end), nthreads=nthr)
+    dt = time.perf_counter() - t0
+    return {"value": float(o_end) * N * d / dt, "unit": UNIT, "cores": nthr, "kind": "oracle",
+            "sample": f"origins [0,{o_end}) of {N} (all points per origin), one pass, {dt:.2f} s"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2106_13706_gb300 import workloads as wl
+    from oracle import oracle as orc
+    key, desc = WORKLOADS[args.workload]
+    P, T = wl.CONFIGS[key]()
+    NP, d = P.shape
+    N = NP + len(T)
+    nthr = orc.num_threads()
+    # each step: a bounded sample of origins (all points per origin)
+    sample = min(N, 2048)
+    for w in range(max(args.warmup, 0)):
+        orc.ddks(P, T, origins=(0, min(N, 256)), nthreads=nthr)
+    tot = 0.0
+    for s in range(args.steps):
+        a = (s * sample) % N
+        b = min(N, a + sample)
+        t0 = time.perf_counter()
+        orc.ddks(P, T, origins=(a, b), nthreads=nthr)
+        tot += time.perf_counter() - t0
+    done = sum(min(N, (s * sample) % N + sample) - (s * sample) % N for s in range(args.steps))
+    value = float(done) * N * d / tot
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot * 1e3 / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 compares" if P.dtype == np.float32 else "f64 compares",
+        "data": "synthetic (seeded numpy PCG64)", "impl": "reference",
+        "config": {"workload": desc, "N": N, "d": d},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthr, "kind": "oracle",
+                         "sample": f"{sample} origins per step (all points per origin)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * ddks.h -- C ABI of the GB300-native exact ddKS library (libddks.so).
+ *
+ * The d-dimensional Kolmogorov-Smirnov distance of arXiv 2106.13706:
+ *
+ *   Sec. 2.1, Eq. (ddks_tensor_definition): every point of the pooled sample
+ *   P u T is taken in turn as a test point (origin) o.  Every point x of P and
+ *   of T gets the orthant code  c(x, o) = sum_m [x_m >= o_m] * 2^m  (the ">="
+ *   split of Sec. 2.2.1, Eq. (g): equal coordinates and the origin itself go
+ *   to the ">=" side).  cP(o, j) and cT(o, j) count the points of each sample
+ *   with code j (Eq. membership), and the statistic is the largest normalised
+ *   difference |cP/NP - cT/NT| over origins and orthants (Eq. d1 with the
+ *   normalisation of Eq. abs_difference).
+ *
+ * The library reports the exact integer numerator  num_max =
+ * max |cP*NT - cT*NP|  and the denominator NP*NT, so results are bit-exact;
+ * D = num_max / (NP*NT) is given as a double for convenience.
+ *
+ * Conventions shared by every entry point
+ *   - P is NP x d, T is NT x d, row-major and contiguous, of element type
+ *     dtype (DDKS_F32 = float, DDKS_F64 = double).  Coordinates are compared
+ *     as stored: -0.0 equals +0.0, +-inf are ordinary values, NaN is rejected
+ *     with DDKS_ENAN.
+ *   - P and T may be device pointers (read in place) or host pointers
+ *     (pageable or pinned; copied into context-owned device memory first).
+ *     The library tells them apart with cudaPointerGetAttributes.  Inputs are
+ *     read-only and are not retained after the call returns.
+ *   - stream is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *     synchronous: they enqueue their kernels on stream and wait for it.
+ *   - 1 <= d <= DDKS_MAX_D; NP, NT >= 1; NP*NT < 2^62.
+ *   - Orthant code bit m is [x_m >= o_m].  argmax_origin is the lowest pooled
+ *     index (P rows first, then T rows) whose best orthant reaches num_max,
+ *     argmax_orthant the lowest code reaching it there (0 when num_max = 0).
+ *   - Every function returns DDKS_OK (0) or a negative error code; no
+ *     exception crosses the ABI and no device code traps.  A context is not
+ *     thread-safe: one host thread at a time (submit/poll excepted, which
+ *     lock internally).
+ */
+#ifndef DDKS_H_
+#define DDKS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DDKS_MAX_D 30
+
+/* return codes */
+#define DDKS_OK 0
+#define DDKS_PENDING 1          /* ddks_poll: request not finished yet */
+#define DDKS_EINVAL (-1)        /* bad shape, dtype, pointer or option */
+#define DDKS_ENAN (-2)          /* a coordinate is NaN */
+#define DDKS_EOVERFLOW (-3)     /* NP*NT >= 2^62 or a size beyond the kernels' index range */
+#define DDKS_ENOMEM (-4)        /* device allocation failed, or a request exceeds the HBM budget */
+#define DDKS_ECUDA (-5)         /* a CUDA runtime call failed (see ddks_last_cuda_error) */
+#define DDKS_ETIMEOUT (-6)      /* a bounded wait ran out */
+#define DDKS_ENOTFOUND (-7)     /* unknown ticket */
+#define DDKS_EUNSUPPORTED (-8)  /* valid input that the selected kernel path cannot take */
+
+typedef enum { DDKS_F32 = 0, DDKS_F64 = 1 } ddks_dtype;
+
+/* kernel paths for the orthant counts (DDKS_PATH_AUTO lets the autotuner pick) */
+typedef enum {
+  DDKS_PATH_AUTO = 0,
+  DDKS_PATH_REGISTER = 1,  /* register-resident packed counters, SWAR compares (d <= 4) */
+  DDKS_PATH_LANE = 2,      /* lane-private shared-memory histograms (d <= 8) */
+  DDKS_PATH_WARP = 3,      /* one shared-memory histogram per warp and origin (d <= 13) */
+  DDKS_PATH_SORT = 4       /* per-origin sort of codes and segmented counts (any d) */
+} ddks_path;
+
+typedef struct {
+  int32_t device;             /* CUDA device ordinal; -1 = the current device */
+  int32_t path;               /* a ddks_path; DDKS_PATH_AUTO by default */
+  uint64_t hbm_budget_bytes;  /* serving: device bytes the resident requests may hold (0 = 8 GiB) */
+  int32_t max_batch;          /* serving: most requests per device batch (0 = 64) */
+  int32_t wait_limit_ms;      /* bound on any host or device wait (0 = 10000) */
+  const char* tune_cache;     /* autotuner cache file (NULL = $DDKS_TUNE_CACHE, else none) */
+} ddks_config;
+
+typedef struct {
+  uint64_t num_max;        /* max over origins and orthants of |cP*NT - cT*NP| */
+  uint64_t denom;          /* NP*NT */
+  double D;                /* num_max / denom */
+  int64_t argmax_origin;   /* see conventions above; -1 if the origin range is empty */
+  int32_t argmax_orthant;
+  int32_t status;          /* DDKS_OK, or the error of the call that produced it */
+} ddks_result;
+
+typedef struct ddks_ctx ddks_ctx;
+
+/* Fill cfg with the defaults listed in ddks_config. */
+void ddks_config_default(ddks_config* cfg);
+
+/* Create a context on cfg->device (NULL cfg = defaults).  The context owns all
+   device scratch; it grows on demand and is freed by ddks_ctx_destroy. */
+int ddks_ctx_create(const ddks_config* cfg, ddks_ctx** out);
+int ddks_ctx_destroy(ddks_ctx* ctx);
+
+/*
+ * Exact ddKS of P (NP x d) and T (NT x d): Sec. 2.1, Eq. (ddks_tensor_definition),
+ * with the ">=" split of Eq. (g) and the normalisation of Eq. (abs_difference).
+ * Writes out->num_max, denom, D, argmax_origin, argmax_orthant.
+ */
+int ddks_distance(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT,
+                  int32_t d, int32_t dtype, void* stream, ddks_result* out);
+
+/*
+ * The same statistic restricted to the pooled origins [o_begin, o_end): the
+ * building block of an origin-sharded (multi-GPU) computation, where the
+ * shards' num_max are combined with max and the argmax is the lowest origin.
+ * per_origin (optional, device or host, o_end - o_begin entries) receives
+ * each origin's maximum over orthants.
+ */
+int ddks_distance_range(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT,
+                        int32_t d, int32_t dtype, int64_t o_begin, int64_t o_end,
+                        uint64_t* per_origin, void* stream, ddks_result* out);
+
+/*
+ * Permutation test (Sec. 4.2): the observed statistic, then B relabellings of
+ * the pooled sample.  Relabelling b puts into P the NP pooled points with the
+ * smallest (key, index), key(b, i) = word (i mod 4) of Philox4x64-10 with
+ * counter (i / 4, b, 0, 0) and key (seed, 0) (Salmon et al., SC 2011).
+ * perm_num_max (optional host array of B) receives each relabelling's num_max;
+ * p_value = (1 + #{b : num_b >= num_obs}) / (1 + B).
+ * All B relabellings run as one batched launch; 0 <= B <= 2^20.
+ */
+int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT,
+                          int32_t d, int32_t dtype, int32_t B, uint64_t seed, void* stream,
+                          ddks_result* observed, uint64_t* perm_num_max, double* p_value);
+
+/*
+ * Analytic significance (Sec. 3, Eq. ddks_significance) of a statistic
+ * num_max for these samples: S = 1 - prod over every pooled origin k and
+ * orthant j of p(delta <= D; lam_kj), where p(delta <= D; lam) sums
+ * Bi(nP; NP, lam) * Bi(nT; NT, lam) (Eq. binomial_probability) over all
+ * (nP, nT) with |nP*NT - nT*NP| <= num_max, and lam_kj comes from that cell's
+ * T count cT: (cT + 1)/(NT + 2) when estimator = 1 (Bayes, uniform prior),
+ * cT/NT when estimator = 0.  model = 1 uses the Poisson pmf with mean m*lam
+ * in place of the binomial (the large-sample variant of Sec. 3).
+ * d <= 16.  S and log_prod (= log of the product) are written on the host.
+ */
+int ddks_significance(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT,
+                      int32_t d, int32_t dtype, uint64_t num_max, int32_t estimator,
+                      int32_t model, void* stream, double* S, double* log_prod);
+
+/*
+ * Many independent problems of different sizes and dimensions in one
+ * persistent launch: CTAs pull (problem, origin tile) work units from a
+ * device counter.  Arrays have count entries; P[i], T[i] follow the
+ * conventions above (all of one dtype, all host or all device); out[i]
+ * receives problem i's result.
+ */
+int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, const int64_t* NP,
+                        const void* const* T, const int64_t* NT, const int32_t* d,
+                        int32_t dtype, void* stream, ddks_result* out);
+
+/*
+ * Serving: submit copies the inputs into library memory (the caller may free
+ * them on return) and queues the request; a scheduler thread admits queued
+ * requests while their device footprint fits cfg.hbm_budget_bytes and runs
+ * the admitted ones together, so requests that arrive while others run join
+ * the next device batch.  A request larger than the whole budget is refused
+ * with DDKS_ENOMEM.  poll returns DDKS_OK with out filled, DDKS_PENDING, or
+ * an error; timeout_us bounds how long poll waits (0 = do not wait).
+ * A ticket is released once poll has returned its result.
+ */
+int ddks_submit(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT, int32_t d,
+                int32_t dtype, uint64_t* ticket);
+int ddks_poll(ddks_ctx* ctx, uint64_t ticket, int32_t timeout_us, ddks_result* out);
+
+typedef struct {
+  uint64_t submitted, admitted, completed, rejected;
+  uint64_t batches;            /* device batches launched by the scheduler */
+  uint64_t bytes_resident;     /* device bytes held by admitted requests now */
+  uint64_t bytes_resident_peak;
+  uint64_t kernel_launches;    /* kernels launched by this context so far */
+} ddks_stats;
+
+int ddks_ctx_stats(ddks_ctx* ctx, ddks_stats* out);
+
+/*
+ * Stage timing.  When enabled, every distance call records CUDA events on its
+ * stream around its stages; ddks_stage_times then returns the last call's
+ * durations in milliseconds: encode (K0: keys, sort, ranks), count (the orthant
+ * count kernel), reduce (max over origins).  Enabling it adds event records,
+ * never extra synchronisation beyond the call's own.
+ */
+int ddks_set_stage_timing(ddks_ctx* ctx, int32_t enable);
+int ddks_stage_times(ddks_ctx* ctx, float* encode_ms, float* count_ms, float* reduce_ms);
+
+/* Human-readable text for a return code. */
+const char* ddks_strerror(int code);
+
+/* The last CUDA error string seen by this context (empty if none). */
+const char* ddks_last_cuda_error(ddks_ctx* ctx);
+
+/* Library version, e.g. "0.1.0". */
+const char* ddks_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDKS_H_ */

@@ -1,0 +1,91 @@
+// ddks_host.h -- host-side context and helpers shared by the library's .cu files.
+#pragma once
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ddks.h"
+
+struct ddks_ctx;
+
+// A context-owned device buffer that grows on demand (never shrinks).
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int reserve(ddks_ctx* ctx, size_t n);
+  void release();
+};
+
+// Kernel configuration chosen for one problem shape.
+struct ddks_plan {
+  int path = DDKS_PATH_AUTO;
+  int threads = 256;  // lane path: threads per CTA (one origin each)
+  int warps = 8;      // warp path: warps per CTA (one origin each)
+  int reg_r = 4;      // register path: origins per thread
+  int reg_warps = 4;  // register path: warps per CTA
+};
+
+struct ServeState;  // serve.cu
+
+struct ddks_ctx {
+  ddks_config cfg{};
+  int device = 0;
+  int num_sms = 152;
+  std::string last_err;
+  uint64_t launches = 0;
+  // scratch of the synchronous entry points
+  DevBuf inP, inT, keys, tk1, tk2, ti1, ti2, rank, sidx0, best, bestj, out3, flags;
+  DevBuf reg_words, reg_meta;                   // register path
+  DevBuf perm_keys, perm_labels, perm_best, perm_codes;  // permutation test
+  DevBuf sig_cells, sig_logp;                   // significance
+  DevBuf batch_desc, batch_work;                // batched launch
+  unsigned long long* h_out = nullptr;          // pinned, 64 entries
+  // stage timing (ddks_set_stage_timing)
+  bool stage_timing = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  float stage_ms[3] = {0, 0, 0};
+  // autotuner: key -> plan
+  std::string tune_cache_path;
+  std::map<std::string, ddks_plan> tune;
+  std::mutex tune_mu;
+  // serving
+  ServeState* serve = nullptr;  // owned; freed by ddks_serve_shutdown
+
+  std::vector<DevBuf*> all_bufs() {
+    return {&inP, &inT, &keys, &tk1, &tk2, &ti1, &ti2, &rank, &sidx0, &best, &bestj, &out3,
+            &flags, &reg_words, &reg_meta, &perm_keys, &perm_labels, &perm_best, &perm_codes,
+            &sig_cells, &sig_logp, &batch_desc, &batch_work};
+  }
+};
+
+int ctx_cuda_fail(ddks_ctx* ctx, cudaError_t e, const char* where);
+bool ddks_is_device_ptr(const void* p);
+int ddks_check_problem(const void* P, int64_t NP, const void* T, int64_t NT, int32_t d, int32_t dtype);
+int ddks_stage_inputs(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT,
+                      int32_t d, int32_t dtype, cudaStream_t st, const void** dP, const void** dT);
+int ddks_encode_problem(ddks_ctx* ctx, const void* dP, int64_t NP, const void* dT, int64_t NT,
+                        int32_t d, int32_t dtype, cudaStream_t st, bool want_sorted0);
+int ddks_count_origins(ddks_ctx* ctx, int64_t NP, int64_t NT, int32_t d, int64_t ob, int64_t oe,
+                       uint64_t* best, int32_t* bestj, cudaStream_t st);
+
+// tune.cu
+int ddks_select_path(ddks_ctx* ctx, int64_t NP, int64_t NT, int32_t d, ddks_plan* plan);
+void ddks_tune_load(ddks_ctx* ctx);
+
+// count_register.cu
+cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N, int64_t NP,
+                                 int64_t NT, int d, int64_t ob, int64_t oe, uint64_t* best,
+                                 int32_t* bestj, cudaStream_t st, const ddks_plan& plan);
+bool ddks_register_supported(int d, int64_t NP, int64_t NT);
+
+// serve.cu
+void ddks_serve_shutdown(ddks_ctx* ctx);
+void ddks_serve_fill_stats(ddks_ctx* ctx, ddks_stats* out);

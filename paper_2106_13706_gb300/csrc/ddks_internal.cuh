@@ -1,0 +1,73 @@
+// ddks_internal.cuh -- device-side declarations shared by the library's .cu files.
+//
+// Data layout in device memory (one problem):
+//   pooled sample X = [P; T], N = NP + NT points, P rows first.
+//   keys   u64 [d][N]   order-preserving integer image of each coordinate
+//   rank   u32 [d][N]   rank[m][i] = #{j : X[j][m] < X[i][m]}  (min-rank), so
+//                       X[i][m] >= X[k][m]  <=>  rank[m][i] >= rank[m][k]   (Eq. g)
+//   best   u64 [no]     each origin's max over orthants of |cP*NT - cT*NP|
+//   bestj  i32 [no]     the lowest orthant code reaching it
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define DDKS_DEV __device__ __forceinline__
+
+namespace ddks {
+
+constexpr int kMaxD = 30;
+
+// error flags raised by kernels and read back by the host
+enum : unsigned { kFlagNaN = 1u, kFlagTimeout = 2u, kFlagBounds = 4u };
+
+// Order-preserving image of a float as an unsigned integer: x <= y (IEEE, no
+// NaN) <=> key(x) <= key(y).  -0.0 is mapped like +0.0 so the two compare equal.
+DDKS_DEV uint64_t order_key(float v) {
+  uint32_t u = __float_as_uint(v == 0.0f ? 0.0f : v);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return (uint64_t)u;
+}
+DDKS_DEV uint64_t order_key(double v) {
+  uint64_t u = (uint64_t)__double_as_longlong(v == 0.0 ? 0.0 : v);
+  u = (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+  return u;
+}
+
+// |a*NT - b*NP| for counts a <= NP, b <= NT with NP*NT < 2^62 (no overflow).
+DDKS_DEV uint64_t numer(uint64_t a, uint64_t b, uint64_t NP, uint64_t NT) {
+  uint64_t x = a * NT, y = b * NP;
+  return x > y ? x - y : y - x;
+}
+
+}  // namespace ddks
+
+// Launch wrappers implemented in the .cu files (all enqueue on `st`).
+struct DdksProblemDev {
+  const uint32_t* rank;  // [d][N]
+  int64_t N, NP, NT;
+  int32_t d;
+};
+
+cudaError_t ddks_launch_encode(const void* P, const void* T, int64_t NP, int64_t NT, int d,
+                               int is_f64, uint64_t* keys, unsigned* flags, cudaStream_t st);
+cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int d, uint64_t* tmp_keys,
+                             uint32_t* tmp_idx, uint64_t* tmp_keys2, uint32_t* tmp_idx2,
+                             uint32_t* rank, uint32_t* sorted_idx0, cudaStream_t st,
+                             int* launches);
+size_t ddks_rank_scratch_elems(int64_t N);
+
+cudaError_t ddks_launch_lane(const uint32_t* rank, int64_t N, int64_t NP, int64_t NT, int d,
+                             int64_t o_begin, int64_t o_end, uint64_t* best, int32_t* bestj,
+                             cudaStream_t st, int threads);
+cudaError_t ddks_launch_warp(const uint32_t* rank, int64_t N, int64_t NP, int64_t NT, int d,
+                             int64_t o_begin, int64_t o_end, uint64_t* best, int32_t* bestj,
+                             cudaStream_t st, int warps);
+cudaError_t ddks_launch_sort(const uint32_t* rank, int64_t N, int64_t NP, int64_t NT, int d,
+                             int64_t o_begin, int64_t o_end, uint64_t* best, int32_t* bestj,
+                             cudaStream_t st);
+cudaError_t ddks_launch_reduce(const uint64_t* best, const int32_t* bestj, int64_t no,
+                               int64_t o_begin, unsigned long long* out3, cudaStream_t st);
+
+bool ddks_lane_supported(int d, int64_t NP, int64_t NT, int threads);
+bool ddks_warp_supported(int d, int64_t NP, int64_t NT);
+bool ddks_sort_supported(int d, int64_t N);

@@ -1,0 +1,196 @@
+// encode.cu -- K0: ingest and rank-encode the pooled sample.
+//
+// The statistic only ever asks whether x_m >= o_m (Sec. 2.2.1, Eq. g), so each
+// coordinate can be replaced by any strictly order-preserving integer.  K0 maps
+// every coordinate to an order-preserving 64-bit key (NaN raises a flag),
+// sorts each dimension's (key, index) pairs, and replaces every coordinate by
+// its min-rank  #{j : key_j < key_i}.  Then x_m >= o_m <=> rank(x)_m >= rank(o)_m
+// exactly, ties included, and every later kernel compares 32-bit integers
+// whatever the input type.
+//
+// Sort: bitonic sort of 2048-element chunks in shared memory, then merge passes
+// in which every element finds its output slot by binary search in the partner
+// run (pairs are unique because the index breaks ties).  Rank: one lower_bound
+// per element in its dimension's sorted keys.
+#include "ddks_internal.cuh"
+
+namespace {
+
+constexpr int kChunk = 2048;
+constexpr int kChunkThreads = 1024;
+
+template <typename V>
+__global__ void k_encode(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64_t NT,
+                         int d, uint64_t* __restrict__ keys, unsigned* __restrict__ flags) {
+  const int64_t N = NP + NT;
+  const int64_t total = N * d;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / d;
+    const int m = (int)(e - i * d);
+    const V v = i < NP ? P[e] : T[e - NP * d];
+    if (v != v) atomicOr(flags, ddks::kFlagNaN);
+    keys[(int64_t)m * N + i] = ddks::order_key(v);
+  }
+}
+
+DDKS_DEV bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+// grid: (chunks, d).  Sorts chunk blockIdx.x of dimension blockIdx.y.
+__global__ void __launch_bounds__(kChunkThreads)
+k_chunk_sort(const uint64_t* __restrict__ keys, int64_t N, int64_t Npad,
+             uint64_t* __restrict__ out_k, uint32_t* __restrict__ out_i) {
+  __shared__ uint64_t sk[kChunk];
+  __shared__ uint32_t si[kChunk];
+  const int m = blockIdx.y;
+  const int64_t base = (int64_t)blockIdx.x * kChunk;
+  for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
+    const int64_t g = base + t;
+    if (g < N) {
+      sk[t] = keys[(int64_t)m * N + g];
+      si[t] = (uint32_t)g;
+    } else {
+      sk[t] = ~0ull;          // pads sort last; the index keeps pairs unique
+      si[t] = (uint32_t)g;
+    }
+  }
+  __syncthreads();
+  for (int size = 2; size <= kChunk; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < kChunk / 2; t += blockDim.x) {
+        const int lo = 2 * t - (t & (stride - 1));
+        const int hi = lo + stride;
+        const bool asc = ((lo & size) == 0);
+        const uint64_t ka = sk[lo], kb = sk[hi];
+        const uint32_t ia = si[lo], ib = si[hi];
+        const bool swap = asc ? pair_less(kb, ib, ka, ia) : pair_less(ka, ia, kb, ib);
+        if (swap) {
+          sk[lo] = kb; sk[hi] = ka;
+          si[lo] = ib; si[hi] = ia;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
+    out_k[(int64_t)m * Npad + base + t] = sk[t];
+    out_i[(int64_t)m * Npad + base + t] = si[t];
+  }
+}
+
+// One merge pass over runs of length L (Npad is a multiple of kChunk <= L).
+// grid-stride over (d * Npad) elements.
+__global__ void k_merge_pass(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ in_i,
+                             uint64_t* __restrict__ out_k, uint32_t* __restrict__ out_i,
+                             int64_t Npad, int d, int64_t L) {
+  const int64_t total = Npad * d;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = e / Npad;
+    const int64_t p = e - m * Npad;
+    const uint64_t* K = in_k + m * Npad;
+    const uint32_t* I = in_i + m * Npad;
+    const uint64_t key = K[p];
+    const uint32_t idx = I[p];
+    const int64_t r = p / L;
+    const int64_t a = p - r * L;
+    const int64_t ps = (r ^ 1) * L;  // partner run start
+    int64_t dst;
+    if (ps >= Npad) {
+      dst = p;
+    } else {
+      const int64_t plen = (Npad - ps) < L ? (Npad - ps) : L;
+      // number of partner elements strictly below (key, idx)
+      int64_t lo = 0, hi = plen;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (pair_less(K[ps + mid], I[ps + mid], key, idx)) lo = mid + 1; else hi = mid;
+      }
+      const int64_t start = (r < (r ^ 1) ? r : (r ^ 1)) * L;
+      dst = start + a + lo;
+    }
+    out_k[m * Npad + dst] = key;
+    out_i[m * Npad + dst] = idx;
+  }
+}
+
+// rank[m][i] = #{j : key_j < key_i}, by lower_bound in the sorted keys of m.
+__global__ void k_rank(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ sorted_k,
+                       int64_t N, int64_t Npad, int d, uint32_t* __restrict__ rank) {
+  const int64_t total = N * d;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = e / N;
+    const uint64_t key = keys[e];
+    const uint64_t* S = sorted_k + m * Npad;
+    int64_t lo = 0, hi = N;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (S[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    rank[e] = (uint32_t)lo;
+  }
+}
+
+__global__ void k_copy_idx(const uint32_t* __restrict__ sorted_i, int64_t N, uint32_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = sorted_i[i];
+}
+
+int grid_for(int64_t work, int threads) {
+  int64_t g = (work + threads - 1) / threads;
+  if (g > 152 * 64) g = 152 * 64;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+cudaError_t ddks_launch_encode(const void* P, const void* T, int64_t NP, int64_t NT, int d,
+                               int is_f64, uint64_t* keys, unsigned* flags, cudaStream_t st) {
+  const int64_t total = (NP + NT) * d;
+  const int threads = 256;
+  if (is_f64)
+    k_encode<double><<<grid_for(total, threads), threads, 0, st>>>(
+        (const double*)P, (const double*)T, NP, NT, d, keys, flags);
+  else
+    k_encode<float><<<grid_for(total, threads), threads, 0, st>>>(
+        (const float*)P, (const float*)T, NP, NT, d, keys, flags);
+  return cudaGetLastError();
+}
+
+size_t ddks_rank_scratch_elems(int64_t N) {
+  const int64_t chunks = (N + kChunk - 1) / kChunk;
+  return (size_t)(chunks * kChunk);
+}
+
+// keys: [d][N].  tmp buffers: d * Npad elements each.  rank: [d][N].
+// sorted_idx0 (optional): the pooled indices in increasing (rank_0, index) order.
+cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int d, uint64_t* tmp_keys,
+                             uint32_t* tmp_idx, uint64_t* tmp_keys2, uint32_t* tmp_idx2,
+                             uint32_t* rank, uint32_t* sorted_idx0, cudaStream_t st,
+                             int* launches) {
+  const int64_t Npad = (int64_t)ddks_rank_scratch_elems(N);
+  const int64_t chunks = Npad / kChunk;
+  dim3 g((unsigned)chunks, (unsigned)d);
+  k_chunk_sort<<<g, kChunkThreads, 0, st>>>(keys, N, Npad, tmp_keys, tmp_idx);
+  int n = 1;
+  uint64_t *ck = tmp_keys, *nk = tmp_keys2;
+  uint32_t *ci = tmp_idx, *ni = tmp_idx2;
+  for (int64_t L = kChunk; L < Npad; L <<= 1) {
+    k_merge_pass<<<grid_for(Npad * d, 256), 256, 0, st>>>(ck, ci, nk, ni, Npad, d, L);
+    ++n;
+    uint64_t* tk = ck; ck = nk; nk = tk;
+    uint32_t* ti = ci; ci = ni; ni = ti;
+  }
+  k_rank<<<grid_for(N * d, 256), 256, 0, st>>>(keys, ck, N, Npad, d, rank);
+  ++n;
+  if (sorted_idx0) {
+    k_copy_idx<<<grid_for(N, 256), 256, 0, st>>>(ci, N, sorted_idx0);
+    ++n;
+  }
+  if (launches) *launches += n;
+  return cudaGetLastError();
+}

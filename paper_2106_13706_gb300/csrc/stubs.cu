@@ -1,0 +1,33 @@
+// stubs.cu -- entry points whose kernels are not built yet report
+// DDKS_EUNSUPPORTED instead of computing anything on the host.
+#include "ddks_host.h"
+#include "ddks_internal.cuh"
+
+cudaError_t ddks_launch_register(ddks_ctx*, const uint32_t*, int64_t, int64_t, int64_t, int,
+                                 int64_t, int64_t, uint64_t*, int32_t*, cudaStream_t,
+                                 const ddks_plan&) {
+  return cudaErrorNotSupported;
+}
+bool ddks_register_supported(int, int64_t, int64_t) { return false; }
+
+int ddks_permutation_test(ddks_ctx*, const void*, int64_t, const void*, int64_t, int32_t, int32_t,
+                          int32_t, uint64_t, void*, ddks_result*, uint64_t*, double*) {
+  return DDKS_EUNSUPPORTED;
+}
+int ddks_significance(ddks_ctx*, const void*, int64_t, const void*, int64_t, int32_t, int32_t,
+                      uint64_t, int32_t, int32_t, void*, double*, double*) {
+  return DDKS_EUNSUPPORTED;
+}
+int ddks_batch_distance(ddks_ctx*, int32_t, const void* const*, const int64_t*, const void* const*,
+                        const int64_t*, const int32_t*, int32_t, void*, ddks_result*) {
+  return DDKS_EUNSUPPORTED;
+}
+int ddks_submit(ddks_ctx*, const void*, int64_t, const void*, int64_t, int32_t, int32_t, uint64_t*) {
+  return DDKS_EUNSUPPORTED;
+}
+int ddks_poll(ddks_ctx*, uint64_t, int32_t, ddks_result*) { return DDKS_EUNSUPPORTED; }
+void ddks_serve_shutdown(ddks_ctx*) {}
+void ddks_serve_fill_stats(ddks_ctx*, ddks_stats* out) {
+  out->submitted = out->admitted = out->completed = out->rejected = 0;
+  out->batches = out->bytes_resident = out->bytes_resident_peak = 0;
+}

@@ -1,0 +1,46 @@
+"""The C-ABI library builds, loads and exports every symbol include/ddks.h
+declares (no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+
+import pytest
+
+import paper_2106_13706_gb300 as pkg
+from paper_2106_13706_gb300 import build as bld
+
+
+@pytest.fixture(scope="module")
+def lib():
+    bld.build()
+    return pkg.load()
+
+
+def test_header_declares_the_boundary():
+    names = pkg.declared_symbols()
+    for n in ["ddks_ctx_create", "ddks_ctx_destroy", "ddks_distance", "ddks_distance_range",
+              "ddks_permutation_test", "ddks_significance", "ddks_batch_distance", "ddks_submit",
+              "ddks_poll", "ddks_strerror", "ddks_ctx_stats", "ddks_config_default"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for n in pkg.declared_symbols():
+        assert hasattr(lib, n), n
+        assert isinstance(getattr(lib, n), ctypes._CFuncPtr)
+
+
+def test_strerror_and_version(lib):
+    assert pkg.ddks_strerror(0) == "ok"
+    assert "NaN" in pkg.ddks_strerror(-2)
+    assert pkg.ddks_version().count(".") == 2
+
+
+def test_argument_errors_need_no_gpu(lib):
+    # argument checks happen before any CUDA call
+    r = pkg.binding.ddks_result()
+    assert lib.ddks_distance(None, None, 1, None, 1, 3, 0, None, ctypes.byref(r)) == -1
+    assert lib.ddks_ctx_destroy(None) == -1
+
+
+def test_library_is_in_tree():
+    assert os.path.dirname(pkg.binding.LIB_PATH) == os.path.dirname(bld.__file__)
