@@ -254,7 +254,7 @@ int ddks_count_origins(ddks_ctx* ctx, int64_t NP, int64_t NT, int32_t d, int64_t
       e = ddks_launch_register(ctx, rank, N, NP, NT, d, ob, oe, best, bestj, st, plan);
       break;
     case DDKS_PATH_LANE:
-      e = ddks_launch_lane(rank, N, NP, NT, d, ob, oe, best, bestj, st, plan.threads);
+      e = ddks_launch_lane(rank, N, NP, NT, d, ob, oe, best, bestj, st, plan.threads, ctx->num_sms);
       ctx->launches += 1;
       break;
     case DDKS_PATH_WARP:

@@ -29,8 +29,7 @@ struct ddks_plan {
   int path = DDKS_PATH_AUTO;
   int threads = 256;  // lane path: threads per CTA (one origin each)
   int warps = 8;      // warp path: warps per CTA (one origin each)
-  int reg_r = 4;      // register path: origins per thread
-  int reg_warps = 4;  // register path: warps per CTA
+  int reg_slices = 0;  // register path: threads sharing one origin group (0 = by size)
 };
 
 struct ServeState;  // serve.cu

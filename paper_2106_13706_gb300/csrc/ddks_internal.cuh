@@ -58,7 +58,7 @@ size_t ddks_rank_scratch_elems(int64_t N);
 
 cudaError_t ddks_launch_lane(const uint32_t* rank, int64_t N, int64_t NP, int64_t NT, int d,
                              int64_t o_begin, int64_t o_end, uint64_t* best, int32_t* bestj,
-                             cudaStream_t st, int threads);
+                             cudaStream_t st, int threads, int num_sms);
 cudaError_t ddks_launch_warp(const uint32_t* rank, int64_t N, int64_t NP, int64_t NT, int d,
                              int64_t o_begin, int64_t o_end, uint64_t* best, int32_t* bestj,
                              cudaStream_t st, int warps);

@@ -3,13 +3,6 @@
 #include "ddks_host.h"
 #include "ddks_internal.cuh"
 
-cudaError_t ddks_launch_register(ddks_ctx*, const uint32_t*, int64_t, int64_t, int64_t, int,
-                                 int64_t, int64_t, uint64_t*, int32_t*, cudaStream_t,
-                                 const ddks_plan&) {
-  return cudaErrorNotSupported;
-}
-bool ddks_register_supported(int, int64_t, int64_t) { return false; }
-
 int ddks_permutation_test(ddks_ctx*, const void*, int64_t, const void*, int64_t, int32_t, int32_t,
                           int32_t, uint64_t, void*, ddks_result*, uint64_t*, double*) {
   return DDKS_EUNSUPPORTED;

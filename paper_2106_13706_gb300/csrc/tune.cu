@@ -77,8 +77,7 @@ void ddks_tune_load(ddks_ctx* ctx) {
   if (!f) return;
   char key[64];
   ddks_plan p;
-  while (std::fscanf(f, "%63s %d %d %d %d %d", key, &p.path, &p.threads, &p.warps, &p.reg_r,
-                     &p.reg_warps) == 6) {
+  while (std::fscanf(f, "%63s %d %d %d %d", key, &p.path, &p.threads, &p.warps, &p.reg_slices) == 5) {
     ctx->tune[key] = p;
   }
   std::fclose(f);

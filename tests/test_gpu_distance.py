@@ -47,6 +47,8 @@ PATHS = [pkg.PATH_LANE, pkg.PATH_WARP, pkg.PATH_SORT]
 
 def _paths_for(d, N):
     out = []
+    if 2 <= d <= 4:
+        out.append(pkg.PATH_REGISTER)
     if d <= 8:
         out.append(pkg.PATH_LANE)
     if d <= 13:
@@ -173,7 +175,7 @@ def test_wide_counters_sampled(torch):
     P = rng.standard_normal((70000, 2)).astype(np.float32)
     T = (rng.standard_normal((3000, 2)) + 0.1).astype(np.float32)
     ranges = [(0, 64), (69990, 70060), (72936, 73000)]
-    for path in (pkg.PATH_LANE, pkg.PATH_WARP):
+    for path in (pkg.PATH_REGISTER, pkg.PATH_LANE, pkg.PATH_WARP):
         with _ctx(path) as c:
             for a, b in ranges:
                 got = c.distance_range(_dev(torch, P), _dev(torch, T), a, b, per_origin=True)
@@ -185,7 +187,7 @@ def test_wide_counters_sampled(torch):
 def test_config1_full(torch):
     P, T = wl.CONFIGS["cfg1_d3_200x200_f32"]()
     ref = orc.ddks(P, T)
-    for path in (pkg.PATH_AUTO, pkg.PATH_LANE, pkg.PATH_WARP, pkg.PATH_SORT):
+    for path in (pkg.PATH_AUTO, pkg.PATH_REGISTER, pkg.PATH_LANE, pkg.PATH_WARP, pkg.PATH_SORT):
         with _ctx(path) as c:
             _same(c.distance(_dev(torch, P), _dev(torch, T)), ref)
 
@@ -201,7 +203,24 @@ def test_config3_full(torch):
 def test_config2_full(torch):
     P, T = wl.CONFIGS["cfg2_d4_20000x20000_f32_ties"]()
     ref = orc.ddks(P, T, per_origin=True)
-    with _ctx() as c:
-        got = c.distance_range(_dev(torch, P), _dev(torch, T), 0, 40000, per_origin=True)
-    assert np.array_equal(got["per_origin"], ref["per_origin"])
-    _same(got, ref)
+    for path in (pkg.PATH_AUTO, pkg.PATH_REGISTER, pkg.PATH_LANE):
+        with _ctx(path) as c:
+            got = c.distance_range(_dev(torch, P), _dev(torch, T), 0, 40000, per_origin=True)
+        assert np.array_equal(got["per_origin"], ref["per_origin"])
+        _same(got, ref)
+
+
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_register_path_rerank_tiles(torch, d):
+    # N > 32768 re-ranks dims 1..d-1 per tile of origins; ties in every
+    # dimension (small integer grid) stress the window between phases
+    rng = np.random.default_rng(40 + d)
+    P = rng.integers(0, 50, size=(20000, d)).astype(np.float32)
+    T = (rng.integers(0, 50, size=(17000, d)) + (rng.random((17000, d)) < 0.3)).astype(np.float32)
+    ranges = [(0, 2000), (19000, 23000), (36000, 37000)]
+    with _ctx(pkg.PATH_REGISTER) as c:
+        for a, b in ranges:
+            got = c.distance_range(_dev(torch, P), _dev(torch, T), a, b, per_origin=True)
+            ref = orc.ddks(P, T, origins=(a, b), per_origin=True)
+            assert np.array_equal(got["per_origin"], ref["per_origin"])
+            _same(got, ref)
