@@ -139,7 +139,7 @@ int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* 
  * T count cT: (cT + 1)/(NT + 2) when estimator = 1 (Bayes, uniform prior),
  * cT/NT when estimator = 0.  model = 1 uses the Poisson pmf with mean m*lam
  * in place of the binomial (the large-sample variant of Sec. 3).
- * d <= 16.  S and log_prod (= log of the product) are written on the host.
+ * d <= 13.  S and log_prod (= log of the product) are written on the host.
  */
 int ddks_significance(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT,
                       int32_t d, int32_t dtype, uint64_t num_max, int32_t estimator,

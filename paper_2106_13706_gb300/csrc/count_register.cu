@@ -292,11 +292,14 @@ DDKS_DEV void run_points(const uint2* __restrict__ tw, int a, int b, const uint3
   }
 }
 
+// Work unit u = (origin block u / C, point chunk u % C): OC origins against the
+// list positions [chunk * CL, (chunk + 1) * CL).  Counts are added into the
+// global gcnt[q][sample][phase][bin] when the unit ends.
 template <int DS>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_register(const uint2* __restrict__ words, const OriginMeta* __restrict__ meta, int64_t no,
-           int64_t N, int64_t NP, int64_t NT, int64_t ob, int S, int TS,
-           uint64_t* __restrict__ best, int32_t* __restrict__ bestj) {
+           int64_t N, int64_t NP, int S, int TS, int C, int64_t CL,
+           uint32_t* __restrict__ gcnt) {
   extern __shared__ __align__(16) uint32_t sm[];
   const int G = kThreads / S;          // origin groups per CTA
   const int OC = G * kR;               // origins per CTA
@@ -304,8 +307,11 @@ k_register(const uint2* __restrict__ words, const OriginMeta* __restrict__ meta,
   uint32_t* cnt = sm + 2 * kTP;                               // [OC][2 samples][2 phases][8 bins]
   const int tid = threadIdx.x;
   const int g = tid / S, s = tid - g * S;
-  const int64_t q0 = (int64_t)blockIdx.x * OC;
-  const int64_t t = q0 / TS;           // re-rank tile (every CTA lies inside one)
+  const int64_t blk = blockIdx.x / C;
+  const int64_t c0 = (int64_t)(blockIdx.x % C) * CL;
+  const int64_t c1 = (c0 + CL) < N ? (c0 + CL) : N;
+  const int64_t q0 = blk * OC;
+  const int64_t t = q0 / TS;           // re-rank tile (every block lies inside one)
   const uint2* tw_all = words + t * N;
   for (int i = tid; i < OC * 32; i += kThreads) cnt[i] = 0;
   uint32_t oA[kR], oB[kR], sP[kR], sT[kR];
@@ -324,8 +330,8 @@ k_register(const uint2* __restrict__ words, const OriginMeta* __restrict__ meta,
 #pragma unroll
   for (int r = 0; r < kR; ++r) acc[r] = Acc{0, 0, 0, 0, 0, 0};
   uint32_t* mycnt = cnt + (g * kR) * 32;  // origin r of this thread: mycnt + r*32 (+16 for T)
-  for (int64_t base = 0; base < N; base += kTP) {
-    const int cntp = (int)((N - base) < kTP ? (N - base) : kTP);
+  for (int64_t base = c0; base < c1; base += kTP) {
+    const int cntp = (int)((c1 - base) < kTP ? (c1 - base) : kTP);
     __syncthreads();
     for (int i = tid; i < cntp; i += kThreads) tile[i] = tw_all[base + i];
     __syncthreads();
@@ -362,14 +368,23 @@ k_register(const uint2* __restrict__ words, const OriginMeta* __restrict__ meta,
     }
   }
   __syncthreads();
-  // one thread per origin: 16 orthants from [sample][phase][bin]
-  for (int ol = tid; ol < OC; ol += kThreads) {
-    const int64_t q = q0 + ol;
-    if (q >= no) continue;
-    const uint32_t* c = cnt + ol * 32;
+  for (int i = tid; i < OC * 32; i += kThreads) {
+    const int64_t q = q0 + i / 32;
+    const uint32_t v = cnt[i];
+    if (q < no && v) atomicAdd(&gcnt[q * 32 + (i & 31)], v);
+  }
+}
+
+// one thread per origin: its 2 * 2^DS orthants from gcnt[q][sample][phase][bin]
+__global__ void k_register_final(const uint32_t* __restrict__ gcnt, const OriginMeta* __restrict__ meta,
+                                 int64_t no, int64_t NP, int64_t NT, int64_t ob, int ds,
+                                 uint64_t* __restrict__ best, int32_t* __restrict__ bestj) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < no;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t* c = gcnt + q * 32;
     uint64_t bv = 0;
     int bj = 0;
-    const int nbin = 1 << DS;
+    const int nbin = 1 << ds;
     for (int code = 0; code < 2 * nbin; ++code) {
       const int ph = code & 1, bin = code >> 1;
       const uint64_t cp = c[ph * 8 + bin], ct = c[16 + ph * 8 + bin];
@@ -400,9 +415,8 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   const int ds = d - 1;
   const int64_t no = oe - ob;
   if (no <= 0) return cudaSuccess;
-  // slices per origin group: enough threads for ~32 resident warps per SM
-  int S = 1;
-  while (S < 16 && (no / kR) * S * 2 <= (int64_t)ctx->num_sms * 1024) S <<= 1;
+  // threads sharing one origin group (point slices inside a CTA tile)
+  int S = 8;
   if (plan.reg_slices > 0 && plan.reg_slices <= 16 && (plan.reg_slices & (plan.reg_slices - 1)) == 0)
     S = plan.reg_slices;  // tuned choice
   const int64_t TS = tile_size(S);
@@ -410,7 +424,8 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   const int64_t ntiles = direct ? 1 : (no + TS - 1) / TS;
   // scratch: listpos N, pprefix N+1, olist no, lut ntiles*ds*N (if !direct), words ntiles*N uint2,
   // meta no
-  const size_t n_u32 = (size_t)N + (size_t)N + 1 + (size_t)no + (direct ? 0 : (size_t)ntiles * ds * N);
+  const size_t n_u32 = (size_t)N + (size_t)N + 1 + (size_t)no + (direct ? 0 : (size_t)ntiles * ds * N) +
+                       (size_t)no * 32;
   int rc = ctx->reg_meta.reserve(ctx, n_u32 * 4 + (size_t)no * sizeof(OriginMeta) + 64);
   if (rc) return cudaErrorMemoryAllocation;
   rc = ctx->reg_words.reserve(ctx, (size_t)ntiles * N * sizeof(uint2));
@@ -418,7 +433,8 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   uint32_t* listpos = (uint32_t*)ctx->reg_meta.ptr;
   uint32_t* pprefix = listpos + N;
   uint32_t* olist = pprefix + N + 1;
-  uint32_t* lut = olist + no;
+  uint32_t* gcnt = olist + no;
+  uint32_t* lut = gcnt + no * 32;
   OriginMeta* meta = reinterpret_cast<OriginMeta*>(
       (reinterpret_cast<uintptr_t>(lut + (direct ? 0 : ntiles * ds * N)) + 15) & ~(uintptr_t)15);
   uint2* words = (uint2*)ctx->reg_words.ptr;
@@ -439,26 +455,39 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   n += 2;
   const int OC = (kThreads / S) * kR;
   const size_t smem = (size_t)kTP * sizeof(uint2) + (size_t)OC * 32 * 4;
-  const unsigned ctas = (unsigned)((no + OC - 1) / OC);
-  cudaError_t e = cudaSuccess;
+  const int64_t blocks = (no + OC - 1) / OC;
+  // point chunks per origin block: about 8 waves of 2 resident CTAs per SM,
+  // chunks of at least 2 tiles
+  const int64_t slots = (int64_t)ctx->num_sms * 2;
+  int64_t C = (8 * slots + blocks - 1) / blocks;
+  const int64_t cmax = (N + 2 * kTP - 1) / (2 * kTP);
+  if (C > cmax) C = cmax;
+  if (C < 1) C = 1;
+  const int64_t CL = (N + C - 1) / C;
+  C = (N + CL - 1) / CL;
+  cudaError_t e = cudaMemsetAsync(gcnt, 0, (size_t)no * 32 * 4, st);
+  if (e != cudaSuccess) return e;
+  const unsigned ctas = (unsigned)(blocks * C);
   switch (ds) {
     case 1:
       e = cudaFuncSetAttribute(k_register<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess)
-        k_register<1><<<ctas, kThreads, smem, st>>>(words, meta, no, N, NP, NT, ob, S, (int)TS, best, bestj);
+        k_register<1><<<ctas, kThreads, smem, st>>>(words, meta, no, N, NP, S, (int)TS, (int)C, CL, gcnt);
       break;
     case 2:
       e = cudaFuncSetAttribute(k_register<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess)
-        k_register<2><<<ctas, kThreads, smem, st>>>(words, meta, no, N, NP, NT, ob, S, (int)TS, best, bestj);
+        k_register<2><<<ctas, kThreads, smem, st>>>(words, meta, no, N, NP, S, (int)TS, (int)C, CL, gcnt);
       break;
     default:
       e = cudaFuncSetAttribute(k_register<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess)
-        k_register<3><<<ctas, kThreads, smem, st>>>(words, meta, no, N, NP, NT, ob, S, (int)TS, best, bestj);
+        k_register<3><<<ctas, kThreads, smem, st>>>(words, meta, no, N, NP, S, (int)TS, (int)C, CL, gcnt);
       break;
   }
-  n += 1;
+  if (e != cudaSuccess) return e;
+  k_register_final<<<grid(no), 256, 0, st>>>(gcnt, meta, no, NP, NT, ob, ds, best, bestj);
+  n += 2;
   ctx->launches += n;
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

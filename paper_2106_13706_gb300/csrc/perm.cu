@@ -1,0 +1,280 @@
+// perm.cu -- A7/A8: the permutation test (Sec. 4.2) as one batched launch.
+//
+// Relabelling b of the pooled sample puts into P the NP pooled points with the
+// smallest (key, index), key(b, i) = word (i mod 4) of Philox4x64-10 (Salmon,
+// Moraes, Dror, Shaw, SC 2011) with counter (i / 4, b, 0, 0) and key (seed, 0).
+//
+// K3 (k_perm_labels): one CTA per relabelling draws the N keys, sorts the
+//   (key, index) pairs in shared memory and sets bit b of the label words of
+//   the NP smallest: labels[i][b / 32] bit (b % 32) = [i in permuted P].
+// K4 (k_perm_count): the orthant code c(o, x) of a pair does not depend on the
+//   labels, so each CTA takes an origin, computes the N codes once into shared
+//   memory together with n(c) = #{x : c(o, x) = c}, and then counts, for every
+//   relabelling b, cP_b(c) = #{x in permuted P : c(o, x) = c} in lane-private
+//   shared histograms (warp w of a chunk owns 32 consecutive relabellings, so
+//   one label word per point serves the whole warp).  With cT_b = n - cP_b the
+//   numerator is |cP_b*NT - cT_b*NP| = |cP_b*N - n*NP|; each thread keeps the
+//   running maximum of its relabellings and finishes with one atomicMax.
+// K_pv (k_perm_pvalue): #{b : num_b >= num_obs}.
+#include "ddks_host.h"
+#include "ddks_internal.cuh"
+
+namespace {
+
+constexpr int kLabelThreads = 1024;
+constexpr int kMaxPermN = 16384;
+constexpr int kCountThreads = 256;
+constexpr int kPtsTile = 64;
+
+DDKS_DEV void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    const uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    const uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
+DDKS_DEV bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+// grid-stride over relabellings; dynamic smem: P2 keys (u64) + P2 indices (u32)
+__global__ void __launch_bounds__(kLabelThreads)
+k_perm_labels(int64_t N, int64_t NP, int B, uint64_t seed, int G, uint32_t* __restrict__ labels) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int P2 = 1;
+  while (P2 < N) P2 <<= 1;
+  uint64_t* sk = reinterpret_cast<uint64_t*>(smraw);
+  uint32_t* si = reinterpret_cast<uint32_t*>(sk + P2);
+  for (int b = blockIdx.x; b < B; b += gridDim.x) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+      if (i < N) {
+        uint64_t c[4] = {(uint64_t)(i >> 2), (uint64_t)b, 0ull, 0ull};
+        philox4x64_10(c, seed, 0ull);
+        sk[i] = c[i & 3];
+      } else {
+        sk[i] = ~0ull;  // pads: largest key, unique index, never among the NP smallest
+      }
+      si[i] = (uint32_t)i;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P2; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int t = threadIdx.x; t < P2 / 2; t += blockDim.x) {
+          const int lo = 2 * t - (t & (stride - 1));
+          const int hi = lo + stride;
+          const bool asc = ((lo & size) == 0);
+          const uint64_t ka = sk[lo], kb = sk[hi];
+          const uint32_t ia = si[lo], ib = si[hi];
+          const bool swap = asc ? pair_less(kb, ib, ka, ia) : pair_less(ka, ia, kb, ib);
+          if (swap) { sk[lo] = kb; sk[hi] = ka; si[lo] = ib; si[hi] = ia; }
+        }
+        __syncthreads();
+      }
+    }
+    for (int r = threadIdx.x; r < NP; r += blockDim.x)
+      atomicOr(&labels[(int64_t)si[r] * G + (b >> 5)], 1u << (b & 31));
+  }
+}
+
+// codes in shared memory: u8 for d <= 8
+template <int D>
+__global__ void __launch_bounds__(kCountThreads)
+k_perm_count(const uint32_t* __restrict__ rank, int64_t N, int64_t NP, int B, int G,
+             const uint32_t* __restrict__ labels, int R, unsigned long long* __restrict__ perm_best) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int NB = 1 << D;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int WARPS = kCountThreads / 32;
+  uint32_t* nbin = reinterpret_cast<uint32_t*>(smraw);            // [NB]
+  uint32_t* hist = nbin + NB;                                      // [R][NB][kCountThreads]
+  uint32_t* ltile = hist + (size_t)R * NB * kCountThreads;         // [kPtsTile][WARPS * R]
+  uint8_t* codes = reinterpret_cast<uint8_t*>(ltile + kPtsTile * WARPS * R);  // [N]
+  __shared__ uint32_t o[D];
+  const int chunk = kCountThreads * R;            // relabellings per pass
+  const int nchunks = (B + chunk - 1) / chunk;
+  const int wpc = WARPS * R;                      // label words per point per pass
+  for (int64_t k = blockIdx.x; k < N; k += gridDim.x) {
+    __syncthreads();
+    if (tid < D) o[tid] = rank[(int64_t)tid * N + k];
+    for (int j = tid; j < NB; j += kCountThreads) nbin[j] = 0;
+    __syncthreads();
+    for (int64_t i = tid; i < N; i += kCountThreads) {
+      uint32_t c = 0;
+#pragma unroll
+      for (int m = 0; m < D; ++m) c |= (uint32_t)(rank[(int64_t)m * N + i] >= o[m]) << m;
+      codes[i] = (uint8_t)c;
+      atomicAdd(&nbin[c], 1u);
+    }
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int b0 = ch * chunk;
+      for (int e = tid; e < R * NB * kCountThreads; e += kCountThreads) hist[e] = 0;
+      for (int64_t base = 0; base < N; base += kPtsTile) {
+        const int cnt = (int)((N - base) < kPtsTile ? (N - base) : kPtsTile);
+        __syncthreads();
+        // label words of this chunk's groups for the tile's points
+        for (int e = tid; e < cnt * wpc; e += kCountThreads) {
+          const int p = e / wpc, w = e - p * wpc;
+          const int grp = (b0 >> 5) + w;
+          ltile[e] = grp < G ? labels[(base + p) * G + grp] : 0u;
+        }
+        __syncthreads();
+        for (int p = 0; p < cnt; ++p) {
+          const uint32_t c = codes[base + p];
+#pragma unroll 4
+          for (int r = 0; r < R; ++r) {
+            // relabelling b = b0 + r*kCountThreads + tid: group (b0>>5) + r*WARPS + warp, bit lane
+            const uint32_t w = ltile[p * wpc + r * WARPS + warp];
+            const uint32_t bit = (w >> lane) & 1u;
+            if (bit) atomicAdd(&hist[((size_t)r * NB + c) * kCountThreads + tid], 1u);
+          }
+        }
+      }
+      __syncthreads();
+      for (int r = 0; r < R; ++r) {
+        const int b = b0 + r * kCountThreads + tid;
+        if (b >= B) continue;
+        uint64_t bv = 0;
+        for (int j = 0; j < NB; ++j) {
+          const uint64_t cp = hist[((size_t)r * NB + j) * kCountThreads + tid];
+          const uint64_t n = nbin[j];
+          const uint64_t x = cp * (uint64_t)N, y = n * (uint64_t)NP;
+          const uint64_t num = x > y ? x - y : y - x;
+          bv = num > bv ? num : bv;
+        }
+        atomicMax(&perm_best[b], (unsigned long long)bv);
+      }
+    }
+  }
+}
+
+__global__ void k_perm_pvalue(const unsigned long long* __restrict__ perm_best, int B,
+                              const unsigned long long* __restrict__ obs,
+                              unsigned long long* __restrict__ count) {
+  unsigned long long c = 0;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x)
+    c += perm_best[b] >= obs[0] ? 1ull : 0ull;
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+template <int D>
+cudaError_t launch_count(const uint32_t* rank, int64_t N, int64_t NP, int B, int G,
+                         const uint32_t* labels, unsigned long long* perm_best, cudaStream_t st,
+                         int num_sms) {
+  constexpr int NB = 1 << D;
+  constexpr int WARPS = kCountThreads / 32;
+  // relabellings per pass: R per thread, as many as fit 96 KB of histograms
+  int R = (96 * 1024) / (NB * kCountThreads * 4);
+  if (R < 1) R = 1;
+  const int need = (B + kCountThreads - 1) / kCountThreads;
+  if (R > need) R = need;
+  if (R > 16) R = 16;
+  const size_t smem = (size_t)NB * 4 + (size_t)R * NB * kCountThreads * 4 +
+                      (size_t)kPtsTile * WARPS * R * 4 + (size_t)N;
+  cudaError_t e = cudaFuncSetAttribute(k_perm_count<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int grid = (int)(N < (int64_t)num_sms * 4 ? N : (int64_t)num_sms * 4);
+  k_perm_count<D><<<grid, kCountThreads, smem, st>>>(rank, N, NP, B, G, labels, R, perm_best);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT,
+                          int32_t d, int32_t dtype, int32_t B, uint64_t seed, void* stream,
+                          ddks_result* observed, uint64_t* perm_num_max, double* p_value) {
+  if (!ctx || !observed) return DDKS_EINVAL;
+  int rc = ddks_check_problem(P, NP, T, NT, d, dtype);
+  if (rc) return observed->status = rc;
+  if (B < 0 || B > (1 << 20)) return observed->status = DDKS_EINVAL;
+  const int64_t N = NP + NT;
+  if (N > kMaxPermN || d > 8) return observed->status = DDKS_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return observed->status = ctx_cuda_fail(ctx, e, "cudaSetDevice");
+  const void *dP, *dT;
+  if ((rc = ddks_stage_inputs(ctx, P, NP, T, NT, d, dtype, st, &dP, &dT))) return observed->status = rc;
+  ddks_plan plan;
+  if ((rc = ddks_select_path(ctx, NP, NT, d, &plan))) return observed->status = rc;
+  if ((rc = ddks_encode_problem(ctx, dP, NP, dT, NT, d, dtype, st, plan.path == DDKS_PATH_REGISTER)))
+    return observed->status = rc;
+  // observed statistic
+  if ((rc = ctx->best.reserve(ctx, 8 * (size_t)N))) return observed->status = rc;
+  if ((rc = ctx->bestj.reserve(ctx, 4 * (size_t)N))) return observed->status = rc;
+  if ((rc = ctx->out3.reserve(ctx, 64))) return observed->status = rc;
+  if ((rc = ddks_count_origins(ctx, NP, NT, d, 0, N, (uint64_t*)ctx->best.ptr, (int32_t*)ctx->bestj.ptr, st)))
+    return observed->status = rc;
+  e = ddks_launch_reduce((const uint64_t*)ctx->best.ptr, (const int32_t*)ctx->bestj.ptr, N, 0,
+                         (unsigned long long*)ctx->out3.ptr, st);
+  ctx->launches += 1;
+  if (e != cudaSuccess) return observed->status = ctx_cuda_fail(ctx, e, "reduce");
+  unsigned long long* out3 = (unsigned long long*)ctx->out3.ptr;
+  const int G = (B + 31) / 32;
+  const int Bc = B > 0 ? B : 1;
+  if ((rc = ctx->perm_labels.reserve(ctx, 4 * (size_t)N * (G > 0 ? G : 1)))) return observed->status = rc;
+  if ((rc = ctx->perm_best.reserve(ctx, 8 * (size_t)Bc))) return observed->status = rc;
+  unsigned long long* pbest = (unsigned long long*)ctx->perm_best.ptr;
+  e = cudaMemsetAsync(out3 + 4, 0, 8, st);  // p-value count
+  if (e == cudaSuccess && B > 0) {
+    e = cudaMemsetAsync(ctx->perm_labels.ptr, 0, 4 * (size_t)N * G, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pbest, 0, 8 * (size_t)B, st);
+    if (e == cudaSuccess) {
+      int P2 = 1;
+      while (P2 < N) P2 <<= 1;
+      const size_t smem = (size_t)P2 * 12;
+      e = cudaFuncSetAttribute(k_perm_labels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) {
+        const int grid = B < ctx->num_sms * 2 ? B : ctx->num_sms * 2;
+        k_perm_labels<<<grid, kLabelThreads, smem, st>>>(N, NP, B, seed, G, (uint32_t*)ctx->perm_labels.ptr);
+        e = cudaGetLastError();
+        ctx->launches += 1;
+      }
+    }
+    if (e == cudaSuccess) {
+      const uint32_t* rank = (const uint32_t*)ctx->rank.ptr;
+      const uint32_t* lab = (const uint32_t*)ctx->perm_labels.ptr;
+      switch (d) {
+        case 1: e = launch_count<1>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
+        case 2: e = launch_count<2>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
+        case 3: e = launch_count<3>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
+        case 4: e = launch_count<4>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
+        case 5: e = launch_count<5>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
+        case 6: e = launch_count<6>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
+        case 7: e = launch_count<7>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
+        default: e = launch_count<8>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
+      }
+      ctx->launches += 1;
+    }
+    if (e == cudaSuccess) {
+      k_perm_pvalue<<<(B + 255) / 256 < 64 ? (B + 255) / 256 : 64, 256, 0, st>>>(pbest, B, out3, out3 + 4);
+      e = cudaGetLastError();
+      ctx->launches += 1;
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->h_out, out3, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->h_out + 8, ctx->flags.ptr, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && perm_num_max && B > 0)
+    e = cudaMemcpyAsync(perm_num_max, pbest, 8 * (size_t)B, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return observed->status = ctx_cuda_fail(ctx, e, "permutation test");
+  if ((unsigned)(ctx->h_out[8] & 0xFFFFFFFFull) & ddks::kFlagNaN) return observed->status = DDKS_ENAN;
+  observed->num_max = ctx->h_out[0];
+  observed->denom = (uint64_t)NP * (uint64_t)NT;
+  observed->D = (double)observed->num_max / (double)observed->denom;
+  observed->argmax_origin = (int64_t)ctx->h_out[1];
+  observed->argmax_orthant = (int32_t)ctx->h_out[2];
+  observed->status = DDKS_OK;
+  const unsigned long long ge = B > 0 ? ctx->h_out[4] : 0ull;
+  if (p_value) *p_value = (double)(1 + ge) / (double)(1 + (int64_t)B);
+  return DDKS_OK;
+}

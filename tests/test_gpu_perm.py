@@ -1,0 +1,58 @@
+"""Permutation test (Sec. 4.2) on the GPU against the oracle: every
+relabelling's integer numerator, the observed statistic and the p-value."""
+import numpy as np
+import pytest
+
+import paper_2106_13706_gb300 as pkg
+from oracle import oracle as orc
+from paper_2106_13706_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    from paper_2106_13706_gb300 import build as b
+    b.build()
+    return t
+
+
+def _check(torch, P, T, B, seed):
+    ref = orc.permutation_test(P, T, B, seed)
+    with pkg.Context(device=0) as c:
+        got = c.permutation_test(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda(), B, seed)
+    assert got["observed"]["num_max"] == ref["num_obs"]
+    assert np.array_equal(got["perm_num_max"], ref["perm_num_max"])
+    assert got["p_value"] == ref["p_value"]
+    return got
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 6, 8])
+def test_small(torch, d):
+    P, T = wl.random_pair(d, 23, 31, d, kind="int")
+    _check(torch, P, T, 77, seed=d)
+    P, T = wl.random_pair(d + 50, 300, 200, d, kind="normal", dtype=np.float64)
+    _check(torch, P, T, 300, seed=99)
+
+
+def test_edges(torch):
+    P, T = wl.random_pair(1, 1, 1, 2)
+    _check(torch, P, T, 5, seed=0)
+    P, T = wl.random_pair(2, 40, 9, 3, kind="shifted")
+    g = _check(torch, P, T, 64, seed=1)
+    assert g["observed"]["num_max"] == 40 * 9
+    P, T = wl.random_pair(3, 30, 30, 3)
+    with pkg.Context(device=0) as c:
+        r = c.permutation_test(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda(), 0, 5)
+        assert r["p_value"] == 1.0
+
+
+def test_config4_mixture_1000(torch):
+    P, T = wl.CONFIGS["cfg4_d3_2000x2000_mixture_null"]()
+    g = _check(torch, P, T, 1000, seed=2021)
+    assert 0.0 < g["p_value"] <= 1.0
+    P, T = wl.CONFIGS["cfg4_d3_2000x2000_mixture_alt"]()
+    g = _check(torch, P, T, 200, seed=7)
+    assert g["p_value"] == 1.0 / 201

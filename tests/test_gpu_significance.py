@@ -1,0 +1,70 @@
+"""Analytic significance (Sec. 3, Eq. ddks_significance) on the GPU against the
+oracle's direct double sum.
+
+Tolerance: both sides work in float64.  The oracle sums the pmf products of
+every admissible (nP, nT) pair; the kernel sums pmf(nP) times the T mass
+outside the admissible interval (prefix/suffix sums), so the two differ only
+by rounding: per cell a few ulps of p, i.e. ~1e-15 absolute on log p, and the
+log of the product adds N * 2^d such terms.  The test allows 1e-9 relative plus
+1e-11 absolute on log(prod) and on S.
+"""
+import numpy as np
+import pytest
+
+import paper_2106_13706_gb300 as pkg
+from oracle import oracle as orc
+from paper_2106_13706_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    from paper_2106_13706_gb300 import build as b
+    b.build()
+    return t
+
+
+def _cmp(torch, P, T, est, model, num=None):
+    if num is None:
+        num = orc.ddks(P, T)["num_max"]
+    S_ref, lp_ref = orc.significance(P, T, num, estimator=est, model=model)
+    with pkg.Context(device=0) as c:
+        S, lp = c.significance(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda(), num,
+                               estimator=est, model=model)
+    assert lp == pytest.approx(lp_ref, rel=1e-9, abs=1e-11)
+    assert S == pytest.approx(S_ref, rel=1e-9, abs=1e-11)
+    return S
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("est,model", [(1, 0), (0, 0), (1, 1)])
+def test_small(torch, d, est, model):
+    P, T = wl.random_pair(10 + d, 17, 23, d, kind="int")
+    _cmp(torch, P, T, est, model)
+    P, T = wl.random_pair(20 + d, 40, 31, d, kind="normal", dtype=np.float64)
+    _cmp(torch, P, T, est, model)
+
+
+def test_extremes(torch):
+    P, T = wl.random_pair(1, 12, 9, 2)
+    # the largest possible statistic: every cell probability is 1
+    assert _cmp(torch, P, T, 1, 0, num=12 * 9) == pytest.approx(0.0, abs=1e-12)
+    # statistic 0: only exact ties in every cell count as "as or less extreme"
+    _cmp(torch, P, T, 1, 0, num=0)
+
+
+def test_config1(torch):
+    P, T = wl.CONFIGS["cfg1_d3_200x200_f32"]()
+    S = _cmp(torch, P, T, 1, 0)
+    assert 0.0 <= S <= 1.0
+
+
+def test_rejects_unsupported(torch):
+    P = np.zeros((5, 14), np.float32)
+    with pkg.Context(device=0) as c:
+        with pytest.raises(pkg.DdksError) as e:
+            c.significance(torch.from_numpy(P).cuda(), torch.from_numpy(P).cuda(), 0)
+        assert e.value.code == -8
