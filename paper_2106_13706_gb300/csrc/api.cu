@@ -43,6 +43,7 @@ void ddks_config_default(ddks_config* cfg) {
 }
 
 int ctx_cuda_fail(ddks_ctx* ctx, cudaError_t e, const char* where) {
+  cudaGetLastError();  // clear a non-sticky error so later calls start clean
   if (ctx) {
     ctx->last_err = std::string(where) + ": " + cudaGetErrorString(e);
   }
@@ -130,6 +131,7 @@ int ddks_ctx_destroy(ddks_ctx* ctx) {
   cudaDeviceSynchronize();
   for (DevBuf* b : ctx->all_bufs()) b->release();
   if (ctx->h_out) cudaFreeHost(ctx->h_out);
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   delete ctx;

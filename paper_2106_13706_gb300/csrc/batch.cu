@@ -1,0 +1,449 @@
+// batch.cu -- many independent ddKS problems of different N and d in one
+// persistent launch (the batched form of Sec. 2.1's statistic).
+//
+// K0b (k_batch_rank): one CTA per (problem, dimension) maps the coordinates to
+//   order-preserving keys, sorts (key, index) in shared memory and writes each
+//   point's min-rank, so x_m >= o_m <=> rank_m(x) >= rank_m(o) (Eq. g).
+// K5 (k_batch_count): a persistent kernel.  Work units are (problem, tile of
+//   64 origins); CTAs take units from a device counter until none are left, so
+//   problems of very different sizes share the GPU without a launch each.  A
+//   unit with d <= 6 keeps lane-private shared histograms (4 threads per
+//   origin), one with 7 <= d <= 11 one shared histogram per warp and origin.
+//   Each origin's max |cP*NT - cT*NP| (Eq. d1) and lowest orthant go to the
+//   problem's slice of best/bestj.
+// K_r (k_batch_reduce): one CTA per problem: max over origins, lowest origin.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "ddks_host.h"
+#include "ddks_internal.cuh"
+
+struct BatchDesc {
+  const void* P;
+  const void* T;
+  int64_t NP, NT;
+  int64_t off_pool;  // offset of the problem in best/bestj (pooled points)
+  int64_t off_rank;  // offset of the problem's [d][N] ranks
+  int64_t unit0;     // first work unit of the problem
+  int32_t d, is_f64;
+};
+
+namespace {
+
+constexpr int kMaxBatchN = 16384;
+constexpr int kThreads = 256;
+constexpr int kOT = 64;        // origins per work unit
+constexpr int kTile = 512;     // points per staged tile
+
+DDKS_DEV bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+__global__ void __launch_bounds__(1024)
+k_batch_rank(const BatchDesc* __restrict__ desc, const int* __restrict__ cta_prob,
+             const int* __restrict__ cta_dim, uint32_t* __restrict__ rank, unsigned* __restrict__ flags) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const BatchDesc D = desc[cta_prob[blockIdx.x]];
+  const int m = cta_dim[blockIdx.x];
+  const int64_t N = D.NP + D.NT;
+  int P2 = 1;
+  while (P2 < N) P2 <<= 1;
+  uint64_t* sk = reinterpret_cast<uint64_t*>(smraw);
+  uint32_t* si = reinterpret_cast<uint32_t*>(sk + P2);
+  for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+    uint64_t key = ~0ull;
+    if (i < N) {
+      if (D.is_f64) {
+        const double v = i < D.NP ? ((const double*)D.P)[(int64_t)i * D.d + m]
+                                  : ((const double*)D.T)[(int64_t)(i - D.NP) * D.d + m];
+        if (v != v) atomicOr(flags, ddks::kFlagNaN);
+        key = ddks::order_key(v);
+      } else {
+        const float v = i < D.NP ? ((const float*)D.P)[(int64_t)i * D.d + m]
+                                 : ((const float*)D.T)[(int64_t)(i - D.NP) * D.d + m];
+        if (v != v) atomicOr(flags, ddks::kFlagNaN);
+        key = ddks::order_key(v);
+      }
+    }
+    sk[i] = key;
+    si[i] = (uint32_t)i;
+  }
+  __syncthreads();
+  for (int size = 2; size <= P2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < P2 / 2; t += blockDim.x) {
+        const int lo = 2 * t - (t & (stride - 1));
+        const int hi = lo + stride;
+        const bool asc = ((lo & size) == 0);
+        const uint64_t ka = sk[lo], kb = sk[hi];
+        const uint32_t ia = si[lo], ib = si[hi];
+        const bool swap = asc ? pair_less(kb, ib, ka, ia) : pair_less(ka, ia, kb, ib);
+        if (swap) { sk[lo] = kb; sk[hi] = ka; si[lo] = ib; si[hi] = ia; }
+      }
+      __syncthreads();
+    }
+  }
+  uint32_t* R = rank + D.off_rank + (int64_t)m * N;
+  for (int p = threadIdx.x; p < N; p += blockDim.x) {
+    const uint64_t key = sk[p];
+    int lo = 0, hi = p;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (sk[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    R[si[p]] = (uint32_t)lo;
+  }
+}
+
+// lane-private histograms: 64 origins x 4 slices
+template <int DD>
+DDKS_DEV void unit_lane(const BatchDesc& D, const uint32_t* __restrict__ rk, int64_t o0,
+                        uint32_t* sm, uint64_t* best, int32_t* bestj) {
+  constexpr int NB = 1 << DD;
+  constexpr int S = kThreads / kOT;
+  const int64_t N = D.NP + D.NT;
+  const int tid = threadIdx.x, ol = tid / S, s = tid - ol * S;
+  const bool wide = D.NP > 65535 || D.NT > 65535;
+  uint32_t* histP = sm;                         // [NB][kThreads]
+  uint32_t* histT = sm + NB * kThreads;         // [NB][kThreads] (wide only)
+  uint32_t* tile = sm + 2 * NB * kThreads;      // [DD][kTile]
+  const int64_t k = o0 + ol;
+  const bool active = k < N;
+  uint32_t o[DD];
+#pragma unroll
+  for (int m = 0; m < DD; ++m) o[m] = active ? rk[(int64_t)m * N + k] : 0u;
+  for (int j = 0; j < NB; ++j) { histP[j * kThreads + tid] = 0; histT[j * kThreads + tid] = 0; }
+  for (int64_t base = 0; base < N; base += kTile) {
+    const int cnt = (int)((N - base) < kTile ? (N - base) : kTile);
+    __syncthreads();
+    for (int e = tid; e < DD * cnt; e += kThreads) {
+      const int m = e / cnt, j = e - m * cnt;
+      tile[m * kTile + j] = rk[(int64_t)m * N + base + j];
+    }
+    __syncthreads();
+    int pend = (int)(D.NP - base);
+    pend = pend < 0 ? 0 : (pend > cnt ? cnt : pend);
+    for (int j = s; j < cnt; j += S) {
+      uint32_t c = 0;
+#pragma unroll
+      for (int m = 0; m < DD; ++m) c |= (uint32_t)(tile[m * kTile + j] >= o[m]) << m;
+      if (j < pend) atomicAdd(&histP[c * kThreads + tid], 1u);
+      else if (wide) atomicAdd(&histT[c * kThreads + tid], 1u);
+      else atomicAdd(&histP[c * kThreads + tid], 1u << 16);
+    }
+  }
+  __syncthreads();
+  uint64_t bv = 0;
+  int bj = 0;
+  if (active) {
+    for (int j = s; j < NB; j += S) {
+      uint64_t a = 0, b = 0;
+      for (int q = 0; q < S; ++q) {
+        const int col = ol * S + q;
+        const uint32_t v = histP[j * kThreads + col];
+        if (wide) { a += v; b += histT[j * kThreads + col]; }
+        else { a += v & 0xFFFFu; b += v >> 16; }
+      }
+      const uint64_t num = ddks::numer(a, b, (uint64_t)D.NP, (uint64_t)D.NT);
+      if (num > bv) { bv = num; bj = j; }
+    }
+  }
+  for (int off = 1; off < S; off <<= 1) {
+    const uint64_t v2 = __shfl_xor_sync(0xffffffffu, bv, off);
+    const int j2 = __shfl_xor_sync(0xffffffffu, bj, off);
+    if (v2 > bv || (v2 == bv && j2 < bj)) { bv = v2; bj = j2; }
+  }
+  if (active && s == 0) {
+    best[D.off_pool + k] = bv;
+    bestj[D.off_pool + k] = bv ? bj : 0;
+  }
+  __syncthreads();
+}
+
+// one shared histogram per warp and origin (7 <= d <= 11), 8 warps x 8 origins
+DDKS_DEV void unit_warp(const BatchDesc& D, const uint32_t* __restrict__ rk, int64_t o0,
+                        uint32_t* sm, uint64_t* best, int32_t* bestj) {
+  const int d = D.d, nb = 1 << d;
+  const int64_t N = D.NP + D.NT;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool wide = D.NP > 65535 || D.NT > 65535;
+  uint32_t* hist = sm + (size_t)warp * nb * 2;
+  for (int it = 0; it < kOT / (kThreads / 32); ++it) {
+    const int64_t k = o0 + it * (kThreads / 32) + warp;
+    if (k >= N) break;
+    for (int j = lane; j < 2 * nb; j += 32) hist[j] = 0;
+    uint32_t o[ddks::kMaxD];
+    for (int m = 0; m < d; ++m) o[m] = rk[(int64_t)m * N + k];
+    __syncwarp();
+    for (int64_t i = lane; i < N; i += 32) {
+      uint32_t c = 0;
+      for (int m = 0; m < d; ++m) c |= (uint32_t)(rk[(int64_t)m * N + i] >= o[m]) << m;
+      const bool isP = i < D.NP;
+      if (wide) atomicAdd(&hist[isP ? c : nb + c], 1u);
+      else atomicAdd(&hist[c], isP ? 1u : (1u << 16));
+    }
+    __syncwarp();
+    uint64_t bv = 0;
+    int bj = 0;
+    for (int j = lane; j < nb; j += 32) {
+      uint64_t a, b;
+      if (wide) { a = hist[j]; b = hist[nb + j]; }
+      else { a = hist[j] & 0xFFFFu; b = hist[j] >> 16; }
+      const uint64_t num = ddks::numer(a, b, (uint64_t)D.NP, (uint64_t)D.NT);
+      if (num > bv) { bv = num; bj = j; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const uint64_t v2 = __shfl_down_sync(0xffffffffu, bv, off);
+      const int j2 = __shfl_down_sync(0xffffffffu, bj, off);
+      if (v2 > bv || (v2 == bv && j2 < bj)) { bv = v2; bj = j2; }
+    }
+    if (lane == 0) {
+      best[D.off_pool + k] = bv;
+      bestj[D.off_pool + k] = bv ? bj : 0;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_batch_count(const BatchDesc* __restrict__ desc, int count, int64_t total_units,
+              const uint32_t* __restrict__ rank, unsigned long long* __restrict__ next_unit,
+              uint64_t* __restrict__ best, int32_t* __restrict__ bestj) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ long long unit;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) unit = (long long)atomicAdd(next_unit, 1ull);
+    __syncthreads();
+    const long long u = unit;
+    if (u >= total_units) break;
+    // problem of this unit: last problem whose unit0 <= u
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (desc[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+    }
+    const BatchDesc D = desc[lo];
+    const int64_t o0 = (u - D.unit0) * kOT;
+    const uint32_t* rk = rank + D.off_rank;
+    switch (D.d) {
+      case 1: unit_lane<1>(D, rk, o0, sm, best, bestj); break;
+      case 2: unit_lane<2>(D, rk, o0, sm, best, bestj); break;
+      case 3: unit_lane<3>(D, rk, o0, sm, best, bestj); break;
+      case 4: unit_lane<4>(D, rk, o0, sm, best, bestj); break;
+      case 5: unit_lane<5>(D, rk, o0, sm, best, bestj); break;
+      case 6: unit_lane<6>(D, rk, o0, sm, best, bestj); break;
+      default: unit_warp(D, rk, o0, sm, best, bestj); break;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+k_batch_reduce(const BatchDesc* __restrict__ desc, const uint64_t* __restrict__ best,
+               const int32_t* __restrict__ bestj, unsigned long long* __restrict__ out) {
+  __shared__ unsigned long long sv[32];
+  __shared__ long long si[32];
+  const BatchDesc D = desc[blockIdx.x];
+  const int64_t no = D.NP + D.NT;
+  const uint64_t* b = best + D.off_pool;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long v = 0;
+  for (int64_t i = threadIdx.x; i < no; i += blockDim.x) v = b[i] > v ? b[i] : v;
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long v2 = __shfl_down_sync(0xffffffffu, v, off);
+    v = v2 > v ? v2 : v;
+  }
+  if (lane == 0) sv[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = sv[w] > m ? sv[w] : m;
+    sv[0] = m;
+  }
+  __syncthreads();
+  const unsigned long long vmax = sv[0];
+  long long idx = no;
+  for (int64_t i = threadIdx.x; i < no; i += blockDim.x)
+    if (b[i] == vmax) { idx = i; break; }
+  for (int off = 16; off > 0; off >>= 1) {
+    const long long i2 = __shfl_down_sync(0xffffffffu, idx, off);
+    idx = i2 < idx ? i2 : idx;
+  }
+  __syncthreads();
+  if (lane == 0) si[warp] = idx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long m = no;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = si[w] < m ? si[w] : m;
+    out[3 * blockIdx.x + 0] = vmax;
+    out[3 * blockIdx.x + 1] = (unsigned long long)m;
+    out[3 * blockIdx.x + 2] = (unsigned long long)(long long)bestj[D.off_pool + m];
+  }
+}
+
+size_t unit_smem(int d) {
+  if (d <= 6) return (size_t)2 * (1u << d) * kThreads * 4 + (size_t)d * kTile * 4;
+  return (size_t)(kThreads / 32) * (1u << d) * 2 * 4;
+}
+
+}  // namespace
+
+// Batched distances for problems that fit the batch kernels (N <= 16384, d <= 11);
+// the others go through the single-problem path.  Synchronous.
+int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, const int64_t* NP,
+                        const void* const* T, const int64_t* NT, const int32_t* d, int32_t dtype,
+                        void* stream, ddks_result* out) {
+  if (!ctx || count < 0 || (count > 0 && (!P || !NP || !T || !NT || !d || !out))) return DDKS_EINVAL;
+  if (count == 0) return DDKS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "cudaSetDevice");
+  const size_t es = dtype == DDKS_F64 ? 8 : 4;
+  std::vector<int> batched, single;
+  for (int i = 0; i < count; ++i) {
+    const int rc = ddks_check_problem(P[i], NP[i], T[i], NT[i], d[i], dtype);
+    if (rc) { out[i].status = rc; return rc; }
+    if (NP[i] + NT[i] <= kMaxBatchN && d[i] <= 11) batched.push_back(i); else single.push_back(i);
+  }
+  int rc = DDKS_OK;
+  if (!batched.empty()) {
+    const int nb = (int)batched.size();
+    // stage host inputs into one device buffer
+    size_t host_bytes = 0;
+    std::vector<char> is_dev(2 * nb);
+    for (int b = 0; b < nb; ++b) {
+      const int i = batched[b];
+      is_dev[2 * b] = ddks_is_device_ptr(P[i]);
+      is_dev[2 * b + 1] = ddks_is_device_ptr(T[i]);
+      if (!is_dev[2 * b]) host_bytes += (es * NP[i] * d[i] + 15) & ~(size_t)15;
+      if (!is_dev[2 * b + 1]) host_bytes += (es * NT[i] * d[i] + 15) & ~(size_t)15;
+    }
+    if (host_bytes && (rc = ctx->inP.reserve(ctx, host_bytes))) return rc;
+    std::vector<BatchDesc> hd(nb);
+    std::vector<int> cta_prob, cta_dim;
+    size_t hoff = 0;
+    int64_t off_pool = 0, off_rank = 0, units = 0;
+    size_t smem_rank = 0, smem_unit = 0;
+    for (int b = 0; b < nb; ++b) {
+      const int i = batched[b];
+      BatchDesc& D = hd[b];
+      D.P = P[i];
+      D.T = T[i];
+      if (!is_dev[2 * b]) {
+        void* dst = (char*)ctx->inP.ptr + hoff;
+        e = cudaMemcpyAsync(dst, P[i], es * NP[i] * d[i], cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "batch copy");
+        D.P = dst;
+        hoff += (es * NP[i] * d[i] + 15) & ~(size_t)15;
+      }
+      if (!is_dev[2 * b + 1]) {
+        void* dst = (char*)ctx->inP.ptr + hoff;
+        e = cudaMemcpyAsync(dst, T[i], es * NT[i] * d[i], cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "batch copy");
+        D.T = dst;
+        hoff += (es * NT[i] * d[i] + 15) & ~(size_t)15;
+      }
+      D.NP = NP[i];
+      D.NT = NT[i];
+      D.d = d[i];
+      D.is_f64 = dtype == DDKS_F64;
+      const int64_t N = NP[i] + NT[i];
+      D.off_pool = off_pool;
+      D.off_rank = off_rank;
+      D.unit0 = units;
+      off_pool += N;
+      off_rank += N * d[i];
+      units += (N + kOT - 1) / kOT;
+      for (int m = 0; m < d[i]; ++m) { cta_prob.push_back(b); cta_dim.push_back(m); }
+      int P2 = 1;
+      while (P2 < N) P2 <<= 1;
+      smem_rank = std::max(smem_rank, (size_t)P2 * 12);
+      smem_unit = std::max(smem_unit, unit_smem(d[i]));
+    }
+    const size_t desc_bytes = sizeof(BatchDesc) * nb + 8 * cta_prob.size() + 64;
+    if ((rc = ctx->batch_desc.reserve(ctx, desc_bytes))) return rc;
+    if ((rc = ctx->rank.reserve(ctx, 4 * (size_t)off_rank))) return rc;
+    if ((rc = ctx->best.reserve(ctx, 8 * (size_t)off_pool))) return rc;
+    if ((rc = ctx->bestj.reserve(ctx, 4 * (size_t)off_pool))) return rc;
+    if ((rc = ctx->batch_work.reserve(ctx, 8 * (3 * (size_t)nb + 4)))) return rc;
+    if ((rc = ctx->flags.reserve(ctx, 64))) return rc;
+    char* dd = (char*)ctx->batch_desc.ptr;
+    BatchDesc* ddesc = (BatchDesc*)dd;
+    int* dprob = (int*)(dd + sizeof(BatchDesc) * nb);
+    int* ddim = dprob + cta_prob.size();
+    // the descriptor upload goes through pinned staging owned by the context
+    const size_t up = sizeof(BatchDesc) * nb + 8 * cta_prob.size();
+    if (ctx->h_stage_bytes < up) {
+      if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+      ctx->h_stage = nullptr;
+      ctx->h_stage_bytes = 0;
+      e = cudaMallocHost(&ctx->h_stage, up * 2);
+      if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "cudaMallocHost");
+      ctx->h_stage_bytes = up * 2;
+    }
+    e = cudaStreamSynchronize(st);  // the staging buffer may still feed an earlier copy
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "batch sync");
+    char* hs = (char*)ctx->h_stage;
+    std::memcpy(hs, hd.data(), sizeof(BatchDesc) * nb);
+    std::memcpy(hs + sizeof(BatchDesc) * nb, cta_prob.data(), 4 * cta_prob.size());
+    std::memcpy(hs + sizeof(BatchDesc) * nb + 4 * cta_prob.size(), cta_dim.data(), 4 * cta_dim.size());
+    e = cudaMemcpyAsync(dd, hs, up, cudaMemcpyHostToDevice, st);
+    unsigned long long* work = (unsigned long long*)ctx->batch_work.ptr;
+    unsigned long long* res = work + 1;
+    if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->flags.ptr, 0, 4, st);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_batch_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rank);
+    if (e == cudaSuccess) {
+      k_batch_rank<<<(unsigned)cta_prob.size(), 1024, smem_rank, st>>>(
+          ddesc, dprob, ddim, (uint32_t*)ctx->rank.ptr, (unsigned*)ctx->flags.ptr);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_batch_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_unit);
+    if (e == cudaSuccess) {
+      int blocks_per_sm = 1;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_batch_count, kThreads, smem_unit);
+      if (blocks_per_sm < 1) blocks_per_sm = 1;
+      int64_t grid = (int64_t)ctx->num_sms * blocks_per_sm;
+      if (grid > units) grid = units;
+      k_batch_count<<<(unsigned)grid, kThreads, smem_unit, st>>>(
+          ddesc, nb, units, (const uint32_t*)ctx->rank.ptr, work, (uint64_t*)ctx->best.ptr,
+          (int32_t*)ctx->bestj.ptr);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      k_batch_reduce<<<nb, 1024, 0, st>>>(ddesc, (const uint64_t*)ctx->best.ptr,
+                                          (const int32_t*)ctx->bestj.ptr, res);
+      e = cudaGetLastError();
+    }
+    ctx->launches += 3;
+    std::vector<unsigned long long> hres(3 * (size_t)nb);
+    unsigned hflags = 0;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hres.data(), res, 8 * 3 * (size_t)nb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflags, ctx->flags.ptr, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "batch");
+    if (hflags & ddks::kFlagNaN) {
+      for (int b = 0; b < nb; ++b) out[batched[b]].status = DDKS_ENAN;
+      return DDKS_ENAN;
+    }
+    for (int b = 0; b < nb; ++b) {
+      ddks_result& r = out[batched[b]];
+      r.num_max = hres[3 * b];
+      r.denom = (uint64_t)hd[b].NP * (uint64_t)hd[b].NT;
+      r.D = (double)r.num_max / (double)r.denom;
+      r.argmax_origin = (int64_t)hres[3 * b + 1];
+      r.argmax_orthant = (int32_t)hres[3 * b + 2];
+      r.status = DDKS_OK;
+    }
+  }
+  for (int i : single) {
+    rc = ddks_distance(ctx, P[i], NP[i], T[i], NT[i], d[i], dtype, stream, &out[i]);
+    if (rc) return rc;
+  }
+  return DDKS_OK;
+}

@@ -47,6 +47,8 @@ struct ddks_ctx {
   DevBuf sig_cells, sig_logp;                   // significance
   DevBuf batch_desc, batch_work;                // batched launch
   unsigned long long* h_out = nullptr;          // pinned, 64 entries
+  void* h_stage = nullptr;                      // pinned staging for uploads
+  size_t h_stage_bytes = 0;
   // stage timing (ddks_set_stage_timing)
   bool stage_timing = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -11,7 +11,8 @@
 //   labels, so each CTA takes an origin, computes the N codes once into shared
 //   memory together with n(c) = #{x : c(o, x) = c}, and then counts, for every
 //   relabelling b, cP_b(c) = #{x in permuted P : c(o, x) = c} in lane-private
-//   shared histograms (warp w of a chunk owns 32 consecutive relabellings, so
+//   shared histograms of 16-bit counters (N <= 16384; warp w of a chunk owns
+//   32 consecutive relabellings, so
 //   one label word per point serves the whole warp).  With cT_b = n - cP_b the
 //   numerator is |cP_b*NT - cT_b*NP| = |cP_b*N - n*NP|; each thread keeps the
 //   running maximum of its relabellings and finishes with one atomicMax.
@@ -93,8 +94,9 @@ k_perm_count(const uint32_t* __restrict__ rank, int64_t N, int64_t NP, int B, in
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int WARPS = kCountThreads / 32;
   uint32_t* nbin = reinterpret_cast<uint32_t*>(smraw);            // [NB]
-  uint32_t* hist = nbin + NB;                                      // [R][NB][kCountThreads]
-  uint32_t* ltile = hist + (size_t)R * NB * kCountThreads;         // [kPtsTile][WARPS * R]
+  constexpr int NW = (NB + 1) / 2;                                 // two 16-bit counters per word
+  uint32_t* hist = nbin + NB;                                      // [R][NW][kCountThreads]
+  uint32_t* ltile = hist + (size_t)R * NW * kCountThreads;         // [kPtsTile][WARPS * R]
   uint8_t* codes = reinterpret_cast<uint8_t*>(ltile + kPtsTile * WARPS * R);  // [N]
   __shared__ uint32_t o[D];
   const int chunk = kCountThreads * R;            // relabellings per pass
@@ -114,7 +116,7 @@ k_perm_count(const uint32_t* __restrict__ rank, int64_t N, int64_t NP, int B, in
     }
     for (int ch = 0; ch < nchunks; ++ch) {
       const int b0 = ch * chunk;
-      for (int e = tid; e < R * NB * kCountThreads; e += kCountThreads) hist[e] = 0;
+      for (int e = tid; e < R * NW * kCountThreads; e += kCountThreads) hist[e] = 0;
       for (int64_t base = 0; base < N; base += kPtsTile) {
         const int cnt = (int)((N - base) < kPtsTile ? (N - base) : kPtsTile);
         __syncthreads();
@@ -132,7 +134,7 @@ k_perm_count(const uint32_t* __restrict__ rank, int64_t N, int64_t NP, int B, in
             // relabelling b = b0 + r*kCountThreads + tid: group (b0>>5) + r*WARPS + warp, bit lane
             const uint32_t w = ltile[p * wpc + r * WARPS + warp];
             const uint32_t bit = (w >> lane) & 1u;
-            if (bit) atomicAdd(&hist[((size_t)r * NB + c) * kCountThreads + tid], 1u);
+            if (bit) atomicAdd(&hist[((size_t)r * NW + (c >> 1)) * kCountThreads + tid], 1u << (16 * (c & 1)));
           }
         }
       }
@@ -142,7 +144,7 @@ k_perm_count(const uint32_t* __restrict__ rank, int64_t N, int64_t NP, int B, in
         if (b >= B) continue;
         uint64_t bv = 0;
         for (int j = 0; j < NB; ++j) {
-          const uint64_t cp = hist[((size_t)r * NB + j) * kCountThreads + tid];
+          const uint64_t cp = (hist[((size_t)r * NW + (j >> 1)) * kCountThreads + tid] >> (16 * (j & 1))) & 0xFFFFu;
           const uint64_t n = nbin[j];
           const uint64_t x = cp * (uint64_t)N, y = n * (uint64_t)NP;
           const uint64_t num = x > y ? x - y : y - x;
@@ -171,12 +173,14 @@ cudaError_t launch_count(const uint32_t* rank, int64_t N, int64_t NP, int B, int
   constexpr int NB = 1 << D;
   constexpr int WARPS = kCountThreads / 32;
   // relabellings per pass: R per thread, as many as fit 96 KB of histograms
-  int R = (96 * 1024) / (NB * kCountThreads * 4);
+  // (16-bit counters, N <= 16384)
+  constexpr int NW = (NB + 1) / 2;
+  int R = (96 * 1024) / (NW * kCountThreads * 4);
   if (R < 1) R = 1;
   const int need = (B + kCountThreads - 1) / kCountThreads;
   if (R > need) R = need;
   if (R > 16) R = 16;
-  const size_t smem = (size_t)NB * 4 + (size_t)R * NB * kCountThreads * 4 +
+  const size_t smem = (size_t)NB * 4 + (size_t)R * NW * kCountThreads * 4 +
                       (size_t)kPtsTile * WARPS * R * 4 + (size_t)N;
   cudaError_t e = cudaFuncSetAttribute(k_perm_count<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);

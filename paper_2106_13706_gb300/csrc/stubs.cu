@@ -3,10 +3,6 @@
 #include "ddks_host.h"
 #include "ddks_internal.cuh"
 
-int ddks_batch_distance(ddks_ctx*, int32_t, const void* const*, const int64_t*, const void* const*,
-                        const int64_t*, const int32_t*, int32_t, void*, ddks_result*) {
-  return DDKS_EUNSUPPORTED;
-}
 int ddks_submit(ddks_ctx*, const void*, int64_t, const void*, int64_t, int32_t, int32_t, uint64_t*) {
   return DDKS_EUNSUPPORTED;
 }

@@ -1,0 +1,55 @@
+"""Many uneven problems in one persistent launch (ddks_batch_distance): each
+result equals the oracle's, and equals the same problem computed alone."""
+import numpy as np
+import pytest
+
+import paper_2106_13706_gb300 as pkg
+from oracle import oracle as orc
+from paper_2106_13706_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    from paper_2106_13706_gb300 import build as b
+    b.build()
+    return t
+
+
+def _key(r):
+    return (r["num_max"], r["denom"], r["argmax_origin"], r["argmax_orthant"])
+
+
+def test_uneven_problems_match_oracle(torch):
+    probs = wl.uneven_problems(seed=0, count=64, n_lo=16, n_hi=1500, dims=tuple(range(1, 12)))
+    with pkg.Context(device=0) as c:
+        got = c.batch_distance([(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()) for P, T in probs])
+        alone = [c.distance(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()) for P, T in probs]
+    for (P, T), g, a in zip(probs, got, alone):
+        ref = orc.ddks(P, T)
+        assert _key(g) == _key(ref)
+        assert _key(a) == _key(ref)
+
+
+def test_host_inputs_and_large_members(torch):
+    probs = wl.uneven_problems(seed=3, count=6, n_lo=50, n_hi=400, dims=(2, 7, 12))
+    P, T = wl.gaussian_pair(seed=9, n_p=9000, n_t=8000, d=3)  # N > 16384: single path
+    probs.append((P, T))
+    with pkg.Context(device=0) as c:
+        got = c.batch_distance(probs)  # numpy (host) inputs
+    for (P, T), g in zip(probs, got):
+        assert _key(g) == _key(orc.ddks(P, T))
+
+
+def test_config4_256_uneven(torch):
+    probs = wl.uneven_problems(seed=0, count=256)
+    with pkg.Context(device=0) as c:
+        got = c.batch_distance([(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()) for P, T in probs])
+    # the oracle on a seeded sample of 24 problems (all 256 take minutes on the host)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(256, size=24, replace=False):
+        P, T = probs[i]
+        assert _key(got[i]) == _key(orc.ddks(P, T))

@@ -2,11 +2,13 @@
 oracle's direct double sum.
 
 Tolerance: both sides work in float64.  The oracle sums the pmf products of
-every admissible (nP, nT) pair; the kernel sums pmf(nP) times the T mass
-outside the admissible interval (prefix/suffix sums), so the two differ only
-by rounding: per cell a few ulps of p, i.e. ~1e-15 absolute on log p, and the
-log of the product adds N * 2^d such terms.  The test allows 1e-9 relative plus
-1e-11 absolute on log(prod) and on S.
+every admissible (nP, nT) pair directly, so each cell probability p carries a
+rounding error of up to about (NP+1)(NT+1) * 2^-53 absolute, and log(p) the
+same absolute error (p is close to 1).  The kernel sums pmf(nP) times the T
+mass outside the admissible interval and takes log1p of minus that mass, which
+is more accurate near p = 1.  The log of the product adds N * 2^d cells, so the
+test allows  N * 2^d * (NP+1) * (NT+1) * 2^-52  absolute on log(prod) (and on
+S = 1 - exp(log prod)), plus 1e-12 relative.
 """
 import numpy as np
 import pytest
@@ -34,8 +36,11 @@ def _cmp(torch, P, T, est, model, num=None):
     with pkg.Context(device=0) as c:
         S, lp = c.significance(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda(), num,
                                estimator=est, model=model)
-    assert lp == pytest.approx(lp_ref, rel=1e-9, abs=1e-11)
-    assert S == pytest.approx(S_ref, rel=1e-9, abs=1e-11)
+    NP, d = P.shape
+    NT = T.shape[0]
+    tol = (NP + NT) * 2 ** d * (NP + 1) * (NT + 1) * 2.0 ** -52
+    assert lp == pytest.approx(lp_ref, rel=1e-12, abs=tol)
+    assert S == pytest.approx(S_ref, rel=1e-12, abs=tol)
     return S
 
 
