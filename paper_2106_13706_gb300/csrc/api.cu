@@ -143,7 +143,7 @@ const char* ddks_last_cuda_error(ddks_ctx* ctx) { return ctx ? ctx->last_err.c_s
 int ddks_ctx_stats(ddks_ctx* ctx, ddks_stats* out) {
   if (!ctx || !out) return DDKS_EINVAL;
   ddks_serve_fill_stats(ctx, out);
-  out->kernel_launches = ctx->launches;
+  out->kernel_launches += ctx->launches;
   return DDKS_OK;
 }
 

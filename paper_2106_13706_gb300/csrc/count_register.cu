@@ -376,7 +376,7 @@ k_register(const uint2* __restrict__ words, const OriginMeta* __restrict__ meta,
 }
 
 // one thread per origin: its 2 * 2^DS orthants from gcnt[q][sample][phase][bin]
-__global__ void k_register_final(const uint32_t* __restrict__ gcnt, const OriginMeta* __restrict__ meta,
+__global__ void k_reg_final(const uint32_t* __restrict__ gcnt, const OriginMeta* __restrict__ meta,
                                  int64_t no, int64_t NP, int64_t NT, int64_t ob, int ds,
                                  uint64_t* __restrict__ best, int32_t* __restrict__ bestj) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < no;
@@ -486,7 +486,7 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
       break;
   }
   if (e != cudaSuccess) return e;
-  k_register_final<<<grid(no), 256, 0, st>>>(gcnt, meta, no, NP, NT, ob, ds, best, bestj);
+  k_reg_final<<<grid(no), 256, 0, st>>>(gcnt, meta, no, NP, NT, ob, ds, best, bestj);
   n += 2;
   ctx->launches += n;
   if (e != cudaSuccess) return e;

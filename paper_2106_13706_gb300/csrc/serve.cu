@@ -1,0 +1,259 @@
+// serve.cu -- continuous batching of two-sample ddKS requests.
+//
+// ddks_submit copies a request's points into library-owned host memory and
+// queues it.  Worker threads (two, each with its own internal context and
+// stream) repeatedly admit queued requests in arrival order while the sum of
+// the admitted requests' device footprints stays within the HBM budget and the
+// batch stays within max_batch, run the admitted requests as one batched
+// launch (batch.cu: one persistent kernel over all their work units), and
+// publish the results.  Requests that arrive while a batch is on the GPU join
+// the next one; with two workers two batches overlap on the device.  A
+// request whose footprint alone exceeds the budget is refused at submit with
+// DDKS_ENOMEM.  ddks_poll reads a result, optionally waiting a bounded time.
+// No device code waits on the host: the only waits are host condition
+// variables with timeouts.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "ddks_host.h"
+#include "ddks_internal.cuh"
+
+namespace {
+
+struct Request {
+  uint64_t ticket = 0;
+  std::vector<char> P, T;
+  int64_t NP = 0, NT = 0;
+  int32_t d = 0, dtype = 0;
+  uint64_t footprint = 0;
+  int status = DDKS_PENDING;
+  ddks_result res{};
+};
+
+constexpr int kWorkers = 2;
+
+}  // namespace
+
+struct ServeState {
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<Request>> pending;
+  std::unordered_map<uint64_t, std::shared_ptr<Request>> reqs;
+  uint64_t next_ticket = 1;
+  uint64_t resident = 0, resident_peak = 0;
+  uint64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, batches = 0;
+  bool stop = false;
+  std::vector<std::thread> workers;
+  std::vector<ddks_ctx*> wctx;
+  std::vector<cudaStream_t> streams;
+};
+
+static uint64_t request_footprint(int64_t NP, int64_t NT, int32_t d, int32_t dtype) {
+  const uint64_t N = (uint64_t)(NP + NT);
+  const uint64_t es = dtype == DDKS_F64 ? 8 : 4;
+  // inputs, ranks, per-origin maxima and arg-maxima, sort and key scratch
+  return N * d * (es + 4 + 8 + 24) + N * 12 + 4096;
+}
+
+static void worker_loop(ddks_ctx* owner, int w) {
+  ServeState* S = owner->serve;
+  ddks_ctx* ctx = S->wctx[w];
+  cudaStream_t st = S->streams[w];
+  cudaSetDevice(ctx->device);
+  const uint64_t budget = owner->cfg.hbm_budget_bytes;
+  const int max_batch = owner->cfg.max_batch;
+  for (;;) {
+    std::vector<std::shared_ptr<Request>> batch;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_work.wait(lk, [&] {
+        if (S->stop) return true;
+        return !S->pending.empty() && S->resident + S->pending.front()->footprint <= budget;
+      });
+      if (S->stop) return;
+      while (!S->pending.empty() && (int)batch.size() < max_batch &&
+             S->resident + S->pending.front()->footprint <= budget) {
+        auto r = S->pending.front();
+        S->pending.pop_front();
+        S->resident += r->footprint;
+        S->admitted += 1;
+        batch.push_back(r);
+      }
+      if (S->resident > S->resident_peak) S->resident_peak = S->resident;
+      S->batches += 1;
+    }
+    // group by dtype (one batched launch per dtype)
+    for (int dt = 0; dt < 2; ++dt) {
+      std::vector<const void*> Ps, Ts;
+      std::vector<int64_t> NPs, NTs;
+      std::vector<int32_t> ds;
+      std::vector<std::shared_ptr<Request>> members;
+      for (auto& r : batch)
+        if (r->dtype == dt) {
+          Ps.push_back(r->P.data());
+          Ts.push_back(r->T.data());
+          NPs.push_back(r->NP);
+          NTs.push_back(r->NT);
+          ds.push_back(r->d);
+          members.push_back(r);
+        }
+      if (members.empty()) continue;
+      std::vector<ddks_result> out(members.size());
+      int rc = ddks_batch_distance(ctx, (int32_t)members.size(), Ps.data(), NPs.data(), Ts.data(),
+                                   NTs.data(), ds.data(), dt, st, out.data());
+      if (rc != DDKS_OK) {
+        // find the failing members one by one so one bad request does not fail the rest
+        for (size_t i = 0; i < members.size(); ++i) {
+          ddks_result one{};
+          const int r1 = ddks_distance(ctx, Ps[i], NPs[i], Ts[i], NTs[i], ds[i], dt, st, &one);
+          out[i] = one;
+          out[i].status = r1;
+        }
+      }
+      std::lock_guard<std::mutex> g(S->mu);
+      for (size_t i = 0; i < members.size(); ++i) {
+        members[i]->res = out[i];
+        members[i]->status = out[i].status;
+        members[i]->P.clear();
+        members[i]->P.shrink_to_fit();
+        members[i]->T.clear();
+        members[i]->T.shrink_to_fit();
+      }
+    }
+    {
+      std::lock_guard<std::mutex> g(S->mu);
+      for (auto& r : batch) {
+        S->resident -= r->footprint;
+        S->completed += 1;
+      }
+    }
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+  }
+}
+
+static int serve_start(ddks_ctx* ctx) {
+  if (ctx->serve) return DDKS_OK;
+  ServeState* S = new (std::nothrow) ServeState();
+  if (!S) return DDKS_ENOMEM;
+  ddks_config cfg = ctx->cfg;
+  cfg.device = ctx->device;
+  for (int w = 0; w < kWorkers; ++w) {
+    ddks_ctx* c = nullptr;
+    int rc = ddks_ctx_create(&cfg, &c);
+    cudaStream_t st = nullptr;
+    cudaError_t e = rc == DDKS_OK ? cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) : cudaSuccess;
+    if (rc != DDKS_OK || e != cudaSuccess) {
+      if (c) ddks_ctx_destroy(c);
+      for (size_t i = 0; i < S->wctx.size(); ++i) {
+        cudaStreamDestroy(S->streams[i]);
+        ddks_ctx_destroy(S->wctx[i]);
+      }
+      delete S;
+      return rc != DDKS_OK ? rc : ctx_cuda_fail(ctx, e, "cudaStreamCreate");
+    }
+    S->wctx.push_back(c);
+    S->streams.push_back(st);
+  }
+  ctx->serve = S;
+  for (int w = 0; w < kWorkers; ++w) S->workers.emplace_back(worker_loop, ctx, w);
+  return DDKS_OK;
+}
+
+void ddks_serve_shutdown(ddks_ctx* ctx) {
+  ServeState* S = ctx->serve;
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  S->cv_done.notify_all();
+  for (auto& t : S->workers) t.join();
+  for (size_t i = 0; i < S->wctx.size(); ++i) {
+    cudaStreamDestroy(S->streams[i]);
+    ddks_ctx_destroy(S->wctx[i]);
+  }
+  delete S;
+  ctx->serve = nullptr;
+}
+
+void ddks_serve_fill_stats(ddks_ctx* ctx, ddks_stats* out) {
+  std::memset(out, 0, sizeof(*out));
+  ServeState* S = ctx->serve;
+  if (!S) return;
+  std::lock_guard<std::mutex> g(S->mu);
+  out->submitted = S->submitted;
+  out->admitted = S->admitted;
+  out->completed = S->completed;
+  out->rejected = S->rejected;
+  out->batches = S->batches;
+  out->bytes_resident = S->resident;
+  out->bytes_resident_peak = S->resident_peak;
+  uint64_t k = 0;
+  for (auto* c : S->wctx) k += c->launches;
+  out->kernel_launches = k;
+}
+
+int ddks_submit(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT, int32_t d,
+                int32_t dtype, uint64_t* ticket) {
+  if (!ctx || !ticket) return DDKS_EINVAL;
+  int rc = ddks_check_problem(P, NP, T, NT, d, dtype);
+  if (rc) return rc;
+  if ((rc = serve_start(ctx))) return rc;
+  ServeState* S = ctx->serve;
+  auto r = std::make_shared<Request>();
+  r->NP = NP;
+  r->NT = NT;
+  r->d = d;
+  r->dtype = dtype;
+  r->footprint = request_footprint(NP, NT, d, dtype);
+  if (r->footprint > ctx->cfg.hbm_budget_bytes) {
+    std::lock_guard<std::mutex> g(S->mu);
+    S->rejected += 1;
+    return DDKS_ENOMEM;
+  }
+  const size_t es = dtype == DDKS_F64 ? 8 : 4;
+  // copy the inputs (host or device) so the caller may free them on return
+  r->P.resize(es * (size_t)NP * d);
+  r->T.resize(es * (size_t)NT * d);
+  cudaError_t e = cudaMemcpy(r->P.data(), P, r->P.size(), cudaMemcpyDefault);
+  if (e == cudaSuccess) e = cudaMemcpy(r->T.data(), T, r->T.size(), cudaMemcpyDefault);
+  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "submit copy");
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    r->ticket = S->next_ticket++;
+    S->reqs[r->ticket] = r;
+    S->pending.push_back(r);
+    S->submitted += 1;
+    *ticket = r->ticket;
+  }
+  S->cv_work.notify_one();
+  return DDKS_OK;
+}
+
+int ddks_poll(ddks_ctx* ctx, uint64_t ticket, int32_t timeout_us, ddks_result* out) {
+  if (!ctx || !out) return DDKS_EINVAL;
+  ServeState* S = ctx->serve;
+  if (!S) return DDKS_ENOTFOUND;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return DDKS_ENOTFOUND;
+  std::shared_ptr<Request> r = it->second;
+  if (r->status == DDKS_PENDING && timeout_us > 0) {
+    S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us),
+                        [&] { return r->status != DDKS_PENDING || S->stop; });
+  }
+  if (r->status == DDKS_PENDING) return DDKS_PENDING;
+  *out = r->res;
+  out->status = r->status;
+  S->reqs.erase(it);
+  return r->status;
+}
