@@ -296,14 +296,14 @@ static int distance_impl(ddks_ctx* ctx, const void* P, int64_t NP, const void* T
   const int64_t no = oe - ob;
   if ((rc = ctx->best.reserve(ctx, 8 * (size_t)(no > 0 ? no : 1)))) return out->status = rc;
   if ((rc = ctx->bestj.reserve(ctx, 4 * (size_t)(no > 0 ? no : 1)))) return out->status = rc;
-  if ((rc = ctx->out3.reserve(ctx, 64))) return out->status = rc;
+  if ((rc = ctx->out3.reserve(ctx, 64 + ddks_reduce_scratch_bytes()))) return out->status = rc;
   if ((rc = ddks_count_origins(ctx, NP, NT, d, ob, oe, (uint64_t*)ctx->best.ptr,
                                (int32_t*)ctx->bestj.ptr, st)))
     return out->status = rc;
   stage_mark(ctx, 2, st);
   e = ddks_launch_reduce((const uint64_t*)ctx->best.ptr, (const int32_t*)ctx->bestj.ptr, no, ob,
-                         (unsigned long long*)ctx->out3.ptr, st);
-  ctx->launches += 1;
+                         (unsigned long long*)ctx->out3.ptr, (char*)ctx->out3.ptr + 64, st);
+  ctx->launches += 2;
   if (e != cudaSuccess) return out->status = ctx_cuda_fail(ctx, e, "reduce");
   stage_mark(ctx, 3, st);
   e = cudaMemcpyAsync(ctx->h_out, ctx->out3.ptr, 3 * sizeof(unsigned long long),

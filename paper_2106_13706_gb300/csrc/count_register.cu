@@ -47,63 +47,33 @@ struct OriginMeta {
 
 // ------------------------------------------------------------------ preparation
 
-// One CTA: exclusive scans over the dimension-0 sorted order.
-//   listpos[p]  position of sorted point p in the list (P points in order, then T)
-//   pprefix[r]  number of P points among sorted positions [0, r), r in [0, N]
-//   olist[q]    pooled index of the q-th origin in [ob, oe), in sorted order
-__global__ void __launch_bounds__(1024)
-k_reg_scan(const uint32_t* __restrict__ sidx0, int64_t N, int64_t NP, int64_t ob, int64_t oe,
-           uint32_t* __restrict__ listpos, uint32_t* __restrict__ pprefix,
-           uint32_t* __restrict__ olist) {
-  __shared__ uint32_t wsP[32], wsO[32];
-  __shared__ uint32_t carryP, carryO;
-  if (threadIdx.x == 0) { carryP = 0; carryO = 0; }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t base = 0; base < N; base += blockDim.x) {
-    const int64_t p = base + threadIdx.x;
-    uint32_t i = 0, fP = 0, fO = 0;
-    if (p < N) {
-      i = sidx0[p];
-      fP = i < (uint64_t)NP ? 1u : 0u;
-      fO = (i >= (uint64_t)ob && i < (uint64_t)oe) ? 1u : 0u;
-    }
-    // inclusive warp scans
-    uint32_t sP = fP, sO = fO;
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t a = __shfl_up_sync(0xffffffffu, sP, off);
-      const uint32_t b = __shfl_up_sync(0xffffffffu, sO, off);
-      if (lane >= off) { sP += a; sO += b; }
-    }
-    if (lane == 31) { wsP[warp] = sP; wsO[warp] = sO; }
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t a = lane < (int)(blockDim.x >> 5) ? wsP[lane] : 0u;
-      uint32_t b = lane < (int)(blockDim.x >> 5) ? wsO[lane] : 0u;
-      for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t x = __shfl_up_sync(0xffffffffu, a, off);
-        const uint32_t y = __shfl_up_sync(0xffffffffu, b, off);
-        if (lane >= off) { a += x; b += y; }
-      }
-      wsP[lane] = a;  // inclusive prefix over warps
-      wsO[lane] = b;
-    }
-    __syncthreads();
-    const uint32_t exP = carryP + (warp ? wsP[warp - 1] : 0u) + sP - fP;
-    const uint32_t exO = carryO + (warp ? wsO[warp - 1] : 0u) + sO - fO;
-    if (p < N) {
-      pprefix[p] = exP;
-      listpos[p] = fP ? exP : (uint32_t)(NP + (p - exP));
-      if (fO) olist[exO] = i;
-    }
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) {
-      carryP = exP + fP;
-      carryO = exO + fO;
-    }
-    __syncthreads();
+// Flags over the dimension-0 sorted order: row 0 [p] = (sorted point p is in P),
+// row 1 [p] = (its pooled index is an origin of [ob, oe)).
+__global__ void k_reg_flags(const uint32_t* __restrict__ sidx0, int64_t N, int64_t NP, int64_t ob,
+                            int64_t oe, uint32_t* __restrict__ fP, uint32_t* __restrict__ fO) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = sidx0[p];
+    fP[p] = i < (uint64_t)NP ? 1u : 0u;
+    fO[p] = (i >= (uint64_t)ob && i < (uint64_t)oe) ? 1u : 0u;
   }
-  if (threadIdx.x == 0) pprefix[N] = carryP;
+}
+
+// After exclusive scans of the flags:
+//   listpos[p]  position of sorted point p in the list (P points in order, then T)
+//   pprefix[r]  number of P points among sorted positions [0, r)
+//   olist[q]    pooled index of the q-th origin in [ob, oe), in sorted order
+__global__ void k_reg_lists(const uint32_t* __restrict__ sidx0, int64_t N, int64_t NP, int64_t ob,
+                            int64_t oe, const uint32_t* __restrict__ pprefix,
+                            const uint32_t* __restrict__ exO, uint32_t* __restrict__ listpos,
+                            uint32_t* __restrict__ olist) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = sidx0[p];
+    const uint32_t pp = pprefix[p];
+    listpos[p] = i < (uint64_t)NP ? pp : (uint32_t)(NP + (p - pp));
+    if (i >= (uint64_t)ob && i < (uint64_t)oe) olist[exO[p]] = i;
+  }
 }
 
 // LUT counts: cnt[t][m'][r] += 1 for every origin q of tile t (m' = m - 1).
@@ -116,42 +86,6 @@ __global__ void k_reg_lut_count(const uint32_t* __restrict__ rank, const uint32_
     const int64_t t = q / TS;
     const uint32_t r = rank[(int64_t)(mm + 1) * N + olist[q]];
     atomicAdd(&lut[(t * ds + mm) * N + r], 1u);
-  }
-}
-
-// In-place inclusive scan of each row (one CTA per row of N entries).
-__global__ void __launch_bounds__(1024)
-k_reg_lut_scan(uint32_t* __restrict__ lut, int64_t N) {
-  __shared__ uint32_t ws[32];
-  __shared__ uint32_t carry;
-  uint32_t* row = lut + (int64_t)blockIdx.x * N;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t base = 0; base < N; base += blockDim.x) {
-    const int64_t p = base + threadIdx.x;
-    const uint32_t v = p < N ? row[p] : 0u;
-    uint32_t s = v;
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t a = __shfl_up_sync(0xffffffffu, s, off);
-      if (lane >= off) s += a;
-    }
-    if (lane == 31) ws[warp] = s;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t a = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0u;
-      for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t x = __shfl_up_sync(0xffffffffu, a, off);
-        if (lane >= off) a += x;
-      }
-      ws[lane] = a;
-    }
-    __syncthreads();
-    const uint32_t inc = carry + (warp ? ws[warp - 1] : 0u) + s;
-    if (p < N) row[p] = inc;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = inc;
-    __syncthreads();
   }
 }
 
@@ -228,13 +162,18 @@ struct Acc {
   uint32_t loA, hiA, loB, hiB;    // 8-bit counters (even / odd bins)
 };
 
+template <int MODE>  // 0: phase A only, 1: phase B only, 2: both
 DDKS_DEV void nib_flush(Acc& a) {
-  a.loA += a.nibA & 0x0F0F0F0Fu;
-  a.hiA += (a.nibA >> 4) & 0x0F0F0F0Fu;
-  a.loB += a.nibB & 0x0F0F0F0Fu;
-  a.hiB += (a.nibB >> 4) & 0x0F0F0F0Fu;
-  a.nibA = 0;
-  a.nibB = 0;
+  if (MODE != 1) {
+    a.loA += a.nibA & 0x0F0F0F0Fu;
+    a.hiA += (a.nibA >> 4) & 0x0F0F0F0Fu;
+    a.nibA = 0;
+  }
+  if (MODE != 0) {
+    a.loB += a.nibB & 0x0F0F0F0Fu;
+    a.hiB += (a.nibB >> 4) & 0x0F0F0F0Fu;
+    a.nibB = 0;
+  }
 }
 
 // add the 8-bit counters into shared counts c[phase][bin] and clear them
@@ -264,26 +203,35 @@ DDKS_DEV void add_point(const uint2 w, int j, const uint32_t (&oA)[kR], const ui
   }
 }
 
-// One run [a, b) of tile positions inside one sample: phase-uniform stretches
-// run without a per-pair choice.  MODE 0: all phase A, 1: all phase B,
-// 2: per origin (position < split -> A).  Full chunks of 15 points are
-// unrolled; the nibbles are spread after every chunk and the bytes are added
-// to the shared counts every 17 chunks (255 points).
 template <int DS, int MODE>
-DDKS_DEV void run_points(const uint2* __restrict__ tw, int a, int b, const uint32_t (&oA)[kR],
-                         const uint32_t (&oB)[kR], const int (&spl)[kR], Acc (&acc)[kR],
-                         int& since_flush, uint32_t* cnt_sample) {
+DDKS_DEV void chunk15(const uint2* __restrict__ tw, int j, const uint32_t (&oA)[kR],
+                      const uint32_t (&oB)[kR], const int (&spl)[kR], Acc (&acc)[kR]) {
+#pragma unroll
+  for (int u = 0; u < 15; ++u) add_point<DS, MODE>(tw[j + u], j + u, oA, oB, spl, acc);
+#pragma unroll
+  for (int r = 0; r < kR; ++r) nib_flush<MODE>(acc[r]);
+}
+
+// Positions [a, b) of one sample in the tile.  Chunks of 15 points: a chunk
+// wholly before every split runs in phase A, one wholly at or after every
+// split in phase B, the rest choose per pair.  The nibbles are spread after
+// every chunk; the bytes go to the shared counts every 17 chunks (255 points).
+template <int DS>
+DDKS_DEV void run_points(const uint2* __restrict__ tw, int a, int b, int lo, int hi,
+                         const uint32_t (&oA)[kR], const uint32_t (&oB)[kR], const int (&spl)[kR],
+                         Acc (&acc)[kR], int& since_flush, uint32_t* cnt_sample) {
   int j = a;
   while (j < b) {
     if (b - j >= 15) {
-#pragma unroll
-      for (int u = 0; u < 15; ++u) add_point<DS, MODE>(tw[j + u], j + u, oA, oB, spl, acc);
+      if (j + 15 <= lo) chunk15<DS, 0>(tw, j, oA, oB, spl, acc);
+      else if (j >= hi) chunk15<DS, 1>(tw, j, oA, oB, spl, acc);
+      else chunk15<DS, 2>(tw, j, oA, oB, spl, acc);
       j += 15;
     } else {
-      for (; j < b; ++j) add_point<DS, MODE>(tw[j], j, oA, oB, spl, acc);
-    }
+      for (; j < b; ++j) add_point<DS, 2>(tw[j], j, oA, oB, spl, acc);
 #pragma unroll
-    for (int r = 0; r < kR; ++r) nib_flush(acc[r]);
+      for (int r = 0; r < kR; ++r) nib_flush<2>(acc[r]);
+    }
     if (++since_flush == 17) {
 #pragma unroll
       for (int r = 0; r < kR; ++r) byte_flush(acc[r], cnt_sample + r * 32);
@@ -330,12 +278,15 @@ k_register(const uint2* __restrict__ words, const OriginMeta* __restrict__ meta,
 #pragma unroll
   for (int r = 0; r < kR; ++r) acc[r] = Acc{0, 0, 0, 0, 0, 0};
   uint32_t* mycnt = cnt + (g * kR) * 32;  // origin r of this thread: mycnt + r*32 (+16 for T)
+  int cur = -1;      // sample whose counts the byte counters hold
+  int since = 0;     // chunks since the last byte flush
   for (int64_t base = c0; base < c1; base += kTP) {
     const int cntp = (int)((c1 - base) < kTP ? (c1 - base) : kTP);
     __syncthreads();
     for (int i = tid; i < cntp; i += kThreads) tile[i] = tw_all[base + i];
     __syncthreads();
-    const int64_t per = (cntp + S - 1) / S;
+    // an odd stride between the slices' ranges keeps their loads in distinct banks
+    const int64_t per = ((cntp + S - 1) / S) | 1;
     int64_t a = base + s * per;
     int64_t b = a + per;
     if (b > base + cntp) b = base + cntp;
@@ -344,6 +295,14 @@ k_register(const uint2* __restrict__ words, const OriginMeta* __restrict__ meta,
       const int64_t pa = part == 0 ? a : (a > NP ? a : NP);
       const int64_t pb = part == 0 ? (b < NP ? b : NP) : b;
       if (pa >= pb) continue;
+      if (part != cur) {
+        if (cur >= 0) {
+#pragma unroll
+          for (int r = 0; r < kR; ++r) byte_flush(acc[r], mycnt + cur * 16 + r * 32);
+        }
+        cur = part;
+        since = 0;
+      }
       // splits relative to the tile, clamped to [-1, kTP + 1]
       int spl[kR];
       int lo = kTP + 1, hi = -1;
@@ -355,17 +314,13 @@ k_register(const uint2* __restrict__ words, const OriginMeta* __restrict__ meta,
         lo = spl[r] < lo ? spl[r] : lo;
         hi = spl[r] > hi ? spl[r] : hi;
       }
-      const int ra = (int)(pa - base), rb = (int)(pb - base);
-      const int m1 = lo < ra ? ra : (lo > rb ? rb : lo);
-      const int m2 = hi < m1 ? m1 : (hi > rb ? rb : hi);
-      int since = 0;
-      uint32_t* cs = mycnt + part * 16;
-      run_points<DS, 0>(tile, ra, m1, oA, oB, spl, acc, since, cs);
-      run_points<DS, 2>(tile, m1, m2, oA, oB, spl, acc, since, cs);
-      run_points<DS, 1>(tile, m2, rb, oA, oB, spl, acc, since, cs);
-#pragma unroll
-      for (int r = 0; r < kR; ++r) byte_flush(acc[r], cs + r * 32);
+      run_points<DS>(tile, (int)(pa - base), (int)(pb - base), lo, hi, oA, oB, spl, acc, since,
+                     mycnt + part * 16);
     }
+  }
+  if (cur >= 0) {
+#pragma unroll
+    for (int r = 0; r < kR; ++r) byte_flush(acc[r], mycnt + cur * 16 + r * 32);
   }
   __syncthreads();
   for (int i = tid; i < OC * 32; i += kThreads) {
@@ -424,31 +379,43 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   const int64_t ntiles = direct ? 1 : (no + TS - 1) / TS;
   // scratch: listpos N, pprefix N+1, olist no, lut ntiles*ds*N (if !direct), words ntiles*N uint2,
   // meta no
-  const size_t n_u32 = (size_t)N + (size_t)N + 1 + (size_t)no + (direct ? 0 : (size_t)ntiles * ds * N) +
-                       (size_t)no * 32;
+  const int64_t lut_rows = direct ? 0 : ntiles * ds;
+  const size_t scan_tmp = ddks_scan_tmp_elems(lut_rows > 2 ? lut_rows : 2, N);
+  const size_t n_u32 = (size_t)N + (size_t)N + 1 + (size_t)N + (size_t)no + (size_t)no * 32 +
+                       (size_t)lut_rows * N + scan_tmp;
   int rc = ctx->reg_meta.reserve(ctx, n_u32 * 4 + (size_t)no * sizeof(OriginMeta) + 64);
   if (rc) return cudaErrorMemoryAllocation;
   rc = ctx->reg_words.reserve(ctx, (size_t)ntiles * N * sizeof(uint2));
   if (rc) return cudaErrorMemoryAllocation;
   uint32_t* listpos = (uint32_t*)ctx->reg_meta.ptr;
   uint32_t* pprefix = listpos + N;
-  uint32_t* olist = pprefix + N + 1;
+  uint32_t* exO = pprefix + N + 1;
+  uint32_t* olist = exO + N;
   uint32_t* gcnt = olist + no;
   uint32_t* lut = gcnt + no * 32;
+  uint32_t* stmp = lut + lut_rows * N;
   OriginMeta* meta = reinterpret_cast<OriginMeta*>(
-      (reinterpret_cast<uintptr_t>(lut + (direct ? 0 : ntiles * ds * N)) + 15) & ~(uintptr_t)15);
+      (reinterpret_cast<uintptr_t>(stmp + scan_tmp) + 15) & ~(uintptr_t)15);
   uint2* words = (uint2*)ctx->reg_words.ptr;
   const uint32_t* sidx0 = (const uint32_t*)ctx->sidx0.ptr;
 
-  k_reg_scan<<<1, 1024, 0, st>>>(sidx0, N, NP, ob, oe, listpos, pprefix, olist);
-  int n = 1;
   auto grid = [](int64_t w) { int64_t g = (w + 255) / 256; return (int)(g > 152 * 32 ? 152 * 32 : (g < 1 ? 1 : g)); };
+  int n = 0;
+  k_reg_flags<<<grid(N), 256, 0, st>>>(sidx0, N, NP, ob, oe, pprefix, exO);
+  ++n;
+  // pprefix and exO are adjacent rows of N + 1 and N entries: scan them separately
+  cudaError_t e0 = ddks_scan_rows(pprefix, pprefix, 1, N, true, stmp, st, &n);
+  if (e0 == cudaSuccess) e0 = ddks_scan_rows(exO, exO, 1, N, true, stmp, st, &n);
+  if (e0 != cudaSuccess) return e0;
+  k_reg_lists<<<grid(N), 256, 0, st>>>(sidx0, N, NP, ob, oe, pprefix, exO, listpos, olist);
+  ++n;
   if (!direct) {
-    cudaError_t e = cudaMemsetAsync(lut, 0, (size_t)ntiles * ds * N * 4, st);
+    cudaError_t e = cudaMemsetAsync(lut, 0, (size_t)lut_rows * N * 4, st);
     if (e != cudaSuccess) return e;
     k_reg_lut_count<<<grid(no * ds), 256, 0, st>>>(rank, olist, N, no, ds, (int)TS, lut);
-    k_reg_lut_scan<<<(unsigned)(ntiles * ds), 1024, 0, st>>>(lut, N);
-    n += 2;
+    ++n;
+    e = ddks_scan_rows(lut, lut, lut_rows, N, false, stmp, st, &n);
+    if (e != cudaSuccess) return e;
   }
   k_reg_words<<<grid(ntiles * N), 256, 0, st>>>(rank, lut, sidx0, listpos, N, ds, ntiles, direct, words);
   k_reg_meta<<<grid(no), 256, 0, st>>>(rank, lut, olist, pprefix, N, NP, no, ds, (int)TS, direct, meta);

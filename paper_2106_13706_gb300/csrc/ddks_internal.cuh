@@ -65,8 +65,14 @@ cudaError_t ddks_launch_warp(const uint32_t* rank, int64_t N, int64_t NP, int64_
 cudaError_t ddks_launch_sort(const uint32_t* rank, int64_t N, int64_t NP, int64_t NT, int d,
                              int64_t o_begin, int64_t o_end, uint64_t* best, int32_t* bestj,
                              cudaStream_t st);
+size_t ddks_reduce_scratch_bytes();
 cudaError_t ddks_launch_reduce(const uint64_t* best, const int32_t* bestj, int64_t no,
-                               int64_t o_begin, unsigned long long* out3, cudaStream_t st);
+                               int64_t o_begin, unsigned long long* out3, void* scratch,
+                               cudaStream_t st);
+
+size_t ddks_scan_tmp_elems(int64_t rows, int64_t n);
+cudaError_t ddks_scan_rows(const uint32_t* in, uint32_t* out, int64_t rows, int64_t n, bool exclusive,
+                           uint32_t* tmp, cudaStream_t st, int* launches);
 
 bool ddks_lane_supported(int d, int64_t NP, int64_t NT, int threads);
 bool ddks_warp_supported(int d, int64_t NP, int64_t NT);

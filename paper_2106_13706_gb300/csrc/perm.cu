@@ -213,12 +213,12 @@ int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* 
   // observed statistic
   if ((rc = ctx->best.reserve(ctx, 8 * (size_t)N))) return observed->status = rc;
   if ((rc = ctx->bestj.reserve(ctx, 4 * (size_t)N))) return observed->status = rc;
-  if ((rc = ctx->out3.reserve(ctx, 64))) return observed->status = rc;
+  if ((rc = ctx->out3.reserve(ctx, 64 + ddks_reduce_scratch_bytes()))) return observed->status = rc;
   if ((rc = ddks_count_origins(ctx, NP, NT, d, 0, N, (uint64_t*)ctx->best.ptr, (int32_t*)ctx->bestj.ptr, st)))
     return observed->status = rc;
   e = ddks_launch_reduce((const uint64_t*)ctx->best.ptr, (const int32_t*)ctx->bestj.ptr, N, 0,
-                         (unsigned long long*)ctx->out3.ptr, st);
-  ctx->launches += 1;
+                         (unsigned long long*)ctx->out3.ptr, (char*)ctx->out3.ptr + 64, st);
+  ctx->launches += 2;
   if (e != cudaSuccess) return observed->status = ctx_cuda_fail(ctx, e, "reduce");
   unsigned long long* out3 = (unsigned long long*)ctx->out3.ptr;
   const int G = (B + 31) / 32;
