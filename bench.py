@@ -36,7 +36,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["cfg2", "cfg1", "cfg3"], default="cfg2")
+    ap.add_argument("--workload", choices=["cfg2", "cfg1", "cfg3", "perm", "batch", "serve"],
+                    default="cfg2")
+    ap.add_argument("--perms", type=int, default=1000)
+    ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--path", type=int, default=0, help="force a kernel path (0 = auto)")
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -302,10 +305,188 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_perm(args):
+    """Permutation test of the 3-component mixture (2 x 2,000 points, d = 3)
+    with B relabellings in one batched launch per step."""
+    import torch
+
+    import paper_2106_13706_gb300 as pkg
+    from paper_2106_13706_gb300 import build as bld
+    from paper_2106_13706_gb300 import workloads as wl
+    bld.build()
+    P, T = wl.CONFIGS["cfg4_d3_2000x2000_mixture_null"]()
+    N, d = len(P) + len(T), P.shape[1]
+    B = args.perms
+    Pd, Td = torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device="cuda")
+    ctx = pkg.Context(device=0)
+    for _ in range(max(args.warmup, 3)):
+        ref = ctx.permutation_test(Pd, Td, B, 2021)
+    ms = []
+    stream = torch.cuda.current_stream()
+    l0 = ctx.stats()["kernel_launches"]
+    for s in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = ctx.permutation_test(Pd, Td, B, 2021)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        assert r["p_value"] == ref["p_value"]
+    launches = ctx.stats()["kernel_launches"] - l0
+    tot = sum(ms)
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as orc
+        nb = 4
+        t0 = time.perf_counter()
+        orc.permutation_test(P, T, nb, 2021, nthreads=orc.num_threads())
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / (dt * (B + 1) / (nb + 1)), "unit": "tests/s", "cores": orc.num_threads(),
+               "kind": "oracle", "sample": f"{nb} relabellings + observed ({dt:.2f} s), scaled to B={B}"}
+    ctx.close()
+    print(json.dumps({
+        "metric": "ddks_perm_tests_per_s", "value": args.steps / (tot * 1e-3), "unit": "tests/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 ranks (f32 input)",
+        "data": "synthetic (seeded numpy PCG64)",
+        "config": {"workload": f"permutation test, 3-component Gaussian mixture d=3 NP=NT=2000, B={B}",
+                   "logical_compares_per_s": (B + 1) * float(N) * N * d * args.steps / (tot * 1e-3)},
+        "cpu_baseline": cpu, "gpu_launches": launches, "p_value": ref["p_value"]}))
+
+
+def run_batch(args):
+    """256 uneven problems (NP, NT log-uniform in [64, 8192], d in 2..8): one
+    batched persistent launch per step vs one ddks_distance call per problem."""
+    import torch
+
+    import paper_2106_13706_gb300 as pkg
+    from paper_2106_13706_gb300 import build as bld
+    from paper_2106_13706_gb300 import workloads as wl
+    bld.build()
+    probs = wl.uneven_problems(seed=0, count=256)
+    dev = [(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()) for P, T in probs]
+    units = sum(float(len(P) + len(T)) ** 2 * P.shape[1] for P, T in probs)
+    ctx = pkg.Context(device=0)
+    for _ in range(max(args.warmup, 3)):
+        ref = ctx.batch_distance(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        got = ctx.batch_distance(dev)
+    tb = (time.perf_counter() - t0) / args.steps
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 4)):
+        one = [ctx.distance(P, T) for P, T in dev]
+    t1 = (time.perf_counter() - t0) / max(1, args.steps // 4)
+    assert [g["num_max"] for g in got] == [o["num_max"] for o in one] == [r["num_max"] for r in ref]
+    ctx.close()
+    print(json.dumps({
+        "metric": "ddks_batch_tests_per_s", "value": 256 / tb, "unit": "tests/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tb * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 ranks (f32 input)",
+        "data": "synthetic (seeded numpy PCG64)",
+        "config": {"workload": "256 problems, NP,NT log-uniform [64,8192], d uniform 2..8, mixtures",
+                   "one_call_per_problem_tests_per_s": 256 / t1, "compares_per_s": units / tb}}))
+
+
+def run_serve(args):
+    """Poisson arrivals (200/s) of requests with NP, NT log-uniform in [100, 50000]
+    and d in {2,3,4,6,8}: submit/poll latency percentiles and throughput, against
+    the same stream served one request per call."""
+    import threading
+
+    import torch
+
+    import paper_2106_13706_gb300 as pkg
+    from paper_2106_13706_gb300 import build as bld
+    from paper_2106_13706_gb300 import workloads as wl
+    bld.build()
+    reqs = wl.serving_requests(seed=0, count=args.requests)
+
+    def replay(serve_fn):
+        lat = [None] * len(reqs)
+        t_start = time.perf_counter()
+        threads = []
+        for i, (arr, P, T) in enumerate(reqs):
+            dt = arr - (time.perf_counter() - t_start)
+            if dt > 0:
+                time.sleep(dt)
+            threads.append(serve_fn(i, P, T, lat))
+        for th in threads:
+            if th is not None:
+                th.join()
+        return lat, time.perf_counter() - t_start
+
+    ctx = pkg.Context(device=0, max_batch=64)
+
+    def submit_fn(i, P, T, lat):
+        t0 = time.perf_counter()
+        tk = ctx.submit(P, T)
+
+        def waiter():
+            while True:
+                rc, r = ctx.poll(tk, 200000)
+                if rc == pkg.DDKS_OK:
+                    lat[i] = time.perf_counter() - t0
+                    return
+        th = threading.Thread(target=waiter)
+        th.start()
+        return th
+
+    lat_b, wall_b = replay(submit_fn)
+    st = ctx.stats()
+    ctx.close()
+    # one request per call, FIFO on one worker thread
+    ctx1 = pkg.Context(device=0)
+    import queue
+    qq = queue.Queue()
+
+    def worker():
+        while True:
+            item = qq.get()
+            if item is None:
+                return
+            i, P, T, t0, lat = item
+            ctx1.distance(P, T)
+            lat[i] = time.perf_counter() - t0
+
+    wth = threading.Thread(target=worker)
+    wth.start()
+
+    def single_fn(i, P, T, lat):
+        qq.put((i, P, T, time.perf_counter(), lat))
+        return None
+
+    lat_s, _ = replay(single_fn)
+    qq.put(None)
+    wth.join()
+    wall_s = max(a + l for (a, _, _), l in zip(reqs, lat_s))
+    ctx1.close()
+    pct = lambda xs, q: float(np.percentile(np.array(xs) * 1e3, q))
+    print(json.dumps({
+        "metric": "ddks_serve_tests_per_s", "value": len(reqs) / wall_b, "unit": "tests/s", "n_gpus": 1,
+        "steps": len(reqs), "warmup": 0, "ms_per_step": wall_b * 1e3 / len(reqs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 ranks (f32 input)",
+        "data": "synthetic (seeded numpy PCG64)",
+        "config": {"workload": f"{len(reqs)} Poisson(200/s) requests, NP,NT log-uniform [100,50000], d in {{2,3,4,6,8}}",
+                   "p50_ms": pct(lat_b, 50), "p99_ms": pct(lat_b, 99), "batches": st["batches"],
+                   "one_per_call": {"tests_per_s": len(reqs) / wall_s, "p50_ms": pct(lat_s, 50),
+                                    "p99_ms": pct(lat_s, 99)},
+                   "bytes_resident_peak": st["bytes_resident_peak"]}}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "perm":
+        run_perm(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

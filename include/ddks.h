@@ -183,8 +183,9 @@ int ddks_ctx_stats(ddks_ctx* ctx, ddks_stats* out);
 /*
  * Stage timing.  When enabled, every distance call records CUDA events on its
  * stream around its stages; ddks_stage_times then returns the last call's
- * durations in milliseconds: encode (K0: keys, sort, ranks), count (the orthant
- * count kernel), reduce (max over origins).  Enabling it adds event records,
+ * durations in milliseconds: encode (K0: keys, sort, ranks, and the register
+ * path's packing of the points), count (the orthant count kernel), reduce
+ * (max over origins).  Enabling it adds event records,
  * never extra synchronisation beyond the call's own.
  */
 int ddks_set_stage_timing(ddks_ctx* ctx, int32_t enable);

@@ -435,6 +435,8 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   cudaError_t e = cudaMemsetAsync(gcnt, 0, (size_t)no * 32 * 4, st);
   if (e != cudaSuccess) return e;
   const unsigned ctas = (unsigned)(blocks * C);
+  // stage timing: the count stage starts here (the preparation above counts as encoding)
+  if (ctx->stage_timing) cudaEventRecord(ctx->ev[1], st);
   switch (ds) {
     case 1:
       e = cudaFuncSetAttribute(k_register<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
