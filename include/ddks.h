@@ -191,6 +191,27 @@ int ddks_ctx_stats(ddks_ctx* ctx, ddks_stats* out);
 int ddks_set_stage_timing(ddks_ctx* ctx, int32_t enable);
 int ddks_stage_times(ddks_ctx* ctx, float* encode_ms, float* count_ms, float* reduce_ms);
 
+/*
+ * ddks_distance_noalloc: the exact distance of ddks_distance for callers that
+ * cannot allocate device memory once they are running -- a latency-critical
+ * loop that must not pay cudaMalloc's synchronisation and unbounded latency,
+ * a process whose device memory is already reserved by another allocator, or
+ * code that must keep a fixed device footprint fixed at start-up.  The paper
+ * has no counterpart; this is a calling convention of the library.
+ *
+ * No context is needed and nothing is allocated: the scratch is one static
+ * device array of about 0.7 MiB that every GPU loading the library holds until
+ * the process exits.  P and T must already be device memory (DDKS_EINVAL
+ * otherwise); out is written on the host after the call synchronises stream.
+ * Limits: NP + NT <= 16384 and d <= 8, else DDKS_EUNSUPPORTED.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array: calls whose work overlaps on the GPU (other streams or
+ * host threads on the same device) race and must be serialised by the caller.
+ */
+int ddks_distance_noalloc(const void* P, int64_t NP, const void* T, int64_t NT, int32_t d,
+                          int32_t dtype, void* stream, ddks_result* out);
+
 /* Human-readable text for a return code. */
 const char* ddks_strerror(int code);
 

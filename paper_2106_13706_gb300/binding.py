@@ -88,6 +88,7 @@ def load():
             "ddks_strerror": (ctypes.c_char_p, [i32]),
             "ddks_last_cuda_error": (ctypes.c_char_p, [vp]),
             "ddks_version": (ctypes.c_char_p, []),
+            "ddks_distance_noalloc": (i32, [vp, i64, vp, i64, i32, i32, vp, R]),
             "ddks_set_stage_timing": (i32, [vp, i32]),
             "ddks_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float),
                                        ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
@@ -195,6 +196,14 @@ def ddks_distance(ctx, P, T, stream=None):
     p, NP, t, NT, d, dt, keep = _pair(P, T)
     r = ddks_result()
     _check(load().ddks_distance(ctx, p, NP, t, NT, d, dt, _stream(stream), ctypes.byref(r)), ctx)
+    return r.as_dict()
+
+
+def ddks_distance_noalloc(P, T, stream=None):
+    """Exact distance without any device allocation (device inputs, N <= 16384, d <= 8)."""
+    p, NP, t, NT, d, dt, keep = _pair(P, T)
+    r = ddks_result()
+    _check(load().ddks_distance_noalloc(p, NP, t, NT, d, dt, _stream(stream), ctypes.byref(r)))
     return r.as_dict()
 
 
