@@ -122,8 +122,9 @@ def peak_lane_ops(torch, dev, sm_max_mhz):
 
 
 def load_traffic(kernel_key):
-    """DRAM bytes per launch of the count kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
+    """DRAM bytes per launch of the count kernel from the committed ncu summary
+    (profiles/traffic.json), if it was taken on the current kernel source."""
+    import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -133,8 +134,10 @@ def load_traffic(kernel_key):
         return None
     if not rec:
         return None
-    from paper_2106_13706_gb300 import build as bld
-    if rec.get("source_digest") != bld._digest():
+    src = os.path.join(ROOT, rec["source"])
+    if not os.path.exists(src):
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec.get("source_sha256_16"):
         return None
     return rec.get("bytes_per_launch")
 
@@ -230,7 +233,7 @@ def run_ours(args):
     if cnt:
         achieved = units / (cnt * 1e-3)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
-                "frac": achieved / peak, "traffic": load_traffic(f"count_{args.workload}"),
+                "frac": achieved / peak, "traffic": load_traffic({"cfg2": "count_d4_20k"}.get(args.workload, "")),
                 "kernel": "orthant count kernel", "kernel_ms": cnt,
                 "peak_basis": f"{sms} SMs x 128 int lanes x {mhz:.0f} MHz (max SM clock)"}
 
