@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -165,6 +166,9 @@ def run_ours(args):
     Td = torch.from_numpy(T).cuda()
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device="cuda")
     ctx = pkg.Context(device=local, path=args.path)
+    tuned = None
+    if args.path == 0 and not args.no_autotune:
+        tuned = ctx.autotune(Pd, Td)  # the project's autotuner picks the kernel shape
     ctx.set_stage_timing(True)
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
@@ -247,6 +251,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32 ranks (f32 input)" if P.dtype == np.float32 else "u32 ranks (f64 input)",
         "data": "synthetic (seeded numpy PCG64)",
         "config": {"workload": desc, "N": N, "d": d, "units_per_step": units,
+                   "kernel_path": (["auto", "register", "lane", "warp", "sort"][tuned[0]] if tuned else
+                                   ["auto", "register", "lane", "warp", "sort"][args.path]),
                    "l2": f"flushed between steps ({args.flush_mb} MB write)", "replicas": world},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "num_max": ref["num_max"], "denom": ref["denom"],

@@ -181,6 +181,19 @@ typedef struct {
 int ddks_ctx_stats(ddks_ctx* ctx, ddks_stats* out);
 
 /*
+ * Autotune the orthant-count kernel for this problem shape: every kernel path
+ * and launch shape that can take it (register path built for 2, 3 or 4
+ * resident CTAs per SM; lane-private histograms with 64, 128 or 256 threads
+ * per CTA; per-warp histograms; the sort path) runs on these inputs, timed
+ * with CUDA events on stream; all must produce the same statistic.  The
+ * fastest is kept for the shape's class (d, log2 NP, log2 NT) in the context
+ * and written to the tune cache file when one is configured; later calls with
+ * DDKS_PATH_AUTO use it.  chosen_path and best_ms (optional) report it.
+ */
+int ddks_autotune(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT, int32_t d,
+                  int32_t dtype, void* stream, int32_t* chosen_path, float* best_ms);
+
+/*
  * Stage timing.  When enabled, every distance call records CUDA events on its
  * stream around its stages; ddks_stage_times then returns the last call's
  * durations in milliseconds: encode (K0: keys, sort, ranks, and the register

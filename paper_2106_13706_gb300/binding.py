@@ -89,6 +89,8 @@ def load():
             "ddks_last_cuda_error": (ctypes.c_char_p, [vp]),
             "ddks_version": (ctypes.c_char_p, []),
             "ddks_distance_noalloc": (i32, [vp, i64, vp, i64, i32, i32, vp, R]),
+            "ddks_autotune": (i32, [vp, vp, i64, vp, i64, i32, i32, vp, ctypes.POINTER(i32),
+                                    ctypes.POINTER(ctypes.c_float)]),
             "ddks_set_stage_timing": (i32, [vp, i32]),
             "ddks_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float),
                                        ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
@@ -286,6 +288,16 @@ def ddks_ctx_stats(ctx):
     return {n: int(getattr(s, n)) for n, _ in ddks_stats._fields_}
 
 
+def ddks_autotune(ctx, P, T, stream=None):
+    """Time every kernel configuration on these inputs; returns (path, ms)."""
+    p, NP, t, NT, d, dt, keep = _pair(P, T)
+    path = ctypes.c_int32(0)
+    ms = ctypes.c_float(0)
+    _check(load().ddks_autotune(ctx, p, NP, t, NT, d, dt, _stream(stream), ctypes.byref(path),
+                                ctypes.byref(ms)), ctx)
+    return int(path.value), float(ms.value)
+
+
 def ddks_set_stage_timing(ctx, enable=True):
     _check(load().ddks_set_stage_timing(ctx, 1 if enable else 0), ctx)
 
@@ -347,6 +359,9 @@ class Context:
 
     def stats(self):
         return ddks_ctx_stats(self.h)
+
+    def autotune(self, P, T, stream=None):
+        return ddks_autotune(self.h, P, T, stream)
 
     def set_stage_timing(self, enable=True):
         ddks_set_stage_timing(self.h, enable)

@@ -245,11 +245,16 @@ int ddks_encode_problem(ddks_ctx* ctx, const void* dP, int64_t NP, const void* d
 // Counts + per-origin maxima for origins [ob, oe) on the encoded problem.
 int ddks_count_origins(ddks_ctx* ctx, int64_t NP, int64_t NT, int32_t d, int64_t ob, int64_t oe,
                        uint64_t* best, int32_t* bestj, cudaStream_t st) {
-  const int64_t N = NP + NT;
-  const uint32_t* rank = (const uint32_t*)ctx->rank.ptr;
   ddks_plan plan;
   int rc = ddks_select_path(ctx, NP, NT, d, &plan);
   if (rc) return rc;
+  return ddks_count_origins_plan(ctx, plan, NP, NT, d, ob, oe, best, bestj, st);
+}
+
+int ddks_count_origins_plan(ddks_ctx* ctx, const ddks_plan& plan, int64_t NP, int64_t NT, int32_t d,
+                            int64_t ob, int64_t oe, uint64_t* best, int32_t* bestj, cudaStream_t st) {
+  const int64_t N = NP + NT;
+  const uint32_t* rank = (const uint32_t*)ctx->rank.ptr;
   cudaError_t e = cudaSuccess;
   switch (plan.path) {
     case DDKS_PATH_REGISTER:

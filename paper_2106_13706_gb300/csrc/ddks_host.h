@@ -29,7 +29,7 @@ struct ddks_plan {
   int path = DDKS_PATH_AUTO;
   int threads = 256;  // lane path: threads per CTA (one origin each)
   int warps = 8;      // warp path: warps per CTA (one origin each)
-  int reg_slices = 0;  // register path: threads sharing one origin group (0 = by size)
+  int reg_occ = 4;    // register path: resident CTAs per SM the kernel is built for (2..4)
 };
 
 struct ServeState;  // serve.cu
@@ -76,6 +76,8 @@ int ddks_encode_problem(ddks_ctx* ctx, const void* dP, int64_t NP, const void* d
                         int32_t d, int32_t dtype, cudaStream_t st, bool want_sorted0);
 int ddks_count_origins(ddks_ctx* ctx, int64_t NP, int64_t NT, int32_t d, int64_t ob, int64_t oe,
                        uint64_t* best, int32_t* bestj, cudaStream_t st);
+int ddks_count_origins_plan(ddks_ctx* ctx, const ddks_plan& plan, int64_t NP, int64_t NT, int32_t d,
+                            int64_t ob, int64_t oe, uint64_t* best, int32_t* bestj, cudaStream_t st);
 
 // tune.cu
 int ddks_select_path(ddks_ctx* ctx, int64_t NP, int64_t NT, int32_t d, ddks_plan* plan);

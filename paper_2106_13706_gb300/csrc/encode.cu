@@ -8,16 +8,20 @@
 // exactly, ties included, and every later kernel compares 32-bit integers
 // whatever the input type.
 //
-// Sort: bitonic sort of 2048-element chunks in shared memory, then merge passes
-// in which every element finds its output slot by binary search in the partner
-// run (pairs are unique because the index breaks ties).  Rank: one lower_bound
-// per element in its dimension's sorted keys.
+// Sort: bitonic sort of 8192-element chunks in shared memory.  With at most 16
+// chunks a dimension (N <= 131072) every element then finds its min-rank as
+// the sum of one lower_bound per sorted chunk, and its position in the full
+// (key, index) order for dimension 0.  Larger inputs merge the chunks in
+// passes in which every element finds its output slot by binary search in the
+// partner run (pairs are unique because the index breaks ties), then take one
+// lower_bound per element in the fully sorted keys.
 #include "ddks_internal.cuh"
 
 namespace {
 
-constexpr int kChunk = 2048;
+constexpr int kChunk = 8192;
 constexpr int kChunkThreads = 1024;
+constexpr int64_t kMaxMultiChunks = 16;  // above this, merge passes
 
 template <typename V>
 __global__ void k_encode(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64_t NT,
@@ -42,8 +46,9 @@ DDKS_DEV bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
 __global__ void __launch_bounds__(kChunkThreads)
 k_chunk_sort(const uint64_t* __restrict__ keys, int64_t N, int64_t Npad,
              uint64_t* __restrict__ out_k, uint32_t* __restrict__ out_i) {
-  __shared__ uint64_t sk[kChunk];
-  __shared__ uint32_t si[kChunk];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  uint64_t* sk = reinterpret_cast<uint64_t*>(smraw);   // [kChunk]
+  uint32_t* si = reinterpret_cast<uint32_t*>(sk + kChunk);
   const int m = blockIdx.y;
   const int64_t base = (int64_t)blockIdx.x * kChunk;
   for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
@@ -116,6 +121,44 @@ __global__ void k_merge_pass(const uint64_t* __restrict__ in_k, const uint32_t* 
   }
 }
 
+// With few sorted chunks: rank[m][i] = sum over chunks of #{keys < key_i}
+// (one lower_bound per chunk), and for dimension 0 the position of (key_i, i)
+// in the full sorted order, which places i in sorted_idx0.
+__global__ void k_rank_multi(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ ck,
+                             const uint32_t* __restrict__ ci, int64_t N, int64_t Npad, int d,
+                             uint32_t* __restrict__ rank, uint32_t* __restrict__ sorted_idx0) {
+  const int64_t total = N * d;
+  const int64_t nch = Npad / kChunk;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = e / N;
+    const int64_t i = e - m * N;
+    const uint64_t key = keys[e];
+    uint32_t r = 0, pos = 0;
+    for (int64_t c = 0; c < nch; ++c) {
+      const uint64_t* K = ck + m * Npad + c * kChunk;
+      int lo = 0, hi = kChunk;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (K[mid] < key) lo = mid + 1; else hi = mid;
+      }
+      r += (uint32_t)lo;
+      if (m == 0 && sorted_idx0) {
+        // continue past equal keys with a smaller index
+        const uint32_t* I = ci + m * Npad + c * kChunk;
+        int lo2 = lo, hi2 = kChunk;
+        while (lo2 < hi2) {
+          const int mid = (lo2 + hi2) >> 1;
+          if (K[mid] == key && I[mid] < (uint32_t)i) lo2 = mid + 1; else hi2 = mid;
+        }
+        pos += (uint32_t)lo2;
+      }
+    }
+    rank[e] = r;
+    if (m == 0 && sorted_idx0) sorted_idx0[pos] = (uint32_t)i;
+  }
+}
+
 // rank[m][i] = #{j : key_j < key_i}, by lower_bound in the sorted keys of m.
 __global__ void k_rank(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ sorted_k,
                        int64_t N, int64_t Npad, int d, uint32_t* __restrict__ rank) {
@@ -175,8 +218,17 @@ cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int d, uint64_t* t
   const int64_t Npad = (int64_t)ddks_rank_scratch_elems(N);
   const int64_t chunks = Npad / kChunk;
   dim3 g((unsigned)chunks, (unsigned)d);
-  k_chunk_sort<<<g, kChunkThreads, 0, st>>>(keys, N, Npad, tmp_keys, tmp_idx);
+  const size_t smem = (size_t)kChunk * 12;
+  cudaError_t e = cudaFuncSetAttribute(k_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_chunk_sort<<<g, kChunkThreads, smem, st>>>(keys, N, Npad, tmp_keys, tmp_idx);
   int n = 1;
+  if (chunks <= kMaxMultiChunks) {
+    k_rank_multi<<<grid_for(N * d, 256), 256, 0, st>>>(keys, tmp_keys, tmp_idx, N, Npad, d, rank,
+                                                       sorted_idx0);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+  }
   uint64_t *ck = tmp_keys, *nk = tmp_keys2;
   uint32_t *ci = tmp_idx, *ni = tmp_idx2;
   for (int64_t L = kChunk; L < Npad; L <<= 1) {

@@ -224,3 +224,14 @@ def test_register_path_rerank_tiles(torch, d):
             ref = orc.ddks(P, T, origins=(a, b), per_origin=True)
             assert np.array_equal(got["per_origin"], ref["per_origin"])
             _same(got, ref)
+
+
+@pytest.mark.parametrize("d", [2, 4, 6])
+def test_autotune_picks_an_agreeing_path(torch, d):
+    P, T = wl.random_pair(60 + d, 3000, 2500, d, kind="normal")
+    ref = orc.ddks(P, T)
+    with _ctx() as c:
+        path, ms = c.autotune(_dev(torch, P), _dev(torch, T))
+        assert path in (pkg.PATH_REGISTER, pkg.PATH_LANE, pkg.PATH_WARP, pkg.PATH_SORT)
+        assert ms > 0
+        _same(c.distance(_dev(torch, P), _dev(torch, T)), ref)
