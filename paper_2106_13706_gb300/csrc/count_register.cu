@@ -44,6 +44,7 @@ constexpr int kOC = kG * kR;       // origins per CTA (128: re-ranked values fit
 constexpr int kCh = 12;            // points per chunk (<= 15 for 4-bit counters)
 constexpr int kTP = kCh * kS * 22; // points per staged tile (2112)
 constexpr int64_t kMaxRegN = 200000;
+constexpr int kSlot = 17;          // shared counter words per origin (16 + 1 pad: no bank aliasing)
 
 struct OriginMeta {
   uint32_t sP, sT;  // splits in list coordinates: P part [0, NP), T part [NP, N)
@@ -211,8 +212,9 @@ k_register(const uint32_t* __restrict__ rankL, const uint32_t* __restrict__ rank
            int64_t CLP, int64_t CLT, int NW, uint32_t* __restrict__ gcnt) {
   extern __shared__ __align__(16) uint32_t sm[];
   uint32_t* tile = sm;                                        // [kTP] packed words
-  uint32_t* cnt = tile + kTP;                                 // [kOC][2 phases][8 bins]
-  uint32_t* bits = cnt + kOC * 16;                            // [DS][NW] bitmaps over ranks
+  uint32_t* raw = tile + kTP;                                 // [DS][kTP] next tile's ranks
+  uint32_t* cnt = raw + DS * kTP;                             // [kOC][17]: [2 phases][8 bins] + pad
+  uint32_t* bits = cnt + kOC * kSlot;                         // [DS][NW] bitmaps over ranks
   uint8_t* pre = reinterpret_cast<uint8_t*>(bits + DS * NW);  // [DS][NW] word prefix counts
   const int tid = threadIdx.x;
   const int g = tid / kS, s = tid - g * kS;
@@ -231,7 +233,7 @@ k_register(const uint32_t* __restrict__ rankL, const uint32_t* __restrict__ rank
   const int nq = (int)((no - q0) < kOC ? (no - q0) : kOC);
 
   // re-rank tables of this CTA's origins
-  for (int i = tid; i < kOC * 16; i += kThreads) cnt[i] = 0;
+  for (int i = tid; i < kOC * kSlot; i += kThreads) cnt[i] = 0;
   for (int i = tid; i < DS * NW; i += kThreads) bits[i] = 0;
   __syncthreads();
   for (int i = tid; i < nq * DS; i += kThreads) {
@@ -282,19 +284,32 @@ k_register(const uint32_t* __restrict__ rankL, const uint32_t* __restrict__ rank
   Acc acc[kR];
 #pragma unroll
   for (int r = 0; r < kR; ++r) acc[r] = Acc{0, 0, 0, 0, 0, 0};
-  uint32_t* mycnt = cnt + (g * kR) * 16;  // origin r of this thread: mycnt + r * 16
-  int since = 0;  // chunks since the last byte flush
+  uint32_t* mycnt = cnt + (g * kR) * kSlot;  // origin r of this thread: mycnt + r * kSlot
+  int since = 0;  // chunk iterations since the last byte flush (uniform across the CTA)
+  // raw ranks of a tile are copied asynchronously while the previous tile is counted
+  auto prefetch = [&](int64_t base) {
+    const int cntp = (int)((c1 - base) < kTP ? (c1 - base) : kTP);
+    for (int i = tid; i < DS * cntp; i += kThreads) {
+      const int mm = i / cntp, ii = i - mm * cntp;
+      const uint32_t* src = rankL + (int64_t)mm * N + base + ii;
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(raw + mm * kTP + ii);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  prefetch(c0);
   for (int64_t base = c0; base < c1; base += kTP) {
     const int cntp = (int)((c1 - base) < kTP ? (c1 - base) : kTP);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     for (int i = tid; i < cntp; i += kThreads) {
       uint32_t w = 0;
 #pragma unroll
-      for (int mm = 0; mm < DS; ++mm)
-        w |= (rerank(mm, rankL[(int64_t)mm * N + base + i]) | 0x100u) << (9 * mm);
+      for (int mm = 0; mm < DS; ++mm) w |= (rerank(mm, raw[mm * kTP + i]) | 0x100u) << (9 * mm);
       tile[i] = w;
     }
     __syncthreads();
+    if (base + kTP < c1) prefetch(base + kTP);
     // splits relative to the tile, clamped to [-1, kTP + 1]
     int spl[kR];
     int lo = kTP + 1, hi = -1;
@@ -306,28 +321,32 @@ k_register(const uint32_t* __restrict__ rankL, const uint32_t* __restrict__ rank
       lo = spl[r] < lo ? spl[r] : lo;
       hi = spl[r] > hi ? spl[r] : hi;
     }
-    for (int j = s * kCh; j < cntp; j += kS * kCh) {
-      const int n = cntp - j < kCh ? cntp - j : kCh;
-      if (n == kCh) {
-        if (j + kCh <= lo) chunk12<DS, 0>(tile, j, ow, spl, acc);
-        else if (j >= hi) chunk12<DS, 1>(tile, j, ow, spl, acc);
-        else chunk12<DS, 2>(tile, j, ow, spl, acc);
-      } else {
-        chunk_partial<DS>(tile, j, n, ow, spl, acc);
+    const int iters = (cntp + kS * kCh - 1) / (kS * kCh);
+    for (int it = 0; it < iters; ++it) {
+      const int j = (it * kS + s) * kCh;
+      if (j < cntp) {
+        const int n = cntp - j < kCh ? cntp - j : kCh;
+        if (n == kCh) {
+          if (j + kCh <= lo) chunk12<DS, 0>(tile, j, ow, spl, acc);
+          else if (j >= hi) chunk12<DS, 1>(tile, j, ow, spl, acc);
+          else chunk12<DS, 2>(tile, j, ow, spl, acc);
+        } else {
+          chunk_partial<DS>(tile, j, n, ow, spl, acc);
+        }
       }
       if (++since == 21) {
 #pragma unroll
-        for (int r = 0; r < kR; ++r) byte_flush(acc[r], mycnt + r * 16);
+        for (int r = 0; r < kR; ++r) byte_flush(acc[r], mycnt + r * kSlot);
         since = 0;
       }
     }
   }
 #pragma unroll
-  for (int r = 0; r < kR; ++r) byte_flush(acc[r], mycnt + r * 16);
+  for (int r = 0; r < kR; ++r) byte_flush(acc[r], mycnt + r * kSlot);
   __syncthreads();
   for (int i = tid; i < nq * 16; i += kThreads) {
-    const uint32_t v = cnt[i];
-    if (v) atomicAdd(&gcnt[(q0 + i / 16) * 32 + sample * 16 + (i & 15)], v);
+    const uint32_t v = cnt[(i >> 4) * kSlot + (i & 15)];
+    if (v) atomicAdd(&gcnt[(q0 + (i >> 4)) * 32 + sample * 16 + (i & 15)], v);
   }
 }
 
@@ -354,7 +373,7 @@ __global__ void k_reg_final(const uint32_t* __restrict__ gcnt, const OriginMeta*
 }
 
 size_t reg_smem(int ds, int NW) {
-  return (size_t)kTP * 4 + (size_t)kOC * 16 * 4 + (size_t)ds * NW * 4 + (size_t)ds * NW + 16;
+  return (size_t)kTP * 4 * (1 + ds) + (size_t)kOC * kSlot * 4 + (size_t)ds * NW * 4 + (size_t)ds * NW + 16;
 }
 
 }  // namespace
@@ -400,7 +419,7 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   n += 2;
   const int64_t blocks = (no + kOC - 1) / kOC;
   // chunks of the lists per origin block: about 8 waves of the resident CTAs
-  const int64_t slots = (int64_t)ctx->num_sms * (plan.reg_occ == 2 || plan.reg_occ == 3 ? plan.reg_occ : 4);
+  const int64_t slots = (int64_t)ctx->num_sms * 3;
   int64_t want = (8 * slots + blocks - 1) / blocks;  // chunks per block
   if (want < 2) want = 2;
   int64_t CL = (N + want - 1) / want;
@@ -414,7 +433,8 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   const unsigned ctas = (unsigned)(blocks * C);
   // stage timing: the count stage starts here (the preparation above counts as encoding)
   if (ctx->stage_timing) cudaEventRecord(ctx->ev[1], st);
-  const int occ = plan.reg_occ == 2 || plan.reg_occ == 3 ? plan.reg_occ : 4;
+  int occ = plan.reg_occ == 2 || plan.reg_occ == 3 ? plan.reg_occ : 4;
+  while (occ > 2 && (size_t)occ * (smem + 1024) > 227u * 1024u) --occ;  // shared memory bound
   auto go = [&](auto kern) -> cudaError_t {
     cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (r != cudaSuccess) return r;
