@@ -8,8 +8,8 @@
 // exactly, ties included, and every later kernel compares 32-bit integers
 // whatever the input type.
 //
-// Sort: bitonic sort of 8192-element chunks in shared memory.  With at most 16
-// chunks a dimension (N <= 131072) every element then finds its min-rank as
+// Sort: bitonic sort of 2048-element chunks in shared memory.  With at most 4
+// chunks a dimension (N <= 8192) every element then finds its min-rank as
 // the sum of one lower_bound per sorted chunk, and its position in the full
 // (key, index) order for dimension 0.  Larger inputs merge the chunks in
 // passes in which every element finds its output slot by binary search in the
@@ -19,9 +19,9 @@
 
 namespace {
 
-constexpr int kChunk = 8192;
+constexpr int kChunk = 2048;
 constexpr int kChunkThreads = 1024;
-constexpr int64_t kMaxMultiChunks = 16;  // above this, merge passes
+constexpr int64_t kMaxMultiChunks = 4;  // above this, merge passes
 
 template <typename V>
 __global__ void k_encode(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64_t NT,

@@ -156,6 +156,195 @@ k_perm_count(const uint32_t* __restrict__ rank, int64_t N, int64_t NP, int B, in
   }
 }
 
+// ---------------------------------------------------------------- bit-sliced K4
+//
+// For N <= 4000 or so (the staged labels and per-warp buckets must fit shared
+// memory) and d <= 5 the relabellings are counted 32 at a time in bit
+// slices.  A pass takes 256 relabellings (8 label words per point, staged in
+// shared memory).  A warp takes an origin, buckets the N points by orthant
+// code (warp-private counting sort: the point order of every bin), and walks
+// the bins: lane (gg, sub) adds the label words of word gg for a quarter of the
+// bin's points into a bit-sliced counter (Harley-Seal carry-save adders over
+// 16 words at a time, higher planes by ripple), so one 32-bit operation counts
+// 32 relabellings.  The four quarters are summed with shuffles, each lane
+// extracts the counts of 8 relabellings, and keeps their running maximum of
+// |cP*N - n*NP| (n = bin size).  The pass ends with one atomicMax per
+// relabelling.
+constexpr int kBitsMaxN = 4096;
+constexpr int kBitsWarps = 8;
+constexpr int kPassWords = 8;                 // label words per point per pass
+constexpr int kPassPerms = 32 * kPassWords;   // 256 relabellings per pass
+constexpr int kHiPlanes = 8;                  // planes of weight 16..2048 (counts < 4096)
+
+DDKS_DEV void csa(uint32_t& h, uint32_t& l, uint32_t a, uint32_t b, uint32_t c) {
+  const uint32_t u = a ^ b;
+  h = (a & b) | (u & c);
+  l = u ^ c;
+}
+
+struct Slices {
+  uint32_t ones, twos, fours, eights;
+  uint32_t hi[kHiPlanes];
+};
+
+DDKS_DEV void slices_zero(Slices& z) {
+  z.ones = z.twos = z.fours = z.eights = 0;
+#pragma unroll
+  for (int k = 0; k < kHiPlanes; ++k) z.hi[k] = 0;
+}
+
+// add a weight-16 word into the high planes
+DDKS_DEV void add16(Slices& z, uint32_t w) {
+#pragma unroll
+  for (int k = 0; k < kHiPlanes; ++k) {
+    const uint32_t t = z.hi[k] & w;
+    z.hi[k] ^= w;
+    w = t;
+  }
+}
+
+// plane k of the counter (weights 1, 2, 4, 8, 16, ..., 2048)
+DDKS_DEV uint32_t plane(const Slices& z, int k) {
+  return k == 0 ? z.ones : k == 1 ? z.twos : k == 2 ? z.fours : k == 3 ? z.eights : z.hi[k - 4];
+}
+
+// z += the counter held by lane (lane ^ off): bit-sliced ripple addition
+DDKS_DEV void add_partner(Slices& z, int off) {
+  constexpr int K = 4 + kHiPlanes;
+  uint32_t carry = 0;
+  uint32_t out[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t a = plane(z, k);
+    const uint32_t b = __shfl_xor_sync(0xffffffffu, a, off);
+    const uint32_t u = a ^ b;
+    out[k] = u ^ carry;
+    carry = (a & b) | (u & carry);
+  }
+  z.ones = out[0]; z.twos = out[1]; z.fours = out[2]; z.eights = out[3];
+#pragma unroll
+  for (int k = 0; k < kHiPlanes; ++k) z.hi[k] = out[4 + k];
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBitsWarps * 32, 1)
+k_perm_bits(const uint32_t* __restrict__ rank, int64_t N, int64_t NP, int B, int G,
+            const uint32_t* __restrict__ labels, unsigned long long* __restrict__ perm_best) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  constexpr int NB = 1 << D;
+  const int n = (int)N;
+  uint32_t* lab = sm;                                            // [N][8]
+  uint8_t* codes = reinterpret_cast<uint8_t*>(lab + n * kPassWords);  // [warps][N]
+  uint16_t* idx = reinterpret_cast<uint16_t*>(codes + kBitsWarps * ((n + 15) & ~15));  // [warps][N]
+  uint32_t* bins = reinterpret_cast<uint32_t*>(idx + kBitsWarps * ((n + 15) & ~15));   // [warps][3][NB]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gg = lane & 7, sub = lane >> 3;
+  uint8_t* wc = codes + warp * ((n + 15) & ~15);
+  uint16_t* wi = idx + warp * ((n + 15) & ~15);
+  uint32_t* wcnt = bins + warp * 3 * NB;   // counts, offsets, cursors
+  const int64_t per = (N + gridDim.x - 1) / gridDim.x;
+  const int64_t k0 = blockIdx.x * per;
+  const int64_t k1 = k0 + per < N ? k0 + per : N;
+  const int npass = (B + kPassPerms - 1) / kPassPerms;
+  for (int pass = 0; pass < npass; ++pass) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * kPassWords; e += blockDim.x) {
+      const int p = e / kPassWords, w = e - p * kPassWords;
+      const int grp = pass * kPassWords + w;
+      lab[e] = grp < G ? labels[(int64_t)p * G + grp] : 0u;
+    }
+    __syncthreads();
+    uint32_t mx[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) mx[t] = 0;
+    for (int64_t k = k0 + warp; k < k1; k += kBitsWarps) {
+      // orthant codes of every point and a counting sort of them (warp-private)
+      uint32_t o[D];
+#pragma unroll
+      for (int m = 0; m < D; ++m) o[m] = rank[(int64_t)m * N + k];
+      if (lane < NB) wcnt[lane] = 0;
+      __syncwarp();
+      for (int i = lane; i < n; i += 32) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int m = 0; m < D; ++m) c |= (uint32_t)(rank[(int64_t)m * N + i] >= o[m]) << m;
+        wc[i] = (uint8_t)c;
+        atomicAdd(&wcnt[c], 1u);
+      }
+      __syncwarp();
+      {
+        const uint32_t v = lane < NB ? wcnt[lane] : 0u;
+        uint32_t incl = v;
+        for (int off = 1; off < 32; off <<= 1) {
+          const uint32_t a = __shfl_up_sync(0xffffffffu, incl, off);
+          if (lane >= off) incl += a;
+        }
+        if (lane < NB) { wcnt[NB + lane] = incl - v; wcnt[2 * NB + lane] = incl - v; }
+      }
+      __syncwarp();
+      for (int i = lane; i < n; i += 32) {
+        const uint32_t c = wc[i];
+        wi[atomicAdd(&wcnt[2 * NB + c], 1u)] = (uint16_t)i;
+      }
+      __syncwarp();
+      for (int j = 0; j < NB; ++j) {
+        const int cnt = (int)wcnt[j];
+        if (cnt == 0) continue;
+        const int start = (int)wcnt[NB + j];
+        // quarter of the bin for this sub-lane: [qa, qb)
+        const int q = (cnt + 3) >> 2;
+        const int qa = start + sub * q;
+        int qb = qa + q;
+        if (qb > start + cnt) qb = start + cnt;
+        Slices z;
+        slices_zero(z);
+        for (int b0 = qa; b0 < qb; b0 += 16) {
+          uint32_t w[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) w[u] = (b0 + u < qb) ? lab[(int)wi[b0 + u] * kPassWords + gg] : 0u;
+          uint32_t tA, tB, fA, fB, eA, eB, s16;
+          csa(tA, z.ones, z.ones, w[0], w[1]);
+          csa(tB, z.ones, z.ones, w[2], w[3]);
+          csa(fA, z.twos, z.twos, tA, tB);
+          csa(tA, z.ones, z.ones, w[4], w[5]);
+          csa(tB, z.ones, z.ones, w[6], w[7]);
+          csa(fB, z.twos, z.twos, tA, tB);
+          csa(eA, z.fours, z.fours, fA, fB);
+          csa(tA, z.ones, z.ones, w[8], w[9]);
+          csa(tB, z.ones, z.ones, w[10], w[11]);
+          csa(fA, z.twos, z.twos, tA, tB);
+          csa(tA, z.ones, z.ones, w[12], w[13]);
+          csa(tB, z.ones, z.ones, w[14], w[15]);
+          csa(fB, z.twos, z.twos, tA, tB);
+          csa(eB, z.fours, z.fours, fA, fB);
+          csa(s16, z.eights, z.eights, eA, eB);
+          add16(z, s16);
+        }
+        // sum the four quarters (lanes gg, gg+8, gg+16, gg+24)
+        add_partner(z, 8);
+        add_partner(z, 16);
+        const uint64_t nb = (uint64_t)cnt * (uint64_t)NP;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int b = sub * 8 + t;
+          uint32_t c = 0;
+#pragma unroll
+          for (int kk = 0; kk < 4 + kHiPlanes; ++kk) c |= ((plane(z, kk) >> b) & 1u) << kk;
+          const uint64_t x = (uint64_t)c * (uint64_t)N;
+          const uint64_t num = x > nb ? x - nb : nb - x;
+          mx[t] = num > mx[t] ? (uint32_t)num : mx[t];
+        }
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int b = pass * kPassPerms + gg * 32 + sub * 8 + t;
+      if (b < B) atomicMax(&perm_best[b], (unsigned long long)mx[t]);
+    }
+  }
+}
+
 __global__ void k_perm_pvalue(const unsigned long long* __restrict__ perm_best, int B,
                               const unsigned long long* __restrict__ obs,
                               unsigned long long* __restrict__ count) {
@@ -245,7 +434,26 @@ int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* 
     if (e == cudaSuccess) {
       const uint32_t* rank = (const uint32_t*)ctx->rank.ptr;
       const uint32_t* lab = (const uint32_t*)ctx->perm_labels.ptr;
-      switch (d) {
+      const int n16 = (int)((N + 15) & ~15);
+      const size_t smem = (size_t)N * kPassWords * 4 + (size_t)kBitsWarps * n16 * 3 +
+                          (size_t)kBitsWarps * 3 * (1 << d) * 4 + 16;
+      if (N <= kBitsMaxN && d <= 5 && smem <= 227u * 1024u) {
+        auto go = [&](auto kern) -> cudaError_t {
+          cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          if (r != cudaSuccess) return r;
+          int grid = ctx->num_sms;
+          if (grid > N) grid = (int)N;
+          kern<<<grid, kBitsWarps * 32, smem, st>>>(rank, N, NP, B, G, lab, pbest);
+          return cudaGetLastError();
+        };
+        switch (d) {
+          case 1: e = go(k_perm_bits<1>); break;
+          case 2: e = go(k_perm_bits<2>); break;
+          case 3: e = go(k_perm_bits<3>); break;
+          case 4: e = go(k_perm_bits<4>); break;
+          default: e = go(k_perm_bits<5>); break;
+        }
+      } else switch (d) {
         case 1: e = launch_count<1>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
         case 2: e = launch_count<2>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
         case 3: e = launch_count<3>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
