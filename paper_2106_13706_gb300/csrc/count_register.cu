@@ -112,9 +112,19 @@ struct Swar {
   static constexpr uint32_t kW = 0x04040400u;
 };
 
+// a * b + c on the FMA pipe: b is the kernel argument `one` (= 1), which the
+// compiler cannot fold, so the add is not moved onto the ALU pipe that the
+// mask and shift already load
+DDKS_DEV uint32_t mad(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+
+// on = -o (the origin's word negated): x - o = x + on
 template <int DS>
-DDKS_DEV uint32_t one_hot(uint32_t x, uint32_t o) {
-  const uint32_t g = (x - o) & Swar<DS>::kGuard;
+DDKS_DEV uint32_t one_hot(uint32_t x, uint32_t on, uint32_t one) {
+  const uint32_t g = mad(on, one, x) & Swar<DS>::kGuard;
   const uint32_t sh = __dp4a(g, Swar<DS>::kW, 0u);
   uint32_t inc;
   asm("shf.l.wrap.b32 %0, %1, %2, %3;" : "=r"(inc) : "r"(0u), "r"(1u), "r"(sh));
@@ -127,15 +137,15 @@ struct Acc {
 };
 
 template <int MODE>  // 0: phase A only, 1: phase B only, 2: both
-DDKS_DEV void nib_flush(Acc& a) {
+DDKS_DEV void nib_flush(Acc& a, uint32_t one) {
   if (MODE != 1) {
-    a.loA += a.nibA & 0x0F0F0F0Fu;
-    a.hiA += (a.nibA >> 4) & 0x0F0F0F0Fu;
+    a.loA = mad(a.nibA & 0x0F0F0F0Fu, one, a.loA);
+    a.hiA = mad((a.nibA >> 4) & 0x0F0F0F0Fu, one, a.hiA);
     a.nibA = 0;
   }
   if (MODE != 0) {
-    a.loB += a.nibB & 0x0F0F0F0Fu;
-    a.hiB += (a.nibB >> 4) & 0x0F0F0F0Fu;
+    a.loB = mad(a.nibB & 0x0F0F0F0Fu, one, a.loB);
+    a.hiB = mad((a.nibB >> 4) & 0x0F0F0F0Fu, one, a.hiB);
     a.nibB = 0;
   }
 }
@@ -157,11 +167,11 @@ DDKS_DEV void byte_flush(Acc& a, uint32_t* c) {
 // two points at once: their one-hots are added with one 3-input add
 template <int DS, int MODE>
 DDKS_DEV void add_two(uint32_t x0, uint32_t x1, int j, const uint32_t (&ow)[kR],
-                      const int (&spl)[kR], Acc (&acc)[kR]) {
+                      const int (&spl)[kR], Acc (&acc)[kR], uint32_t one) {
 #pragma unroll
   for (int r = 0; r < kR; ++r) {
-    const uint32_t i0 = one_hot<DS>(x0, ow[r]);
-    const uint32_t i1 = one_hot<DS>(x1, ow[r]);
+    const uint32_t i0 = one_hot<DS>(x0, ow[r], one);
+    const uint32_t i1 = one_hot<DS>(x1, ow[r], one);
     if (MODE == 0) {
       acc[r].nibA = acc[r].nibA + i0 + i1;
     } else if (MODE == 1) {
@@ -175,31 +185,32 @@ DDKS_DEV void add_two(uint32_t x0, uint32_t x1, int j, const uint32_t (&ow)[kR],
 
 template <int DS, int MODE>
 DDKS_DEV void chunk12(const uint32_t* __restrict__ tile, int j, const uint32_t (&ow)[kR],
-                      const int (&spl)[kR], Acc (&acc)[kR]) {
+                      const int (&spl)[kR], Acc (&acc)[kR], uint32_t one) {
   const uint4* p = reinterpret_cast<const uint4*>(tile + j);
 #pragma unroll
   for (int v = 0; v < 3; ++v) {
     const uint4 w = p[v];
-    add_two<DS, MODE>(w.x, w.y, j + 4 * v, ow, spl, acc);
-    add_two<DS, MODE>(w.z, w.w, j + 4 * v + 2, ow, spl, acc);
+    add_two<DS, MODE>(w.x, w.y, j + 4 * v, ow, spl, acc, one);
+    add_two<DS, MODE>(w.z, w.w, j + 4 * v + 2, ow, spl, acc, one);
   }
 #pragma unroll
-  for (int r = 0; r < kR; ++r) nib_flush<MODE>(acc[r]);
+  for (int r = 0; r < kR; ++r) nib_flush<MODE>(acc[r], one);
 }
 
 template <int DS>
 DDKS_DEV void chunk_partial(const uint32_t* __restrict__ tile, int j, int n,
-                            const uint32_t (&ow)[kR], const int (&spl)[kR], Acc (&acc)[kR]) {
+                            const uint32_t (&ow)[kR], const int (&spl)[kR], Acc (&acc)[kR],
+                            uint32_t one) {
   for (int u = 0; u < n; ++u) {
     const uint32_t x = tile[j + u];
 #pragma unroll
     for (int r = 0; r < kR; ++r) {
-      const uint32_t inc = one_hot<DS>(x, ow[r]);
+      const uint32_t inc = one_hot<DS>(x, ow[r], one);
       if (j + u < spl[r]) acc[r].nibA += inc; else acc[r].nibB += inc;
     }
   }
 #pragma unroll
-  for (int r = 0; r < kR; ++r) nib_flush<2>(acc[r]);
+  for (int r = 0; r < kR; ++r) nib_flush<2>(acc[r], one);
 }
 
 // Unit u: origin block u / C, chunk u % C of the lists, where chunks
@@ -209,7 +220,7 @@ template <int DS, int OCC>
 __global__ void __launch_bounds__(kThreads, OCC)
 k_register(const uint32_t* __restrict__ rankL, const uint32_t* __restrict__ rank,
            const OriginMeta* __restrict__ meta, int64_t no, int64_t N, int64_t NP, int C, int CP,
-           int64_t CLP, int64_t CLT, int NW, uint32_t* __restrict__ gcnt) {
+           int64_t CLP, int64_t CLT, int NW, uint32_t one, uint32_t* __restrict__ gcnt) {
   extern __shared__ __align__(16) uint32_t sm[];
   uint32_t* tile = sm;                                        // [kTP] packed words
   uint32_t* raw = tile + kTP;                                 // [DS][kTP] next tile's ranks
@@ -274,7 +285,7 @@ k_register(const uint32_t* __restrict__ rankL, const uint32_t* __restrict__ rank
       uint32_t w = 0;
 #pragma unroll
       for (int mm = 0; mm < DS; ++mm) w |= rerank(mm, rank[(int64_t)(mm + 1) * N + m.k]) << (9 * mm);
-      ow[r] = w;
+      ow[r] = 0u - w;  // negated: the subtract becomes a multiply-add
       sa[r] = (int)(sample == 0 ? m.sP : m.sT);
     } else {
       ow[r] = 0;  // padding origin: its counts are discarded
@@ -327,11 +338,11 @@ k_register(const uint32_t* __restrict__ rankL, const uint32_t* __restrict__ rank
       if (j < cntp) {
         const int n = cntp - j < kCh ? cntp - j : kCh;
         if (n == kCh) {
-          if (j + kCh <= lo) chunk12<DS, 0>(tile, j, ow, spl, acc);
-          else if (j >= hi) chunk12<DS, 1>(tile, j, ow, spl, acc);
-          else chunk12<DS, 2>(tile, j, ow, spl, acc);
+          if (j + kCh <= lo) chunk12<DS, 0>(tile, j, ow, spl, acc, one);
+          else if (j >= hi) chunk12<DS, 1>(tile, j, ow, spl, acc, one);
+          else chunk12<DS, 2>(tile, j, ow, spl, acc, one);
         } else {
-          chunk_partial<DS>(tile, j, n, ow, spl, acc);
+          chunk_partial<DS>(tile, j, n, ow, spl, acc, one);
         }
       }
       if (++since == 21) {
@@ -438,7 +449,7 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   auto go = [&](auto kern) -> cudaError_t {
     cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (r != cudaSuccess) return r;
-    kern<<<ctas, kThreads, smem, st>>>(rankL, rank, meta, no, N, NP, (int)C, (int)CP, CLP, CLT, NW, gcnt);
+    kern<<<ctas, kThreads, smem, st>>>(rankL, rank, meta, no, N, NP, (int)C, (int)CP, CLP, CLT, NW, 1u, gcnt);
     return cudaGetLastError();
   };
   if (ds == 1) e = occ == 2 ? go(k_register<1, 2>) : occ == 3 ? go(k_register<1, 3>) : go(k_register<1, 4>);
