@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--workload", choices=["cfg2", "cfg1", "cfg3", "perm", "batch", "serve"],
                     default="cfg2")
     ap.add_argument("--perms", type=int, default=1000)
-    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--requests", type=int, default=600)
     ap.add_argument("--path", type=int, default=0, help="force a kernel path (0 = auto)")
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")

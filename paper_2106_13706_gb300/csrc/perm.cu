@@ -4,9 +4,9 @@
 // smallest (key, index), key(b, i) = word (i mod 4) of Philox4x64-10 (Salmon,
 // Moraes, Dror, Shaw, SC 2011) with counter (i / 4, b, 0, 0) and key (seed, 0).
 //
-// K3 (k_perm_labels): one CTA per relabelling draws the N keys, sorts the
-//   (key, index) pairs in shared memory and sets bit b of the label words of
-//   the NP smallest: labels[i][b / 32] bit (b % 32) = [i in permuted P].
+// K3 (k_perm_labels_warp): one warp per relabelling draws the N keys, selects
+//   the NP smallest (key, index) pairs by radix selection and sets bit b of
+//   their label words: labels[i][b / 32] bit (b % 32) = [i in permuted P].
 // K4 (k_perm_count): the orthant code c(o, x) of a pair does not depend on the
 //   labels, so each CTA takes an origin, computes the N codes once into shared
 //   memory together with n(c) = #{x : c(o, x) = c}, and then counts, for every
@@ -22,7 +22,6 @@
 
 namespace {
 
-constexpr int kLabelThreads = 1024;
 constexpr int kMaxPermN = 16384;
 constexpr int kCountThreads = 256;
 constexpr int kPtsTile = 64;
@@ -40,47 +39,86 @@ DDKS_DEV void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
   }
 }
 
-DDKS_DEV bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
-  return ka < kb || (ka == kb && ia < ib);
-}
 
-// grid-stride over relabellings; dynamic smem: P2 keys (u64) + P2 indices (u32)
-__global__ void __launch_bounds__(kLabelThreads)
-k_perm_labels(int64_t N, int64_t NP, int B, uint64_t seed, int G, uint32_t* __restrict__ labels) {
+// K3, one warp per relabelling: the N Philox keys go to warp-private shared
+// memory, a most-significant-digit radix selection (eight 8-bit digits) finds
+// the NP-th smallest key K* and how many keys equal to K* belong to P, and
+// the points with key < K*, plus the lowest-index ones with key == K*, get
+// bit b.  Same labels as sorting the (key, index) pairs.
+__global__ void k_perm_labels_warp(int64_t N, int64_t NP, int B, uint64_t seed, int G,
+                                   int warps_per_cta, uint32_t* __restrict__ labels) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  int P2 = 1;
-  while (P2 < N) P2 <<= 1;
-  uint64_t* sk = reinterpret_cast<uint64_t*>(smraw);
-  uint32_t* si = reinterpret_cast<uint32_t*>(sk + P2);
-  for (int b = blockIdx.x; b < B; b += gridDim.x) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < P2; i += blockDim.x) {
-      if (i < N) {
-        uint64_t c[4] = {(uint64_t)(i >> 2), (uint64_t)b, 0ull, 0ull};
-        philox4x64_10(c, seed, 0ull);
-        sk[i] = c[i & 3];
-      } else {
-        sk[i] = ~0ull;  // pads: largest key, unique index, never among the NP smallest
-      }
-      si[i] = (uint32_t)i;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp >= warps_per_cta) return;
+  const int n = (int)N;
+  uint64_t* key = reinterpret_cast<uint64_t*>(smraw) + (size_t)warp * n;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(reinterpret_cast<uint64_t*>(smraw) + (size_t)warps_per_cta * n) +
+                   warp * 256;
+  for (int b = blockIdx.x * warps_per_cta + warp; b < B; b += gridDim.x * warps_per_cta) {
+    for (int c = lane; 4 * c < n; c += 32) {
+      uint64_t ctr[4] = {(uint64_t)c, (uint64_t)b, 0ull, 0ull};
+      philox4x64_10(ctr, seed, 0ull);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (4 * c + q < n) key[4 * c + q] = ctr[q];
     }
-    __syncthreads();
-    for (int size = 2; size <= P2; size <<= 1) {
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int t = threadIdx.x; t < P2 / 2; t += blockDim.x) {
-          const int lo = 2 * t - (t & (stride - 1));
-          const int hi = lo + stride;
-          const bool asc = ((lo & size) == 0);
-          const uint64_t ka = sk[lo], kb = sk[hi];
-          const uint32_t ia = si[lo], ib = si[hi];
-          const bool swap = asc ? pair_less(kb, ib, ka, ia) : pair_less(ka, ia, kb, ib);
-          if (swap) { sk[lo] = kb; sk[hi] = ka; si[lo] = ib; si[hi] = ia; }
+    __syncwarp();
+    uint64_t prefix = 0, pmask = 0;
+    uint32_t target = (uint32_t)(NP - 1);  // 0-based rank of the last P point
+    for (int dg = 7; dg >= 0; --dg) {
+      for (int v = lane; v < 256; v += 32) hist[v] = 0;
+      __syncwarp();
+      for (int i = lane; i < n; i += 32) {
+        const uint64_t k = key[i];
+        if ((k & pmask) == prefix) atomicAdd(&hist[(k >> (8 * dg)) & 255u], 1u);
+      }
+      __syncwarp();
+      // lane l owns digits 8l..8l+7: find the digit holding rank `target`
+      uint32_t h[8], loc = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { h[q] = hist[8 * lane + q]; loc += h[q]; }
+      uint32_t incl = loc;
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t a = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += a;
+      }
+      const uint32_t excl = incl - loc;
+      const bool mine = target >= excl && target < incl;
+      const unsigned owner = __ffs(__ballot_sync(0xffffffffu, mine)) - 1;
+      uint32_t digit = 0, below = 0;
+      if (mine) {
+        uint32_t run = excl;
+        bool found = false;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (!found && target < run + h[q]) {
+            digit = 8 * lane + q;
+            below = run;
+            found = true;
+          }
+          run += h[q];
         }
-        __syncthreads();
       }
+      digit = __shfl_sync(0xffffffffu, digit, owner);
+      below = __shfl_sync(0xffffffffu, below, owner);
+      target -= below;
+      prefix |= (uint64_t)digit << (8 * dg);
+      pmask |= (uint64_t)255 << (8 * dg);
+      __syncwarp();
     }
-    for (int r = threadIdx.x; r < NP; r += blockDim.x)
-      atomicOr(&labels[(int64_t)si[r] * G + (b >> 5)], 1u << (b & 31));
+    // keys < prefix go to P; of the keys == prefix, the (target + 1) lowest indices
+    uint32_t taken = 0;
+    for (int base = 0; base < n; base += 32) {
+      const int i = base + lane;
+      const uint64_t k = i < n ? key[i] : ~0ull;
+      const bool eq = i < n && k == prefix;
+      const unsigned m = __ballot_sync(0xffffffffu, eq);
+      const uint32_t before = taken + __popc(m & ((1u << lane) - 1u));
+      const bool inP = i < n && (k < prefix || (eq && before <= target));
+      if (inP) atomicOr(&labels[(int64_t)i * G + (b >> 5)], 1u << (b & 31));
+      taken += __popc(m);
+    }
+    __syncwarp();
   }
 }
 
@@ -420,13 +458,16 @@ int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* 
     e = cudaMemsetAsync(ctx->perm_labels.ptr, 0, 4 * (size_t)N * G, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(pbest, 0, 8 * (size_t)B, st);
     if (e == cudaSuccess) {
-      int P2 = 1;
-      while (P2 < N) P2 <<= 1;
-      const size_t smem = (size_t)P2 * 12;
-      e = cudaFuncSetAttribute(k_perm_labels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      int wpc = (int)((200 * 1024) / ((size_t)N * 8 + 1024));
+      if (wpc > 8) wpc = 8;
+      if (wpc < 1) wpc = 1;
+      const size_t smem = (size_t)wpc * ((size_t)N * 8 + 1024);
+      e = cudaFuncSetAttribute(k_perm_labels_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess) {
-        const int grid = B < ctx->num_sms * 2 ? B : ctx->num_sms * 2;
-        k_perm_labels<<<grid, kLabelThreads, smem, st>>>(N, NP, B, seed, G, (uint32_t*)ctx->perm_labels.ptr);
+        int grid = (B + wpc - 1) / wpc;
+        if (grid > ctx->num_sms * 4) grid = ctx->num_sms * 4;
+        k_perm_labels_warp<<<grid, wpc * 32, smem, st>>>(N, NP, B, seed, G, wpc,
+                                                         (uint32_t*)ctx->perm_labels.ptr);
         e = cudaGetLastError();
         ctx->launches += 1;
       }
