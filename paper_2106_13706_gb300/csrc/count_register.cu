@@ -253,20 +253,37 @@ k_register(const uint32_t* __restrict__ rankL, const uint32_t* __restrict__ rank
     atomicOr(&bits[m * NW + (r >> 5)], 1u << (r & 31));
   }
   __syncthreads();
-  if (tid < 32 * DS) {  // one warp per dimension: exclusive prefix of popcounts
-    const int m = tid >> 5, lane = tid & 31;
-    uint32_t carry = 0;
-    for (int base = 0; base < NW; base += 32) {
-      const int w = base + lane;
-      const uint32_t c = w < NW ? (uint32_t)__popc(bits[m * NW + w]) : 0u;
-      uint32_t incl = c;
-      for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t a = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += a;
+  {  // exclusive prefix of the popcounts, per dimension: each warp scans one
+     // contiguous segment of every dimension, segment totals combine in cnt
+    const int warp = tid >> 5, lane = tid & 31;
+    constexpr int W = kThreads / 32;
+    const int seg = (NW + W - 1) / W;
+    uint32_t* segsum = cnt;  // [DS][W], cleared again below
+    for (int m = 0; m < DS; ++m) {
+      const int a = warp * seg, b = a + seg < NW ? a + seg : NW;
+      uint32_t carry = 0;
+      for (int base = a; base < b; base += 32) {
+        const int w = base + lane;
+        const uint32_t c = w < b ? (uint32_t)__popc(bits[m * NW + w]) : 0u;
+        uint32_t incl = c;
+        for (int off = 1; off < 32; off <<= 1) {
+          const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
+          if (lane >= off) incl += x;
+        }
+        if (w < b) pre[m * NW + w] = (uint8_t)(carry + incl - c);
+        carry += __shfl_sync(0xffffffffu, incl, 31);
       }
-      if (w < NW) pre[m * NW + w] = (uint8_t)(carry + incl - c);
-      carry += __shfl_sync(0xffffffffu, incl, 31);
+      if (lane == 0) segsum[m * W + warp] = carry;
     }
+    __syncthreads();
+    for (int m = 0; m < DS; ++m) {
+      uint32_t off = 0;
+      for (int w = 0; w < warp; ++w) off += segsum[m * W + w];
+      const int a = warp * seg, b = a + seg < NW ? a + seg : NW;
+      for (int w = a + lane; w < b; w += 32) pre[m * NW + w] = (uint8_t)(pre[m * NW + w] + off);
+    }
+    __syncthreads();
+    for (int i = tid; i < DS * W; i += kThreads) segsum[i] = 0;
   }
   __syncthreads();
   // x' = #{distinct origin values whose rank <= r}
@@ -300,11 +317,12 @@ k_register(const uint32_t* __restrict__ rankL, const uint32_t* __restrict__ rank
   // raw ranks of a tile are copied asynchronously while the previous tile is counted
   auto prefetch = [&](int64_t base) {
     const int cntp = (int)((c1 - base) < kTP ? (c1 - base) : kTP);
-    for (int i = tid; i < DS * cntp; i += kThreads) {
-      const int mm = i / cntp, ii = i - mm * cntp;
-      const uint32_t* src = rankL + (int64_t)mm * N + base + ii;
-      const unsigned dst = (unsigned)__cvta_generic_to_shared(raw + mm * kTP + ii);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+#pragma unroll
+    for (int mm = 0; mm < DS; ++mm) {
+      const uint32_t* src = rankL + (int64_t)mm * N + base;
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(raw + mm * kTP);
+      for (int i = tid; i < cntp; i += kThreads)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + 4u * i), "l"(src + i) : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
