@@ -447,9 +447,9 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   k_reg_meta<<<grid(no), 256, 0, st>>>(rank, olist, pprefix, NP, no, meta);
   n += 2;
   const int64_t blocks = (no + kOC - 1) / kOC;
-  // chunks of the lists per origin block: about 8 waves of the resident CTAs
+  // chunks of the lists per origin block: about 3 waves of the resident CTAs
   const int64_t slots = (int64_t)ctx->num_sms * 3;
-  int64_t want = (8 * slots + blocks - 1) / blocks;  // chunks per block
+  int64_t want = (3 * slots + blocks - 1) / blocks;  // chunks per block
   if (want < 2) want = 2;
   int64_t CL = (N + want - 1) / want;
   if (CL < 2 * kTP) CL = 2 * kTP;
