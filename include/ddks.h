@@ -77,6 +77,7 @@ typedef struct {
   int32_t max_batch;          /* serving: most requests per device batch (0 = 64) */
   int32_t wait_limit_ms;      /* bound on any host or device wait (0 = 10000) */
   const char* tune_cache;     /* autotuner cache file (NULL = $DDKS_TUNE_CACHE, else none) */
+  int32_t graphs;             /* 1 (default): replay CUDA graphs for repeated calls, see below; 0 = off */
 } ddks_config;
 
 typedef struct {
@@ -94,7 +95,19 @@ typedef struct ddks_ctx ddks_ctx;
 void ddks_config_default(ddks_config* cfg);
 
 /* Create a context on cfg->device (NULL cfg = defaults).  The context owns all
-   device scratch; it grows on demand and is freed by ddks_ctx_destroy. */
+   device scratch; it grows on demand and is freed by ddks_ctx_destroy.
+
+   Graph replay (cfg.graphs = 1): ddks_distance, ddks_distance_range,
+   ddks_permutation_test and ddks_batch_distance enqueue their kernels as one
+   CUDA graph when a call repeats an earlier one's shapes (NP, NT, d, dtype,
+   origin range, B, the kernel path) and device input addresses.  The second
+   such call captures the graph, later ones replay it with one launch.  The
+   graph reads the inputs at replay time, so new values at the same addresses
+   are seen; the permutation seed is uploaded per call, so it may change.  A
+   capture is dropped when the context's scratch has been reallocated since.
+   Host inputs are copied into context scratch first and so always repeat.
+   While stage timing (ddks_set_stage_timing) is on, calls run kernel by
+   kernel, so that the stage events bracket the stages. */
 int ddks_ctx_create(const ddks_config* cfg, ddks_ctx** out);
 int ddks_ctx_destroy(ddks_ctx* ctx);
 
@@ -175,7 +188,9 @@ typedef struct {
   uint64_t batches;            /* device batches launched by the scheduler */
   uint64_t bytes_resident;     /* device bytes held by admitted requests now */
   uint64_t bytes_resident_peak;
-  uint64_t kernel_launches;    /* kernels launched by this context so far */
+  uint64_t kernel_launches;    /* kernels launched by this context so far (graph replays included) */
+  uint64_t graph_captures;     /* CUDA graphs captured by this context */
+  uint64_t graph_replays;      /* calls served by replaying a captured graph */
 } ddks_stats;
 
 int ddks_ctx_stats(ddks_ctx* ctx, ddks_stats* out);

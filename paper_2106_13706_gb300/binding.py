@@ -38,7 +38,8 @@ class DdksError(RuntimeError):
 class ddks_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_int32),
-                ("wait_limit_ms", ctypes.c_int32), ("tune_cache", ctypes.c_char_p)]
+                ("wait_limit_ms", ctypes.c_int32), ("tune_cache", ctypes.c_char_p),
+                ("graphs", ctypes.c_int32)]
 
 
 class ddks_result(ctypes.Structure):
@@ -55,7 +56,7 @@ class ddks_result(ctypes.Structure):
 class ddks_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("submitted", "admitted", "completed", "rejected", "batches", "bytes_resident",
-                 "bytes_resident_peak", "kernel_launches")]
+                 "bytes_resident_peak", "kernel_launches", "graph_captures", "graph_replays")]
 
 
 def load():
@@ -178,13 +179,14 @@ def _pair(P, T):
 
 # ------------------------------------------------------------------ entry points
 def ddks_ctx_create(device=-1, path=PATH_AUTO, hbm_budget_bytes=0, max_batch=0, wait_limit_ms=0,
-                    tune_cache=None):
+                    tune_cache=None, graphs=True):
     lib = load()
     cfg = ddks_config()
     lib.ddks_config_default(ctypes.byref(cfg))
     cfg.device, cfg.path = device, path
     cfg.hbm_budget_bytes, cfg.max_batch, cfg.wait_limit_ms = hbm_budget_bytes, max_batch, wait_limit_ms
     cfg.tune_cache = tune_cache.encode() if tune_cache else None
+    cfg.graphs = 1 if graphs else 0
     h = ctypes.c_void_p()
     _check(lib.ddks_ctx_create(ctypes.byref(cfg), ctypes.byref(h)), what="ddks_ctx_create")
     return h

@@ -40,6 +40,7 @@ void ddks_config_default(ddks_config* cfg) {
   cfg->max_batch = 0;
   cfg->wait_limit_ms = 0;
   cfg->tune_cache = nullptr;
+  cfg->graphs = 1;
 }
 
 int ctx_cuda_fail(ddks_ctx* ctx, cudaError_t e, const char* where) {
@@ -65,6 +66,7 @@ int DevBuf::reserve(ddks_ctx* ctx, size_t n) {
   if (ptr) cudaFree(ptr);
   ptr = nullptr;
   bytes = 0;
+  ++ctx->buf_gen;  // graphs captured before this point hold the old address
   size_t want = n + n / 4 + 256;
   cudaError_t e = cudaMalloc(&ptr, want);
   if (e != cudaSuccess) {
@@ -129,6 +131,7 @@ int ddks_ctx_destroy(ddks_ctx* ctx) {
   cudaSetDevice(ctx->device);
   ddks_serve_shutdown(ctx);
   cudaDeviceSynchronize();
+  ddks_graph_clear(ctx);
   for (DevBuf* b : ctx->all_bufs()) b->release();
   if (ctx->h_out) cudaFreeHost(ctx->h_out);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -144,6 +147,8 @@ int ddks_ctx_stats(ddks_ctx* ctx, ddks_stats* out) {
   if (!ctx || !out) return DDKS_EINVAL;
   ddks_serve_fill_stats(ctx, out);
   out->kernel_launches += ctx->launches;
+  out->graph_captures = ctx->graph_captures;
+  out->graph_replays = ctx->graph_replays;
   return DDKS_OK;
 }
 
@@ -169,9 +174,12 @@ int ddks_stage_times(ddks_ctx* ctx, float* encode_ms, float* count_ms, float* re
   return DDKS_OK;
 }
 
-static void stage_mark(ddks_ctx* ctx, int i, cudaStream_t st) {
+// Records stage event i on st (stage timing turns graph replay off, so this
+// never runs inside a capture).
+void ddks_stage_mark(ddks_ctx* ctx, int i, cudaStream_t st) {
   if (ctx->stage_timing) cudaEventRecord(ctx->ev[i], st);
 }
+static void stage_mark(ddks_ctx* ctx, int i, cudaStream_t st) { ddks_stage_mark(ctx, i, st); }
 
 static void stage_collect(ddks_ctx* ctx) {
   if (!ctx->stage_timing) return;
@@ -294,23 +302,33 @@ static int distance_impl(ddks_ctx* ctx, const void* P, int64_t NP, const void* T
   if ((rc = ddks_stage_inputs(ctx, P, NP, T, NT, d, dtype, st, &dP, &dT))) return out->status = rc;
   ddks_plan plan;
   if ((rc = ddks_select_path(ctx, NP, NT, d, &plan))) return out->status = rc;
-  stage_mark(ctx, 0, st);
-  if ((rc = ddks_encode_problem(ctx, dP, NP, dT, NT, d, dtype, st, plan.path == DDKS_PATH_REGISTER)))
-    return out->status = rc;
-  stage_mark(ctx, 1, st);
   const int64_t no = oe - ob;
-  if ((rc = ctx->best.reserve(ctx, 8 * (size_t)(no > 0 ? no : 1)))) return out->status = rc;
-  if ((rc = ctx->bestj.reserve(ctx, 4 * (size_t)(no > 0 ? no : 1)))) return out->status = rc;
-  if ((rc = ctx->out3.reserve(ctx, 64 + ddks_reduce_scratch_bytes()))) return out->status = rc;
-  if ((rc = ddks_count_origins(ctx, NP, NT, d, ob, oe, (uint64_t*)ctx->best.ptr,
-                               (int32_t*)ctx->bestj.ptr, st)))
-    return out->status = rc;
-  stage_mark(ctx, 2, st);
-  e = ddks_launch_reduce((const uint64_t*)ctx->best.ptr, (const int32_t*)ctx->bestj.ptr, no, ob,
-                         (unsigned long long*)ctx->out3.ptr, (char*)ctx->out3.ptr + 64, st);
-  ctx->launches += 2;
-  if (e != cudaSuccess) return out->status = ctx_cuda_fail(ctx, e, "reduce");
-  stage_mark(ctx, 3, st);
+  GraphKey key;
+  key.add(1).add((uint64_t)NP).add((uint64_t)NT).add((uint64_t)d).add((uint64_t)dtype);
+  key.add((uint64_t)ob).add((uint64_t)oe).add((uint64_t)plan.path).add((uint64_t)plan.threads);
+  key.add((uint64_t)plan.warps).add((uint64_t)plan.reg_occ).add_ptr(dP).add_ptr(dT);
+  key.add((uint64_t)ctx->stage_timing);
+  rc = ddks_graph_run(ctx, key.h, st, [&](cudaStream_t s) -> int {
+    int r;
+    stage_mark(ctx, 0, s);
+    if ((r = ddks_encode_problem(ctx, dP, NP, dT, NT, d, dtype, s, plan.path == DDKS_PATH_REGISTER)))
+      return r;
+    stage_mark(ctx, 1, s);
+    if ((r = ctx->best.reserve(ctx, 8 * (size_t)(no > 0 ? no : 1)))) return r;
+    if ((r = ctx->bestj.reserve(ctx, 4 * (size_t)(no > 0 ? no : 1)))) return r;
+    if ((r = ctx->out3.reserve(ctx, 64 + ddks_reduce_scratch_bytes()))) return r;
+    if ((r = ddks_count_origins_plan(ctx, plan, NP, NT, d, ob, oe, (uint64_t*)ctx->best.ptr,
+                                     (int32_t*)ctx->bestj.ptr, s)))
+      return r;
+    stage_mark(ctx, 2, s);
+    cudaError_t ee = ddks_launch_reduce((const uint64_t*)ctx->best.ptr, (const int32_t*)ctx->bestj.ptr, no,
+                                        ob, (unsigned long long*)ctx->out3.ptr, (char*)ctx->out3.ptr + 64, s);
+    ctx->launches += 2;
+    if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "reduce");
+    stage_mark(ctx, 3, s);
+    return DDKS_OK;
+  });
+  if (rc) return out->status = rc;
   e = cudaMemcpyAsync(ctx->h_out, ctx->out3.ptr, 3 * sizeof(unsigned long long),
                       cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
@@ -322,6 +340,7 @@ static int distance_impl(ddks_ctx* ctx, const void* P, int64_t NP, const void* T
   stage_collect(ctx);
   const unsigned flags = (unsigned)(ctx->h_out[4] & 0xFFFFFFFFull);
   if (flags & ddks::kFlagNaN) return out->status = DDKS_ENAN;
+  if (flags & ddks::kFlagTimeout) return out->status = DDKS_ETIMEOUT;
   out->num_max = ctx->h_out[0];
   out->denom = (uint64_t)NP * (uint64_t)NT;
   out->D = (double)out->num_max / (double)out->denom;

@@ -390,36 +390,46 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
     std::memcpy(hs + sizeof(BatchDesc) * nb, cta_prob.data(), 4 * cta_prob.size());
     std::memcpy(hs + sizeof(BatchDesc) * nb + 4 * cta_prob.size(), cta_dim.data(), 4 * cta_dim.size());
     e = cudaMemcpyAsync(dd, hs, up, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "batch descriptors");
     unsigned long long* work = (unsigned long long*)ctx->batch_work.ptr;
     unsigned long long* res = work + 1;
-    if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, 8, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->flags.ptr, 0, 4, st);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_batch_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rank);
-    if (e == cudaSuccess) {
-      k_batch_rank<<<(unsigned)cta_prob.size(), 1024, smem_rank, st>>>(
-          ddesc, dprob, ddim, (uint32_t*)ctx->rank.ptr, (unsigned*)ctx->flags.ptr);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_batch_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_unit);
-    if (e == cudaSuccess) {
-      int blocks_per_sm = 1;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_batch_count, kThreads, smem_unit);
-      if (blocks_per_sm < 1) blocks_per_sm = 1;
-      int64_t grid = (int64_t)ctx->num_sms * blocks_per_sm;
-      if (grid > units) grid = units;
-      k_batch_count<<<(unsigned)grid, kThreads, smem_unit, st>>>(
-          ddesc, nb, units, (const uint32_t*)ctx->rank.ptr, work, (uint64_t*)ctx->best.ptr,
-          (int32_t*)ctx->bestj.ptr);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
-      k_batch_reduce<<<nb, 1024, 0, st>>>(ddesc, (const uint64_t*)ctx->best.ptr,
-                                          (const int32_t*)ctx->bestj.ptr, res);
-      e = cudaGetLastError();
-    }
-    ctx->launches += 3;
+    // the descriptors hold every shape and input address the kernels see
+    GraphKey key;
+    key.add(3).add((uint64_t)nb).add((uint64_t)units).add((uint64_t)smem_rank).add((uint64_t)smem_unit);
+    key.add_bytes(hs, up);
+    rc = ddks_graph_run(ctx, key.h, st, [&](cudaStream_t s) -> int {
+      cudaError_t ee = cudaMemsetAsync(work, 0, 8, s);
+      if (ee == cudaSuccess) ee = cudaMemsetAsync(ctx->flags.ptr, 0, 4, s);
+      if (ee == cudaSuccess)
+        ee = cudaFuncSetAttribute(k_batch_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rank);
+      if (ee == cudaSuccess) {
+        k_batch_rank<<<(unsigned)cta_prob.size(), 1024, smem_rank, s>>>(
+            ddesc, dprob, ddim, (uint32_t*)ctx->rank.ptr, (unsigned*)ctx->flags.ptr);
+        ee = cudaGetLastError();
+      }
+      if (ee == cudaSuccess)
+        ee = cudaFuncSetAttribute(k_batch_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_unit);
+      if (ee == cudaSuccess) {
+        int blocks_per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_batch_count, kThreads, smem_unit);
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+        int64_t grid = (int64_t)ctx->num_sms * blocks_per_sm;
+        if (grid > units) grid = units;
+        k_batch_count<<<(unsigned)grid, kThreads, smem_unit, s>>>(
+            ddesc, nb, units, (const uint32_t*)ctx->rank.ptr, work, (uint64_t*)ctx->best.ptr,
+            (int32_t*)ctx->bestj.ptr);
+        ee = cudaGetLastError();
+      }
+      if (ee == cudaSuccess) {
+        k_batch_reduce<<<nb, 1024, 0, s>>>(ddesc, (const uint64_t*)ctx->best.ptr,
+                                           (const int32_t*)ctx->bestj.ptr, res);
+        ee = cudaGetLastError();
+      }
+      ctx->launches += 3;
+      if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "batch");
+      return DDKS_OK;
+    });
+    if (rc) return rc;
     std::vector<unsigned long long> hres(3 * (size_t)nb);
     unsigned hflags = 0;
     if (e == cudaSuccess)

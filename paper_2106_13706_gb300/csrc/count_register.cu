@@ -461,7 +461,7 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   const size_t smem = reg_smem(ds, NW);
   const unsigned ctas = (unsigned)(blocks * C);
   // stage timing: the count stage starts here (the preparation above counts as encoding)
-  if (ctx->stage_timing) cudaEventRecord(ctx->ev[1], st);
+  ddks_stage_mark(ctx, 1, st);
   int occ = plan.reg_occ == 2 || plan.reg_occ == 3 ? plan.reg_occ : 4;
   while (occ > 2 && (size_t)occ * (smem + 1024) > 227u * 1024u) --occ;  // shared memory bound
   auto go = [&](auto kern) -> cudaError_t {

@@ -34,6 +34,16 @@ struct ddks_plan {
 
 struct ServeState;  // serve.cu
 
+// A captured CUDA graph for one repeated call (graph.cu).
+struct GraphEntry {
+  uint64_t key = 0;            // hash of the call's shapes, plan and device addresses
+  uint64_t gen = 0;            // ctx->buf_gen when captured
+  cudaGraphExec_t exec = nullptr;
+  uint64_t kernels = 0;        // kernels one replay launches
+  uint64_t last_use = 0;
+  bool primed = false;         // a direct run of this key has succeeded
+};
+
 struct ddks_ctx {
   ddks_config cfg{};
   int device = 0;
@@ -59,6 +69,11 @@ struct ddks_ctx {
   std::mutex tune_mu;
   // serving
   ServeState* serve = nullptr;  // owned; freed by ddks_serve_shutdown
+  // graph replay (graph.cu); buf_gen counts scratch reallocations
+  uint64_t buf_gen = 0;
+  cudaStream_t cap_st = nullptr;
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_tick = 0, graph_captures = 0, graph_replays = 0;
 
   std::vector<DevBuf*> all_bufs() {
     return {&inP, &inT, &keys, &tk1, &tk2, &ti1, &ti2, &rank, &sidx0, &best, &bestj, &out3,
@@ -74,6 +89,7 @@ int ddks_stage_inputs(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, i
                       int32_t d, int32_t dtype, cudaStream_t st, const void** dP, const void** dT);
 int ddks_encode_problem(ddks_ctx* ctx, const void* dP, int64_t NP, const void* dT, int64_t NT,
                         int32_t d, int32_t dtype, cudaStream_t st, bool want_sorted0);
+void ddks_stage_mark(ddks_ctx* ctx, int i, cudaStream_t st);
 int ddks_count_origins(ddks_ctx* ctx, int64_t NP, int64_t NT, int32_t d, int64_t ob, int64_t oe,
                        uint64_t* best, int32_t* bestj, cudaStream_t st);
 int ddks_count_origins_plan(ddks_ctx* ctx, const ddks_plan& plan, int64_t NP, int64_t NT, int32_t d,
@@ -88,6 +104,49 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
                                  int64_t NT, int d, int64_t ob, int64_t oe, uint64_t* best,
                                  int32_t* bestj, cudaStream_t st, const ddks_plan& plan);
 bool ddks_register_supported(int d, int64_t NP, int64_t NT);
+
+// graph.cu: a hash of everything a captured graph depends on
+struct GraphKey {
+  uint64_t h = 1469598103934665603ull;  // FNV-1a
+  GraphKey& add(uint64_t v) {
+    for (int i = 0; i < 8; ++i) { h ^= (v >> (8 * i)) & 0xFF; h *= 1099511628211ull; }
+    return *this;
+  }
+  GraphKey& add_ptr(const void* p) { return add((uint64_t)(uintptr_t)p); }
+  GraphKey& add_bytes(const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+    return *this;
+  }
+};
+// mode 0: run body directly on st; 1: body is being captured on *run_st;
+// 2: a captured graph was launched on st
+int ddks_graph_begin(ddks_ctx* ctx, uint64_t key, cudaStream_t st, cudaStream_t* run_st, int* mode);
+int ddks_graph_end(ddks_ctx* ctx, uint64_t key, cudaStream_t st, int mode, int body_rc, uint64_t l0,
+                   uint64_t g0);
+void ddks_graph_mark(ddks_ctx* ctx, uint64_t key);
+void ddks_graph_clear(ddks_ctx* ctx);
+
+// Run body(stream) directly, or through the graph captured for `key` (the
+// graph replay note in ddks.h).  body enqueues work only: no synchronisation,
+// no host reads of device results.
+template <typename F>
+int ddks_graph_run(ddks_ctx* ctx, uint64_t key, cudaStream_t st, F&& body) {
+  cudaStream_t run_st = st;
+  int mode = 0;
+  int rc = ddks_graph_begin(ctx, key, st, &run_st, &mode);
+  if (rc) return rc;
+  if (mode == 2) return 0;  // replayed
+  const uint64_t l0 = ctx->launches, g0 = ctx->buf_gen;
+  const int brc = body(run_st);
+  if (mode == 0) {  // direct
+    if (brc == 0) ddks_graph_mark(ctx, key);
+    return brc;
+  }
+  rc = ddks_graph_end(ctx, key, st, mode, brc, l0, g0);
+  if (rc == 1) return body(st);  // capture dropped: run directly
+  return rc;
+}
 
 // serve.cu
 void ddks_serve_shutdown(ddks_ctx* ctx);

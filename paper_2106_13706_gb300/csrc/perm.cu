@@ -45,9 +45,10 @@ DDKS_DEV void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
 // the NP-th smallest key K* and how many keys equal to K* belong to P, and
 // the points with key < K*, plus the lowest-index ones with key == K*, get
 // bit b.  Same labels as sorting the (key, index) pairs.
-__global__ void k_perm_labels_warp(int64_t N, int64_t NP, int B, uint64_t seed, int G,
-                                   int warps_per_cta, uint32_t* __restrict__ labels) {
+__global__ void k_perm_labels_warp(int64_t N, int64_t NP, int B, const unsigned long long* __restrict__ seedp,
+                                   int G, int warps_per_cta, uint32_t* __restrict__ labels) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  const uint64_t seed = *seedp;  // from device memory, so a captured graph serves every seed
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp >= warps_per_cta) return;
   const int n = (int)N;
@@ -435,85 +436,99 @@ int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* 
   if ((rc = ddks_stage_inputs(ctx, P, NP, T, NT, d, dtype, st, &dP, &dT))) return observed->status = rc;
   ddks_plan plan;
   if ((rc = ddks_select_path(ctx, NP, NT, d, &plan))) return observed->status = rc;
-  if ((rc = ddks_encode_problem(ctx, dP, NP, dT, NT, d, dtype, st, plan.path == DDKS_PATH_REGISTER)))
-    return observed->status = rc;
-  // observed statistic
-  if ((rc = ctx->best.reserve(ctx, 8 * (size_t)N))) return observed->status = rc;
-  if ((rc = ctx->bestj.reserve(ctx, 4 * (size_t)N))) return observed->status = rc;
   if ((rc = ctx->out3.reserve(ctx, 64 + ddks_reduce_scratch_bytes()))) return observed->status = rc;
-  if ((rc = ddks_count_origins(ctx, NP, NT, d, 0, N, (uint64_t*)ctx->best.ptr, (int32_t*)ctx->bestj.ptr, st)))
-    return observed->status = rc;
-  e = ddks_launch_reduce((const uint64_t*)ctx->best.ptr, (const int32_t*)ctx->bestj.ptr, N, 0,
-                         (unsigned long long*)ctx->out3.ptr, (char*)ctx->out3.ptr + 64, st);
-  ctx->launches += 2;
-  if (e != cudaSuccess) return observed->status = ctx_cuda_fail(ctx, e, "reduce");
   unsigned long long* out3 = (unsigned long long*)ctx->out3.ptr;
+  // out3: [0..2] observed result, [4] #{b : num_b >= num_obs}, [6] seed
+  ctx->h_out[16] = seed;
+  e = cudaMemcpyAsync(out3 + 6, ctx->h_out + 16, 8, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return observed->status = ctx_cuda_fail(ctx, e, "seed upload");
   const int G = (B + 31) / 32;
   const int Bc = B > 0 ? B : 1;
-  if ((rc = ctx->perm_labels.reserve(ctx, 4 * (size_t)N * (G > 0 ? G : 1)))) return observed->status = rc;
-  if ((rc = ctx->perm_best.reserve(ctx, 8 * (size_t)Bc))) return observed->status = rc;
-  unsigned long long* pbest = (unsigned long long*)ctx->perm_best.ptr;
-  e = cudaMemsetAsync(out3 + 4, 0, 8, st);  // p-value count
-  if (e == cudaSuccess && B > 0) {
-    e = cudaMemsetAsync(ctx->perm_labels.ptr, 0, 4 * (size_t)N * G, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(pbest, 0, 8 * (size_t)B, st);
-    if (e == cudaSuccess) {
-      int wpc = (int)((200 * 1024) / ((size_t)N * 8 + 1024));
-      if (wpc > 8) wpc = 8;
-      if (wpc < 1) wpc = 1;
-      const size_t smem = (size_t)wpc * ((size_t)N * 8 + 1024);
-      e = cudaFuncSetAttribute(k_perm_labels_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) {
-        int grid = (B + wpc - 1) / wpc;
-        if (grid > ctx->num_sms * 4) grid = ctx->num_sms * 4;
-        k_perm_labels_warp<<<grid, wpc * 32, smem, st>>>(N, NP, B, seed, G, wpc,
-                                                         (uint32_t*)ctx->perm_labels.ptr);
-        e = cudaGetLastError();
+  GraphKey key;
+  key.add(2).add((uint64_t)NP).add((uint64_t)NT).add((uint64_t)d).add((uint64_t)dtype).add((uint64_t)B);
+  key.add((uint64_t)plan.path).add((uint64_t)plan.threads).add((uint64_t)plan.warps);
+  key.add((uint64_t)plan.reg_occ).add_ptr(dP).add_ptr(dT).add((uint64_t)ctx->stage_timing);
+  rc = ddks_graph_run(ctx, key.h, st, [&](cudaStream_t s) -> int {
+    int r;
+    if ((r = ddks_encode_problem(ctx, dP, NP, dT, NT, d, dtype, s, plan.path == DDKS_PATH_REGISTER))) return r;
+    // observed statistic
+    if ((r = ctx->best.reserve(ctx, 8 * (size_t)N))) return r;
+    if ((r = ctx->bestj.reserve(ctx, 4 * (size_t)N))) return r;
+    if ((r = ddks_count_origins_plan(ctx, plan, NP, NT, d, 0, N, (uint64_t*)ctx->best.ptr,
+                                     (int32_t*)ctx->bestj.ptr, s)))
+      return r;
+    cudaError_t ee = ddks_launch_reduce((const uint64_t*)ctx->best.ptr, (const int32_t*)ctx->bestj.ptr, N, 0,
+                                        out3, (char*)ctx->out3.ptr + 64, s);
+    ctx->launches += 2;
+    if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "reduce");
+    if ((r = ctx->perm_labels.reserve(ctx, 4 * (size_t)N * (G > 0 ? G : 1)))) return r;
+    if ((r = ctx->perm_best.reserve(ctx, 8 * (size_t)Bc))) return r;
+    unsigned long long* pbest = (unsigned long long*)ctx->perm_best.ptr;
+    ee = cudaMemsetAsync(out3 + 4, 0, 8, s);  // p-value count
+    if (ee == cudaSuccess && B > 0) {
+      ee = cudaMemsetAsync(ctx->perm_labels.ptr, 0, 4 * (size_t)N * G, s);
+      if (ee == cudaSuccess) ee = cudaMemsetAsync(pbest, 0, 8 * (size_t)B, s);
+      if (ee == cudaSuccess) {
+        int wpc = (int)((200 * 1024) / ((size_t)N * 8 + 1024));
+        if (wpc > 8) wpc = 8;
+        if (wpc < 1) wpc = 1;
+        const size_t smem = (size_t)wpc * ((size_t)N * 8 + 1024);
+        ee = cudaFuncSetAttribute(k_perm_labels_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (ee == cudaSuccess) {
+          int grid = (B + wpc - 1) / wpc;
+          if (grid > ctx->num_sms * 4) grid = ctx->num_sms * 4;
+          k_perm_labels_warp<<<grid, wpc * 32, smem, s>>>(N, NP, B, out3 + 6, G, wpc,
+                                                          (uint32_t*)ctx->perm_labels.ptr);
+          ee = cudaGetLastError();
+          ctx->launches += 1;
+        }
+      }
+      if (ee == cudaSuccess) {
+        const uint32_t* rank = (const uint32_t*)ctx->rank.ptr;
+        const uint32_t* lab = (const uint32_t*)ctx->perm_labels.ptr;
+        const int n16 = (int)((N + 15) & ~15);
+        const size_t smem = (size_t)N * kPassWords * 4 + (size_t)kBitsWarps * n16 * 3 +
+                            (size_t)kBitsWarps * 3 * (1 << d) * 4 + 16;
+        if (N <= kBitsMaxN && d <= 5 && smem <= 227u * 1024u) {
+          auto go = [&](auto kern) -> cudaError_t {
+            cudaError_t q = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (q != cudaSuccess) return q;
+            int grid = ctx->num_sms;
+            if (grid > N) grid = (int)N;
+            kern<<<grid, kBitsWarps * 32, smem, s>>>(rank, N, NP, B, G, lab, pbest);
+            return cudaGetLastError();
+          };
+          switch (d) {
+            case 1: ee = go(k_perm_bits<1>); break;
+            case 2: ee = go(k_perm_bits<2>); break;
+            case 3: ee = go(k_perm_bits<3>); break;
+            case 4: ee = go(k_perm_bits<4>); break;
+            default: ee = go(k_perm_bits<5>); break;
+          }
+        } else switch (d) {
+          case 1: ee = launch_count<1>(rank, N, NP, B, G, lab, pbest, s, ctx->num_sms); break;
+          case 2: ee = launch_count<2>(rank, N, NP, B, G, lab, pbest, s, ctx->num_sms); break;
+          case 3: ee = launch_count<3>(rank, N, NP, B, G, lab, pbest, s, ctx->num_sms); break;
+          case 4: ee = launch_count<4>(rank, N, NP, B, G, lab, pbest, s, ctx->num_sms); break;
+          case 5: ee = launch_count<5>(rank, N, NP, B, G, lab, pbest, s, ctx->num_sms); break;
+          case 6: ee = launch_count<6>(rank, N, NP, B, G, lab, pbest, s, ctx->num_sms); break;
+          case 7: ee = launch_count<7>(rank, N, NP, B, G, lab, pbest, s, ctx->num_sms); break;
+          default: ee = launch_count<8>(rank, N, NP, B, G, lab, pbest, s, ctx->num_sms); break;
+        }
+        ctx->launches += 1;
+      }
+      if (ee == cudaSuccess) {
+        k_perm_pvalue<<<(B + 255) / 256 < 64 ? (B + 255) / 256 : 64, 256, 0, s>>>(pbest, B, out3, out3 + 4);
+        ee = cudaGetLastError();
         ctx->launches += 1;
       }
     }
-    if (e == cudaSuccess) {
-      const uint32_t* rank = (const uint32_t*)ctx->rank.ptr;
-      const uint32_t* lab = (const uint32_t*)ctx->perm_labels.ptr;
-      const int n16 = (int)((N + 15) & ~15);
-      const size_t smem = (size_t)N * kPassWords * 4 + (size_t)kBitsWarps * n16 * 3 +
-                          (size_t)kBitsWarps * 3 * (1 << d) * 4 + 16;
-      if (N <= kBitsMaxN && d <= 5 && smem <= 227u * 1024u) {
-        auto go = [&](auto kern) -> cudaError_t {
-          cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-          if (r != cudaSuccess) return r;
-          int grid = ctx->num_sms;
-          if (grid > N) grid = (int)N;
-          kern<<<grid, kBitsWarps * 32, smem, st>>>(rank, N, NP, B, G, lab, pbest);
-          return cudaGetLastError();
-        };
-        switch (d) {
-          case 1: e = go(k_perm_bits<1>); break;
-          case 2: e = go(k_perm_bits<2>); break;
-          case 3: e = go(k_perm_bits<3>); break;
-          case 4: e = go(k_perm_bits<4>); break;
-          default: e = go(k_perm_bits<5>); break;
-        }
-      } else switch (d) {
-        case 1: e = launch_count<1>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
-        case 2: e = launch_count<2>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
-        case 3: e = launch_count<3>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
-        case 4: e = launch_count<4>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
-        case 5: e = launch_count<5>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
-        case 6: e = launch_count<6>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
-        case 7: e = launch_count<7>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
-        default: e = launch_count<8>(rank, N, NP, B, G, lab, pbest, st, ctx->num_sms); break;
-      }
-      ctx->launches += 1;
-    }
-    if (e == cudaSuccess) {
-      k_perm_pvalue<<<(B + 255) / 256 < 64 ? (B + 255) / 256 : 64, 256, 0, st>>>(pbest, B, out3, out3 + 4);
-      e = cudaGetLastError();
-      ctx->launches += 1;
-    }
-  }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ctx->h_out, out3, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "permutation test");
+    return DDKS_OK;
+  });
+  if (rc) return observed->status = rc;
+  unsigned long long* pbest = (unsigned long long*)ctx->perm_best.ptr;
+  e = cudaMemcpyAsync(ctx->h_out, out3, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->h_out + 8, ctx->flags.ptr, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && perm_num_max && B > 0)
@@ -521,6 +536,7 @@ int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* 
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return observed->status = ctx_cuda_fail(ctx, e, "permutation test");
   if ((unsigned)(ctx->h_out[8] & 0xFFFFFFFFull) & ddks::kFlagNaN) return observed->status = DDKS_ENAN;
+  if ((unsigned)(ctx->h_out[8] & 0xFFFFFFFFull) & ddks::kFlagTimeout) return observed->status = DDKS_ETIMEOUT;
   observed->num_max = ctx->h_out[0];
   observed->denom = (uint64_t)NP * (uint64_t)NT;
   observed->D = (double)observed->num_max / (double)observed->denom;

@@ -145,6 +145,7 @@ static int serve_start(ddks_ctx* ctx) {
   if (!S) return DDKS_ENOMEM;
   ddks_config cfg = ctx->cfg;
   cfg.device = ctx->device;
+  cfg.graphs = 0;  // device batches rarely repeat a membership: capture would not pay
   for (int w = 0; w < kWorkers; ++w) {
     ddks_ctx* c = nullptr;
     int rc = ddks_ctx_create(&cfg, &c);

@@ -226,6 +226,23 @@ def test_register_path_rerank_tiles(torch, d):
             _same(got, ref)
 
 
+@pytest.mark.parametrize("d,n_p,n_t", [(4, 40000, 25000), (3, 60000, 41000)])
+def test_register_path_large_n_tables(torch, d, n_p, n_t):
+    # above ~60k (d=4) / ~91k (d=3) points the pack kernel re-ranks through
+    # bitmap + prefix tables instead of byte tables; sampled origins, ties
+    rng = np.random.default_rng(70 + d)
+    P = rng.integers(0, 3000, size=(n_p, d)).astype(np.float32)
+    T = (rng.integers(0, 3000, size=(n_t, d)) + (rng.random((n_t, d)) < 0.3)).astype(np.float32)
+    N = n_p + n_t
+    ranges = [(0, 150), (n_p - 70, n_p + 90), (N - 130, N)]
+    with _ctx(pkg.PATH_REGISTER) as c:
+        for a, b in ranges:
+            got = c.distance_range(_dev(torch, P), _dev(torch, T), a, b, per_origin=True)
+            ref = orc.ddks(P, T, origins=(a, b), per_origin=True)
+            assert np.array_equal(got["per_origin"], ref["per_origin"])
+            _same(got, ref)
+
+
 @pytest.mark.parametrize("d", [2, 4, 6])
 def test_autotune_picks_an_agreeing_path(torch, d):
     P, T = wl.random_pair(60 + d, 3000, 2500, d, kind="normal")
