@@ -226,10 +226,10 @@ def test_register_path_rerank_tiles(torch, d):
             _same(got, ref)
 
 
-@pytest.mark.parametrize("d,n_p,n_t", [(4, 40000, 25000), (3, 60000, 41000)])
-def test_register_path_large_n_tables(torch, d, n_p, n_t):
-    # above ~60k (d=4) / ~91k (d=3) points the pack kernel re-ranks through
-    # bitmap + prefix tables instead of byte tables; sampled origins, ties
+@pytest.mark.parametrize("d,n_p,n_t", [(4, 40000, 25000), (3, 60000, 41000), (2, 100000, 50000)])
+def test_register_path_large_n(torch, d, n_p, n_t):
+    # large re-rank tables; at 150k points the list chunks of a work unit hit
+    # their 16-bit cap; sampled origins, ties in every dimension
     rng = np.random.default_rng(70 + d)
     P = rng.integers(0, 3000, size=(n_p, d)).astype(np.float32)
     T = (rng.integers(0, 3000, size=(n_t, d)) + (rng.random((n_t, d)) < 0.3)).astype(np.float32)
