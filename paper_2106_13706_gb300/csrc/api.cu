@@ -273,8 +273,14 @@ int ddks_count_origins_plan(ddks_ctx* ctx, const ddks_plan& plan, int64_t NP, in
       ctx->launches += 1;
       break;
     case DDKS_PATH_WARP:
-      e = ddks_launch_warp(rank, N, NP, NT, d, ob, oe, best, bestj, st, plan.warps);
-      ctx->launches += 1;
+      if (ddks_warp16_supported(d, NP, NT)) {
+        int n = 0;
+        e = ddks_launch_warp16(ctx, rank, N, NP, NT, d, ob, oe, best, bestj, st, &n);
+        ctx->launches += n;
+      } else {
+        e = ddks_launch_warp(rank, N, NP, NT, d, ob, oe, best, bestj, st, plan.warps);
+        ctx->launches += 1;
+      }
       break;
     case DDKS_PATH_SORT:
       e = ddks_launch_sort(rank, N, NP, NT, d, ob, oe, best, bestj, st);

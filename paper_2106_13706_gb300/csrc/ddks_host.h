@@ -53,6 +53,7 @@ struct ddks_ctx {
   // scratch of the synchronous entry points
   DevBuf inP, inT, keys, tk1, tk2, ti1, ti2, rank, sidx0, best, bestj, out3, flags;
   DevBuf reg_words, reg_meta;                   // register path
+  DevBuf warp_words;                            // warp path: packed rank pairs
   DevBuf perm_keys, perm_labels, perm_best, perm_codes;  // permutation test
   DevBuf sig_cells, sig_logp;                   // significance
   DevBuf batch_desc, batch_work;                // batched launch
@@ -77,7 +78,7 @@ struct ddks_ctx {
 
   std::vector<DevBuf*> all_bufs() {
     return {&inP, &inT, &keys, &tk1, &tk2, &ti1, &ti2, &rank, &sidx0, &best, &bestj, &out3,
-            &flags, &reg_words, &reg_meta, &perm_keys, &perm_labels, &perm_best, &perm_codes,
+            &flags, &reg_words, &reg_meta, &warp_words, &perm_keys, &perm_labels, &perm_best, &perm_codes,
             &sig_cells, &sig_logp, &batch_desc, &batch_work};
   }
 };
@@ -147,6 +148,12 @@ int ddks_graph_run(ddks_ctx* ctx, uint64_t key, cudaStream_t st, F&& body) {
   if (rc == 1) return body(st);  // capture dropped: run directly
   return rc;
 }
+
+// count_warp.cu
+bool ddks_warp16_supported(int d, int64_t NP, int64_t NT);
+cudaError_t ddks_launch_warp16(ddks_ctx* ctx, const uint32_t* rank, int64_t N, int64_t NP, int64_t NT,
+                               int d, int64_t o_begin, int64_t o_end, uint64_t* best, int32_t* bestj,
+                               cudaStream_t st, int* launches);
 
 // serve.cu
 void ddks_serve_shutdown(ddks_ctx* ctx);
