@@ -23,6 +23,8 @@
 namespace {
 
 constexpr int kMaxPermN = 16384;
+constexpr int kLabWarps = 8;     // relabellings per CTA (one per warp)
+constexpr int kLabCand = 256;    // largest bucket ranked by brute force
 constexpr int kCountThreads = 256;
 constexpr int kPtsTile = 64;
 
@@ -45,33 +47,40 @@ DDKS_DEV void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
 // the NP-th smallest key K* and how many keys equal to K* belong to P, and
 // the points with key < K*, plus the lowest-index ones with key == K*, get
 // bit b.  Same labels as sorting the (key, index) pairs.
-__global__ void k_perm_labels_warp(int64_t N, int64_t NP, int B, const unsigned long long* __restrict__ seedp,
-                                   int G, int warps_per_cta, uint32_t* __restrict__ labels) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+// K3, one warp per relabelling, without storing the keys: the warp regenerates
+// the relabelling's N Philox keys in each pass.  Most-significant-digit radix
+// selection (8-bit digits, histograms in warp-private shared memory) narrows
+// the NP-th smallest key to one bucket of at most kLabCand keys (usually one
+// histogram pass); the bucket's (key, index) pairs are collected and ranked
+// by brute force, which gives the threshold pair (K*, i*); a last pass sets
+// bit b for every point with (key, i) <= (K*, i*) -- exactly the NP smallest
+// (key, index) pairs, as sorting them would.
+__global__ void __launch_bounds__(kLabWarps * 32)
+k_perm_labels_warp(int64_t N, int64_t NP, int B, const unsigned long long* __restrict__ seedp, int G,
+                   uint32_t* __restrict__ labels, unsigned* __restrict__ flags) {
+  __shared__ uint32_t hist_all[kLabWarps][256];
+  __shared__ unsigned long long ck_all[kLabWarps][kLabCand];
+  __shared__ uint32_t ci_all[kLabWarps][kLabCand];
   const uint64_t seed = *seedp;  // from device memory, so a captured graph serves every seed
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp >= warps_per_cta) return;
+  uint32_t* hist = hist_all[warp];
+  unsigned long long* ck = ck_all[warp];
+  uint32_t* ci = ci_all[warp];
   const int n = (int)N;
-  uint64_t* key = reinterpret_cast<uint64_t*>(smraw) + (size_t)warp * n;
-  uint32_t* hist = reinterpret_cast<uint32_t*>(reinterpret_cast<uint64_t*>(smraw) + (size_t)warps_per_cta * n) +
-                   warp * 256;
-  for (int b = blockIdx.x * warps_per_cta + warp; b < B; b += gridDim.x * warps_per_cta) {
-    for (int c = lane; 4 * c < n; c += 32) {
-      uint64_t ctr[4] = {(uint64_t)c, (uint64_t)b, 0ull, 0ull};
-      philox4x64_10(ctr, seed, 0ull);
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (4 * c + q < n) key[4 * c + q] = ctr[q];
-    }
-    __syncwarp();
+  const int nc = (n + 3) / 4;  // Philox calls per relabelling
+  for (int b = blockIdx.x * kLabWarps + warp; b < B; b += gridDim.x * kLabWarps) {
     uint64_t prefix = 0, pmask = 0;
     uint32_t target = (uint32_t)(NP - 1);  // 0-based rank of the last P point
-    for (int dg = 7; dg >= 0; --dg) {
+    uint32_t bucket = (uint32_t)n;
+    for (int dg = 7; dg >= 0 && bucket > (uint32_t)kLabCand; --dg) {
       for (int v = lane; v < 256; v += 32) hist[v] = 0;
       __syncwarp();
-      for (int i = lane; i < n; i += 32) {
-        const uint64_t k = key[i];
-        if ((k & pmask) == prefix) atomicAdd(&hist[(k >> (8 * dg)) & 255u], 1u);
+      for (int c = lane; c < nc; c += 32) {
+        uint64_t ctr[4] = {(uint64_t)c, (uint64_t)b, 0ull, 0ull};
+        philox4x64_10(ctr, seed, 0ull);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (4 * c + q < n && (ctr[q] & pmask) == prefix) atomicAdd(&hist[(ctr[q] >> (8 * dg)) & 255u], 1u);
       }
       __syncwarp();
       // lane l owns digits 8l..8l+7: find the digit holding rank `target`
@@ -86,7 +95,7 @@ __global__ void k_perm_labels_warp(int64_t N, int64_t NP, int B, const unsigned 
       const uint32_t excl = incl - loc;
       const bool mine = target >= excl && target < incl;
       const unsigned owner = __ffs(__ballot_sync(0xffffffffu, mine)) - 1;
-      uint32_t digit = 0, below = 0;
+      uint32_t digit = 0, below = 0, size = 0;
       if (mine) {
         uint32_t run = excl;
         bool found = false;
@@ -95,6 +104,7 @@ __global__ void k_perm_labels_warp(int64_t N, int64_t NP, int B, const unsigned 
           if (!found && target < run + h[q]) {
             digit = 8 * lane + q;
             below = run;
+            size = h[q];
             found = true;
           }
           run += h[q];
@@ -102,22 +112,59 @@ __global__ void k_perm_labels_warp(int64_t N, int64_t NP, int B, const unsigned 
       }
       digit = __shfl_sync(0xffffffffu, digit, owner);
       below = __shfl_sync(0xffffffffu, below, owner);
+      bucket = __shfl_sync(0xffffffffu, size, owner);
       target -= below;
       prefix |= (uint64_t)digit << (8 * dg);
       pmask |= (uint64_t)255 << (8 * dg);
       __syncwarp();
     }
-    // keys < prefix go to P; of the keys == prefix, the (target + 1) lowest indices
-    uint32_t taken = 0;
-    for (int base = 0; base < n; base += 32) {
-      const int i = base + lane;
-      const uint64_t k = i < n ? key[i] : ~0ull;
-      const bool eq = i < n && k == prefix;
-      const unsigned m = __ballot_sync(0xffffffffu, eq);
-      const uint32_t before = taken + __popc(m & ((1u << lane) - 1u));
-      const bool inP = i < n && (k < prefix || (eq && before <= target));
-      if (inP) atomicOr(&labels[(int64_t)i * G + (b >> 5)], 1u << (b & 31));
-      taken += __popc(m);
+    // collect the bucket (keys matching the prefix), then rank it by brute force
+    uint32_t cnt = 0;
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+      const int c = c0 + lane;
+      uint64_t ctr[4] = {(uint64_t)c, (uint64_t)b, 0ull, 0ull};
+      if (c < nc) philox4x64_10(ctr, seed, 0ull);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool in = c < nc && 4 * c + q < n && (ctr[q] & pmask) == prefix;
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (in) {
+          const uint32_t pos = cnt + __popc(m & ((1u << lane) - 1u));
+          if (pos < (uint32_t)kLabCand) { ck[pos] = ctr[q]; ci[pos] = (uint32_t)(4 * c + q); }
+        }
+        cnt += __popc(m);
+      }
+    }
+    __syncwarp();
+    const int nb = (int)(cnt < (uint32_t)kLabCand ? cnt : (uint32_t)kLabCand);
+    if (cnt > (uint32_t)kLabCand && lane == 0) atomicOr(flags, ddks::kFlagBounds);  // > 256 equal keys
+    unsigned long long tk = 0;
+    uint32_t ti = 0;
+    bool found = false;
+    for (int j = lane; j < nb; j += 32) {
+      const unsigned long long kj = ck[j];
+      const uint32_t ij = ci[j];
+      uint32_t r = 0;
+      for (int t = 0; t < nb; ++t) {
+        const unsigned long long kt = ck[t];
+        r += (kt < kj || (kt == kj && ci[t] < ij)) ? 1u : 0u;
+      }
+      if (r == target) { tk = kj; ti = ij; found = true; }
+    }
+    const unsigned own = __ballot_sync(0xffffffffu, found);
+    const int src = own ? __ffs(own) - 1 : 0;
+    tk = __shfl_sync(0xffffffffu, tk, src);
+    ti = __shfl_sync(0xffffffffu, ti, src);
+    // the NP smallest (key, index) pairs: (key, i) <= (tk, ti)
+    for (int c = lane; c < nc; c += 32) {
+      uint64_t ctr[4] = {(uint64_t)c, (uint64_t)b, 0ull, 0ull};
+      philox4x64_10(ctr, seed, 0ull);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = 4 * c + q;
+        if (i < n && (ctr[q] < tk || (ctr[q] == tk && (uint32_t)i <= ti)))
+          atomicOr(&labels[(int64_t)i * G + (b >> 5)], 1u << (b & 31));
+      }
     }
     __syncwarp();
   }
@@ -197,20 +244,21 @@ k_perm_count(const uint32_t* __restrict__ rank, int64_t N, int64_t NP, int B, in
 
 // ---------------------------------------------------------------- bit-sliced K4
 //
-// For N <= 4000 or so (the staged labels and per-warp buckets must fit shared
-// memory) and d <= 5 the relabellings are counted 32 at a time in bit
-// slices.  A pass takes 256 relabellings (8 label words per point, staged in
-// shared memory).  A warp takes an origin, buckets the N points by orthant
-// code (warp-private counting sort: the point order of every bin), and walks
-// the bins: lane (gg, sub) adds the label words of word gg for a quarter of the
-// bin's points into a bit-sliced counter (Harley-Seal carry-save adders over
-// 16 words at a time, higher planes by ripple), so one 32-bit operation counts
+// For N <= 4096 and d <= 5 the relabellings are counted 32 at a time in bit
+// slices.  First every origin's points are bucketed by orthant code (one
+// counting sort per origin, kept in global memory for all passes).  A pass
+// takes 256 relabellings: each CTA stages their label words (8 per point) in
+// shared memory, and a warp takes an origin and walks its buckets: lane
+// (gg, sub) adds the label words of word gg for a quarter of the bucket's
+// points into a bit-sliced counter (Harley-Seal carry-save adders over 16
+// words at a time, higher planes by ripple), so one 32-bit operation counts
 // 32 relabellings.  The four quarters are summed with shuffles, each lane
 // extracts the counts of 8 relabellings, and keeps their running maximum of
-// |cP*N - n*NP| (n = bin size).  The pass ends with one atomicMax per
-// relabelling.
+// |cP*N - n*NP| (n = bucket size).  The pass ends with a shared then a global
+// atomicMax per relabelling.
 constexpr int kBitsMaxN = 4096;
-constexpr int kBitsWarps = 8;
+constexpr int kSortWarps = 8;
+constexpr int kBits2Threads = 1024;
 constexpr int kPassWords = 8;                 // label words per point per pass
 constexpr int kPassPerms = 32 * kPassWords;   // 256 relabellings per pass
 constexpr int kHiPlanes = 8;                  // planes of weight 16..2048 (counts < 4096)
@@ -265,122 +313,136 @@ DDKS_DEV void add_partner(Slices& z, int off) {
   for (int k = 0; k < kHiPlanes; ++k) z.hi[k] = out[4 + k];
 }
 
+// Bucket sort of every origin's points by orthant code, done once for all
+// passes: sidx[o][.] lists the pooled points in code order, boff[o][c] is
+// where code c starts (boff[o][NB] = N).  One warp per origin; the codes go
+// through warp-private shared memory.
 template <int D>
-__global__ void __launch_bounds__(kBitsWarps * 32, 1)
-k_perm_bits(const uint32_t* __restrict__ rank, int64_t N, int64_t NP, int B, int G,
-            const uint32_t* __restrict__ labels, unsigned long long* __restrict__ perm_best) {
+__global__ void __launch_bounds__(kSortWarps * 32)
+k_perm_sort(const uint32_t* __restrict__ rank, int N, uint16_t* __restrict__ sidx,
+            uint16_t* __restrict__ boff) {
+  extern __shared__ __align__(16) unsigned char smb[];
+  constexpr int NB = 1 << D;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* cur = reinterpret_cast<uint32_t*>(smb) + warp * NB;               // [warps][NB]
+  uint8_t* wc = smb + kSortWarps * NB * 4 + (size_t)warp * ((N + 15) & ~15);  // [warps][N]
+  for (int o = blockIdx.x * kSortWarps + warp; o < N; o += gridDim.x * kSortWarps) {
+    uint32_t orank[D];
+#pragma unroll
+    for (int m = 0; m < D; ++m) orank[m] = rank[(int64_t)m * N + o];
+    if (lane < NB) cur[lane] = 0;
+    __syncwarp();
+    for (int i = lane; i < N; i += 32) {
+      uint32_t c = 0;
+#pragma unroll
+      for (int m = 0; m < D; ++m) c |= (uint32_t)(rank[(int64_t)m * N + i] >= orank[m]) << m;
+      wc[i] = (uint8_t)c;
+      atomicAdd(&cur[c], 1u);
+    }
+    __syncwarp();
+    {
+      const uint32_t v = lane < NB ? cur[lane] : 0u;
+      uint32_t incl = v;
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
+      }
+      if (lane < NB) {
+        cur[lane] = incl - v;
+        boff[(size_t)o * (NB + 1) + lane] = (uint16_t)(incl - v);
+      }
+      if (lane == 0) boff[(size_t)o * (NB + 1) + NB] = (uint16_t)N;
+    }
+    __syncwarp();
+    uint16_t* out = sidx + (size_t)o * N;
+    for (int i = lane; i < N; i += 32) out[atomicAdd(&cur[wc[i]], 1u)] = (uint16_t)i;
+    __syncwarp();
+  }
+}
+
+// One pass of 256 relabellings: the CTA stages their label words (8 per
+// point), each warp takes origins and walks their code buckets.
+template <int D>
+__global__ void __launch_bounds__(kBits2Threads, 1)
+k_perm_bits(const uint16_t* __restrict__ sidx, const uint16_t* __restrict__ boff, int N, int NP, int B,
+            int G, int pass, const uint32_t* __restrict__ labels, unsigned long long* __restrict__ perm_best) {
   extern __shared__ __align__(16) uint32_t sm[];
   constexpr int NB = 1 << D;
-  const int n = (int)N;
-  uint32_t* lab = sm;                                            // [N][8]
-  uint8_t* codes = reinterpret_cast<uint8_t*>(lab + n * kPassWords);  // [warps][N]
-  uint16_t* idx = reinterpret_cast<uint16_t*>(codes + kBitsWarps * ((n + 15) & ~15));  // [warps][N]
-  uint32_t* bins = reinterpret_cast<uint32_t*>(idx + kBitsWarps * ((n + 15) & ~15));   // [warps][3][NB]
+  uint32_t* lab = sm;                                         // [N][8]
+  uint32_t* cmax = lab + (size_t)N * kPassWords;              // [256] per-CTA maxima
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int W = blockDim.x >> 5;
   const int gg = lane & 7, sub = lane >> 3;
-  uint8_t* wc = codes + warp * ((n + 15) & ~15);
-  uint16_t* wi = idx + warp * ((n + 15) & ~15);
-  uint32_t* wcnt = bins + warp * 3 * NB;   // counts, offsets, cursors
-  const int64_t per = (N + gridDim.x - 1) / gridDim.x;
-  const int64_t k0 = blockIdx.x * per;
-  const int64_t k1 = k0 + per < N ? k0 + per : N;
-  const int npass = (B + kPassPerms - 1) / kPassPerms;
-  for (int pass = 0; pass < npass; ++pass) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < n * kPassWords; e += blockDim.x) {
-      const int p = e / kPassWords, w = e - p * kPassWords;
-      const int grp = pass * kPassWords + w;
-      lab[e] = grp < G ? labels[(int64_t)p * G + grp] : 0u;
-    }
-    __syncthreads();
-    uint32_t mx[8];
+  for (int e = threadIdx.x; e < N * kPassWords; e += blockDim.x) {
+    const int p = e / kPassWords, w = e - p * kPassWords;
+    const int grp = pass * kPassWords + w;
+    lab[e] = grp < G ? labels[(int64_t)p * G + grp] : 0u;
+  }
+  for (int t = threadIdx.x; t < kPassPerms; t += blockDim.x) cmax[t] = 0;
+  __syncthreads();
+  uint32_t mx[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) mx[t] = 0;
-    for (int64_t k = k0 + warp; k < k1; k += kBitsWarps) {
-      // orthant codes of every point and a counting sort of them (warp-private)
-      uint32_t o[D];
+  for (int t = 0; t < 8; ++t) mx[t] = 0;
+  for (int o = blockIdx.x * W + warp; o < N; o += gridDim.x * W) {
+    const uint16_t* si = sidx + (size_t)o * N;
+    const uint16_t* bo = boff + (size_t)o * (NB + 1);
+    for (int j = 0; j < NB; ++j) {
+      const int start = bo[j];
+      const int cnt = (int)bo[j + 1] - start;
+      if (cnt == 0) continue;
+      // quarter of the bucket for this sub-lane: [qa, qb)
+      const int q = (cnt + 3) >> 2;
+      const int qa = start + sub * q;
+      int qb = qa + q;
+      if (qb > start + cnt) qb = start + cnt;
+      Slices z;
+      slices_zero(z);
+      for (int b0 = qa; b0 < qb; b0 += 16) {
+        uint32_t w[16];
 #pragma unroll
-      for (int m = 0; m < D; ++m) o[m] = rank[(int64_t)m * N + k];
-      if (lane < NB) wcnt[lane] = 0;
-      __syncwarp();
-      for (int i = lane; i < n; i += 32) {
+        for (int u = 0; u < 16; ++u) w[u] = (b0 + u < qb) ? lab[(int)si[b0 + u] * kPassWords + gg] : 0u;
+        uint32_t tA, tB, fA, fB, eA, eB, s16;
+        csa(tA, z.ones, z.ones, w[0], w[1]);
+        csa(tB, z.ones, z.ones, w[2], w[3]);
+        csa(fA, z.twos, z.twos, tA, tB);
+        csa(tA, z.ones, z.ones, w[4], w[5]);
+        csa(tB, z.ones, z.ones, w[6], w[7]);
+        csa(fB, z.twos, z.twos, tA, tB);
+        csa(eA, z.fours, z.fours, fA, fB);
+        csa(tA, z.ones, z.ones, w[8], w[9]);
+        csa(tB, z.ones, z.ones, w[10], w[11]);
+        csa(fA, z.twos, z.twos, tA, tB);
+        csa(tA, z.ones, z.ones, w[12], w[13]);
+        csa(tB, z.ones, z.ones, w[14], w[15]);
+        csa(fB, z.twos, z.twos, tA, tB);
+        csa(eB, z.fours, z.fours, fA, fB);
+        csa(s16, z.eights, z.eights, eA, eB);
+        add16(z, s16);
+      }
+      // sum the four quarters (lanes gg, gg+8, gg+16, gg+24)
+      add_partner(z, 8);
+      add_partner(z, 16);
+      const uint64_t nb = (uint64_t)cnt * (uint64_t)NP;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int b = sub * 8 + t;
         uint32_t c = 0;
 #pragma unroll
-        for (int m = 0; m < D; ++m) c |= (uint32_t)(rank[(int64_t)m * N + i] >= o[m]) << m;
-        wc[i] = (uint8_t)c;
-        atomicAdd(&wcnt[c], 1u);
+        for (int kk = 0; kk < 4 + kHiPlanes; ++kk) c |= ((plane(z, kk) >> b) & 1u) << kk;
+        const uint64_t x = (uint64_t)c * (uint64_t)N;
+        const uint64_t num = x > nb ? x - nb : nb - x;
+        mx[t] = num > mx[t] ? (uint32_t)num : mx[t];
       }
-      __syncwarp();
-      {
-        const uint32_t v = lane < NB ? wcnt[lane] : 0u;
-        uint32_t incl = v;
-        for (int off = 1; off < 32; off <<= 1) {
-          const uint32_t a = __shfl_up_sync(0xffffffffu, incl, off);
-          if (lane >= off) incl += a;
-        }
-        if (lane < NB) { wcnt[NB + lane] = incl - v; wcnt[2 * NB + lane] = incl - v; }
-      }
-      __syncwarp();
-      for (int i = lane; i < n; i += 32) {
-        const uint32_t c = wc[i];
-        wi[atomicAdd(&wcnt[2 * NB + c], 1u)] = (uint16_t)i;
-      }
-      __syncwarp();
-      for (int j = 0; j < NB; ++j) {
-        const int cnt = (int)wcnt[j];
-        if (cnt == 0) continue;
-        const int start = (int)wcnt[NB + j];
-        // quarter of the bin for this sub-lane: [qa, qb)
-        const int q = (cnt + 3) >> 2;
-        const int qa = start + sub * q;
-        int qb = qa + q;
-        if (qb > start + cnt) qb = start + cnt;
-        Slices z;
-        slices_zero(z);
-        for (int b0 = qa; b0 < qb; b0 += 16) {
-          uint32_t w[16];
-#pragma unroll
-          for (int u = 0; u < 16; ++u) w[u] = (b0 + u < qb) ? lab[(int)wi[b0 + u] * kPassWords + gg] : 0u;
-          uint32_t tA, tB, fA, fB, eA, eB, s16;
-          csa(tA, z.ones, z.ones, w[0], w[1]);
-          csa(tB, z.ones, z.ones, w[2], w[3]);
-          csa(fA, z.twos, z.twos, tA, tB);
-          csa(tA, z.ones, z.ones, w[4], w[5]);
-          csa(tB, z.ones, z.ones, w[6], w[7]);
-          csa(fB, z.twos, z.twos, tA, tB);
-          csa(eA, z.fours, z.fours, fA, fB);
-          csa(tA, z.ones, z.ones, w[8], w[9]);
-          csa(tB, z.ones, z.ones, w[10], w[11]);
-          csa(fA, z.twos, z.twos, tA, tB);
-          csa(tA, z.ones, z.ones, w[12], w[13]);
-          csa(tB, z.ones, z.ones, w[14], w[15]);
-          csa(fB, z.twos, z.twos, tA, tB);
-          csa(eB, z.fours, z.fours, fA, fB);
-          csa(s16, z.eights, z.eights, eA, eB);
-          add16(z, s16);
-        }
-        // sum the four quarters (lanes gg, gg+8, gg+16, gg+24)
-        add_partner(z, 8);
-        add_partner(z, 16);
-        const uint64_t nb = (uint64_t)cnt * (uint64_t)NP;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int b = sub * 8 + t;
-          uint32_t c = 0;
-#pragma unroll
-          for (int kk = 0; kk < 4 + kHiPlanes; ++kk) c |= ((plane(z, kk) >> b) & 1u) << kk;
-          const uint64_t x = (uint64_t)c * (uint64_t)N;
-          const uint64_t num = x > nb ? x - nb : nb - x;
-          mx[t] = num > mx[t] ? (uint32_t)num : mx[t];
-        }
-      }
-      __syncwarp();
     }
+  }
+  // relabelling gg * 32 + sub * 8 + t of this pass: CTA maximum, then global
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int b = pass * kPassPerms + gg * 32 + sub * 8 + t;
-      if (b < B) atomicMax(&perm_best[b], (unsigned long long)mx[t]);
-    }
+  for (int t = 0; t < 8; ++t)
+    if (mx[t]) atomicMax(&cmax[gg * 32 + sub * 8 + t], mx[t]);
+  __syncthreads();
+  for (int t = threadIdx.x; t < kPassPerms; t += blockDim.x) {
+    const int b = pass * kPassPerms + t;
+    if (b < B && cmax[t]) atomicMax(&perm_best[b], (unsigned long long)cmax[t]);
   }
 }
 
@@ -469,41 +531,45 @@ int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* 
       ee = cudaMemsetAsync(ctx->perm_labels.ptr, 0, 4 * (size_t)N * G, s);
       if (ee == cudaSuccess) ee = cudaMemsetAsync(pbest, 0, 8 * (size_t)B, s);
       if (ee == cudaSuccess) {
-        int wpc = (int)((200 * 1024) / ((size_t)N * 8 + 1024));
-        if (wpc > 8) wpc = 8;
-        if (wpc < 1) wpc = 1;
-        const size_t smem = (size_t)wpc * ((size_t)N * 8 + 1024);
-        ee = cudaFuncSetAttribute(k_perm_labels_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (ee == cudaSuccess) {
-          int grid = (B + wpc - 1) / wpc;
-          if (grid > ctx->num_sms * 4) grid = ctx->num_sms * 4;
-          k_perm_labels_warp<<<grid, wpc * 32, smem, s>>>(N, NP, B, out3 + 6, G, wpc,
-                                                          (uint32_t*)ctx->perm_labels.ptr);
-          ee = cudaGetLastError();
-          ctx->launches += 1;
-        }
+        int grid = (B + kLabWarps - 1) / kLabWarps;
+        if (grid > ctx->num_sms * 8) grid = ctx->num_sms * 8;
+        k_perm_labels_warp<<<grid, kLabWarps * 32, 0, s>>>(N, NP, B, out3 + 6, G, (uint32_t*)ctx->perm_labels.ptr,
+                                                           (unsigned*)ctx->flags.ptr);
+        ee = cudaGetLastError();
+        ctx->launches += 1;
       }
       if (ee == cudaSuccess) {
         const uint32_t* rank = (const uint32_t*)ctx->rank.ptr;
         const uint32_t* lab = (const uint32_t*)ctx->perm_labels.ptr;
-        const int n16 = (int)((N + 15) & ~15);
-        const size_t smem = (size_t)N * kPassWords * 4 + (size_t)kBitsWarps * n16 * 3 +
-                            (size_t)kBitsWarps * 3 * (1 << d) * 4 + 16;
-        if (N <= kBitsMaxN && d <= 5 && smem <= 227u * 1024u) {
-          auto go = [&](auto kern) -> cudaError_t {
-            cudaError_t q = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const size_t smem2 = (size_t)N * kPassWords * 4 + (size_t)kPassPerms * 4;
+        if (N <= kBitsMaxN && d <= 5 && smem2 <= 227u * 1024u) {
+          const int nb1 = (1 << d) + 1;
+          ee = ctx->perm_codes.reserve(ctx, (size_t)N * N * 2 + (size_t)N * nb1 * 2 + 64) ? cudaErrorMemoryAllocation
+                                                                                            : cudaSuccess;
+          uint16_t* sidx = (uint16_t*)ctx->perm_codes.ptr;
+          uint16_t* boff = sidx + (size_t)N * N;
+          const size_t smem1 = (size_t)kSortWarps * (1 << d) * 4 + (size_t)kSortWarps * ((N + 15) & ~15);
+          auto go = [&](auto sortk, auto bitsk) -> cudaError_t {
+            cudaError_t q = cudaFuncSetAttribute(sortk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
             if (q != cudaSuccess) return q;
-            int grid = ctx->num_sms;
-            if (grid > N) grid = (int)N;
-            kern<<<grid, kBitsWarps * 32, smem, s>>>(rank, N, NP, B, G, lab, pbest);
-            return cudaGetLastError();
+            int g1 = (int)((N + kSortWarps - 1) / kSortWarps);
+            sortk<<<g1, kSortWarps * 32, smem1, s>>>(rank, (int)N, sidx, boff);
+            q = cudaFuncSetAttribute(bitsk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+            if (q != cudaSuccess) return q;
+            const int npass = (B + kPassPerms - 1) / kPassPerms;
+            for (int pass = 0; pass < npass && q == cudaSuccess; ++pass) {
+              bitsk<<<ctx->num_sms, kBits2Threads, smem2, s>>>(sidx, boff, (int)N, (int)NP, B, G, pass, lab, pbest);
+              q = cudaGetLastError();
+            }
+            ctx->launches += npass;  // plus the sort, counted below
+            return q;
           };
-          switch (d) {
-            case 1: ee = go(k_perm_bits<1>); break;
-            case 2: ee = go(k_perm_bits<2>); break;
-            case 3: ee = go(k_perm_bits<3>); break;
-            case 4: ee = go(k_perm_bits<4>); break;
-            default: ee = go(k_perm_bits<5>); break;
+          if (ee == cudaSuccess) switch (d) {
+            case 1: ee = go(k_perm_sort<1>, k_perm_bits<1>); break;
+            case 2: ee = go(k_perm_sort<2>, k_perm_bits<2>); break;
+            case 3: ee = go(k_perm_sort<3>, k_perm_bits<3>); break;
+            case 4: ee = go(k_perm_sort<4>, k_perm_bits<4>); break;
+            default: ee = go(k_perm_sort<5>, k_perm_bits<5>); break;
           }
         } else switch (d) {
           case 1: ee = launch_count<1>(rank, N, NP, B, G, lab, pbest, s, ctx->num_sms); break;
@@ -537,6 +603,7 @@ int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* 
   if (e != cudaSuccess) return observed->status = ctx_cuda_fail(ctx, e, "permutation test");
   if ((unsigned)(ctx->h_out[8] & 0xFFFFFFFFull) & ddks::kFlagNaN) return observed->status = DDKS_ENAN;
   if ((unsigned)(ctx->h_out[8] & 0xFFFFFFFFull) & ddks::kFlagTimeout) return observed->status = DDKS_ETIMEOUT;
+  if ((unsigned)(ctx->h_out[8] & 0xFFFFFFFFull) & ddks::kFlagBounds) return observed->status = DDKS_EUNSUPPORTED;
   observed->num_max = ctx->h_out[0];
   observed->denom = (uint64_t)NP * (uint64_t)NT;
   observed->D = (double)observed->num_max / (double)observed->denom;

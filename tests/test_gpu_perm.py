@@ -56,3 +56,10 @@ def test_config4_mixture_1000(torch):
     P, T = wl.CONFIGS["cfg4_d3_2000x2000_mixture_alt"]()
     g = _check(torch, P, T, 200, seed=7)
     assert g["p_value"] == 1.0 / 201
+
+
+def test_large_n_labels(torch):
+    # N = 9000 > 256: the label kernel narrows the NP-th key by radix digits
+    # before ranking its bucket; the lane-histogram counter takes N > 4096
+    P, T = wl.random_pair(11, 5000, 4000, 2, kind="normal")
+    _check(torch, P, T, 20, seed=123456789)
