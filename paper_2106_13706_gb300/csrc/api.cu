@@ -233,6 +233,7 @@ int ddks_encode_problem(ddks_ctx* ctx, const void* dP, int64_t NP, const void* d
   if ((rc = ctx->ti2.reserve(ctx, 4 * npad * d))) return rc;
   if ((rc = ctx->rank.reserve(ctx, 4 * (size_t)N * d))) return rc;
   if ((rc = ctx->sidx0.reserve(ctx, 4 * (size_t)N))) return rc;
+  if (want_sorted0 && (rc = ctx->pfx0.reserve(ctx, 4 * ((size_t)N + 2 * ddks_rank_pfx_elems(N))))) return rc;
   if ((rc = ctx->flags.reserve(ctx, 64))) return rc;
   cudaError_t e = cudaMemsetAsync(ctx->flags.ptr, 0, 4, st);
   if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "memset flags");
@@ -240,12 +241,14 @@ int ddks_encode_problem(ddks_ctx* ctx, const void* dP, int64_t NP, const void* d
                          (unsigned*)ctx->flags.ptr, st);
   if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "encode");
   ctx->launches += 1;
-  int n = 0;
-  e = ddks_launch_rank((const uint64_t*)ctx->keys.ptr, N, d, (uint64_t*)ctx->tk1.ptr,
+  int n = 0, pfx_done = 0;
+  uint32_t* pfx0 = want_sorted0 ? (uint32_t*)ctx->pfx0.ptr : nullptr;
+  e = ddks_launch_rank((const uint64_t*)ctx->keys.ptr, N, NP, d, (uint64_t*)ctx->tk1.ptr,
                        (uint32_t*)ctx->ti1.ptr, (uint64_t*)ctx->tk2.ptr, (uint32_t*)ctx->ti2.ptr,
                        (uint32_t*)ctx->rank.ptr, want_sorted0 ? (uint32_t*)ctx->sidx0.ptr : nullptr,
-                       st, &n);
+                       pfx0, pfx0 ? pfx0 + N : nullptr, &pfx_done, st, &n);
   ctx->launches += n;
+  ctx->pfx0_valid = pfx_done != 0;
   if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "rank");
   return DDKS_OK;
 }

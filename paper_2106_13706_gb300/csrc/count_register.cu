@@ -78,6 +78,7 @@ __global__ void k_reg_flags(const uint32_t* __restrict__ sidx0, int64_t N, int64
 //                   (P points by increasing rank_0 at [0, NP), T points at
 //                   [NPpad, NPpad + NT); the padding positions hold rank 0)
 //   olist[q]        pooled index of the q-th origin of [ob, oe), in sorted order
+//                   (exO = nullptr: every point is an origin, q = p)
 __global__ void k_reg_lists(const uint32_t* __restrict__ sidx0, const uint32_t* __restrict__ rank,
                             int64_t N, int64_t NP, int64_t NPpad, int64_t Lrow, int ds, int64_t ob,
                             int64_t oe, const uint32_t* __restrict__ pprefix,
@@ -96,7 +97,7 @@ __global__ void k_reg_lists(const uint32_t* __restrict__ sidx0, const uint32_t* 
     const uint32_t pp = pprefix[p];
     const int64_t pos = i < (uint64_t)NP ? (int64_t)pp : NPpad + (p - pp);
     for (int m = 0; m < ds; ++m) rankL[(int64_t)m * Lrow + pos] = rank[(int64_t)(m + 1) * N + i];
-    if (i >= (uint64_t)ob && i < (uint64_t)oe) olist[exO[p]] = i;
+    if (i >= (uint64_t)ob && i < (uint64_t)oe) olist[exO ? exO[p] : (uint32_t)p] = i;
   }
 }
 
@@ -722,11 +723,19 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
 
   auto grid = [](int64_t w) { int64_t g = (w + 255) / 256; return (int)(g > 152 * 32 ? 152 * 32 : (g < 1 ? 1 : g)); };
   int n = 0;
-  k_reg_flags<<<grid(N), 256, 0, st>>>(sidx0, N, NP, ob, oe, pprefix, exO);
-  ++n;
-  cudaError_t e = ddks_scan_rows(pprefix, pprefix, 1, N, true, stmp, st, &n);
-  if (e == cudaSuccess) e = ddks_scan_rows(exO, exO, 1, N, true, stmp, st, &n);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (ob == 0 && oe == N && ctx->pfx0_valid) {
+    // the rank kernel already produced the P prefix over the sorted order, and
+    // with every point an origin the origin prefix is the position itself
+    pprefix = (uint32_t*)ctx->pfx0.ptr;
+    exO = nullptr;
+  } else {
+    k_reg_flags<<<grid(N), 256, 0, st>>>(sidx0, N, NP, ob, oe, pprefix, exO);
+    ++n;
+    e = ddks_scan_rows(pprefix, pprefix, 1, N, true, stmp, st, &n);
+    if (e == cudaSuccess) e = ddks_scan_rows(exO, exO, 1, N, true, stmp, st, &n);
+    if (e != cudaSuccess) return e;
+  }
   k_reg_lists<<<grid(N), 256, 0, st>>>(sidx0, rank, N, NP, NPpad, Lrow, ds, ob, oe, pprefix, exO, rankL,
                                        olist);
   k_reg_meta<<<grid(no), 256, 0, st>>>(rank, olist, pprefix, N, no, ds, meta, orank);

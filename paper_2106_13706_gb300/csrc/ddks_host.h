@@ -52,6 +52,8 @@ struct ddks_ctx {
   uint64_t launches = 0;
   // scratch of the synchronous entry points
   DevBuf inP, inT, keys, tk1, tk2, ti1, ti2, rank, sidx0, best, bestj, out3, flags;
+  DevBuf pfx0;         // P points before each dimension-0 sorted position (+ chunk scratch)
+  bool pfx0_valid = false;  // pfx0 holds the current problem's prefix
   DevBuf reg_words, reg_meta;                   // register path
   DevBuf warp_words;                            // warp path: packed rank pairs
   DevBuf perm_keys, perm_labels, perm_best, perm_codes;  // permutation test
@@ -77,7 +79,7 @@ struct ddks_ctx {
   uint64_t graph_tick = 0, graph_captures = 0, graph_replays = 0;
 
   std::vector<DevBuf*> all_bufs() {
-    return {&inP, &inT, &keys, &tk1, &tk2, &ti1, &ti2, &rank, &sidx0, &best, &bestj, &out3,
+    return {&inP, &inT, &keys, &tk1, &tk2, &ti1, &ti2, &rank, &sidx0, &pfx0, &best, &bestj, &out3,
             &flags, &reg_words, &reg_meta, &warp_words, &perm_keys, &perm_labels, &perm_best, &perm_codes,
             &sig_cells, &sig_logp, &batch_desc, &batch_work};
   }

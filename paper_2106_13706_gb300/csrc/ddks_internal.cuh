@@ -50,10 +50,11 @@ struct DdksProblemDev {
 
 cudaError_t ddks_launch_encode(const void* P, const void* T, int64_t NP, int64_t NT, int d,
                                int is_f64, uint64_t* keys, unsigned* flags, cudaStream_t st);
-cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int d, uint64_t* tmp_keys,
+cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int64_t NP, int d, uint64_t* tmp_keys,
                              uint32_t* tmp_idx, uint64_t* tmp_keys2, uint32_t* tmp_idx2,
-                             uint32_t* rank, uint32_t* sorted_idx0, cudaStream_t st,
-                             int* launches);
+                             uint32_t* rank, uint32_t* sorted_idx0, uint32_t* pprefix0, uint32_t* cpfx,
+                             int* pfx_done, cudaStream_t st, int* launches);
+size_t ddks_rank_pfx_elems(int64_t N);
 size_t ddks_rank_scratch_elems(int64_t N);
 
 cudaError_t ddks_launch_lane(const uint32_t* rank, int64_t N, int64_t NP, int64_t NT, int d,

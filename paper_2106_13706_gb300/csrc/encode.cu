@@ -21,7 +21,7 @@ namespace {
 
 constexpr int kChunk = 2048;
 constexpr int kChunkThreads = 1024;
-constexpr int64_t kMaxMultiChunks = 4;  // above this, merge passes
+constexpr int64_t kMaxMultiChunks = 4;  // above this (N > 8192), merge passes
 
 template <typename V>
 __global__ void k_encode(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64_t NT,
@@ -43,9 +43,11 @@ DDKS_DEV bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
 }
 
 // grid: (chunks, d).  Sorts chunk blockIdx.x of dimension blockIdx.y.
+// With out_p (dimension 0 only), also writes out_p[base + t] = #{j < t :
+// sorted element j of the chunk is a P point}.
 __global__ void __launch_bounds__(kChunkThreads)
-k_chunk_sort(const uint64_t* __restrict__ keys, int64_t N, int64_t Npad,
-             uint64_t* __restrict__ out_k, uint32_t* __restrict__ out_i) {
+k_chunk_sort(const uint64_t* __restrict__ keys, int64_t N, int64_t Npad, int64_t NP,
+             uint64_t* __restrict__ out_k, uint32_t* __restrict__ out_i, uint32_t* __restrict__ out_p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   uint64_t* sk = reinterpret_cast<uint64_t*>(smraw);   // [kChunk]
   uint32_t* si = reinterpret_cast<uint32_t*>(sk + kChunk);
@@ -83,13 +85,46 @@ k_chunk_sort(const uint64_t* __restrict__ keys, int64_t N, int64_t Npad,
     out_k[(int64_t)m * Npad + base + t] = sk[t];
     out_i[(int64_t)m * Npad + base + t] = si[t];
   }
+  if (out_p && m == 0) {
+    // exclusive prefix of the P flags of the sorted chunk: thread t owns
+    // elements 2t, 2t+1
+    __shared__ uint32_t wsum[kChunkThreads / 32 + 1];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t f0 = si[2 * t] < (uint64_t)NP ? 1u : 0u, f1 = si[2 * t + 1] < (uint64_t)NP ? 1u : 0u;
+    const uint32_t v = f0 + f1;
+    uint32_t incl = v;
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += x;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = wsum[lane];
+      uint32_t wi = w;
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, wi, off);
+        if (lane >= off) wi += x;
+      }
+      wsum[lane] = wi - w;
+      if (lane == 31) wsum[32] = wi;
+    }
+    __syncthreads();
+    const uint32_t ex = wsum[warp] + incl - v;
+    uint32_t* P = out_p + base;
+    P[2 * t] = ex;
+    P[2 * t + 1] = ex + f0;
+  }
 }
 
 // One merge pass over runs of length L (Npad is a multiple of kChunk <= L).
-// grid-stride over (d * Npad) elements.
+// grid-stride over (d * Npad) elements.  With in_p / out_p, dimension 0 also
+// carries each element's count of P points before it within its run: after
+// the merge that is its own count plus the partner run's count below its slot.
 __global__ void k_merge_pass(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ in_i,
                              uint64_t* __restrict__ out_k, uint32_t* __restrict__ out_i,
-                             int64_t Npad, int d, int64_t L) {
+                             const uint32_t* __restrict__ in_p, uint32_t* __restrict__ out_p,
+                             int64_t Npad, int64_t NP, int d, int64_t L) {
   const int64_t total = Npad * d;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -103,6 +138,7 @@ __global__ void k_merge_pass(const uint64_t* __restrict__ in_k, const uint32_t* 
     const int64_t a = p - r * L;
     const int64_t ps = (r ^ 1) * L;  // partner run start
     int64_t dst;
+    uint32_t pc = (in_p && m == 0) ? in_p[p] : 0u;
     if (ps >= Npad) {
       dst = p;
     } else {
@@ -115,47 +151,82 @@ __global__ void k_merge_pass(const uint64_t* __restrict__ in_k, const uint32_t* 
       }
       const int64_t start = (r < (r ^ 1) ? r : (r ^ 1)) * L;
       dst = start + a + lo;
+      if (in_p && m == 0)
+        pc += lo < plen ? in_p[ps + lo]
+                        : in_p[ps + plen - 1] + (I[ps + plen - 1] < (uint64_t)NP ? 1u : 0u);
     }
     out_k[m * Npad + dst] = key;
     out_i[m * Npad + dst] = idx;
+    if (in_p && m == 0) out_p[dst] = pc;
   }
 }
 
 // With few sorted chunks: rank[m][i] = sum over chunks of #{keys < key_i}
 // (one lower_bound per chunk), and for dimension 0 the position of (key_i, i)
-// in the full sorted order, which places i in sorted_idx0.
+// in the full sorted order, which places i in sorted_idx0.  The searches of up
+// to 8 chunks advance together (independent loads in flight).
 __global__ void k_rank_multi(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ ck,
-                             const uint32_t* __restrict__ ci, int64_t N, int64_t Npad, int d,
-                             uint32_t* __restrict__ rank, uint32_t* __restrict__ sorted_idx0) {
+                             const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cpfx,
+                             int64_t N, int64_t NPc, int64_t Npad, int d, uint32_t* __restrict__ rank,
+                             uint32_t* __restrict__ sorted_idx0, uint32_t* __restrict__ pprefix0) {
+  constexpr int kG = 8;
   const int64_t total = N * d;
-  const int64_t nch = Npad / kChunk;
+  const int nch = (int)(Npad / kChunk);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t m = e / N;
     const int64_t i = e - m * N;
     const uint64_t key = keys[e];
-    uint32_t r = 0, pos = 0;
-    for (int64_t c = 0; c < nch; ++c) {
-      const uint64_t* K = ck + m * Npad + c * kChunk;
-      int lo = 0, hi = kChunk;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (K[mid] < key) lo = mid + 1; else hi = mid;
-      }
-      r += (uint32_t)lo;
-      if (m == 0 && sorted_idx0) {
-        // continue past equal keys with a smaller index
-        const uint32_t* I = ci + m * Npad + c * kChunk;
-        int lo2 = lo, hi2 = kChunk;
-        while (lo2 < hi2) {
-          const int mid = (lo2 + hi2) >> 1;
-          if (K[mid] == key && I[mid] < (uint32_t)i) lo2 = mid + 1; else hi2 = mid;
+    const bool want_pos = m == 0 && sorted_idx0;
+    uint32_t r = 0, pos = 0, pb = 0;
+    for (int c0 = 0; c0 < nch; c0 += kG) {
+      int lo[kG], hi[kG];
+#pragma unroll
+      for (int g = 0; g < kG; ++g) { lo[g] = 0; hi[g] = c0 + g < nch ? kChunk : 0; }
+      const uint64_t* K = ck + m * Npad + (int64_t)c0 * kChunk;
+      for (int step = 0; step < 12; ++step) {  // 2^11 = kChunk: at most 12 halvings
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+          if (lo[g] < hi[g]) {
+            const int mid = (lo[g] + hi[g]) >> 1;
+            if (K[g * kChunk + mid] < key) lo[g] = mid + 1; else hi[g] = mid;
+          }
         }
-        pos += (uint32_t)lo2;
+      }
+#pragma unroll
+      for (int g = 0; g < kG; ++g) r += (uint32_t)lo[g];
+      if (want_pos) {
+        // continue past equal keys with a smaller index
+        const uint32_t* I = ci + m * Npad + (int64_t)c0 * kChunk;
+        int lo2[kG], hi2[kG];
+#pragma unroll
+        for (int g = 0; g < kG; ++g) { lo2[g] = lo[g]; hi2[g] = c0 + g < nch ? kChunk : 0; }
+        for (int step = 0; step < 12; ++step) {
+#pragma unroll
+          for (int g = 0; g < kG; ++g) {
+            if (lo2[g] < hi2[g]) {
+              const int mid = (lo2[g] + hi2[g]) >> 1;
+              if (K[g * kChunk + mid] == key && I[g * kChunk + mid] < (uint32_t)i) lo2[g] = mid + 1;
+              else hi2[g] = mid;
+            }
+          }
+        }
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+          pos += (uint32_t)lo2[g];
+          if (pprefix0 && c0 + g < nch) {
+            const int64_t cb = (int64_t)(c0 + g) * kChunk;  // dimension 0: chunk start
+            pb += lo2[g] < kChunk ? cpfx[cb + lo2[g]]
+                                  : cpfx[cb + kChunk - 1] + (ci[cb + kChunk - 1] < (uint64_t)NPc ? 1u : 0u);
+          }
+        }
       }
     }
     rank[e] = r;
-    if (m == 0 && sorted_idx0) sorted_idx0[pos] = (uint32_t)i;
+    if (want_pos) {
+      sorted_idx0[pos] = (uint32_t)i;
+      if (pprefix0) pprefix0[pos] = pb;  // P points before position pos
+    }
   }
 }
 
@@ -177,10 +248,13 @@ __global__ void k_rank(const uint64_t* __restrict__ keys, const uint64_t* __rest
   }
 }
 
-__global__ void k_copy_idx(const uint32_t* __restrict__ sorted_i, int64_t N, uint32_t* __restrict__ out) {
+__global__ void k_copy_idx(const uint32_t* __restrict__ sorted_i, const uint32_t* __restrict__ sorted_p,
+                           int64_t N, uint32_t* __restrict__ out, uint32_t* __restrict__ out_p) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x)
+       i += (int64_t)gridDim.x * blockDim.x) {
     out[i] = sorted_i[i];
+    if (out_p) out_p[i] = sorted_p[i];
+  }
 }
 
 int grid_for(int64_t work, int threads) {
@@ -211,36 +285,45 @@ size_t ddks_rank_scratch_elems(int64_t N) {
 
 // keys: [d][N].  tmp buffers: d * Npad elements each.  rank: [d][N].
 // sorted_idx0 (optional): the pooled indices in increasing (rank_0, index) order.
-cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int d, uint64_t* tmp_keys,
+// pprefix0 (optional, with sorted_idx0; u32 [N] plus 2 * ddks_rank_pfx_elems(N)
+// of scratch at cpfx): pprefix0[p] = #{P points among sorted positions < p}.
+size_t ddks_rank_pfx_elems(int64_t N) { return ddks_rank_scratch_elems(N); }
+
+cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int64_t NP, int d, uint64_t* tmp_keys,
                              uint32_t* tmp_idx, uint64_t* tmp_keys2, uint32_t* tmp_idx2,
-                             uint32_t* rank, uint32_t* sorted_idx0, cudaStream_t st,
-                             int* launches) {
+                             uint32_t* rank, uint32_t* sorted_idx0, uint32_t* pprefix0, uint32_t* cpfx,
+                             int* pfx_done, cudaStream_t st, int* launches) {
   const int64_t Npad = (int64_t)ddks_rank_scratch_elems(N);
   const int64_t chunks = Npad / kChunk;
   dim3 g((unsigned)chunks, (unsigned)d);
   const size_t smem = (size_t)kChunk * 12;
+  const bool pfx = sorted_idx0 && pprefix0 && cpfx;
+  if (pfx_done) *pfx_done = pfx ? 1 : 0;
   cudaError_t e = cudaFuncSetAttribute(k_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_chunk_sort<<<g, kChunkThreads, smem, st>>>(keys, N, Npad, tmp_keys, tmp_idx);
+  uint32_t* cp = pfx ? cpfx : nullptr;             // [Npad] P prefixes, dimension 0
+  uint32_t* cp2 = pfx ? cpfx + Npad : nullptr;     // [Npad] the other merge buffer
+  k_chunk_sort<<<g, kChunkThreads, smem, st>>>(keys, N, Npad, NP, tmp_keys, tmp_idx, cp);
   int n = 1;
   if (chunks <= kMaxMultiChunks) {
-    k_rank_multi<<<grid_for(N * d, 256), 256, 0, st>>>(keys, tmp_keys, tmp_idx, N, Npad, d, rank,
-                                                       sorted_idx0);
+    k_rank_multi<<<grid_for(N * d, 256), 256, 0, st>>>(keys, tmp_keys, tmp_idx, cp, N, NP, Npad, d, rank,
+                                                       sorted_idx0, pfx ? pprefix0 : nullptr);
     if (launches) *launches += 2;
     return cudaGetLastError();
   }
   uint64_t *ck = tmp_keys, *nk = tmp_keys2;
   uint32_t *ci = tmp_idx, *ni = tmp_idx2;
   for (int64_t L = kChunk; L < Npad; L <<= 1) {
-    k_merge_pass<<<grid_for(Npad * d, 256), 256, 0, st>>>(ck, ci, nk, ni, Npad, d, L);
+    k_merge_pass<<<grid_for(Npad * d, 256), 256, 0, st>>>(ck, ci, nk, ni, cp, cp2, Npad, NP, d, L);
     ++n;
     uint64_t* tk = ck; ck = nk; nk = tk;
     uint32_t* ti = ci; ci = ni; ni = ti;
+    uint32_t* tp = cp; cp = cp2; cp2 = tp;
   }
   k_rank<<<grid_for(N * d, 256), 256, 0, st>>>(keys, ck, N, Npad, d, rank);
   ++n;
   if (sorted_idx0) {
-    k_copy_idx<<<grid_for(N, 256), 256, 0, st>>>(ci, N, sorted_idx0);
+    k_copy_idx<<<grid_for(N, 256), 256, 0, st>>>(ci, cp, N, sorted_idx0, pfx ? pprefix0 : nullptr);
     ++n;
   }
   if (launches) *launches += n;
