@@ -263,13 +263,15 @@ int ddks_count_origins(ddks_ctx* ctx, int64_t NP, int64_t NT, int32_t d, int64_t
 }
 
 int ddks_count_origins_plan(ddks_ctx* ctx, const ddks_plan& plan, int64_t NP, int64_t NT, int32_t d,
-                            int64_t ob, int64_t oe, uint64_t* best, int32_t* bestj, cudaStream_t st) {
+                            int64_t ob, int64_t oe, uint64_t* best, int32_t* bestj, cudaStream_t st,
+                            unsigned long long* out3, bool* reduced) {
+  if (reduced) *reduced = false;
   const int64_t N = NP + NT;
   const uint32_t* rank = (const uint32_t*)ctx->rank.ptr;
   cudaError_t e = cudaSuccess;
   switch (plan.path) {
     case DDKS_PATH_REGISTER:
-      e = ddks_launch_register(ctx, rank, N, NP, NT, d, ob, oe, best, bestj, st, plan);
+      e = ddks_launch_register(ctx, rank, N, NP, NT, d, ob, oe, best, bestj, st, plan, out3, reduced);
       break;
     case DDKS_PATH_LANE:
       e = ddks_launch_lane(rank, N, NP, NT, d, ob, oe, best, bestj, st, plan.threads, ctx->num_sms);
@@ -326,14 +328,17 @@ static int distance_impl(ddks_ctx* ctx, const void* P, int64_t NP, const void* T
     if ((r = ctx->best.reserve(ctx, 8 * (size_t)(no > 0 ? no : 1)))) return r;
     if ((r = ctx->bestj.reserve(ctx, 4 * (size_t)(no > 0 ? no : 1)))) return r;
     if ((r = ctx->out3.reserve(ctx, 64 + ddks_reduce_scratch_bytes()))) return r;
+    bool reduced = false;
     if ((r = ddks_count_origins_plan(ctx, plan, NP, NT, d, ob, oe, (uint64_t*)ctx->best.ptr,
-                                     (int32_t*)ctx->bestj.ptr, s)))
+                                     (int32_t*)ctx->bestj.ptr, s, (unsigned long long*)ctx->out3.ptr, &reduced)))
       return r;
     stage_mark(ctx, 2, s);
-    cudaError_t ee = ddks_launch_reduce((const uint64_t*)ctx->best.ptr, (const int32_t*)ctx->bestj.ptr, no,
-                                        ob, (unsigned long long*)ctx->out3.ptr, (char*)ctx->out3.ptr + 64, s);
-    ctx->launches += 2;
-    if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "reduce");
+    if (!reduced) {
+      cudaError_t ee = ddks_launch_reduce((const uint64_t*)ctx->best.ptr, (const int32_t*)ctx->bestj.ptr, no,
+                                          ob, (unsigned long long*)ctx->out3.ptr, (char*)ctx->out3.ptr + 64, s);
+      ctx->launches += 2;
+      if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "reduce");
+    }
     stage_mark(ctx, 3, s);
     return DDKS_OK;
   });

@@ -439,6 +439,25 @@ DDKS_DEV void chunk_partial(const uint32_t* __restrict__ tile, int j, int n,
   for (int r = 0; r < kR; ++r) nib_flush<2>(acc[r], one);
 }
 
+DDKS_DEV void origin_best(const uint32_t* __restrict__ gcnt, int64_t q, int ds, int64_t NP, int64_t NT,
+                          uint64_t& bv, int& bj);
+
+// Fused final step (out3 != nullptr): per-origin maxima into best/bestj at
+// pooled index - ob, and the result {num_max, arg-max origin, orthant} into
+// out3.  done: [blocks + 1] zeroed tickets; packed: one zeroed word holding
+// max over origins of (num << kPackShift) | (kPackMask - position).
+struct OriginMetaFinal {
+  unsigned long long* out3;
+  unsigned* done;
+  unsigned long long* packed;
+  uint64_t* best;
+  int32_t* bestj;
+  int64_t ob;
+  int blocks;
+};
+constexpr int kPackShift = 26;                       // positions < 2^26; numerators < 2^38
+constexpr unsigned long long kPackMask = (1ull << kPackShift) - 1;
+
 // ---- bulk asynchronous copies with mbarrier completion
 
 DDKS_DEV void mbar_init(uint32_t bar, uint32_t count) {
@@ -489,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, OCC)
 k_register(const uint8_t* __restrict__ planes, const uint8_t* __restrict__ oplanes,
            const OriginMeta* __restrict__ meta, int64_t no, int64_t NP, int64_t NT, int64_t NPpad,
            int64_t Lrow, int C, int CP, int64_t CLP, int64_t CLT, uint32_t one,
-           uint32_t* __restrict__ gcnt, unsigned* __restrict__ flags) {
+           uint32_t* __restrict__ gcnt, unsigned* __restrict__ flags, const OriginMetaFinal fin) {
   extern __shared__ __align__(16) uint32_t sm[];
   uint32_t* tile = sm;                                            // [kTP] assembled words
   uint8_t* raw = reinterpret_cast<uint8_t*>(tile + kTP);          // [2][DS][kTP] plane ring
@@ -644,6 +663,57 @@ k_register(const uint8_t* __restrict__ planes, const uint8_t* __restrict__ oplan
     const uint32_t v = (b & 4) ? (w >> 16) : (w & 0xFFFFu);
     if (v) atomicAdd(&gcnt[(q0 + (i >> 4)) * 32 + sample * 16 + (i & 15)], v);
   }
+  if (!fin.out3) return;
+  // The last unit of an origin block to finish turns the block's counts into
+  // per-origin maxima and a packed (num, origin) candidate for the global
+  // maximum; the last block to finish writes the result.  Tickets only: no
+  // CTA waits for another.
+  __shared__ unsigned ticket;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) ticket = atomicAdd(&fin.done[blk], 1u);
+  __syncthreads();
+  if (ticket != (unsigned)(C - 1)) return;
+  __threadfence();
+  for (int q = tid; q < nq; q += kThreads) {
+    uint64_t bv;
+    int bj;
+    origin_best(gcnt, q0 + q, DS, NP, NT, bv, bj);
+    const uint32_t k = meta[q0 + q].k;
+    const int64_t pos = (int64_t)k - fin.ob;
+    fin.best[pos] = bv;
+    fin.bestj[pos] = bj;
+    // larger numerator first, then the lower origin
+    atomicMax(fin.packed, (bv << kPackShift) | (kPackMask - (unsigned long long)pos));
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) ticket = atomicAdd(&fin.done[fin.blocks], 1u);
+  __syncthreads();
+  if (ticket != (unsigned)(fin.blocks - 1) || tid != 0) return;
+  __threadfence();
+  const unsigned long long pk = atomicAdd(fin.packed, 0ull);
+  const int64_t pos = (int64_t)(kPackMask - (pk & kPackMask));
+  fin.out3[0] = pk >> kPackShift;
+  fin.out3[1] = (unsigned long long)(fin.ob + pos);
+  fin.out3[2] = (unsigned long long)(long long)__ldcg(&fin.bestj[pos]);
+}
+
+// The best orthant of origin q from its counts gcnt[q][sample][phase][bin]
+// (the code's bit 0 is the phase, i.e. dimension 0).  Reads through L2: the
+// counts were added by other CTAs.
+DDKS_DEV void origin_best(const uint32_t* __restrict__ gcnt, int64_t q, int ds, int64_t NP, int64_t NT,
+                          uint64_t& bv, int& bj) {
+  const uint32_t* c = gcnt + q * 32;
+  bv = 0;
+  bj = 0;
+  const int nbin = 1 << ds;
+  for (int code = 0; code < 2 * nbin; ++code) {
+    const int ph = code & 1, bin = code >> 1;
+    const uint64_t cp = __ldcg(&c[ph * 8 + bin]), ct = __ldcg(&c[16 + ph * 8 + bin]);
+    const uint64_t num = ddks::numer(cp, ct, (uint64_t)NP, (uint64_t)NT);
+    if (num > bv) { bv = num; bj = code; }
+  }
 }
 
 // one thread per origin: its 2 * 2^DS orthants from gcnt[q][sample][phase][bin]
@@ -652,16 +722,9 @@ __global__ void k_reg_final(const uint32_t* __restrict__ gcnt, const OriginMeta*
                             uint64_t* __restrict__ best, int32_t* __restrict__ bestj) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < no;
        q += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t* c = gcnt + q * 32;
-    uint64_t bv = 0;
-    int bj = 0;
-    const int nbin = 1 << ds;
-    for (int code = 0; code < 2 * nbin; ++code) {
-      const int ph = code & 1, bin = code >> 1;
-      const uint64_t cp = c[ph * 8 + bin], ct = c[16 + ph * 8 + bin];
-      const uint64_t num = ddks::numer(cp, ct, (uint64_t)NP, (uint64_t)NT);
-      if (num > bv) { bv = num; bj = code; }
-    }
+    uint64_t bv;
+    int bj;
+    origin_best(gcnt, q, ds, NP, NT, bv, bj);
     const uint32_t k = meta[q].k;
     best[k - ob] = bv;
     bestj[k - ob] = bj;
@@ -687,7 +750,9 @@ bool ddks_register_supported(int d, int64_t NP, int64_t NT) {
 
 cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N, int64_t NP,
                                  int64_t NT, int d, int64_t ob, int64_t oe, uint64_t* best,
-                                 int32_t* bestj, cudaStream_t st, const ddks_plan& plan) {
+                                 int32_t* bestj, cudaStream_t st, const ddks_plan& plan,
+                                 unsigned long long* out3, bool* reduced) {
+  if (reduced) *reduced = false;
   if (!ddks_register_supported(d, NP, NT)) return cudaErrorInvalidValue;
   const int ds = d - 1;
   const int64_t no = oe - ob;
@@ -696,11 +761,12 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   const int64_t blocks = (no + kOC - 1) / kOC;
   const int64_t NPpad = (NP + 15) & ~(int64_t)15, NTpad = (NT + 15) & ~(int64_t)15;
   const int64_t Lrow = NPpad + NTpad;
-  // scratch (u32): pprefix N, exO N, olist no, gcnt no*32, rankL ds*Lrow, orank ds*no,
-  // scan tmp; then meta
+  // scratch (u32): pprefix N, exO N, olist no, gcnt no*32 + tickets (blocks + 1) + packed (2),
+  // rankL ds*Lrow, orank ds*no, scan tmp; then meta
   const size_t scan_tmp = ddks_scan_tmp_elems(1, N);
-  const size_t n_u32 =
-      (size_t)N * 2 + (size_t)no + (size_t)no * 32 + (size_t)ds * Lrow + (size_t)ds * no + scan_tmp;
+  const size_t n_fin = (size_t)blocks + 1 + 4;
+  const size_t n_u32 = (size_t)N * 2 + (size_t)no + (size_t)no * 32 + n_fin + (size_t)ds * Lrow +
+                       (size_t)ds * no + scan_tmp;
   int rc = ctx->reg_meta.reserve(ctx, n_u32 * 4 + (size_t)no * sizeof(OriginMeta) + 64);
   if (rc) return cudaErrorMemoryAllocation;
   // byte planes [blocks][ds][Lrow] and origin planes [blocks][ds][128]
@@ -710,8 +776,12 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   uint32_t* exO = pprefix + N;
   uint32_t* olist = exO + N;
   uint32_t* gcnt = olist + no;
+  unsigned* done = gcnt + no * 32;  // [blocks + 1] tickets, then the packed maximum (8-byte aligned)
+  unsigned long long* packed = reinterpret_cast<unsigned long long*>(
+      (reinterpret_cast<uintptr_t>(done + blocks + 1) + 7) & ~(uintptr_t)7);
   // rankL must be 16-byte aligned for the pack kernel's vector loads
-  uint32_t* rankL = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(gcnt + no * 32) + 15) & ~(uintptr_t)15);
+  uint32_t* rankL = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(gcnt + no * 32 + n_fin) + 15) &
+                                                ~(uintptr_t)15);
   uint32_t* orank = rankL + (size_t)ds * Lrow;
   uint32_t* stmp = orank + (size_t)ds * no;
   OriginMeta* meta = reinterpret_cast<OriginMeta*>(
@@ -774,24 +844,30 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   const int64_t CLP = (((NP + CP - 1) / CP) + 15) & ~(int64_t)15;
   const int64_t CLT = (((NT + CT - 1) / CT) + 15) & ~(int64_t)15;
   const int64_t C = CP + CT;
-  e = cudaMemsetAsync(gcnt, 0, (size_t)no * 32 * 4, st);
+  e = cudaMemsetAsync(gcnt, 0, ((size_t)no * 32 + n_fin) * 4, st);
   if (e != cudaSuccess) return e;
   const size_t smem = reg_smem(ds);
   const unsigned ctas = (unsigned)(blocks * C);
   const int occ = plan.reg_occ == 2 || plan.reg_occ == 3 ? plan.reg_occ : 4;
+  OriginMetaFinal fin{out3, done, packed, best, bestj, ob, (int)blocks};
   auto go = [&](auto kern) -> cudaError_t {
     cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (r != cudaSuccess) return r;
     kern<<<ctas, kThreads, smem, st>>>(planes, oplanes, meta, no, NP, NT, NPpad, Lrow, (int)C, (int)CP, CLP,
-                                        CLT, 1u, gcnt, flags);
+                                        CLT, 1u, gcnt, flags, fin);
     return cudaGetLastError();
   };
   if (ds == 1) e = occ == 2 ? go(k_register<1, 2>) : occ == 3 ? go(k_register<1, 3>) : go(k_register<1, 4>);
   else if (ds == 2) e = occ == 2 ? go(k_register<2, 2>) : occ == 3 ? go(k_register<2, 3>) : go(k_register<2, 4>);
   else e = occ == 2 ? go(k_register<3, 2>) : occ == 3 ? go(k_register<3, 3>) : go(k_register<3, 4>);
   if (e != cudaSuccess) return e;
-  k_reg_final<<<grid(no), 256, 0, st>>>(gcnt, meta, no, NP, NT, ob, ds, best, bestj);
-  n += 2;
+  ++n;
+  if (out3) {
+    if (reduced) *reduced = true;
+  } else {
+    k_reg_final<<<grid(no), 256, 0, st>>>(gcnt, meta, no, NP, NT, ob, ds, best, bestj);
+    ++n;
+  }
   ctx->launches += n;
   return cudaGetLastError();
 }

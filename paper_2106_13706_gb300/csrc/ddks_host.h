@@ -95,17 +95,22 @@ int ddks_encode_problem(ddks_ctx* ctx, const void* dP, int64_t NP, const void* d
 void ddks_stage_mark(ddks_ctx* ctx, int i, cudaStream_t st);
 int ddks_count_origins(ddks_ctx* ctx, int64_t NP, int64_t NT, int32_t d, int64_t ob, int64_t oe,
                        uint64_t* best, int32_t* bestj, cudaStream_t st);
+// out3 / reduced as for ddks_launch_register (only the register path reduces)
 int ddks_count_origins_plan(ddks_ctx* ctx, const ddks_plan& plan, int64_t NP, int64_t NT, int32_t d,
-                            int64_t ob, int64_t oe, uint64_t* best, int32_t* bestj, cudaStream_t st);
+                            int64_t ob, int64_t oe, uint64_t* best, int32_t* bestj, cudaStream_t st,
+                            unsigned long long* out3 = nullptr, bool* reduced = nullptr);
 
 // tune.cu
 int ddks_select_path(ddks_ctx* ctx, int64_t NP, int64_t NT, int32_t d, ddks_plan* plan);
 void ddks_tune_load(ddks_ctx* ctx);
 
 // count_register.cu
+// out3 (optional): the kernel also reduces over origins and writes
+// {num_max, arg-max origin, orthant} there; *reduced tells whether it did.
 cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N, int64_t NP,
                                  int64_t NT, int d, int64_t ob, int64_t oe, uint64_t* best,
-                                 int32_t* bestj, cudaStream_t st, const ddks_plan& plan);
+                                 int32_t* bestj, cudaStream_t st, const ddks_plan& plan,
+                                 unsigned long long* out3 = nullptr, bool* reduced = nullptr);
 bool ddks_register_supported(int d, int64_t NP, int64_t NT);
 
 // graph.cu: a hash of everything a captured graph depends on

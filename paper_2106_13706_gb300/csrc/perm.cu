@@ -516,13 +516,17 @@ int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* 
     // observed statistic
     if ((r = ctx->best.reserve(ctx, 8 * (size_t)N))) return r;
     if ((r = ctx->bestj.reserve(ctx, 4 * (size_t)N))) return r;
+    bool reduced = false;
     if ((r = ddks_count_origins_plan(ctx, plan, NP, NT, d, 0, N, (uint64_t*)ctx->best.ptr,
-                                     (int32_t*)ctx->bestj.ptr, s)))
+                                     (int32_t*)ctx->bestj.ptr, s, out3, &reduced)))
       return r;
-    cudaError_t ee = ddks_launch_reduce((const uint64_t*)ctx->best.ptr, (const int32_t*)ctx->bestj.ptr, N, 0,
-                                        out3, (char*)ctx->out3.ptr + 64, s);
-    ctx->launches += 2;
-    if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "reduce");
+    cudaError_t ee = cudaSuccess;
+    if (!reduced) {
+      ee = ddks_launch_reduce((const uint64_t*)ctx->best.ptr, (const int32_t*)ctx->bestj.ptr, N, 0, out3,
+                              (char*)ctx->out3.ptr + 64, s);
+      ctx->launches += 2;
+      if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "reduce");
+    }
     if ((r = ctx->perm_labels.reserve(ctx, 4 * (size_t)N * (G > 0 ? G : 1)))) return r;
     if ((r = ctx->perm_best.reserve(ctx, 8 * (size_t)Bc))) return r;
     unsigned long long* pbest = (unsigned long long*)ctx->perm_best.ptr;
