@@ -122,6 +122,23 @@ def peak_lane_ops(torch, dev, sm_max_mhz):
     return sms * 128 * mhz * 1e6, sms, mhz
 
 
+def peak_compares(torch, dev, sm_max_mhz, path, d):
+    """Compare-rate roofline of the count kernel's path, in compares/s.
+
+    Register path (d = 2..4, bit-sliced): one 3-input logic op on the ALU pipe
+    (64 lanes/clk/SM) decides one bit of 32 seven-bit comparisons, so a pair
+    costs 7 (d - 1) / 32 ALU lane-ops and its dimension 0 none (sorted order):
+    peak = SMs x 64 x clock x 32 d / (7 (d - 1)).  Other paths compare one
+    dimension of one pair per lane-op: peak = SMs x 128 lanes x clock."""
+    lanes, sms, mhz = peak_lane_ops(torch, dev, sm_max_mhz)
+    if path == "register" and d >= 2:
+        peak = sms * 64 * mhz * 1e6 * 32.0 * d / (7.0 * (d - 1))
+        basis = (f"{sms} SMs x 64 ALU lanes x {mhz:.0f} MHz x 32 bit slices x d/(7(d-1)) "
+                 "(7 logic ops per 32 seven-bit compares; dimension 0 by sorted order)")
+        return peak, basis
+    return lanes, f"{sms} SMs x 128 int lanes x {mhz:.0f} MHz (max SM clock)"
+
+
 def load_traffic(kernel_key):
     """DRAM bytes per launch of the count kernel from the committed ncu summary
     (profiles/traffic.json), if it was taken on the current kernel source."""
@@ -231,15 +248,20 @@ def run_ours(args):
                "d2h_bytes_per_step": 3 * 8 + 4}
 
     clocks = sampler.summary()
-    peak, sms, mhz = peak_lane_ops(torch, local, clocks.get("sm_max_mhz"))
+    path_name = (["auto", "register", "lane", "warp", "sort"][tuned[0]] if tuned else
+                 ["auto", "register", "lane", "warp", "sort"][args.path])
+    if path_name == "auto":
+        path_name = "register" if 2 <= d <= 4 else ("warp" if d <= 13 else "sort")
+    peak, basis = peak_compares(torch, local, clocks.get("sm_max_mhz"), path_name, d)
+    lane_peak = peak_lane_ops(torch, local, clocks.get("sm_max_mhz"))[0]
     cnt = statistics.mean(count_ms) if count_ms else None
     roof = None
     if cnt:
         achieved = units / (cnt * 1e-3)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
                 "frac": achieved / peak, "traffic": load_traffic({"cfg2": "count_d4_20k"}.get(args.workload, "")),
-                "kernel": "orthant count kernel", "kernel_ms": cnt,
-                "peak_basis": f"{sms} SMs x 128 int lanes x {mhz:.0f} MHz (max SM clock)"}
+                "kernel": "orthant count stage (re-rank pack + count + fused reduction)", "kernel_ms": cnt,
+                "peak_basis": basis, "compares_per_lane_op": achieved / lane_peak}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

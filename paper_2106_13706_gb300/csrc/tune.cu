@@ -114,7 +114,7 @@ int ddks_autotune(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64
   if ((rc = ctx->bestj.reserve(ctx, 4 * (size_t)N))) return rc;
   if ((rc = ctx->out3.reserve(ctx, 64 + ddks_reduce_scratch_bytes()))) return rc;
   std::vector<ddks_plan> cands;
-  for (int occ = 2; occ <= 4; ++occ) {
+  for (int occ : {4, 6, 8}) {
     ddks_plan p; p.path = DDKS_PATH_REGISTER; p.reg_occ = occ; cands.push_back(p);
   }
   for (int th : {64, 128, 256}) {
