@@ -39,8 +39,9 @@
 
 namespace {
 
-constexpr int kThreads = 128;         // one origin slot per thread
-constexpr int kOC = kThreads;         // origin slots per block
+constexpr int kThreads = 64;          // threads per CTA of the count kernel
+constexpr int kOPL = 2;               // origin slots per thread
+constexpr int kOC = kThreads * kOPL;  // origin slots per block (128)
 constexpr int kOB = kOC - 1;          // origins per block (x' <= 127 fits 7 bits)
 constexpr int kBits = 7;              // planes per dimension
 constexpr int kTG = 64;               // groups (of 32 points) per staged tile
@@ -416,7 +417,9 @@ DDKS_DEV void origin_best(const uint32_t* __restrict__ gcnt, const OriginMeta& m
 
 // Unit u: origin block u / C, chunk u % C of the groups, where chunks [0, CP)
 // cover the P list's groups [0, GP) in pieces of CGP and chunks [CP, C) the T
-// list's groups [GP, GP + GT) in pieces of CGT.
+// list's groups [GP, GP + GT) in pieces of CGT.  Thread t holds origin slots
+// t and t + kThreads of the block (kOPL = 2 origins per lane share every
+// broadcast load of a group record).
 template <int DS, int OCC>
 __global__ void __launch_bounds__(kThreads, OCC)
 k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes,
@@ -462,24 +465,39 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
   __syncthreads();
   if (tid == 0 && ntiles > 0) issue(0);
 
-  // this lane's origin: comparison masks s[m][k] = all ones where bit k of o'_m is set
-  const int64_t q = (int64_t)blk * kOB + tid;
-  const bool real = tid < kOB && q < no;
-  uint32_t s[DS][kBits];
+  // this lane's origins: comparison masks s[o][m][k] = all ones where bit k
+  // of o'_m is set, and the split (sample-local)
+  bool real[kOPL];
+  int64_t q[kOPL];
+  uint32_t s[kOPL][DS][kBits];
+  int split[kOPL];
 #pragma unroll
-  for (int m = 0; m < DS; ++m) {
-    const uint32_t o = real ? (uint32_t)oplanes[((size_t)blk * DS + m) * kOC + tid] : 0u;
+  for (int o = 0; o < kOPL; ++o) {
+    const int slot = tid + o * kThreads;
+    q[o] = (int64_t)blk * kOB + slot;
+    real[o] = slot < kOB && q[o] < no;
 #pragma unroll
-    for (int k = 0; k < kBits; ++k) s[m][k] = 0u - ((o >> k) & 1u);
+    for (int m = 0; m < DS; ++m) {
+      const uint32_t v = real[o] ? (uint32_t)oplanes[((size_t)blk * DS + m) * kOC + slot] : 0u;
+#pragma unroll
+      for (int k = 0; k < kBits; ++k) s[o][m][k] = 0u - ((v >> k) & 1u);
+    }
+    split[o] = 0;
+    if (real[o]) {
+      const OriginMeta mt = meta[q[o]];
+      split[o] = (int)(sample == 0 ? mt.sP : mt.sT);
+    }
   }
-  int split = 0;  // sample-local
-  if (real) {
-    const OriginMeta mt = meta[q];
-    split = (int)(sample == 0 ? mt.sP : mt.sT);
-  }
-  uint32_t accA[NS], accB[NS];  // all points, phase-B points
+  // acc[S]: points so far in all dimensions of S; snap[S]: acc at the origin's
+  // split (phase A part); the phase-B part is acc - snap
+  uint32_t acc[kOPL][NS], snap[kOPL][NS];
+  bool crossed[kOPL];
 #pragma unroll
-  for (int S = 0; S < NS; ++S) accA[S] = accB[S] = 0;
+  for (int o = 0; o < kOPL; ++o) {
+    crossed[o] = (g0 - gbase) * 32 >= split[o];  // the unit starts in phase B
+#pragma unroll
+    for (int S = 0; S < NS; ++S) acc[o][S] = snap[o][S] = 0;
+  }
   for (int t = 0; t < ntiles; ++t) {
     const int base = g0 + t * kTG;
     const int n = (g1 - base) < kTG ? (g1 - base) : kTG;
@@ -489,42 +507,41 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
     if (ok) {
       const uint4* tile = reinterpret_cast<const uint4*>(tiles + (t & 1) * kTG * RW);
       for (int gi = 0; gi < n; ++gi) {
-        // compare the group's 32 points with this lane's origin, dimension by dimension
-        uint32_t G[DS];
+        // compare the group's 32 points with both origins, dimension by dimension
+        uint32_t G[kOPL][DS];
 #pragma unroll
         for (int m = 0; m < DS; ++m) {
           const uint4 a = tile[(gi * RW + m * 8) / 4];
           const uint4 b = tile[(gi * RW + m * 8) / 4 + 1];
           const uint32_t pl[kBits] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z};
-          uint32_t r = 0xFFFFFFFFu;
 #pragma unroll
-          for (int k = 0; k < kBits; ++k) r = cmp_step(s[m][k], pl[k], r);
-          G[m] = r;
-        }
-        uint32_t M[NS + 1];
-        M[0] = 0xFFFFFFFFu;
+          for (int o = 0; o < kOPL; ++o) {
+            uint32_t r = 0xFFFFFFFFu;
 #pragma unroll
-        for (int S = 1; S <= NS; ++S) {
-          // G of the lowest dimension in S; every index folds in the unrolled loop
-          const uint32_t gl = (S & 1) ? G[0] : ((S & 2) ? G[DS > 1 ? 1 : 0] : G[DS > 2 ? 2 : 0]);
-          M[S] = M[S & (S - 1)] & gl;
+            for (int k = 0; k < kBits; ++k) r = cmp_step(s[o][m][k], pl[k], r);
+            G[o][m] = r;
+          }
         }
         const int pos0 = (base + gi - gbase) * 32;  // sample-local position of bit 0
-        if (pos0 + 32 <= split || pos0 >= split) {
-          const uint32_t isB = pos0 >= split ? 1u : 0u;
+#pragma unroll
+        for (int o = 0; o < kOPL; ++o) {
+          uint32_t M[NS + 1];
+          M[0] = 0xFFFFFFFFu;
 #pragma unroll
           for (int S = 1; S <= NS; ++S) {
-            const uint32_t c = (uint32_t)__popc(M[S]);
-            accA[S - 1] += c;
-            accB[S - 1] += c * isB;
+            // G of the lowest dimension in S; every index folds in the unrolled loop
+            const uint32_t gl = (S & 1) ? G[o][0] : ((S & 2) ? G[o][DS > 1 ? 1 : 0] : G[o][DS > 2 ? 2 : 0]);
+            M[S] = M[S & (S - 1)] & gl;
           }
-        } else {
-          const uint32_t pb = 0xFFFFFFFFu << (split - pos0);  // phase-B points of the group
+          if (!crossed[o] && pos0 + 32 > split[o]) {
+            // the group holds the origin's split, or begins phase B
+            const uint32_t pa = pos0 < split[o] ? ~(0xFFFFFFFFu << (split[o] - pos0)) : 0u;  // phase-A points
 #pragma unroll
-          for (int S = 1; S <= NS; ++S) {
-            accA[S - 1] += (uint32_t)__popc(M[S]);
-            accB[S - 1] += (uint32_t)__popc(M[S] & pb);
+            for (int S = 1; S <= NS; ++S) snap[o][S - 1] = acc[o][S - 1] + (uint32_t)__popc(M[S] & pa);
+            crossed[o] = true;
           }
+#pragma unroll
+          for (int S = 1; S <= NS; ++S) acc[o][S - 1] += (uint32_t)__popc(M[S]);
         }
       }
     }
@@ -538,12 +555,16 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
       return;
     }
   }
-  if (real) {
-    uint32_t* c = gcnt + q * kCnt;
+#pragma unroll
+  for (int o = 0; o < kOPL; ++o) {
+    if (!real[o]) continue;
+    uint32_t* c = gcnt + q[o] * kCnt;
 #pragma unroll
     for (int S = 0; S < NS; ++S) {
-      if (accA[S]) atomicAdd(&c[(sample * 2 + 0) * NS + S], accA[S]);
-      if (accB[S]) atomicAdd(&c[(sample * 2 + 1) * NS + S], accB[S]);
+      const uint32_t all = acc[o][S];
+      const uint32_t b = crossed[o] ? all - snap[o][S] : 0u;
+      if (all) atomicAdd(&c[(sample * 2 + 0) * NS + S], all);
+      if (b) atomicAdd(&c[(sample * 2 + 1) * NS + S], b);
     }
   }
   // The last unit of an origin block to finish turns the block's counters
@@ -557,11 +578,13 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
   __syncthreads();
   if (ticket != (unsigned)(C - 1)) return;
   __threadfence();
-  if (real) {
+#pragma unroll
+  for (int o = 0; o < kOPL; ++o) {
+    if (!real[o]) continue;
     uint64_t bv;
     int bj;
-    const OriginMeta mt = meta[q];
-    origin_best<DS>(gcnt, mt, q, NP, NT, bv, bj);
+    const OriginMeta mt = meta[q[o]];
+    origin_best<DS>(gcnt, mt, q[o], NP, NT, bv, bj);
     const int64_t pos = (int64_t)mt.k - fin.ob;
     fin.best[pos] = bv;
     fin.bestj[pos] = bj;
@@ -679,7 +702,7 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   if (e != cudaSuccess) return e;
   ++n;
   // chunks of the groups per origin block: about 3 waves of the resident CTAs
-  const int64_t slots = (int64_t)ctx->num_sms * 8;
+  const int64_t slots = (int64_t)ctx->num_sms * 12;
   int64_t want = (3 * slots + blocks - 1) / blocks;  // chunks per block
   if (want < 2) want = 2;
   int64_t CG = (ngroups + want - 1) / want;
@@ -691,7 +714,8 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   if (e != cudaSuccess) return e;
   const size_t smem = reg_smem(ds);
   const unsigned ctas = (unsigned)(blocks * C);
-  const int occ = plan.reg_occ == 4 || plan.reg_occ == 8 ? plan.reg_occ : 6;  // CTAs per SM
+  // resident 64-thread CTAs per SM the kernel is built for: 8, 12 or 16
+  const int occ = plan.reg_occ == 4 ? 8 : plan.reg_occ == 8 ? 16 : 12;
   Final fin{out3, done, packed, best, bestj, ob, (int)blocks};
   auto go = [&](auto kern) -> cudaError_t {
     cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -700,9 +724,9 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
                                         CGT, gcnt, flags, fin);
     return cudaGetLastError();
   };
-  if (ds == 1) e = occ == 4 ? go(k_register<1, 4>) : occ == 6 ? go(k_register<1, 6>) : go(k_register<1, 8>);
-  else if (ds == 2) e = occ == 4 ? go(k_register<2, 4>) : occ == 6 ? go(k_register<2, 6>) : go(k_register<2, 8>);
-  else e = occ == 4 ? go(k_register<3, 4>) : occ == 6 ? go(k_register<3, 6>) : go(k_register<3, 8>);
+  if (ds == 1) e = occ == 8 ? go(k_register<1, 8>) : occ == 12 ? go(k_register<1, 12>) : go(k_register<1, 16>);
+  else if (ds == 2) e = occ == 8 ? go(k_register<2, 8>) : occ == 12 ? go(k_register<2, 12>) : go(k_register<2, 16>);
+  else e = occ == 8 ? go(k_register<3, 8>) : occ == 12 ? go(k_register<3, 12>) : go(k_register<3, 16>);
   if (e != cudaSuccess) return e;
   ++n;
   if (reduced) *reduced = out3 != nullptr;

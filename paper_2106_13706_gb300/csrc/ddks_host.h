@@ -29,7 +29,7 @@ struct ddks_plan {
   int path = DDKS_PATH_AUTO;
   int threads = 256;  // lane path: threads per CTA (one origin each)
   int warps = 8;      // warp path: warps per CTA (one origin each)
-  int reg_occ = 6;    // register path: resident CTAs per SM the kernel is built for (4, 6 or 8)
+  int reg_occ = 4;    // register path occupancy class: 4, 6, 8 (8, 12, 16 resident 64-thread CTAs per SM)
 };
 
 struct ServeState;  // serve.cu
