@@ -398,3 +398,157 @@ int oracle_num_threads(void) {
   return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ vdKS, rdKS
+ *
+ * The two approximations of Sec. 2.2 (Alg. vdKS, Alg. rdKS), step by step in
+ * the algorithms' order, with the readings of the garbled or silent points:
+ *   - NormalizeData / the normalised sample space: per dimension, the pooled
+ *     sample is shifted and rescaled to [0, 1] with its minimum and maximum,
+ *     x' = (x - lo) / (hi - lo); a constant dimension maps to 0.
+ *   - vdKS IndexFromPoint: voxel coordinate c_m = floor(x'_m * V), with
+ *     x'_m = 1 put in the last voxel V - 1.
+ *   - vdKS SumOrthants: the orthants around a filled voxel c split the voxel
+ *     grid with the same ">=" convention as ddKS (voxel c' is on the upper
+ *     side of dimension m iff c'_m >= c_m); the statistic is the largest
+ *     ABSOLUTE orthant sum of Diff = (T fraction - P fraction) over the voxels
+ *     filled by either sample.  Exact integer numerator: Diff * NP * NT =
+ *     nT * NP - nP * NT per voxel.
+ *   - rdKS IdentifyCorners: the d + 1 corners are the origin and the d unit
+ *     vectors of the normalised space; distances are Euclidean, compared as
+ *     squared distances summed in dimension order (no fused multiply-add).
+ *   - rdKS GetDFromCornerLists: the two-sample Kolmogorov-Smirnov statistic
+ *     of the two sorted distance lists, sup_r |F_P(r) - F_T(r)| with
+ *     F(r) = #{distance <= r} / n, i.e. evaluated after all distances equal
+ *     to r; the statistic is the largest over the corners.
+ */
+
+static int normalise(const void* P, int64_t NP, const void* T, int64_t NT, int d, int is_f64,
+                     double* out) {
+  const int64_t N = NP + NT;
+  for (int m = 0; m < d; ++m) {
+    double lo = pooled_coord(P, T, NP, d, is_f64, 0, m), hi = lo;
+    for (int64_t i = 1; i < N; ++i) {
+      const double v = pooled_coord(P, T, NP, d, is_f64, i, m);
+      if (v < lo) lo = v;
+      if (v > hi) hi = v;
+    }
+    const double span = hi - lo;
+    for (int64_t i = 0; i < N; ++i) {
+      const double v = pooled_coord(P, T, NP, d, is_f64, i, m);
+      out[i * d + m] = span > 0.0 ? (v - lo) / span : 0.0;
+    }
+  }
+  return ORC_OK;
+}
+
+int oracle_vdks(const void* P, int64_t NP, const void* T, int64_t NT, int d, int is_f64, int V,
+                uint64_t* num_max) {
+  int rc = check_args(P, NP, T, NT, d, is_f64);
+  if (rc) return rc;
+  if (V < 1 || !num_max) return ORC_EINVAL;
+  double cells_d = 1.0;
+  for (int m = 0; m < d; ++m) cells_d *= V;
+  if (cells_d > (double)(1 << 24)) return ORC_EINVAL;
+  const int64_t cells = (int64_t)cells_d, N = NP + NT;
+  double* xn = (double*)malloc(sizeof(double) * (size_t)(N * d));
+  int64_t* diff = (int64_t*)calloc((size_t)cells, sizeof(int64_t));
+  unsigned char* filled = (unsigned char*)calloc((size_t)cells, 1);
+  int* coord = (int*)malloc(sizeof(int) * (size_t)d);
+  int* ccur = (int*)malloc(sizeof(int) * (size_t)d);
+  int64_t* osum = (int64_t*)malloc(sizeof(int64_t) * ((size_t)1 << d));
+  if (!xn || !diff || !filled || !coord || !ccur || !osum) {
+    free(xn); free(diff); free(filled); free(coord); free(ccur); free(osum);
+    return ORC_ENOMEM;
+  }
+  normalise(P, NP, T, NT, d, is_f64, xn);
+  /* voxel occupation: Diff numerator nT * NP - nP * NT */
+  for (int64_t i = 0; i < N; ++i) {
+    int64_t idx = 0, stride = 1;
+    for (int m = 0; m < d; ++m) {
+      int c = (int)floor(xn[i * d + m] * (double)V);
+      if (c > V - 1) c = V - 1;
+      idx += (int64_t)c * stride;
+      stride *= V;
+    }
+    diff[idx] += i < NP ? -(int64_t)NT : (int64_t)NP;
+    filled[idx] = 1;
+  }
+  uint64_t best = 0;
+  for (int64_t f = 0; f < cells; ++f) {
+    if (!filled[f]) continue;
+    int64_t r = f;
+    for (int m = 0; m < d; ++m) { coord[m] = (int)(r % V); r /= V; }
+    for (int j = 0; j < (1 << d); ++j) osum[j] = 0;
+    /* every voxel goes to the orthant of its sides relative to voxel f */
+    for (int64_t c = 0; c < cells; ++c) {
+      int64_t t = c;
+      int code = 0;
+      for (int m = 0; m < d; ++m) {
+        ccur[m] = (int)(t % V);
+        t /= V;
+        if (ccur[m] >= coord[m]) code |= 1 << m;
+      }
+      osum[code] += diff[c];
+    }
+    for (int j = 0; j < (1 << d); ++j) {
+      const uint64_t a = (uint64_t)(osum[j] < 0 ? -osum[j] : osum[j]);
+      if (a > best) best = a;
+    }
+  }
+  *num_max = best;
+  free(xn); free(diff); free(filled); free(coord); free(ccur); free(osum);
+  return ORC_OK;
+}
+
+typedef struct {
+  double r;
+  int is_t;
+} orc_dist;
+
+static int cmp_dist(const void* a, const void* b) {
+  const double x = ((const orc_dist*)a)->r, y = ((const orc_dist*)b)->r;
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+int oracle_rdks(const void* P, int64_t NP, const void* T, int64_t NT, int d, int is_f64,
+                uint64_t* num_max, uint64_t* per_corner /* d + 1 entries or NULL */) {
+  int rc = check_args(P, NP, T, NT, d, is_f64);
+  if (rc) return rc;
+  if (!num_max) return ORC_EINVAL;
+  const int64_t N = NP + NT;
+  double* xn = (double*)malloc(sizeof(double) * (size_t)(N * d));
+  orc_dist* list = (orc_dist*)malloc(sizeof(orc_dist) * (size_t)N);
+  if (!xn || !list) { free(xn); free(list); return ORC_ENOMEM; }
+  normalise(P, NP, T, NT, d, is_f64, xn);
+  uint64_t best = 0;
+  for (int corner = 0; corner <= d; ++corner) {
+    /* corner 0: the origin; corner m + 1: unit vector m */
+    for (int64_t i = 0; i < N; ++i) {
+      double s = 0.0;
+      for (int m = 0; m < d; ++m) {
+        const double c = (corner == m + 1) ? 1.0 : 0.0;
+        const double t = xn[i * d + m] - c;
+        const double sq = t * t;
+        s = s + sq;
+      }
+      list[i].r = s;
+      list[i].is_t = i >= NP;
+    }
+    qsort(list, (size_t)N, sizeof(orc_dist), cmp_dist);
+    int64_t cp = 0, ct = 0;
+    uint64_t cb = 0;
+    for (int64_t i = 0; i < N; ++i) {
+      if (list[i].is_t) ++ct; else ++cp;
+      if (i + 1 < N && list[i + 1].r == list[i].r) continue;  /* after all equal distances */
+      const int64_t x = cp * NT, y = ct * NP;
+      const uint64_t v = (uint64_t)(x > y ? x - y : y - x);
+      if (v > cb) cb = v;
+    }
+    if (per_corner) per_corner[corner] = cb;
+    if (cb > best) best = cb;
+  }
+  *num_max = best;
+  free(xn); free(list);
+  return ORC_OK;
+}

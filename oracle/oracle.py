@@ -47,7 +47,8 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    # no fused multiply-add: the rdKS distances are summed as written
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -85,6 +86,10 @@ def _load():
             lib.oracle_significance.restype = i32
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = i32
+            lib.oracle_vdks.argtypes = [vp, i64, vp, i64, i32, i32, i32, ctypes.POINTER(u64)]
+            lib.oracle_vdks.restype = i32
+            lib.oracle_rdks.argtypes = [vp, i64, vp, i64, i32, i32, ctypes.POINTER(u64), vp]
+            lib.oracle_rdks.restype = i32
             _lib = lib
     return _lib
 
@@ -192,6 +197,33 @@ def significance(P, T, num_max: int, estimator: int = 1, model: int = 0):
     if rc != ORC_OK:
         raise OracleError(rc)
     return float(S.value), float(lp.value)
+
+
+def vdks(P, T, voxels_per_dim: int):
+    """Alg. vdKS (voxel approximation): returns dict(num_max, denom, D)."""
+    lib = _load()
+    P, T, f64 = _prep(P, T)
+    NP, d = P.shape
+    NT = T.shape[0]
+    num = ctypes.c_uint64(0)
+    rc = lib.oracle_vdks(P.ctypes.data, NP, T.ctypes.data, NT, d, f64, int(voxels_per_dim), ctypes.byref(num))
+    if rc != ORC_OK:
+        raise OracleError(rc)
+    return dict(num_max=int(num.value), denom=NP * NT, D=int(num.value) / float(NP * NT))
+
+
+def rdks(P, T):
+    """Alg. rdKS (radial approximation): returns dict(num_max, denom, D, per_corner)."""
+    lib = _load()
+    P, T, f64 = _prep(P, T)
+    NP, d = P.shape
+    NT = T.shape[0]
+    num = ctypes.c_uint64(0)
+    pc = np.zeros(d + 1, dtype=np.uint64)
+    rc = lib.oracle_rdks(P.ctypes.data, NP, T.ctypes.data, NT, d, f64, ctypes.byref(num), pc.ctypes.data)
+    if rc != ORC_OK:
+        raise OracleError(rc)
+    return dict(num_max=int(num.value), denom=NP * NT, D=int(num.value) / float(NP * NT), per_corner=pc)
 
 
 def brute_force_ddks(P, T):
