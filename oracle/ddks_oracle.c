@@ -41,6 +41,7 @@
 #define ORC_ENAN -2
 #define ORC_EOVERFLOW -3
 #define ORC_ENOMEM -4
+#define ORC_RDKS_MAX_D 4096
 
 /* coordinate m of pooled point i: P rows first, then T rows */
 static double pooled_coord(const void* P, const void* T, int64_t NP, int d,
@@ -52,8 +53,9 @@ static double pooled_coord(const void* P, const void* T, int64_t NP, int d,
   return is_f64 ? ((const double*)T)[t * d + m] : (double)((const float*)T)[t * d + m];
 }
 
-static int check_args(const void* P, int64_t NP, const void* T, int64_t NT, int d, int is_f64) {
-  if (!P || !T || NP < 1 || NT < 1 || d < 1 || d > 30) return ORC_EINVAL;
+static int check_args_dmax(const void* P, int64_t NP, const void* T, int64_t NT, int d, int is_f64,
+                           int dmax) {
+  if (!P || !T || NP < 1 || NT < 1 || d < 1 || d > dmax) return ORC_EINVAL;
   /* NP*NT must stay below 2^62 so every numerator fits an int64 */
   if ((double)NP * (double)NT >= 4.611686018427387904e18) return ORC_EOVERFLOW;
   int64_t N = NP + NT;
@@ -63,6 +65,10 @@ static int check_args(const void* P, int64_t NP, const void* T, int64_t NT, int 
       if (v != v) return ORC_ENAN;
     }
   return ORC_OK;
+}
+
+static int check_args(const void* P, int64_t NP, const void* T, int64_t NT, int d, int is_f64) {
+  return check_args_dmax(P, NP, T, NT, d, is_f64, 30);
 }
 
 static int cmp_u64(const void* a, const void* b) {
@@ -405,7 +411,9 @@ int oracle_num_threads(void) {
  * the algorithms' order, with the readings of the garbled or silent points:
  *   - NormalizeData / the normalised sample space: per dimension, the pooled
  *     sample is shifted and rescaled to [0, 1] with its minimum and maximum,
- *     x' = (x - lo) / (hi - lo); a constant dimension maps to 0.
+ *     x' = (x - lo) / (hi - lo); a constant dimension maps to 0.  The
+ *     rescaling needs a finite range: an infinite coordinate, or a range
+ *     hi - lo that overflows to infinity, is rejected (ORC_EINVAL).
  *   - vdKS IndexFromPoint: voxel coordinate c_m = floor(x'_m * V), with
  *     x'_m = 1 put in the last voxel V - 1.
  *   - vdKS SumOrthants: the orthants around a filled voxel c split the voxel
@@ -434,6 +442,7 @@ static int normalise(const void* P, int64_t NP, const void* T, int64_t NT, int d
       if (v > hi) hi = v;
     }
     const double span = hi - lo;
+    if (!isfinite(lo) || !isfinite(hi) || !isfinite(span)) return ORC_EINVAL;
     for (int64_t i = 0; i < N; ++i) {
       const double v = pooled_coord(P, T, NP, d, is_f64, i, m);
       out[i * d + m] = span > 0.0 ? (v - lo) / span : 0.0;
@@ -461,7 +470,10 @@ int oracle_vdks(const void* P, int64_t NP, const void* T, int64_t NT, int d, int
     free(xn); free(diff); free(filled); free(coord); free(ccur); free(osum);
     return ORC_ENOMEM;
   }
-  normalise(P, NP, T, NT, d, is_f64, xn);
+  if (normalise(P, NP, T, NT, d, is_f64, xn) != ORC_OK) {
+    free(xn); free(diff); free(filled); free(coord); free(ccur); free(osum);
+    return ORC_EINVAL;
+  }
   /* voxel occupation: Diff numerator nT * NP - nP * NT */
   for (int64_t i = 0; i < N; ++i) {
     int64_t idx = 0, stride = 1;
@@ -513,14 +525,19 @@ static int cmp_dist(const void* a, const void* b) {
 
 int oracle_rdks(const void* P, int64_t NP, const void* T, int64_t NT, int d, int is_f64,
                 uint64_t* num_max, uint64_t* per_corner /* d + 1 entries or NULL */) {
-  int rc = check_args(P, NP, T, NT, d, is_f64);
+  /* rdKS is linear in d (Sec. 2.2, and the 1000-dimensional study of Sec. 4),
+     so it takes up to ORC_RDKS_MAX_D dimensions rather than ddKS's 30 */
+  int rc = check_args_dmax(P, NP, T, NT, d, is_f64, ORC_RDKS_MAX_D);
   if (rc) return rc;
   if (!num_max) return ORC_EINVAL;
   const int64_t N = NP + NT;
   double* xn = (double*)malloc(sizeof(double) * (size_t)(N * d));
   orc_dist* list = (orc_dist*)malloc(sizeof(orc_dist) * (size_t)N);
   if (!xn || !list) { free(xn); free(list); return ORC_ENOMEM; }
-  normalise(P, NP, T, NT, d, is_f64, xn);
+  if (normalise(P, NP, T, NT, d, is_f64, xn) != ORC_OK) {
+    free(xn); free(list);
+    return ORC_EINVAL;
+  }
   uint64_t best = 0;
   for (int corner = 0; corner <= d; ++corner) {
     /* corner 0: the origin; corner m + 1: unit vector m */

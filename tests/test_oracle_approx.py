@@ -125,6 +125,33 @@ def test_rdks_one_dimension_with_ties():
     assert orc.rdks(P, T)["num_max"] == _ks_num(P[:, 0], T[:, 0])
 
 
+def test_rdks_high_dimension_matches_brute_force():
+    # rdKS is not limited to ddKS's 30 dimensions (linear in d, Sec. 4's
+    # 1000-dimensional study); a few corners of a 40-dimensional case
+    rng = np.random.default_rng(40)
+    P, T = rng.random((12, 40)), rng.random((9, 40)) ** 1.5
+    r = orc.rdks(P, T)
+    for c in (0, 1, 17, 40):
+        assert int(r["per_corner"][c]) == _brute_corner(P, T, c)
+    assert r["num_max"] == max(int(v) for v in r["per_corner"])
+
+
+@pytest.mark.parametrize("bad", [np.inf, -np.inf, "overflow"])
+def test_normalisation_needs_a_finite_range(bad):
+    # NormalizeData rescales every dimension by its range: an infinite
+    # coordinate, or a range that overflows, has no normalised image
+    P = np.array([[0.0, 1.0], [2.0, 3.0]])
+    T = np.array([[1.0, 1.0], [0.5, 2.5]])
+    if bad == "overflow":
+        P[0, 1], T[0, 1] = -1.5e308, 1.5e308
+    else:
+        T[1, 0] = bad
+    for f in (lambda: orc.vdks(P, T, 4), lambda: orc.rdks(P, T)):
+        with pytest.raises(orc.OracleError):
+            f()
+    assert orc.ddks(P, T)["denom"] == 4  # the exact statistic takes them
+
+
 # ------------------------------------------------------------- planted mistakes
 import ctypes  # noqa: E402
 import os  # noqa: E402
