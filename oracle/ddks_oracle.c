@@ -452,7 +452,7 @@ static int normalise(const void* P, int64_t NP, const void* T, int64_t NT, int d
 }
 
 int oracle_vdks(const void* P, int64_t NP, const void* T, int64_t NT, int d, int is_f64, int V,
-                uint64_t* num_max) {
+                uint64_t* num_max, int64_t* argmax_voxel /* or NULL */, int32_t* argmax_orthant /* or NULL */) {
   int rc = check_args(P, NP, T, NT, d, is_f64);
   if (rc) return rc;
   if (V < 1 || !num_max) return ORC_EINVAL;
@@ -487,6 +487,8 @@ int oracle_vdks(const void* P, int64_t NP, const void* T, int64_t NT, int d, int
     filled[idx] = 1;
   }
   uint64_t best = 0;
+  int64_t bf = -1; /* the lowest filled voxel, then the lowest orthant, reaching the max */
+  int bjj = 0;
   for (int64_t f = 0; f < cells; ++f) {
     if (!filled[f]) continue;
     int64_t r = f;
@@ -505,10 +507,12 @@ int oracle_vdks(const void* P, int64_t NP, const void* T, int64_t NT, int d, int
     }
     for (int j = 0; j < (1 << d); ++j) {
       const uint64_t a = (uint64_t)(osum[j] < 0 ? -osum[j] : osum[j]);
-      if (a > best) best = a;
+      if (a > best || bf < 0) { best = a; bf = f; bjj = j; }
     }
   }
   *num_max = best;
+  if (argmax_voxel) *argmax_voxel = bf;
+  if (argmax_orthant) *argmax_orthant = bjj;
   free(xn); free(diff); free(filled); free(coord); free(ccur); free(osum);
   return ORC_OK;
 }

@@ -86,7 +86,8 @@ def _load():
             lib.oracle_significance.restype = i32
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = i32
-            lib.oracle_vdks.argtypes = [vp, i64, vp, i64, i32, i32, i32, ctypes.POINTER(u64)]
+            lib.oracle_vdks.argtypes = [vp, i64, vp, i64, i32, i32, i32, ctypes.POINTER(u64),
+                                        ctypes.POINTER(i64), ctypes.POINTER(i32)]
             lib.oracle_vdks.restype = i32
             lib.oracle_rdks.argtypes = [vp, i64, vp, i64, i32, i32, ctypes.POINTER(u64), vp]
             lib.oracle_rdks.restype = i32
@@ -200,16 +201,22 @@ def significance(P, T, num_max: int, estimator: int = 1, model: int = 0):
 
 
 def vdks(P, T, voxels_per_dim: int):
-    """Alg. vdKS (voxel approximation): returns dict(num_max, denom, D)."""
+    """Alg. vdKS (voxel approximation): returns dict(num_max, denom, D,
+    argmax_voxel, argmax_orthant), the arg-max being the lowest filled voxel
+    (linear index sum_m c_m V^m) and then the lowest orthant reaching num_max."""
     lib = _load()
     P, T, f64 = _prep(P, T)
     NP, d = P.shape
     NT = T.shape[0]
     num = ctypes.c_uint64(0)
-    rc = lib.oracle_vdks(P.ctypes.data, NP, T.ctypes.data, NT, d, f64, int(voxels_per_dim), ctypes.byref(num))
+    av = ctypes.c_int64(0)
+    aj = ctypes.c_int32(0)
+    rc = lib.oracle_vdks(P.ctypes.data, NP, T.ctypes.data, NT, d, f64, int(voxels_per_dim), ctypes.byref(num),
+                         ctypes.byref(av), ctypes.byref(aj))
     if rc != ORC_OK:
         raise OracleError(rc)
-    return dict(num_max=int(num.value), denom=NP * NT, D=int(num.value) / float(NP * NT))
+    return dict(num_max=int(num.value), denom=NP * NT, D=int(num.value) / float(NP * NT),
+                argmax_voxel=int(av.value), argmax_orthant=int(aj.value))
 
 
 def rdks(P, T):

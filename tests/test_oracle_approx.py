@@ -45,6 +45,29 @@ def test_vdks_hand_cases():
         assert orc.vdks(P, T, 64)["num_max"] == case["num_max"], case["name"]
 
 
+def test_vdks_argmax_is_the_lowest_voxel_and_orthant():
+    # brute force over the voxel grid in numpy: orthant sums at every filled
+    # voxel, the first (voxel, orthant) in increasing order reaching the max
+    rng = np.random.default_rng(12)
+    for d, V in [(2, 5), (3, 3)]:
+        P, T = rng.normal(size=(60, d)), rng.normal(0.3, 1.0, size=(45, d))
+        X = np.concatenate([P, T])
+        lo, hi = X.min(axis=0), X.max(axis=0)
+        vox = np.minimum(np.floor((X - lo) / (hi - lo) * V), V - 1).astype(np.int64)
+        lin = (vox * (V ** np.arange(d))).sum(axis=1)
+        w = np.where(np.arange(len(X)) < len(P), -len(T), len(P))
+        best, arg = -1, None
+        for f in sorted(set(lin.tolist())):
+            cf = vox[lin == f][0]
+            codes = ((vox >= cf) * (1 << np.arange(d))).sum(axis=1)
+            for j in range(1 << d):
+                a = abs(int(w[codes == j].sum()))
+                if a > best:
+                    best, arg = a, (f, j)
+        r = orc.vdks(P, T, V)
+        assert (r["num_max"], r["argmax_voxel"], r["argmax_orthant"]) == (best, arg[0], arg[1])
+
+
 def test_vdks_single_voxel_is_zero():
     rng = np.random.default_rng(1)
     P, T = rng.random((30, 3)), rng.random((20, 3)) + 0.5
@@ -182,7 +205,7 @@ def _mutant(tmp_path, name, old, new):
                     "-lm"], check=True, capture_output=True)
     lib = ctypes.CDLL(str(so))
     i64, i32, u64, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p
-    lib.oracle_vdks.argtypes = [vp, i64, vp, i64, i32, i32, i32, ctypes.POINTER(u64)]
+    lib.oracle_vdks.argtypes = [vp, i64, vp, i64, i32, i32, i32, ctypes.POINTER(u64), vp, vp]
     lib.oracle_vdks.restype = i32
     lib.oracle_rdks.argtypes = [vp, i64, vp, i64, i32, i32, ctypes.POINTER(u64), vp]
     lib.oracle_rdks.restype = i32
@@ -195,7 +218,8 @@ def _mutant(tmp_path, name, old, new):
 def _m_vdks(lib, P, T, V):
     P, T = np.ascontiguousarray(P, np.float64), np.ascontiguousarray(T, np.float64)
     n = ctypes.c_uint64(0)
-    assert lib.oracle_vdks(P.ctypes.data, len(P), T.ctypes.data, len(T), P.shape[1], 1, V, ctypes.byref(n)) == 0
+    assert lib.oracle_vdks(P.ctypes.data, len(P), T.ctypes.data, len(T), P.shape[1], 1, V, ctypes.byref(n), None,
+                           None) == 0
     return n.value
 
 
