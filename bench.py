@@ -36,8 +36,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["cfg2", "cfg1", "cfg3", "perm", "batch", "serve"],
-                    default="cfg2")
+    ap.add_argument("--workload", choices=["cfg2", "cfg1", "cfg3", "perm", "batch", "serve", "vdks", "rdks",
+                                           "rdks_large"], default="cfg2")
     ap.add_argument("--perms", type=int, default=1000)
     ap.add_argument("--requests", type=int, default=600)
     ap.add_argument("--path", type=int, default=0, help="force a kernel path (0 = auto)")
@@ -53,6 +53,36 @@ WORKLOADS = {
     "cfg1": ("cfg1_d3_200x200_f32", "exact ddKS d=3 NP=NT=200 f32 gaussian, T shifted by 0.2"),
     "cfg3": ("cfg3_d12_4096x4096_f64", "exact ddKS d=12 NP=NT=4096 f64 uniform, T coord 5 ~ Beta(2,2)"),
 }
+
+
+# The approximations of Sec. 2.2, each measured under its own metric.
+APPROX = {
+    "vdks": ("vdKS (Alg. vdKS) d=3 NP=NT=8,000,000 f32, P ~ N(0,I3), T ~ N(0.2*1,I3), 32 voxels per dimension",
+             "vdks_points_per_s", "points/s"),
+    "rdks": ("rdKS (Alg. rdKS) d=1000 NP=NT=100 f32, diagonal versus uniform (Sec. 4's 1000-dimensional case)",
+             "rdks_tests_per_s", "tests/s"),
+    "rdks_large": ("rdKS (Alg. rdKS) d=3 NP=NT=1,000,000 f32, P ~ N(0,I3), T ~ N(0.05*1,I3)",
+                   "rdks_points_per_s", "points/s"),
+}
+FP64_NOMINAL_FLOPS = 1.25e12  # GB300 FP64, FMA counted as 2 FLOP
+
+
+def approx_inputs(name):
+    """(P, T, voxels per dimension or None) of an approximation workload."""
+    from paper_2106_13706_gb300 import workloads as wl
+    if name == "vdks":
+        return wl.gaussian_pair(0, 8_000_000, 8_000_000, 3, shift=0.2) + (32,)
+    if name == "rdks":
+        return wl.dvu_pair(0, 100, 100, 1000) + (None,)
+    return wl.gaussian_pair(0, 1_000_000, 1_000_000, 3, shift=0.05) + (None,)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except (OSError, ValueError):
+        return {}
 
 
 def dist_env():
@@ -336,6 +366,210 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def approx_cpu(name, P, T, V, budget_s=8.0):
+    """The oracle as it stands (one host core) on a bounded sample of the
+    workload: the first n points of each sample, n doubled until the budget."""
+    from oracle import oracle as orc
+    d = P.shape[1]
+    if name == "rdks":
+        reps, t0 = 0, time.perf_counter()
+        while reps < 3 or time.perf_counter() - t0 < 1.0:
+            orc.rdks(P, T)
+            reps += 1
+        dt = time.perf_counter() - t0
+        return {"value": reps / dt, "unit": "tests/s", "cores": 1, "kind": "oracle",
+                "sample": f"the full test, {reps} repetitions in {dt:.2f} s"}
+    n, best = 25_000, None
+    while True:
+        Ps, Ts = P[:n], T[:n]
+        t0 = time.perf_counter()
+        (orc.vdks(Ps, Ts, V) if V else orc.rdks(Ps, Ts))
+        dt = time.perf_counter() - t0
+        best = (n, dt)
+        if dt * 2.2 > budget_s or 2 * n > len(P):
+            break
+        n *= 2
+    n, dt = best
+    return {"value": 2 * n / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} points of each sample ({2 * n} pooled, d={d}), one call, {dt:.2f} s"}
+
+
+def run_approx(args):
+    """vdKS / rdKS: one ddks_vdks / ddks_rdks call per step on device-resident
+    inputs (graph-replayed), then a few steps with stage timing for the
+    roofline of the dominant stage."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2106_13706_gb300 as pkg
+    from paper_2106_13706_gb300 import build as bld
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    bld.build()
+    desc, metric, unit = APPROX[args.workload]
+    P, T, V = approx_inputs(args.workload)
+    NP, d = P.shape
+    NT = T.shape[0]
+    N = NP + NT
+    units = 1.0 if unit == "tests/s" else float(N)
+
+    def call(c, A, B):
+        return c.vdks(A, B, V) if V else c.rdks(A, B)
+
+    Pd, Td = torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device="cuda")
+    ctx = pkg.Context(device=local)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        ref = call(ctx, Pd, Td)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.2)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = ctx.stats()["kernel_launches"]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        r = call(ctx, Pd, Td)
+        ev[s][1].record(stream)
+        if r["num_max"] != ref["num_max"]:
+            raise RuntimeError("result changed between steps")
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = ctx.stats()["kernel_launches"] - l0
+    sampler.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = units * args.steps * world / (total_ms * 1e-3)
+
+    # stages (kernel by kernel while stage timing is on)
+    ctx.set_stage_timing(True)
+    stages = []
+    for _ in range(max(5, min(args.steps, 20))):
+        flush.zero_()
+        call(ctx, Pd, Td)
+        stages.append(ctx.stage_times())
+    ctx.set_stage_timing(False)
+    st = [statistics.mean(x[i] for x in stages) for i in range(3)]
+    peaks = measured_peaks()
+    if V:
+        # dominant: the voxel pass, HBM-bound: reads every coordinate once
+        # and updates the 2 x V^d voxel counters
+        nbytes = N * d * P.itemsize + 8 * V ** d
+        ach = nbytes / (st[1] * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs") or 6800.0
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": "voxel pass (k_vdks_thresholds + k_vdks_voxel)",
+                "kernel_ms": st[1], "algorithmic_bytes": nbytes,
+                "peak_basis": "measured copy bandwidth" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s",
+                "range_stage": {"kernel": "k_minmax", "ms": st[0],
+                                "achieved_gbs": N * d * P.itemsize / (st[0] * 1e-3) / 1e9},
+                "stage_ms": {"range": st[0], "voxel": st[1], "suffix_and_orthants": st[2]}}
+    elif args.workload == "rdks":
+        # dominant: the corner distances, FP64-bound: per point the d + 1
+        # corner sums share the running sum of the first m squares, so
+        # d (d + 1) / 2 + d dependent double adds
+        ops = N * (d * (d + 1) / 2 + d)
+        ach = ops / (st[0] * 1e-3)
+        peak = FP64_NOMINAL_FLOPS / 2
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "FP64 adds/s", "frac": ach / peak,
+                "traffic": None, "kernel": "range + corner distances (k_minmax + k_rdks_dist_warp)",
+                "kernel_ms": st[0], "algorithmic_ops": ops,
+                "peak_basis": "nominal FP64 1.25 TFLOP/s (FMA = 2 FLOP): 6.25e11 adds/s",
+                "stage_ms": {"range_and_distances": st[0], "sort": st[1], "ks_walk": st[2]}}
+    else:
+        # dominant: the sort of the d + 1 distance lists (chunk sort + merge
+        # passes); algorithmic bytes: each 8-byte key read and written once
+        S = d + 1
+        nbytes = S * N * 16
+        ach = nbytes / (st[1] * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs") or 6800.0
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": "sort of the corner distance lists (k_chunk_sort + k_merge_pass)",
+                "kernel_ms": st[1], "algorithmic_bytes": nbytes,
+                "peak_basis": "measured copy bandwidth" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s",
+                "stage_ms": {"range_and_distances": st[0], "sort": st[1], "ks_walk": st[2]}}
+
+    e2e = None
+    if not args.no_e2e:
+        Ph, Th = torch.from_numpy(P).pin_memory(), torch.from_numpy(T).pin_memory()
+        for _ in range(3):
+            call(ctx, Ph, Th)
+        tot = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            r2 = call(ctx, Ph, Th)
+            tot += time.perf_counter() - a
+        if r2["num_max"] != ref["num_max"]:
+            raise RuntimeError("host-input result differs")
+        e2e = {"value": units * args.steps * world / tot, "unit": unit,
+               "h2d_bytes_per_step": int(P.nbytes + T.nbytes),
+               "d2h_bytes_per_step": 3 * 8 + 4 + (0 if V else 8 * (d + 1))}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = approx_cpu(args.workload, P, T, V)
+    clocks = sampler.summary()
+    ctx.close()
+    out = {
+        "metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 normalisation, u32 voxel counts" if V else "f64 distances, u64 keys",
+        "data": "synthetic (seeded numpy PCG64)",
+        "config": {"workload": desc, "N": N, "d": d, "voxels_per_dim": V, "units_per_step": units,
+                   "l2": f"flushed between steps ({args.flush_mb} MB write)", "replicas": world},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "num_max": ref["num_max"], "denom": ref["denom"],
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference_approx(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    desc, metric, unit = APPROX[args.workload]
+    P, T, V = approx_inputs(args.workload)
+    d = P.shape[1]
+    from oracle import oracle as orc
+    # each step: the oracle on a bounded sample (rdks: the whole 200-point test)
+    n = len(P) if args.workload == "rdks" else 50_000
+    Ps, Ts = P[:n], T[:n]
+    for _ in range(max(args.warmup, 0)):
+        (orc.vdks(Ps, Ts, V) if V else orc.rdks(Ps, Ts))
+    tot = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        (orc.vdks(Ps, Ts, V) if V else orc.rdks(Ps, Ts))
+        tot += time.perf_counter() - t0
+    per = 1.0 if unit == "tests/s" else 2.0 * n
+    value = per * args.steps / tot
+    sample = "the full test per step" if args.workload == "rdks" else f"first {n} points of each sample per step"
+    print(json.dumps({
+        "metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot * 1e3 / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded numpy PCG64)",
+        "impl": "reference", "config": {"workload": desc, "N": len(P) + len(T), "d": d, "voxels_per_dim": V},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
 def run_perm(args):
     """Permutation test of the 3-component mixture (2 x 2,000 points, d = 3)
     with B relabellings in one batched launch per step."""
@@ -511,7 +745,12 @@ def run_serve(args):
 def main():
     args = parse()
     if args.impl == "reference":
-        run_reference(args)
+        if args.workload in APPROX:
+            run_reference_approx(args)
+        else:
+            run_reference(args)
+    elif args.workload in APPROX:
+        run_approx(args)
     elif args.workload == "perm":
         run_perm(args)
     elif args.workload == "batch":

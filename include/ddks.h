@@ -46,6 +46,8 @@ extern "C" {
 #endif
 
 #define DDKS_MAX_D 30
+#define DDKS_VDKS_MAX_D 10    /* ddks_vdks: most dimensions */
+#define DDKS_RDKS_MAX_D 4096  /* ddks_rdks: most dimensions */
 
 /* return codes */
 #define DDKS_OK 0
@@ -213,8 +215,11 @@ int ddks_autotune(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64
  * stream around its stages; ddks_stage_times then returns the last call's
  * durations in milliseconds: encode (K0: keys, sort, ranks, and the register
  * path's packing of the points), count (the orthant count kernel), reduce
- * (max over origins).  Enabling it adds event records,
- * never extra synchronisation beyond the call's own.
+ * (max over origins).  For ddks_vdks the three stages are the range
+ * reduction, the voxel pass (thresholds and counts) and the suffix sums with
+ * the orthant evaluation; for ddks_rdks the range reduction with the corner
+ * distances, the sort, and the Kolmogorov-Smirnov walk.  Enabling it adds
+ * event records, never extra synchronisation beyond the call's own.
  */
 int ddks_set_stage_timing(ddks_ctx* ctx, int32_t enable);
 int ddks_stage_times(ddks_ctx* ctx, float* encode_ms, float* count_ms, float* reduce_ms);
@@ -239,6 +244,46 @@ int ddks_stage_times(ddks_ctx* ctx, float* encode_ms, float* count_ms, float* re
  */
 int ddks_distance_noalloc(const void* P, int64_t NP, const void* T, int64_t NT, int32_t d,
                           int32_t dtype, void* stream, ddks_result* out);
+
+/*
+ * vdKS, the voxel approximation of Sec. 2.2 (Alg. vdKS).  NormalizeData
+ * rescales every dimension of the pooled sample to [0, 1] by its minimum and
+ * maximum, x' = (x - lo) / (hi - lo) in IEEE double (0 for a constant
+ * dimension).  Each point falls in voxel c with c_m = floor(x'_m * V)
+ * (x'_m = 1 in voxel V - 1) of the V^d voxels, V = voxels_per_dim; voxel c
+ * holds Diff(c) = nT(c)/NT - nP(c)/NP.  For every voxel filled by either
+ * sample, the 2^d orthants around it split the voxels with the ">=" side
+ * convention of ddKS (voxel c' on the upper side of dimension m iff
+ * c'_m >= c_m), and the statistic is the largest absolute orthant sum of Diff
+ * (Alg. vdKS takes a "max" of the orthant sums: read as the largest |sum|,
+ * as in Eq. d1).  num_max is that sum times NP*NT, an exact integer;
+ * argmax_origin is the lowest filled voxel reaching it (linear index
+ * sum_m c_m V^m) and argmax_orthant its lowest orthant code there.
+ * 1 <= d <= DDKS_VDKS_MAX_D and V^d <= 2^28 (else DDKS_EUNSUPPORTED);
+ * V >= 1.  Coordinates must be finite and every range hi - lo must not
+ * overflow (DDKS_EINVAL); NaN gives DDKS_ENAN.  Conventions as above.
+ */
+int ddks_vdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT, int32_t d,
+              int32_t dtype, int32_t voxels_per_dim, void* stream, ddks_result* out);
+
+/*
+ * rdKS, the radial approximation of Sec. 2.2 (Alg. rdKS).  After the same
+ * NormalizeData rescaling as ddks_vdks, the d + 1 corners are the origin
+ * (corner 0) and the unit vectors e_m (corner m + 1).  For each corner, the
+ * points' squared Euclidean distances to it (the squares of x'_m - corner_m
+ * added in dimension order, each operation rounded in IEEE double) are
+ * compared as two samples by the two-sample Kolmogorov-Smirnov statistic
+ * sup_r |F_P(r) - F_T(r)| with F(r) = #{distance <= r} / n (the merge of the
+ * two sorted lists in Alg. rdKS, read with absolute differences and after
+ * all distances equal to r).  num_max is the largest over corners times
+ * NP*NT; argmax_origin is the lowest corner reaching it, argmax_orthant 0.
+ * per_corner (optional, host or device, d + 1 entries) receives each
+ * corner's numerator.  1 <= d <= DDKS_RDKS_MAX_D (rdKS is linear in d; the
+ * paper runs it at d = 1000, Sec. 4); (NP + NT) * (d + 1) must stay below
+ * about 4e9 (DDKS_EOVERFLOW).  Finite coordinates as for ddks_vdks.
+ */
+int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT, int32_t d,
+              int32_t dtype, void* stream, ddks_result* out, uint64_t* per_corner);
 
 /* Human-readable text for a return code. */
 const char* ddks_strerror(int code);

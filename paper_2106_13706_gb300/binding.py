@@ -21,6 +21,8 @@ DDKS_PENDING = 1
 DDKS_F32, DDKS_F64 = 0, 1
 PATH_AUTO, PATH_REGISTER, PATH_LANE, PATH_WARP, PATH_SORT = 0, 1, 2, 3, 4
 MAX_D = 30
+VDKS_MAX_D = 10
+RDKS_MAX_D = 4096
 
 _lib = None
 _lock = threading.Lock()
@@ -90,6 +92,8 @@ def load():
             "ddks_last_cuda_error": (ctypes.c_char_p, [vp]),
             "ddks_version": (ctypes.c_char_p, []),
             "ddks_distance_noalloc": (i32, [vp, i64, vp, i64, i32, i32, vp, R]),
+            "ddks_vdks": (i32, [vp, vp, i64, vp, i64, i32, i32, i32, vp, R]),
+            "ddks_rdks": (i32, [vp, vp, i64, vp, i64, i32, i32, vp, R, vp]),
             "ddks_autotune": (i32, [vp, vp, i64, vp, i64, i32, i32, vp, ctypes.POINTER(i32),
                                     ctypes.POINTER(ctypes.c_float)]),
             "ddks_set_stage_timing": (i32, [vp, i32]),
@@ -224,6 +228,29 @@ def ddks_distance_range(ctx, P, T, o_begin, o_end, per_origin=False, stream=None
     return out
 
 
+def ddks_vdks(ctx, P, T, voxels_per_dim, stream=None):
+    """Voxel approximation (Alg. vdKS): dict with num_max, denom, D, the
+    arg-max voxel (argmax_origin) and orthant."""
+    p, NP, t, NT, d, dt, keep = _pair(P, T)
+    r = ddks_result()
+    _check(load().ddks_vdks(ctx, p, NP, t, NT, d, dt, int(voxels_per_dim), _stream(stream),
+                            ctypes.byref(r)), ctx)
+    return r.as_dict()
+
+
+def ddks_rdks(ctx, P, T, stream=None):
+    """Radial approximation (Alg. rdKS): dict with num_max, denom, D, the
+    arg-max corner (argmax_origin) and per_corner numerators (d + 1)."""
+    p, NP, t, NT, d, dt, keep = _pair(P, T)
+    r = ddks_result()
+    pc = np.zeros(d + 1, dtype=np.uint64)
+    _check(load().ddks_rdks(ctx, p, NP, t, NT, d, dt, _stream(stream), ctypes.byref(r),
+                            pc.ctypes.data), ctx)
+    out = r.as_dict()
+    out["per_corner"] = pc
+    return out
+
+
 def ddks_permutation_test(ctx, P, T, B, seed, stream=None, want_perm=True):
     p, NP, t, NT, d, dt, keep = _pair(P, T)
     r = ddks_result()
@@ -343,6 +370,12 @@ class Context:
 
     def distance_range(self, P, T, o_begin, o_end, per_origin=False, stream=None):
         return ddks_distance_range(self.h, P, T, o_begin, o_end, per_origin, stream)
+
+    def vdks(self, P, T, voxels_per_dim, stream=None):
+        return ddks_vdks(self.h, P, T, voxels_per_dim, stream)
+
+    def rdks(self, P, T, stream=None):
+        return ddks_rdks(self.h, P, T, stream)
 
     def permutation_test(self, P, T, B, seed, stream=None, want_perm=True):
         return ddks_permutation_test(self.h, P, T, B, seed, stream, want_perm)

@@ -181,7 +181,7 @@ void ddks_stage_mark(ddks_ctx* ctx, int i, cudaStream_t st) {
 }
 static void stage_mark(ddks_ctx* ctx, int i, cudaStream_t st) { ddks_stage_mark(ctx, i, st); }
 
-static void stage_collect(ddks_ctx* ctx) {
+void ddks_stage_collect(ddks_ctx* ctx) {
   if (!ctx->stage_timing) return;
   for (int i = 0; i < 3; ++i) {
     float ms = 0;
@@ -351,7 +351,7 @@ static int distance_impl(ddks_ctx* ctx, const void* P, int64_t NP, const void* T
     e = cudaMemcpyAsync(per_origin, ctx->best.ptr, 8 * (size_t)no, cudaMemcpyDefault, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return out->status = ctx_cuda_fail(ctx, e, "result copy");
-  stage_collect(ctx);
+  ddks_stage_collect(ctx);
   const unsigned flags = (unsigned)(ctx->h_out[4] & 0xFFFFFFFFull);
   if (flags & ddks::kFlagNaN) return out->status = DDKS_ENAN;
   if (flags & ddks::kFlagTimeout) return out->status = DDKS_ETIMEOUT;

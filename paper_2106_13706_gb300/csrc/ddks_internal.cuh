@@ -18,7 +18,9 @@ namespace ddks {
 constexpr int kMaxD = 30;
 
 // error flags raised by kernels and read back by the host
-enum : unsigned { kFlagNaN = 1u, kFlagTimeout = 2u, kFlagBounds = 4u };
+// (kFlagRange: a coordinate range that cannot be rescaled to [0, 1], the
+// normalisation of the vdKS / rdKS approximations)
+enum : unsigned { kFlagNaN = 1u, kFlagTimeout = 2u, kFlagBounds = 4u, kFlagRange = 8u };
 
 // Order-preserving image of a float as an unsigned integer: x <= y (IEEE, no
 // NaN) <=> key(x) <= key(y).  -0.0 is mapped like +0.0 so the two compare equal.
@@ -56,6 +58,10 @@ cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int64_t NP, int d,
                              int* pfx_done, cudaStream_t st, int* launches);
 size_t ddks_rank_pfx_elems(int64_t N);
 size_t ddks_rank_scratch_elems(int64_t N);
+cudaError_t ddks_launch_sort_segments(const uint64_t* keys, int64_t N, int64_t NP, int S, uint64_t* k1,
+                                      uint32_t* i1, uint32_t* p1, uint64_t* k2, uint32_t* i2,
+                                      uint32_t* p2, const uint64_t** out_k, const uint32_t** out_i,
+                                      const uint32_t** out_p, cudaStream_t st, int* launches);
 
 cudaError_t ddks_launch_lane(const uint32_t* rank, int64_t N, int64_t NP, int64_t NT, int d,
                              int64_t o_begin, int64_t o_end, uint64_t* best, int32_t* bestj,

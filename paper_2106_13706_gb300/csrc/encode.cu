@@ -43,11 +43,12 @@ DDKS_DEV bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
 }
 
 // grid: (chunks, d).  Sorts chunk blockIdx.x of dimension blockIdx.y.
-// With out_p (dimension 0 only), also writes out_p[base + t] = #{j < t :
-// sorted element j of the chunk is a P point}.
+// With out_p, dimensions m < pfx_dims also write out_p[m * Npad + base + t] =
+// #{j < t : sorted element j of the chunk is a P point}.
 __global__ void __launch_bounds__(kChunkThreads)
 k_chunk_sort(const uint64_t* __restrict__ keys, int64_t N, int64_t Npad, int64_t NP,
-             uint64_t* __restrict__ out_k, uint32_t* __restrict__ out_i, uint32_t* __restrict__ out_p) {
+             uint64_t* __restrict__ out_k, uint32_t* __restrict__ out_i, uint32_t* __restrict__ out_p,
+             int pfx_dims) {
   extern __shared__ __align__(16) unsigned char smraw[];
   uint64_t* sk = reinterpret_cast<uint64_t*>(smraw);   // [kChunk]
   uint32_t* si = reinterpret_cast<uint32_t*>(sk + kChunk);
@@ -85,7 +86,7 @@ k_chunk_sort(const uint64_t* __restrict__ keys, int64_t N, int64_t Npad, int64_t
     out_k[(int64_t)m * Npad + base + t] = sk[t];
     out_i[(int64_t)m * Npad + base + t] = si[t];
   }
-  if (out_p && m == 0) {
+  if (out_p && m < pfx_dims) {
     // exclusive prefix of the P flags of the sorted chunk: thread t owns
     // elements 2t, 2t+1
     __shared__ uint32_t wsum[kChunkThreads / 32 + 1];
@@ -111,20 +112,21 @@ k_chunk_sort(const uint64_t* __restrict__ keys, int64_t N, int64_t Npad, int64_t
     }
     __syncthreads();
     const uint32_t ex = wsum[warp] + incl - v;
-    uint32_t* P = out_p + base;
+    uint32_t* P = out_p + (int64_t)m * Npad + base;
     P[2 * t] = ex;
     P[2 * t + 1] = ex + f0;
   }
 }
 
 // One merge pass over runs of length L (Npad is a multiple of kChunk <= L).
-// grid-stride over (d * Npad) elements.  With in_p / out_p, dimension 0 also
-// carries each element's count of P points before it within its run: after
-// the merge that is its own count plus the partner run's count below its slot.
+// grid-stride over (d * Npad) elements.  With in_p / out_p, dimensions
+// m < pfx_dims also carry each element's count of P points before it within
+// its run: after the merge that is its own count plus the partner run's count
+// below its slot.
 __global__ void k_merge_pass(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ in_i,
                              uint64_t* __restrict__ out_k, uint32_t* __restrict__ out_i,
                              const uint32_t* __restrict__ in_p, uint32_t* __restrict__ out_p,
-                             int64_t Npad, int64_t NP, int d, int64_t L) {
+                             int64_t Npad, int64_t NP, int d, int64_t L, int pfx_dims) {
   const int64_t total = Npad * d;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -138,7 +140,9 @@ __global__ void k_merge_pass(const uint64_t* __restrict__ in_k, const uint32_t* 
     const int64_t a = p - r * L;
     const int64_t ps = (r ^ 1) * L;  // partner run start
     int64_t dst;
-    uint32_t pc = (in_p && m == 0) ? in_p[p] : 0u;
+    const bool carry = in_p && m < pfx_dims;
+    const uint32_t* Pin = carry ? in_p + m * Npad : nullptr;
+    uint32_t pc = carry ? Pin[p] : 0u;
     if (ps >= Npad) {
       dst = p;
     } else {
@@ -151,13 +155,13 @@ __global__ void k_merge_pass(const uint64_t* __restrict__ in_k, const uint32_t* 
       }
       const int64_t start = (r < (r ^ 1) ? r : (r ^ 1)) * L;
       dst = start + a + lo;
-      if (in_p && m == 0)
-        pc += lo < plen ? in_p[ps + lo]
-                        : in_p[ps + plen - 1] + (I[ps + plen - 1] < (uint64_t)NP ? 1u : 0u);
+      if (carry)
+        pc += lo < plen ? Pin[ps + lo]
+                        : Pin[ps + plen - 1] + (I[ps + plen - 1] < (uint64_t)NP ? 1u : 0u);
     }
     out_k[m * Npad + dst] = key;
     out_i[m * Npad + dst] = idx;
-    if (in_p && m == 0) out_p[dst] = pc;
+    if (carry) out_p[m * Npad + dst] = pc;
   }
 }
 
@@ -303,7 +307,7 @@ cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int64_t NP, int d,
   if (e != cudaSuccess) return e;
   uint32_t* cp = pfx ? cpfx : nullptr;             // [Npad] P prefixes, dimension 0
   uint32_t* cp2 = pfx ? cpfx + Npad : nullptr;     // [Npad] the other merge buffer
-  k_chunk_sort<<<g, kChunkThreads, smem, st>>>(keys, N, Npad, NP, tmp_keys, tmp_idx, cp);
+  k_chunk_sort<<<g, kChunkThreads, smem, st>>>(keys, N, Npad, NP, tmp_keys, tmp_idx, cp, 1);
   int n = 1;
   if (chunks <= kMaxMultiChunks) {
     k_rank_multi<<<grid_for(N * d, 256), 256, 0, st>>>(keys, tmp_keys, tmp_idx, cp, N, NP, Npad, d, rank,
@@ -314,7 +318,7 @@ cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int64_t NP, int d,
   uint64_t *ck = tmp_keys, *nk = tmp_keys2;
   uint32_t *ci = tmp_idx, *ni = tmp_idx2;
   for (int64_t L = kChunk; L < Npad; L <<= 1) {
-    k_merge_pass<<<grid_for(Npad * d, 256), 256, 0, st>>>(ck, ci, nk, ni, cp, cp2, Npad, NP, d, L);
+    k_merge_pass<<<grid_for(Npad * d, 256), 256, 0, st>>>(ck, ci, nk, ni, cp, cp2, Npad, NP, d, L, 1);
     ++n;
     uint64_t* tk = ck; ck = nk; nk = tk;
     uint32_t* ti = ci; ci = ni; ni = ti;
@@ -326,6 +330,39 @@ cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int64_t NP, int d,
     k_copy_idx<<<grid_for(N, 256), 256, 0, st>>>(ci, cp, N, sorted_idx0, pfx ? pprefix0 : nullptr);
     ++n;
   }
+  if (launches) *launches += n;
+  return cudaGetLastError();
+}
+
+// Sort S segments of N keys each ([S][N]; ties broken by the pooled index) and
+// carry, for every segment, the count of P points (index < NP) before each
+// sorted position.  Buffers hold S * ddks_rank_scratch_elems(N) elements each
+// (k1/k2 keys, i1/i2 indices, p1/p2 prefixes); *out_k, *out_i, *out_p point at
+// the ones holding the result, laid out [S][Npad] with positions >= N padding.
+cudaError_t ddks_launch_sort_segments(const uint64_t* keys, int64_t N, int64_t NP, int S, uint64_t* k1,
+                                      uint32_t* i1, uint32_t* p1, uint64_t* k2, uint32_t* i2,
+                                      uint32_t* p2, const uint64_t** out_k, const uint32_t** out_i,
+                                      const uint32_t** out_p, cudaStream_t st, int* launches) {
+  const int64_t Npad = (int64_t)ddks_rank_scratch_elems(N);
+  const int64_t chunks = Npad / kChunk;
+  const size_t smem = (size_t)kChunk * 12;
+  cudaError_t e = cudaFuncSetAttribute(k_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_chunk_sort<<<dim3((unsigned)chunks, (unsigned)S), kChunkThreads, smem, st>>>(keys, N, Npad, NP, k1, i1,
+                                                                                  p1, S);
+  int n = 1;
+  uint64_t *ck = k1, *nk = k2;
+  uint32_t *ci = i1, *ni = i2, *cp = p1, *np = p2;
+  for (int64_t L = kChunk; L < Npad; L <<= 1) {
+    k_merge_pass<<<grid_for(Npad * S, 256), 256, 0, st>>>(ck, ci, nk, ni, cp, np, Npad, NP, S, L, S);
+    ++n;
+    uint64_t* tk = ck; ck = nk; nk = tk;
+    uint32_t* ti = ci; ci = ni; ni = ti;
+    uint32_t* tp = cp; cp = np; np = tp;
+  }
+  *out_k = ck;
+  *out_i = ci;
+  *out_p = cp;
   if (launches) *launches += n;
   return cudaGetLastError();
 }

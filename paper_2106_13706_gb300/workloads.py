@@ -82,6 +82,17 @@ def mixture_pair(seed=0, n_p=2000, n_t=2000, d=3, shift=0.0, sigma=0.5, dtype=np
     return P.astype(dtype), T.astype(dtype)
 
 
+def dvu_pair(seed=0, n_p=100, n_t=100, d=1000, dtype=np.float32):
+    """Diagonal versus uniform (Sec. 4.1): P uniform on the diagonal of the
+    unit cube (every coordinate of a point equal to one U[0,1] draw), T
+    uniform in [0,1]^d."""
+    rng = np.random.default_rng(seed)
+    u = rng.random(n_p)
+    P = np.repeat(u[:, None], d, axis=1)
+    T = rng.random((n_t, d))
+    return P.astype(dtype), T.astype(dtype)
+
+
 def log_uniform_int(rng, lo, hi, size=None):
     """Integers log-uniform in [lo, hi]."""
     v = np.exp(rng.uniform(math.log(lo), math.log(hi + 1), size=size))

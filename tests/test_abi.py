@@ -19,7 +19,8 @@ def test_header_declares_the_boundary():
     names = pkg.declared_symbols()
     for n in ["ddks_ctx_create", "ddks_ctx_destroy", "ddks_distance", "ddks_distance_range",
               "ddks_permutation_test", "ddks_significance", "ddks_batch_distance", "ddks_submit",
-              "ddks_poll", "ddks_strerror", "ddks_ctx_stats", "ddks_config_default"]:
+              "ddks_poll", "ddks_strerror", "ddks_ctx_stats", "ddks_config_default", "ddks_vdks",
+              "ddks_rdks"]:
         assert n in names
 
 
@@ -40,6 +41,8 @@ def test_argument_errors_need_no_gpu(lib):
     r = pkg.binding.ddks_result()
     assert lib.ddks_distance(None, None, 1, None, 1, 3, 0, None, ctypes.byref(r)) == -1
     assert lib.ddks_ctx_destroy(None) == -1
+    assert lib.ddks_vdks(None, None, 1, None, 1, 3, 0, 8, None, ctypes.byref(r)) == -1
+    assert lib.ddks_rdks(None, None, 1, None, 1, 3, 0, None, ctypes.byref(r), None) == -1
 
 
 def test_library_is_in_tree():
