@@ -424,7 +424,11 @@ int oracle_num_threads(void) {
  *     nT * NP - nP * NT per voxel.
  *   - rdKS IdentifyCorners: the d + 1 corners are the origin and the d unit
  *     vectors of the normalised space; distances are Euclidean, compared as
- *     squared distances summed in dimension order (no fused multiply-add).
+ *     squared distances.  rdKS is linear in d (Sec. 2.2, Sec. 4), so a
+ *     point's squared distances come from its squared norm
+ *     s = x'_0^2 + ... + x'_{d-1}^2 (added in dimension order): s itself for
+ *     the origin and (s - 2 x'_m) + 1 for the unit vector e_m, each operation
+ *     rounded in IEEE double (no fused multiply-add).
  *   - rdKS GetDFromCornerLists: the two-sample Kolmogorov-Smirnov statistic
  *     of the two sorted distance lists, sup_r |F_P(r) - F_T(r)| with
  *     F(r) = #{distance <= r} / n, i.e. evaluated after all distances equal
@@ -536,24 +540,35 @@ int oracle_rdks(const void* P, int64_t NP, const void* T, int64_t NT, int d, int
   if (!num_max) return ORC_EINVAL;
   const int64_t N = NP + NT;
   double* xn = (double*)malloc(sizeof(double) * (size_t)(N * d));
+  double* norm2 = (double*)malloc(sizeof(double) * (size_t)N);
   orc_dist* list = (orc_dist*)malloc(sizeof(orc_dist) * (size_t)N);
-  if (!xn || !list) { free(xn); free(list); return ORC_ENOMEM; }
+  if (!xn || !norm2 || !list) { free(xn); free(norm2); free(list); return ORC_ENOMEM; }
   if (normalise(P, NP, T, NT, d, is_f64, xn) != ORC_OK) {
-    free(xn); free(list);
+    free(xn); free(norm2); free(list);
     return ORC_EINVAL;
   }
   uint64_t best = 0;
+  /* squared norms in the normalised space, added in dimension order */
+  for (int64_t i = 0; i < N; ++i) {
+    double s = 0.0;
+    for (int m = 0; m < d; ++m) {
+      const double x = xn[i * d + m];
+      const double sq = x * x;
+      s = s + sq;
+    }
+    norm2[i] = s;
+  }
   for (int corner = 0; corner <= d; ++corner) {
-    /* corner 0: the origin; corner m + 1: unit vector m */
+    /* corner 0: the origin, |x'|^2; corner m + 1: unit vector m,
+       |x' - e_m|^2 = (|x'|^2 - 2 x'_m) + 1 */
     for (int64_t i = 0; i < N; ++i) {
-      double s = 0.0;
-      for (int m = 0; m < d; ++m) {
-        const double c = (corner == m + 1) ? 1.0 : 0.0;
-        const double t = xn[i * d + m] - c;
-        const double sq = t * t;
-        s = s + sq;
+      double r = norm2[i];
+      if (corner > 0) {
+        const double x = xn[i * d + corner - 1];
+        const double t = r - 2.0 * x;
+        r = t + 1.0;
       }
-      list[i].r = s;
+      list[i].r = r;
       list[i].is_t = i >= NP;
     }
     qsort(list, (size_t)N, sizeof(orc_dist), cmp_dist);
@@ -570,6 +585,6 @@ int oracle_rdks(const void* P, int64_t NP, const void* T, int64_t NT, int d, int
     if (cb > best) best = cb;
   }
   *num_max = best;
-  free(xn); free(list);
+  free(xn); free(norm2); free(list);
   return ORC_OK;
 }

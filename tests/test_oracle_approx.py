@@ -189,8 +189,8 @@ APPROX_MUTATIONS = [
     ("vdks_swapped_weights", "diff[idx] += i < NP ? -(int64_t)NT : (int64_t)NP;",
      "diff[idx] += i < NP ? -(int64_t)NP : (int64_t)NT;"),
     ("rdks_inside_ties", "if (i + 1 < N && list[i + 1].r == list[i].r) continue;", ""),
-    ("rdks_wrong_corner", "const double c = (corner == m + 1) ? 1.0 : 0.0;",
-     "const double c = (corner == m) ? 1.0 : 0.0;"),
+    ("rdks_wrong_corner", "const double x = xn[i * d + corner - 1];", "const double x = xn[i * d + corner % d];"),
+    ("rdks_wrong_expansion", "const double t = r - 2.0 * x;", "const double t = r - x;"),
     ("rdks_unnormalised", "out[i * d + m] = span > 0.0 ? (v - lo) / span : 0.0;", "out[i * d + m] = v;"),
 ]
 
