@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["cfg2", "cfg1", "cfg3", "perm", "batch", "serve", "vdks", "rdks",
-                                           "rdks_large"], default="cfg2")
+                                           "rdks_large", "dom2d"], default="cfg2")
     ap.add_argument("--perms", type=int, default=1000)
     ap.add_argument("--requests", type=int, default=600)
     ap.add_argument("--path", type=int, default=0, help="force a kernel path (0 = auto)")
@@ -64,7 +64,6 @@ APPROX = {
     "rdks_large": ("rdKS (Alg. rdKS) d=3 NP=NT=1,000,000 f32, P ~ N(0,I3), T ~ N(0.05*1,I3)",
                    "rdks_points_per_s", "points/s"),
 }
-FP64_NOMINAL_FLOPS = 1.25e12  # GB300 FP64, FMA counted as 2 FLOP
 
 
 def approx_inputs(name):
@@ -476,28 +475,21 @@ def run_approx(args):
                 "range_stage": {"kernel": "k_minmax", "ms": st[0],
                                 "achieved_gbs": N * d * P.itemsize / (st[0] * 1e-3) / 1e9},
                 "stage_ms": {"range": st[0], "voxel": st[1], "suffix_and_orthants": st[2]}}
-    elif args.workload == "rdks":
-        # dominant: the corner distances, FP64-bound: per point the d + 1
-        # corner sums share the running sum of the first m squares, so
-        # d (d + 1) / 2 + d dependent double adds
-        ops = N * (d * (d + 1) / 2 + d)
-        ach = ops / (st[0] * 1e-3)
-        peak = FP64_NOMINAL_FLOPS / 2
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "FP64 adds/s", "frac": ach / peak,
-                "traffic": None, "kernel": "range + corner distances (k_minmax + k_rdks_dist_warp)",
-                "kernel_ms": st[0], "algorithmic_ops": ops,
-                "peak_basis": "nominal FP64 1.25 TFLOP/s (FMA = 2 FLOP): 6.25e11 adds/s",
-                "stage_ms": {"range_and_distances": st[0], "sort": st[1], "ks_walk": st[2]}}
     else:
-        # dominant: the sort of the d + 1 distance lists (chunk sort + merge
-        # passes); algorithmic bytes: each 8-byte key read and written once
+        # rdKS stages: range + corner distances (reads the coordinates, writes
+        # one 8-byte key per point and corner), the sort of the d + 1 lists
+        # (algorithmic: each key read and written once), the KS walk.  The
+        # roofline is taken on the slowest stage, all HBM-bound.
         S = d + 1
-        nbytes = S * N * 16
-        ach = nbytes / (st[1] * 1e-3) / 1e9
+        stage_bytes = [N * d * P.itemsize + S * N * 8, S * N * 16, S * N * 16]
+        names = ["range + corner distances (k_minmax + k_rdks_dist_*)",
+                 "sort of the corner distance lists (k_chunk_sort + k_merge_tile)",
+                 "KS walk (k_rdks_walk + k_rdks_final)"]
+        k = max(range(3), key=lambda i: st[i])
+        ach = stage_bytes[k] / (st[k] * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs") or 6800.0
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": None, "kernel": "sort of the corner distance lists (k_chunk_sort + k_merge_pass)",
-                "kernel_ms": st[1], "algorithmic_bytes": nbytes,
+                "traffic": None, "kernel": names[k], "kernel_ms": st[k], "algorithmic_bytes": stage_bytes[k],
                 "peak_basis": "measured copy bandwidth" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s",
                 "stage_ms": {"range_and_distances": st[0], "sort": st[1], "ks_walk": st[2]}}
 
@@ -540,6 +532,35 @@ def run_approx(args):
         dist.destroy_process_group()
 
 
+def run_reference_dom2d(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    from paper_2106_13706_gb300 import workloads as wl
+    P, T = wl.gaussian_pair(0, 1_000_000, 1_000_000, 2, shift=0.05)
+    N = len(P) + len(T)
+    no = 1000  # origins per step, all points per origin
+    nthr = orc.num_threads()
+    for _ in range(max(args.warmup, 0)):
+        orc.ddks(P, T, origins=(0, 100), nthreads=nthr)
+    tot = 0.0
+    for s_ in range(args.steps):
+        a = (s_ * no) % N
+        t0 = time.perf_counter()
+        orc.ddks(P, T, origins=(a, a + no), nthreads=nthr)
+        tot += time.perf_counter() - t0
+    value = no * args.steps / tot
+    print(json.dumps({
+        "metric": "ddks_d2_points_per_s", "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot * 1e3 / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 compares", "data": "synthetic (seeded numpy PCG64)",
+        "impl": "reference", "config": {"workload": DOM2D, "N": N, "d": 2},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": nthr, "kind": "oracle",
+                         "sample": f"{no} origins per step by the O(N^2) definition, scaled to the whole test"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
 def run_reference_approx(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -568,6 +589,105 @@ def run_reference_approx(args):
         "impl": "reference", "config": {"workload": desc, "N": len(P) + len(T), "d": d, "voxels_per_dim": V},
         "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+DOM2D = ("exact ddKS d=2 NP=NT=1,000,000 f32, P ~ N(0,I2), T ~ N(0.05*1,I2), range-query path "
+         "(O(N log N), no pairwise compares)")
+
+
+def run_dom2d(args):
+    """Exact d = 2 statistic by the range-query path (a separate metric: it
+    skips the pairwise compares).  One ddks_distance call per step on
+    device-resident inputs."""
+    import torch
+
+    import paper_2106_13706_gb300 as pkg
+    from paper_2106_13706_gb300 import build as bld
+    from paper_2106_13706_gb300 import workloads as wl
+    bld.build()
+    P, T = wl.gaussian_pair(0, 1_000_000, 1_000_000, 2, shift=0.05)
+    N, d = len(P) + len(T), 2
+    Pd, Td = torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device="cuda")
+    ctx = pkg.Context(device=0, path=pkg.PATH_DOMINANCE)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        ref = ctx.distance(Pd, Td)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.2)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = ctx.stats()["kernel_launches"]
+    torch.cuda.synchronize()
+    for s_ in range(args.steps):
+        flush.zero_()
+        ev[s_][0].record(stream)
+        r = ctx.distance(Pd, Td)
+        ev[s_][1].record(stream)
+        if r["num_max"] != ref["num_max"]:
+            raise RuntimeError("result changed between steps")
+    torch.cuda.synchronize()
+    launches = ctx.stats()["kernel_launches"] - l0
+    sampler.stop()
+    tot = sum(a.elapsed_time(b) for a, b in ev)
+    ctx.set_stage_timing(True)
+    stages = []
+    for _ in range(5):
+        flush.zero_()
+        ctx.distance(Pd, Td)
+        stages.append(ctx.stage_times())
+    ctx.set_stage_timing(False)
+    st = [statistics.mean(x[i] for x in stages) for i in range(3)]
+    # the range queries: per origin three wavelet-matrix walks of L levels,
+    # two 8-byte rank lookups (prefix word + bit word) per level
+    L = max(1, (N - 1).bit_length())
+    nbytes = N * 3 * L * 2 * 8
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs") or 6800.0
+    ach = nbytes / (st[1] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+            "kernel": "matrix build + range queries (k_dom_bits/scatter/query)", "kernel_ms": st[1],
+            "algorithmic_bytes": nbytes,
+            "peak_basis": "measured copy bandwidth" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s",
+            "note": "the lookups are random 8-byte reads of L2-resident bit vectors; HBM is the reference only",
+            "stage_ms": {"encode": st[0], "count": st[1], "reduce": st[2]}}
+    e2e = None
+    if not args.no_e2e:
+        Ph, Th = torch.from_numpy(P).pin_memory(), torch.from_numpy(T).pin_memory()
+        for _ in range(3):
+            ctx.distance(Ph, Th)
+        t_e = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            r2 = ctx.distance(Ph, Th)
+            t_e += time.perf_counter() - a
+        assert r2["num_max"] == ref["num_max"]
+        e2e = {"value": N * args.steps / t_e, "unit": "points/s", "h2d_bytes_per_step": int(P.nbytes + T.nbytes),
+               "d2h_bytes_per_step": 3 * 8 + 4}
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as orc
+        no = 2000
+        t0 = time.perf_counter()
+        orc.ddks(P, T, origins=(0, no), nthreads=orc.num_threads())
+        dt = time.perf_counter() - t0
+        cpu = {"value": no / dt, "unit": "points/s", "cores": orc.num_threads(), "kind": "oracle",
+               "sample": f"origins [0,{no}) of {N} by the O(N^2) definition ({dt:.2f} s), scaled to the whole "
+                         "test: N / (time x N / origins)"}
+    clocks = sampler.summary()
+    ctx.close()
+    ms = tot / args.steps
+    print(json.dumps({
+        "metric": "ddks_d2_points_per_s", "value": N / (ms * 1e-3), "unit": "points/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 ranks (f32 input)", "data": "synthetic (seeded numpy PCG64)",
+        "config": {"workload": DOM2D, "N": N, "d": d, "l2": f"flushed between steps ({args.flush_mb} MB write)",
+                   "equivalent_compares_per_s": float(N) * N * d / (ms * 1e-3)},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "num_max": ref["num_max"], "denom": ref["denom"]}))
 
 
 def run_perm(args):
@@ -747,10 +867,14 @@ def main():
     if args.impl == "reference":
         if args.workload in APPROX:
             run_reference_approx(args)
+        elif args.workload == "dom2d":
+            run_reference_dom2d(args)
         else:
             run_reference(args)
     elif args.workload in APPROX:
         run_approx(args)
+    elif args.workload == "dom2d":
+        run_dom2d(args)
     elif args.workload == "perm":
         run_perm(args)
     elif args.workload == "batch":

@@ -66,10 +66,11 @@ typedef enum { DDKS_F32 = 0, DDKS_F64 = 1 } ddks_dtype;
 /* kernel paths for the orthant counts (DDKS_PATH_AUTO lets the autotuner pick) */
 typedef enum {
   DDKS_PATH_AUTO = 0,
-  DDKS_PATH_REGISTER = 1,  /* register-resident packed counters, SWAR compares (d <= 4) */
+  DDKS_PATH_REGISTER = 1,  /* bit-sliced compares, register counters (d = 2..4) */
   DDKS_PATH_LANE = 2,      /* lane-private shared-memory histograms (d <= 8) */
   DDKS_PATH_WARP = 3,      /* one shared-memory histogram per warp and origin (d <= 13) */
-  DDKS_PATH_SORT = 4       /* per-origin sort of codes and segmented counts (any d) */
+  DDKS_PATH_SORT = 4,      /* per-origin sort of codes and segmented counts (any d) */
+  DDKS_PATH_DOMINANCE = 5  /* d = 2 only: quadrant counts by range queries, O(N log N) work */
 } ddks_path;
 
 typedef struct {
@@ -199,9 +200,10 @@ int ddks_ctx_stats(ddks_ctx* ctx, ddks_stats* out);
 
 /*
  * Autotune the orthant-count kernel for this problem shape: every kernel path
- * and launch shape that can take it (register path built for 2, 3 or 4
- * resident CTAs per SM; lane-private histograms with 64, 128 or 256 threads
- * per CTA; per-warp histograms; the sort path) runs on these inputs, timed
+ * and launch shape that can take it (the bit-sliced register path built for 8,
+ * 12 or 16 resident CTAs per SM; lane-private histograms with 64, 128 or 256
+ * threads per CTA; per-warp histograms; the sort path; for d = 2 the
+ * range-query path) runs on these inputs, timed
  * with CUDA events on stream; all must produce the same statistic.  The
  * fastest is kept for the shape's class (d, log2 NP, log2 NT) in the context
  * and written to the tune cache file when one is configured; later calls with
@@ -270,12 +272,14 @@ int ddks_vdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
  * rdKS, the radial approximation of Sec. 2.2 (Alg. rdKS).  After the same
  * NormalizeData rescaling as ddks_vdks, the d + 1 corners are the origin
  * (corner 0) and the unit vectors e_m (corner m + 1).  For each corner, the
- * points' squared Euclidean distances to it (the squares of x'_m - corner_m
- * added in dimension order, each operation rounded in IEEE double) are
- * compared as two samples by the two-sample Kolmogorov-Smirnov statistic
+ * points' squared Euclidean distances to it are compared as two samples by
+ * the two-sample Kolmogorov-Smirnov statistic
  * sup_r |F_P(r) - F_T(r)| with F(r) = #{distance <= r} / n (the merge of the
  * two sorted lists in Alg. rdKS, read with absolute differences and after
- * all distances equal to r).  num_max is the largest over corners times
+ * all distances equal to r).  The squared distance of a point is its
+ * squared norm s (the squares of x'_m added in dimension order) for the
+ * origin and (s - 2 x'_m) + 1 for e_m, each operation rounded in IEEE double,
+ * which keeps a point's work linear in d.  num_max is the largest over corners times
  * NP*NT; argmax_origin is the lowest corner reaching it, argmax_orthant 0.
  * per_corner (optional, host or device, d + 1 entries) receives each
  * corner's numerator.  1 <= d <= DDKS_RDKS_MAX_D (rdKS is linear in d; the

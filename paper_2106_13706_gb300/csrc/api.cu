@@ -102,7 +102,7 @@ int ddks_ctx_create(const ddks_config* cfg, ddks_ctx** out) {
   ddks_ctx* ctx = new (std::nothrow) ddks_ctx();
   if (!ctx) return DDKS_ENOMEM;
   if (cfg) ctx->cfg = *cfg; else ddks_config_default(&ctx->cfg);
-  if (ctx->cfg.path < DDKS_PATH_AUTO || ctx->cfg.path > DDKS_PATH_SORT) { delete ctx; return DDKS_EINVAL; }
+  if (ctx->cfg.path < DDKS_PATH_AUTO || ctx->cfg.path > DDKS_PATH_DOMINANCE) { delete ctx; return DDKS_EINVAL; }
   if (ctx->cfg.hbm_budget_bytes == 0) ctx->cfg.hbm_budget_bytes = 8ull << 30;
   if (ctx->cfg.max_batch <= 0) ctx->cfg.max_batch = 64;
   if (ctx->cfg.wait_limit_ms <= 0) ctx->cfg.wait_limit_ms = 10000;
@@ -291,6 +291,13 @@ int ddks_count_origins_plan(ddks_ctx* ctx, const ddks_plan& plan, int64_t NP, in
       e = ddks_launch_sort(rank, N, NP, NT, d, ob, oe, best, bestj, st);
       ctx->launches += 1;
       break;
+    case DDKS_PATH_DOMINANCE: {
+      if (!ctx->pfx0_valid) return DDKS_EUNSUPPORTED;  // needs K0's dimension-0 order and P prefix
+      int n = 0;
+      e = ddks_launch_dominance(ctx, rank, N, NP, NT, ob, oe, best, bestj, st, &n);
+      ctx->launches += n;
+      break;
+    }
     default:
       return DDKS_EUNSUPPORTED;
   }
@@ -322,7 +329,8 @@ static int distance_impl(ddks_ctx* ctx, const void* P, int64_t NP, const void* T
   rc = ddks_graph_run(ctx, key.h, st, [&](cudaStream_t s) -> int {
     int r;
     stage_mark(ctx, 0, s);
-    if ((r = ddks_encode_problem(ctx, dP, NP, dT, NT, d, dtype, s, plan.path == DDKS_PATH_REGISTER)))
+    if ((r = ddks_encode_problem(ctx, dP, NP, dT, NT, d, dtype, s,
+                                 plan.path == DDKS_PATH_REGISTER || plan.path == DDKS_PATH_DOMINANCE)))
       return r;
     stage_mark(ctx, 1, s);
     if ((r = ctx->best.reserve(ctx, 8 * (size_t)(no > 0 ? no : 1)))) return r;

@@ -15,7 +15,7 @@
 //                    exact thresholds (k_vdks_thresholds) by integer key
 //                    compares instead of a double divide per coordinate: FP64
 //                    runs at a small fraction of the integer rate on this GPU.
-//   k_vdks_suffix*   d passes of suffix sums: U(c) = sum over the voxels c' with
+//   k_vdks_suffix    d passes of suffix sums: U(c) = sum over the voxels c' with
 //                    c'_m >= c_m in every dimension of nT*NP - nP*NT (the first
 //                    pass forms the differences from the counts)
 //   k_vdks_eval      at every filled voxel c: F(A) = U(c with the coordinates
@@ -28,10 +28,10 @@
 //                    voxel and then the lowest orthant; the last CTA reduces
 //                    the CTAs' partial results.
 // rdKS
-//   k_rdks_dist_*    squared distance of each point to each corner, summed in
-//                    dimension order; corner 0 is the origin, corner m + 1 the
-//                    unit vector of dimension m.  The running sum over the
-//                    first m terms is shared by corner m + 1.
+//   k_rdks_dist_*    squared distance of each point to each corner: corner 0
+//                    (the origin) is the squared norm s (squares added in
+//                    dimension order), corner m + 1 (the unit vector of
+//                    dimension m) is (s - 2 x'_m) + 1, so a point costs O(d)
 //   sort             the K0 chunk sort and merge passes over the d + 1 corner
 //                    segments, carrying the P count before each position
 //   k_rdks_walk      at the last position of every run of equal distances:
@@ -43,6 +43,7 @@
 #include <cstring>
 
 #include "../../include/ddks.h"
+#include "bulk_copy.cuh"
 #include "ddks_internal.cuh"
 #include "ddks_host.h"
 
@@ -54,6 +55,7 @@ constexpr int kVdksMaxD = DDKS_VDKS_MAX_D;
 constexpr int kRdksThreadMaxD = 16;  // up to here one thread computes all corners of a point
 constexpr uint64_t kVdksMaxCells = 1ull << 28;
 constexpr int64_t kVdksMaxThresholds = 4096;  // d * (V - 1) keys staged in shared memory
+constexpr size_t kVdksMaxHistSmem = 200 * 1024;   // private histogram + thresholds per CTA
 
 // Inverse of ddks::order_key for doubles (-0.0 comes back as +0.0).
 DDKS_DEV double key_value(ull k) {
@@ -73,14 +75,24 @@ DDKS_DEV const V* point_row(const V* P, const V* T, int64_t NP, int d, int64_t i
 // Order keys in the input type's own width: u32 for float, u64 for double
 // (ddks::order_key's mapping, -0.0 like +0.0), and back.
 template <typename V> struct NativeKey;
+// raw(v) is the same map without the -0.0 fix (-0.0 just below +0.0): NaNs
+// land outside [raw(-inf), raw(+inf)].
 template <> struct NativeKey<float> {
   using K = uint32_t;
   static DDKS_DEV K key(float v) { return (K)ddks::order_key(v); }
+  static DDKS_DEV K raw(float v) {
+    const uint32_t u = __float_as_uint(v);
+    return (u >> 31) ? ~u : (u | 0x80000000u);
+  }
   static DDKS_DEV float value(K k) { return __uint_as_float((k >> 31) ? (k & 0x7FFFFFFFu) : ~k); }
 };
 template <> struct NativeKey<double> {
   using K = ull;
   static DDKS_DEV K key(double v) { return (K)ddks::order_key(v); }
+  static DDKS_DEV K raw(double v) {
+    const ull u = (ull)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+  }
   static DDKS_DEV double value(K k) { return key_value(k); }
 };
 
@@ -126,43 +138,84 @@ DDKS_DEV void block_best(ull& n, long long& c, int& j) {
 
 // Per-dimension minimum and maximum of the pooled sample (the range
 // NormalizeData rescales by), reduced as order keys of the input type and
-// stored as order keys of doubles.  Thread tid reads elements tid, tid + S,
-// ... of the pooled row-major array, S a multiple of d, so all of them lie in
-// dimension tid mod d.  gmin / gmax start at ~0 / 0.  NaN and infinite
-// coordinates raise kFlagNaN / kFlagRange.
+// stored as order keys of doubles (an all-zero dimension may come back as
+// -0.0, which rescales every coordinate the same way as +0.0).  Each thread
+// reads 16-byte vectors of VEC
+// consecutive elements at t0, t0 + S, ... of P's and then T's row-major
+// array, S a multiple of both d and VEC, so element j of its vectors always
+// lies in dimension (t0 + j) mod d.  gmin / gmax start at ~0 / 0.  NaN and
+// infinite coordinates raise kFlagNaN / kFlagRange, found from each CTA's
+// extreme keys.
 template <typename V>
 __global__ void __launch_bounds__(kThreads)
-k_minmax(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64_t NT, int d,
+k_minmax(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64_t NT, int d, int64_t S,
          ull* __restrict__ gmin, ull* __restrict__ gmax, unsigned* __restrict__ flags) {
   using NK = NativeKey<V>;
   using K = typename NK::K;
+  constexpr int VEC = 16 / (int)sizeof(V);
   extern __shared__ __align__(16) unsigned char smm_raw[];
   K* smin = reinterpret_cast<K*>(smm_raw);  // [2][d]
   K* smax = smin + d;
   for (int m = threadIdx.x; m < d; m += blockDim.x) { smin[m] = ~(K)0; smax[m] = (K)0; }
   __syncthreads();
-  const int64_t nP = NP * d, total = (NP + NT) * d;
-  const int64_t S = ((int64_t)gridDim.x * blockDim.x / d) * d;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid < S && tid < total) {
-    K lo = ~(K)0, hi = (K)0;
-    unsigned bad = 0;
-    for (int64_t e = tid; e < total; e += S) {
-      const V v = e < nP ? P[e] : T[e - nP];
-      if (v != v) bad |= ddks::kFlagNaN;
-      else if (isinf(v)) bad |= ddks::kFlagRange;
-      const K k = NK::key(v);
-      lo = k < lo ? k : lo;
-      hi = k > hi ? k : hi;
+  const int64_t t0 = (int64_t)VEC * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (t0 < S) {
+    K lo[VEC], hi[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) { lo[j] = ~(K)0; hi[j] = (K)0; }
+    for (int a = 0; a < 2; ++a) {
+      const V* X = a ? T : P;
+      const int64_t n = (a ? NT : NP) * d;
+      const bool vec_ok = ((uintptr_t)X & 15) == 0;
+      constexpr int B = 4;  // vectors whose loads are issued together
+      for (int64_t e0 = t0; e0 < n; e0 += (int64_t)B * S) {
+        V v[B][VEC];
+        int cnt[B];  // elements of each vector inside the array
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+          const int64_t e = e0 + (int64_t)u * S;
+          cnt[u] = e >= n ? 0 : (n - e < VEC ? (int)(n - e) : VEC);
+          if (vec_ok && cnt[u] == VEC) {
+            if constexpr (VEC == 4) {
+              const float4 q = *reinterpret_cast<const float4*>(X + e);
+              v[u][0] = q.x; v[u][1] = q.y; v[u][2] = q.z; v[u][3] = q.w;
+            } else {
+              const double2 q = *reinterpret_cast<const double2*>(X + e);
+              v[u][0] = q.x; v[u][1] = q.y;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) v[u][j] = j < cnt[u] ? X[e + j] : (V)0;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) {
+            if (j >= cnt[u]) continue;
+            const K k = NK::raw(v[u][j]);
+            lo[j] = k < lo[j] ? k : lo[j];
+            hi[j] = k > hi[j] ? k : hi[j];
+          }
+        }
+      }
     }
-    const int m = (int)(tid % d);
-    atomicMin(&smin[m], lo);
-    atomicMax(&smax[m], hi);
-    if (bad) atomicOr(flags, bad);
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      if (lo[j] != ~(K)0) {  // element j of some vector was seen
+        const int m = (int)((t0 + j) % d);
+        atomicMin(&smin[m], lo[j]);
+        atomicMax(&smax[m], hi[j]);
+      }
+    }
   }
   __syncthreads();
+  // NaN keys lie outside [raw(-inf), raw(+inf)]; infinities at its ends
+  const K kninf = NK::raw(-__int_as_float(0x7f800000)), kpinf = NK::raw(__int_as_float(0x7f800000));
   for (int m = threadIdx.x; m < d; m += blockDim.x)
     if (smin[m] != ~(K)0) {
+      if (smin[m] < kninf || smax[m] > kpinf) atomicOr(flags, ddks::kFlagNaN);
+      else if (smin[m] == kninf || smax[m] == kpinf) atomicOr(flags, ddks::kFlagRange);
       atomicMin(&gmin[m], (ull)ddks::order_key((double)NK::value(smin[m])));
       atomicMax(&gmax[m], (ull)ddks::order_key((double)NK::value(smax[m])));
     }
@@ -181,10 +234,10 @@ DDKS_DEV void check_spans(const ull* gmin, const ull* gmax, int d, unsigned* fla
 // m is a non-decreasing step function of its value (every operation of the
 // rescaling is monotone), so it equals the number of thresholds t_k <= v,
 // t_k = the least value of the input type with coordinate >= k, k = 1..V-1.
-// Thread (m, k) finds t_k by bisection over the input type's order keys in
-// [key(lo), key(hi)] with the exact double arithmetic of voxel_coord;
-// thr[m * (V - 1) + k - 1] = key(t_k), or ~0 (never reached) for a constant
-// dimension.
+// Warp (m, k) finds t_k by a 32-way search over the input type's order keys
+// in [key(lo), key(hi)], each lane evaluating voxel_coord (the exact double
+// arithmetic) at one probe per round; thr[m * (V - 1) + k - 1] = key(t_k),
+// or ~0 (never reached) for a constant dimension.
 template <typename V>
 __global__ void __launch_bounds__(kThreads)
 k_vdks_thresholds(const ull* __restrict__ gmin, const ull* __restrict__ gmax, int d, int Vd,
@@ -192,26 +245,107 @@ k_vdks_thresholds(const ull* __restrict__ gmin, const ull* __restrict__ gmax, in
   using NK = NativeKey<V>;
   using K = typename NK::K;
   const int per = Vd - 1;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);  // warp-uniform
   if (t >= d * per) return;
   const int m = t / per, k = t - m * per + 1;
   const double lo = key_value(gmin[m]), hi = key_value(gmax[m]);
   const double span = __dsub_rn(hi, lo);
   K res = ~(K)0;
   if (span > 0.0 && !isinf(span)) {
-    K a = NK::key((V)lo), b = NK::key((V)hi);  // the coordinate of hi is V - 1 >= k
+    // invariant: the answer is in [a, b] and the coordinate of b is >= k
+    K a = NK::key((V)lo), b = NK::key((V)hi);
     while (a < b) {
-      const K mid = a + (b - a) / 2;
-      if (voxel_coord((double)NK::value(mid), lo, span, Vd) >= k) b = mid; else a = mid + 1;
+      const K step = (b - a) / 32 + 1;
+      const K c = a + (K)lane * step;
+      const bool pr = c >= b || voxel_coord((double)NK::value(c), lo, span, Vd) >= k;
+      const unsigned bal = __ballot_sync(0xffffffffu, pr);
+      const int f = __ffs(bal) - 1;
+      if (f < 0) {
+        a = a + (K)31 * step + 1;
+      } else if (f == 0) {
+        b = a;
+      } else {
+        const K cf = a + (K)f * step;
+        a = a + (K)(f - 1) * step + 1;
+        b = cf < b ? cf : b;
+      }
     }
     res = a;
   }
-  thr[t] = res;
+  if (lane == 0) thr[t] = res;
+}
+
+// Thresholds staged in shared memory: per dimension V + 1 slots, slot k
+// (1 <= k <= V - 1) holding t_k and sentinels below (slot 0) and above
+// (slot V).  Float inputs keep the threshold values (compared as floats,
+// -0.0 == +0.0), double inputs their order keys.
+template <typename V> struct StagedThr { using T = typename NativeKey<V>::K; };
+template <> struct StagedThr<float> { using T = float; };
+
+template <typename V>
+DDKS_DEV void stage_thresholds(typename StagedThr<V>::T* sthr, const typename NativeKey<V>::K* thr, int d, int Vd) {
+  using S = typename StagedThr<V>::T;
+  const int per = Vd - 1, w = Vd + 1;
+  for (int t = threadIdx.x; t < d * w; t += blockDim.x) {
+    const int m = t / w, k = t - m * w;
+    S v;
+    if constexpr (sizeof(V) == 4) {
+      v = k == 0 ? -__int_as_float(0x7f800000) : (k == Vd ? __int_as_float(0x7f800000)
+                                                         : NativeKey<float>::value(thr[m * per + k - 1]));
+    } else {
+      v = k == 0 ? (S)0 : (k == Vd ? ~(S)0 : thr[m * per + k - 1]);
+    }
+    sthr[t] = v;
+  }
+}
+
+// Voxel index sum_m c_m V^m of a point row: from the staged thresholds, or
+// from the double rescaling.  DM = d when d <= 4, else an upper bound.
+// Float inputs: a single-precision estimate of the coordinate is within one
+// of the exact one (its relative error is below 2^-22 and V <= 4096 here), so
+// one compare with each neighbouring threshold gives the exact count
+// #{k : t_k <= v}.  Double inputs (whose float estimate can be far off) walk
+// from the estimate to the count by order-key compares.
+template <typename V, int DM>
+DDKS_DEV uint32_t voxel_index(const V* row, int d, int Vd, const typename StagedThr<V>::T* sthr, bool use_thr,
+                              const double* slo, const double* sspan, const float* flo, const float* fsc) {
+  using NK = NativeKey<V>;
+  using K = typename NK::K;
+  constexpr bool exact = DM <= 4;
+  const int per = Vd - 1, w = Vd + 1;
+  uint32_t idx = 0, stride = 1;
+#pragma unroll
+  for (int m = 0; m < DM; ++m) {
+    if (exact || m < d) {
+      int c;
+      if (use_thr) {
+        const V v = row[m];
+        const float e = fminf(fmaxf(((float)v - flo[m]) * fsc[m], 0.0f), (float)per);
+        const int c0 = (int)e;
+        const typename StagedThr<V>::T* tm = sthr + m * w;
+        if constexpr (sizeof(V) == 4) {
+          c = c0 + (v >= tm[c0 + 1] ? 1 : 0) - (v < tm[c0] ? 1 : 0);
+          c = c < 0 ? 0 : (c > per ? per : c);
+        } else {
+          const K kv = NK::key(v);
+          c = c0;
+          while (c < per && tm[c + 1] <= kv) ++c;
+          while (c > 0 && tm[c] > kv) --c;
+        }
+      } else {
+        c = voxel_coord((double)row[m], slo[m], sspan[m], Vd);
+      }
+      idx += (uint32_t)c * stride;
+      stride *= (uint32_t)Vd;
+    }
+  }
+  return idx;
 }
 
 // Voxel of every pooled point; cnt[2 * voxel + (point is in T)] += 1.
-// use_thr: coordinates from the thresholds (staged in shared memory, a binary
-// search of integer keys per dimension); else from the double rescaling.
+// use_thr: coordinates from the thresholds (staged in shared memory); else
+// from the double rescaling.
 template <typename V>
 __global__ void __launch_bounds__(kThreads)
 k_vdks_voxel(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64_t NT, int d, int Vd,
@@ -221,16 +355,20 @@ k_vdks_voxel(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64
   using NK = NativeKey<V>;
   using K = typename NK::K;
   extern __shared__ __align__(16) unsigned char vox_raw[];
-  K* sthr = reinterpret_cast<K*>(vox_raw);  // [d][V - 1] on the threshold path
+  using SK = typename StagedThr<V>::T;
+  SK* sthr = reinterpret_cast<SK*>(vox_raw);  // [d][V + 1] on the threshold path
   __shared__ double slo[kVdksMaxD], sspan[kVdksMaxD];
+  __shared__ float flo[kVdksMaxD], fsc[kVdksMaxD];
   const int per = Vd - 1;
   if (threadIdx.x < d) {
     const double lo = key_value(gmin[threadIdx.x]);
+    const double sp = __dsub_rn(key_value(gmax[threadIdx.x]), lo);
     slo[threadIdx.x] = lo;
-    sspan[threadIdx.x] = __dsub_rn(key_value(gmax[threadIdx.x]), lo);
+    sspan[threadIdx.x] = sp;
+    flo[threadIdx.x] = (float)lo;
+    fsc[threadIdx.x] = sp > 0.0 ? (float)((double)Vd / sp) : 0.0f;
   }
-  if (use_thr)
-    for (int t = threadIdx.x; t < d * per; t += blockDim.x) sthr[t] = thr[t];
+  if (use_thr) stage_thresholds<V>(sthr, thr, d, Vd);
   check_spans(gmin, gmax, d, flags);
   __syncthreads();
   const int64_t N = NP + NT;
@@ -243,74 +381,224 @@ k_vdks_voxel(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64
     uint32_t key = 0xFFFFFFFFu;
     if (i < N) {
       const V* row = point_row(P, T, NP, d, i);
-      uint32_t idx = 0, stride = 1;
-#pragma unroll
-      for (int m = 0; m < kVdksMaxD; ++m) {
-        if (m < d) {
-          int c;
-          if (use_thr) {
-            const K kv = NK::key(row[m]);
-            const K* tm = sthr + m * per;
-            int a = 0, z = per;
-            while (a < z) {
-              const int mid = (a + z) >> 1;
-              if (tm[mid] <= kv) a = mid + 1; else z = mid;
-            }
-            c = a;
-          } else {
-            c = voxel_coord((double)row[m], slo[m], sspan[m], Vd);
-          }
-          idx += (uint32_t)c * stride;
-          stride *= (uint32_t)Vd;
-        }
-      }
-      key = 2u * idx + (i >= NP ? 1u : 0u);
+      key = 2u * voxel_index<V, kVdksMaxD>(row, d, Vd, sthr, use_thr != 0, slo, sspan, flo, fsc) +
+            (i >= NP ? 1u : 0u);
     }
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     if (i < N && lane == __ffs(peers) - 1) atomicAdd(&cnt[key], (uint32_t)__popc(peers));
   }
 }
 
-// Suffix sums along dimension 0 (lines of Vd consecutive voxels), one warp
-// per line, forming the differences nT*NP - nP*NT from the counts.
+constexpr int kVoxThreads = 512;
+
+// Voxel counts in a CTA-private shared-memory histogram: CTAs [0, bP) take
+// equal slices of P, the others of T.  Each CTA writes its whole histogram
+// (zeros included) to hist_all[blockIdx.x][cells]; k_vdks_gather sums them.
+// U points per thread per round, their loads issued together; DM >= d.
+template <typename V, int U, int DM>
+__global__ void __launch_bounds__(kVoxThreads)
+k_vdks_voxel_smem(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64_t NT, int d, int Vd,
+                  const ull* __restrict__ gmin, const ull* __restrict__ gmax,
+                  const typename NativeKey<V>::K* __restrict__ thr, int use_thr, uint32_t cells, int bP,
+                  uint32_t* __restrict__ hist_all, unsigned* __restrict__ flags) {
+  using K = typename NativeKey<V>::K;
+  extern __shared__ __align__(16) unsigned char vs_raw[];
+  uint32_t* hist = reinterpret_cast<uint32_t*>(vs_raw);
+  using SK = typename StagedThr<V>::T;
+  SK* sthr = reinterpret_cast<SK*>(vs_raw + (((size_t)cells * 4 + 15) & ~(size_t)15));
+  __shared__ double slo[kVdksMaxD], sspan[kVdksMaxD];
+  __shared__ float flo[kVdksMaxD], fsc[kVdksMaxD];
+  const int per = Vd - 1;
+  for (uint32_t c = threadIdx.x; c < cells; c += blockDim.x) hist[c] = 0u;
+  if (threadIdx.x < d) {
+    const double lo = key_value(gmin[threadIdx.x]);
+    const double sp = __dsub_rn(key_value(gmax[threadIdx.x]), lo);
+    slo[threadIdx.x] = lo;
+    sspan[threadIdx.x] = sp;
+    flo[threadIdx.x] = (float)lo;
+    fsc[threadIdx.x] = sp > 0.0 ? (float)((double)Vd / sp) : 0.0f;
+  }
+  if (use_thr) stage_thresholds<V>(sthr, thr, d, Vd);
+  check_spans(gmin, gmax, d, flags);
+  __syncthreads();
+  const bool isT = (int)blockIdx.x >= bP;
+  const V* X = isT ? T : P;
+  const int64_t n = isT ? NT : NP;
+  const int nb = isT ? (int)gridDim.x - bP : bP;
+  const int b = isT ? (int)blockIdx.x - bP : (int)blockIdx.x;
+  const int64_t beg = n * b / nb, end = n * (b + 1) / nb;
+  for (int64_t i0 = beg + threadIdx.x; i0 < end; i0 += (int64_t)U * blockDim.x) {
+    V v[U][DM];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + (int64_t)u * blockDim.x;
+#pragma unroll
+      for (int m = 0; m < DM; ++m)
+        v[u][m] = (m < d && i < end) ? X[i * d + m] : (V)0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (i0 + (int64_t)u * blockDim.x < end)
+        atomicAdd(&hist[voxel_index<V, DM>(v[u], d, Vd, sthr, use_thr != 0, slo, sspan, flo, fsc)], 1u);
+    }
+  }
+  __syncthreads();
+  uint32_t* out = hist_all + (size_t)blockIdx.x * cells;
+  for (uint32_t c = threadIdx.x; c < cells; c += blockDim.x) out[c] = hist[c];
+}
+
+constexpr int kVoxStages = 3;                    // bulk-copy ring depth
+constexpr int kVoxBulkThreads = 1024;
+constexpr size_t kVoxMaxDynSmem = 227 * 1024 - 1024;  // dynamic shared memory of one CTA
+
+// The same counts with the CTA's rows streamed into shared memory by bulk
+// asynchronous copies: a ring of kVoxStages chunks of rc rows, so that two
+// chunks are in flight while one is counted.  CTA boundaries and rc are
+// multiples of r0 rows (r0 rows = a multiple of 16 bytes; the sample bases
+// are 16-byte aligned), so every copy starts and ends on 16 bytes; rows past
+// the last such boundary (fewer than r0, at the sample's end) are read
+// directly.  A wait that runs out (1 s) sets kFlagTimeout, waits (bounded)
+// for the CTA's copies still in flight and returns without its counts.
+// Shared memory: hist [cells] u32 at 0, thresholds at thr_off, stages at
+// stage_off (stage_bytes each).
+template <typename V, int DM>
+__global__ void __launch_bounds__(kVoxBulkThreads)
+k_vdks_voxel_bulk(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64_t NT, int d, int Vd,
+                  const ull* __restrict__ gmin, const ull* __restrict__ gmax,
+                  const typename NativeKey<V>::K* __restrict__ thr, int use_thr, uint32_t cells, int bP, int r0,
+                  int rc, uint32_t thr_off, uint32_t stage_off, uint32_t stage_bytes,
+                  uint32_t* __restrict__ hist_all, unsigned* __restrict__ flags) {
+  namespace bk = ddks::bulk;
+  using K = typename NativeKey<V>::K;
+  extern __shared__ __align__(16) unsigned char vb_raw[];
+  __shared__ __align__(8) unsigned long long bars[kVoxStages];
+  uint32_t* hist = reinterpret_cast<uint32_t*>(vb_raw);
+  using SK = typename StagedThr<V>::T;
+  SK* sthr = reinterpret_cast<SK*>(vb_raw + thr_off);
+  __shared__ double slo[kVdksMaxD], sspan[kVdksMaxD];
+  __shared__ float flo[kVdksMaxD], fsc[kVdksMaxD];
+  const int tid = threadIdx.x;
+  const int per = Vd - 1;
+  for (uint32_t c = tid; c < cells; c += blockDim.x) hist[c] = 0u;
+  if (tid < d) {
+    const double lo = key_value(gmin[tid]);
+    const double sp = __dsub_rn(key_value(gmax[tid]), lo);
+    slo[tid] = lo;
+    sspan[tid] = sp;
+    flo[tid] = (float)lo;
+    fsc[tid] = sp > 0.0 ? (float)((double)Vd / sp) : 0.0f;
+  }
+  if (use_thr) stage_thresholds<V>(sthr, thr, d, Vd);
+  check_spans(gmin, gmax, d, flags);
+  const uint32_t bar_s = (uint32_t)__cvta_generic_to_shared(bars);
+  const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(vb_raw + stage_off);
+  if (tid == 0) {
+    for (int k = 0; k < kVoxStages; ++k) bk::mbar_init(bar_s + 8u * k, 1);
+    bk::mbar_init_fence();
+  }
+  __syncthreads();
+  const bool isT = (int)blockIdx.x >= bP;
+  const V* X = isT ? T : P;
+  const int64_t n = isT ? NT : NP;
+  const int nb = isT ? (int)gridDim.x - bP : bP;
+  const int b = isT ? (int)blockIdx.x - bP : (int)blockIdx.x;
+  const int64_t beg = (n * b / nb) / r0 * r0;
+  const int64_t end = b + 1 >= nb ? n : (n * (b + 1) / nb) / r0 * r0;
+  const int64_t end_al = beg + (end - beg) / r0 * r0;
+  const int64_t nrows = end_al - beg;
+  const int nch = (int)((nrows + rc - 1) / rc);
+  // chunks run from the end of the slice backwards: the range pass just read
+  // the arrays forwards, so their ends are the likeliest to be still in L2
+  auto chunk_row = [&](int c) -> int64_t { return beg + (int64_t)(nch - 1 - c) * rc; };
+  auto issue = [&](int c) {  // thread 0: chunk c into stage c % kVoxStages
+    const int64_t r = chunk_row(c);
+    const int64_t cnt = end_al - r < rc ? end_al - r : rc;
+    const uint32_t bar = bar_s + 8u * (uint32_t)(c % kVoxStages);
+    bk::fence_async();
+    bk::mbar_expect(bar, (uint32_t)(cnt * d * (int64_t)sizeof(V)));
+    bk::load(stage_s + (uint32_t)(c % kVoxStages) * stage_bytes, X + r * d, (uint32_t)(cnt * d * (int64_t)sizeof(V)),
+             bar);
+  };
+  if (tid == 0)
+    for (int c = 0; c < kVoxStages - 1 && c < nch; ++c) issue(c);
+  for (int c = 0; c < nch; ++c) {
+    // stage (c - 1) % kVoxStages was released by the barrier that ended chunk c - 1
+    if (tid == 0 && c + kVoxStages - 1 < nch) issue(c + kVoxStages - 1);
+    const bool ok = bk::wait(bar_s + 8u * (uint32_t)(c % kVoxStages), (uint32_t)((c / kVoxStages) & 1));
+    if (ok) {
+      const int64_t r = chunk_row(c);
+      const int cnt = (int)(end_al - r < rc ? end_al - r : rc);
+      const V* st = reinterpret_cast<const V*>(vb_raw + stage_off + (size_t)(c % kVoxStages) * stage_bytes);
+      for (int q = tid; q < cnt; q += blockDim.x)
+        atomicAdd(&hist[voxel_index<V, DM>(st + (size_t)q * d, d, Vd, sthr, use_thr != 0, slo, sspan, flo, fsc)],
+                  1u);
+    }
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(flags, ddks::kFlagTimeout);
+        // copies of chunks c .. c + kVoxStages - 2 may still be in flight
+        for (int k = c; k < c + kVoxStages - 1 && k < nch; ++k)
+          bk::wait(bar_s + 8u * (uint32_t)(k % kVoxStages), (uint32_t)((k / kVoxStages) & 1));
+      }
+      return;
+    }
+  }
+  for (int64_t i = end_al + tid; i < end; i += blockDim.x)
+    atomicAdd(&hist[voxel_index<V, DM>(X + i * d, d, Vd, sthr, use_thr != 0, slo, sspan, flo, fsc)], 1u);
+  __syncthreads();
+  uint32_t* out = hist_all + (size_t)blockIdx.x * cells;
+  for (uint32_t c = tid; c < cells; c += blockDim.x) out[c] = hist[c];
+}
+
+// cnt[2c] = sum of the P CTAs' counts of voxel c, cnt[2c + 1] the T CTAs'.
+// CTA of 32 voxels x 8 groups of slices (threadIdx.y), reduced in shared memory.
 __global__ void __launch_bounds__(kThreads)
-k_vdks_suffix0(const uint32_t* __restrict__ cnt, long long* __restrict__ U, uint32_t lines, int Vd,
-               long long NP, long long NT) {
+k_vdks_gather(const uint32_t* __restrict__ hist_all, uint32_t cells, int bP, int nb, uint32_t* __restrict__ cnt) {
+  __shared__ uint32_t sa[8][32], st[8][32];
+  const uint32_t c = blockIdx.x * 32 + threadIdx.x;
+  const int g = threadIdx.y;
+  uint32_t a = 0, t = 0;
+  if (c < cells) {
+    for (int b = g; b < nb; b += 8) {
+      const uint32_t v = hist_all[(size_t)b * cells + c];
+      if (b < bP) a += v; else t += v;
+    }
+  }
+  sa[g][threadIdx.x] = a;
+  st[g][threadIdx.x] = t;
+  __syncthreads();
+  if (g == 0 && c < cells) {
+    for (int k = 1; k < 8; ++k) { a += sa[k][threadIdx.x]; t += st[k][threadIdx.x]; }
+    cnt[2 * c] = a;
+    cnt[2 * c + 1] = t;
+  }
+}
+
+// Suffix sums along one dimension: voxel lines of Vd elements at stride
+// `inner` (= Vd^m for dimension m), one warp per line scanning 32 elements
+// at a time from the top end.  With cnt (the pass of dimension 0) the line
+// values are first formed from the counts, nT*NP - nP*NT.
+__global__ void __launch_bounds__(kThreads)
+k_vdks_suffix(const uint32_t* __restrict__ cnt, long long* __restrict__ U, uint32_t lines, int Vd,
+              uint32_t inner, long long NP, long long NT) {
   const int lane = threadIdx.x & 31;
   const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t l = w0; l < lines; l += nw) {
-    const uint64_t base = (uint64_t)l * Vd;
+    const uint32_t lo = l % inner, hi = l / inner;
+    const uint64_t base = (uint64_t)hi * inner * (uint64_t)Vd + lo;
     long long carry = 0;
     for (int j0 = Vd - 32; j0 > -32; j0 -= 32) {
       const int j = j0 + lane;
+      const uint64_t a = base + (uint64_t)(j >= 0 ? j : 0) * inner;
       long long v = 0;
-      if (j >= 0) {
-        const uint64_t a = base + (uint64_t)j;
-        v = (long long)cnt[2 * a + 1] * NP - (long long)cnt[2 * a] * NT;
-      }
+      if (j >= 0) v = cnt ? (long long)cnt[2 * a + 1] * NP - (long long)cnt[2 * a] * NT : U[a];
       for (int off = 1; off < 32; off <<= 1) {
         const long long o = __shfl_down_sync(0xffffffffu, v, off);
         if (lane + off < 32) v += o;
       }
       v += carry;
-      if (j >= 0) U[base + (uint64_t)j] = v;
+      if (j >= 0) U[a] = v;
       carry = __shfl_sync(0xffffffffu, v, 0);
-    }
-  }
-}
-
-// Suffix sums along a dimension with stride `inner` (= Vd^m, m >= 1), one
-// thread per line.
-__global__ void __launch_bounds__(kThreads)
-k_vdks_suffix(long long* __restrict__ U, uint32_t lines, int Vd, uint32_t inner) {
-  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < lines; l += gridDim.x * blockDim.x) {
-    const uint32_t lo = l % inner, hi = l / inner;
-    const uint64_t base = (uint64_t)hi * inner * (uint64_t)Vd + lo;
-    long long acc = 0;
-    for (int j = Vd - 1; j >= 0; --j) {
-      const uint64_t a = base + (uint64_t)j * inner;
-      acc += U[a];
-      U[a] = acc;
     }
   }
 }
@@ -413,7 +701,13 @@ k_vdks_eval(const long long* __restrict__ U, const uint32_t* __restrict__ cnt, u
 
 // ------------------------------------------------------------------ rdKS
 
-DDKS_DEV ull dist_key(double s) { return (ull)__double_as_longlong(s); }  // s >= +0: bits are ordered
+// Squared distances are ordered through ddks::order_key (a rounded
+// (s - 2x) + 1 can be a little below zero; -0.0 keys like +0.0).
+DDKS_DEV ull dist_key(double r) { return (ull)ddks::order_key(r); }
+
+// |x' - e_m|^2 from the squared norm s: (s - 2 x'_m) + 1, rounded twice
+// (2 x'_m is exact).
+DDKS_DEV double corner_dist(double s, double x) { return __dadd_rn(__dsub_rn(s, __dmul_rn(2.0, x)), 1.0); }
 
 // One thread per point, all d + 1 corners (d <= kRdksThreadMaxD).
 template <typename V>
@@ -432,45 +726,34 @@ k_rdks_dist_thread(const V* __restrict__ P, const V* __restrict__ T, int64_t NP,
   const int64_t N = NP + NT;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const V* row = point_row(P, T, NP, d, i);
-    double x[kRdksThreadMaxD], q[kRdksThreadMaxD];
+    double x[kRdksThreadMaxD];
+    double s = 0.0;  // squared norm, added in dimension order
 #pragma unroll
     for (int m = 0; m < kRdksThreadMaxD; ++m) {
       x[m] = 0.0;
-      q[m] = 0.0;
       if (m < d) {
         x[m] = rescale((double)row[m], slo[m], sspan[m]);
-        q[m] = __dmul_rn(x[m], x[m]);
+        s = __dadd_rn(s, __dmul_rn(x[m], x[m]));
       }
     }
-    double pre = 0.0;  // sum of q[0..m) in dimension order
+    keys[i] = dist_key(s);
 #pragma unroll
-    for (int m = 0; m < kRdksThreadMaxD; ++m) {
-      if (m < d) {
-        const double t = __dsub_rn(x[m], 1.0);
-        double s = __dadd_rn(pre, __dmul_rn(t, t));
-#pragma unroll
-        for (int mm = m + 1; mm < kRdksThreadMaxD; ++mm)
-          if (mm < d) s = __dadd_rn(s, q[mm]);
-        keys[(int64_t)(m + 1) * N + i] = dist_key(s);
-        pre = __dadd_rn(pre, q[m]);
-      }
-    }
-    keys[i] = dist_key(pre);
+    for (int m = 0; m < kRdksThreadMaxD; ++m)
+      if (m < d) keys[(int64_t)(m + 1) * N + i] = dist_key(corner_dist(s, x[m]));
   }
 }
 
-// One warp per point (any d): lanes rescale and square the coordinates into
-// shared memory, lane 0 forms the running sums, lanes take one corner each.
+// Any d: one warp per point.  Lanes rescale coordinates into shared memory,
+// lane 0 adds the squares in dimension order, lanes then write the corners.
 template <typename V>
 __global__ void __launch_bounds__(kThreads)
 k_rdks_dist_warp(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64_t NT, int d,
                  const ull* __restrict__ gmin, const ull* __restrict__ gmax, ull* __restrict__ keys,
                  unsigned* __restrict__ flags) {
-  extern __shared__ double sd[];  // per warp: x'[d], x'^2[d], running sums[d]
+  extern __shared__ double sd[];  // per warp: x'[d], x'^2[d]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwb = blockDim.x >> 5;
-  double* xs = sd + (size_t)w * 3 * d;
+  double* xs = sd + (size_t)w * 2 * d;
   double* q = xs + d;
-  double* pre = q + d;
   check_spans(gmin, gmax, d, flags);
   const int64_t N = NP + NT;
   for (int64_t i = (int64_t)blockIdx.x * nwb + w; i < N; i += (int64_t)gridDim.x * nwb) {
@@ -482,21 +765,21 @@ k_rdks_dist_warp(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, i
       q[m] = __dmul_rn(x, x);
     }
     __syncwarp();
-    if (lane == 0) {
-      double s = 0.0;
-      for (int m = 0; m < d; ++m) {
-        pre[m] = s;
-        s = __dadd_rn(s, q[m]);
+    double s = 0.0;
+    if (lane == 0) {  // in dimension order; loads run ahead of the dependent adds
+      int m = 0;
+      for (; m + 8 <= d; m += 8) {
+        double t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = q[m + u];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s = __dadd_rn(s, t[u]);
       }
+      for (; m < d; ++m) s = __dadd_rn(s, q[m]);
       keys[i] = dist_key(s);
     }
-    __syncwarp();
-    for (int m = lane; m < d; m += 32) {
-      const double t = __dsub_rn(xs[m], 1.0);
-      double s = __dadd_rn(pre[m], __dmul_rn(t, t));
-      for (int mm = m + 1; mm < d; ++mm) s = __dadd_rn(s, q[mm]);
-      keys[(int64_t)(m + 1) * N + i] = dist_key(s);
-    }
+    s = __shfl_sync(0xffffffffu, s, 0);
+    for (int m = lane; m < d; m += 32) keys[(int64_t)(m + 1) * N + i] = dist_key(corner_dist(s, xs[m]));
     __syncwarp();
   }
 }
@@ -523,6 +806,85 @@ k_rdks_walk(const ull* __restrict__ K, const uint32_t* __restrict__ I, const uin
     best = o > best ? o : best;
   }
   if ((threadIdx.x & 31) == 0 && best) atomicMax(per_corner + s, best);
+}
+
+// Small samples (N <= 1024): one warp per corner sorts the corner's (key,
+// index) pairs in registers -- lane l holds positions l*E .. l*E+E-1 of the
+// 32*E >= N padded list; bitonic stages of stride < E stay in the lane,
+// larger strides pair lane l with l ^ (stride / E) by shuffles -- then walks
+// the sorted list (P counts by a warp scan) and writes the corner's maximum.
+template <int E>
+__global__ void __launch_bounds__(kThreads)
+k_rdks_small(const ull* __restrict__ keys, int N, int64_t NP, int64_t NT, int S, ull* __restrict__ per_corner) {
+  constexpr int n = 32 * E;
+  const int lane = threadIdx.x & 31;
+  const int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);  // warp-uniform
+  if (s >= S) return;
+  ull k[E];
+  uint32_t ix[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int p = lane * E + j;
+    k[j] = p < N ? keys[(int64_t)s * N + p] : ~0ull;  // pads sort last
+    ix[j] = (uint32_t)p;
+  }
+  for (int size = 2; size <= n; size <<= 1) {
+    int stride = size >> 1;
+    for (; stride >= E; stride >>= 1) {
+      const int xm = stride / E;
+      const bool lower = (lane & xm) == 0;
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const ull ok = __shfl_xor_sync(0xffffffffu, k[j], xm);
+        const uint32_t oi = __shfl_xor_sync(0xffffffffu, ix[j], xm);
+        const bool asc = ((lane * E + j) & size) == 0;
+        const bool less = k[j] < ok || (k[j] == ok && ix[j] < oi);
+        if ((lower == asc) != less) { k[j] = ok; ix[j] = oi; }
+      }
+    }
+#pragma unroll
+    for (int sd = E / 2; sd >= 1; sd >>= 1) {
+      if (sd > stride) continue;
+#pragma unroll
+      for (int a = 0; a < E; ++a) {
+        if (a & sd) continue;
+        const int b = a | sd;
+        const bool asc = ((lane * E + a) & size) == 0;
+        const bool bl = k[b] < k[a] || (k[b] == k[a] && ix[b] < ix[a]);
+        if (asc == bl) {
+          const ull tk = k[a]; k[a] = k[b]; k[b] = tk;
+          const uint32_t ti = ix[a]; ix[a] = ix[b]; ix[b] = ti;
+        }
+      }
+    }
+  }
+  // P points before each position: lane totals, then an exclusive warp scan
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int j = 0; j < E; ++j) cnt += ix[j] < (uint64_t)NP ? 1u : 0u;
+  uint32_t incl = cnt;
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += x;
+  }
+  uint32_t cp = incl - cnt;
+  const ull next0 = __shfl_down_sync(0xffffffffu, k[0], 1);  // first key of the next lane
+  ull best = 0;
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int p = lane * E + j;
+    cp += ix[j] < (uint64_t)NP ? 1u : 0u;
+    const ull nk = j + 1 < E ? k[j + 1 < E ? j + 1 : j] : next0;
+    if (p < N && (p == N - 1 || nk != k[j])) {
+      const ull v = ddks::numer(cp, (uint64_t)(p + 1) - cp, (uint64_t)NP, (uint64_t)NT);
+      best = v > best ? v : best;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const ull o = __shfl_down_sync(0xffffffffu, best, off);
+    best = o > best ? o : best;
+  }
+  if (lane == 0) per_corner[s] = best;
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -563,23 +925,91 @@ int map_flags(ddks_ctx* ctx, unsigned flags) {
   (void)ctx;
   if (flags & ddks::kFlagNaN) return DDKS_ENAN;
   if (flags & ddks::kFlagRange) return DDKS_EINVAL;
+  if (flags & ddks::kFlagTimeout) return DDKS_ETIMEOUT;
   return DDKS_OK;
 }
 
 template <typename V>
 cudaError_t launch_minmax(const void* P, const void* T, int64_t NP, int64_t NT, int d, ull* gmin, ull* gmax,
                           unsigned* flags, int num_sms, cudaStream_t st) {
+  constexpr int VEC = 16 / (int)sizeof(V);
   const int64_t total = (NP + NT) * d;
-  int g = grid_cap(total, kThreads, num_sms * 8);
-  const int need = (d + kThreads - 1) / kThreads;  // at least d threads
+  const int64_t L = (d % VEC == 0) ? d : (d % 2 == 0 && VEC == 4 ? 2 * (int64_t)d : (int64_t)VEC * d);  // lcm(VEC, d)
+  int g = grid_cap((total + VEC - 1) / VEC, kThreads, num_sms * 8);
+  const int need = (int)((L + (int64_t)VEC * kThreads - 1) / ((int64_t)VEC * kThreads));  // S >= L
   if (g < need) g = need;
+  const int64_t S = ((int64_t)g * kThreads * VEC / L) * L;
   const size_t smem = 2 * sizeof(typename NativeKey<V>::K) * (size_t)d;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_minmax<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_minmax<V><<<g, kThreads, smem, st>>>((const V*)P, (const V*)T, NP, NT, d, gmin, gmax, flags);
+  k_minmax<V><<<g, kThreads, smem, st>>>((const V*)P, (const V*)T, NP, NT, d, S, gmin, gmax, flags);
   return cudaGetLastError();
+}
+
+template <typename V>
+cudaError_t launch_voxel_smem(const void* P, const void* T, int64_t NP, int64_t NT, int d, int Vd, const ull* gmin,
+                              const ull* gmax, const void* thr, bool use_thr, uint32_t cells, int bP, int nb,
+                              uint32_t* hall, unsigned* flags, size_t smem, cudaStream_t st) {
+  using K = typename NativeKey<V>::K;
+  constexpr int U4 = sizeof(V) == 4 ? 4 : 2;
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<nb, kVoxThreads, smem, st>>>((const V*)P, (const V*)T, NP, NT, d, Vd, gmin, gmax, (const K*)thr,
+                                       use_thr ? 1 : 0, cells, bP, hall, flags);
+    return cudaGetLastError();
+  };
+  if (d == 1) return go(k_vdks_voxel_smem<V, U4, 1>);
+  if (d == 2) return go(k_vdks_voxel_smem<V, U4, 2>);
+  if (d == 3) return go(k_vdks_voxel_smem<V, U4, 3>);
+  if (d == 4) return go(k_vdks_voxel_smem<V, U4, 4>);
+  return go(k_vdks_voxel_smem<V, 1, kVdksMaxD>);
+}
+
+// Shared-memory plan of k_vdks_voxel_bulk; false when it does not fit.
+struct BulkPlan {
+  int r0 = 0, rc = 0;
+  uint32_t thr_off = 0, stage_off = 0, stage_bytes = 0;
+  size_t smem = 0;
+};
+bool plan_voxel_bulk(uint32_t cells, int d, size_t ks, int64_t nthr, size_t es, BulkPlan* bp) {
+  const size_t rowb = (size_t)d * es;
+  size_t g = 16, a = rowb;  // r0 = 16 / gcd(16, row bytes)
+  while (a) { const size_t t = g % a; g = a; a = t; }
+  bp->r0 = (int)(16 / g);
+  bp->thr_off = (uint32_t)(((size_t)cells * 4 + 15) & ~(size_t)15);
+  bp->stage_off = (uint32_t)((bp->thr_off + ks * (size_t)nthr + 15) & ~(size_t)15);
+  if (bp->stage_off >= kVoxMaxDynSmem) return false;
+  size_t ch = (kVoxMaxDynSmem - bp->stage_off) / kVoxStages;
+  if (ch > 32 * 1024) ch = 32 * 1024;
+  const size_t unit = (size_t)bp->r0 * rowb;  // a multiple of 16
+  bp->rc = (int)(ch / unit) * bp->r0;
+  if (bp->rc < bp->r0 || bp->rc * rowb < 4096) return false;
+  bp->stage_bytes = (uint32_t)((size_t)bp->rc * rowb);
+  bp->smem = bp->stage_off + (size_t)kVoxStages * bp->stage_bytes;
+  return bp->smem <= kVoxMaxDynSmem;
+}
+
+template <typename V>
+cudaError_t launch_voxel_bulk(const void* P, const void* T, int64_t NP, int64_t NT, int d, int Vd, const ull* gmin,
+                              const ull* gmax, const void* thr, bool use_thr, uint32_t cells, int bP, int nb,
+                              uint32_t* hall, unsigned* flags, const BulkPlan& bp, cudaStream_t st) {
+  using K = typename NativeKey<V>::K;
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bp.smem);
+    if (e != cudaSuccess) return e;
+    kern<<<nb, kVoxBulkThreads, bp.smem, st>>>((const V*)P, (const V*)T, NP, NT, d, Vd, gmin, gmax, (const K*)thr,
+                                              use_thr ? 1 : 0, cells, bP, bp.r0, bp.rc, bp.thr_off, bp.stage_off,
+                                          bp.stage_bytes, hall, flags);
+    return cudaGetLastError();
+  };
+  if (d == 1) return go(k_vdks_voxel_bulk<V, 1>);
+  if (d == 2) return go(k_vdks_voxel_bulk<V, 2>);
+  if (d == 3) return go(k_vdks_voxel_bulk<V, 3>);
+  if (d == 4) return go(k_vdks_voxel_bulk<V, 4>);
+  return go(k_vdks_voxel_bulk<V, kVdksMaxD>);
 }
 
 template <int R>
@@ -644,12 +1074,27 @@ int ddks_vdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
   const int64_t nthr_all = (int64_t)d * (Vd - 1);
   const bool use_thr = nthr_all <= kVdksMaxThresholds && (int64_t)(Vd - 1) * 64 <= NP + NT;
   const SmallLayout L(d, (((size_t)blocks * 20 + 15) & ~(size_t)15) + 8 * (size_t)nthr_all);
+  // CTA-private shared-memory histograms (one CTA per SM, P and T CTAs apart)
+  // when the voxels fit and every CTA has many points per voxel to count
+  const size_t ks = dtype == DDKS_F64 ? 8 : 4;
+  const int64_t nstaged = (int64_t)d * (Vd + 1);  // staged thresholds with their sentinels
+  const size_t hsm = (((size_t)cells * 4 + 15) & ~(size_t)15) + (use_thr ? ks * (size_t)nstaged : 0);
+  const int nbh = ctx->num_sms;
+  const bool smem_hist = hsm <= kVdksMaxHistSmem && NP + NT >= 16 * (int64_t)cells && nbh >= 2;
+  int bP = (int)((double)nbh * (double)NP / (double)(NP + NT) + 0.5);
+  bP = bP < 1 ? 1 : (bP > nbh - 1 ? nbh - 1 : bP);
   if ((rc = ctx->apx_small.reserve(ctx, L.bytes))) return out->status = rc;
   if ((rc = ctx->apx_cnt.reserve(ctx, 8 * (size_t)cells))) return out->status = rc;
   if ((rc = ctx->apx_U.reserve(ctx, 8 * (size_t)cells))) return out->status = rc;
+  if (smem_hist && (rc = ctx->apx_hist.reserve(ctx, 4 * (size_t)cells * nbh))) return out->status = rc;
+  // stream the rows with bulk copies when the ring fits beside the histogram
+  // and both sample bases are 16-byte aligned
+  BulkPlan bp;
+  const bool bulk = smem_hist && ((uintptr_t)dP & 15) == 0 && ((uintptr_t)dT & 15) == 0 &&
+                    plan_voxel_bulk(cells, d, ks, use_thr ? nstaged : 0, ks, &bp);
   GraphKey key;
   key.add(7).add((uint64_t)NP).add((uint64_t)NT).add((uint64_t)d).add((uint64_t)dtype).add((uint64_t)Vd);
-  key.add((uint64_t)use_thr).add((uint64_t)ctx->stage_timing);
+  key.add((uint64_t)use_thr).add((uint64_t)smem_hist).add((uint64_t)bulk).add((uint64_t)ctx->stage_timing);
   key.add_ptr(dP).add_ptr(dT);
   rc = ddks_graph_run(ctx, key.h, st, [&](cudaStream_t s) -> int {
     char* sm = (char*)ctx->apx_small.ptr;
@@ -666,7 +1111,7 @@ int ddks_vdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
     cudaError_t ee = cudaMemsetAsync(sm + L.flags, 0, 8, s);
     if (ee == cudaSuccess) ee = cudaMemsetAsync(gmin, 0xFF, 8 * (size_t)d, s);
     if (ee == cudaSuccess) ee = cudaMemsetAsync(gmax, 0, 8 * (size_t)d, s);
-    if (ee == cudaSuccess) ee = cudaMemsetAsync(cnt, 0, 8 * (size_t)cells, s);
+    if (ee == cudaSuccess && !smem_hist) ee = cudaMemsetAsync(cnt, 0, 8 * (size_t)cells, s);
     if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "vdks memset");
     ddks_stage_mark(ctx, 0, s);
     const bool f64 = dtype == DDKS_F64;
@@ -676,29 +1121,44 @@ int ddks_vdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
     ddks_stage_mark(ctx, 1, s);
     const int gv = grid_cap(NP + NT, kThreads, ctx->num_sms * 8);
     const int nthr = d * (Vd - 1);
-    const size_t ks = f64 ? 8 : 4;
     if (use_thr && nthr > 0) {
-      const int gt = (nthr + kThreads - 1) / kThreads;
+      const int gt = (int)(((int64_t)nthr * 32 + kThreads - 1) / kThreads);  // a warp per threshold
       if (f64)
         k_vdks_thresholds<double><<<gt, kThreads, 0, s>>>(gmin, gmax, d, Vd, (ull*)thr);
       else
         k_vdks_thresholds<float><<<gt, kThreads, 0, s>>>(gmin, gmax, d, Vd, (uint32_t*)thr);
       ctx->launches += 1;
     }
-    const size_t vsm = use_thr ? ks * (size_t)nthr : 0;
-    if (f64)
-      k_vdks_voxel<double><<<gv, kThreads, vsm, s>>>((const double*)dP, (const double*)dT, NP, NT, d, Vd, gmin,
-                                                     gmax, (const ull*)thr, use_thr ? 1 : 0, cnt, flags);
-    else
-      k_vdks_voxel<float><<<gv, kThreads, vsm, s>>>((const float*)dP, (const float*)dT, NP, NT, d, Vd, gmin,
-                                                    gmax, (const uint32_t*)thr, use_thr ? 1 : 0, cnt, flags);
+    if (smem_hist) {
+      uint32_t* hall = (uint32_t*)ctx->apx_hist.ptr;
+      if (bulk)
+        ee = f64 ? launch_voxel_bulk<double>(dP, dT, NP, NT, d, Vd, gmin, gmax, thr, use_thr, cells, bP, nbh, hall,
+                                             flags, bp, s)
+                 : launch_voxel_bulk<float>(dP, dT, NP, NT, d, Vd, gmin, gmax, thr, use_thr, cells, bP, nbh, hall,
+                                            flags, bp, s);
+      else
+        ee = f64 ? launch_voxel_smem<double>(dP, dT, NP, NT, d, Vd, gmin, gmax, thr, use_thr, cells, bP, nbh, hall,
+                                             flags, hsm, s)
+                 : launch_voxel_smem<float>(dP, dT, NP, NT, d, Vd, gmin, gmax, thr, use_thr, cells, bP, nbh, hall,
+                                            flags, hsm, s);
+      if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "vdks voxel attribute");
+      k_vdks_gather<<<(cells + 31) / 32, dim3(32, 8), 0, s>>>(hall, cells, bP, nbh, cnt);
+      ctx->launches += 1;
+    } else {
+      const size_t vsm = use_thr ? ks * (size_t)nstaged : 0;
+      if (f64)
+        k_vdks_voxel<double><<<gv, kThreads, vsm, s>>>((const double*)dP, (const double*)dT, NP, NT, d, Vd, gmin,
+                                                       gmax, (const ull*)thr, use_thr ? 1 : 0, cnt, flags);
+      else
+        k_vdks_voxel<float><<<gv, kThreads, vsm, s>>>((const float*)dP, (const float*)dT, NP, NT, d, Vd, gmin,
+                                                      gmax, (const uint32_t*)thr, use_thr ? 1 : 0, cnt, flags);
+    }
     ddks_stage_mark(ctx, 2, s);
     const uint32_t lines = cells / (uint32_t)Vd;
-    k_vdks_suffix0<<<grid_cap(lines, kThreads / 32, ctx->num_sms * 8), kThreads, 0, s>>>(cnt, U, lines, Vd,
-                                                                                        NP, NT);
-    uint32_t inner = (uint32_t)Vd;
-    for (int m = 1; m < d; ++m, inner *= (uint32_t)Vd)
-      k_vdks_suffix<<<grid_cap(lines, kThreads, ctx->num_sms * 8), kThreads, 0, s>>>(U, lines, Vd, inner);
+    const int gs = grid_cap(lines, kThreads / 32, ctx->num_sms * 8);
+    uint32_t inner = 1;
+    for (int m = 0; m < d; ++m, inner *= (uint32_t)Vd)
+      k_vdks_suffix<<<gs, kThreads, 0, s>>>(m == 0 ? cnt : nullptr, U, lines, Vd, inner, NP, NT);
     ctx->launches += 3 + (d - 1) + 1;
     ull* out3 = (ull*)sm;
     switch (d <= 5 ? 0 : d - 5) {
@@ -742,12 +1202,9 @@ int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
   if ((rc = ctx->ti2.reserve(ctx, 4 * segs))) return out->status = rc;
   if ((rc = ctx->apx_cnt.reserve(ctx, 4 * segs))) return out->status = rc;  // P prefixes
   if ((rc = ctx->apx_U.reserve(ctx, 4 * segs))) return out->status = rc;
-  // warp kernel: shared memory of 3 * d doubles per warp
-  int nwb = 1;
-  if (d > kRdksThreadMaxD) {
-    nwb = (int)((200 * 1024) / (24 * (size_t)d));
-    nwb = nwb < 1 ? 1 : (nwb > kThreads / 32 ? kThreads / 32 : nwb);
-  }
+  // warp kernel: shared memory of 2 * d doubles per warp
+  int nwb = (int)((96 * 1024) / (16 * (size_t)d));
+  nwb = nwb < 1 ? 1 : (nwb > 2 ? 2 : nwb);
   GraphKey key;
   key.add(8).add((uint64_t)NP).add((uint64_t)NT).add((uint64_t)d).add((uint64_t)dtype);
   key.add_ptr(dP).add_ptr(dT).add((uint64_t)ctx->stage_timing);
@@ -777,8 +1234,8 @@ int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
         k_rdks_dist_thread<float><<<g, kThreads, 0, s>>>((const float*)dP, (const float*)dT, NP, NT, d, gmin,
                                                          gmax, keys, flags);
     } else {
-      const size_t smem = (size_t)nwb * 24 * (size_t)d;
-      const int g = grid_cap(N, nwb, ctx->num_sms * 8);
+      const size_t smem = (size_t)nwb * 16 * (size_t)d;
+      const int g = grid_cap(N, nwb, ctx->num_sms * 16);
       if (f64) {
         ee = cudaFuncSetAttribute(k_rdks_dist_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (ee == cudaSuccess)
@@ -794,6 +1251,26 @@ int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
     }
     ctx->launches += 2;
     ddks_stage_mark(ctx, 1, s);
+    if (N <= 1024) {  // sort and walk each corner in one warp
+      const int gsm = (int)(((int64_t)S * 32 + kThreads - 1) / kThreads);
+      const int E = N <= 32 ? 1 : N <= 64 ? 2 : N <= 128 ? 4 : N <= 256 ? 8 : N <= 512 ? 16 : 32;
+      const ull* kk = (const ull*)keys;
+      switch (E) {
+        case 1: k_rdks_small<1><<<gsm, kThreads, 0, s>>>(kk, (int)N, NP, NT, S, pc); break;
+        case 2: k_rdks_small<2><<<gsm, kThreads, 0, s>>>(kk, (int)N, NP, NT, S, pc); break;
+        case 4: k_rdks_small<4><<<gsm, kThreads, 0, s>>>(kk, (int)N, NP, NT, S, pc); break;
+        case 8: k_rdks_small<8><<<gsm, kThreads, 0, s>>>(kk, (int)N, NP, NT, S, pc); break;
+        case 16: k_rdks_small<16><<<gsm, kThreads, 0, s>>>(kk, (int)N, NP, NT, S, pc); break;
+        default: k_rdks_small<32><<<gsm, kThreads, 0, s>>>(kk, (int)N, NP, NT, S, pc); break;
+      }
+      ddks_stage_mark(ctx, 2, s);
+      k_rdks_final<<<1, kThreads, 0, s>>>(pc, S, (ull*)sm);
+      ctx->launches += 2;
+      ee = cudaGetLastError();
+      if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "rdks kernels");
+      ddks_stage_mark(ctx, 3, s);
+      return DDKS_OK;
+    }
     const uint64_t* sk;
     const uint32_t *si, *sp;
     int n = 0;

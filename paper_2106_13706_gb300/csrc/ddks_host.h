@@ -59,7 +59,8 @@ struct ddks_ctx {
   DevBuf perm_keys, perm_labels, perm_best, perm_codes;  // permutation test
   DevBuf sig_cells, sig_logp;                   // significance
   DevBuf batch_desc, batch_work;                // batched launch
-  DevBuf apx_small, apx_cnt, apx_U;             // vdKS / rdKS (approx.cu)
+  DevBuf apx_small, apx_cnt, apx_U, apx_hist;   // vdKS / rdKS (approx.cu)
+  DevBuf dom_work;                              // d = 2 range-query path (dominance.cu)
   unsigned long long* h_out = nullptr;          // pinned, 64 entries
   void* h_stage = nullptr;                      // pinned staging for uploads
   size_t h_stage_bytes = 0;
@@ -82,7 +83,7 @@ struct ddks_ctx {
   std::vector<DevBuf*> all_bufs() {
     return {&inP, &inT, &keys, &tk1, &tk2, &ti1, &ti2, &rank, &sidx0, &pfx0, &best, &bestj, &out3,
             &flags, &reg_words, &reg_meta, &warp_words, &perm_keys, &perm_labels, &perm_best, &perm_codes,
-            &sig_cells, &sig_logp, &batch_desc, &batch_work, &apx_small, &apx_cnt, &apx_U};
+            &sig_cells, &sig_logp, &batch_desc, &batch_work, &apx_small, &apx_cnt, &apx_U, &apx_hist, &dom_work};
   }
 };
 
@@ -157,6 +158,12 @@ int ddks_graph_run(ddks_ctx* ctx, uint64_t key, cudaStream_t st, F&& body) {
   if (rc == 1) return body(st);  // capture dropped: run directly
   return rc;
 }
+
+// dominance.cu
+bool ddks_dominance_supported(int d, int64_t NP, int64_t NT);
+cudaError_t ddks_launch_dominance(ddks_ctx* ctx, const uint32_t* rank, int64_t N, int64_t NP, int64_t NT,
+                                  int64_t ob, int64_t oe, uint64_t* best, int32_t* bestj, cudaStream_t st,
+                                  int* launches);
 
 // count_warp.cu
 bool ddks_warp16_supported(int d, int64_t NP, int64_t NT);

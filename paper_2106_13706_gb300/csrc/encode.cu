@@ -12,15 +12,18 @@
 // chunks a dimension (N <= 8192) every element then finds its min-rank as
 // the sum of one lower_bound per sorted chunk, and its position in the full
 // (key, index) order for dimension 0.  Larger inputs merge the chunks in
-// passes in which every element finds its output slot by binary search in the
-// partner run (pairs are unique because the index breaks ties), then take one
-// lower_bound per element in the fully sorted keys.
+// passes: each CTA produces 2048 consecutive outputs of a merged pair of runs,
+// finding where its output range starts in the two runs by a merge-path
+// search (pairs are unique because the index breaks ties), staging both input
+// ranges in shared memory and merging them there.  The last pass writes the
+// min-ranks (and dimension 0's sorted order) directly instead of the merged
+// arrays.
 #include "ddks_internal.cuh"
 
 namespace {
 
 constexpr int kChunk = 2048;
-constexpr int kChunkThreads = 1024;
+constexpr int kChunkThreads = 256;  // 8 positions per thread
 constexpr int64_t kMaxMultiChunks = 4;  // above this (N > 8192), merge passes
 
 template <typename V>
@@ -42,57 +45,104 @@ DDKS_DEV bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
   return ka < kb || (ka == kb && ia < ib);
 }
 
-// grid: (chunks, d).  Sorts chunk blockIdx.x of dimension blockIdx.y.
-// With out_p, dimensions m < pfx_dims also write out_p[m * Npad + base + t] =
-// #{j < t : sorted element j of the chunk is a P point}.
+// grid: (chunks, d).  Sorts chunk blockIdx.x of dimension blockIdx.y by
+// (key, index) with a bitonic network.  Thread t holds the 8 consecutive
+// positions 8t .. 8t+7 in registers: compare-exchange stages of stride 1, 2, 4
+// stay inside a thread, strides 8 .. 128 pair thread t with t ^ (stride / 8)
+// of the same warp (shuffles), strides >= 256 go through shared memory.
+// With out_p, dimensions m < pfx_dims also write out_p[m * Npad + base + p] =
+// #{q < p : sorted element q of the chunk is a P point}.
 __global__ void __launch_bounds__(kChunkThreads)
 k_chunk_sort(const uint64_t* __restrict__ keys, int64_t N, int64_t Npad, int64_t NP,
              uint64_t* __restrict__ out_k, uint32_t* __restrict__ out_i, uint32_t* __restrict__ out_p,
              int pfx_dims) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  uint64_t* sk = reinterpret_cast<uint64_t*>(smraw);   // [kChunk]
-  uint32_t* si = reinterpret_cast<uint32_t*>(sk + kChunk);
+  constexpr int E = kChunk / kChunkThreads;  // 8
+  __shared__ uint64_t sk[kChunk];
+  __shared__ uint32_t si[kChunk];
+  __shared__ uint32_t wsum[kChunkThreads / 32 + 1];
   const int m = blockIdx.y;
+  const int t = threadIdx.x;
   const int64_t base = (int64_t)blockIdx.x * kChunk;
-  for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
-    const int64_t g = base + t;
-    if (g < N) {
-      sk[t] = keys[(int64_t)m * N + g];
-      si[t] = (uint32_t)g;
-    } else {
-      sk[t] = ~0ull;          // pads sort last; the index keeps pairs unique
-      si[t] = (uint32_t)g;
-    }
+  const int q0 = t * E;
+  uint64_t k[E];
+  uint32_t ix[E];
+  // coalesced loads through shared memory
+  for (int q = t; q < kChunk; q += kChunkThreads) {
+    const int64_t g = base + q;
+    sk[q] = g < N ? keys[(int64_t)m * N + g] : ~0ull;  // pads sort last; the index keeps pairs unique
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    k[j] = sk[q0 + j];
+    ix[j] = (uint32_t)(base + q0 + j);
   }
   __syncthreads();
   for (int size = 2; size <= kChunk; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = threadIdx.x; t < kChunk / 2; t += blockDim.x) {
-        const int lo = 2 * t - (t & (stride - 1));
-        const int hi = lo + stride;
-        const bool asc = ((lo & size) == 0);
-        const uint64_t ka = sk[lo], kb = sk[hi];
-        const uint32_t ia = si[lo], ib = si[hi];
-        const bool swap = asc ? pair_less(kb, ib, ka, ia) : pair_less(ka, ia, kb, ib);
-        if (swap) {
-          sk[lo] = kb; sk[hi] = ka;
-          si[lo] = ib; si[hi] = ia;
+    int stride = size >> 1;
+    if (stride >= 8 * 32) {  // partners in other warps: through shared memory
+#pragma unroll
+      for (int j = 0; j < E; ++j) { sk[q0 + j] = k[j]; si[q0 + j] = ix[j]; }
+      __syncthreads();
+      for (; stride >= 8 * 32; stride >>= 1) {
+        for (int pr = t; pr < kChunk / 2; pr += kChunkThreads) {
+          const int lo = 2 * pr - (pr & (stride - 1));
+          const int hi = lo + stride;
+          const bool asc = (lo & size) == 0;
+          const uint64_t ka = sk[lo], kb = sk[hi];
+          const uint32_t ia = si[lo], ib = si[hi];
+          if (asc ? pair_less(kb, ib, ka, ia) : pair_less(ka, ia, kb, ib)) {
+            sk[lo] = kb; sk[hi] = ka;
+            si[lo] = ib; si[hi] = ia;
+          }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int j = 0; j < E; ++j) { k[j] = sk[q0 + j]; ix[j] = si[q0 + j]; }
+      __syncthreads();  // the next size writes these slots again
+    }
+    for (; stride >= E; stride >>= 1) {  // partner thread t ^ (stride / E) in this warp
+      const int xm = stride / E;
+      const bool lower = (t & xm) == 0;
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const uint64_t ok = __shfl_xor_sync(0xffffffffu, k[j], xm);
+        const uint32_t oi = __shfl_xor_sync(0xffffffffu, ix[j], xm);
+        const bool asc = ((q0 + j) & size) == 0;
+        const bool keep_min = lower == asc;
+        if (keep_min != pair_less(k[j], ix[j], ok, oi)) { k[j] = ok; ix[j] = oi; }
+      }
+    }
+#pragma unroll
+    for (int sd = E / 2; sd >= 1; sd >>= 1) {  // inside the thread (sd <= stride: indices stay static)
+      if (sd > stride) continue;
+#pragma unroll
+      for (int a = 0; a < E; ++a) {
+        if (a & sd) continue;
+        const int b = a | sd;
+        const bool asc = ((q0 + a) & size) == 0;
+        if (asc ? pair_less(k[b], ix[b], k[a], ix[a]) : pair_less(k[a], ix[a], k[b], ix[b])) {
+          const uint64_t tk = k[a]; k[a] = k[b]; k[b] = tk;
+          const uint32_t ti = ix[a]; ix[a] = ix[b]; ix[b] = ti;
         }
       }
-      __syncthreads();
     }
   }
-  for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
-    out_k[(int64_t)m * Npad + base + t] = sk[t];
-    out_i[(int64_t)m * Npad + base + t] = si[t];
+  // coalesced stores through shared memory
+#pragma unroll
+  for (int j = 0; j < E; ++j) { sk[q0 + j] = k[j]; si[q0 + j] = ix[j]; }
+  __syncthreads();
+  for (int q = t; q < kChunk; q += kChunkThreads) {
+    out_k[(int64_t)m * Npad + base + q] = sk[q];
+    out_i[(int64_t)m * Npad + base + q] = si[q];
   }
   if (out_p && m < pfx_dims) {
-    // exclusive prefix of the P flags of the sorted chunk: thread t owns
-    // elements 2t, 2t+1
-    __shared__ uint32_t wsum[kChunkThreads / 32 + 1];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const uint32_t f0 = si[2 * t] < (uint64_t)NP ? 1u : 0u, f1 = si[2 * t + 1] < (uint64_t)NP ? 1u : 0u;
-    const uint32_t v = f0 + f1;
+    // exclusive prefix of the P flags over the sorted chunk
+    const int lane = t & 31, warp = t >> 5;
+    uint32_t f[E], v = 0;
+#pragma unroll
+    for (int j = 0; j < E; ++j) { f[j] = ix[j] < (uint64_t)NP ? 1u : 0u; v += f[j]; }
     uint32_t incl = v;
     for (int off = 1; off < 32; off <<= 1) {
       const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
@@ -101,67 +151,203 @@ k_chunk_sort(const uint64_t* __restrict__ keys, int64_t N, int64_t Npad, int64_t
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-      const uint32_t w = wsum[lane];
+      const uint32_t w = lane < kChunkThreads / 32 ? wsum[lane] : 0u;
       uint32_t wi = w;
       for (int off = 1; off < 32; off <<= 1) {
         const uint32_t x = __shfl_up_sync(0xffffffffu, wi, off);
         if (lane >= off) wi += x;
       }
-      wsum[lane] = wi - w;
-      if (lane == 31) wsum[32] = wi;
+      if (lane < kChunkThreads / 32) wsum[lane] = wi - w;
     }
     __syncthreads();
-    const uint32_t ex = wsum[warp] + incl - v;
-    uint32_t* P = out_p + (int64_t)m * Npad + base;
-    P[2 * t] = ex;
-    P[2 * t + 1] = ex + f0;
+    uint32_t ex = wsum[warp] + incl - v;
+#pragma unroll
+    for (int j = 0; j < E; ++j) { si[q0 + j] = ex; ex += f[j]; }  // si is free again after the copy above
+    __syncthreads();
+    uint32_t* Pout = out_p + (int64_t)m * Npad + base;
+    for (int q = t; q < kChunk; q += kChunkThreads) Pout[q] = si[q];
   }
 }
 
-// One merge pass over runs of length L (Npad is a multiple of kChunk <= L).
-// grid-stride over (d * Npad) elements.  With in_p / out_p, dimensions
-// m < pfx_dims also carry each element's count of P points before it within
-// its run: after the merge that is its own count plus the partner run's count
-// below its slot.
-__global__ void k_merge_pass(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ in_i,
-                             uint64_t* __restrict__ out_k, uint32_t* __restrict__ out_i,
-                             const uint32_t* __restrict__ in_p, uint32_t* __restrict__ out_p,
-                             int64_t Npad, int64_t NP, int d, int64_t L, int pfx_dims) {
-  const int64_t total = Npad * d;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t m = e / Npad;
-    const int64_t p = e - m * Npad;
-    const uint64_t* K = in_k + m * Npad;
-    const uint32_t* I = in_i + m * Npad;
-    const uint64_t key = K[p];
-    const uint32_t idx = I[p];
-    const int64_t r = p / L;
-    const int64_t a = p - r * L;
-    const int64_t ps = (r ^ 1) * L;  // partner run start
-    int64_t dst;
-    const bool carry = in_p && m < pfx_dims;
-    const uint32_t* Pin = carry ? in_p + m * Npad : nullptr;
-    uint32_t pc = carry ? Pin[p] : 0u;
-    if (ps >= Npad) {
-      dst = p;
+// One merge pass over runs of length L (a multiple of kChunk; Npad a multiple
+// of kChunk): grid (Npad / kChunk, d), CTA (x, m) writes sorted positions
+// [x * kChunk, (x + 1) * kChunk) of dimension m.  Its pair of runs A, B; the
+// merge-path search gives a0 = the number of A elements among the first D
+// outputs of the pair; the CTA stages A[a0, a1) and B[b0, b1) in shared
+// memory, then each thread merges kMergeEach outputs from its own merge-path
+// split.  With in_p / out_p, dimensions m < pfx_dims also carry each element's
+// count of P points (index < NP) before it: preA(i) + preB(j) for the i A and
+// j B elements that precede it, preX(p) being X's carried count at p (for p at
+// the end of X: the last count plus the last element's flag).
+constexpr int kMergeThreads = 256;
+constexpr int kMergeEach = kChunk / kMergeThreads;  // 8 outputs per thread
+
+DDKS_DEV int64_t merge_path(const uint64_t* Ak, const uint32_t* Ai, int64_t na, const uint64_t* Bk,
+                            const uint32_t* Bi, int64_t nb, int64_t D) {
+  int64_t lo = D > nb ? D - nb : 0, hi = D < na ? D : na;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (pair_less(Ak[mid], Ai[mid], Bk[D - 1 - mid], Bi[D - 1 - mid])) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// With rank (the last pass, whose pair of runs is the whole dimension) the
+// CTA writes no merged arrays: each output p < N gives rank[m][index] = its
+// min-rank (the position of the first equal key: p itself when the key
+// differs from the previous output, found for each thread's first output by
+// lower_bound in both runs), and for dimension 0 sorted_idx0[p] = index and
+// pprefix0[p] = the carried P count.
+// The same search by a whole warp: 32 probes per round (the answer a is the
+// first index at which A[a] < B[D-1-a] fails), so a run of 2^k elements
+// takes about k / 5 rounds of dependent global loads instead of k.
+DDKS_DEV int64_t merge_path_warp(const uint64_t* Ak, const uint32_t* Ai, int64_t na, const uint64_t* Bk,
+                                 const uint32_t* Bi, int64_t nb, int64_t D) {
+  const int lane = threadIdx.x & 31;
+  int64_t lo = D > nb ? D - nb : 0, hi = D < na ? D : na;
+  while (lo < hi) {
+    const int64_t step = (hi - lo) / 32 + 1;
+    const int64_t c = lo + lane * step;
+    const bool past = c >= hi || !pair_less(Ak[c], Ai[c], Bk[D - 1 - c], Bi[D - 1 - c]);  // answer <= c
+    const unsigned bal = __ballot_sync(0xffffffffu, past);
+    const int f = __ffs(bal) - 1;
+    if (f < 0) {
+      lo = lo + 31 * step + 1;
+    } else if (f == 0) {
+      hi = lo;
     } else {
-      const int64_t plen = (Npad - ps) < L ? (Npad - ps) : L;
-      // number of partner elements strictly below (key, idx)
-      int64_t lo = 0, hi = plen;
-      while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (pair_less(K[ps + mid], I[ps + mid], key, idx)) lo = mid + 1; else hi = mid;
-      }
-      const int64_t start = (r < (r ^ 1) ? r : (r ^ 1)) * L;
-      dst = start + a + lo;
-      if (carry)
-        pc += lo < plen ? Pin[ps + lo]
-                        : Pin[ps + plen - 1] + (I[ps + plen - 1] < (uint64_t)NP ? 1u : 0u);
+      const int64_t cf = lo + f * step;
+      lo = lo + (f - 1) * step + 1;
+      hi = cf < hi ? cf : hi;
     }
-    out_k[m * Npad + dst] = key;
-    out_i[m * Npad + dst] = idx;
-    if (carry) out_p[m * Npad + dst] = pc;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kMergeThreads)
+k_merge_tile(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ in_i,
+             uint64_t* __restrict__ out_k, uint32_t* __restrict__ out_i,
+             const uint32_t* __restrict__ in_p, uint32_t* __restrict__ out_p,
+             int64_t Npad, int64_t NP, int64_t L, int pfx_dims, int64_t N, uint32_t* __restrict__ rank,
+             uint32_t* __restrict__ sorted_idx0, uint32_t* __restrict__ pprefix0) {
+  __shared__ uint64_t sk[kChunk];
+  __shared__ uint32_t si[kChunk];
+  __shared__ uint32_t sp[kChunk + 2];
+  __shared__ int64_t s_a0, s_a1;
+  const int64_t m = blockIdx.y;
+  const int64_t pos0 = (int64_t)blockIdx.x * kChunk;
+  const uint64_t* K = in_k + m * Npad;
+  const uint32_t* I = in_i + m * Npad;
+  const bool carry = in_p && m < pfx_dims;
+  const uint32_t* Pin = carry ? in_p + m * Npad : nullptr;
+  const int64_t run0 = (pos0 / (2 * L)) * (2 * L);
+  const int64_t na = (Npad - run0) < L ? (Npad - run0) : L;
+  const int64_t bS = run0 + L;
+  const int64_t nb = bS >= Npad ? 0 : ((Npad - bS) < L ? (Npad - bS) : L);
+  if (nb == 0) {  // no partner: the run is already in place
+    for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
+      const int64_t p = pos0 + t;
+      out_k[m * Npad + p] = K[p];
+      out_i[m * Npad + p] = I[p];
+      if (carry) out_p[m * Npad + p] = Pin[p];
+    }
+    return;
+  }
+  const uint64_t *Ak = K + run0, *Bk = K + bS;
+  const uint32_t *Ai = I + run0, *Bi = I + bS;
+  const int64_t D0 = pos0 - run0, D1 = D0 + kChunk;  // runs are multiples of kChunk
+  if (threadIdx.x < 32) {
+    const int64_t a = merge_path_warp(Ak, Ai, na, Bk, Bi, nb, D0);
+    if (threadIdx.x == 0) s_a0 = a;
+  } else if (threadIdx.x < 64) {
+    const int64_t a = merge_path_warp(Ak, Ai, na, Bk, Bi, nb, D1);
+    if (threadIdx.x == 32) s_a1 = a;
+  }
+  __syncthreads();
+  const int64_t a0 = s_a0, a1 = s_a1, b0 = D0 - a0, b1 = D1 - a1;
+  const int nA = (int)(a1 - a0), nB = (int)(b1 - b0);
+  for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
+    if (t < nA) { sk[t] = Ak[a0 + t]; si[t] = Ai[a0 + t]; }
+    else { sk[t] = Bk[b0 + t - nA]; si[t] = Bi[b0 + t - nA]; }
+  }
+  // carried counts: sp[0..nA] = preA(a0 .. a1), sp[nA+1 .. nA+1+nB] = preB(b0 .. b1)
+  if (carry) {
+    const uint32_t* PA = Pin + run0;
+    const uint32_t* PB = Pin + bS;
+    for (int t = threadIdx.x; t < kChunk + 2; t += blockDim.x) {
+      uint32_t v;
+      if (t <= nA) {
+        const int64_t p = a0 + t;
+        v = p < na ? PA[p] : PA[na - 1] + (Ai[na - 1] < (uint64_t)NP ? 1u : 0u);
+      } else {
+        const int64_t p = b0 + (t - nA - 1);
+        v = p < nb ? PB[p] : PB[nb - 1] + (Bi[nb - 1] < (uint64_t)NP ? 1u : 0u);
+      }
+      sp[t] = v;
+    }
+  }
+  __syncthreads();
+  const uint64_t *sAk = sk, *sBk = sk + nA;
+  const uint32_t *sAi = si, *sBi = si + nA;
+  const int d0 = threadIdx.x * kMergeEach;
+  int i = (int)merge_path(sAk, sAi, nA, sBk, sBi, nB, d0);
+  int j = d0 - i;
+  if (rank) {
+    const int64_t p0 = pos0 + d0;
+    const uint64_t first = (i < nA && (j >= nB || pair_less(sAk[i], sAi[i], sBk[j], sBi[j]))) ? sAk[i] : sBk[j];
+    // #{keys < first} in the two runs: the min-rank of the first output
+    int64_t lo = 0, hi = na;
+    while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (Ak[mid] < first) lo = mid + 1; else hi = mid; }
+    int64_t r = lo;
+    lo = 0; hi = nb;
+    while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (Bk[mid] < first) lo = mid + 1; else hi = mid; }
+    r += lo;
+    uint64_t prev = first;
+    uint32_t* R = rank + m * N;
+#pragma unroll
+    for (int e = 0; e < kMergeEach; ++e) {
+      const int64_t p = p0 + e;
+      const bool takeA = j >= nB || (i < nA && pair_less(sAk[i], sAi[i], sBk[j], sBi[j]));
+      const uint32_t pc = carry ? sp[i] + sp[nA + 1 + j] : 0u;
+      const uint64_t key = takeA ? sAk[i] : sBk[j];
+      const uint32_t idx = takeA ? sAi[i] : sBi[j];
+      if (takeA) ++i; else ++j;
+      if (key != prev) r = p;
+      prev = key;
+      if (p < N) {
+        R[idx] = (uint32_t)r;
+        if (m == 0 && sorted_idx0) {
+          sorted_idx0[p] = idx;
+          if (pprefix0) pprefix0[p] = pc;
+        }
+      }
+    }
+    return;
+  }
+  uint64_t ok[kMergeEach];
+  uint32_t oi[kMergeEach], op[kMergeEach];
+#pragma unroll
+  for (int e = 0; e < kMergeEach; ++e) {
+    const bool takeA = j >= nB || (i < nA && pair_less(sAk[i], sAi[i], sBk[j], sBi[j]));
+    op[e] = carry ? sp[i] + sp[nA + 1 + j] : 0u;
+    if (takeA) { ok[e] = sAk[i]; oi[e] = sAi[i]; ++i; }
+    else { ok[e] = sBk[j]; oi[e] = sBi[j]; ++j; }
+  }
+  // through shared memory, so that the global stores are coalesced
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < kMergeEach; ++e) {
+    sk[d0 + e] = ok[e];
+    si[d0 + e] = oi[e];
+    if (carry) sp[d0 + e] = op[e];
+  }
+  __syncthreads();
+  uint64_t* Ok = out_k + m * Npad + pos0;
+  uint32_t* Oi = out_i + m * Npad + pos0;
+  for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
+    Ok[t] = sk[t];
+    Oi[t] = si[t];
+    if (carry) out_p[m * Npad + pos0 + t] = sp[t];
   }
 }
 
@@ -234,33 +420,6 @@ __global__ void k_rank_multi(const uint64_t* __restrict__ keys, const uint64_t* 
   }
 }
 
-// rank[m][i] = #{j : key_j < key_i}, by lower_bound in the sorted keys of m.
-__global__ void k_rank(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ sorted_k,
-                       int64_t N, int64_t Npad, int d, uint32_t* __restrict__ rank) {
-  const int64_t total = N * d;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t m = e / N;
-    const uint64_t key = keys[e];
-    const uint64_t* S = sorted_k + m * Npad;
-    int64_t lo = 0, hi = N;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (S[mid] < key) lo = mid + 1; else hi = mid;
-    }
-    rank[e] = (uint32_t)lo;
-  }
-}
-
-__global__ void k_copy_idx(const uint32_t* __restrict__ sorted_i, const uint32_t* __restrict__ sorted_p,
-                           int64_t N, uint32_t* __restrict__ out, uint32_t* __restrict__ out_p) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    out[i] = sorted_i[i];
-    if (out_p) out_p[i] = sorted_p[i];
-  }
-}
-
 int grid_for(int64_t work, int threads) {
   int64_t g = (work + threads - 1) / threads;
   if (g > 152 * 64) g = 152 * 64;
@@ -300,14 +459,11 @@ cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int64_t NP, int d,
   const int64_t Npad = (int64_t)ddks_rank_scratch_elems(N);
   const int64_t chunks = Npad / kChunk;
   dim3 g((unsigned)chunks, (unsigned)d);
-  const size_t smem = (size_t)kChunk * 12;
   const bool pfx = sorted_idx0 && pprefix0 && cpfx;
   if (pfx_done) *pfx_done = pfx ? 1 : 0;
-  cudaError_t e = cudaFuncSetAttribute(k_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   uint32_t* cp = pfx ? cpfx : nullptr;             // [Npad] P prefixes, dimension 0
   uint32_t* cp2 = pfx ? cpfx + Npad : nullptr;     // [Npad] the other merge buffer
-  k_chunk_sort<<<g, kChunkThreads, smem, st>>>(keys, N, Npad, NP, tmp_keys, tmp_idx, cp, 1);
+  k_chunk_sort<<<g, kChunkThreads, 0, st>>>(keys, N, Npad, NP, tmp_keys, tmp_idx, cp, 1);
   int n = 1;
   if (chunks <= kMaxMultiChunks) {
     k_rank_multi<<<grid_for(N * d, 256), 256, 0, st>>>(keys, tmp_keys, tmp_idx, cp, N, NP, Npad, d, rank,
@@ -318,17 +474,14 @@ cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int64_t NP, int d,
   uint64_t *ck = tmp_keys, *nk = tmp_keys2;
   uint32_t *ci = tmp_idx, *ni = tmp_idx2;
   for (int64_t L = kChunk; L < Npad; L <<= 1) {
-    k_merge_pass<<<grid_for(Npad * d, 256), 256, 0, st>>>(ck, ci, nk, ni, cp, cp2, Npad, NP, d, L, 1);
+    const bool last = 2 * L >= Npad;  // the final pass writes ranks instead of merged arrays
+    k_merge_tile<<<dim3((unsigned)chunks, (unsigned)d), kMergeThreads, 0, st>>>(
+        ck, ci, nk, ni, cp, cp2, Npad, NP, L, 1, N, last ? rank : nullptr, last ? sorted_idx0 : nullptr,
+        last && pfx ? pprefix0 : nullptr);
     ++n;
     uint64_t* tk = ck; ck = nk; nk = tk;
     uint32_t* ti = ci; ci = ni; ni = ti;
     uint32_t* tp = cp; cp = cp2; cp2 = tp;
-  }
-  k_rank<<<grid_for(N * d, 256), 256, 0, st>>>(keys, ck, N, Npad, d, rank);
-  ++n;
-  if (sorted_idx0) {
-    k_copy_idx<<<grid_for(N, 256), 256, 0, st>>>(ci, cp, N, sorted_idx0, pfx ? pprefix0 : nullptr);
-    ++n;
   }
   if (launches) *launches += n;
   return cudaGetLastError();
@@ -345,16 +498,15 @@ cudaError_t ddks_launch_sort_segments(const uint64_t* keys, int64_t N, int64_t N
                                       const uint32_t** out_p, cudaStream_t st, int* launches) {
   const int64_t Npad = (int64_t)ddks_rank_scratch_elems(N);
   const int64_t chunks = Npad / kChunk;
-  const size_t smem = (size_t)kChunk * 12;
-  cudaError_t e = cudaFuncSetAttribute(k_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_chunk_sort<<<dim3((unsigned)chunks, (unsigned)S), kChunkThreads, smem, st>>>(keys, N, Npad, NP, k1, i1,
+  k_chunk_sort<<<dim3((unsigned)chunks, (unsigned)S), kChunkThreads, 0, st>>>(keys, N, Npad, NP, k1, i1,
                                                                                   p1, S);
   int n = 1;
   uint64_t *ck = k1, *nk = k2;
   uint32_t *ci = i1, *ni = i2, *cp = p1, *np = p2;
   for (int64_t L = kChunk; L < Npad; L <<= 1) {
-    k_merge_pass<<<grid_for(Npad * S, 256), 256, 0, st>>>(ck, ci, nk, ni, cp, np, Npad, NP, S, L, S);
+    k_merge_tile<<<dim3((unsigned)chunks, (unsigned)S), kMergeThreads, 0, st>>>(ck, ci, nk, ni, cp, np, Npad, NP,
+                                                                                 L, S, N, nullptr, nullptr,
+                                                                                 nullptr);
     ++n;
     uint64_t* tk = ck; ck = nk; nk = tk;
     uint32_t* ti = ci; ci = ni; ni = ti;

@@ -15,6 +15,8 @@
 #include "ddks_host.h"
 #include "ddks_internal.cuh"
 
+constexpr int64_t kDominanceMinN = 32768;
+
 static std::string tune_key(int64_t NP, int64_t NT, int32_t d) {
   auto bucket = [](int64_t n) {
     int b = 0;
@@ -33,12 +35,18 @@ static bool plan_ok(const ddks_plan& p, int64_t NP, int64_t NT, int32_t d) {
     case DDKS_PATH_LANE: return ddks_lane_supported(d, NP, NT, p.threads);
     case DDKS_PATH_WARP: return ddks_warp_supported(d, NP, NT);
     case DDKS_PATH_SORT: return ddks_sort_supported(d, NP + NT);
+    case DDKS_PATH_DOMINANCE: return ddks_dominance_supported(d, NP, NT);
     default: return false;
   }
 }
 
 static ddks_plan default_plan(int64_t NP, int64_t NT, int32_t d) {
   ddks_plan p;
+  // d = 2 with many points: O(N log N) range queries beat the N^2 compares
+  if (d == 2 && NP + NT >= kDominanceMinN && ddks_dominance_supported(d, NP, NT)) {
+    p.path = DDKS_PATH_DOMINANCE;
+    return p;
+  }
   if (ddks_register_supported(d, NP, NT)) {
     p.path = DDKS_PATH_REGISTER;
     return p;
@@ -122,6 +130,7 @@ int ddks_autotune(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64
   }
   { ddks_plan p; p.path = DDKS_PATH_WARP; p.warps = 8; cands.push_back(p); }
   { ddks_plan p; p.path = DDKS_PATH_SORT; cands.push_back(p); }
+  { ddks_plan p; p.path = DDKS_PATH_DOMINANCE; cands.push_back(p); }
   cudaEvent_t a, b;
   if ((e = cudaEventCreate(&a)) != cudaSuccess) return ctx_cuda_fail(ctx, e, "cudaEventCreate");
   if ((e = cudaEventCreate(&b)) != cudaSuccess) { cudaEventDestroy(a); return ctx_cuda_fail(ctx, e, "cudaEventCreate"); }

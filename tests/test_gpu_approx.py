@@ -60,6 +60,10 @@ VDKS_CASES = [
     # many voxels per dimension for the points: the double rescaling of
     # every coordinate instead of the thresholds
     (3, 300, 300, 40, "normal"), (2, 400, 300, 200, "int"), (1, 2000, 1500, 100000, "normal"),
+    # many points per voxel: CTA-private shared-memory histograms (with the
+    # thresholds for d <= 4 and d > 4, and with the double rescaling)
+    (4, 6000, 5000, 5, "normal"), (6, 3000, 3000, 2, "int"), (1, 2000, 1500, 100, "normal"),
+    (2, 9000, 200, 7, "normal"),
 ]
 
 
@@ -89,10 +93,26 @@ def test_vdks_dvu_and_mixture(torch, ctx):
         _vdks_same(ctx.vdks(_dev(torch, P), _dev(torch, T), V), orc.vdks(P, T, V))
 
 
-def test_vdks_large_full_grid(torch, ctx):
-    # the bench's grid (32^3 voxels, float32 Gaussian pair) at 400k points:
-    # every voxel the oracle visits is checked
-    P, T = wl.gaussian_pair(0, 200_000, 200_000, 3, shift=0.2)
+@pytest.mark.parametrize("d,V", [(3, 6), (6, 2)])
+def test_vdks_unaligned_rows(torch, ctx, d, V):
+    # rows that start off a 16-byte boundary: the shared-memory histogram
+    # path without bulk copies
+    P, T = wl.random_pair(77 + d, 6000, 5500, d, kind="normal")
+    Pb = torch.zeros((len(P) + 1, d), dtype=torch.float32, device="cuda")
+    Tb = torch.zeros((len(T) + 1, d), dtype=torch.float32, device="cuda")
+    Pb[1:] = _dev(torch, P)
+    Tb[1:] = _dev(torch, T)
+    Pv, Tv = Pb[1:], Tb[1:]
+    assert Pv.is_contiguous() and Pv.data_ptr() % 16 != 0
+    _vdks_same(ctx.vdks(Pv, Tv, V), orc.vdks(P, T, V))
+
+
+@pytest.mark.parametrize("n", [200_000, 300_000])
+def test_vdks_large_full_grid(torch, ctx, n):
+    # the bench's grid (32^3 voxels, float32 Gaussian pair): at 400k points
+    # the voxel counts go to global memory, at 600k (16 points per voxel) to
+    # CTA-private shared-memory histograms like the bench's 16M points
+    P, T = wl.gaussian_pair(0, n, n, 3, shift=0.2)
     _vdks_same(ctx.vdks(_dev(torch, P), _dev(torch, T), 32), orc.vdks(P, T, 32))
 
 

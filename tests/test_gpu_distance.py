@@ -249,6 +249,6 @@ def test_autotune_picks_an_agreeing_path(torch, d):
     ref = orc.ddks(P, T)
     with _ctx() as c:
         path, ms = c.autotune(_dev(torch, P), _dev(torch, T))
-        assert path in (pkg.PATH_REGISTER, pkg.PATH_LANE, pkg.PATH_WARP, pkg.PATH_SORT)
+        assert path in (pkg.PATH_REGISTER, pkg.PATH_LANE, pkg.PATH_WARP, pkg.PATH_SORT, pkg.PATH_DOMINANCE)
         assert ms > 0
         _same(c.distance(_dev(torch, P), _dev(torch, T)), ref)
