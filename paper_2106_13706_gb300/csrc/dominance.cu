@@ -18,8 +18,10 @@
 // over the P points only.  Level l of a matrix holds one bit per position
 // (bit L-1-l of the value), a per-word prefix count of ones, and the next
 // level's order: a stable partition, zeros first.  A query walks the L levels
-// with two rank lookups each.  Build: per level a bit kernel (warp ballots), a
-// scan of the word counts and a scatter kernel; query: one thread per origin.
+// with two rank lookups each (an 8-byte word record plus a superblock
+// prefix).  Build: per level a bit kernel (warp ballots; prefixes within
+// superblocks of 256 words), a scan of the superblock totals and a scatter
+// kernel; query: one thread per origin.
 #include <cstring>
 
 #include "../../include/ddks.h"
@@ -30,36 +32,38 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// One wavelet matrix in device memory: level lv's bit words at
-// B + lv * bstride, its prefix counts (ones before each word, nw + 1 entries)
-// at R + lv * rstride.
+constexpr int kScanThreads = 1024;
+constexpr int kMaxLevels = 32;
+constexpr int kSBWords = 256;  // words per superblock (8192 positions), one CTA of k_dom_bits
+
+// One wavelet matrix in device memory.  Level lv: records at rec + lv * stride,
+// record w = {ones in the words of its superblock before w, bit word w};
+// superblock prefixes at sb + lv * sbstride (ones before each superblock).
 struct WMView {
-  const uint32_t* B;
-  const uint32_t* R;
-  uint32_t n, nw;
-  uint32_t bstride, rstride;
+  const uint2* rec;
+  const uint32_t* sb;
+  uint32_t stride, sbstride;
   int L;
 };
 
-DDKS_DEV uint32_t rank1(const uint32_t* B, const uint32_t* R, uint32_t k) {
-  const uint32_t w = k >> 5, b = k & 31;
-  return R[w] + (b ? (uint32_t)__popc(B[w] & ((1u << b) - 1u)) : 0u);
+DDKS_DEV uint32_t rank1(const uint2* rec, const uint32_t* sb, uint32_t k) {
+  const uint2 r = rec[k >> 5];
+  const uint32_t b = k & 31;
+  return sb[k >> 13] + r.x + (b ? (uint32_t)__popc(r.y & ((1u << b) - 1u)) : 0u);
 }
 
-// #{k in [l, r) : value(k) >= v}
-DDKS_DEV uint32_t count_ge(const WMView& wm, uint32_t l, uint32_t r, uint32_t v) {
+// #{k in [l, r) : value(k) >= v}; Z[lv] = zeros of level lv
+DDKS_DEV uint32_t count_ge(const WMView& wm, const uint32_t* Z, uint32_t l, uint32_t r, uint32_t v) {
   const uint32_t len = r - l;
   uint32_t less = 0;
-  for (int lv = 0; lv < wm.L; ++lv) {
-    if (l >= r) break;
-    const uint32_t* B = wm.B + (size_t)lv * wm.bstride;
-    const uint32_t* R = wm.R + (size_t)lv * wm.rstride;
-    const uint32_t ol = rank1(B, R, l), orr = rank1(B, R, r);
-    const uint32_t Z = wm.n - R[wm.nw];
+  for (int lv = 0; lv < wm.L && l < r; ++lv) {
+    const uint2* rec = wm.rec + (size_t)lv * wm.stride;
+    const uint32_t* sb = wm.sb + (size_t)lv * wm.sbstride;
+    const uint32_t ol = rank1(rec, sb, l), orr = rank1(rec, sb, r);
     if ((v >> (wm.L - 1 - lv)) & 1u) {
       less += (r - l) - (orr - ol);  // the zeros of this level are smaller
-      l = Z + ol;
-      r = Z + orr;
+      l = Z[lv] + ol;
+      r = Z[lv] + orr;
     } else {
       l -= ol;
       r -= orr;
@@ -69,74 +73,143 @@ DDKS_DEV uint32_t count_ge(const WMView& wm, uint32_t l, uint32_t r, uint32_t v)
 }
 
 // Level-0 values: y ranks in dimension-0 order, for all points (matrix 0) and
-// for the P points (matrix 1, positions = P points before the position).
+// for the P points (matrix 1, positions = P points before the position);
+// hy[y] counts the P points of each y rank.
 __global__ void __launch_bounds__(kThreads)
 k_dom_init(const uint32_t* __restrict__ rank, const uint32_t* __restrict__ sorted_idx0,
            const uint32_t* __restrict__ pprefix0, int64_t N, int64_t NP, uint32_t* __restrict__ v_all,
-           uint32_t* __restrict__ v_p) {
+           uint32_t* __restrict__ v_p, uint32_t* __restrict__ hy) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t i = sorted_idx0[k];
     const uint32_t y = rank[N + i];
     v_all[k] = y;
-    if (i < (uint64_t)NP) v_p[pprefix0[k]] = y;
+    if (i < (uint64_t)NP) {
+      v_p[pprefix0[k]] = y;
+      atomicAdd(&hy[y], 1u);
+    }
   }
 }
 
-// Bit words of one level for both matrices (blockIdx.y = matrix): cnt[w] =
-// ones of word w (0 past the matrix's last word, up to nwmax + 1 words).
-__global__ void __launch_bounds__(kThreads)
-k_dom_bits(const uint32_t* __restrict__ vals, uint32_t n0, uint32_t n1, uint32_t nmax, uint32_t nwmax, int bit,
-           uint32_t* __restrict__ Bout, uint32_t* __restrict__ cnt) {
+// Bit words of one level: CTA (x, matrix) covers superblock x (kSBWords
+// words).  Writes each word's bits and its prefix within the superblock into
+// the records, and the superblock's total into sbcnt.
+__global__ void __launch_bounds__(kSBWords)
+k_dom_bits(const uint32_t* __restrict__ vals, uint32_t n0, uint32_t n1, uint32_t nmax, uint32_t recw,
+           uint32_t nsb, int bit, uint2* __restrict__ rec, uint32_t* __restrict__ sbcnt) {
+  __shared__ uint32_t cw[kSBWords];
+  __shared__ uint32_t ws[kSBWords / 32];
   const int mtx = blockIdx.y;
   const uint32_t n = mtx ? n1 : n0;
   const uint32_t* v = vals + (size_t)mtx * nmax;
-  uint32_t* B = Bout + (size_t)mtx * nwmax;
-  uint32_t* C = cnt + (size_t)mtx * (nwmax + 1);
-  const uint32_t words = nwmax + 1;
-  for (uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w0 < words;
-       w0 += (gridDim.x * blockDim.x) >> 5) {
-    const uint32_t k = w0 * 32 + (threadIdx.x & 31);
+  uint2* R = rec + (size_t)mtx * recw;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t w0 = blockIdx.x * kSBWords;
+  // warp `warp` builds words w0 + warp, w0 + warp + 8, ...
+  for (int j = warp; j < kSBWords; j += kSBWords / 32) {
+    const uint32_t k = (w0 + j) * 32 + lane;
     const bool one = k < n && ((v[k] >> bit) & 1u);
     const uint32_t word = __ballot_sync(0xffffffffu, one);
-    if ((threadIdx.x & 31) == 0) {
-      if (w0 < nwmax) B[w0] = word;
-      C[w0] = (uint32_t)__popc(word);
+    if (lane == 0) {
+      cw[j] = word;
     }
+  }
+  __syncthreads();
+  const uint32_t word = cw[threadIdx.x];
+  const uint32_t c = (uint32_t)__popc(word);
+  uint32_t incl = c;
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += x;
+  }
+  if (lane == 31) ws[warp] = incl;
+  __syncthreads();
+  uint32_t before = 0;
+  for (int q = 0; q < warp; ++q) before += ws[q];
+  const uint32_t w = w0 + threadIdx.x;
+  if (w < recw) R[w] = make_uint2(before + incl - c, word);
+  if (threadIdx.x == kSBWords - 1) sbcnt[(size_t)mtx * nsb + blockIdx.x] = before + incl;
+}
+
+// One CTA per matrix: exclusive prefix of the superblock totals into sb (nsb
+// + 1 entries, the last the level's ones); Z[matrix * kMaxLevels + lv] =
+// zeros of the level.
+__global__ void __launch_bounds__(kScanThreads)
+k_dom_sbscan(const uint32_t* __restrict__ sbcnt, uint32_t* __restrict__ sb, uint32_t n0, uint32_t n1, uint32_t nsb,
+             uint32_t sbw, int lv, uint32_t* __restrict__ Z) {
+  __shared__ uint32_t ws[kScanThreads / 32];
+  __shared__ uint32_t carry;
+  const int mtx = blockIdx.x;
+  const uint32_t n = mtx ? n1 : n0;
+  const uint32_t* C = sbcnt + (size_t)mtx * nsb;
+  uint32_t* S = sb + (size_t)mtx * sbw;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t t0 = 0; t0 < nsb + 1; t0 += kScanThreads) {  // tiles of coalesced entries
+    const uint32_t i = t0 + threadIdx.x;
+    const uint32_t c = i < nsb ? C[i] : 0u;
+    uint32_t incl = c;
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += x;
+    }
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t t = ws[lane];
+      uint32_t ti = t;
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, ti, off);
+        if (lane >= off) ti += x;
+      }
+      ws[lane] = ti - t;
+    }
+    __syncthreads();
+    const uint32_t ex = carry + ws[warp] + incl - c;
+    if (i <= nsb) S[i] = ex;
+    if (i == nsb) Z[mtx * kMaxLevels + lv] = n - ex;  // ex = all ones of the level
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) carry = ex + c;
+    __syncthreads();
   }
 }
 
 // Stable partition of one level (zeros first) into the next level's order.
 __global__ void __launch_bounds__(kThreads)
 k_dom_scatter(const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout, uint32_t n0, uint32_t n1,
-              uint32_t nmax, uint32_t nwmax, int bit, const uint32_t* __restrict__ Bl,
-              const uint32_t* __restrict__ Rl) {
+              uint32_t nmax, uint32_t recw, uint32_t sbw, int bit, int lv, const uint2* __restrict__ rec,
+              const uint32_t* __restrict__ sb, const uint32_t* __restrict__ Z) {
   const int mtx = blockIdx.y;
   const uint32_t n = mtx ? n1 : n0;
-  const uint32_t nw = (n + 31) / 32;
   const uint32_t* v = vin + (size_t)mtx * nmax;
   uint32_t* o = vout + (size_t)mtx * nmax;
-  const uint32_t* B = Bl + (size_t)mtx * nwmax;
-  const uint32_t* R = Rl + (size_t)mtx * (nwmax + 1);
-  const uint32_t Z = n - R[nw];
+  const uint2* R = rec + (size_t)mtx * recw;
+  const uint32_t* S = sb + (size_t)mtx * sbw;
+  const uint32_t z = Z[mtx * kMaxLevels + lv];
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const uint32_t x = v[k];
-    const uint32_t ones = rank1(B, R, k);
-    o[((x >> bit) & 1u) ? Z + ones : k - ones] = x;
+    const uint32_t ones = rank1(R, S, k);
+    o[((x >> bit) & 1u) ? z + ones : k - ones] = x;
   }
 }
 
 // Per origin: the four quadrant counts of each sample and the best orthant.
+// hyx[v] = P points with y rank < v.
 __global__ void __launch_bounds__(kThreads)
-k_dom_query(const uint32_t* __restrict__ rank, const uint32_t* __restrict__ pprefix0, int64_t N, int64_t NP,
-            int64_t NT, int64_t ob, int64_t oe, WMView wa, WMView wp, uint64_t* __restrict__ best,
+k_dom_query(const uint32_t* __restrict__ rank, const uint32_t* __restrict__ pprefix0,
+            const uint32_t* __restrict__ hyx, int64_t N, int64_t NP, int64_t NT, int64_t ob, int64_t oe,
+            WMView wa, WMView wp, const uint32_t* __restrict__ Zg, uint64_t* __restrict__ best,
             int32_t* __restrict__ bestj) {
+  __shared__ uint32_t Z[2 * kMaxLevels];
+  if (threadIdx.x < 2 * kMaxLevels) Z[threadIdx.x] = Zg[threadIdx.x];
+  __syncthreads();
   for (int64_t o = ob + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < oe;
        o += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t rx = rank[o], ry = rank[N + o];
     const uint32_t lxp = rx < (uint64_t)N ? pprefix0[rx] : (uint32_t)NP;  // P points with x_0 < o_0
-    const uint64_t a3 = count_ge(wa, rx, (uint32_t)N, ry);                // both >=, all points
-    const uint64_t p3 = count_ge(wp, lxp, (uint32_t)NP, ry);              // both >=, P
-    const uint64_t pyu = count_ge(wp, 0, (uint32_t)NP, ry);               // P with x_1 >= o_1
+    const uint64_t a3 = count_ge(wa, Z, rx, (uint32_t)N, ry);             // both >=, all points
+    const uint64_t p3 = count_ge(wp, Z + kMaxLevels, lxp, (uint32_t)NP, ry);  // both >=, P
+    const uint64_t pyu = (uint64_t)NP - hyx[ry];                          // P with x_1 >= o_1
     const uint64_t axu = (uint64_t)N - rx, pxu = (uint64_t)NP - lxp;      // x_0 >= o_0
     const uint64_t ayu = (uint64_t)N - ry;                                // x_1 >= o_1
     uint64_t cp[4], ca[4];
@@ -179,50 +252,64 @@ cudaError_t ddks_launch_dominance(ddks_ctx* ctx, const uint32_t* rank, int64_t N
   int n = 0;
   int L = 1;
   while (((int64_t)1 << L) < N) ++L;  // values (ranks) < N <= 2^L
+  if (L > kMaxLevels) return cudaErrorInvalidValue;
   const uint32_t n0 = (uint32_t)N, n1 = (uint32_t)NP, nmax = n0;
-  const uint32_t nwmax = (nmax + 31) / 32;
-  // scratch: values [2 bufs][2 matrices][nmax], bits [L][2][nwmax], prefixes
-  // [L][2][nwmax + 1], counts [2][nwmax + 1], scan temp
-  const size_t scan_tmp = ddks_scan_tmp_elems(2, nwmax + 1);
-  const size_t words = (size_t)4 * nmax + (size_t)L * 2 * nwmax + (size_t)L * 2 * (nwmax + 1) +
-                       2 * (size_t)(nwmax + 1) + scan_tmp;
+  // records per matrix and level: whole superblocks covering position nmax
+  // (rank1 may look at word nmax / 32)
+  const uint32_t nsb = nmax / (32 * kSBWords) + 1;
+  const uint32_t recw = nsb * kSBWords;
+  const uint32_t sbw = nsb + 1;
+  // scratch (u32 words): values [2 bufs][2 matrices][nmax]; records
+  // [L][2][recw] (2 words each); superblock prefixes [L][2][sbw]; superblock
+  // totals [2][nsb]; Z [2][kMaxLevels]; P counts per y rank [N + 1] and their
+  // prefix [N + 1]
+  const size_t recwords = (size_t)L * 2 * recw * 2;
+  const size_t scan_tmp = ddks_scan_tmp_elems(1, N + 1);
+  const size_t words = (size_t)4 * nmax + recwords + (size_t)L * 2 * sbw + 2 * (size_t)nsb + 2 * kMaxLevels +
+                       2 * (size_t)(N + 1) + scan_tmp + 4;
   int rc = ctx->dom_work.reserve(ctx, 4 * words);
   if (rc) return cudaErrorMemoryAllocation;
   uint32_t* base = (uint32_t*)ctx->dom_work.ptr;
   uint32_t* vbuf[2] = {base, base + 2 * (size_t)nmax};
-  uint32_t* Bw = base + 4 * (size_t)nmax;
-  uint32_t* Rw = Bw + (size_t)L * 2 * nwmax;
-  uint32_t* cnt = Rw + (size_t)L * 2 * (nwmax + 1);
-  uint32_t* tmp = cnt + 2 * (size_t)(nwmax + 1);
+  uint2* rec = reinterpret_cast<uint2*>(base + 4 * (size_t)nmax);  // 8-byte aligned: 4 nmax words
+  uint32_t* sbp = base + 4 * (size_t)nmax + recwords;
+  uint32_t* sbcnt = sbp + (size_t)L * 2 * sbw;
+  uint32_t* Zg = sbcnt + 2 * (size_t)nsb;
+  uint32_t* hy = Zg + 2 * kMaxLevels;
+  uint32_t* hyx = hy + (N + 1);
+  uint32_t* tmp = hyx + (N + 1);
   const uint32_t* sorted_idx0 = (const uint32_t*)ctx->sidx0.ptr;
   const uint32_t* pprefix0 = (const uint32_t*)ctx->pfx0.ptr;
+  cudaError_t e = cudaMemsetAsync(hy, 0, 4 * (size_t)(N + 1), st);
+  if (e != cudaSuccess) return e;
   k_dom_init<<<grid_for(N, kThreads, ctx->num_sms * 8), kThreads, 0, st>>>(rank, sorted_idx0, pprefix0, N, NP,
-                                                                         vbuf[0], vbuf[0] + nmax);
+                                                                         vbuf[0], vbuf[0] + nmax, hy);
   ++n;
-  const dim3 gw((unsigned)grid_for((int64_t)(nwmax + 1) * 32, kThreads, ctx->num_sms * 8), 2);
+  int sl = 0;
+  e = ddks_scan_rows(hy, hyx, 1, N + 1, true, tmp, st, &sl);
+  if (e != cudaSuccess) return e;
+  n += sl;
   const dim3 gs((unsigned)grid_for(nmax, kThreads, ctx->num_sms * 8), 2);
   for (int lv = 0; lv < L; ++lv) {
     const int bit = L - 1 - lv;
-    uint32_t* Bl = Bw + (size_t)lv * 2 * nwmax;
-    uint32_t* Rl = Rw + (size_t)lv * 2 * (nwmax + 1);
-    k_dom_bits<<<gw, kThreads, 0, st>>>(vbuf[lv & 1], n0, n1, nmax, nwmax, bit, Bl, cnt);
-    ++n;
-    int sl = 0;
-    cudaError_t e = ddks_scan_rows(cnt, Rl, 2, nwmax + 1, true, tmp, st, &sl);
-    if (e != cudaSuccess) return e;
-    n += sl;
+    uint2* rl = rec + (size_t)lv * 2 * recw;
+    uint32_t* sl_ = sbp + (size_t)lv * 2 * sbw;
+    k_dom_bits<<<dim3(nsb, 2), kSBWords, 0, st>>>(vbuf[lv & 1], n0, n1, nmax, recw, nsb, bit, rl, sbcnt);
+    k_dom_sbscan<<<2, kScanThreads, 0, st>>>(sbcnt, sl_, n0, n1, nsb, sbw, lv, Zg);
+    n += 2;
     if (lv + 1 < L) {
-      k_dom_scatter<<<gs, kThreads, 0, st>>>(vbuf[lv & 1], vbuf[(lv + 1) & 1], n0, n1, nmax, nwmax, bit, Bl, Rl);
+      k_dom_scatter<<<gs, kThreads, 0, st>>>(vbuf[lv & 1], vbuf[(lv + 1) & 1], n0, n1, nmax, recw, sbw, bit, lv, rl,
+                                             sl_, Zg);
       ++n;
     }
   }
-  // query views: levels are [lv][matrix][words]
-  const WMView wa{Bw, Rw, n0, (n0 + 31) / 32, 2 * nwmax, 2 * (nwmax + 1), L};
-  const WMView wp{Bw + nwmax, Rw + (nwmax + 1), n1, (n1 + 31) / 32, 2 * nwmax, 2 * (nwmax + 1), L};
+  // query views: levels are [lv][matrix][recw records], [lv][matrix][sbw prefixes]
+  const WMView wa{rec, sbp, 2 * recw, 2 * sbw, L};
+  const WMView wp{rec + recw, sbp + sbw, 2 * recw, 2 * sbw, L};
   const int64_t no = oe - ob;
   if (no > 0) {
-    k_dom_query<<<grid_for(no, kThreads, ctx->num_sms * 16), kThreads, 0, st>>>(rank, pprefix0, N, NP, NT, ob, oe,
-                                                                              wa, wp, best, bestj);
+    k_dom_query<<<grid_for(no, kThreads, ctx->num_sms * 16), kThreads, 0, st>>>(rank, pprefix0, hyx, N, NP, NT, ob,
+                                                                              oe, wa, wp, Zg, best, bestj);
     ++n;
   }
   if (launches) *launches += n;
