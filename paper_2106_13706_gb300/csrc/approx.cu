@@ -80,9 +80,9 @@ template <typename V> struct NativeKey;
 template <> struct NativeKey<float> {
   using K = uint32_t;
   static DDKS_DEV K key(float v) { return (K)ddks::order_key(v); }
-  static DDKS_DEV K raw(float v) {
-    const uint32_t u = __float_as_uint(v);
-    return (u >> 31) ? ~u : (u | 0x80000000u);
+  static DDKS_DEV K raw(float v) {  // = u ^ (sign ? 0xFFFFFFFF : 0x80000000), two ALU ops
+    const int32_t i = __float_as_int(v);
+    return (K)(i ^ ((i >> 31) | (int32_t)0x80000000));
   }
   static DDKS_DEV float value(K k) { return __uint_as_float((k >> 31) ? (k & 0x7FFFFFFFu) : ~k); }
 };
@@ -90,8 +90,8 @@ template <> struct NativeKey<double> {
   using K = ull;
   static DDKS_DEV K key(double v) { return (K)ddks::order_key(v); }
   static DDKS_DEV K raw(double v) {
-    const ull u = (ull)__double_as_longlong(v);
-    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+    const long long i = __double_as_longlong(v);
+    return (K)(i ^ ((i >> 63) | (long long)0x8000000000000000ll));
   }
   static DDKS_DEV double value(K k) { return key_value(k); }
 };

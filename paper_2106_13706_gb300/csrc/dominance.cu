@@ -36,13 +36,14 @@ constexpr int kScanThreads = 1024;
 constexpr int kMaxLevels = 32;
 constexpr int kSBWords = 256;  // words per superblock (8192 positions), one CTA of k_dom_bits
 
-// One wavelet matrix in device memory.  Level lv: records at rec + lv * stride,
-// record w = {ones in the words of its superblock before w, bit word w};
-// superblock prefixes at sb + lv * sbstride (ones before each superblock).
+// One wavelet matrix in device memory for the queries.  Level lv: records at
+// rec + lv * stride, record w = {ones before word w, bit word w}.  (While a
+// level is built its records count only the ones within their superblock of
+// kSBWords words, with the superblock prefixes beside them; k_dom_finalize
+// adds those in once every level exists.)
 struct WMView {
   const uint2* rec;
-  const uint32_t* sb;
-  uint32_t stride, sbstride;
+  uint32_t stride;
   int L;
 };
 
@@ -52,14 +53,20 @@ DDKS_DEV uint32_t rank1(const uint2* rec, const uint32_t* sb, uint32_t k) {
   return sb[k >> 13] + r.x + (b ? (uint32_t)__popc(r.y & ((1u << b) - 1u)) : 0u);
 }
 
-// #{k in [l, r) : value(k) >= v}; Z[lv] = zeros of level lv
+// After k_dom_finalize the records hold absolute prefixes: one load per rank.
+DDKS_DEV uint32_t rank1_abs(const uint2* rec, uint32_t k) {
+  const uint2 r = rec[k >> 5];
+  const uint32_t b = k & 31;
+  return r.x + (b ? (uint32_t)__popc(r.y & ((1u << b) - 1u)) : 0u);
+}
+
+// #{k in [l, r) : value(k) >= v}; Z[lv] = zeros of level lv (finalized records)
 DDKS_DEV uint32_t count_ge(const WMView& wm, const uint32_t* Z, uint32_t l, uint32_t r, uint32_t v) {
   const uint32_t len = r - l;
   uint32_t less = 0;
   for (int lv = 0; lv < wm.L && l < r; ++lv) {
     const uint2* rec = wm.rec + (size_t)lv * wm.stride;
-    const uint32_t* sb = wm.sb + (size_t)lv * wm.sbstride;
-    const uint32_t ol = rank1(rec, sb, l), orr = rank1(rec, sb, r);
+    const uint32_t ol = rank1_abs(rec, l), orr = rank1_abs(rec, r);
     if ((v >> (wm.L - 1 - lv)) & 1u) {
       less += (r - l) - (orr - ol);  // the zeros of this level are smaller
       l = Z[lv] + ol;
@@ -104,14 +111,20 @@ k_dom_bits(const uint32_t* __restrict__ vals, uint32_t n0, uint32_t n1, uint32_t
   uint2* R = rec + (size_t)mtx * recw;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t w0 = blockIdx.x * kSBWords;
-  // warp `warp` builds words w0 + warp, w0 + warp + 8, ...
-  for (int j = warp; j < kSBWords; j += kSBWords / 32) {
-    const uint32_t k = (w0 + j) * 32 + lane;
-    const bool one = k < n && ((v[k] >> bit) & 1u);
-    const uint32_t word = __ballot_sync(0xffffffffu, one);
-    if (lane == 0) {
-      cw[j] = word;
-    }
+  // warp `warp` builds words w0 + warp + 8 q, q < 32: all loads first, then
+  // the ballots
+  constexpr int kPerWarp = kSBWords / (kSBWords / 32);
+  uint32_t x[kPerWarp];
+#pragma unroll
+  for (int q = 0; q < kPerWarp; ++q) {
+    const uint32_t k = (w0 + warp + 8 * q) * 32 + lane;
+    x[q] = k < n ? v[k] : 0u;
+  }
+#pragma unroll
+  for (int q = 0; q < kPerWarp; ++q) {
+    const uint32_t k = (w0 + warp + 8 * q) * 32 + lane;
+    const uint32_t word = __ballot_sync(0xffffffffu, k < n && ((x[q] >> bit) & 1u));
+    if (lane == 0) cw[warp + 8 * q] = word;
   }
   __syncthreads();
   const uint32_t word = cw[threadIdx.x];
@@ -171,6 +184,19 @@ k_dom_sbscan(const uint32_t* __restrict__ sbcnt, uint32_t* __restrict__ sb, uint
     __syncthreads();
     if (threadIdx.x == kScanThreads - 1) carry = ex + c;
     __syncthreads();
+  }
+}
+
+// Adds the superblock prefixes into the records of every level and matrix
+// (recs records of recw per matrix and level), for the queries.
+__global__ void __launch_bounds__(kThreads)
+k_dom_finalize(uint2* __restrict__ rec, const uint32_t* __restrict__ sb, uint64_t recs, uint32_t recw,
+               uint32_t sbw) {
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < recs;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t row = t / recw;  // level * 2 + matrix
+    const uint32_t w = (uint32_t)(t - row * recw);
+    rec[t].x += sb[row * sbw + (w / kSBWords)];
   }
 }
 
@@ -303,9 +329,12 @@ cudaError_t ddks_launch_dominance(ddks_ctx* ctx, const uint32_t* rank, int64_t N
       ++n;
     }
   }
+  k_dom_finalize<<<grid_for((int64_t)L * 2 * recw, kThreads, ctx->num_sms * 8), kThreads, 0, st>>>(
+      rec, sbp, (uint64_t)L * 2 * recw, recw, sbw);
+  ++n;
   // query views: levels are [lv][matrix][recw records], [lv][matrix][sbw prefixes]
-  const WMView wa{rec, sbp, 2 * recw, 2 * sbw, L};
-  const WMView wp{rec + recw, sbp + sbw, 2 * recw, 2 * sbw, L};
+  const WMView wa{rec, 2 * recw, L};
+  const WMView wp{rec + recw, 2 * recw, L};
   const int64_t no = oe - ob;
   if (no > 0) {
     k_dom_query<<<grid_for(no, kThreads, ctx->num_sms * 16), kThreads, 0, st>>>(rank, pprefix0, hyx, N, NP, NT, ob,

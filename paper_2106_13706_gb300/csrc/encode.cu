@@ -22,8 +22,9 @@
 
 namespace {
 
-constexpr int kChunk = 2048;
-constexpr int kChunkThreads = 256;  // 8 positions per thread
+constexpr int kChunk = 2048;       // sorted chunks and merge tiles
+constexpr int kSortEach = 8;       // sorted positions per thread of k_chunk_sort
+constexpr int kChunkThreads = kChunk / kSortEach;
 constexpr int64_t kMaxMultiChunks = 4;  // above this (N > 8192), merge passes
 
 template <typename V>
@@ -52,13 +53,17 @@ DDKS_DEV bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
 // of the same warp (shuffles), strides >= 256 go through shared memory.
 // With out_p, dimensions m < pfx_dims also write out_p[m * Npad + base + p] =
 // #{q < p : sorted element q of the chunk is a P point}.
-__global__ void __launch_bounds__(kChunkThreads)
+template <int CH>
+__global__ void __launch_bounds__(CH / kSortEach)
 k_chunk_sort(const uint64_t* __restrict__ keys, int64_t N, int64_t Npad, int64_t NP,
              uint64_t* __restrict__ out_k, uint32_t* __restrict__ out_i, uint32_t* __restrict__ out_p,
              int pfx_dims) {
-  constexpr int E = kChunk / kChunkThreads;  // 8
-  __shared__ uint64_t sk[kChunk];
-  __shared__ uint32_t si[kChunk];
+  constexpr int E = kSortEach;
+  constexpr int kChunk = CH;  // this kernel's chunk
+  constexpr int kChunkThreads = CH / kSortEach;
+  extern __shared__ __align__(16) unsigned char cs_raw[];
+  uint64_t* sk = reinterpret_cast<uint64_t*>(cs_raw);   // [CH]
+  uint32_t* si = reinterpret_cast<uint32_t*>(sk + CH);  // [CH]
   __shared__ uint32_t wsum[kChunkThreads / 32 + 1];
   const int m = blockIdx.y;
   const int t = threadIdx.x;
@@ -179,8 +184,11 @@ k_chunk_sort(const uint64_t* __restrict__ keys, int64_t N, int64_t Npad, int64_t
 // count of P points (index < NP) before it: preA(i) + preB(j) for the i A and
 // j B elements that precede it, preX(p) being X's carried count at p (for p at
 // the end of X: the last count plus the last element's flag).
-constexpr int kMergeThreads = 256;
-constexpr int kMergeEach = kChunk / kMergeThreads;  // 8 outputs per thread
+constexpr int kMergeEach = 8;  // outputs per thread
+
+// Outputs per merge CTA: 1024 for small inputs (twice the CTAs, half the
+// latency chain each), 2048 otherwise.
+int merge_tile_for(int64_t N) { return N <= 131072 ? 1024 : 2048; }
 
 DDKS_DEV int64_t merge_path(const uint64_t* Ak, const uint32_t* Ai, int64_t na, const uint64_t* Bk,
                             const uint32_t* Bi, int64_t nb, int64_t D) {
@@ -224,12 +232,14 @@ DDKS_DEV int64_t merge_path_warp(const uint64_t* Ak, const uint32_t* Ai, int64_t
   return lo;
 }
 
-__global__ void __launch_bounds__(kMergeThreads)
+template <int TILE>
+__global__ void __launch_bounds__(TILE / kMergeEach)
 k_merge_tile(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ in_i,
              uint64_t* __restrict__ out_k, uint32_t* __restrict__ out_i,
              const uint32_t* __restrict__ in_p, uint32_t* __restrict__ out_p,
              int64_t Npad, int64_t NP, int64_t L, int pfx_dims, int64_t N, uint32_t* __restrict__ rank,
              uint32_t* __restrict__ sorted_idx0, uint32_t* __restrict__ pprefix0) {
+  constexpr int kChunk = TILE;  // outputs of this CTA (runs stay multiples of the 2048-element chunks)
   __shared__ uint64_t sk[kChunk];
   __shared__ uint32_t si[kChunk];
   __shared__ uint32_t sp[kChunk + 2];
@@ -355,11 +365,14 @@ k_merge_tile(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ in_
 // (one lower_bound per chunk), and for dimension 0 the position of (key_i, i)
 // in the full sorted order, which places i in sorted_idx0.  The searches of up
 // to 8 chunks advance together (independent loads in flight).
+template <int CH>
 __global__ void k_rank_multi(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ ck,
                              const uint32_t* __restrict__ ci, const uint32_t* __restrict__ cpfx,
                              int64_t N, int64_t NPc, int64_t Npad, int d, uint32_t* __restrict__ rank,
                              uint32_t* __restrict__ sorted_idx0, uint32_t* __restrict__ pprefix0) {
   constexpr int kG = 8;
+  constexpr int kChunk = CH;
+  constexpr int kSteps = CH == 2048 ? 12 : 14;  // at most log2(CH) + 1 halvings
   const int64_t total = N * d;
   const int nch = (int)(Npad / kChunk);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -374,7 +387,7 @@ __global__ void k_rank_multi(const uint64_t* __restrict__ keys, const uint64_t* 
 #pragma unroll
       for (int g = 0; g < kG; ++g) { lo[g] = 0; hi[g] = c0 + g < nch ? kChunk : 0; }
       const uint64_t* K = ck + m * Npad + (int64_t)c0 * kChunk;
-      for (int step = 0; step < 12; ++step) {  // 2^11 = kChunk: at most 12 halvings
+      for (int step = 0; step < kSteps; ++step) {
 #pragma unroll
         for (int g = 0; g < kG; ++g) {
           if (lo[g] < hi[g]) {
@@ -391,7 +404,7 @@ __global__ void k_rank_multi(const uint64_t* __restrict__ keys, const uint64_t* 
         int lo2[kG], hi2[kG];
 #pragma unroll
         for (int g = 0; g < kG; ++g) { lo2[g] = lo[g]; hi2[g] = c0 + g < nch ? kChunk : 0; }
-        for (int step = 0; step < 12; ++step) {
+        for (int step = 0; step < kSteps; ++step) {
 #pragma unroll
           for (int g = 0; g < kG; ++g) {
             if (lo2[g] < hi2[g]) {
@@ -441,9 +454,24 @@ cudaError_t ddks_launch_encode(const void* P, const void* T, int64_t NP, int64_t
   return cudaGetLastError();
 }
 
+namespace {
+// 2048-element chunks throughout: 8192-element chunks (one CTA of 1024
+// threads each) measured slower on both the mid-size inputs (too few CTAs,
+// searches of 14 steps) and the large ones (more sorting work per element).
+int64_t chunk_for(int64_t) { return kChunk; }
+
+cudaError_t launch_chunk_sort(int64_t CH, dim3 g, const uint64_t* keys, int64_t N, int64_t Npad, int64_t NP,
+                              uint64_t* out_k, uint32_t* out_i, uint32_t* out_p, int pfx_dims, cudaStream_t st) {
+  const size_t smem = (size_t)CH * 12;
+  k_chunk_sort<kChunk><<<g, kChunk / kSortEach, smem, st>>>(keys, N, Npad, NP, out_k, out_i, out_p, pfx_dims);
+  return cudaGetLastError();
+}
+}  // namespace
+
 size_t ddks_rank_scratch_elems(int64_t N) {
-  const int64_t chunks = (N + kChunk - 1) / kChunk;
-  return (size_t)(chunks * kChunk);
+  const int64_t CH = chunk_for(N);
+  const int64_t chunks = (N + CH - 1) / CH;
+  return (size_t)(chunks * CH);
 }
 
 // keys: [d][N].  tmp buffers: d * Npad elements each.  rank: [d][N].
@@ -457,27 +485,36 @@ cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int64_t NP, int d,
                              uint32_t* rank, uint32_t* sorted_idx0, uint32_t* pprefix0, uint32_t* cpfx,
                              int* pfx_done, cudaStream_t st, int* launches) {
   const int64_t Npad = (int64_t)ddks_rank_scratch_elems(N);
-  const int64_t chunks = Npad / kChunk;
-  dim3 g((unsigned)chunks, (unsigned)d);
+  const int64_t CH = chunk_for(N);
+  const int64_t chunks = Npad / CH;
   const bool pfx = sorted_idx0 && pprefix0 && cpfx;
   if (pfx_done) *pfx_done = pfx ? 1 : 0;
   uint32_t* cp = pfx ? cpfx : nullptr;             // [Npad] P prefixes, dimension 0
   uint32_t* cp2 = pfx ? cpfx + Npad : nullptr;     // [Npad] the other merge buffer
-  k_chunk_sort<<<g, kChunkThreads, 0, st>>>(keys, N, Npad, NP, tmp_keys, tmp_idx, cp, 1);
+  cudaError_t e = launch_chunk_sort(CH, dim3((unsigned)chunks, (unsigned)d), keys, N, Npad, NP, tmp_keys, tmp_idx,
+                                    cp, 1, st);
+  if (e != cudaSuccess) return e;
   int n = 1;
   if (chunks <= kMaxMultiChunks) {
-    k_rank_multi<<<grid_for(N * d, 256), 256, 0, st>>>(keys, tmp_keys, tmp_idx, cp, N, NP, Npad, d, rank,
-                                                       sorted_idx0, pfx ? pprefix0 : nullptr);
+    k_rank_multi<kChunk><<<grid_for(N * d, 256), 256, 0, st>>>(keys, tmp_keys, tmp_idx, cp, N, NP, Npad, d, rank,
+                                                               sorted_idx0, pfx ? pprefix0 : nullptr);
     if (launches) *launches += 2;
     return cudaGetLastError();
   }
+  const int TILE = merge_tile_for(N);
+  const int64_t tiles = Npad / TILE;
   uint64_t *ck = tmp_keys, *nk = tmp_keys2;
   uint32_t *ci = tmp_idx, *ni = tmp_idx2;
-  for (int64_t L = kChunk; L < Npad; L <<= 1) {
+  for (int64_t L = CH; L < Npad; L <<= 1) {
     const bool last = 2 * L >= Npad;  // the final pass writes ranks instead of merged arrays
-    k_merge_tile<<<dim3((unsigned)chunks, (unsigned)d), kMergeThreads, 0, st>>>(
-        ck, ci, nk, ni, cp, cp2, Npad, NP, L, 1, N, last ? rank : nullptr, last ? sorted_idx0 : nullptr,
-        last && pfx ? pprefix0 : nullptr);
+    if (TILE == 1024)
+      k_merge_tile<1024><<<dim3((unsigned)tiles, (unsigned)d), 1024 / kMergeEach, 0, st>>>(
+          ck, ci, nk, ni, cp, cp2, Npad, NP, L, 1, N, last ? rank : nullptr, last ? sorted_idx0 : nullptr,
+          last && pfx ? pprefix0 : nullptr);
+    else
+      k_merge_tile<2048><<<dim3((unsigned)tiles, (unsigned)d), 2048 / kMergeEach, 0, st>>>(
+          ck, ci, nk, ni, cp, cp2, Npad, NP, L, 1, N, last ? rank : nullptr, last ? sorted_idx0 : nullptr,
+          last && pfx ? pprefix0 : nullptr);
     ++n;
     uint64_t* tk = ck; ck = nk; nk = tk;
     uint32_t* ti = ci; ci = ni; ni = ti;
@@ -497,16 +534,22 @@ cudaError_t ddks_launch_sort_segments(const uint64_t* keys, int64_t N, int64_t N
                                       uint32_t* p2, const uint64_t** out_k, const uint32_t** out_i,
                                       const uint32_t** out_p, cudaStream_t st, int* launches) {
   const int64_t Npad = (int64_t)ddks_rank_scratch_elems(N);
-  const int64_t chunks = Npad / kChunk;
-  k_chunk_sort<<<dim3((unsigned)chunks, (unsigned)S), kChunkThreads, 0, st>>>(keys, N, Npad, NP, k1, i1,
-                                                                                  p1, S);
+  const int64_t CH = chunk_for(N);
+  cudaError_t e = launch_chunk_sort(CH, dim3((unsigned)(Npad / CH), (unsigned)S), keys, N, Npad, NP, k1, i1, p1, S,
+                                    st);
+  if (e != cudaSuccess) return e;
   int n = 1;
+  const int TILE = merge_tile_for(N);
+  const int64_t tiles = Npad / TILE;
   uint64_t *ck = k1, *nk = k2;
   uint32_t *ci = i1, *ni = i2, *cp = p1, *np = p2;
-  for (int64_t L = kChunk; L < Npad; L <<= 1) {
-    k_merge_tile<<<dim3((unsigned)chunks, (unsigned)S), kMergeThreads, 0, st>>>(ck, ci, nk, ni, cp, np, Npad, NP,
-                                                                                 L, S, N, nullptr, nullptr,
-                                                                                 nullptr);
+  for (int64_t L = CH; L < Npad; L <<= 1) {
+    if (TILE == 1024)
+      k_merge_tile<1024><<<dim3((unsigned)tiles, (unsigned)S), 1024 / kMergeEach, 0, st>>>(
+          ck, ci, nk, ni, cp, np, Npad, NP, L, S, N, nullptr, nullptr, nullptr);
+    else
+      k_merge_tile<2048><<<dim3((unsigned)tiles, (unsigned)S), 2048 / kMergeEach, 0, st>>>(
+          ck, ci, nk, ni, cp, np, Npad, NP, L, S, N, nullptr, nullptr, nullptr);
     ++n;
     uint64_t* tk = ck; ck = nk; nk = tk;
     uint32_t* ti = ci; ci = ni; ni = ti;
