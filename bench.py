@@ -479,7 +479,7 @@ def run_approx(args):
         ach = nbytes / (st[1] * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs") or 6800.0
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": None, "kernel": "voxel pass (k_vdks_thresholds + k_vdks_voxel)",
+                "traffic": load_traffic("vdks_voxel"), "kernel": "voxel pass (k_vdks_thresholds + k_vdks_voxel)",
                 "kernel_ms": st[1], "algorithmic_bytes": nbytes,
                 "peak_basis": "measured copy bandwidth" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s",
                 "range_stage": {"kernel": "k_minmax", "ms": st[0],
