@@ -190,3 +190,17 @@ def test_errors(torch, ctx):
     # the context stays usable after the errors
     _vdks_same(ctx.vdks(_dev(torch, P), _dev(torch, T), 4), orc.vdks(P, T, 4))
     _rdks_same(ctx.rdks(_dev(torch, P), _dev(torch, T)), orc.rdks(P, T))
+
+
+def test_vdks_bench_workload_full_size(torch, ctx):
+    # the bench's vdKS workload itself (8M + 8M float32, 32 voxels per
+    # dimension: bulk-copy voxel pass, CTA-private histograms), checked whole
+    P, T = wl.gaussian_pair(0, 8_000_000, 8_000_000, 3, shift=0.2)
+    _vdks_same(ctx.vdks(_dev(torch, P), _dev(torch, T), 32), orc.vdks(P, T, 32))
+
+
+def test_rdks_bench_workload_full_size(torch, ctx):
+    # the bench's large rdKS workload (1M + 1M float32, d = 3), checked whole
+    P, T = wl.gaussian_pair(0, 1_000_000, 1_000_000, 3, shift=0.05)
+    _rdks_same(ctx.rdks(_dev(torch, P), _dev(torch, T)), orc.rdks(P, T))
+
