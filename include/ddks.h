@@ -81,6 +81,9 @@ typedef struct {
   int32_t wait_limit_ms;      /* bound on any host or device wait (0 = 10000) */
   const char* tune_cache;     /* autotuner cache file (NULL = $DDKS_TUNE_CACHE, else none) */
   int32_t graphs;             /* 1 (default): replay CUDA graphs for repeated calls, see below; 0 = off */
+  int64_t radix_min_n;        /* pooled sizes N from which the key sorts (the per-dimension ranks of the
+                                 exact paths, the rdKS distance orders) run as LSD radix sorts instead of
+                                 chunk sorts + merges; 0 = the built-in default, -1 = never */
 } ddks_config;
 
 typedef struct {

@@ -41,7 +41,7 @@ class ddks_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_int32),
                 ("wait_limit_ms", ctypes.c_int32), ("tune_cache", ctypes.c_char_p),
-                ("graphs", ctypes.c_int32)]
+                ("graphs", ctypes.c_int32), ("radix_min_n", ctypes.c_int64)]
 
 
 class ddks_result(ctypes.Structure):
@@ -183,7 +183,7 @@ def _pair(P, T):
 
 # ------------------------------------------------------------------ entry points
 def ddks_ctx_create(device=-1, path=PATH_AUTO, hbm_budget_bytes=0, max_batch=0, wait_limit_ms=0,
-                    tune_cache=None, graphs=True):
+                    tune_cache=None, graphs=True, radix_min_n=0):
     lib = load()
     cfg = ddks_config()
     lib.ddks_config_default(ctypes.byref(cfg))
@@ -191,6 +191,7 @@ def ddks_ctx_create(device=-1, path=PATH_AUTO, hbm_budget_bytes=0, max_batch=0, 
     cfg.hbm_budget_bytes, cfg.max_batch, cfg.wait_limit_ms = hbm_budget_bytes, max_batch, wait_limit_ms
     cfg.tune_cache = tune_cache.encode() if tune_cache else None
     cfg.graphs = 1 if graphs else 0
+    cfg.radix_min_n = radix_min_n
     h = ctypes.c_void_p()
     _check(lib.ddks_ctx_create(ctypes.byref(cfg), ctypes.byref(h)), what="ddks_ctx_create")
     return h

@@ -784,7 +784,7 @@ k_rdks_dist_warp(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, i
   }
 }
 
-// grid (x, S): corner blockIdx.y.  K, I, Pf are the sorted segments [S][Npad].
+// grid (x, S): corner blockIdx.y.  K, I, Pf are the sorted segments, rows Npad apart.
 __global__ void __launch_bounds__(kThreads)
 k_rdks_walk(const ull* __restrict__ K, const uint32_t* __restrict__ I, const uint32_t* __restrict__ Pf,
             int64_t N, int64_t Npad, int64_t NP, int64_t NT, ull* __restrict__ per_corner) {
@@ -1202,6 +1202,8 @@ int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
   if ((rc = ctx->ti2.reserve(ctx, 4 * segs))) return out->status = rc;
   if ((rc = ctx->apx_cnt.reserve(ctx, 4 * segs))) return out->status = rc;  // P prefixes
   if ((rc = ctx->apx_U.reserve(ctx, 4 * segs))) return out->status = rc;
+  const bool radix = N > 1024 && ddks_use_radix(ctx, N);
+  if (radix && (rc = ctx->radix.reserve(ctx, 4 * ddks_radix_scratch_words(N, S, S)))) return out->status = rc;
   // warp kernel: shared memory of 2 * d doubles per warp
   int nwb = (int)((96 * 1024) / (16 * (size_t)d));
   nwb = nwb < 1 ? 1 : (nwb > 2 ? 2 : nwb);
@@ -1274,16 +1276,27 @@ int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
     const uint64_t* sk;
     const uint32_t *si, *sp;
     int n = 0;
-    ee = ddks_launch_sort_segments((const uint64_t*)keys, N, NP, S, (uint64_t*)ctx->tk1.ptr, (uint32_t*)ctx->ti1.ptr,
-                                   (uint32_t*)ctx->apx_cnt.ptr, (uint64_t*)ctx->tk2.ptr, (uint32_t*)ctx->ti2.ptr,
-                                   (uint32_t*)ctx->apx_U.ptr, &sk, &si, &sp, s, &n);
+    int64_t rstride = Npad;  // row stride of the sorted keys, indices and P prefixes
+    if (radix) {
+      uint32_t* rsx = (uint32_t*)ctx->radix.ptr;
+      ee = ddks_radix_sort((const uint64_t*)keys, (uint64_t*)ctx->tk1.ptr, (uint32_t*)ctx->ti1.ptr,
+                           (uint64_t*)ctx->tk2.ptr, (uint32_t*)ctx->ti2.ptr, N, N, S, 64, rsx, &sk, &si, s, &n);
+      if (ee == cudaSuccess)
+        ee = ddks_radix_ranks(sk, si, N, N, S, NP, nullptr, (uint32_t*)ctx->apx_cnt.ptr, S, nullptr, rsx, s, &n);
+      sp = (const uint32_t*)ctx->apx_cnt.ptr;
+      rstride = N;
+    } else {
+      ee = ddks_launch_sort_segments((const uint64_t*)keys, N, NP, S, (uint64_t*)ctx->tk1.ptr, (uint32_t*)ctx->ti1.ptr,
+                                     (uint32_t*)ctx->apx_cnt.ptr, (uint64_t*)ctx->tk2.ptr, (uint32_t*)ctx->ti2.ptr,
+                                     (uint32_t*)ctx->apx_U.ptr, &sk, &si, &sp, s, &n);
+    }
     ctx->launches += n;
     if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "rdks sort");
     ddks_stage_mark(ctx, 2, s);
     int gx = grid_cap(N, kThreads, ctx->num_sms * 8);
     const int per = (ctx->num_sms * 8 + S - 1) / S;
     if (gx > per) gx = per < 1 ? 1 : per;
-    k_rdks_walk<<<dim3((unsigned)gx, (unsigned)S), kThreads, 0, s>>>((const ull*)sk, si, sp, N, Npad, NP, NT,
+    k_rdks_walk<<<dim3((unsigned)gx, (unsigned)S), kThreads, 0, s>>>((const ull*)sk, si, sp, N, rstride, NP, NT,
                                                                       pc);
     k_rdks_final<<<1, kThreads, 0, s>>>(pc, S, (ull*)sm);
     ctx->launches += 2;

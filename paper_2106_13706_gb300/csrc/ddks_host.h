@@ -54,6 +54,7 @@ struct ddks_ctx {
   DevBuf inP, inT, keys, tk1, tk2, ti1, ti2, rank, sidx0, best, bestj, out3, flags;
   DevBuf pfx0;         // P points before each dimension-0 sorted position (+ chunk scratch)
   bool pfx0_valid = false;  // pfx0 holds the current problem's prefix
+  const uint32_t* sorted_rows = nullptr;  // K0 by radix sort: pooled indices per dimension in sorted order, [d][N]
   DevBuf reg_words, reg_meta;                   // register path
   DevBuf warp_words;                            // warp path: packed rank pairs
   DevBuf perm_keys, perm_labels, perm_best, perm_codes;  // permutation test
@@ -61,6 +62,7 @@ struct ddks_ctx {
   DevBuf batch_desc, batch_work;                // batched launch
   DevBuf apx_small, apx_cnt, apx_U, apx_hist;   // vdKS / rdKS (approx.cu)
   DevBuf dom_work;                              // d = 2 range-query path (dominance.cu)
+  DevBuf radix;                                 // radix sort counts / offsets / flags (radix.cu)
   unsigned long long* h_out = nullptr;          // pinned, 64 entries
   void* h_stage = nullptr;                      // pinned staging for uploads
   size_t h_stage_bytes = 0;
@@ -83,7 +85,8 @@ struct ddks_ctx {
   std::vector<DevBuf*> all_bufs() {
     return {&inP, &inT, &keys, &tk1, &tk2, &ti1, &ti2, &rank, &sidx0, &pfx0, &best, &bestj, &out3,
             &flags, &reg_words, &reg_meta, &warp_words, &perm_keys, &perm_labels, &perm_best, &perm_codes,
-            &sig_cells, &sig_logp, &batch_desc, &batch_work, &apx_small, &apx_cnt, &apx_U, &apx_hist, &dom_work};
+            &sig_cells, &sig_logp, &batch_desc, &batch_work, &apx_small, &apx_cnt, &apx_U, &apx_hist, &dom_work,
+            &radix};
   }
 };
 
@@ -95,6 +98,7 @@ int ddks_stage_inputs(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, i
 int ddks_encode_problem(ddks_ctx* ctx, const void* dP, int64_t NP, const void* dT, int64_t NT,
                         int32_t d, int32_t dtype, cudaStream_t st, bool want_sorted0);
 void ddks_stage_mark(ddks_ctx* ctx, int i, cudaStream_t st);
+bool ddks_use_radix(const ddks_ctx* ctx, int64_t N);  // tune.cu: radix sort vs chunk sort + merges
 void ddks_stage_collect(ddks_ctx* ctx);  // after the stream has synchronised
 int ddks_count_origins(ddks_ctx* ctx, int64_t NP, int64_t NT, int32_t d, int64_t ob, int64_t oe,
                        uint64_t* best, int32_t* bestj, cudaStream_t st);

@@ -55,7 +55,8 @@ cudaError_t ddks_launch_encode(const void* P, const void* T, int64_t NP, int64_t
 cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int64_t NP, int d, uint64_t* tmp_keys,
                              uint32_t* tmp_idx, uint64_t* tmp_keys2, uint32_t* tmp_idx2,
                              uint32_t* rank, uint32_t* sorted_idx0, uint32_t* pprefix0, uint32_t* cpfx,
-                             int* pfx_done, cudaStream_t st, int* launches);
+                             int* pfx_done, cudaStream_t st, int* launches, int key_bits = 64,
+                             uint32_t* radix_scratch = nullptr, const uint32_t** sorted_rows = nullptr);
 size_t ddks_rank_pfx_elems(int64_t N);
 size_t ddks_rank_scratch_elems(int64_t N);
 cudaError_t ddks_launch_sort_segments(const uint64_t* keys, int64_t N, int64_t NP, int S, uint64_t* k1,
@@ -76,6 +77,16 @@ size_t ddks_reduce_scratch_bytes();
 cudaError_t ddks_launch_reduce(const uint64_t* best, const int32_t* bestj, int64_t no,
                                int64_t o_begin, unsigned long long* out3, void* scratch,
                                cudaStream_t st);
+
+// radix.cu: stable LSD radix sort of key rows carrying their positions, and
+// min-ranks / P prefixes / dimension-0 order from the sorted rows.
+size_t ddks_radix_scratch_words(int64_t n, int64_t rows, int64_t pfx_rows);
+cudaError_t ddks_radix_sort(const uint64_t* keys, uint64_t* ka, uint32_t* ia, uint64_t* kb, uint32_t* ib, int64_t n,
+                            int64_t stride, int64_t rows, int nbits, uint32_t* scratch, const uint64_t** out_k,
+                            const uint32_t** out_i, cudaStream_t st, int* launches);
+cudaError_t ddks_radix_ranks(const uint64_t* sk, const uint32_t* si, int64_t n, int64_t stride, int64_t rows,
+                             int64_t NP, uint32_t* rank, uint32_t* pfx, int64_t pfx_rows, uint32_t* sorted_idx0,
+                             uint32_t* scratch, cudaStream_t st, int* launches);
 
 size_t ddks_scan_tmp_elems(int64_t rows, int64_t n);
 cudaError_t ddks_scan_rows(const uint32_t* in, uint32_t* out, int64_t rows, int64_t n, bool exclusive,

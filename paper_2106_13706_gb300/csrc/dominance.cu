@@ -220,17 +220,22 @@ k_dom_scatter(const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout, uin
 }
 
 // Per origin: the four quadrant counts of each sample and the best orthant.
-// hyx[v] = P points with y rank < v.
+// hyx[v] = P points with y rank < v.  order (optional, with [ob, oe) the
+// whole pooled range): the origins in dimension-1 order.  Neighbouring
+// threads then share the high bits of their y ranks, so the upper ends of
+// their query ranges (N and NP at level 0, then fixed by those bits) follow
+// the same positions and their record loads coincide.
 __global__ void __launch_bounds__(kThreads)
 k_dom_query(const uint32_t* __restrict__ rank, const uint32_t* __restrict__ pprefix0,
             const uint32_t* __restrict__ hyx, int64_t N, int64_t NP, int64_t NT, int64_t ob, int64_t oe,
-            WMView wa, WMView wp, const uint32_t* __restrict__ Zg, uint64_t* __restrict__ best,
-            int32_t* __restrict__ bestj) {
+            WMView wa, WMView wp, const uint32_t* __restrict__ Zg, const uint32_t* __restrict__ order,
+            uint64_t* __restrict__ best, int32_t* __restrict__ bestj) {
   __shared__ uint32_t Z[2 * kMaxLevels];
   if (threadIdx.x < 2 * kMaxLevels) Z[threadIdx.x] = Zg[threadIdx.x];
   __syncthreads();
-  for (int64_t o = ob + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < oe;
-       o += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t k = ob + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < oe;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = order ? (int64_t)order[k] : k;
     const uint32_t rx = rank[o], ry = rank[N + o];
     const uint32_t lxp = rx < (uint64_t)N ? pprefix0[rx] : (uint32_t)NP;  // P points with x_0 < o_0
     const uint64_t a3 = count_ge(wa, Z, rx, (uint32_t)N, ry);             // both >=, all points
@@ -337,8 +342,9 @@ cudaError_t ddks_launch_dominance(ddks_ctx* ctx, const uint32_t* rank, int64_t N
   const WMView wp{rec + recw, 2 * recw, L};
   const int64_t no = oe - ob;
   if (no > 0) {
+    const uint32_t* order = (ob == 0 && oe == N && ctx->sorted_rows) ? ctx->sorted_rows + N : nullptr;
     k_dom_query<<<grid_for(no, kThreads, ctx->num_sms * 16), kThreads, 0, st>>>(rank, pprefix0, hyx, N, NP, NT, ob,
-                                                                              oe, wa, wp, Zg, best, bestj);
+                                                                              oe, wa, wp, Zg, order, best, bestj);
     ++n;
   }
   if (launches) *launches += n;

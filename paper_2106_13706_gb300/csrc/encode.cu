@@ -506,10 +506,29 @@ size_t ddks_rank_scratch_elems(int64_t N) {
 // of scratch at cpfx): pprefix0[p] = #{P points among sorted positions < p}.
 size_t ddks_rank_pfx_elems(int64_t N) { return ddks_rank_scratch_elems(N); }
 
+// With radix_scratch (ddks_radix_scratch_words(N, d, 1) words): the radix
+// sort of radix.cu over the low key_bits of the keys replaces the chunk sort
+// and merges; pprefix0 then needs no cpfx scratch, and *sorted_rows (if
+// given) points at the pooled indices of every dimension in sorted order,
+// [d][N] inside the tmp_idx buffers (nullptr on the merge path).
 cudaError_t ddks_launch_rank(const uint64_t* keys, int64_t N, int64_t NP, int d, uint64_t* tmp_keys,
                              uint32_t* tmp_idx, uint64_t* tmp_keys2, uint32_t* tmp_idx2,
                              uint32_t* rank, uint32_t* sorted_idx0, uint32_t* pprefix0, uint32_t* cpfx,
-                             int* pfx_done, cudaStream_t st, int* launches) {
+                             int* pfx_done, cudaStream_t st, int* launches, int key_bits,
+                             uint32_t* radix_scratch, const uint32_t** sorted_rows) {
+  if (sorted_rows) *sorted_rows = nullptr;
+  if (radix_scratch) {
+    const bool pfx = sorted_idx0 && pprefix0;
+    if (pfx_done) *pfx_done = pfx ? 1 : 0;
+    const uint64_t* sk;
+    const uint32_t* si;
+    cudaError_t e = ddks_radix_sort(keys, tmp_keys, tmp_idx, tmp_keys2, tmp_idx2, N, N, d, key_bits, radix_scratch,
+                                    &sk, &si, st, launches);
+    if (e != cudaSuccess) return e;
+    if (sorted_rows) *sorted_rows = si;
+    return ddks_radix_ranks(sk, si, N, N, d, NP, rank, pfx ? pprefix0 : nullptr, 1, sorted_idx0, radix_scratch, st,
+                            launches);
+  }
   const int64_t Npad = (int64_t)ddks_rank_scratch_elems(N);
   const int64_t CH = chunk_for(N);
   const int64_t chunks = Npad / CH;

@@ -1,0 +1,345 @@
+// radix.cu -- stable LSD radix sort of rows of 64-bit order keys with their
+// positions, and what the exact and rdKS paths need from a sorted row: each
+// element's min-rank (the first sorted position of its key) and the count of
+// P points (pooled index < NP) before each sorted position.
+//
+// One pass per 8-bit digit, lowest first: k_radix_hist counts the digits of
+// each tile of 2048 consecutive elements; a scan of each digit's counts over
+// the tiles plus a scan of the digit totals gives every (digit, tile) pair
+// its first output position; k_radix_scatter ranks its tile stably by the digit
+// (warp-level match of equal digits, per-warp digit counters in shared
+// memory), places the tile in digit order in shared memory and writes each
+// digit's run to its output range.  Stable inside tiles and across them, so
+// after the last pass every row is sorted by key with ties in input order
+// (the pooled index, as the inputs carry their positions).
+//
+// k_radix_rank_tiles turns sorted rows into min-ranks: a position starts a
+// run when its key differs from its left neighbour, and the run start of a
+// position is the last run start at or before it (a running maximum), seeded
+// per tile by a binary search when the tile opens inside a run.
+#include <cstdint>
+
+#include "ddks_internal.cuh"
+
+namespace {
+
+constexpr int kRT = 256;             // threads per CTA (8 warps)
+constexpr int kRW = kRT / 32;
+constexpr int kRI = 8;               // elements per thread
+constexpr int kRTile = kRT * kRI;    // 2048 elements per tile
+constexpr int64_t kSelfScanTiles = 64;  // up to here the scatter CTAs sum the counts themselves
+
+DDKS_DEV uint32_t digit_of(uint64_t k, int shift) { return (uint32_t)(k >> shift) & 255u; }
+
+// exclusive prefix sum over the CTA's threads; ws: kRW words
+DDKS_DEV uint32_t block_exscan(uint32_t v, uint32_t* ws) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += x;
+  }
+  if (lane == 31) ws[warp] = incl;
+  __syncthreads();
+  uint32_t carry = 0;
+  for (int q = 0; q < warp; ++q) carry += ws[q];
+  __syncthreads();  // ws is free again on return
+  return carry + incl - v;
+}
+
+// exclusive running maximum over the CTA's threads (0 for thread 0); ws: kRW words
+DDKS_DEV uint32_t block_exmax(uint32_t v, uint32_t* ws) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl = x > incl ? x : incl;
+  }
+  if (lane == 31) ws[warp] = incl;
+  const uint32_t up = __shfl_up_sync(0xffffffffu, incl, 1);
+  __syncthreads();
+  uint32_t r = lane ? up : 0u;
+  for (int q = 0; q < warp; ++q) r = ws[q] > r ? ws[q] : r;
+  __syncthreads();
+  return r;
+}
+
+// cnt[(row * 256 + digit) * tiles + tile] = elements of the tile with that digit
+__global__ void __launch_bounds__(kRT)
+k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int64_t stride, int shift, int64_t tiles,
+             uint32_t* __restrict__ cnt) {
+  __shared__ uint32_t h[256];
+  const int64_t row = blockIdx.y, tile = blockIdx.x;
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t* K = keys + row * stride + tile * kRTile;
+  const int64_t nv = n - tile * kRTile;
+#pragma unroll
+  for (int j = 0; j < kRI; ++j) {
+    const int64_t e = j * kRT + threadIdx.x;
+    if (e < nv) atomicAdd(&h[digit_of(K[e], shift)], 1u);
+  }
+  __syncthreads();
+  cnt[((size_t)row * 256 + threadIdx.x) * tiles + tile] = h[threadIdx.x];
+}
+
+// Grid (256, rows): CTA (digit, row) turns the digit's tile counts into
+// exclusive prefixes over the tiles (off) and the row's digit total (tot).
+__global__ void __launch_bounds__(kRT)
+k_radix_tile_scan(const uint32_t* __restrict__ cnt, int64_t tiles, uint32_t* __restrict__ off,
+                  uint32_t* __restrict__ tot) {
+  __shared__ uint32_t ws[kRW];
+  const size_t rd = (size_t)blockIdx.y * 256 + blockIdx.x;
+  const uint32_t* C = cnt + rd * tiles;
+  uint32_t* O = off + rd * tiles;
+  uint32_t carry = 0;
+  for (int64_t b0 = 0; b0 < tiles; b0 += 4 * kRT) {
+    uint32_t c[4], s = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t q = b0 + 4 * threadIdx.x + j;
+      c[j] = q < tiles ? C[q] : 0u;
+      s += c[j];
+    }
+    const uint32_t ex = block_exscan(s, ws);
+    uint32_t run = carry + ex;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t q = b0 + 4 * threadIdx.x + j;
+      if (q < tiles) O[q] = run;
+      run += c[j];
+    }
+    // the chunk's total: the last thread's exclusive prefix plus its sum
+    if (threadIdx.x == kRT - 1) ws[0] = ex + s;
+    __syncthreads();
+    carry += ws[0];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tot[rd] = carry;
+}
+
+// One digit pass, in -> out.  in_i == nullptr: the input indices are the
+// positions.  off / tot: k_radix_tile_scan of this pass's counts cnt, or
+// nullptr to have every CTA sum the counts of its row itself (few tiles).
+__global__ void __launch_bounds__(kRT, 4)
+k_radix_scatter(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ in_i, uint64_t* __restrict__ out_k,
+                uint32_t* __restrict__ out_i, int64_t n, int64_t stride, int shift, int64_t tiles,
+                const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off, const uint32_t* __restrict__ tot) {
+  __shared__ uint64_t sk[kRTile];
+  __shared__ uint32_t si[kRTile];
+  __shared__ uint32_t wcnt[kRW][256];
+  __shared__ uint32_t soff[256], sbeg[256];
+  __shared__ uint32_t ws[kRW];
+  const int64_t row = blockIdx.y, tile = blockIdx.x;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int64_t base = tile * kRTile;
+  const int nvalid = (int)(n - base < kRTile ? n - base : kRTile);
+  const uint64_t* K = in_k + row * stride + base;
+  const uint32_t* I = in_i ? in_i + row * stride + base : nullptr;
+  uint32_t gpre = 0, gtot = 0;  // digit t before this tile / in the whole row
+  if (off) {
+    gpre = off[((size_t)row * 256 + t) * tiles + tile];
+    gtot = tot[(size_t)row * 256 + t];
+  } else {
+    const uint32_t* C = cnt + ((size_t)row * 256 + t) * tiles;
+    for (int64_t q = 0; q < tiles; ++q) {
+      const uint32_t c = C[q];
+      gpre += q < tile ? c : 0u;
+      gtot += c;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kRW; ++q) wcnt[q][t] = 0;
+  // Warp-striped positions: element j of lane l in warp w sits at
+  // w*256 + j*32 + l, so ranking in (j, lane) order within a warp and the
+  // warps in order is stable.  Positions past the row's end take the largest
+  // key (digit 255, ranked after every element of the tile).
+  uint64_t k[kRI];
+  uint32_t ix[kRI], r[kRI];
+#pragma unroll
+  for (int j = 0; j < kRI; ++j) {
+    const int q = w * (kRI * 32) + j * 32 + lane;
+    const bool v = q < nvalid;
+    k[j] = v ? K[q] : ~0ull;
+    ix[j] = v ? (I ? I[q] : (uint32_t)(base + q)) : 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kRI; ++j) {
+    const uint32_t dg = digit_of(k[j], shift);
+    const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+    r[j] = wcnt[w][dg] + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    __syncwarp();
+    if ((peers >> lane) == 1u) wcnt[w][dg] += (uint32_t)__popc(peers);  // the group's highest lane
+    __syncwarp();
+  }
+  __syncthreads();
+  // thread t owns digit t: first the warps' offsets inside the digit, then
+  // the digit's offset inside the tile
+  uint32_t dsum = 0;
+#pragma unroll
+  for (int q = 0; q < kRW; ++q) {
+    const uint32_t c = wcnt[q][t];
+    wcnt[q][t] = dsum;
+    dsum += c;
+  }
+  const uint32_t dbeg = block_exscan(dsum, ws);
+  sbeg[t] = dbeg;
+  soff[t] = block_exscan(gtot, ws) + gpre;
+#pragma unroll
+  for (int q = 0; q < kRW; ++q) wcnt[q][t] += dbeg;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kRI; ++j) {
+    const uint32_t lr = wcnt[w][digit_of(k[j], shift)] + r[j];
+    sk[lr] = k[j];
+    si[lr] = ix[j];
+  }
+  __syncthreads();
+  uint64_t* OK = out_k + row * stride;
+  uint32_t* OI = out_i + row * stride;
+  for (int q = t; q < nvalid; q += kRT) {
+    const uint64_t kk = sk[q];
+    const uint32_t dg = digit_of(kk, shift);
+    const uint32_t dst = soff[dg] + (uint32_t)q - sbeg[dg];
+    OK[dst] = kk;
+    OI[dst] = si[q];
+  }
+}
+
+// Min-ranks from sorted rows: rank[row][idx(p)] = first position of key(p)
+// (rank may be nullptr); rows below pfx_rows also get flag[row][p] =
+// [idx(p) < NP]; with sorted_idx0, row 0 gets sorted_idx0[p] = idx(p).
+__global__ void __launch_bounds__(kRT)
+k_radix_rank_tiles(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ si, int64_t n, int64_t stride,
+                   int64_t NP, uint32_t* __restrict__ rank, uint32_t* __restrict__ flag, int64_t pfx_rows,
+                   uint32_t* __restrict__ sorted_idx0) {
+  __shared__ uint64_t kt[kRTile + 1];  // kt[q + 1] = key at base + q, kt[0] = key at base - 1
+  __shared__ uint32_t ws[kRW];
+  __shared__ uint32_t seed_s;
+  const int64_t row = blockIdx.y, tile = blockIdx.x;
+  const int t = threadIdx.x;
+  const int64_t base = tile * kRTile;
+  const int nvalid = (int)(n - base < kRTile ? n - base : kRTile);
+  const uint64_t* K = sk + row * stride;
+  const uint32_t* I = si + row * stride;
+  for (int q = t; q < nvalid; q += kRT) kt[q + 1] = K[base + q];
+  if (t == 0) {
+    // the run start of the tile's first key: base unless the run began before
+    int64_t lo = base;
+    if (base > 0) {
+      const uint64_t key = K[base], left = K[base - 1];
+      kt[0] = left;
+      if (left == key) {
+        int64_t hi = base - 1;  // K[hi] == key: the lower bound lies in [0, hi]
+        lo = 0;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (K[mid] < key) lo = mid + 1; else hi = mid;
+        }
+      }
+    }
+    seed_s = (uint32_t)lo;
+  }
+  __syncthreads();
+  // thread t covers the tile positions [t*8, t*8 + 8)
+  uint32_t last = 0;
+#pragma unroll
+  for (int j = 0; j < kRI; ++j) {
+    const int q = t * kRI + j;
+    if (q < nvalid && (base + q == 0 || kt[q + 1] != kt[q])) last = (uint32_t)(base + q);
+  }
+  uint32_t rs = block_exmax(last, ws);
+  rs = rs > seed_s ? rs : seed_s;
+  const bool pf = row < pfx_rows;
+  const bool s0 = row == 0 && sorted_idx0 != nullptr;
+#pragma unroll
+  for (int j = 0; j < kRI; ++j) {
+    const int q = t * kRI + j;
+    if (q < nvalid) {
+      if (base + q == 0 || kt[q + 1] != kt[q]) rs = (uint32_t)(base + q);
+      const uint32_t i = I[base + q];
+      if (rank) rank[row * n + i] = rs;
+      if (pf) flag[row * n + base + q] = (uint64_t)i < (uint64_t)NP ? 1u : 0u;
+      if (s0) sorted_idx0[base + q] = i;
+    }
+  }
+}
+
+}  // namespace
+
+size_t ddks_radix_scratch_words(int64_t n, int64_t rows, int64_t pfx_rows) {
+  const int64_t tiles = (n + kRTile - 1) / kRTile;
+  const size_t cnt = (size_t)rows * 256 * (size_t)tiles;
+  const size_t a = 2 * cnt + (size_t)rows * 256;
+  const size_t b = (size_t)pfx_rows * (size_t)n + ddks_scan_tmp_elems(pfx_rows, n);
+  return a > b ? a : b;
+}
+
+// Sorts rows of n keys (row r at keys + r * stride) by their low nbits (a
+// multiple of 8, at most 64), each key carrying its position in the row.
+// Passes alternate between (ka, ia) and (kb, ib), [rows][stride] each, and
+// *out_k / *out_i point at the pair holding the result.  scratch:
+// ddks_radix_scratch_words(n, rows, .) words.
+cudaError_t ddks_radix_sort(const uint64_t* keys, uint64_t* ka, uint32_t* ia, uint64_t* kb, uint32_t* ib, int64_t n,
+                            int64_t stride, int64_t rows, int nbits, uint32_t* scratch, const uint64_t** out_k,
+                            const uint32_t** out_i, cudaStream_t st, int* launches) {
+  if (n <= 0 || rows <= 0 || rows > 65535 || nbits <= 0 || nbits > 64 || nbits % 8 || n > 0xFFFFFFFFll)
+    return cudaErrorInvalidValue;
+  const int64_t tiles = (n + kRTile - 1) / kRTile;
+  const size_t ncnt = (size_t)rows * 256 * (size_t)tiles;
+  uint32_t* cnt = scratch;
+  uint32_t* off = scratch + ncnt;
+  uint32_t* tot = off + ncnt;
+  const dim3 g((unsigned)tiles, (unsigned)rows);
+  const bool self_scan = tiles <= kSelfScanTiles;
+  const uint64_t* ck = keys;
+  const uint32_t* ci = nullptr;
+  uint64_t* dk = ka;
+  uint32_t* di = ia;
+  int nl = 0;
+  for (int shift = 0; shift < nbits; shift += 8) {
+    k_radix_hist<<<g, kRT, 0, st>>>(ck, n, stride, shift, tiles, cnt);
+    if (!self_scan) {
+      k_radix_tile_scan<<<dim3(256, (unsigned)rows), kRT, 0, st>>>(cnt, tiles, off, tot);
+      ++nl;
+    }
+    k_radix_scatter<<<g, kRT, 0, st>>>(ck, ci, dk, di, n, stride, shift, tiles, cnt, self_scan ? nullptr : off,
+                                       tot);
+    nl += 2;
+    ck = dk;
+    ci = di;
+    dk = dk == ka ? kb : ka;
+    di = di == ia ? ib : ia;
+  }
+  *out_k = ck;
+  *out_i = ci;
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}
+
+// From sorted rows (sk, si; [rows][stride]): rank[row][i] = min-rank of
+// element i, [rows][n] (rank may be nullptr); pfx[row][p] = P points (index
+// < NP) before sorted position p for rows [0, pfx_rows), [pfx_rows][n] (pfx
+// may be nullptr); sorted_idx0[p] = the index at sorted position p of row 0
+// (may be nullptr).  scratch as for the sort, with pfx_rows.
+cudaError_t ddks_radix_ranks(const uint64_t* sk, const uint32_t* si, int64_t n, int64_t stride, int64_t rows,
+                             int64_t NP, uint32_t* rank, uint32_t* pfx, int64_t pfx_rows, uint32_t* sorted_idx0,
+                             uint32_t* scratch, cudaStream_t st, int* launches) {
+  if (n <= 0 || rows <= 0 || rows > 65535) return cudaErrorInvalidValue;
+  const int64_t tiles = (n + kRTile - 1) / kRTile;
+  if (!pfx) pfx_rows = 0;
+  uint32_t* flag = scratch;
+  uint32_t* tmp = scratch + (size_t)pfx_rows * (size_t)n;
+  k_radix_rank_tiles<<<dim3((unsigned)tiles, (unsigned)rows), kRT, 0, st>>>(sk, si, n, stride, NP, rank, flag,
+                                                                             pfx_rows, sorted_idx0);
+  int nl = 1;
+  if (pfx_rows > 0) {
+    cudaError_t e = ddks_scan_rows(flag, pfx, pfx_rows, n, true, tmp, st, &nl);
+    if (e != cudaSuccess) return e;
+  }
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}

@@ -16,6 +16,13 @@
 #include "ddks_internal.cuh"
 
 constexpr int64_t kDominanceMinN = 32768;
+constexpr int64_t kRadixMinN = 65536;  // pooled N from which key sorts use the radix sort
+
+bool ddks_use_radix(const ddks_ctx* ctx, int64_t N) {
+  const int64_t m = ctx->cfg.radix_min_n;
+  if (m < 0) return false;
+  return N >= (m == 0 ? kRadixMinN : m);
+}
 
 static std::string tune_key(int64_t NP, int64_t NT, int32_t d) {
   auto bucket = [](int64_t n) {
