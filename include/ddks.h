@@ -83,7 +83,8 @@ typedef struct {
   int32_t graphs;             /* 1 (default): replay CUDA graphs for repeated calls, see below; 0 = off */
   int64_t radix_min_n;        /* pooled sizes N from which the key sorts (the per-dimension ranks of the
                                  exact paths, the rdKS distance orders) run as LSD radix sorts instead of
-                                 chunk sorts + merges; 0 = the built-in default, -1 = never */
+                                 chunk sorts + merges; 0 = the built-in defaults (16384 for float32
+                                 inputs, 131072 for float64 and the rdKS distances), -1 = never */
 } ddks_config;
 
 typedef struct {
@@ -291,6 +292,18 @@ int ddks_vdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
  */
 int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT, int32_t d,
               int32_t dtype, void* stream, ddks_result* out, uint64_t* per_corner);
+
+/*
+ * The NormalizeData rescale of one dimension (Alg. vdKS, Alg. rdKS) as the
+ * rdKS distance kernel computes it: out[i] = (v[i] - lo) / span, the
+ * subtraction and the division each rounded to nearest in IEEE double (0 for
+ * span == 0).  The kernel forms the quotient from RN(1 / span) with FMAs and
+ * certifies it by its exact remainder (the division itself where the
+ * certificate fails), so out must equal the plain IEEE expression bit for
+ * bit.  v, out: n doubles, both device or both host memory.  span >= 0 and
+ * finite, lo finite (DDKS_EINVAL otherwise); n >= 0.
+ */
+int ddks_rescale(ddks_ctx* ctx, const double* v, int64_t n, double lo, double span, double* out, void* stream);
 
 /* Human-readable text for a return code. */
 const char* ddks_strerror(int code);

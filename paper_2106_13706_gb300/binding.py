@@ -94,6 +94,7 @@ def load():
             "ddks_distance_noalloc": (i32, [vp, i64, vp, i64, i32, i32, vp, R]),
             "ddks_vdks": (i32, [vp, vp, i64, vp, i64, i32, i32, i32, vp, R]),
             "ddks_rdks": (i32, [vp, vp, i64, vp, i64, i32, i32, vp, R, vp]),
+            "ddks_rescale": (i32, [vp, vp, i64, ctypes.c_double, ctypes.c_double, vp, vp]),
             "ddks_autotune": (i32, [vp, vp, i64, vp, i64, i32, i32, vp, ctypes.POINTER(i32),
                                     ctypes.POINTER(ctypes.c_float)]),
             "ddks_set_stage_timing": (i32, [vp, i32]),
@@ -252,6 +253,26 @@ def ddks_rdks(ctx, P, T, stream=None):
     return out
 
 
+def ddks_rescale(ctx, v, lo, span, stream=None):
+    """NormalizeData of one dimension, (v - lo) / span in IEEE double, on the
+    device: v a float64 torch tensor (device; the result is a new device
+    tensor) or array-like (host; the result is a numpy array)."""
+    p, n, cols, dt, keep = _arr(v)
+    if dt != DDKS_F64 or cols != 1:
+        raise ValueError("expected a 1-D float64 array")
+    try:
+        import torch
+        if isinstance(keep, torch.Tensor):
+            out = torch.empty(n, dtype=torch.float64, device=keep.device)
+            _check(load().ddks_rescale(ctx, p, n, float(lo), float(span), out.data_ptr(), _stream(stream)), ctx)
+            return out
+    except ImportError:
+        pass
+    out = np.empty(n, dtype=np.float64)
+    _check(load().ddks_rescale(ctx, p, n, float(lo), float(span), out.ctypes.data, _stream(stream)), ctx)
+    return out
+
+
 def ddks_permutation_test(ctx, P, T, B, seed, stream=None, want_perm=True):
     p, NP, t, NT, d, dt, keep = _pair(P, T)
     r = ddks_result()
@@ -374,6 +395,9 @@ class Context:
 
     def vdks(self, P, T, voxels_per_dim, stream=None):
         return ddks_vdks(self.h, P, T, voxels_per_dim, stream)
+
+    def rescale(self, v, lo, span, stream=None):
+        return ddks_rescale(self.h, v, lo, span, stream)
 
     def rdks(self, P, T, stream=None):
         return ddks_rdks(self.h, P, T, stream)

@@ -234,7 +234,8 @@ int ddks_encode_problem(ddks_ctx* ctx, const void* dP, int64_t NP, const void* d
   if ((rc = ctx->rank.reserve(ctx, 4 * (size_t)N * d))) return rc;
   if ((rc = ctx->sidx0.reserve(ctx, 4 * (size_t)N))) return rc;
   if (want_sorted0 && (rc = ctx->pfx0.reserve(ctx, 4 * ((size_t)N + 2 * ddks_rank_pfx_elems(N))))) return rc;
-  const bool radix = ddks_use_radix(ctx, N);
+  const int key_bits = dtype == DDKS_F64 ? 64 : 32;
+  const bool radix = ddks_use_radix(ctx, N, key_bits);
   if (radix && (rc = ctx->radix.reserve(ctx, 4 * ddks_radix_scratch_words(N, d, 1)))) return rc;
   if ((rc = ctx->flags.reserve(ctx, 64))) return rc;
   cudaError_t e = cudaMemsetAsync(ctx->flags.ptr, 0, 4, st);
@@ -248,7 +249,7 @@ int ddks_encode_problem(ddks_ctx* ctx, const void* dP, int64_t NP, const void* d
   e = ddks_launch_rank((const uint64_t*)ctx->keys.ptr, N, NP, d, (uint64_t*)ctx->tk1.ptr,
                        (uint32_t*)ctx->ti1.ptr, (uint64_t*)ctx->tk2.ptr, (uint32_t*)ctx->ti2.ptr,
                        (uint32_t*)ctx->rank.ptr, want_sorted0 ? (uint32_t*)ctx->sidx0.ptr : nullptr,
-                       pfx0, pfx0 ? pfx0 + N : nullptr, &pfx_done, st, &n, dtype == DDKS_F64 ? 64 : 32,
+                       pfx0, pfx0 ? pfx0 + N : nullptr, &pfx_done, st, &n, key_bits,
                        radix ? (uint32_t*)ctx->radix.ptr : nullptr, &ctx->sorted_rows);
   ctx->launches += n;
   ctx->pfx0_valid = pfx_done != 0;

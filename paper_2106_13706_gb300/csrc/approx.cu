@@ -40,6 +40,7 @@
 //                    max per corner
 //   k_rdks_final     max over corners, lowest corner
 #include <climits>
+#include <cmath>
 #include <cstring>
 
 #include "../../include/ddks.h"
@@ -65,6 +66,44 @@ DDKS_DEV double key_value(ull k) {
 
 DDKS_DEV double rescale(double v, double lo, double span) {
   return span > 0.0 ? __ddiv_rn(__dsub_rn(v, lo), span) : 0.0;
+}
+
+// The same correctly rounded x' = (v - lo) / span with fewer FP64
+// instructions (GB300's FP64 rate is low, and the division sequence and
+// floating-point compares all issue on that pipe).  rcp = RN(1 / span), or
+// 0 for a span outside [2^-900, 2^1000) (division used throughout).
+// q0 = RN(a * rcp), one correction q = RN(q0 + r0 * rcp) with the exact
+// remainder r0 = a - q0 * span (Markstein's step).  q is returned only when
+// certified: with the exact remainder r = a - q * span, q is the nearest
+// double to a / span when |r| <= span * g / 2, g the smaller of the gaps
+// next to q (a quotient of doubles is never a midpoint, so the nearest double
+// is unique).  The range checks and the certificate compare bit patterns of
+// non-negative doubles as integers, and span * g / 2 is span with its
+// exponent field raised (everything stays normal for a, q0 >= 2^-900).
+// Otherwise, or when the certificate fails, the IEEE division.
+DDKS_DEV double rescale_rcp(double v, double lo, double span, double rcp) {
+  constexpr long long kMinBits = 0x07B0000000000000ll;  // bit pattern of 2^-900
+  const double a = __dsub_rn(v, lo);                    // >= +0: lo is the minimum
+  const long long ab = __double_as_longlong(a);
+  if (ab >= kMinBits && __double_as_longlong(rcp) != 0) {
+    const double q0 = __dmul_rn(a, rcp);
+    if (__double_as_longlong(q0) >= kMinBits) {
+      const double q = __fma_rn(__fma_rn(-q0, span, a), rcp, q0);
+      const double r = __fma_rn(-q, span, a);
+      const long long qb = __double_as_longlong(q);
+      // g / 2 = 2^(E - 53), or 2^(E - 54) when q is a power of two (E its exponent)
+      const long long sh = ((qb >> 52) & 0x7FF) - 1023 - ((qb & 0xFFFFFFFFFFFFFll) == 0 ? 54 : 53);
+      const long long lim = __double_as_longlong(span) + sh * (1ll << 52);
+      if ((__double_as_longlong(r) & 0x7FFFFFFFFFFFFFFFll) <= lim) return q;
+    }
+  }
+  if (ab == 0 || !(span > 0.0)) return 0.0;
+  return __ddiv_rn(a, span);
+}
+
+// RN(1 / span) for rescale_rcp, or 0 where it takes the division path.
+DDKS_DEV double rescale_rcp_of(double span) {
+  return (span >= 0x1p-900 && span < 0x1p1000) ? __drcp_rn(span) : 0.0;
 }
 
 template <typename V>
@@ -705,9 +744,16 @@ k_vdks_eval(const long long* __restrict__ U, const uint32_t* __restrict__ cnt, u
 // (s - 2x) + 1 can be a little below zero; -0.0 keys like +0.0).
 DDKS_DEV ull dist_key(double r) { return (ull)ddks::order_key(r); }
 
-// |x' - e_m|^2 from the squared norm s: (s - 2 x'_m) + 1, rounded twice
-// (2 x'_m is exact).
-DDKS_DEV double corner_dist(double s, double x) { return __dadd_rn(__dsub_rn(s, __dmul_rn(2.0, x)), 1.0); }
+// |x' - e_m|^2 from the squared norm s: (s - 2 x'_m) + 1, each step rounded;
+// 2 x'_m is exact, so one FMA rounds s - 2 x'_m.
+DDKS_DEV double corner_dist(double s, double x) { return __dadd_rn(__fma_rn(-2.0, x, s), 1.0); }
+
+__global__ void __launch_bounds__(kThreads)
+k_rescale(const double* __restrict__ v, int64_t n, double lo, double span, double* __restrict__ out) {
+  const double rcp = rescale_rcp_of(span);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = rescale_rcp(v[i], lo, span, rcp);
+}
 
 // One thread per point, all d + 1 corners (d <= kRdksThreadMaxD).
 template <typename V>
@@ -715,11 +761,13 @@ __global__ void __launch_bounds__(kThreads)
 k_rdks_dist_thread(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64_t NT, int d,
                    const ull* __restrict__ gmin, const ull* __restrict__ gmax, ull* __restrict__ keys,
                    unsigned* __restrict__ flags) {
-  __shared__ double slo[kRdksThreadMaxD], sspan[kRdksThreadMaxD];
+  __shared__ double slo[kRdksThreadMaxD], sspan[kRdksThreadMaxD], srcp[kRdksThreadMaxD];
   if (threadIdx.x < d) {
     const double lo = key_value(gmin[threadIdx.x]);
+    const double span = __dsub_rn(key_value(gmax[threadIdx.x]), lo);
     slo[threadIdx.x] = lo;
-    sspan[threadIdx.x] = __dsub_rn(key_value(gmax[threadIdx.x]), lo);
+    sspan[threadIdx.x] = span;
+    srcp[threadIdx.x] = rescale_rcp_of(span);
   }
   check_spans(gmin, gmax, d, flags);
   __syncthreads();
@@ -727,12 +775,13 @@ k_rdks_dist_thread(const V* __restrict__ P, const V* __restrict__ T, int64_t NP,
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const V* row = point_row(P, T, NP, d, i);
     double x[kRdksThreadMaxD];
-    double s = 0.0;  // squared norm, added in dimension order
+    x[0] = rescale_rcp((double)row[0], slo[0], sspan[0], srcp[0]);
+    double s = __dmul_rn(x[0], x[0]);  // squared norm, added in dimension order (0 + x0^2 = x0^2)
 #pragma unroll
-    for (int m = 0; m < kRdksThreadMaxD; ++m) {
+    for (int m = 1; m < kRdksThreadMaxD; ++m) {
       x[m] = 0.0;
       if (m < d) {
-        x[m] = rescale((double)row[m], slo[m], sspan[m]);
+        x[m] = rescale_rcp((double)row[m], slo[m], sspan[m], srcp[m]);
         s = __dadd_rn(s, __dmul_rn(x[m], x[m]));
       }
     }
@@ -1177,6 +1226,39 @@ int ddks_vdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
   return finish(ctx, st, L, NP, NT, out, nullptr, nullptr, 0);
 }
 
+int ddks_rescale(ddks_ctx* ctx, const double* v, int64_t n, double lo, double span, double* out, void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!v || !out))) return DDKS_EINVAL;
+  if (!std::isfinite(lo) || !std::isfinite(span) || span < 0.0) return DDKS_EINVAL;
+  if (n == 0) return DDKS_OK;
+  const bool dv = ddks_is_device_ptr(v), dout = ddks_is_device_ptr(out);
+  if (dv != dout) return DDKS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "cudaSetDevice");
+  const double* dvp = v;
+  double* dop = out;
+  if (!dv) {
+    int rc = ctx->inP.reserve(ctx, 8 * (size_t)n);
+    if (rc == DDKS_OK) rc = ctx->inT.reserve(ctx, 8 * (size_t)n);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(ctx->inP.ptr, v, 8 * (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "copy rescale input");
+    dvp = (const double*)ctx->inP.ptr;
+    dop = (double*)ctx->inT.ptr;
+  }
+  k_rescale<<<grid_cap(n, kThreads, ctx->num_sms * 8), kThreads, 0, st>>>(dvp, n, lo, span, dop);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "rescale");
+  ctx->launches += 1;
+  if (!dv) {
+    e = cudaMemcpyAsync(out, dop, 8 * (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "copy rescale output");
+  }
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "rescale sync");
+  return DDKS_OK;
+}
+
 int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT, int32_t d,
               int32_t dtype, void* stream, ddks_result* out, uint64_t* per_corner) {
   if (!ctx || !out) return DDKS_EINVAL;
@@ -1202,7 +1284,7 @@ int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
   if ((rc = ctx->ti2.reserve(ctx, 4 * segs))) return out->status = rc;
   if ((rc = ctx->apx_cnt.reserve(ctx, 4 * segs))) return out->status = rc;  // P prefixes
   if ((rc = ctx->apx_U.reserve(ctx, 4 * segs))) return out->status = rc;
-  const bool radix = N > 1024 && ddks_use_radix(ctx, N);
+  const bool radix = N > 1024 && ddks_use_radix(ctx, N, 64);
   if (radix && (rc = ctx->radix.reserve(ctx, 4 * ddks_radix_scratch_words(N, S, S)))) return out->status = rc;
   // warp kernel: shared memory of 2 * d doubles per warp
   int nwb = (int)((96 * 1024) / (16 * (size_t)d));

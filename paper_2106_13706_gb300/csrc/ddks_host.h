@@ -98,7 +98,7 @@ int ddks_stage_inputs(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, i
 int ddks_encode_problem(ddks_ctx* ctx, const void* dP, int64_t NP, const void* dT, int64_t NT,
                         int32_t d, int32_t dtype, cudaStream_t st, bool want_sorted0);
 void ddks_stage_mark(ddks_ctx* ctx, int i, cudaStream_t st);
-bool ddks_use_radix(const ddks_ctx* ctx, int64_t N);  // tune.cu: radix sort vs chunk sort + merges
+bool ddks_use_radix(const ddks_ctx* ctx, int64_t N, int key_bits);  // tune.cu: radix vs chunk sort + merges
 void ddks_stage_collect(ddks_ctx* ctx);  // after the stream has synchronised
 int ddks_count_origins(ddks_ctx* ctx, int64_t NP, int64_t NT, int32_t d, int64_t ob, int64_t oe,
                        uint64_t* best, int32_t* bestj, cudaStream_t st);

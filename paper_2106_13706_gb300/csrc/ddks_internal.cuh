@@ -30,7 +30,8 @@ DDKS_DEV uint64_t order_key(float v) {
   return (uint64_t)u;
 }
 DDKS_DEV uint64_t order_key(double v) {
-  uint64_t u = (uint64_t)__double_as_longlong(v == 0.0 ? 0.0 : v);
+  uint64_t u = (uint64_t)__double_as_longlong(v);
+  if ((u << 1) == 0) u = 0;  // -0.0 as +0.0 (an integer test: FP64 compares are costly here)
   u = (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
   return u;
 }

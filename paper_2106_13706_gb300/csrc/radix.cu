@@ -25,11 +25,24 @@ namespace {
 
 constexpr int kRT = 256;             // threads per CTA (8 warps)
 constexpr int kRW = kRT / 32;
-constexpr int kRI = 8;               // elements per thread
-constexpr int kRTile = kRT * kRI;    // 2048 elements per tile
-constexpr int64_t kSelfScanTiles = 64;  // up to here the scatter CTAs sum the counts themselves
+constexpr int kRI = 8;               // elements per thread of the rank kernel
+constexpr int kRTile = kRT * kRI;    // 2048 positions per rank tile
+constexpr int64_t kSelfScanTiles = 128;  // up to here the scatter CTAs sum the counts themselves
 
 DDKS_DEV uint32_t digit_of(uint64_t k, int shift) { return (uint32_t)(k >> shift) & 255u; }
+
+// Lanes of the (fully active) warp whose 8-bit digit equals this lane's:
+// one ballot per digit bit (cheaper than match.any here).
+DDKS_DEV uint32_t same_digit_lanes(uint32_t dg) {
+  uint32_t m = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (dg >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? bal : ~bal;
+  }
+  return m;
+}
 
 // exclusive prefix sum over the CTA's threads; ws: kRW words
 DDKS_DEV uint32_t block_exscan(uint32_t v, uint32_t* ws) {
@@ -48,38 +61,34 @@ DDKS_DEV uint32_t block_exscan(uint32_t v, uint32_t* ws) {
   return carry + incl - v;
 }
 
-// exclusive running maximum over the CTA's threads (0 for thread 0); ws: kRW words
-DDKS_DEV uint32_t block_exmax(uint32_t v, uint32_t* ws) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t incl = v;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl = x > incl ? x : incl;
-  }
-  if (lane == 31) ws[warp] = incl;
-  const uint32_t up = __shfl_up_sync(0xffffffffu, incl, 1);
-  __syncthreads();
-  uint32_t r = lane ? up : 0u;
-  for (int q = 0; q < warp; ++q) r = ws[q] > r ? ws[q] : r;
-  __syncthreads();
-  return r;
-}
-
-// cnt[(row * 256 + digit) * tiles + tile] = elements of the tile with that digit
+// cnt[(row * 256 + digit) * tiles + tile] = elements of the tile with that
+// digit.  Lanes with equal digits add once per group (high key bytes take
+// few values, and same-address shared atomics serialise).
+template <int RI>
 __global__ void __launch_bounds__(kRT)
 k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int64_t stride, int shift, int64_t tiles,
              uint32_t* __restrict__ cnt) {
+  constexpr int kTile = kRT * RI;
   __shared__ uint32_t h[256];
   const int64_t row = blockIdx.y, tile = blockIdx.x;
+  const int lane = threadIdx.x & 31;
   h[threadIdx.x] = 0;
   __syncthreads();
-  const uint64_t* K = keys + row * stride + tile * kRTile;
-  const int64_t nv = n - tile * kRTile;
+  const uint64_t* K = keys + row * stride + tile * kTile;
+  const int64_t nv = n - tile * kTile;
+  uint64_t k[RI];
 #pragma unroll
-  for (int j = 0; j < kRI; ++j) {
+  for (int j = 0; j < RI; ++j) {
     const int64_t e = j * kRT + threadIdx.x;
-    if (e < nv) atomicAdd(&h[digit_of(K[e], shift)], 1u);
+    k[j] = e < nv ? K[e] : 0ull;
+  }
+#pragma unroll
+  for (int j = 0; j < RI; ++j) {
+    const bool v = j * kRT + (int64_t)threadIdx.x < nv;
+    const uint32_t vm = __ballot_sync(0xffffffffu, v);
+    const uint32_t dg = digit_of(k[j], shift);
+    const uint32_t peers = same_digit_lanes(dg) & vm;
+    if (v && (peers >> lane) == 1u) atomicAdd(&h[dg], (uint32_t)__popc(peers));
   }
   __syncthreads();
   cnt[((size_t)row * 256 + threadIdx.x) * tiles + tile] = h[threadIdx.x];
@@ -123,19 +132,21 @@ k_radix_tile_scan(const uint32_t* __restrict__ cnt, int64_t tiles, uint32_t* __r
 // One digit pass, in -> out.  in_i == nullptr: the input indices are the
 // positions.  off / tot: k_radix_tile_scan of this pass's counts cnt, or
 // nullptr to have every CTA sum the counts of its row itself (few tiles).
+template <int RI>
 __global__ void __launch_bounds__(kRT, 4)
 k_radix_scatter(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ in_i, uint64_t* __restrict__ out_k,
                 uint32_t* __restrict__ out_i, int64_t n, int64_t stride, int shift, int64_t tiles,
                 const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off, const uint32_t* __restrict__ tot) {
-  __shared__ uint64_t sk[kRTile];
-  __shared__ uint32_t si[kRTile];
+  constexpr int kTile = kRT * RI;
+  __shared__ uint64_t sk[kTile];
+  __shared__ uint32_t si[kTile];
   __shared__ uint32_t wcnt[kRW][256];
   __shared__ uint32_t soff[256], sbeg[256];
   __shared__ uint32_t ws[kRW];
   const int64_t row = blockIdx.y, tile = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int64_t base = tile * kRTile;
-  const int nvalid = (int)(n - base < kRTile ? n - base : kRTile);
+  const int64_t base = tile * kTile;
+  const int nvalid = (int)(n - base < kTile ? n - base : kTile);
   const uint64_t* K = in_k + row * stride + base;
   const uint32_t* I = in_i ? in_i + row * stride + base : nullptr;
   uint32_t gpre = 0, gtot = 0;  // digit t before this tile / in the whole row
@@ -144,6 +155,7 @@ k_radix_scatter(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ 
     gtot = tot[(size_t)row * 256 + t];
   } else {
     const uint32_t* C = cnt + ((size_t)row * 256 + t) * tiles;
+#pragma unroll 8
     for (int64_t q = 0; q < tiles; ++q) {
       const uint32_t c = C[q];
       gpre += q < tile ? c : 0u;
@@ -153,23 +165,23 @@ k_radix_scatter(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ 
 #pragma unroll
   for (int q = 0; q < kRW; ++q) wcnt[q][t] = 0;
   // Warp-striped positions: element j of lane l in warp w sits at
-  // w*256 + j*32 + l, so ranking in (j, lane) order within a warp and the
+  // w*32*RI + j*32 + l, so ranking in (j, lane) order within a warp and the
   // warps in order is stable.  Positions past the row's end take the largest
   // key (digit 255, ranked after every element of the tile).
-  uint64_t k[kRI];
-  uint32_t ix[kRI], r[kRI];
+  uint64_t k[RI];
+  uint32_t ix[RI], r[RI];
 #pragma unroll
-  for (int j = 0; j < kRI; ++j) {
-    const int q = w * (kRI * 32) + j * 32 + lane;
+  for (int j = 0; j < RI; ++j) {
+    const int q = w * (RI * 32) + j * 32 + lane;
     const bool v = q < nvalid;
     k[j] = v ? K[q] : ~0ull;
     ix[j] = v ? (I ? I[q] : (uint32_t)(base + q)) : 0u;
   }
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < kRI; ++j) {
+  for (int j = 0; j < RI; ++j) {
     const uint32_t dg = digit_of(k[j], shift);
-    const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+    const uint32_t peers = same_digit_lanes(dg);
     r[j] = wcnt[w][dg] + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     __syncwarp();
     if ((peers >> lane) == 1u) wcnt[w][dg] += (uint32_t)__popc(peers);  // the group's highest lane
@@ -192,7 +204,7 @@ k_radix_scatter(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ 
   for (int q = 0; q < kRW; ++q) wcnt[q][t] += dbeg;
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < kRI; ++j) {
+  for (int j = 0; j < RI; ++j) {
     const uint32_t lr = wcnt[w][digit_of(k[j], shift)] + r[j];
     sk[lr] = k[j];
     si[lr] = ix[j];
@@ -212,15 +224,18 @@ k_radix_scatter(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ 
 // Min-ranks from sorted rows: rank[row][idx(p)] = first position of key(p)
 // (rank may be nullptr); rows below pfx_rows also get flag[row][p] =
 // [idx(p) < NP]; with sorted_idx0, row 0 gets sorted_idx0[p] = idx(p).
+// Positions are visited warp-coalesced: segment s = j * 8 + warp covers the
+// 32 positions s * 32 + lane of the tile, in increasing order of s.
 __global__ void __launch_bounds__(kRT)
 k_radix_rank_tiles(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ si, int64_t n, int64_t stride,
                    int64_t NP, uint32_t* __restrict__ rank, uint32_t* __restrict__ flag, int64_t pfx_rows,
                    uint32_t* __restrict__ sorted_idx0) {
+  constexpr int kSeg = kRI * kRW;      // 64 segments of 32 positions
   __shared__ uint64_t kt[kRTile + 1];  // kt[q + 1] = key at base + q, kt[0] = key at base - 1
-  __shared__ uint32_t ws[kRW];
+  __shared__ uint32_t seg_pre[kSeg];   // last run start up to the end of each segment
   __shared__ uint32_t seed_s;
   const int64_t row = blockIdx.y, tile = blockIdx.x;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int64_t base = tile * kRTile;
   const int nvalid = (int)(n - base < kRTile ? n - base : kRTile);
   const uint64_t* K = sk + row * stride;
@@ -244,22 +259,42 @@ k_radix_rank_tiles(const uint64_t* __restrict__ sk, const uint32_t* __restrict__
     seed_s = (uint32_t)lo;
   }
   __syncthreads();
-  // thread t covers the tile positions [t*8, t*8 + 8)
-  uint32_t last = 0;
+  uint32_t hm[kRI];  // run-start lanes of segment j * 8 + w
 #pragma unroll
   for (int j = 0; j < kRI; ++j) {
-    const int q = t * kRI + j;
-    if (q < nvalid && (base + q == 0 || kt[q + 1] != kt[q])) last = (uint32_t)(base + q);
+    const int q = j * kRT + t;
+    const bool head = q < nvalid && (base + q == 0 || kt[q + 1] != kt[q]);
+    hm[j] = __ballot_sync(0xffffffffu, head);
+    if (lane == 0) seg_pre[j * kRW + w] = hm[j] ? (uint32_t)(base + j * kRT + w * 32 + 31 - __clz(hm[j])) : 0u;
   }
-  uint32_t rs = block_exmax(last, ws);
-  rs = rs > seed_s ? rs : seed_s;
+  __syncthreads();
+  if (w == 0) {  // running maximum over the 64 segments, seeded
+    uint32_t a = seg_pre[2 * lane], b = seg_pre[2 * lane + 1];
+    a = a > seed_s ? a : seed_s;
+    b = b > a ? b : a;
+    uint32_t incl = b;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl = x > incl ? x : incl;
+    }
+    const uint32_t ex = __shfl_up_sync(0xffffffffu, incl, 1);
+    const uint32_t before = lane ? (ex > seed_s ? ex : seed_s) : seed_s;
+    seg_pre[2 * lane] = a > before ? a : before;
+    seg_pre[2 * lane + 1] = incl;
+  }
+  __syncthreads();
+  const uint32_t lt = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);  // lanes <= this one
   const bool pf = row < pfx_rows;
   const bool s0 = row == 0 && sorted_idx0 != nullptr;
 #pragma unroll
   for (int j = 0; j < kRI; ++j) {
-    const int q = t * kRI + j;
+    const int q = j * kRT + t;
     if (q < nvalid) {
-      if (base + q == 0 || kt[q + 1] != kt[q]) rs = (uint32_t)(base + q);
+      const int sg = j * kRW + w;
+      const uint32_t m = hm[j] & lt;
+      const uint32_t rs = m ? (uint32_t)(base + j * kRT + w * 32 + 31 - __clz(m))
+                            : (sg ? seg_pre[sg - 1] : seed_s);
       const uint32_t i = I[base + q];
       if (rank) rank[row * n + i] = rs;
       if (pf) flag[row * n + base + q] = (uint64_t)i < (uint64_t)NP ? 1u : 0u;
@@ -270,8 +305,19 @@ k_radix_rank_tiles(const uint64_t* __restrict__ sk, const uint32_t* __restrict__
 
 }  // namespace
 
+namespace {
+// Elements per thread of the sort passes: 8 (2048-element tiles), or 2 for
+// sorts of under about 38 such tiles, which then spread over more SMs.
+// (4-element tiles measured slower than 8 for 40k-200k keys per row: the
+// per-CTA fixed work outweighs the extra parallelism.)
+int sort_ri(int64_t n, int64_t rows) {
+  const int64_t t8 = rows * ((n + 2047) / 2048);
+  return t8 >= 38 ? 8 : 2;
+}
+}  // namespace
+
 size_t ddks_radix_scratch_words(int64_t n, int64_t rows, int64_t pfx_rows) {
-  const int64_t tiles = (n + kRTile - 1) / kRTile;
+  const int64_t tiles = (n + kRT * 2 - 1) / (kRT * 2);  // the smallest sort tile
   const size_t cnt = (size_t)rows * 256 * (size_t)tiles;
   const size_t a = 2 * cnt + (size_t)rows * 256;
   const size_t b = (size_t)pfx_rows * (size_t)n + ddks_scan_tmp_elems(pfx_rows, n);
@@ -288,7 +334,8 @@ cudaError_t ddks_radix_sort(const uint64_t* keys, uint64_t* ka, uint32_t* ia, ui
                             const uint32_t** out_i, cudaStream_t st, int* launches) {
   if (n <= 0 || rows <= 0 || rows > 65535 || nbits <= 0 || nbits > 64 || nbits % 8 || n > 0xFFFFFFFFll)
     return cudaErrorInvalidValue;
-  const int64_t tiles = (n + kRTile - 1) / kRTile;
+  const int RI = sort_ri(n, rows);
+  const int64_t tiles = (n + kRT * RI - 1) / (kRT * RI);
   const size_t ncnt = (size_t)rows * 256 * (size_t)tiles;
   uint32_t* cnt = scratch;
   uint32_t* off = scratch + ncnt;
@@ -301,13 +348,15 @@ cudaError_t ddks_radix_sort(const uint64_t* keys, uint64_t* ka, uint32_t* ia, ui
   uint32_t* di = ia;
   int nl = 0;
   for (int shift = 0; shift < nbits; shift += 8) {
-    k_radix_hist<<<g, kRT, 0, st>>>(ck, n, stride, shift, tiles, cnt);
+    if (RI == 8) k_radix_hist<8><<<g, kRT, 0, st>>>(ck, n, stride, shift, tiles, cnt);
+    else k_radix_hist<2><<<g, kRT, 0, st>>>(ck, n, stride, shift, tiles, cnt);
     if (!self_scan) {
       k_radix_tile_scan<<<dim3(256, (unsigned)rows), kRT, 0, st>>>(cnt, tiles, off, tot);
       ++nl;
     }
-    k_radix_scatter<<<g, kRT, 0, st>>>(ck, ci, dk, di, n, stride, shift, tiles, cnt, self_scan ? nullptr : off,
-                                       tot);
+    const uint32_t* o = self_scan ? nullptr : off;
+    if (RI == 8) k_radix_scatter<8><<<g, kRT, 0, st>>>(ck, ci, dk, di, n, stride, shift, tiles, cnt, o, tot);
+    else k_radix_scatter<2><<<g, kRT, 0, st>>>(ck, ci, dk, di, n, stride, shift, tiles, cnt, o, tot);
     nl += 2;
     ck = dk;
     ci = di;

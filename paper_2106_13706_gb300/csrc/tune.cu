@@ -16,12 +16,18 @@
 #include "ddks_internal.cuh"
 
 constexpr int64_t kDominanceMinN = 32768;
-constexpr int64_t kRadixMinN = 65536;  // pooled N from which key sorts use the radix sort
+// Pooled N from which key sorts use the radix sort by default: 32-bit keys
+// (float32 inputs, 4 digit passes) and 64-bit keys (8 passes).  Measured on
+// GB300 against the chunk sort + merges: 32-bit radix ahead from ~16k keys
+// per row, 64-bit from a few hundred thousand.
+constexpr int64_t kRadixMinN32 = 16384;
+constexpr int64_t kRadixMinN64 = 131072;
 
-bool ddks_use_radix(const ddks_ctx* ctx, int64_t N) {
+bool ddks_use_radix(const ddks_ctx* ctx, int64_t N, int key_bits) {
   const int64_t m = ctx->cfg.radix_min_n;
   if (m < 0) return false;
-  return N >= (m == 0 ? kRadixMinN : m);
+  if (m > 0) return N >= m;
+  return N >= (key_bits <= 32 ? kRadixMinN32 : kRadixMinN64);
 }
 
 static std::string tune_key(int64_t NP, int64_t NT, int32_t d) {

@@ -20,7 +20,7 @@ def test_header_declares_the_boundary():
     for n in ["ddks_ctx_create", "ddks_ctx_destroy", "ddks_distance", "ddks_distance_range",
               "ddks_permutation_test", "ddks_significance", "ddks_batch_distance", "ddks_submit",
               "ddks_poll", "ddks_strerror", "ddks_ctx_stats", "ddks_config_default", "ddks_vdks",
-              "ddks_rdks"]:
+              "ddks_rdks", "ddks_rescale"]:
         assert n in names
 
 
@@ -43,6 +43,9 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.ddks_ctx_destroy(None) == -1
     assert lib.ddks_vdks(None, None, 1, None, 1, 3, 0, 8, None, ctypes.byref(r)) == -1
     assert lib.ddks_rdks(None, None, 1, None, 1, 3, 0, None, ctypes.byref(r), None) == -1
+    lib.ddks_rescale.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.ddks_rescale(None, None, 1, 0.0, 1.0, None, None) == -1
 
 
 def test_library_is_in_tree():

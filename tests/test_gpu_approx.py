@@ -204,3 +204,46 @@ def test_rdks_bench_workload_full_size(torch, ctx):
     P, T = wl.gaussian_pair(0, 1_000_000, 1_000_000, 3, shift=0.05)
     _rdks_same(ctx.rdks(_dev(torch, P), _dev(torch, T)), orc.rdks(P, T))
 
+
+
+def _ieee_rescale(v, lo, span):
+    # NormalizeData in plain IEEE double: numpy's subtraction and division round to nearest
+    if span == 0.0:
+        return np.zeros_like(v)
+    return (v - lo) / span
+
+
+@pytest.mark.parametrize("lo,span", [(0.0, 1.0), (-3.25, 7.5), (1.0, 3.0), (-1e-3, 2.0 ** -20 * 3),
+                                     (12345.678, 0.1), (-2.0 ** 40, 2.0 ** 41 + 1.0), (0.5, 2.0 ** -1000),
+                                     (-7.0, 2.0 ** 60 * 1.75), (3.0, 0.0)])
+def test_rescale_is_ieee_division(torch, ctx, lo, span):
+    # the FMA quotient with its remainder certificate against the IEEE expression, bit for bit
+    rng = np.random.default_rng(abs(hash((lo, span))) % 2 ** 32)
+    n = 1 << 20
+    u = rng.random(n)
+    v = lo + u * span
+    v = np.minimum(np.maximum(v, lo), lo + span)
+    # values whose quotients sit at binade edges, tiny offsets, the ends of the range
+    ks = rng.integers(1, 60, 4096)
+    edge = lo + span * np.ldexp(1.0, -ks) * (1.0 + rng.integers(-3, 4, 4096) * 2.0 ** -52)
+    tiny = lo + np.ldexp(rng.random(4096), -rng.integers(900, 1074, 4096))
+    v = np.concatenate([v, edge, tiny, [lo, lo + span, np.nextafter(lo, np.inf)]])
+    v = v[(v >= lo) & (v <= lo + span) & np.isfinite(v)]
+    ref = _ieee_rescale(v, lo, span)
+    got = ctx.rescale(_dev(torch, v), lo, span).cpu().numpy()
+    assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+    got_h = ctx.rescale(v, lo, span)
+    assert np.array_equal(got_h.view(np.uint64), ref.view(np.uint64))
+
+
+def test_rescale_random_operands(torch, ctx):
+    # random doubles of every magnitude as (v - lo, span) pairs, many per call
+    rng = np.random.default_rng(11)
+    for _ in range(8):
+        span = float(np.ldexp(1.0 + rng.random(), int(rng.integers(-1000, 1000))))
+        e = rng.integers(-1074, 1, 1 << 18)
+        v = np.ldexp(rng.random(1 << 18), e) * span
+        v = np.minimum(v, span)
+        ref = _ieee_rescale(v, 0.0, span)
+        got = ctx.rescale(_dev(torch, v), 0.0, span).cpu().numpy()
+        assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))

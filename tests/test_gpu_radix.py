@@ -86,8 +86,11 @@ def test_rdks_with_radix_sort(torch, d, n_p, n_t, kind, dtype):
     assert got["argmax_origin"] == int(np.argmax(ref["per_corner"] == ref["num_max"]))
 
 
-def test_rdks_radix_and_merge_agree_large(torch):
-    P, T = wl.gaussian_pair(8, 150_000, 150_001, 3, shift=0.05)
+@pytest.mark.parametrize("n_p,n_t", [(100_000, 100_000), (150_000, 150_001)])
+def test_rdks_radix_and_merge_agree_large(torch, n_p, n_t):
+    # 4 rows of 200k (98 tiles of 2048: counts summed by the scatter CTAs)
+    # and of 300k (147 tiles: the count scan kernel)
+    P, T = wl.gaussian_pair(8, n_p, n_t, 3, shift=0.05)
     Pd, Td = _dev(torch, P), _dev(torch, T)
     res = []
     for m in (1, -1):
