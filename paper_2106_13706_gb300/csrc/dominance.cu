@@ -219,6 +219,62 @@ k_dom_scatter(const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout, uin
   }
 }
 
+// The same with the superblock scan folded in (nsb + 1 <= kFusedSB): every
+// CTA scans the level's superblock totals into shared memory itself; CTA 0
+// of each matrix also stores the prefixes (for k_dom_finalize) and the
+// level's zeros Z (for the queries).  Saves the scan kernel per level.
+constexpr uint32_t kFusedSB = 8192;
+__global__ void __launch_bounds__(kThreads)
+k_dom_scatter_fused(const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout, uint32_t n0, uint32_t n1,
+                    uint32_t nmax, uint32_t recw, uint32_t nsb, uint32_t sbw, int bit, int lv,
+                    const uint2* __restrict__ rec, const uint32_t* __restrict__ sbcnt, uint32_t* __restrict__ sb,
+                    uint32_t* __restrict__ Zg) {
+  extern __shared__ uint32_t ssb[];  // nsb + 1 prefixes
+  __shared__ uint32_t ws[kThreads / 32];
+  __shared__ uint32_t carry;
+  const int mtx = blockIdx.y;
+  const uint32_t n = mtx ? n1 : n0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t* C = sbcnt + (size_t)mtx * nsb;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t t0 = 0; t0 < nsb + 1; t0 += kThreads) {
+    const uint32_t i = t0 + threadIdx.x;
+    const uint32_t c = i < nsb ? C[i] : 0u;
+    uint32_t incl = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += x;
+    }
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    uint32_t before = carry;
+    for (int q = 0; q < warp; ++q) before += ws[q];
+    const uint32_t ex = before + incl - c;
+    if (i <= nsb) ssb[i] = ex;
+    __syncthreads();
+    if (threadIdx.x == kThreads - 1) carry = ex + c;
+    __syncthreads();
+  }
+  const uint32_t z = n - ssb[nsb];  // ssb[nsb] = the level's ones
+  if (blockIdx.x == 0) {
+    uint32_t* S = sb + (size_t)mtx * sbw;
+    for (uint32_t i = threadIdx.x; i <= nsb; i += kThreads) S[i] = ssb[i];
+    if (threadIdx.x == 0) Zg[mtx * kMaxLevels + lv] = z;
+  }
+  const uint32_t* v = vin + (size_t)mtx * nmax;
+  uint32_t* o = vout + (size_t)mtx * nmax;
+  const uint2* R = rec + (size_t)mtx * recw;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const uint32_t x = v[k];
+    const uint2 r = R[k >> 5];
+    const uint32_t b = k & 31;
+    const uint32_t ones = ssb[k >> 13] + r.x + (b ? (uint32_t)__popc(r.y & ((1u << b) - 1u)) : 0u);
+    o[((x >> bit) & 1u) ? z + ones : k - ones] = x;
+  }
+}
+
 // Per origin: the four quadrant counts of each sample and the best orthant.
 // hyx[v] = P points with y rank < v.  order (optional, with [ob, oe) the
 // whole pooled range): the origins in dimension-1 order.  Neighbouring
@@ -326,8 +382,15 @@ cudaError_t ddks_launch_dominance(ddks_ctx* ctx, const uint32_t* rank, int64_t N
     uint2* rl = rec + (size_t)lv * 2 * recw;
     uint32_t* sl_ = sbp + (size_t)lv * 2 * sbw;
     k_dom_bits<<<dim3(nsb, 2), kSBWords, 0, st>>>(vbuf[lv & 1], n0, n1, nmax, recw, nsb, bit, rl, sbcnt);
+    ++n;
+    if (lv + 1 < L && nsb + 1 <= kFusedSB) {
+      k_dom_scatter_fused<<<gs, kThreads, 4 * (nsb + 1), st>>>(vbuf[lv & 1], vbuf[(lv + 1) & 1], n0, n1, nmax, recw, nsb, sbw,
+                                                   bit, lv, rl, sbcnt, sl_, Zg);
+      ++n;
+      continue;
+    }
     k_dom_sbscan<<<2, kScanThreads, 0, st>>>(sbcnt, sl_, n0, n1, nsb, sbw, lv, Zg);
-    n += 2;
+    ++n;
     if (lv + 1 < L) {
       k_dom_scatter<<<gs, kThreads, 0, st>>>(vbuf[lv & 1], vbuf[(lv + 1) & 1], n0, n1, nmax, recw, sbw, bit, lv, rl,
                                              sl_, Zg);

@@ -16,7 +16,9 @@
 // k_radix_rank_tiles turns sorted rows into min-ranks: a position starts a
 // run when its key differs from its left neighbour, and the run start of a
 // position is the last run start at or before it (a running maximum), seeded
-// per tile by a binary search when the tile opens inside a run.
+// per tile by a binary search when the tile opens inside a run.  The P counts
+// before each position are per-tile prefixes of ballot counts plus the sum of
+// the earlier tiles' totals (k_radix_pfx_carry).
 #include <cstdint>
 
 #include "ddks_internal.cuh"
@@ -222,17 +224,20 @@ k_radix_scatter(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ 
 }
 
 // Min-ranks from sorted rows: rank[row][idx(p)] = first position of key(p)
-// (rank may be nullptr); rows below pfx_rows also get flag[row][p] =
-// [idx(p) < NP]; with sorted_idx0, row 0 gets sorted_idx0[p] = idx(p).
-// Positions are visited warp-coalesced: segment s = j * 8 + warp covers the
-// 32 positions s * 32 + lane of the tile, in increasing order of s.
+// (rank may be nullptr); rows below pfx_rows also get pfx[row][p] = P points
+// (idx < NP) before position p within the tile and tp[row][tile] = the
+// tile's P points (k_radix_pfx_carry adds the earlier tiles' counts); with
+// sorted_idx0, row 0 gets sorted_idx0[p] = idx(p).  Positions are visited
+// warp-coalesced: segment s = j * 8 + warp covers the 32 positions
+// s * 32 + lane of the tile, in increasing order of s.
 __global__ void __launch_bounds__(kRT)
 k_radix_rank_tiles(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ si, int64_t n, int64_t stride,
-                   int64_t NP, uint32_t* __restrict__ rank, uint32_t* __restrict__ flag, int64_t pfx_rows,
-                   uint32_t* __restrict__ sorted_idx0) {
+                   int64_t NP, uint32_t* __restrict__ rank, uint32_t* __restrict__ pfx, uint32_t* __restrict__ tp,
+                   int64_t pfx_rows, uint32_t* __restrict__ sorted_idx0) {
   constexpr int kSeg = kRI * kRW;      // 64 segments of 32 positions
   __shared__ uint64_t kt[kRTile + 1];  // kt[q + 1] = key at base + q, kt[0] = key at base - 1
   __shared__ uint32_t seg_pre[kSeg];   // last run start up to the end of each segment
+  __shared__ uint32_t seg_p[kSeg];     // P points before each segment (within the tile)
   __shared__ uint32_t seed_s;
   const int64_t row = blockIdx.y, tile = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -287,6 +292,31 @@ k_radix_rank_tiles(const uint64_t* __restrict__ sk, const uint32_t* __restrict__
   const uint32_t lt = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);  // lanes <= this one
   const bool pf = row < pfx_rows;
   const bool s0 = row == 0 && sorted_idx0 != nullptr;
+  uint32_t ix[kRI], pm[kRI];
+#pragma unroll
+  for (int j = 0; j < kRI; ++j) {
+    const int q = j * kRT + t;
+    ix[j] = q < nvalid ? I[base + q] : 0u;
+    pm[j] = __ballot_sync(0xffffffffu, q < nvalid && (uint64_t)ix[j] < (uint64_t)NP);
+    if (pf && lane == 0) seg_p[j * kRW + w] = (uint32_t)__popc(pm[j]);
+  }
+  if (pf) {
+    __syncthreads();
+    if (w == 0) {  // exclusive sums over the 64 segments; the tile's total to tp
+      const uint32_t a = seg_p[2 * lane], b = seg_p[2 * lane + 1];
+      uint32_t incl = a + b;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += x;
+      }
+      const uint32_t ex = incl - a - b;
+      seg_p[2 * lane] = ex;
+      seg_p[2 * lane + 1] = ex + a;
+      if (lane == 31) tp[row * gridDim.x + tile] = incl;
+    }
+    __syncthreads();
+  }
 #pragma unroll
   for (int j = 0; j < kRI; ++j) {
     const int q = j * kRT + t;
@@ -295,12 +325,35 @@ k_radix_rank_tiles(const uint64_t* __restrict__ sk, const uint32_t* __restrict__
       const uint32_t m = hm[j] & lt;
       const uint32_t rs = m ? (uint32_t)(base + j * kRT + w * 32 + 31 - __clz(m))
                             : (sg ? seg_pre[sg - 1] : seed_s);
-      const uint32_t i = I[base + q];
+      const uint32_t i = ix[j];
       if (rank) rank[row * n + i] = rs;
-      if (pf) flag[row * n + base + q] = (uint64_t)i < (uint64_t)NP ? 1u : 0u;
+      if (pf) pfx[row * n + base + q] = seg_p[sg] + (uint32_t)__popc(pm[j] & (lt >> 1));
       if (s0) sorted_idx0[base + q] = i;
     }
   }
+}
+
+// Grid (tiles, pfx_rows): adds the P points of the row's earlier tiles to the
+// tile's in-tile prefixes.
+__global__ void __launch_bounds__(kRT)
+k_radix_pfx_carry(uint32_t* __restrict__ pfx, const uint32_t* __restrict__ tp, int64_t n) {
+  __shared__ uint32_t ws[kRW];
+  const int64_t row = blockIdx.y, tile = blockIdx.x;
+  if (tile == 0) return;
+  const uint32_t* TP = tp + row * gridDim.x;
+  uint32_t c = 0;
+  for (int64_t q = threadIdx.x; q < tile; q += kRT) c += TP[q];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+  __syncthreads();
+  uint32_t carry = 0;
+#pragma unroll
+  for (int q = 0; q < kRW; ++q) carry += ws[q];
+  const int64_t base = tile * kRTile;
+  const int nvalid = (int)(n - base < kRTile ? n - base : kRTile);
+  uint32_t* Pr = pfx + row * n + base;
+  for (int q = threadIdx.x; q < nvalid; q += kRT) Pr[q] += carry;
 }
 
 }  // namespace
@@ -320,7 +373,7 @@ size_t ddks_radix_scratch_words(int64_t n, int64_t rows, int64_t pfx_rows) {
   const int64_t tiles = (n + kRT * 2 - 1) / (kRT * 2);  // the smallest sort tile
   const size_t cnt = (size_t)rows * 256 * (size_t)tiles;
   const size_t a = 2 * cnt + (size_t)rows * 256;
-  const size_t b = (size_t)pfx_rows * (size_t)n + ddks_scan_tmp_elems(pfx_rows, n);
+  const size_t b = (size_t)pfx_rows * (size_t)((n + kRTile - 1) / kRTile);
   return a > b ? a : b;
 }
 
@@ -380,14 +433,13 @@ cudaError_t ddks_radix_ranks(const uint64_t* sk, const uint32_t* si, int64_t n, 
   if (n <= 0 || rows <= 0 || rows > 65535) return cudaErrorInvalidValue;
   const int64_t tiles = (n + kRTile - 1) / kRTile;
   if (!pfx) pfx_rows = 0;
-  uint32_t* flag = scratch;
-  uint32_t* tmp = scratch + (size_t)pfx_rows * (size_t)n;
-  k_radix_rank_tiles<<<dim3((unsigned)tiles, (unsigned)rows), kRT, 0, st>>>(sk, si, n, stride, NP, rank, flag,
+  uint32_t* tp = scratch;  // [pfx_rows][tiles] P points per tile
+  k_radix_rank_tiles<<<dim3((unsigned)tiles, (unsigned)rows), kRT, 0, st>>>(sk, si, n, stride, NP, rank, pfx, tp,
                                                                              pfx_rows, sorted_idx0);
   int nl = 1;
-  if (pfx_rows > 0) {
-    cudaError_t e = ddks_scan_rows(flag, pfx, pfx_rows, n, true, tmp, st, &nl);
-    if (e != cudaSuccess) return e;
+  if (pfx_rows > 0 && tiles > 1) {
+    k_radix_pfx_carry<<<dim3((unsigned)tiles, (unsigned)pfx_rows), kRT, 0, st>>>(pfx, tp, n);
+    ++nl;
   }
   if (launches) *launches += nl;
   return cudaGetLastError();
