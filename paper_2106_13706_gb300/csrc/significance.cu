@@ -251,6 +251,7 @@ int ddks_significance(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, i
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "significance");
   if ((unsigned)(ctx->h_out[4] & 0xFFFFFFFFull) & ddks::kFlagNaN) return DDKS_ENAN;
+  if ((unsigned)(ctx->h_out[4] & 0xFFFFFFFFull) & ddks::kFlagTimeout) return DDKS_ETIMEOUT;
   double v[2];
   memcpy(v, ctx->h_out, sizeof v);
   *S = v[0];
