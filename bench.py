@@ -492,8 +492,10 @@ def run_approx(args):
         # roofline is taken on the slowest stage, all HBM-bound.
         S = d + 1
         stage_bytes = [N * d * P.itemsize + S * N * 8, S * N * 16, S * N * 16]
-        names = ["range + corner distances (k_minmax + k_rdks_dist_*)",
-                 "sort of the corner distance lists (k_chunk_sort + k_merge_tile)",
+        sort_name = ("per-corner warp sort and walk (k_rdks_small)" if N <= 1024 else
+                     "sort of the corner distance lists (radix: k_radix_hist/tile_scan/scatter, k_radix_rank_tiles)"
+                     if N >= 131072 else "sort of the corner distance lists (k_chunk_sort + k_merge_tile)")
+        names = ["range + corner distances (k_minmax + k_rdks_dist_*)", sort_name,
                  "KS walk (k_rdks_walk + k_rdks_final)"]
         k = max(range(3), key=lambda i: st[i])
         ach = stage_bytes[k] / (st[k] * 1e-3) / 1e9
@@ -649,10 +651,10 @@ def run_dom2d(args):
         stages.append(ctx.stage_times())
     ctx.set_stage_timing(False)
     st = [statistics.mean(x[i] for x in stages) for i in range(3)]
-    # the range queries: per origin three wavelet-matrix walks of L levels,
-    # two 8-byte rank lookups (prefix word + bit word) per level
+    # the range queries: per origin two wavelet-matrix walks (all points, P
+    # points) of L levels, two 8-byte record lookups (range ends) per level
     L = max(1, (N - 1).bit_length())
-    nbytes = N * 3 * L * 2 * 8
+    nbytes = N * 2 * L * 2 * 8
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs") or 6800.0
     ach = nbytes / (st[1] * 1e-3) / 1e9
