@@ -255,8 +255,10 @@ k_radix_rank_tiles(const uint64_t* __restrict__ sk, const uint32_t* __restrict__
   const int nvalid = (int)(n - base < kRTile ? n - base : kRTile);
   const uint64_t* K = sk + row * stride;
   const uint32_t* I = si + row * stride;
-  for (int q = t; q < nvalid; q += kRT) kt[q + 1] = K[base + q];
-  if (t == 0) {
+  const bool want_rank = rank != nullptr;  // without ranks the keys are not read
+  if (want_rank)
+    for (int q = t; q < nvalid; q += kRT) kt[q + 1] = K[base + q];
+  if (t == 0 && want_rank) {
     // the run start of the tile's first key: base unless the run began before
     int64_t lo = base;
     if (base > 0) {
@@ -278,12 +280,12 @@ k_radix_rank_tiles(const uint64_t* __restrict__ sk, const uint32_t* __restrict__
 #pragma unroll
   for (int j = 0; j < kRI; ++j) {
     const int q = j * kRT + t;
-    const bool head = q < nvalid && (base + q == 0 || kt[q + 1] != kt[q]);
+    const bool head = want_rank && q < nvalid && (base + q == 0 || kt[q + 1] != kt[q]);
     hm[j] = __ballot_sync(0xffffffffu, head);
     if (lane == 0) seg_pre[j * kRW + w] = hm[j] ? (uint32_t)(base + j * kRT + w * 32 + 31 - __clz(hm[j])) : 0u;
   }
   __syncthreads();
-  if (w == 0) {  // running maximum over the 64 segments, seeded
+  if (w == 0 && want_rank) {  // running maximum over the 64 segments, seeded
     uint32_t a = seg_pre[2 * lane], b = seg_pre[2 * lane + 1];
     a = a > seed_s ? a : seed_s;
     b = b > a ? b : a;
