@@ -10,18 +10,21 @@
 // dimension-1 rank of the point at position k.  The other three quadrants
 // follow from the marginals: #{x_0 >= o_0} = N - rank_0(o) (its P part from
 // K0's P prefix at that position), #{x_1 >= o_1} = N - rank_1(o) (its P part
-// by a second query over the whole range).
+// from a histogram of the P points' y ranks).
 //
 // The range queries run on two wavelet matrices (the wavelet tree variant of
-// Information Systems 47, 2015): one over the y ranks of all points in
-// dimension-0 order, one
-// over the P points only.  Level l of a matrix holds one bit per position
-// (bit L-1-l of the value), a per-word prefix count of ones, and the next
-// level's order: a stable partition, zeros first.  A query walks the L levels
-// with two rank lookups each (an 8-byte word record plus a superblock
-// prefix).  Build: per level a bit kernel (warp ballots; prefixes within
-// superblocks of 256 words), a scan of the superblock totals and a scatter
-// kernel; query: one thread per origin.
+// Information Systems 47, 2015) over a 4-letter alphabet: one over the y
+// ranks of all points in dimension-0 order, one over the P points only.
+// Level l of a matrix holds the 2-bit symbol (bits 2(LL-1-l) and up) of
+// every position as two bit planes, per 32 positions the counts of symbols
+// >= 1, >= 2, >= 3 before them, and the next level's order: a stable
+// partition by symbol.  A query walks the LL = ceil(L/2) levels with two
+// record lookups each (16 bytes: both planes and three 16-bit counts
+// relative to a superblock of 65,536 positions, whose bases sit in shared
+// memory), half the levels of the binary matrix.  Build: per level a bit
+// kernel (warp ballots; counts within 8,192-position chunks), a scan of the
+// chunk totals and a scatter kernel; a finalize pass makes the counts
+// superblock-relative; query: one thread per origin.
 #include <cstring>
 
 #include "../../include/ddks.h"
@@ -31,52 +34,59 @@
 namespace {
 
 constexpr int kThreads = 256;
-
 constexpr int kScanThreads = 1024;
-constexpr int kMaxLevels = 32;
-constexpr int kSBWords = 256;  // words per superblock (8192 positions), one CTA of k_dom_bits
+constexpr int kMaxLevels = 16;         // 2-bit levels: ranks below 2^32
+constexpr int kChunkWords = 256;       // words per chunk (8192 positions), one CTA of k_quad_bits
+constexpr int kChunkShift = 13;
+constexpr int kSBChunks = 8;           // chunks per superblock (65536 positions)
+constexpr int kSBShift = 16;
+constexpr int kSmemBases = 2048;       // superblock bases held in shared memory by the query (uint4 each)
 
-// One wavelet matrix in device memory for the queries.  Level lv: records at
-// rec + lv * stride, record w = {ones before word w, bit word w}.  (While a
-// level is built its records count only the ones within their superblock of
-// kSBWords words, with the superblock prefixes beside them; k_dom_finalize
-// adds those in once every level exists.)
-struct WMView {
-  const uint2* rec;
-  uint32_t stride;
-  int L;
+// Ranks at position k from record r (word k / 32) and superblock base s:
+// g[c] = #{positions < k with symbol >= c}, c = 0..4 (g[0] = k, g[4] = 0).
+struct Ge {
+  uint32_t g1, g2, g3;
+};
+DDKS_DEV Ge ranks_at(uint4 r, uint4 s, uint32_t k) {
+  const uint32_t b = k & 31;
+  const uint32_t below = b ? ((1u << b) - 1u) : 0u;
+  Ge o;
+  o.g1 = s.x + (r.z & 0xFFFFu) + (uint32_t)__popc((r.x | r.y) & below);
+  o.g2 = s.y + (r.z >> 16) + (uint32_t)__popc(r.y & below);
+  o.g3 = s.z + r.w + (uint32_t)__popc((r.x & r.y) & below);
+  return o;
+}
+DDKS_DEV uint32_t ge_pick(const Ge& g, uint32_t k, uint32_t c) {
+  return c == 0 ? k : c == 1 ? g.g1 : c == 2 ? g.g2 : c == 3 ? g.g3 : 0u;
+}
+
+// One finalized matrix for the queries: level lv's records at rec + lv *
+// stride, its superblock bases at sb + lv * sbstride, its bucket starts
+// (first position of each symbol in the next order) at st + lv * 4.
+struct QView {
+  const uint4* rec;
+  const uint4* sb;
+  const uint32_t* st;
+  uint32_t stride, sbstride;
+  int LL;
 };
 
-DDKS_DEV uint32_t rank1(const uint2* rec, const uint32_t* sb, uint32_t k) {
-  const uint2 r = rec[k >> 5];
-  const uint32_t b = k & 31;
-  return sb[k >> 13] + r.x + (b ? (uint32_t)__popc(r.y & ((1u << b) - 1u)) : 0u);
-}
-
-// After k_dom_finalize the records hold absolute prefixes: one load per rank.
-DDKS_DEV uint32_t rank1_abs(const uint2* rec, uint32_t k) {
-  const uint2 r = rec[k >> 5];
-  const uint32_t b = k & 31;
-  return r.x + (b ? (uint32_t)__popc(r.y & ((1u << b) - 1u)) : 0u);
-}
-
-// #{k in [l, r) : value(k) >= v}; Z[lv] = zeros of level lv (finalized records)
-DDKS_DEV uint32_t count_ge(const WMView& wm, const uint32_t* Z, uint32_t l, uint32_t r, uint32_t v) {
-  const uint32_t len = r - l;
-  uint32_t less = 0;
-  for (int lv = 0; lv < wm.L && l < r; ++lv) {
-    const uint2* rec = wm.rec + (size_t)lv * wm.stride;
-    const uint32_t ol = rank1_abs(rec, l), orr = rank1_abs(rec, r);
-    if ((v >> (wm.L - 1 - lv)) & 1u) {
-      less += (r - l) - (orr - ol);  // the zeros of this level are smaller
-      l = Z[lv] + ol;
-      r = Z[lv] + orr;
-    } else {
-      l -= ol;
-      r -= orr;
-    }
+// #{k in [lo, hi) : value(k) >= v}
+DDKS_DEV uint32_t count_ge4(const QView& q, uint32_t lo, uint32_t hi, uint32_t v) {
+  uint32_t greater = 0;
+  for (int lv = 0; lv < q.LL && lo < hi; ++lv) {
+    const uint32_t c = (v >> (2 * (q.LL - 1 - lv))) & 3u;
+    const uint4* R = q.rec + (size_t)lv * q.stride;
+    const uint4* S = q.sb + (size_t)lv * q.sbstride;
+    const Ge a = ranks_at(R[lo >> 5], S[lo >> kSBShift], lo);
+    const Ge b = ranks_at(R[hi >> 5], S[hi >> kSBShift], hi);
+    const uint32_t a1 = ge_pick(a, lo, c + 1), b1 = ge_pick(b, hi, c + 1);
+    greater += b1 - a1;  // symbols above v's at this level
+    const uint32_t s0 = q.st[lv * 4 + c];
+    lo = s0 + ge_pick(a, lo, c) - a1;
+    hi = s0 + ge_pick(b, hi, c) - b1;
   }
-  return len - less;
+  return greater + (hi > lo ? hi - lo : 0u);
 }
 
 // Level-0 values: y ranks in dimension-0 order, for all points (matrix 0) and
@@ -97,23 +107,23 @@ k_dom_init(const uint32_t* __restrict__ rank, const uint32_t* __restrict__ sorte
   }
 }
 
-// Bit words of one level: CTA (x, matrix) covers superblock x (kSBWords
-// words).  Writes each word's bits and its prefix within the superblock into
-// the records, and the superblock's total into sbcnt.
-__global__ void __launch_bounds__(kSBWords)
-k_dom_bits(const uint32_t* __restrict__ vals, uint32_t n0, uint32_t n1, uint32_t nmax, uint32_t recw,
-           uint32_t nsb, int bit, uint2* __restrict__ rec, uint32_t* __restrict__ sbcnt) {
-  __shared__ uint32_t cw[kSBWords];
-  __shared__ uint32_t ws[kSBWords / 32];
+// Symbol planes of one level: CTA (x, matrix) covers chunk x (kChunkWords
+// words).  Record w = {plane 0, plane 1, counts of symbols >= 1 and >= 2
+// before the word within the chunk (16 bits each), of >= 3}; the chunk's
+// three totals go to ctot[(matrix * nchunks + x) * 4 + c - 1].
+__global__ void __launch_bounds__(kChunkWords)
+k_quad_bits(const uint32_t* __restrict__ vals, uint32_t n0, uint32_t n1, uint32_t nmax, uint32_t recw,
+            uint32_t nchunks, int shift, uint4* __restrict__ rec, uint32_t* __restrict__ ctot) {
+  __shared__ uint32_t cw0[kChunkWords], cw1[kChunkWords];
+  __shared__ unsigned long long ws[kChunkWords / 32];
   const int mtx = blockIdx.y;
   const uint32_t n = mtx ? n1 : n0;
   const uint32_t* v = vals + (size_t)mtx * nmax;
-  uint2* R = rec + (size_t)mtx * recw;
+  uint4* R = rec + (size_t)mtx * recw;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t w0 = blockIdx.x * kSBWords;
-  // warp `warp` builds words w0 + warp + 8 q, q < 32: all loads first, then
-  // the ballots
-  constexpr int kPerWarp = kSBWords / (kSBWords / 32);
+  const uint32_t w0 = blockIdx.x * kChunkWords;
+  // warp `warp` builds words w0 + warp + 8 q, q < 32: all loads first, then the ballots
+  constexpr int kPerWarp = kChunkWords / (kChunkWords / 32);
   uint32_t x[kPerWarp];
 #pragma unroll
   for (int q = 0; q < kPerWarp; ++q) {
@@ -123,155 +133,136 @@ k_dom_bits(const uint32_t* __restrict__ vals, uint32_t n0, uint32_t n1, uint32_t
 #pragma unroll
   for (int q = 0; q < kPerWarp; ++q) {
     const uint32_t k = (w0 + warp + 8 * q) * 32 + lane;
-    const uint32_t word = __ballot_sync(0xffffffffu, k < n && ((x[q] >> bit) & 1u));
-    if (lane == 0) cw[warp + 8 * q] = word;
+    const uint32_t sym = k < n ? (x[q] >> shift) & 3u : 0u;
+    const uint32_t b0 = __ballot_sync(0xffffffffu, sym & 1u);
+    const uint32_t b1 = __ballot_sync(0xffffffffu, (sym >> 1) & 1u);
+    if (lane == 0) {
+      cw0[warp + 8 * q] = b0;
+      cw1[warp + 8 * q] = b1;
+    }
   }
   __syncthreads();
-  const uint32_t word = cw[threadIdx.x];
-  const uint32_t c = (uint32_t)__popc(word);
-  uint32_t incl = c;
+  const uint32_t p0 = cw0[threadIdx.x], p1 = cw1[threadIdx.x];
+  // the three counts packed 21 bits apart (a chunk holds at most 8192 of each)
+  const unsigned long long c = (unsigned long long)__popc(p0 | p1) | ((unsigned long long)__popc(p1) << 21) |
+                               ((unsigned long long)__popc(p0 & p1) << 42);
+  unsigned long long incl = c;
+#pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl += x;
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += y;
   }
   if (lane == 31) ws[warp] = incl;
   __syncthreads();
-  uint32_t before = 0;
+  unsigned long long before = 0;
   for (int q = 0; q < warp; ++q) before += ws[q];
+  const unsigned long long ex = before + incl - c;
+  const uint32_t e1 = (uint32_t)(ex & 0x1FFFFFu), e2 = (uint32_t)((ex >> 21) & 0x1FFFFFu),
+                 e3 = (uint32_t)(ex >> 42);
   const uint32_t w = w0 + threadIdx.x;
-  if (w < recw) R[w] = make_uint2(before + incl - c, word);
-  if (threadIdx.x == kSBWords - 1) sbcnt[(size_t)mtx * nsb + blockIdx.x] = before + incl;
+  if (w < recw) R[w] = make_uint4(p0, p1, e1 | (e2 << 16), e3);
+  if (threadIdx.x == kChunkWords - 1) {
+    const unsigned long long t = before + incl;
+    uint32_t* T = ctot + ((size_t)mtx * nchunks + blockIdx.x) * 4;
+    T[0] = (uint32_t)(t & 0x1FFFFFu);
+    T[1] = (uint32_t)((t >> 21) & 0x1FFFFFu);
+    T[2] = (uint32_t)(t >> 42);
+  }
 }
 
-// One CTA per matrix: exclusive prefix of the superblock totals into sb (nsb
-// + 1 entries, the last the level's ones); Z[matrix * kMaxLevels + lv] =
-// zeros of the level.
+// One CTA per matrix: exclusive prefixes of the chunk totals into cpre
+// (nchunks + 1 entries of 4 words, the last the level's totals) and the
+// level's bucket starts st[matrix][lv][c] = #{symbols < c}.
 __global__ void __launch_bounds__(kScanThreads)
-k_dom_sbscan(const uint32_t* __restrict__ sbcnt, uint32_t* __restrict__ sb, uint32_t n0, uint32_t n1, uint32_t nsb,
-             uint32_t sbw, int lv, uint32_t* __restrict__ Z) {
-  __shared__ uint32_t ws[kScanThreads / 32];
-  __shared__ uint32_t carry;
+k_quad_cscan(const uint32_t* __restrict__ ctot, uint32_t* __restrict__ cpre, uint32_t n0, uint32_t n1,
+             uint32_t nchunks, size_t cpre_mstride, int lv, uint32_t* __restrict__ st) {
+  __shared__ uint32_t ws[3][kScanThreads / 32];
+  __shared__ uint32_t carry[3];
   const int mtx = blockIdx.x;
   const uint32_t n = mtx ? n1 : n0;
-  const uint32_t* C = sbcnt + (size_t)mtx * nsb;
-  uint32_t* S = sb + (size_t)mtx * sbw;
+  const uint32_t* C = ctot + (size_t)mtx * nchunks * 4;
+  uint32_t* P = cpre + (size_t)mtx * cpre_mstride;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry = 0;
+  if (threadIdx.x < 3) carry[threadIdx.x] = 0;
   __syncthreads();
-  for (uint32_t t0 = 0; t0 < nsb + 1; t0 += kScanThreads) {  // tiles of coalesced entries
+  for (uint32_t t0 = 0; t0 < nchunks + 1; t0 += kScanThreads) {
     const uint32_t i = t0 + threadIdx.x;
-    const uint32_t c = i < nsb ? C[i] : 0u;
-    uint32_t incl = c;
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += x;
-    }
-    if (lane == 31) ws[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      const uint32_t t = ws[lane];
-      uint32_t ti = t;
+    uint32_t ex[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const uint32_t v = i < nchunks ? C[(size_t)i * 4 + c] : 0u;
+      uint32_t incl = v;
       for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t x = __shfl_up_sync(0xffffffffu, ti, off);
-        if (lane >= off) ti += x;
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
       }
-      ws[lane] = ti - t;
+      if (lane == 31) ws[c][warp] = incl;
+      __syncthreads();
+      uint32_t before = carry[c];
+      for (int q = 0; q < warp; ++q) before += ws[c][q];
+      ex[c] = before + incl - v;
+      __syncthreads();
+      if (threadIdx.x == kScanThreads - 1) carry[c] = ex[c] + v;
+      __syncthreads();
     }
-    __syncthreads();
-    const uint32_t ex = carry + ws[warp] + incl - c;
-    if (i <= nsb) S[i] = ex;
-    if (i == nsb) Z[mtx * kMaxLevels + lv] = n - ex;  // ex = all ones of the level
-    __syncthreads();
-    if (threadIdx.x == kScanThreads - 1) carry = ex + c;
-    __syncthreads();
+    if (i <= nchunks) {
+      P[(size_t)i * 4 + 0] = ex[0];
+      P[(size_t)i * 4 + 1] = ex[1];
+      P[(size_t)i * 4 + 2] = ex[2];
+      P[(size_t)i * 4 + 3] = 0u;
+    }
+    if (i == nchunks) {  // ex = the level's totals of symbols >= 1, 2, 3
+      uint32_t* S = st + ((size_t)mtx * kMaxLevels + lv) * 4;
+      S[0] = 0u;
+      S[1] = n - ex[0];
+      S[2] = n - ex[1];
+      S[3] = n - ex[2];
+    }
   }
 }
 
-// Adds the superblock prefixes into the records of every level and matrix
-// (recs records of recw per matrix and level), for the queries.
+// Stable partition of one level by symbol into the next level's order.
 __global__ void __launch_bounds__(kThreads)
-k_dom_finalize(uint2* __restrict__ rec, const uint32_t* __restrict__ sb, uint64_t recs, uint32_t recw,
-               uint32_t sbw) {
+k_quad_scatter(const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout, uint32_t n0, uint32_t n1,
+               uint32_t nmax, uint32_t recw, size_t cpre_mstride, int shift, int lv, const uint4* __restrict__ rec,
+               const uint32_t* __restrict__ cpre, const uint32_t* __restrict__ st) {
+  const int mtx = blockIdx.y;
+  const uint32_t n = mtx ? n1 : n0;
+  const uint32_t* v = vin + (size_t)mtx * nmax;
+  uint32_t* o = vout + (size_t)mtx * nmax;
+  const uint4* R = rec + (size_t)mtx * recw;
+  const uint4* P = reinterpret_cast<const uint4*>(cpre + (size_t)mtx * cpre_mstride);
+  const uint32_t* S = st + ((size_t)mtx * kMaxLevels + lv) * 4;
+  const uint32_t s1 = S[1], s2 = S[2], s3 = S[3];
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const uint32_t y = v[k];
+    const uint32_t c = (y >> shift) & 3u;
+    const Ge g = ranks_at(R[k >> 5], P[k >> kChunkShift], k);  // chunk-relative records + chunk prefix
+    const uint32_t eq = ge_pick(g, k, c) - ge_pick(g, k, c + 1);
+    const uint32_t s0 = c == 0 ? 0u : c == 1 ? s1 : c == 2 ? s2 : s3;
+    o[s0 + eq] = y;
+  }
+}
+
+// Makes the records superblock-relative (absolute count = chunk prefix +
+// record, minus the superblock's base) and writes the superblock bases
+// sb[row][j] = cpre[row][j * kSBChunks] (row = level * 2 + matrix).
+__global__ void __launch_bounds__(kThreads)
+k_quad_finalize(uint4* __restrict__ rec, const uint32_t* __restrict__ cpre, uint4* __restrict__ sb, uint64_t recs,
+                uint32_t recw, size_t cpre_mstride, uint32_t nsb) {
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < recs;
        t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t row = t / recw;  // level * 2 + matrix
+    const uint64_t row = t / recw;
     const uint32_t w = (uint32_t)(t - row * recw);
-    rec[t].x += sb[row * sbw + (w / kSBWords)];
-  }
-}
-
-// Stable partition of one level (zeros first) into the next level's order.
-__global__ void __launch_bounds__(kThreads)
-k_dom_scatter(const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout, uint32_t n0, uint32_t n1,
-              uint32_t nmax, uint32_t recw, uint32_t sbw, int bit, int lv, const uint2* __restrict__ rec,
-              const uint32_t* __restrict__ sb, const uint32_t* __restrict__ Z) {
-  const int mtx = blockIdx.y;
-  const uint32_t n = mtx ? n1 : n0;
-  const uint32_t* v = vin + (size_t)mtx * nmax;
-  uint32_t* o = vout + (size_t)mtx * nmax;
-  const uint2* R = rec + (size_t)mtx * recw;
-  const uint32_t* S = sb + (size_t)mtx * sbw;
-  const uint32_t z = Z[mtx * kMaxLevels + lv];
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const uint32_t x = v[k];
-    const uint32_t ones = rank1(R, S, k);
-    o[((x >> bit) & 1u) ? z + ones : k - ones] = x;
-  }
-}
-
-// The same with the superblock scan folded in (nsb + 1 <= kFusedSB): every
-// CTA scans the level's superblock totals into shared memory itself; CTA 0
-// of each matrix also stores the prefixes (for k_dom_finalize) and the
-// level's zeros Z (for the queries).  Saves the scan kernel per level.
-constexpr uint32_t kFusedSB = 8192;
-__global__ void __launch_bounds__(kThreads)
-k_dom_scatter_fused(const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout, uint32_t n0, uint32_t n1,
-                    uint32_t nmax, uint32_t recw, uint32_t nsb, uint32_t sbw, int bit, int lv,
-                    const uint2* __restrict__ rec, const uint32_t* __restrict__ sbcnt, uint32_t* __restrict__ sb,
-                    uint32_t* __restrict__ Zg) {
-  extern __shared__ uint32_t ssb[];  // nsb + 1 prefixes
-  __shared__ uint32_t ws[kThreads / 32];
-  __shared__ uint32_t carry;
-  const int mtx = blockIdx.y;
-  const uint32_t n = mtx ? n1 : n0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t* C = sbcnt + (size_t)mtx * nsb;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (uint32_t t0 = 0; t0 < nsb + 1; t0 += kThreads) {
-    const uint32_t i = t0 + threadIdx.x;
-    const uint32_t c = i < nsb ? C[i] : 0u;
-    uint32_t incl = c;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += x;
-    }
-    if (lane == 31) ws[warp] = incl;
-    __syncthreads();
-    uint32_t before = carry;
-    for (int q = 0; q < warp; ++q) before += ws[q];
-    const uint32_t ex = before + incl - c;
-    if (i <= nsb) ssb[i] = ex;
-    __syncthreads();
-    if (threadIdx.x == kThreads - 1) carry = ex + c;
-    __syncthreads();
-  }
-  const uint32_t z = n - ssb[nsb];  // ssb[nsb] = the level's ones
-  if (blockIdx.x == 0) {
-    uint32_t* S = sb + (size_t)mtx * sbw;
-    for (uint32_t i = threadIdx.x; i <= nsb; i += kThreads) S[i] = ssb[i];
-    if (threadIdx.x == 0) Zg[mtx * kMaxLevels + lv] = z;
-  }
-  const uint32_t* v = vin + (size_t)mtx * nmax;
-  uint32_t* o = vout + (size_t)mtx * nmax;
-  const uint2* R = rec + (size_t)mtx * recw;
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const uint32_t x = v[k];
-    const uint2 r = R[k >> 5];
-    const uint32_t b = k & 31;
-    const uint32_t ones = ssb[k >> 13] + r.x + (b ? (uint32_t)__popc(r.y & ((1u << b) - 1u)) : 0u);
-    o[((x >> bit) & 1u) ? z + ones : k - ones] = x;
+    const uint32_t chunk = w / kChunkWords, sbi = chunk / kSBChunks;
+    const uint4* P = reinterpret_cast<const uint4*>(cpre + row * cpre_mstride);
+    const uint4 pc = P[chunk], pb = P[sbi * kSBChunks];
+    uint4 r = rec[t];
+    const uint32_t a1 = pc.x + (r.z & 0xFFFFu) - pb.x, a2 = pc.y + (r.z >> 16) - pb.y, a3 = pc.z + r.w - pb.z;
+    r.z = a1 | (a2 << 16);
+    r.w = a3;
+    rec[t] = r;
+    if (w == sbi * kSBChunks * kChunkWords) sb[row * nsb + sbi] = make_uint4(pb.x, pb.y, pb.z, 0u);
   }
 }
 
@@ -279,23 +270,33 @@ k_dom_scatter_fused(const uint32_t* __restrict__ vin, uint32_t* __restrict__ vou
 // hyx[v] = P points with y rank < v.  order (optional, with [ob, oe) the
 // whole pooled range): the origins in dimension-1 order.  Neighbouring
 // threads then share the high bits of their y ranks, so the upper ends of
-// their query ranges (N and NP at level 0, then fixed by those bits) follow
-// the same positions and their record loads coincide.
+// their query ranges (N and NP at level 0, then fixed by those symbols)
+// follow the same positions and their record loads coincide.  Superblock
+// bases (sbwords uint4 for both matrices and every level) are staged in
+// shared memory when they fit.
 __global__ void __launch_bounds__(kThreads)
 k_dom_query(const uint32_t* __restrict__ rank, const uint32_t* __restrict__ pprefix0,
             const uint32_t* __restrict__ hyx, int64_t N, int64_t NP, int64_t NT, int64_t ob, int64_t oe,
-            WMView wa, WMView wp, const uint32_t* __restrict__ Zg, const uint32_t* __restrict__ order,
-            uint64_t* __restrict__ best, int32_t* __restrict__ bestj) {
-  __shared__ uint32_t Z[2 * kMaxLevels];
-  if (threadIdx.x < 2 * kMaxLevels) Z[threadIdx.x] = Zg[threadIdx.x];
+            QView wa, QView wp, uint32_t sbwords, const uint32_t* __restrict__ order, uint64_t* __restrict__ best,
+            int32_t* __restrict__ bestj) {
+  extern __shared__ uint4 ssb[];  // sbwords entries when they fit, else unused
+  __shared__ uint32_t sst[2 * kMaxLevels * 4];
+  if (sbwords <= kSmemBases) {  // wa.sb .. wa.sb + sbwords holds both matrices' bases
+    for (uint32_t i = threadIdx.x; i < sbwords; i += blockDim.x) ssb[i] = wa.sb[i];
+    wp.sb = ssb + (wp.sb - wa.sb);
+    wa.sb = ssb;
+  }
+  for (int i = threadIdx.x; i < 2 * kMaxLevels * 4; i += blockDim.x) sst[i] = wa.st[i];
   __syncthreads();
+  wp.st = sst + (wp.st - wa.st);
+  wa.st = sst;
   for (int64_t k = ob + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < oe;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = order ? (int64_t)order[k] : k;
     const uint32_t rx = rank[o], ry = rank[N + o];
     const uint32_t lxp = rx < (uint64_t)N ? pprefix0[rx] : (uint32_t)NP;  // P points with x_0 < o_0
-    const uint64_t a3 = count_ge(wa, Z, rx, (uint32_t)N, ry);             // both >=, all points
-    const uint64_t p3 = count_ge(wp, Z + kMaxLevels, lxp, (uint32_t)NP, ry);  // both >=, P
+    const uint64_t a3 = count_ge4(wa, rx, (uint32_t)N, ry);                // both >=, all points
+    const uint64_t p3 = count_ge4(wp, lxp, (uint32_t)NP, ry);              // both >=, P
     const uint64_t pyu = (uint64_t)NP - hyx[ry];                          // P with x_1 >= o_1
     const uint64_t axu = (uint64_t)N - rx, pxu = (uint64_t)NP - lxp;      // x_0 >= o_0
     const uint64_t ayu = (uint64_t)N - ry;                                // x_1 >= o_1
@@ -339,30 +340,35 @@ cudaError_t ddks_launch_dominance(ddks_ctx* ctx, const uint32_t* rank, int64_t N
   int n = 0;
   int L = 1;
   while (((int64_t)1 << L) < N) ++L;  // values (ranks) < N <= 2^L
-  if (L > kMaxLevels) return cudaErrorInvalidValue;
+  const int LL = (L + 1) / 2;         // 2-bit levels
+  if (LL > kMaxLevels) return cudaErrorInvalidValue;
   const uint32_t n0 = (uint32_t)N, n1 = (uint32_t)NP, nmax = n0;
-  // records per matrix and level: whole superblocks covering position nmax
-  // (rank1 may look at word nmax / 32)
-  const uint32_t nsb = nmax / (32 * kSBWords) + 1;
-  const uint32_t recw = nsb * kSBWords;
-  const uint32_t sbw = nsb + 1;
+  // records per matrix and level: whole chunks covering position nmax (a
+  // lookup may read word nmax / 32); superblock bases per matrix and level
+  const uint32_t nchunks = nmax / (32 * kChunkWords) + 1;
+  const uint32_t recw = nchunks * kChunkWords;
+  const uint32_t nsb = (nchunks + kSBChunks - 1) / kSBChunks;
+  const size_t cpre_mstride = (size_t)(nchunks + 1) * 4;  // words per matrix and level
   // scratch (u32 words): values [2 bufs][2 matrices][nmax]; records
-  // [L][2][recw] (2 words each); superblock prefixes [L][2][sbw]; superblock
-  // totals [2][nsb]; Z [2][kMaxLevels]; P counts per y rank [N + 1] and their
-  // prefix [N + 1]
-  const size_t recwords = (size_t)L * 2 * recw * 2;
+  // [LL][2][recw] uint4; chunk prefixes [LL][2][nchunks + 1][4]; superblock
+  // bases [LL][2][nsb] uint4; chunk totals [2][nchunks][4]; bucket starts
+  // [2][kMaxLevels][4]; P counts per y rank [N + 1] and their prefix [N + 1]
+  const size_t recwords = (size_t)LL * 2 * recw * 4;
+  const size_t prewords = (size_t)LL * 2 * cpre_mstride;
+  const size_t sbwords = (size_t)LL * 2 * nsb * 4;
   const size_t scan_tmp = ddks_scan_tmp_elems(1, N + 1);
-  const size_t words = (size_t)4 * nmax + recwords + (size_t)L * 2 * sbw + 2 * (size_t)nsb + 2 * kMaxLevels +
-                       2 * (size_t)(N + 1) + scan_tmp + 4;
+  const size_t words = (size_t)4 * nmax + recwords + prewords + sbwords + (size_t)2 * nchunks * 4 +
+                       2 * kMaxLevels * 4 + 2 * (size_t)(N + 1) + scan_tmp + 8;
   int rc = ctx->dom_work.reserve(ctx, 4 * words);
   if (rc) return cudaErrorMemoryAllocation;
   uint32_t* base = (uint32_t*)ctx->dom_work.ptr;
   uint32_t* vbuf[2] = {base, base + 2 * (size_t)nmax};
-  uint2* rec = reinterpret_cast<uint2*>(base + 4 * (size_t)nmax);  // 8-byte aligned: 4 nmax words
-  uint32_t* sbp = base + 4 * (size_t)nmax + recwords;
-  uint32_t* sbcnt = sbp + (size_t)L * 2 * sbw;
-  uint32_t* Zg = sbcnt + 2 * (size_t)nsb;
-  uint32_t* hy = Zg + 2 * kMaxLevels;
+  uint4* rec = reinterpret_cast<uint4*>(base + 4 * (size_t)nmax);  // 16-byte aligned: 4 nmax words
+  uint32_t* cpre = base + 4 * (size_t)nmax + recwords;
+  uint4* sbb = reinterpret_cast<uint4*>(cpre + prewords);  // prewords is a multiple of 4
+  uint32_t* ctot = reinterpret_cast<uint32_t*>(sbb) + sbwords;
+  uint32_t* stg = ctot + (size_t)2 * nchunks * 4;
+  uint32_t* hy = stg + 2 * kMaxLevels * 4;
   uint32_t* hyx = hy + (N + 1);
   uint32_t* tmp = hyx + (N + 1);
   const uint32_t* sorted_idx0 = (const uint32_t*)ctx->sidx0.ptr;
@@ -377,37 +383,32 @@ cudaError_t ddks_launch_dominance(ddks_ctx* ctx, const uint32_t* rank, int64_t N
   if (e != cudaSuccess) return e;
   n += sl;
   const dim3 gs((unsigned)grid_for(nmax, kThreads, ctx->num_sms * 8), 2);
-  for (int lv = 0; lv < L; ++lv) {
-    const int bit = L - 1 - lv;
-    uint2* rl = rec + (size_t)lv * 2 * recw;
-    uint32_t* sl_ = sbp + (size_t)lv * 2 * sbw;
-    k_dom_bits<<<dim3(nsb, 2), kSBWords, 0, st>>>(vbuf[lv & 1], n0, n1, nmax, recw, nsb, bit, rl, sbcnt);
-    ++n;
-    if (lv + 1 < L && nsb + 1 <= kFusedSB) {
-      k_dom_scatter_fused<<<gs, kThreads, 4 * (nsb + 1), st>>>(vbuf[lv & 1], vbuf[(lv + 1) & 1], n0, n1, nmax, recw, nsb, sbw,
-                                                   bit, lv, rl, sbcnt, sl_, Zg);
-      ++n;
-      continue;
-    }
-    k_dom_sbscan<<<2, kScanThreads, 0, st>>>(sbcnt, sl_, n0, n1, nsb, sbw, lv, Zg);
-    ++n;
-    if (lv + 1 < L) {
-      k_dom_scatter<<<gs, kThreads, 0, st>>>(vbuf[lv & 1], vbuf[(lv + 1) & 1], n0, n1, nmax, recw, sbw, bit, lv, rl,
-                                             sl_, Zg);
+  for (int lv = 0; lv < LL; ++lv) {
+    const int shift = 2 * (LL - 1 - lv);
+    uint4* rl = rec + (size_t)lv * 2 * recw;
+    uint32_t* pl = cpre + (size_t)lv * 2 * cpre_mstride;
+    k_quad_bits<<<dim3(nchunks, 2), kChunkWords, 0, st>>>(vbuf[lv & 1], n0, n1, nmax, recw, nchunks, shift, rl, ctot);
+    k_quad_cscan<<<2, kScanThreads, 0, st>>>(ctot, pl, n0, n1, nchunks, cpre_mstride, lv, stg);
+    n += 2;
+    if (lv + 1 < LL) {
+      k_quad_scatter<<<gs, kThreads, 0, st>>>(vbuf[lv & 1], vbuf[(lv + 1) & 1], n0, n1, nmax, recw, cpre_mstride,
+                                              shift, lv, rl, pl, stg);
       ++n;
     }
   }
-  k_dom_finalize<<<grid_for((int64_t)L * 2 * recw, kThreads, ctx->num_sms * 8), kThreads, 0, st>>>(
-      rec, sbp, (uint64_t)L * 2 * recw, recw, sbw);
+  k_quad_finalize<<<grid_for((int64_t)LL * 2 * recw, kThreads, ctx->num_sms * 8), kThreads, 0, st>>>(
+      rec, cpre, sbb, (uint64_t)LL * 2 * recw, recw, cpre_mstride, nsb);
   ++n;
-  // query views: levels are [lv][matrix][recw records], [lv][matrix][sbw prefixes]
-  const WMView wa{rec, 2 * recw, L};
-  const WMView wp{rec + recw, 2 * recw, L};
+  // query views: levels are [lv][matrix][recw records], [lv][matrix][nsb bases]
+  const QView wa{rec, sbb, stg, 2 * recw, 2 * nsb, LL};
+  const QView wp{rec + recw, sbb + nsb, stg + kMaxLevels * 4, 2 * recw, 2 * nsb, LL};
   const int64_t no = oe - ob;
   if (no > 0) {
     const uint32_t* order = (ob == 0 && oe == N && ctx->sorted_rows) ? ctx->sorted_rows + N : nullptr;
-    k_dom_query<<<grid_for(no, kThreads, ctx->num_sms * 16), kThreads, 0, st>>>(rank, pprefix0, hyx, N, NP, NT, ob,
-                                                                              oe, wa, wp, Zg, order, best, bestj);
+    const uint32_t nbases = (uint32_t)(LL * 2 * nsb);
+    const size_t qsmem = nbases <= (uint32_t)kSmemBases ? 16 * (size_t)nbases : 0;
+    k_dom_query<<<grid_for(no, kThreads, ctx->num_sms * 16), kThreads, qsmem, st>>>(
+        rank, pprefix0, hyx, N, NP, NT, ob, oe, wa, wp, nbases, order, best, bestj);
     ++n;
   }
   if (launches) *launches += n;
