@@ -71,6 +71,21 @@ struct QView {
   int LL;
 };
 
+// The two counts one query step needs at position k: x = #{< k with symbol
+// >= c}, y = #{< k with symbol >= c + 1} (two popcounts: the masks, counts
+// and bases of classes c and c + 1 are selected first).
+DDKS_DEV void ranks_c(uint4 r, uint4 s, uint32_t k, uint32_t c, uint32_t& x, uint32_t& y) {
+  const uint32_t b = k & 31;
+  const uint32_t below = b ? ((1u << b) - 1u) : 0u;
+  const uint32_t m1 = r.x | r.y, m2 = r.y, m3 = r.x & r.y;
+  const uint32_t q1 = s.x + (r.z & 0xFFFFu), q2 = s.y + (r.z >> 16), q3 = s.z + r.w;
+  // class c (c >= 1) and class c + 1 (c + 1 <= 3)
+  const uint32_t mc = c == 1 ? m1 : c == 2 ? m2 : m3, qc = c == 1 ? q1 : c == 2 ? q2 : q3;
+  const uint32_t mu = c == 0 ? m1 : c == 1 ? m2 : m3, qu = c == 0 ? q1 : c == 1 ? q2 : q3;
+  x = c == 0 ? k : qc + (uint32_t)__popc(mc & below);
+  y = c == 3 ? 0u : qu + (uint32_t)__popc(mu & below);
+}
+
 // #{k in [lo, hi) : value(k) >= v}
 DDKS_DEV uint32_t count_ge4(const QView& q, uint32_t lo, uint32_t hi, uint32_t v) {
   uint32_t greater = 0;
@@ -78,13 +93,13 @@ DDKS_DEV uint32_t count_ge4(const QView& q, uint32_t lo, uint32_t hi, uint32_t v
     const uint32_t c = (v >> (2 * (q.LL - 1 - lv))) & 3u;
     const uint4* R = q.rec + (size_t)lv * q.stride;
     const uint4* S = q.sb + (size_t)lv * q.sbstride;
-    const Ge a = ranks_at(R[lo >> 5], S[lo >> kSBShift], lo);
-    const Ge b = ranks_at(R[hi >> 5], S[hi >> kSBShift], hi);
-    const uint32_t a1 = ge_pick(a, lo, c + 1), b1 = ge_pick(b, hi, c + 1);
-    greater += b1 - a1;  // symbols above v's at this level
+    uint32_t ax, ay, bx, by;
+    ranks_c(R[lo >> 5], S[lo >> kSBShift], lo, c, ax, ay);
+    ranks_c(R[hi >> 5], S[hi >> kSBShift], hi, c, bx, by);
+    greater += by - ay;  // symbols above v's at this level
     const uint32_t s0 = q.st[lv * 4 + c];
-    lo = s0 + ge_pick(a, lo, c) - a1;
-    hi = s0 + ge_pick(b, hi, c) - b1;
+    lo = s0 + ax - ay;
+    hi = s0 + bx - by;
   }
   return greater + (hi > lo ? hi - lo : 0u);
 }

@@ -27,19 +27,22 @@ constexpr int kSortEach = 4;       // sorted positions per thread of k_chunk_sor
 constexpr int kChunkThreads = kChunk / kSortEach;
 constexpr int64_t kMaxMultiChunks = 4;  // above this (N > 8192), merge passes
 
+// One thread per point: its d coordinates (row-major input) to the key rows
+// [d][N] (consecutive points of a warp write consecutive keys of each row).
 template <typename V>
 __global__ void k_encode(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64_t NT,
                          int d, uint64_t* __restrict__ keys, unsigned* __restrict__ flags) {
   const int64_t N = NP + NT;
-  const int64_t total = N * d;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / d;
-    const int m = (int)(e - i * d);
-    const V v = i < NP ? P[e] : T[e - NP * d];
-    if (v != v) atomicOr(flags, ddks::kFlagNaN);
-    keys[(int64_t)m * N + i] = ddks::order_key(v);
+  bool nan = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const V* row = i < NP ? P + i * d : T + (i - NP) * d;
+    for (int m = 0; m < d; ++m) {
+      const V v = row[m];
+      nan |= v != v;
+      keys[(int64_t)m * N + i] = ddks::order_key(v);
+    }
   }
+  if (nan) atomicOr(flags, ddks::kFlagNaN);
 }
 
 DDKS_DEV bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
@@ -468,7 +471,7 @@ int grid_for(int64_t work, int threads) {
 
 cudaError_t ddks_launch_encode(const void* P, const void* T, int64_t NP, int64_t NT, int d,
                                int is_f64, uint64_t* keys, unsigned* flags, cudaStream_t st) {
-  const int64_t total = (NP + NT) * d;
+  const int64_t total = NP + NT;  // one thread per point
   const int threads = 256;
   if (is_f64)
     k_encode<double><<<grid_for(total, threads), threads, 0, st>>>(
