@@ -111,3 +111,24 @@ def test_dominance_partial_ranges_with_radix(torch):
             assert np.array_equal(got["per_origin"][: b - a], ref["per_origin"][: b - a])
             assert (got["num_max"], got["argmax_origin"], got["argmax_orthant"]) == (
                 ref["num_max"], ref["argmax_origin"], ref["argmax_orthant"])
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_radix_special_values(torch, dtype):
+    # -0.0 ties with +0.0, infinities sort to the ends, NaN reports ENAN
+    rng = np.random.default_rng(21)
+    P = rng.choice([0.0, -0.0, 1.5, -np.inf, np.inf, 2.0], size=(3000, 2)).astype(dtype)
+    T = rng.choice([0.0, -0.0, -1.5, np.inf, 2.0], size=(2500, 2)).astype(dtype)
+    N = 5500
+    ref = orc.ddks(P, T, origins=(0, N), per_origin=True)
+    for path in (pkg.PATH_DOMINANCE, pkg.PATH_AUTO):
+        with pkg.Context(device=0, path=path, radix_min_n=1) as c:
+            got = c.distance_range(_dev(torch, P), _dev(torch, T), 0, N, per_origin=True)
+            assert (got["num_max"], got["argmax_origin"], got["argmax_orthant"]) == (
+                ref["num_max"], ref["argmax_origin"], ref["argmax_orthant"])
+            assert np.array_equal(got["per_origin"][:N], ref["per_origin"][:N])
+            bad = P.copy()
+            bad[7, 1] = np.nan
+            with pytest.raises(pkg.DdksError) as e:
+                c.distance(_dev(torch, bad), _dev(torch, T))
+            assert e.value.code == -2
