@@ -32,8 +32,11 @@
 //                    (the origin) is the squared norm s (squares added in
 //                    dimension order), corner m + 1 (the unit vector of
 //                    dimension m) is (s - 2 x'_m) + 1, so a point costs O(d)
-//   sort             the K0 chunk sort and merge passes over the d + 1 corner
-//                    segments, carrying the P count before each position
+//   sort             the d + 1 corner lists: from 131,072 points the LSD
+//                    radix sort of radix.cu (then k_rdks_ptile counts each
+//                    tile's P points and k_rdks_walk_tiles walks with in-tile
+//                    prefixes), else the K0 chunk sort and merge passes,
+//                    carrying the P count before each position
 //   k_rdks_walk      at the last position of every run of equal distances:
 //                    |cP*NT - cT*NP| of the counts up to and including it
 //                    (both empirical CDFs evaluated after the tied values);
@@ -857,6 +860,110 @@ k_rdks_walk(const ull* __restrict__ K, const uint32_t* __restrict__ I, const uin
   if ((threadIdx.x & 31) == 0 && best) atomicMax(per_corner + s, best);
 }
 
+// The walk over radix-sorted lists (rows N apart) without a stored P prefix.
+// Tiles of kWalkTile positions, grid (tiles, S).  k_rdks_ptile counts each
+// tile's P points; k_rdks_walk_tiles adds the earlier tiles' counts (a CTA
+// sum) to in-tile prefixes of ballot counts over warp segments of 32
+// positions, then evaluates the run ends as k_rdks_walk does.
+constexpr int kWalkEach = 8;
+constexpr int kWalkTile = kThreads * kWalkEach;  // 2048 positions
+constexpr int kWalkSeg = kWalkTile / 32;          // 64 segments
+
+__global__ void __launch_bounds__(kThreads)
+k_rdks_ptile(const uint32_t* __restrict__ I, int64_t N, int64_t NP, uint32_t* __restrict__ tp) {
+  __shared__ uint32_t ws[kThreads / 32];
+  const int64_t s = blockIdx.y, base = (int64_t)blockIdx.x * kWalkTile;
+  const uint32_t* Is = I + s * N + base;
+  const int nvalid = (int)(N - base < kWalkTile ? N - base : kWalkTile);
+  uint32_t c = 0;
+#pragma unroll
+  for (int j = 0; j < kWalkEach; ++j) {
+    const int q = j * kThreads + threadIdx.x;
+    c += (q < nvalid && (uint64_t)Is[q] < (uint64_t)NP) ? 1u : 0u;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kThreads / 32; ++w) t += ws[w];
+    tp[s * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_rdks_walk_tiles(const ull* __restrict__ K, const uint32_t* __restrict__ I, const uint32_t* __restrict__ tp,
+                  int64_t N, int64_t NP, int64_t NT, ull* __restrict__ per_corner) {
+  __shared__ uint32_t seg[kWalkSeg];
+  __shared__ uint32_t ws[kThreads / 32];
+  __shared__ ull wbest[kThreads / 32];
+  const int64_t s = blockIdx.y, tile = blockIdx.x, base = tile * kWalkTile;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const ull* Ks = K + s * N;
+  const uint32_t* Is = I + s * N;
+  const int nvalid = (int)(N - base < kWalkTile ? N - base : kWalkTile);
+  // P points in the earlier tiles of this list
+  uint32_t c = 0;
+  for (int64_t q = t; q < tile; q += kThreads) c += tp[s * gridDim.x + q];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+  if (lane == 0) ws[w] = c;
+  uint32_t ix[kWalkEach], pm[kWalkEach];
+#pragma unroll
+  for (int j = 0; j < kWalkEach; ++j) {
+    const int q = j * kThreads + t;
+    ix[j] = q < nvalid ? Is[base + q] : 0u;
+    pm[j] = __ballot_sync(0xffffffffu, q < nvalid && (uint64_t)ix[j] < (uint64_t)NP);
+    if (lane == 0) seg[j * (kThreads / 32) + w] = (uint32_t)__popc(pm[j]);
+  }
+  __syncthreads();
+  if (w == 0) {  // exclusive sums over the 64 segments (positions s * 32 + lane)
+    const uint32_t a = seg[2 * lane], b = seg[2 * lane + 1];
+    uint32_t incl = a + b;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += x;
+    }
+    const uint32_t ex = incl - a - b;
+    seg[2 * lane] = ex;
+    seg[2 * lane + 1] = ex + a;
+  }
+  __syncthreads();
+  uint32_t carry = 0;
+#pragma unroll
+  for (int q = 0; q < kThreads / 32; ++q) carry += ws[q];
+  const uint32_t below = (1u << lane) - 1u;  // lane 0: none
+  ull best = 0;
+#pragma unroll
+  for (int j = 0; j < kWalkEach; ++j) {
+    const int q = j * kThreads + t;
+    if (q < nvalid) {
+      const int64_t p = base + q;
+      if (p == N - 1 || Ks[p + 1] != Ks[p]) {
+        const uint64_t cp = (uint64_t)carry + seg[j * (kThreads / 32) + w] + (uint32_t)__popc(pm[j] & below) +
+                            ((uint64_t)ix[j] < (uint64_t)NP ? 1u : 0u);
+        const uint64_t ct = (uint64_t)p + 1 - cp;
+        const ull v = ddks::numer(cp, ct, (uint64_t)NP, (uint64_t)NT);
+        best = v > best ? v : best;
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const ull o = __shfl_down_sync(0xffffffffu, best, off);
+    best = o > best ? o : best;
+  }
+  if (lane == 0) wbest[w] = best;
+  __syncthreads();
+  if (t == 0) {
+    ull b = 0;
+    for (int q = 0; q < kThreads / 32; ++q) b = wbest[q] > b ? wbest[q] : b;
+    if (b) atomicMax(per_corner + s, b);
+  }
+}
+
 // Small samples (N <= 1024): one warp per corner sorts the corner's (key,
 // index) pairs in registers -- lane l holds positions l*E .. l*E+E-1 of the
 // 32*E >= N padded list; bitonic stages of stride < E stay in the lane,
@@ -1285,7 +1392,7 @@ int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
   if ((rc = ctx->apx_cnt.reserve(ctx, 4 * segs))) return out->status = rc;  // P prefixes
   if ((rc = ctx->apx_U.reserve(ctx, 4 * segs))) return out->status = rc;
   const bool radix = N > 1024 && ddks_use_radix(ctx, N, 64);
-  if (radix && (rc = ctx->radix.reserve(ctx, 4 * ddks_radix_scratch_words(N, S, S)))) return out->status = rc;
+  if (radix && (rc = ctx->radix.reserve(ctx, 4 * ddks_radix_scratch_words(N, S, 0)))) return out->status = rc;
   // warp kernel: shared memory of 2 * d doubles per warp
   int nwb = (int)((96 * 1024) / (16 * (size_t)d));
   nwb = nwb < 1 ? 1 : (nwb > 2 ? 2 : nwb);
@@ -1358,15 +1465,24 @@ int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
     const uint64_t* sk;
     const uint32_t *si, *sp;
     int n = 0;
-    int64_t rstride = Npad;  // row stride of the sorted keys, indices and P prefixes
     if (radix) {
       uint32_t* rsx = (uint32_t*)ctx->radix.ptr;
       ee = ddks_radix_sort((const uint64_t*)keys, (uint64_t*)ctx->tk1.ptr, (uint32_t*)ctx->ti1.ptr,
                            (uint64_t*)ctx->tk2.ptr, (uint32_t*)ctx->ti2.ptr, N, N, S, 64, rsx, &sk, &si, s, &n);
-      if (ee == cudaSuccess)
-        ee = ddks_radix_ranks(sk, si, N, N, S, NP, nullptr, (uint32_t*)ctx->apx_cnt.ptr, S, nullptr, rsx, s, &n);
-      sp = (const uint32_t*)ctx->apx_cnt.ptr;
-      rstride = N;
+      ctx->launches += n;
+      if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "rdks sort");
+      ddks_stage_mark(ctx, 2, s);
+      // per-tile P counts, then the walk with in-tile prefixes
+      const unsigned wt = (unsigned)((N + kWalkTile - 1) / kWalkTile);
+      uint32_t* tp = (uint32_t*)ctx->apx_cnt.ptr;  // [S][wt]
+      k_rdks_ptile<<<dim3(wt, (unsigned)S), kThreads, 0, s>>>(si, N, NP, tp);
+      k_rdks_walk_tiles<<<dim3(wt, (unsigned)S), kThreads, 0, s>>>((const ull*)sk, si, tp, N, NP, NT, pc);
+      k_rdks_final<<<1, kThreads, 0, s>>>(pc, S, (ull*)sm);
+      ctx->launches += 3;
+      ee = cudaGetLastError();
+      if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "rdks kernels");
+      ddks_stage_mark(ctx, 3, s);
+      return DDKS_OK;
     } else {
       ee = ddks_launch_sort_segments((const uint64_t*)keys, N, NP, S, (uint64_t*)ctx->tk1.ptr, (uint32_t*)ctx->ti1.ptr,
                                      (uint32_t*)ctx->apx_cnt.ptr, (uint64_t*)ctx->tk2.ptr, (uint32_t*)ctx->ti2.ptr,
@@ -1378,8 +1494,7 @@ int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
     int gx = grid_cap(N, kThreads, ctx->num_sms * 8);
     const int per = (ctx->num_sms * 8 + S - 1) / S;
     if (gx > per) gx = per < 1 ? 1 : per;
-    k_rdks_walk<<<dim3((unsigned)gx, (unsigned)S), kThreads, 0, s>>>((const ull*)sk, si, sp, N, rstride, NP, NT,
-                                                                      pc);
+    k_rdks_walk<<<dim3((unsigned)gx, (unsigned)S), kThreads, 0, s>>>((const ull*)sk, si, sp, N, Npad, NP, NT, pc);
     k_rdks_final<<<1, kThreads, 0, s>>>(pc, S, (ull*)sm);
     ctx->launches += 2;
     ee = cudaGetLastError();
