@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--workload", choices=["cfg2", "cfg1", "cfg3", "perm", "batch", "serve", "vdks", "rdks",
                                            "rdks_large", "dom2d"], default="cfg2")
     ap.add_argument("--perms", type=int, default=1000)
-    ap.add_argument("--requests", type=int, default=600)
+    ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--path", type=int, default=0, help="force a kernel path (0 = auto)")
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -753,6 +753,25 @@ def run_perm(args):
         "cpu_baseline": cpu, "gpu_launches": launches, "p_value": ref["p_value"]}))
 
 
+def oracle_problems(problems, results, picks, budget_s=20.0):
+    """The CPU oracle (all host cores) on chosen problems of a batch or a
+    request stream, within a time budget: whole problems per second and a
+    parity check of each checked problem's num_max against the GPU result."""
+    from oracle import oracle as orc
+    nthr = orc.num_threads()
+    done, mism, t_used = 0, 0, 0.0
+    for i in picks:
+        P, T = problems[i]
+        t0 = time.perf_counter()
+        ref = orc.ddks(P, T, nthreads=nthr)
+        t_used += time.perf_counter() - t0
+        done += 1
+        mism += int(ref["num_max"] != results[i])
+        if t_used > budget_s:
+            break
+    return done, mism, t_used, nthr
+
+
 def run_batch(args):
     """256 uneven problems (NP, NT log-uniform in [64, 8192], d in 2..8): one
     batched persistent launch per step vs one ddks_distance call per problem."""
@@ -779,13 +798,24 @@ def run_batch(args):
     t1 = (time.perf_counter() - t0) / max(1, args.steps // 4)
     assert [g["num_max"] for g in got] == [o["num_max"] for o in one] == [r["num_max"] for r in ref]
     ctx.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle on a seeded sample of the batch's problems, with parity
+        order = list(np.random.default_rng(1).permutation(len(probs)))
+        done, mism, t_used, nthr = oracle_problems(probs, [g["num_max"] for g in got], order, budget_s=15.0)
+        if mism:
+            raise SystemExit(f"batch parity: {mism} of {done} sampled problems differ from the oracle")
+        cpu = {"value": done / t_used, "unit": "tests/s", "cores": nthr, "kind": "oracle",
+               "sample": f"{done} of the 256 problems in seeded random order (15 s budget), "
+                         f"num_max equal to the GPU batch for all {done}"}
     print(json.dumps({
         "metric": "ddks_batch_tests_per_s", "value": 256 / tb, "unit": "tests/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tb * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32 ranks (f32 input)",
         "data": "synthetic (seeded numpy PCG64)",
         "config": {"workload": "256 problems, NP,NT log-uniform [64,8192], d uniform 2..8, mixtures",
-                   "one_call_per_problem_tests_per_s": 256 / t1, "compares_per_s": units / tb}}))
+                   "one_call_per_problem_tests_per_s": 256 / t1, "compares_per_s": units / tb},
+        "cpu_baseline": cpu}))
 
 
 def run_serve(args):
@@ -817,6 +847,7 @@ def run_serve(args):
         return lat, time.perf_counter() - t_start
 
     ctx = pkg.Context(device=0, max_batch=64)
+    nums = [None] * len(reqs)  # num_max of each request as served
 
     def submit_fn(i, P, T, lat):
         t0 = time.perf_counter()
@@ -828,6 +859,7 @@ def run_serve(args):
                 if rc != pkg.DDKS_PENDING:
                     if rc == pkg.DDKS_OK:
                         lat[i] = time.perf_counter() - t0
+                        nums[i] = r["num_max"]
                     return
         th = threading.Thread(target=waiter, daemon=True)
         th.start()
@@ -878,6 +910,24 @@ def run_serve(args):
         qq.put(None)
         wth.join()
     ctx1.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        # parity with the oracle: every request with N <= 5,000, then a seeded
+        # 5% sample of the larger ones, within a 30 s budget
+        sizes = [len(P) + len(T) for _, P, T in reqs]
+        small = [i for i, n in enumerate(sizes) if n <= 5000]
+        large = [i for i, n in enumerate(sizes) if n > 5000]
+        rng = np.random.default_rng(5)
+        pick_large = list(rng.choice(large, size=max(1, len(large) // 20), replace=False)) if large else []
+        done, mism, t_used, nthr = oracle_problems([(P, T) for _, P, T in reqs], nums, small + pick_large,
+                                                   budget_s=30.0)
+        if mism:
+            raise SystemExit(f"serving parity: {mism} of {done} checked requests differ from the oracle")
+        n_small = min(done, len(small))
+        cpu = {"value": done / t_used, "unit": "tests/s", "cores": nthr, "kind": "oracle",
+               "sample": f"{n_small} of {len(small)} requests with N <= 5,000 and {done - n_small} of a seeded "
+                         f"5% sample of the {len(large)} larger ones (30 s budget); num_max equal to the "
+                         f"served result for all {done}"}
     pct = lambda xs, q: float(np.percentile(np.array(xs) * 1e3, q))
     print(json.dumps({
         "metric": "ddks_serve_tests_per_s", "value": len(reqs) / wall_b, "unit": "tests/s", "n_gpus": 1,
@@ -891,7 +941,8 @@ def run_serve(args):
                    "saturated": {"tests_per_s": len(reqs) / wall_bs,
                                  "one_per_call_tests_per_s": len(reqs) / wall_ss,
                                  "note": "all requests submitted at once"},
-                   "bytes_resident_peak": st["bytes_resident_peak"]}}))
+                   "bytes_resident_peak": st["bytes_resident_peak"]},
+        "cpu_baseline": cpu}))
 
 
 def main():
