@@ -50,3 +50,13 @@ def test_argument_errors_need_no_gpu(lib):
 
 def test_library_is_in_tree():
     assert os.path.dirname(pkg.binding.LIB_PATH) == os.path.dirname(bld.__file__)
+
+
+def test_config_defaults(lib):
+    cfg = pkg.binding.ddks_config()
+    cfg.radix_min_n = 123
+    lib.ddks_config_default(ctypes.byref(cfg))
+    assert cfg.radix_min_n == 0 and cfg.graphs == 1 and cfg.device == -1
+    # the binding's struct matches the header's field order up to the last field
+    names = [n for n, _ in pkg.binding.ddks_config._fields_]
+    assert names[-1] == "radix_min_n" and names.index("graphs") == len(names) - 2
