@@ -86,23 +86,40 @@ DDKS_DEV void ranks_c(uint4 r, uint4 s, uint32_t k, uint32_t c, uint32_t& x, uin
   y = c == 3 ? 0u : qu + (uint32_t)__popc(mu & below);
 }
 
-// #{k in [lo, hi) : value(k) >= v}
-DDKS_DEV uint32_t count_ge4(const QView& q, uint32_t lo, uint32_t hi, uint32_t v) {
-  uint32_t greater = 0;
-  for (int lv = 0; lv < q.LL && lo < hi; ++lv) {
-    const uint32_t c = (v >> (2 * (q.LL - 1 - lv))) & 3u;
-    const uint4* R = q.rec + (size_t)lv * q.stride;
-    const uint4* S = q.sb + (size_t)lv * q.sbstride;
-    uint32_t ax, ay, bx, by;
-    ranks_c(R[lo >> 5], S[lo >> kSBShift], lo, c, ax, ay);
-    ranks_c(R[hi >> 5], S[hi >> kSBShift], hi, c, bx, by);
-    greater += by - ay;  // symbols above v's at this level
-    const uint32_t s0 = q.st[lv * 4 + c];
-    lo = s0 + ax - ay;
-    hi = s0 + bx - by;
+// #{k in [la, ha) : value(k) >= v} in the all-points matrix and
+// #{k in [lp, hp) : value(k) >= v} in the P matrix, both walks at once (v's
+// symbol at each level picks the bucket; the symbols above it count as
+// greater): the two dependent chains of record loads
+// advance together, so their latencies overlap.  A walk whose range is empty
+// keeps looking up its (equal) ends and adds nothing.
+DDKS_DEV void count_ge4_pair(const QView& qa, const QView& qp, uint32_t la, uint32_t ha, uint32_t lp, uint32_t hp,
+                             uint32_t v, uint32_t& ga, uint32_t& gp) {
+  ga = 0;
+  gp = 0;
+  for (int lv = 0; lv < qa.LL && (la < ha || lp < hp); ++lv) {
+    const uint32_t c = (v >> (2 * (qa.LL - 1 - lv))) & 3u;
+    const uint4* Ra = qa.rec + (size_t)lv * qa.stride;
+    const uint4* Sa = qa.sb + (size_t)lv * qa.sbstride;
+    const uint4* Rp = qp.rec + (size_t)lv * qp.stride;
+    const uint4* Sp = qp.sb + (size_t)lv * qp.sbstride;
+    const uint4 ra0 = Ra[la >> 5], ra1 = Ra[ha >> 5], rp0 = Rp[lp >> 5], rp1 = Rp[hp >> 5];
+    uint32_t ax, ay, bx, by, cx, cy, dx, dy;
+    ranks_c(ra0, Sa[la >> kSBShift], la, c, ax, ay);
+    ranks_c(ra1, Sa[ha >> kSBShift], ha, c, bx, by);
+    ranks_c(rp0, Sp[lp >> kSBShift], lp, c, cx, cy);
+    ranks_c(rp1, Sp[hp >> kSBShift], hp, c, dx, dy);
+    ga += by - ay;
+    gp += dy - cy;
+    const uint32_t sa = qa.st[lv * 4 + c], sp = qp.st[lv * 4 + c];
+    la = sa + ax - ay;
+    ha = sa + bx - by;
+    lp = sp + cx - cy;
+    hp = sp + dx - dy;
   }
-  return greater + (hi > lo ? hi - lo : 0u);
+  ga += ha > la ? ha - la : 0u;
+  gp += hp > lp ? hp - lp : 0u;
 }
+
 
 // Level-0 values: y ranks in dimension-0 order, for all points (matrix 0) and
 // for the P points (matrix 1, positions = P points before the position);
@@ -310,8 +327,10 @@ k_dom_query(const uint32_t* __restrict__ rank, const uint32_t* __restrict__ ppre
     const int64_t o = order ? (int64_t)order[k] : k;
     const uint32_t rx = rank[o], ry = rank[N + o];
     const uint32_t lxp = rx < (uint64_t)N ? pprefix0[rx] : (uint32_t)NP;  // P points with x_0 < o_0
-    const uint64_t a3 = count_ge4(wa, rx, (uint32_t)N, ry);                // both >=, all points
-    const uint64_t p3 = count_ge4(wp, lxp, (uint32_t)NP, ry);              // both >=, P
+    uint32_t ga, gp;
+    count_ge4_pair(wa, wp, rx, (uint32_t)N, lxp, (uint32_t)NP, ry, ga, gp);
+    const uint64_t a3 = ga;  // both >=, all points
+    const uint64_t p3 = gp;  // both >=, P
     const uint64_t pyu = (uint64_t)NP - hyx[ry];                          // P with x_1 >= o_1
     const uint64_t axu = (uint64_t)N - rx, pxu = (uint64_t)NP - lxp;      // x_0 >= o_0
     const uint64_t ayu = (uint64_t)N - ry;                                // x_1 >= o_1
