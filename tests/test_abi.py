@@ -60,3 +60,14 @@ def test_config_defaults(lib):
     # the binding's struct matches the header's field order up to the last field
     names = [n for n, _ in pkg.binding.ddks_config._fields_]
     assert names[-1] == "radix_min_n" and names.index("graphs") == len(names) - 2
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without the built library every entry point raises
+    b = pkg.binding
+    monkeypatch.setattr(b, "_lib", None)
+    monkeypatch.setattr(b, "LIB_PATH", str(tmp_path / "libddks.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        b.load()
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        b.ddks_ctx_create(device=0)
