@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-study", action="store_true", help="perm workload: skip the significance study")
     return ap.parse_args()
 
 
@@ -303,8 +304,16 @@ def run_ours(args):
                 "stage_ms": {"encode": statistics.mean(enc_ms), "count": cnt, "reduce": statistics.mean(red_ms)}}
 
     cpu = None
+    parity = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(P, T, d)
+        cpu, oref = cpu_baseline(P, T, d)
+        # the oracle ran over every origin: the timed result must equal it
+        got = (ref["num_max"], ref["denom"], ref["argmax_origin"], ref["argmax_orthant"])
+        want = (oref["num_max"], oref["denom"], oref["argmax_origin"], oref["argmax_orthant"])
+        if got != want:
+            raise RuntimeError(f"parity failure: GPU {got} != oracle {want}")
+        parity = {"equal": True, "num_max_oracle": oref["num_max"],
+                  "checked": "num_max, denom, arg-max origin and orthant against the oracle over all origins"}
     ctx.close()
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -316,7 +325,7 @@ def run_ours(args):
                                    ["auto", "register", "lane", "warp", "sort"][args.path]),
                    "l2": f"flushed between steps ({args.flush_mb} MB write)", "replicas": world},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks, "num_max": ref["num_max"], "denom": ref["denom"],
+        "clocks": clocks, "num_max": ref["num_max"], "denom": ref["denom"], "parity": parity,
         "wall_s_timed": wall,
     }
     if rank == 0:
@@ -332,10 +341,10 @@ def cpu_baseline(P, T, d, max_origins=None):
     nthr = orc.num_threads()
     o_end = N if max_origins is None else min(N, max_origins)
     t0 = time.perf_counter()
-    orc.ddks(P, T, origins=(0, o_end), nthreads=nthr)
+    res = orc.ddks(P, T, origins=(0, o_end), nthreads=nthr)
     dt = time.perf_counter() - t0
-    return {"value": float(o_end) * N * d / dt, "unit": UNIT, "cores": nthr, "kind": "oracle",
-            "sample": f"origins [0,{o_end}) of {N} (all points per origin), one pass, {dt:.2f} s"}
+    return ({"value": float(o_end) * N * d / dt, "unit": UNIT, "cores": nthr, "kind": "oracle",
+             "sample": f"origins [0,{o_end}) of {N} (all points per origin), one pass, {dt:.2f} s"}, res)
 
 
 def run_reference(args):
@@ -734,14 +743,24 @@ def run_perm(args):
     launches = ctx.stats()["kernel_launches"] - l0
     tot = sum(ms)
     cpu = None
+    parity = None
     if not args.no_cpu_baseline:
         from oracle import oracle as orc
         nb = 4
         t0 = time.perf_counter()
-        orc.permutation_test(P, T, nb, 2021, nthreads=orc.num_threads())
+        oref = orc.permutation_test(P, T, nb, 2021, nthreads=orc.num_threads())
         dt = time.perf_counter() - t0
         cpu = {"value": 1.0 / (dt * (B + 1) / (nb + 1)), "unit": "tests/s", "cores": orc.num_threads(),
                "kind": "oracle", "sample": f"{nb} relabellings + observed ({dt:.2f} s), scaled to B={B}"}
+        # relabelling b depends on (seed, b) only: the first nb of the warm-up
+        # call (seed 2021) must equal the oracle's
+        got = [int(x) for x in ref["perm_num_max"][:nb]]
+        want = [int(x) for x in oref["perm_num_max"][:nb]]
+        if got != want or ref["observed"]["num_max"] != oref["observed"]["num_max"]:
+            raise RuntimeError(f"parity failure: GPU {got} != oracle {want}")
+        parity = {"equal": True, "num_max_oracle": int(oref["observed"]["num_max"]),
+                  "checked": f"observed num_max and the first {nb} relabellings' num_max against the oracle"}
+    study = significance_study(ctx, torch, wl, quick=args.steps < 5) if not args.no_study else None
     ctx.close()
     print(json.dumps({
         "metric": "ddks_perm_tests_per_s", "value": args.steps / (tot * 1e-3), "unit": "tests/s",
@@ -750,7 +769,45 @@ def run_perm(args):
         "data": "synthetic (seeded numpy PCG64)",
         "config": {"workload": f"permutation test, 3-component Gaussian mixture d=3 NP=NT=2000, B={B}",
                    "logical_compares_per_s": (B + 1) * float(N) * N * d * args.steps / (tot * 1e-3)},
-        "cpu_baseline": cpu, "gpu_launches": launches, "p_value": ref["p_value"]}))
+        "cpu_baseline": cpu, "gpu_launches": launches, "p_value": ref["p_value"], "parity": parity,
+        "significance_vs_permutation": study}))
+
+
+def significance_study(ctx, torch, wl, quick=False, alpha=0.05, B=1000):
+    """Analytic significance S (Sec. 3, Eq. ddks_significance; binomial and
+    Poisson cells, Bayes rate) beside the permutation p-value of the same
+    samples, under the null and an alternative, over many seeds: the
+    comparison of Sec. 3 (its type I / power statement uses DVU, d = 3,
+    50 points per sample).  Everything runs on the GPU."""
+    def one(P, T, seed):
+        Pd, Td = torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()
+        pr = ctx.permutation_test(Pd, Td, B, 7000 + seed, want_perm=False)
+        num = pr["observed"]["num_max"]
+        S_bin, _ = ctx.significance(Pd, Td, num, 1, 0)
+        S_poi, _ = ctx.significance(Pd, Td, num, 1, 1)
+        return S_bin, S_poi, pr["p_value"]
+
+    cases = {
+        "dvu_d3_50x50": (lambda s: wl.dvu_null_pair(s, 50, 50, 3), lambda s: wl.dvu_pair(s, 50, 50, 3),
+                         40 if quick else 200),
+        "mixture_d3_2000x2000": (lambda s: wl.mixture_pair(seed=s, shift=0.0),
+                                 lambda s: wl.mixture_pair(seed=s, shift=0.2), 5 if quick else 20),
+    }
+    out = {"alpha": alpha, "B": B}
+    for name, (null_fn, alt_fn, seeds) in cases.items():
+        row = {"seeds": seeds}
+        for hyp, fn in (("null", null_fn), ("alt", alt_fn)):
+            r = np.array([one(*fn(s), s) for s in range(seeds)])
+            Sb, Sp, pp = r[:, 0], r[:, 1], r[:, 2]
+            row[hyp] = {
+                "reject_rate_S_binomial": float((Sb < alpha).mean()),
+                "reject_rate_S_poisson": float((Sp < alpha).mean()),
+                "reject_rate_p_perm": float((pp < alpha).mean()),
+                "median_S_binomial": float(np.median(Sb)), "median_p_perm": float(np.median(pp)),
+                "same_decision": float(((Sb < alpha) == (pp < alpha)).mean()),
+            }
+        out[name] = row
+    return out
 
 
 def oracle_problems(problems, results, picks, budget_s=20.0):

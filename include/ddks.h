@@ -78,7 +78,8 @@ typedef struct {
   int32_t path;               /* a ddks_path; DDKS_PATH_AUTO by default */
   uint64_t hbm_budget_bytes;  /* serving: device bytes the resident requests may hold (0 = 8 GiB) */
   int32_t max_batch;          /* serving: most requests per device batch (0 = 64) */
-  int32_t wait_limit_ms;      /* bound on any host or device wait (0 = 10000) */
+  int32_t wait_limit_ms;      /* bound on each host wait (0 = 10000) and, when set, on each
+                                 device-side wait for an asynchronous copy (0 = 1000 there) */
   const char* tune_cache;     /* autotuner cache file (NULL = $DDKS_TUNE_CACHE, else none) */
   int32_t graphs;             /* 1 (default): replay CUDA graphs for repeated calls, see below; 0 = off */
   int64_t radix_min_n;        /* pooled sizes N from which the key sorts (the per-dimension ranks of the
@@ -240,11 +241,14 @@ int ddks_stage_times(ddks_ctx* ctx, float* encode_ms, float* count_ms, float* re
  *
  * No context is needed and nothing is allocated: the scratch is one static
  * device array of about 0.7 MiB that every GPU loading the library holds until
- * the process exits.  P and T must already be device memory (DDKS_EINVAL
- * otherwise); out is written on the host after the call synchronises stream.
- * Limits: NP + NT <= 16384 and d <= 8, else DDKS_EUNSUPPORTED.
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  All calls
+ * the process exits.  P and T must already be device memory of the current
+ * device, or managed memory (DDKS_EINVAL otherwise, including device memory
+ * of another GPU); out is written on the host after the call synchronises
+ * stream.  Limits: NP + NT <= 16384 and d <= 8, else DDKS_EUNSUPPORTED.
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing), so a device reset between
+ * calls leaves no stale address; make the first call on a device before any
+ * stream capture, since that lookup may load the module.  All calls
  * share the one array: calls whose work overlaps on the GPU (other streams or
  * host threads on the same device) race and must be serialised by the caller.
  */
@@ -304,6 +308,41 @@ int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
  * finite, lo finite (DDKS_EINVAL otherwise); n >= 0.
  */
 int ddks_rescale(ddks_ctx* ctx, const double* v, int64_t n, double lo, double span, double* out, void* stream);
+
+/*
+ * Bound on each device-side wait of a kernel for one of its own asynchronous
+ * bulk copies (the streamed count and voxel kernels), in nanoseconds of the
+ * GPU's global timer; 0 restores the value fixed at creation (the config's
+ * wait_limit_ms, else 1 s).  A wait that runs out makes its CTA wait (at most
+ * 1 s more) for its copies still in flight and return; the call then returns
+ * DDKS_ETIMEOUT and the context stays usable.  A copy normally lands within
+ * microseconds, so only a broken device reaches the default bound.  The
+ * paper has no counterpart (failure handling of the library).
+ */
+int ddks_set_device_wait_limit(ddks_ctx* ctx, uint64_t limit_ns);
+
+/*
+ * Self-test of the bounded device wait: one kernel arms an mbarrier for a
+ * 16-byte transaction that no copy ever delivers and waits with the
+ * context's bound.  Returns DDKS_ETIMEOUT (the expected outcome) and the time
+ * the wait took in *waited_ns (may be NULL); nothing faults or hangs, and the
+ * context remains usable.  Synchronous on stream.  The paper has no
+ * counterpart.
+ */
+int ddks_wait_selftest(ddks_ctx* ctx, void* stream, uint64_t* waited_ns);
+
+/*
+ * How every entry point treats an input pointer, from the memory type that
+ * cudaPointerGetAttributes reports (cudaMemoryType: 0 unregistered, 1 host,
+ * 2 device, 3 managed) and, for device memory, the device that holds it.
+ * Returns 1 when the pointer is read in place (device memory of `device`, the
+ * device the call runs on, or managed memory), 0 when the call copies it from
+ * the host (pinned or pageable host memory), and DDKS_EINVAL for device
+ * memory of another GPU or an unknown type: such inputs are refused rather
+ * than read across devices.  Pure function; needs no GPU.  The paper has no
+ * counterpart.
+ */
+int ddks_classify_pointer(int32_t memory_type, int32_t pointer_device, int32_t device);
 
 /* Human-readable text for a return code. */
 const char* ddks_strerror(int code);

@@ -91,6 +91,9 @@ def load():
             "ddks_strerror": (ctypes.c_char_p, [i32]),
             "ddks_last_cuda_error": (ctypes.c_char_p, [vp]),
             "ddks_version": (ctypes.c_char_p, []),
+            "ddks_classify_pointer": (i32, [i32, i32, i32]),
+            "ddks_set_device_wait_limit": (i32, [vp, u64]),
+            "ddks_wait_selftest": (i32, [vp, vp, ctypes.POINTER(u64)]),
             "ddks_distance_noalloc": (i32, [vp, i64, vp, i64, i32, i32, vp, R]),
             "ddks_vdks": (i32, [vp, vp, i64, vp, i64, i32, i32, i32, vp, R]),
             "ddks_rdks": (i32, [vp, vp, i64, vp, i64, i32, i32, vp, R, vp]),
@@ -364,6 +367,20 @@ def ddks_version():
     return load().ddks_version().decode()
 
 
+def ddks_set_device_wait_limit(ctx, limit_ns):
+    """Bound (ns) on each device-side wait for an asynchronous copy; 0 = the default."""
+    _check(load().ddks_set_device_wait_limit(ctx, int(limit_ns)), ctx, "ddks_set_device_wait_limit")
+
+
+def ddks_wait_selftest(ctx, stream=None):
+    """(return code, waited ns) of one wait on a phase that never completes."""
+    w = ctypes.c_uint64()
+    rc = load().ddks_wait_selftest(ctx, _stream(stream), ctypes.byref(w))
+    if rc != -6:  # DDKS_ETIMEOUT is the expected outcome
+        _check(rc, ctx, "ddks_wait_selftest")
+    return rc, int(w.value)
+
+
 class Context:
     """Owns a ddks_ctx; `with Context() as c: c.distance(P, T)`."""
 
@@ -428,3 +445,9 @@ class Context:
 
     def stage_times(self):
         return ddks_stage_times(self.h)
+
+    def set_device_wait_limit(self, limit_ns):
+        ddks_set_device_wait_limit(self.h, limit_ns)
+
+    def wait_selftest(self, stream=None):
+        return ddks_wait_selftest(self.h, stream)

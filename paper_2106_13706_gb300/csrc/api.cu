@@ -51,14 +51,28 @@ int ctx_cuda_fail(ddks_ctx* ctx, cudaError_t e, const char* where) {
   return e == cudaErrorMemoryAllocation ? DDKS_ENOMEM : DDKS_ECUDA;
 }
 
-bool ddks_is_device_ptr(const void* p) {
+int ddks_classify_pointer(int32_t memory_type, int32_t pointer_device, int32_t device) {
+  switch (memory_type) {
+    case cudaMemoryTypeDevice:  // device memory is read in place only on its own device
+      return pointer_device == device ? 1 : DDKS_EINVAL;
+    case cudaMemoryTypeManaged:
+      return 1;
+    case cudaMemoryTypeUnregistered:
+    case cudaMemoryTypeHost:
+      return 0;
+    default:
+      return DDKS_EINVAL;
+  }
+}
+
+int ddks_pointer_kind(const void* p, int device) {
   cudaPointerAttributes a;
   cudaError_t e = cudaPointerGetAttributes(&a, p);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;  // not known to CUDA: plain host memory
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return ddks_classify_pointer((int32_t)a.type, (int32_t)a.device, (int32_t)device);
 }
 
 int DevBuf::reserve(ddks_ctx* ctx, size_t n) {
@@ -105,6 +119,8 @@ int ddks_ctx_create(const ddks_config* cfg, ddks_ctx** out) {
   if (ctx->cfg.path < DDKS_PATH_AUTO || ctx->cfg.path > DDKS_PATH_DOMINANCE) { delete ctx; return DDKS_EINVAL; }
   if (ctx->cfg.hbm_budget_bytes == 0) ctx->cfg.hbm_budget_bytes = 8ull << 30;
   if (ctx->cfg.max_batch <= 0) ctx->cfg.max_batch = 64;
+  if (ctx->cfg.wait_limit_ms > 0)
+    ctx->dev_wait_ns = ctx->dev_wait_cfg_ns = (unsigned long long)ctx->cfg.wait_limit_ms * 1000000ull;
   if (ctx->cfg.wait_limit_ms <= 0) ctx->cfg.wait_limit_ms = 10000;
   int dev = ctx->cfg.device;
   cudaError_t e;
@@ -200,7 +216,9 @@ int ddks_stage_inputs(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, i
                       int32_t d, int32_t dtype, cudaStream_t st, const void** dP,
                       const void** dT) {
   const size_t es = dtype == DDKS_F64 ? 8 : 4;
-  const bool devP = ddks_is_device_ptr(P), devT = ddks_is_device_ptr(T);
+  const int kP = ddks_pointer_kind(P, ctx->device), kT = ddks_pointer_kind(T, ctx->device);
+  if (kP < 0 || kT < 0) return DDKS_EINVAL;  // device memory of another GPU
+  const bool devP = kP == 1, devT = kT == 1;
   *dP = P;
   *dT = T;
   if (!devP) {

@@ -499,7 +499,8 @@ constexpr size_t kVoxMaxDynSmem = 227 * 1024 - 1024;  // dynamic shared memory o
 // multiples of r0 rows (r0 rows = a multiple of 16 bytes; the sample bases
 // are 16-byte aligned), so every copy starts and ends on 16 bytes; rows past
 // the last such boundary (fewer than r0, at the sample's end) are read
-// directly.  A wait that runs out (1 s) sets kFlagTimeout, waits (bounded)
+// directly.  A wait that runs out (the context's device wait bound, 1 s by
+// default) sets kFlagTimeout, waits (bounded)
 // for the CTA's copies still in flight and returns without its counts.
 // Shared memory: hist [cells] u32 at 0, thresholds at thr_off, stages at
 // stage_off (stage_bytes each).
@@ -509,7 +510,7 @@ k_vdks_voxel_bulk(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, 
                   const ull* __restrict__ gmin, const ull* __restrict__ gmax,
                   const typename NativeKey<V>::K* __restrict__ thr, int use_thr, uint32_t cells, int bP, int r0,
                   int rc, uint32_t thr_off, uint32_t stage_off, uint32_t stage_bytes,
-                  uint32_t* __restrict__ hist_all, unsigned* __restrict__ flags) {
+                  uint32_t* __restrict__ hist_all, unsigned* __restrict__ flags, unsigned long long wait_ns) {
   namespace bk = ddks::bulk;
   using K = typename NativeKey<V>::K;
   extern __shared__ __align__(16) unsigned char vb_raw[];
@@ -566,7 +567,7 @@ k_vdks_voxel_bulk(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, 
   for (int c = 0; c < nch; ++c) {
     // stage (c - 1) % kVoxStages was released by the barrier that ended chunk c - 1
     if (tid == 0 && c + kVoxStages - 1 < nch) issue(c + kVoxStages - 1);
-    const bool ok = bk::wait(bar_s + 8u * (uint32_t)(c % kVoxStages), (uint32_t)((c / kVoxStages) & 1));
+    const bool ok = bk::wait(bar_s + 8u * (uint32_t)(c % kVoxStages), (uint32_t)((c / kVoxStages) & 1), wait_ns);
     if (ok) {
       const int64_t r = chunk_row(c);
       const int cnt = (int)(end_al - r < rc ? end_al - r : rc);
@@ -580,7 +581,7 @@ k_vdks_voxel_bulk(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, 
         atomicOr(flags, ddks::kFlagTimeout);
         // copies of chunks c .. c + kVoxStages - 2 may still be in flight
         for (int k = c; k < c + kVoxStages - 1 && k < nch; ++k)
-          bk::wait(bar_s + 8u * (uint32_t)(k % kVoxStages), (uint32_t)((k / kVoxStages) & 1));
+          bk::wait(bar_s + 8u * (uint32_t)(k % kVoxStages), (uint32_t)((k / kVoxStages) & 1), bk::kDrainNs);
       }
       return;
     }
@@ -1151,14 +1152,15 @@ bool plan_voxel_bulk(uint32_t cells, int d, size_t ks, int64_t nthr, size_t es, 
 template <typename V>
 cudaError_t launch_voxel_bulk(const void* P, const void* T, int64_t NP, int64_t NT, int d, int Vd, const ull* gmin,
                               const ull* gmax, const void* thr, bool use_thr, uint32_t cells, int bP, int nb,
-                              uint32_t* hall, unsigned* flags, const BulkPlan& bp, cudaStream_t st) {
+                              uint32_t* hall, unsigned* flags, const BulkPlan& bp, cudaStream_t st,
+                              unsigned long long wait_ns) {
   using K = typename NativeKey<V>::K;
   auto go = [&](auto kern) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bp.smem);
     if (e != cudaSuccess) return e;
     kern<<<nb, kVoxBulkThreads, bp.smem, st>>>((const V*)P, (const V*)T, NP, NT, d, Vd, gmin, gmax, (const K*)thr,
                                               use_thr ? 1 : 0, cells, bP, bp.r0, bp.rc, bp.thr_off, bp.stage_off,
-                                          bp.stage_bytes, hall, flags);
+                                          bp.stage_bytes, hall, flags, wait_ns);
     return cudaGetLastError();
   };
   if (d == 1) return go(k_vdks_voxel_bulk<V, 1>);
@@ -1289,9 +1291,9 @@ int ddks_vdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
       uint32_t* hall = (uint32_t*)ctx->apx_hist.ptr;
       if (bulk)
         ee = f64 ? launch_voxel_bulk<double>(dP, dT, NP, NT, d, Vd, gmin, gmax, thr, use_thr, cells, bP, nbh, hall,
-                                             flags, bp, s)
+                                             flags, bp, s, ctx->dev_wait_ns)
                  : launch_voxel_bulk<float>(dP, dT, NP, NT, d, Vd, gmin, gmax, thr, use_thr, cells, bP, nbh, hall,
-                                            flags, bp, s);
+                                            flags, bp, s, ctx->dev_wait_ns);
       else
         ee = f64 ? launch_voxel_smem<double>(dP, dT, NP, NT, d, Vd, gmin, gmax, thr, use_thr, cells, bP, nbh, hall,
                                              flags, hsm, s)
@@ -1337,8 +1339,9 @@ int ddks_rescale(ddks_ctx* ctx, const double* v, int64_t n, double lo, double sp
   if (!ctx || n < 0 || (n > 0 && (!v || !out))) return DDKS_EINVAL;
   if (!std::isfinite(lo) || !std::isfinite(span) || span < 0.0) return DDKS_EINVAL;
   if (n == 0) return DDKS_OK;
-  const bool dv = ddks_is_device_ptr(v), dout = ddks_is_device_ptr(out);
-  if (dv != dout) return DDKS_EINVAL;
+  const int kv = ddks_pointer_kind(v, ctx->device), kout = ddks_pointer_kind(out, ctx->device);
+  if (kv < 0 || kout < 0 || kv != kout) return DDKS_EINVAL;
+  const bool dv = kv == 1;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "cudaSetDevice");

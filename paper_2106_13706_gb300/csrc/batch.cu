@@ -315,8 +315,10 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
     std::vector<char> is_dev(2 * nb);
     for (int b = 0; b < nb; ++b) {
       const int i = batched[b];
-      is_dev[2 * b] = ddks_is_device_ptr(P[i]);
-      is_dev[2 * b + 1] = ddks_is_device_ptr(T[i]);
+      const int kP = ddks_pointer_kind(P[i], ctx->device), kT = ddks_pointer_kind(T[i], ctx->device);
+      if (kP < 0 || kT < 0) { out[i].status = DDKS_EINVAL; return DDKS_EINVAL; }  // another GPU's memory
+      is_dev[2 * b] = kP == 1;
+      is_dev[2 * b + 1] = kT == 1;
       if (!is_dev[2 * b]) host_bytes += (es * NP[i] * d[i] + 15) & ~(size_t)15;
       if (!is_dev[2 * b + 1]) host_bytes += (es * NT[i] * d[i] + 15) & ~(size_t)15;
     }

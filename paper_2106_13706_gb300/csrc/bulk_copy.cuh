@@ -8,7 +8,11 @@
 namespace ddks {
 namespace bulk {
 
-constexpr unsigned long long kWaitNs = 1000000000ull;  // bound on one wait (1 s)
+constexpr unsigned long long kWaitNs = 1000000000ull;   // default bound on one wait (1 s)
+// Bound on the waits for copies still in flight after a wait gave up: these
+// copies were issued and land within microseconds, and no CTA may exit while
+// one of its copies can still write its shared memory.
+constexpr unsigned long long kDrainNs = 1000000000ull;
 
 DDKS_DEV void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -39,8 +43,9 @@ DDKS_DEV unsigned long long global_ns() {
   return t;
 }
 
-// Waits for phase `parity` of `bar` to complete; false after kWaitNs.
-DDKS_DEV bool wait(uint32_t bar, uint32_t parity) {
+// Waits for phase `parity` of `bar` to complete; false once limit_ns of
+// %globaltimer have passed since the first unsuccessful try.
+DDKS_DEV bool wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
   unsigned long long t0 = 0;
   for (int it = 0;; ++it) {
     uint32_t done;
@@ -52,7 +57,7 @@ DDKS_DEV bool wait(uint32_t bar, uint32_t parity) {
         : "memory");
     if (done) return true;
     if (it == 0) t0 = global_ns();
-    else if (global_ns() - t0 > kWaitNs) return false;
+    else if (global_ns() - t0 > limit_ns) return false;
   }
 }
 

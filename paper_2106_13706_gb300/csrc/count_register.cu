@@ -34,10 +34,13 @@
 // an mbarrier, and every lane reads the same record (broadcast loads).  The
 // last unit of a block turns the block's counters into per-origin maxima and
 // the last block writes the result.
+#include "bulk_copy.cuh"
 #include "ddks_host.h"
 #include "ddks_internal.cuh"
 
 namespace {
+
+namespace bk = ddks::bulk;
 
 constexpr int kThreads = 64;          // threads per CTA of the count kernel
 constexpr int kOPL = 2;               // origin slots per thread
@@ -49,7 +52,6 @@ constexpr int64_t kMaxRegN = 200000;
 constexpr int kPackThreads = 512;     // one origin block per CTA
 constexpr int kPack4Threads = 1024;   // four origin blocks per CTA
 constexpr int kCnt = 32;              // counters per origin: [sample][all, B][subset] (<= 2*2*7 used)
-constexpr unsigned long long kWaitNs = 1000000000ull;  // bound on one tile wait (1 s)
 
 // record of one group: per dimension 8 words (7 planes + 1 pad), 16-byte aligned
 template <int DS>
@@ -324,48 +326,6 @@ struct Final {
 constexpr int kPackShift = 26;                       // positions < 2^26; numerators < 2^38
 constexpr unsigned long long kPackMask = (1ull << kPackShift) - 1;
 
-// ---- bulk asynchronous copies with mbarrier completion
-
-DDKS_DEV void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-// expect `bytes` more transaction bytes on the current phase of `bar`
-DDKS_DEV void mbar_expect(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-// global -> shared bulk copy of `bytes` (a multiple of 16, both addresses
-// 16-byte aligned), counted on `bar`
-DDKS_DEV void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
-DDKS_DEV unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Waits for phase `parity` of `bar` to complete; false after kWaitNs.
-DDKS_DEV bool mbar_wait(uint32_t bar, uint32_t parity) {
-  unsigned long long t0 = 0;
-  for (int it = 0;; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (it == 0) t0 = global_ns();
-    else if (global_ns() - t0 > kWaitNs) return false;
-  }
-}
-
 // The orthant counts of one origin and sample from its subset counters:
 // n[0] = all points of the phase, n[S] = points in all dimensions of S.
 template <int DS>
@@ -425,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, OCC)
 k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes,
            const OriginMeta* __restrict__ meta, int64_t no, int64_t NP, int64_t NT, int64_t ngroups,
            int C, int CP, int GP, int GT, int CGP, int CGT, uint32_t* __restrict__ gcnt,
-           unsigned* __restrict__ flags, const Final fin) {
+           unsigned* __restrict__ flags, const Final fin, unsigned long long wait_ns) {
   constexpr int RW = Rec<DS>::kWords;
   constexpr int NS = Rec<DS>::kNS;
   extern __shared__ __align__(16) uint32_t sm[];
@@ -452,15 +412,15 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
     const int n = (g1 - base) < kTG ? (g1 - base) : kTG;
     const uint32_t bytes = (uint32_t)(n * RW * 4);
     const uint32_t bar = bar_s + 8u * (t & 1);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect(bar, bytes);
-    bulk_load(tiles_s + (uint32_t)((t & 1) * kTG * RW * 4), rec + ((size_t)blk * ngroups + base) * RW, bytes,
+    bk::fence_async();
+    bk::mbar_expect(bar, bytes);
+    bk::load(tiles_s + (uint32_t)((t & 1) * kTG * RW * 4), rec + ((size_t)blk * ngroups + base) * RW, bytes,
               bar);
   };
   if (tid == 0) {
-    mbar_init(bar_s, 1);
-    mbar_init(bar_s + 8, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bk::mbar_init(bar_s, 1);
+    bk::mbar_init(bar_s + 8, 1);
+    bk::mbar_init_fence();
   }
   __syncthreads();
   if (tid == 0 && ntiles > 0) issue(0);
@@ -503,7 +463,7 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
     const int n = (g1 - base) < kTG ? (g1 - base) : kTG;
     // stage (t + 1) & 1 was released by the barrier that ended tile t - 1
     if (tid == 0 && t + 1 < ntiles) issue(t + 1);
-    const bool ok = mbar_wait(bar_s + 8u * (t & 1), (uint32_t)((t >> 1) & 1));
+    const bool ok = bk::wait(bar_s + 8u * (t & 1), (uint32_t)((t >> 1) & 1), wait_ns);
     if (ok) {
       const uint4* tile = reinterpret_cast<const uint4*>(tiles + (t & 1) * kTG * RW);
       for (int gi = 0; gi < n; ++gi) {
@@ -549,8 +509,10 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(flags, ddks::kFlagTimeout);
-        // the copy of tile t + 1 may still be in flight: give it a bounded wait
-        if (t + 1 < ntiles) mbar_wait(bar_s + 8u * ((t + 1) & 1), (uint32_t)(((t + 1) >> 1) & 1));
+        // the copies of tiles t and t + 1 may still be in flight: wait for
+        // them (bounded) so that none lands after the CTA has exited
+        for (int k = t; k < t + 2 && k < ntiles; ++k)
+          bk::wait(bar_s + 8u * (k & 1), (uint32_t)((k >> 1) & 1), bk::kDrainNs);
       }
       return;
     }
@@ -721,7 +683,7 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
     cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (r != cudaSuccess) return r;
     kern<<<ctas, kThreads, smem, st>>>(rec, oplanes, meta, no, NP, NT, ngroups, (int)C, (int)CP, GP, GT, CGP,
-                                        CGT, gcnt, flags, fin);
+                                        CGT, gcnt, flags, fin, ctx->dev_wait_ns);
     return cudaGetLastError();
   };
   if (ds == 1) e = occ == 8 ? go(k_register<1, 8>) : occ == 12 ? go(k_register<1, 12>) : go(k_register<1, 16>);

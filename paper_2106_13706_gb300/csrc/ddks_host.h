@@ -48,6 +48,10 @@ struct ddks_ctx {
   ddks_config cfg{};
   int device = 0;
   int num_sms = 152;
+  // bound on each device-side wait for an asynchronous copy (ns): the
+  // config's wait_limit_ms when given, else 1 s; ddks_set_device_wait_limit
+  unsigned long long dev_wait_ns = 1000000000ull;
+  unsigned long long dev_wait_cfg_ns = 1000000000ull;  // the value fixed at creation
   std::string last_err;
   uint64_t launches = 0;
   // scratch of the synchronous entry points
@@ -91,7 +95,9 @@ struct ddks_ctx {
 };
 
 int ctx_cuda_fail(ddks_ctx* ctx, cudaError_t e, const char* where);
-bool ddks_is_device_ptr(const void* p);
+// 1: device memory of `device` or managed memory (read in place); 0: host
+// memory (copied by the call); DDKS_EINVAL: device memory of another GPU.
+int ddks_pointer_kind(const void* p, int device);
 int ddks_check_problem(const void* P, int64_t NP, const void* T, int64_t NT, int32_t d, int32_t dtype);
 int ddks_stage_inputs(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT,
                       int32_t d, int32_t dtype, cudaStream_t st, const void** dP, const void** dT);
@@ -147,6 +153,7 @@ void ddks_graph_clear(ddks_ctx* ctx);
 // no host reads of device results.
 template <typename F>
 int ddks_graph_run(ddks_ctx* ctx, uint64_t key, cudaStream_t st, F&& body) {
+  key = GraphKey().add(key).add(ctx->dev_wait_ns).h;  // the wait bound is a kernel argument too
   cudaStream_t run_st = st;
   int mode = 0;
   int rc = ddks_graph_begin(ctx, key, st, &run_st, &mode);

@@ -4,9 +4,9 @@
 // All scratch lives in one file-scope device array of kNoallocScratch bytes
 // that every GPU loading the library holds until the process exits.  Host code
 // never passes the array's name to a kernel (in host code that name is only a
-// host-side stand-in, not a device address): on the first call on a device,
-// with that device current, cudaGetSymbolAddress yields the array's device
-// address, which is cached per device and passed to the kernels.  Every call
+// host-side stand-in, not a device address): every call, with the device
+// current, asks cudaGetSymbolAddress for the array's device address on that
+// device and passes it to the kernels.  Every call
 // reuses the same array, so calls whose work overlaps on the GPU (different
 // streams, or host threads, on one device) race; the NaN flag, the only state
 // that must start at zero, is cleared by each call.
@@ -37,7 +37,6 @@ constexpr size_t kNoallocScratch =
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch];
 
 std::mutex g_mu;
-void* g_addr[128] = {};
 int g_sms[128] = {};
 
 DDKS_DEV bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
@@ -98,21 +97,22 @@ int fail(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? DDKS_ENOMEM : DDKS_ECUDA;
 }
 
-// Device address of the scratch array on the current device (set up once per device).
+// Device address of the scratch array on the current device, looked up on
+// every call (no allocation; a device reset reloads the module, so a cached
+// address could go stale), and the device's SM count (cached per device).
 int scratch_on_device(int dev, void** addr, int* sms) {
-  std::lock_guard<std::mutex> g(g_mu);
   if (dev < 0 || dev >= 128) return DDKS_EINVAL;
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return fail(e);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return fail(e);
+  std::lock_guard<std::mutex> g(g_mu);
+  if (!g_sms[dev]) {
     int n = 0;
     e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail(e);
-    g_addr[dev] = p;
     g_sms[dev] = n;
   }
-  *addr = g_addr[dev];
+  *addr = p;
   *sms = g_sms[dev];
   return DDKS_OK;
 }
@@ -131,12 +131,13 @@ int ddks_distance_noalloc(const void* P, int64_t NP, const void* T, int64_t NT, 
     cudaGetLastError();
     return out->status = DDKS_EINVAL;
   }
-  if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) ||
-      (ta.type != cudaMemoryTypeDevice && ta.type != cudaMemoryTypeManaged))
-    return out->status = DDKS_EINVAL;  // inputs must already be in device memory
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return out->status = fail(e);
+  // inputs must already be device memory of this device (or managed memory)
+  if (ddks_classify_pointer((int32_t)pa.type, (int32_t)pa.device, dev) != 1 ||
+      ddks_classify_pointer((int32_t)ta.type, (int32_t)ta.device, dev) != 1)
+    return out->status = DDKS_EINVAL;
   void* base = nullptr;
   int sms = 0;
   int rc = scratch_on_device(dev, &base, &sms);

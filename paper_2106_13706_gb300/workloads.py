@@ -93,6 +93,17 @@ def dvu_pair(seed=0, n_p=100, n_t=100, d=1000, dtype=np.float32):
     return P.astype(dtype), T.astype(dtype)
 
 
+def dvu_null_pair(seed=0, n_p=50, n_t=50, d=3, dtype=np.float32):
+    """Both samples from the diagonal distribution of DVU (the null case of
+    the type I study of Sec. 3)."""
+    rng = np.random.default_rng(seed)
+    u = rng.random(n_p)
+    v = rng.random(n_t)
+    P = np.repeat(u[:, None], d, axis=1)
+    T = np.repeat(v[:, None], d, axis=1)
+    return P.astype(dtype), T.astype(dtype)
+
+
 def log_uniform_int(rng, lo, hi, size=None):
     """Integers log-uniform in [lo, hi]."""
     v = np.exp(rng.uniform(math.log(lo), math.log(hi + 1), size=size))

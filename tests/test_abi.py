@@ -71,3 +71,13 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         b.load()
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         b.ddks_ctx_create(device=0)
+
+
+def test_pointer_classification_refuses_other_devices(lib):
+    # cudaMemoryType: 0 unregistered, 1 host, 2 device, 3 managed
+    f = lib.ddks_classify_pointer
+    assert f(2, 0, 0) == 1 and f(2, 3, 3) == 1      # device memory of the call's device: in place
+    assert f(2, 1, 0) == -1 and f(2, 0, 1) == -1    # another GPU's memory: refused, never read
+    assert f(3, 0, 1) == 1                          # managed memory: in place
+    assert f(0, -2, 0) == 0 and f(1, 0, 5) == 0     # host memory: copied by the call
+    assert f(7, 0, 0) == -1                         # unknown type

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import paper_2106_13706_gb300 as pkg
+from oracle import oracle as orc
 from paper_2106_13706_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -54,6 +55,32 @@ def test_two_calls_in_a_row_match_ddks_distance(torch):
             assert rc1 == 0 and rc2 == 0
             assert _key(r1) == _key(ref)
             assert _key(r2) == _key(ref)
+
+
+def _tied_normal(seed, n_p, n_t, d, dtype):
+    P, T = wl.random_pair(seed, n_p, n_t, d, kind="normal", dtype=dtype)
+    rng = np.random.default_rng(seed + 1)
+    k = max(1, n_t // 100)  # 1% of T's rows copy P rows exactly
+    T[rng.choice(n_t, k, replace=False)] = P[rng.choice(n_p, k, replace=False)]
+    return P, T
+
+
+@pytest.mark.parametrize("case", ["f32_int_d8_max", "f64_tied_d8_max", "f32_d7"])
+def test_at_the_stated_limits_against_the_oracle(torch, case):
+    # N = NP + NT = 16384 (the largest shared-memory sort) with d = 8 (the
+    # narrowest lane configuration), in both precisions, with many ties
+    if case == "f32_int_d8_max":
+        P, T = wl.random_pair(21, 8000, 8384, 8, kind="int")
+    elif case == "f64_tied_d8_max":
+        P, T = _tied_normal(22, 9000, 7384, 8, np.float64)
+    else:
+        P, T = _tied_normal(23, 5000, 6001, 7, np.float32)
+    ref = orc.ddks(P, T)
+    Pd, Td = torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()
+    for _ in range(2):
+        rc, r = _noalloc_via_abi(torch, Pd, Td)
+        assert rc == 0
+        assert _key(r) == (ref["num_max"], ref["denom"], ref["argmax_origin"], ref["argmax_orthant"])
 
 
 def test_limits_and_errors(torch):
