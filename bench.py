@@ -756,9 +756,9 @@ def run_perm(args):
         # call (seed 2021) must equal the oracle's
         got = [int(x) for x in ref["perm_num_max"][:nb]]
         want = [int(x) for x in oref["perm_num_max"][:nb]]
-        if got != want or ref["observed"]["num_max"] != oref["observed"]["num_max"]:
+        if got != want or ref["observed"]["num_max"] != oref["num_obs"]:
             raise RuntimeError(f"parity failure: GPU {got} != oracle {want}")
-        parity = {"equal": True, "num_max_oracle": int(oref["observed"]["num_max"]),
+        parity = {"equal": True, "num_max_oracle": int(oref["num_obs"]),
                   "checked": f"observed num_max and the first {nb} relabellings' num_max against the oracle"}
     study = significance_study(ctx, torch, wl, quick=args.steps < 5) if not args.no_study else None
     ctx.close()
