@@ -86,6 +86,10 @@ typedef struct {
                                  exact paths, the rdKS distance orders) run as LSD radix sorts instead of
                                  chunk sorts + merges; 0 = the built-in defaults (16384 for float32
                                  inputs, 131072 for float64 and the rdKS distances), -1 = never */
+  int32_t register_variant;   /* the bit-sliced kernel of DDKS_PATH_REGISTER (d = 2..4): 0 = automatic
+                                 (planes built in shared memory by the count kernel where the re-rank
+                                 tables fit, else staged by a pack kernel), 1 = staged by a pack kernel */
+  int32_t reserved;
 } ddks_config;
 
 typedef struct {

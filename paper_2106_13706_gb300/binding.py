@@ -41,7 +41,8 @@ class ddks_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_int32),
                 ("wait_limit_ms", ctypes.c_int32), ("tune_cache", ctypes.c_char_p),
-                ("graphs", ctypes.c_int32), ("radix_min_n", ctypes.c_int64)]
+                ("graphs", ctypes.c_int32), ("radix_min_n", ctypes.c_int64),
+                ("register_variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ddks_result(ctypes.Structure):
@@ -187,7 +188,7 @@ def _pair(P, T):
 
 # ------------------------------------------------------------------ entry points
 def ddks_ctx_create(device=-1, path=PATH_AUTO, hbm_budget_bytes=0, max_batch=0, wait_limit_ms=0,
-                    tune_cache=None, graphs=True, radix_min_n=0):
+                    tune_cache=None, graphs=True, radix_min_n=0, register_variant=0):
     lib = load()
     cfg = ddks_config()
     lib.ddks_config_default(ctypes.byref(cfg))
@@ -196,6 +197,7 @@ def ddks_ctx_create(device=-1, path=PATH_AUTO, hbm_budget_bytes=0, max_batch=0, 
     cfg.tune_cache = tune_cache.encode() if tune_cache else None
     cfg.graphs = 1 if graphs else 0
     cfg.radix_min_n = radix_min_n
+    cfg.register_variant = register_variant
     h = ctypes.c_void_p()
     _check(lib.ddks_ctx_create(ctypes.byref(cfg), ctypes.byref(h)), what="ddks_ctx_create")
     return h

@@ -117,6 +117,7 @@ int ddks_ctx_create(const ddks_config* cfg, ddks_ctx** out) {
   if (!ctx) return DDKS_ENOMEM;
   if (cfg) ctx->cfg = *cfg; else ddks_config_default(&ctx->cfg);
   if (ctx->cfg.path < DDKS_PATH_AUTO || ctx->cfg.path > DDKS_PATH_DOMINANCE) { delete ctx; return DDKS_EINVAL; }
+  if (ctx->cfg.register_variant < 0 || ctx->cfg.register_variant > 1) { delete ctx; return DDKS_EINVAL; }
   if (ctx->cfg.hbm_budget_bytes == 0) ctx->cfg.hbm_budget_bytes = 8ull << 30;
   if (ctx->cfg.max_batch <= 0) ctx->cfg.max_batch = 64;
   if (ctx->cfg.wait_limit_ms > 0)
@@ -346,7 +347,7 @@ static int distance_impl(ddks_ctx* ctx, const void* P, int64_t NP, const void* T
   GraphKey key;
   key.add(1).add((uint64_t)NP).add((uint64_t)NT).add((uint64_t)d).add((uint64_t)dtype);
   key.add((uint64_t)ob).add((uint64_t)oe).add((uint64_t)plan.path).add((uint64_t)plan.threads);
-  key.add((uint64_t)plan.warps).add((uint64_t)plan.reg_occ).add_ptr(dP).add_ptr(dT);
+  key.add((uint64_t)plan.warps).add((uint64_t)plan.reg_occ).add((uint64_t)plan.fused).add_ptr(dP).add_ptr(dT);
   key.add((uint64_t)ctx->stage_timing);
   rc = ddks_graph_run(ctx, key.h, st, [&](cudaStream_t s) -> int {
     int r;

@@ -35,6 +35,7 @@
 // last unit of a block turns the block's counters into per-origin maxima and
 // the last block writes the result.
 #include "bulk_copy.cuh"
+#include "count_register.cuh"
 #include "ddks_host.h"
 #include "ddks_internal.cuh"
 
@@ -42,28 +43,21 @@ namespace {
 
 namespace bk = ddks::bulk;
 
+using namespace ddks_reg;
+
 constexpr int kThreads = 64;          // threads per CTA of the count kernel
 constexpr int kOPL = 2;               // origin slots per thread
-constexpr int kOC = kThreads * kOPL;  // origin slots per block (128)
-constexpr int kOB = kOC - 1;          // origins per block (x' <= 127 fits 7 bits)
-constexpr int kBits = 7;              // planes per dimension
+static_assert(kThreads * kOPL == kOC, "one origin block per CTA");
 constexpr int kTG = 64;               // groups (of 32 points) per staged tile
 constexpr int64_t kMaxRegN = 200000;
 constexpr int kPackThreads = 512;     // one origin block per CTA
 constexpr int kPack4Threads = 1024;   // four origin blocks per CTA
-constexpr int kCnt = 32;              // counters per origin: [sample][all, B][subset] (<= 2*2*7 used)
 
 // record of one group: per dimension 8 words (7 planes + 1 pad), 16-byte aligned
 template <int DS>
 struct Rec {
   static constexpr int kWords = 8 * DS;
   static constexpr int kNS = (1 << DS) - 1;  // non-empty subsets of the DS dimensions
-};
-
-struct OriginMeta {
-  uint32_t sP, sT;  // splits, sample-local: P points / T points with a smaller dimension-0 rank
-  uint32_t k;       // pooled index
-  uint32_t pad;
 };
 
 // ------------------------------------------------------------------ preparation
@@ -127,36 +121,6 @@ __global__ void k_reg_meta(const uint32_t* __restrict__ rank, const uint32_t* __
     for (int mm = 0; mm < ds; ++mm) orank[(int64_t)mm * no + q] = rank[(int64_t)(mm + 1) * N + k];
   }
 }
-
-// Block-wide exclusive scan of one value per thread (THREADS threads, a
-// multiple of 32 up to 1024).
-template <int THREADS>
-DDKS_DEV uint32_t block_exscan(uint32_t v, uint32_t* tmp /* >= 33 words */) {
-  constexpr int kWarps = THREADS / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t incl = v;
-  for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl += x;
-  }
-  if (lane == 31) tmp[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    const uint32_t w = lane < kWarps ? tmp[lane] : 0u;
-    uint32_t wi = w;
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t x = __shfl_up_sync(0xffffffffu, wi, off);
-      if (lane >= off) wi += x;
-    }
-    if (lane < kWarps) tmp[lane] = wi - w;
-  }
-  __syncthreads();
-  const uint32_t r = tmp[warp] + incl - v;
-  __syncthreads();
-  return r;
-}
-
-
 
 // 4x4 byte transpose: out[k] byte g = in[g] byte k
 DDKS_DEV void transpose4(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3, uint32_t (&o)[4]) {
@@ -246,14 +210,7 @@ k_reg_pack(const uint32_t* __restrict__ rankL, const uint32_t* __restrict__ oran
   // exchanging half blocks with the partner lane; keep[j] masks the bits a
   // lane keeps in the round of width j
   uint32_t keep[5];
-  {
-    uint32_t m = 0xFFFF0000u;
-#pragma unroll
-    for (int rd = 0, j = 16; rd < 5; ++rd, j >>= 1) {
-      keep[rd] = (lane & j) ? ~(m >> j) : ~m;
-      m ^= m >> (j >> 1);
-    }
-  }
+  transpose_masks(lane, keep);
   constexpr int kU = 4;  // groups in flight per warp
   constexpr int kW = THREADS / 32;
   const int g = lane >> 3, k = lane & 7;
@@ -299,81 +256,6 @@ k_reg_pack(const uint32_t* __restrict__ rankL, const uint32_t* __restrict__ oran
 }
 
 // ------------------------------------------------------------------ main kernel
-
-// One bit of the bit-sliced comparison, from the least significant bit up:
-// r = s ? (pl & r) : (pl | r), s = all ones where the origin's bit is set --
-// one 3-input logic op (truth table 0x8E for operands s, pl, r).
-DDKS_DEV uint32_t cmp_step(uint32_t s, uint32_t pl, uint32_t r) {
-  uint32_t d;
-  asm("lop3.b32 %0, %1, %2, %3, 0x8E;" : "=r"(d) : "r"(s), "r"(pl), "r"(r));
-  return d;
-}
-
-// Fused final step: per-origin maxima into best/bestj at pooled index - ob,
-// and (out3 != nullptr) the result {num_max, arg-max origin, orthant} into
-// out3.  done:
-// [blocks + 1] zeroed tickets; packed: one zeroed word holding the maximum
-// over origins of (num << kPackShift) | (kPackMask - position).
-struct Final {
-  unsigned long long* out3;
-  unsigned* done;
-  unsigned long long* packed;
-  uint64_t* best;
-  int32_t* bestj;
-  int64_t ob;
-  int blocks;
-};
-constexpr int kPackShift = 26;                       // positions < 2^26; numerators < 2^38
-constexpr unsigned long long kPackMask = (1ull << kPackShift) - 1;
-
-// The orthant counts of one origin and sample from its subset counters:
-// n[0] = all points of the phase, n[S] = points in all dimensions of S.
-template <int DS>
-DDKS_DEV void orthants(const uint32_t (&n)[1 << DS], uint32_t (&cnt)[1 << DS]) {
-#pragma unroll
-  for (int B = 0; B < (1 << DS); ++B) {
-    int64_t v = 0;
-#pragma unroll
-    for (int S = 0; S < (1 << DS); ++S)
-      if ((S & B) == B) v += (__popc(S ^ B) & 1) ? -(int64_t)n[S] : (int64_t)n[S];
-    cnt[B] = (uint32_t)v;
-  }
-}
-
-// The best code of origin q: counters c[sample][0 = all, 1 = phase B][S - 1].
-template <int DS>
-DDKS_DEV void origin_best(const uint32_t* __restrict__ gcnt, const OriginMeta& mt, int64_t q, int64_t NP,
-                          int64_t NT, uint64_t& bv, int& bj) {
-  constexpr int NS = (1 << DS) - 1;
-  const uint32_t* c = gcnt + q * kCnt;
-  uint32_t cnt[2][2][1 << DS];  // [sample][phase A, B][bin]
-#pragma unroll
-  for (int smp = 0; smp < 2; ++smp) {
-    const uint32_t size = smp == 0 ? (uint32_t)NP : (uint32_t)NT;
-    const uint32_t split = smp == 0 ? mt.sP : mt.sT;
-    uint32_t nA[1 << DS], nB[1 << DS];
-    nA[0] = split;
-    nB[0] = size - split;
-#pragma unroll
-    for (int S = 1; S <= NS; ++S) {
-      const uint32_t all = __ldcg(&c[(smp * 2 + 0) * NS + S - 1]);
-      const uint32_t b = __ldcg(&c[(smp * 2 + 1) * NS + S - 1]);
-      nA[S] = all - b;
-      nB[S] = b;
-    }
-    orthants<DS>(nA, cnt[smp][0]);
-    orthants<DS>(nB, cnt[smp][1]);
-  }
-  bv = 0;
-  bj = 0;
-  // code = bin << 1 | phase (bit 0 is dimension 0), lowest code first
-#pragma unroll
-  for (int code = 0; code < (2 << DS); ++code) {
-    const int ph = code & 1, bin = code >> 1;
-    const uint64_t num = ddks::numer(cnt[0][ph][bin], cnt[1][ph][bin], (uint64_t)NP, (uint64_t)NT);
-    if (num > bv) { bv = num; bj = code; }
-  }
-}
 
 // Unit u: origin block u / C, chunk u % C of the groups, where chunks [0, CP)
 // cover the P list's groups [0, GP) in pieces of CGP and chunks [CP, C) the T
@@ -546,7 +428,7 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
     uint64_t bv;
     int bj;
     const OriginMeta mt = meta[q[o]];
-    origin_best<DS>(gcnt, mt, q[o], NP, NT, bv, bj);
+    origin_best<DS, false>(gcnt, mt, q[o], NP, NT, bv, bj);
     const int64_t pos = (int64_t)mt.k - fin.ob;
     fin.best[pos] = bv;
     fin.bestj[pos] = bj;
@@ -603,8 +485,10 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   int rc = ctx->reg_meta.reserve(ctx, n_u32 * 4 + (size_t)no * sizeof(OriginMeta) + 64);
   if (rc) return cudaErrorMemoryAllocation;
   // group records [blocks][ngroups][ds][8] u32 and origin values [blocks][ds][128] u8
-  const size_t rec_words = (size_t)blocks * ngroups * ds * 8;
-  rc = ctx->reg_words.reserve(ctx, rec_words * 4 + (size_t)blocks * ds * kOC);
+  const bool fused = plan.fused && ddks_fused_supported(ds, N);
+  const size_t rec_words = fused ? 0 : (size_t)blocks * ngroups * ds * 8;
+  rc = ctx->reg_words.reserve(ctx, fused ? ddks_fused_scratch_bytes(ds, N, blocks)
+                                         : rec_words * 4 + (size_t)blocks * ds * kOC);
   if (rc) return cudaErrorMemoryAllocation;
   uint32_t* pprefix = (uint32_t*)ctx->reg_meta.ptr;
   uint32_t* exO = pprefix + N;
@@ -645,6 +529,16 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   n += 2;
   // stage timing: the count stage (re-rank packing included) starts here
   ddks_stage_mark(ctx, 1, st);
+  if (fused) {
+    e = cudaMemsetAsync(gcnt, 0, ((size_t)no * kCnt + n_fin) * 4, st);
+    if (e == cudaSuccess)
+      e = ddks_fused_count(ctx, ds, rankL, orank, meta, no, N, NP, NT, NPpad, Lrow, gcnt, done, packed, best, bestj,
+                           ob, out3, flags, ctx->reg_words.ptr, st, &n);
+    if (e != cudaSuccess) return e;
+    if (reduced) *reduced = out3 != nullptr;
+    ctx->launches += n;
+    return cudaSuccess;
+  }
   if (pack_smem(NW, 4) <= kPackSmemMax) {
     const size_t psmem = pack_smem(NW, 4);
     e = cudaFuncSetAttribute(k_reg_pack<4, kPack4Threads>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -509,7 +509,7 @@ int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* 
   GraphKey key;
   key.add(2).add((uint64_t)NP).add((uint64_t)NT).add((uint64_t)d).add((uint64_t)dtype).add((uint64_t)B);
   key.add((uint64_t)plan.path).add((uint64_t)plan.threads).add((uint64_t)plan.warps);
-  key.add((uint64_t)plan.reg_occ).add_ptr(dP).add_ptr(dT).add((uint64_t)ctx->stage_timing);
+  key.add((uint64_t)plan.reg_occ).add((uint64_t)plan.fused).add_ptr(dP).add_ptr(dT).add((uint64_t)ctx->stage_timing);
   rc = ddks_graph_run(ctx, key.h, st, [&](cudaStream_t s) -> int {
     int r;
     if ((r = ddks_encode_problem(ctx, dP, NP, dT, NT, d, dtype, s, plan.path == DDKS_PATH_REGISTER))) return r;

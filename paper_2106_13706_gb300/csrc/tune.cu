@@ -81,6 +81,7 @@ int ddks_select_path(ddks_ctx* ctx, int64_t NP, int64_t NT, int32_t d, ddks_plan
     const int forced = ctx->cfg.path;
     p.path = forced;
     if (forced == DDKS_PATH_LANE) p.threads = d <= 4 ? 256 : (d <= 6 ? 128 : 64);
+    if (forced == DDKS_PATH_REGISTER) p.fused = ctx->cfg.register_variant == 1 ? 0 : 1;
     if (!plan_ok(p, NP, NT, d)) return DDKS_EUNSUPPORTED;
     *plan = p;
     return DDKS_OK;
@@ -101,7 +102,7 @@ void ddks_tune_load(ddks_ctx* ctx) {
   if (!f) return;
   char key[64];
   ddks_plan p;
-  while (std::fscanf(f, "%63s %d %d %d %d", key, &p.path, &p.threads, &p.warps, &p.reg_occ) == 5) {
+  while (std::fscanf(f, "%63s %d %d %d %d %d", key, &p.path, &p.threads, &p.warps, &p.reg_occ, &p.fused) == 6) {
     ctx->tune[key] = p;
   }
   std::fclose(f);
@@ -113,8 +114,8 @@ static void tune_save(ddks_ctx* ctx) {
   FILE* f = std::fopen(tmp.c_str(), "w");
   if (!f) return;
   for (auto& kv : ctx->tune)
-    std::fprintf(f, "%s %d %d %d %d\n", kv.first.c_str(), kv.second.path, kv.second.threads,
-                 kv.second.warps, kv.second.reg_occ);
+    std::fprintf(f, "%s %d %d %d %d %d\n", kv.first.c_str(), kv.second.path, kv.second.threads,
+                 kv.second.warps, kv.second.reg_occ, kv.second.fused);
   std::fclose(f);
   std::rename(tmp.c_str(), ctx->tune_cache_path.c_str());
 }
@@ -135,8 +136,9 @@ int ddks_autotune(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64
   if ((rc = ctx->bestj.reserve(ctx, 4 * (size_t)N))) return rc;
   if ((rc = ctx->out3.reserve(ctx, 64 + ddks_reduce_scratch_bytes()))) return rc;
   std::vector<ddks_plan> cands;
+  { ddks_plan p; p.path = DDKS_PATH_REGISTER; p.fused = 1; cands.push_back(p); }
   for (int occ : {4, 6, 8}) {
-    ddks_plan p; p.path = DDKS_PATH_REGISTER; p.reg_occ = occ; cands.push_back(p);
+    ddks_plan p; p.path = DDKS_PATH_REGISTER; p.reg_occ = occ; p.fused = 0; cands.push_back(p);
   }
   for (int th : {64, 128, 256}) {
     ddks_plan p; p.path = DDKS_PATH_LANE; p.threads = th; cands.push_back(p);

@@ -56,10 +56,12 @@ def test_config_defaults(lib):
     cfg = pkg.binding.ddks_config()
     cfg.radix_min_n = 123
     lib.ddks_config_default(ctypes.byref(cfg))
-    assert cfg.radix_min_n == 0 and cfg.graphs == 1 and cfg.device == -1
-    # the binding's struct matches the header's field order up to the last field
+    assert cfg.radix_min_n == 0 and cfg.graphs == 1 and cfg.device == -1 and cfg.register_variant == 0
+    # the binding's struct matches the header's field order and size
     names = [n for n, _ in pkg.binding.ddks_config._fields_]
-    assert names[-1] == "radix_min_n" and names.index("graphs") == len(names) - 2
+    assert names[-3:] == ["radix_min_n", "register_variant", "reserved"]
+    assert names.index("graphs") == len(names) - 4
+    assert ctypes.sizeof(pkg.binding.ddks_config) == 56
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
