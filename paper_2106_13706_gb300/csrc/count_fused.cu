@@ -102,18 +102,17 @@ k_fused_tables(const uint32_t* __restrict__ orank, int64_t no, int W, uint2* __r
 #pragma unroll
     for (int m = 0; m < DS; ++m) c += (uint32_t)__popc(bits[m * W + w]) << (8 * m);
   uint32_t run = block_exscan<kPrepThreads>(c, tmp);
-  uint2* out = tab + (int64_t)blk * tab_stride(DS, W);
   for (int w = wa; w < wb; ++w) {
 #pragma unroll
     for (int m = 0; m < DS; ++m) {
       const uint32_t bw = bits[m * W + w];
-      const uint32_t p = (run >> (8 * m)) & 0xFFu;
-      out[m * W + w] = make_uint2(bw, p);
-      pf[m * W + w] = (uint8_t)p;
+      pf[m * W + w] = (uint8_t)((run >> (8 * m)) & 0xFFu);
       run += (uint32_t)__popc(bw) << (8 * m);
     }
   }
   __syncthreads();
+  uint2* out = tab + (int64_t)blk * tab_stride(DS, W);
+  for (int i = tid; i < DS * W; i += kPrepThreads) out[i] = make_uint2(bits[i], pf[i]);
   for (int i = tid; i < DS * kOC; i += kPrepThreads) {
     const int m = i / kOC, slot = i - m * kOC;
     const int64_t q = (int64_t)blk * kOB + slot;
@@ -251,11 +250,19 @@ k_fused(const uint32_t* __restrict__ rankL, const uint2* __restrict__ tab, const
       const int64_t lbase = smp == 0 ? 0 : NPpad;  // list position of the sample's first point
       const uint32_t wlo = smp == 0 ? wloP : wloT, whi = smp == 0 ? whiP : whiT;
       const uint32_t sp0 = smp == 0 ? spP[0] : spT[0], sp1 = smp == 0 ? spP[1] : spT[1];
-      uint32_t a[2][NS], b[2][NS];  // phase-A and phase-B counters of this thread's origins
+      // acc[o][S]: this pair's points so far >= origin o in every dimension
+      // of S; snap[o][S]: acc at the origin's split.  A pair visits its
+      // groups in increasing order, so its groups before the split are
+      // wholly phase A, those after it wholly phase B.
+      uint32_t acc_r[2][NS], snap[2][NS];
+      bool crossed[2];
 #pragma unroll
-      for (int o = 0; o < 2; ++o)
+      for (int o = 0; o < 2; ++o) {
+        crossed[o] = false;
 #pragma unroll
-        for (int S = 0; S < NS; ++S) a[o][S] = b[o][S] = 0u;
+        for (int S = 0; S < NS; ++S) acc_r[o][S] = snap[o][S] = 0u;
+      }
+      bool all_crossed = false;  // warp-uniform: past the block's window
       const int nb = (int)((pb - pa + kBG - 1) / kBG);
       // thread 0 of the pair: the ranks of batch i into stage st
       auto issue = [&](int i, uint32_t st) {
@@ -321,6 +328,37 @@ k_fused(const uint32_t* __restrict__ rankL, const uint2* __restrict__ tab, const
               G[o][m] = r;
             }
           }
+          if (!all_crossed && gl >= wlo) {
+            if (gl >= whi) {
+              // past every split of the block: the rest is phase B
+#pragma unroll
+              for (int o = 0; o < 2; ++o)
+                if (!crossed[o]) {
+#pragma unroll
+                  for (int S = 0; S < NS; ++S) snap[o][S] = acc_r[o][S];
+                  crossed[o] = true;
+                }
+              all_crossed = true;
+            } else {
+              // a group that may hold some origin's split
+#pragma unroll
+              for (int o = 0; o < 2; ++o) {
+                const uint32_t sp = o == 0 ? sp0 : sp1, pos0 = gl * 32u;
+                if (!crossed[o] && sp < pos0 + 32u) {
+                  const uint32_t pam = sp > pos0 ? (1u << (sp - pos0)) - 1u : 0u;  // phase-A points
+#pragma unroll
+                  for (int S = 1; S <= NS; ++S) {
+                    uint32_t Ms = pam;  // phase-A points >= the origin in every dimension of S
+#pragma unroll
+                    for (int m = 0; m < DS; ++m)
+                      if ((S >> m) & 1) Ms &= G[o][m];
+                    snap[o][S - 1] = acc_r[o][S - 1] + (uint32_t)__popc(Ms);
+                  }
+                  crossed[o] = true;
+                }
+              }
+            }
+          }
 #pragma unroll
           for (int o = 0; o < 2; ++o) {
             // M[S] = the group's points >= the origin in every dimension of S
@@ -331,25 +369,21 @@ k_fused(const uint32_t* __restrict__ rankL, const uint2* __restrict__ tab, const
               const uint32_t gdim = (S & 1) ? G[o][0] : ((S & 2) ? G[o][DS > 1 ? 1 : 0] : G[o][DS > 2 ? 2 : 0]);
               M[S] = M[S & (S - 1)] & gdim;
             }
-            if (gl < wlo) {
 #pragma unroll
-              for (int S = 1; S <= NS; ++S) a[o][S - 1] += (uint32_t)__popc(M[S]);
-            } else if (gl >= whi) {
-#pragma unroll
-              for (int S = 1; S <= NS; ++S) b[o][S - 1] += (uint32_t)__popc(M[S]);
-            } else {
-              // the group holds some origin's split: phase-A points per origin
-              const uint32_t sp = o == 0 ? sp0 : sp1, pos0 = gl * 32u;
-              const uint32_t pam = sp >= pos0 + 32u ? 0xFFFFFFFFu : (sp > pos0 ? (1u << (sp - pos0)) - 1u : 0u);
-#pragma unroll
-              for (int S = 1; S <= NS; ++S) {
-                a[o][S - 1] += (uint32_t)__popc(M[S] & pam);
-                b[o][S - 1] += (uint32_t)__popc(M[S] & ~pam);
-              }
-            }
+            for (int S = 1; S <= NS; ++S) acc_r[o][S - 1] += (uint32_t)__popc(M[S]);
           }
         }
       }
+      // phase A = the snapshot (all of acc if the pair never passed the
+      // split), phase B = the rest
+      uint32_t a[2][NS], b[2][NS];
+#pragma unroll
+      for (int o = 0; o < 2; ++o)
+#pragma unroll
+        for (int S = 0; S < NS; ++S) {
+          a[o][S] = crossed[o] ? snap[o][S] : acc_r[o][S];
+          b[o][S] = acc_r[o][S] - a[o][S];
+        }
       if (aborted) s_abort = 1u;
       // the pairs' counters, summed in shared memory
 #pragma unroll
