@@ -86,9 +86,12 @@ typedef struct {
                                  exact paths, the rdKS distance orders) run as LSD radix sorts instead of
                                  chunk sorts + merges; 0 = the built-in defaults (16384 for float32
                                  inputs, 131072 for float64 and the rdKS distances), -1 = never */
-  int32_t register_variant;   /* the bit-sliced kernel of DDKS_PATH_REGISTER (d = 2..4): 0 = automatic
-                                 (planes built in shared memory by the count kernel where the re-rank
-                                 tables fit, else staged by a pack kernel), 1 = staged by a pack kernel */
+  int32_t register_variant;   /* the bit-sliced kernel of DDKS_PATH_REGISTER (d = 2..4) when that path is
+                                 forced: 0 = automatic (the bit planes staged in global memory by a
+                                 pack kernel), 1 = staged by the pack kernel, 2..4 = built in shared
+                                 memory by the count kernel itself (where the re-rank tables fit) with count
+                                 kernel shape 1..3 (4 warp pairs at 2 CTAs/SM; 4 pairs at 1 CTA/SM,
+                                 unrolled; 2 pairs at 3 CTAs/SM) */
   int32_t reserved;
 } ddks_config;
 

@@ -117,7 +117,7 @@ int ddks_ctx_create(const ddks_config* cfg, ddks_ctx** out) {
   if (!ctx) return DDKS_ENOMEM;
   if (cfg) ctx->cfg = *cfg; else ddks_config_default(&ctx->cfg);
   if (ctx->cfg.path < DDKS_PATH_AUTO || ctx->cfg.path > DDKS_PATH_DOMINANCE) { delete ctx; return DDKS_EINVAL; }
-  if (ctx->cfg.register_variant < 0 || ctx->cfg.register_variant > 1) { delete ctx; return DDKS_EINVAL; }
+  if (ctx->cfg.register_variant < 0 || ctx->cfg.register_variant > 4) { delete ctx; return DDKS_EINVAL; }
   if (ctx->cfg.hbm_budget_bytes == 0) ctx->cfg.hbm_budget_bytes = 8ull << 30;
   if (ctx->cfg.max_batch <= 0) ctx->cfg.max_batch = 64;
   if (ctx->cfg.wait_limit_ms > 0)

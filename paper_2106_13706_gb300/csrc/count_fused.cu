@@ -40,8 +40,6 @@ namespace {
 using namespace ddks_reg;
 namespace bk = ddks::bulk;
 
-constexpr int kPairs = 4;               // warp pairs per CTA
-constexpr int kFThreads = 64 * kPairs;  // threads per CTA of the count kernel
 constexpr int kBG = 16;                 // groups per batch (each warp of a pair builds 8)
 constexpr int kPrepThreads = 256;
 
@@ -51,9 +49,9 @@ __host__ __device__ constexpr int64_t tab_stride(int ds, int W) { return ((int64
 // Dynamic shared memory of the count kernel, in this order:
 //   stab  uint2 [DS][W] (padded to 16 bytes)   the current block's table
 //   acc   u32 [kOC][2][NS]                    a piece's counters, summed over the pairs
-//   per warp pair: rbuf u32 [2][DS][kBG * 32] ranks of a batch (two stages)
+//   per warp pair (NPR of them): rbuf u32 [2][DS][kBG * 32] ranks of a batch (two stages)
 //                  pbuf u32 [2][kBG][DS][8]   bit planes of a batch (two stages)
-template <int DS>
+template <int DS, int NPR>
 struct FusedSmem {
   static constexpr int NS = (1 << DS) - 1;
   static constexpr size_t acc_bytes = (size_t)kOC * 2 * NS * 4;
@@ -61,7 +59,7 @@ struct FusedSmem {
   static constexpr size_t pbuf_bytes = (size_t)2 * kBG * DS * 8 * 4;
   static constexpr size_t pair_bytes = rbuf_bytes + pbuf_bytes;
   __host__ __device__ static constexpr size_t tab_bytes(int W) { return (size_t)tab_stride(DS, W) * 8; }
-  __host__ __device__ static constexpr size_t total(int W) { return tab_bytes(W) + acc_bytes + kPairs * pair_bytes; }
+  __host__ __device__ static constexpr size_t total(int W) { return tab_bytes(W) + acc_bytes + NPR * pair_bytes; }
 };
 
 // ------------------------------------------------------------------ prep
@@ -148,13 +146,16 @@ DDKS_DEV uint32_t rerank(const uint2* __restrict__ row, uint32_t r) {
 // Persistent count kernel: CTA b takes units [units * b / grid, units * (b + 1)
 // / grid) of the (origin block, group) sequence, block-major, within a block
 // the P list's GP groups then the T list's GT groups.
-template <int DS>
-__global__ void __launch_bounds__(kFThreads)
+// NPR warp pairs per CTA; MINB resident CTAs per SM the registers are budgeted
+// for; UNR the unroll of the group loop.
+template <int DS, int NPR, int MINB, int UNR>
+__global__ void __launch_bounds__(64 * NPR, MINB)
 k_fused(const uint32_t* __restrict__ rankL, const uint2* __restrict__ tab, const uint8_t* __restrict__ oval,
         const OriginMeta* __restrict__ meta, int64_t no, int64_t NP, int64_t NT, int64_t NPpad, int64_t Lrow,
         int W, int GP, int GT, int64_t units, uint32_t* __restrict__ gcnt, unsigned* __restrict__ flags,
         const Final fin, unsigned long long wait_ns) {
-  using SM = FusedSmem<DS>;
+  using SM = FusedSmem<DS, NPR>;
+  constexpr int kPairs = NPR, kFThreads = 64 * NPR;
   constexpr int NS = SM::NS;
   extern __shared__ __align__(16) unsigned char fraw[];
   __shared__ __align__(8) unsigned long long bars[1 + 2 * kPairs];
@@ -178,9 +179,6 @@ k_fused(const uint32_t* __restrict__ rankL, const uint2* __restrict__ tab, const
   }
   for (int i = tid; i < kOC * 2 * NS; i += kFThreads) acc[i] = 0u;
   __syncthreads();
-  uint32_t keep[5];
-  transpose_masks(lane, keep);
-
   const int64_t per = (int64_t)GP + GT;
   const int64_t u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
   uint32_t visits = 0;  // table loads so far (the phase of bars[0])
@@ -250,19 +248,28 @@ k_fused(const uint32_t* __restrict__ rankL, const uint2* __restrict__ tab, const
       const int64_t lbase = smp == 0 ? 0 : NPpad;  // list position of the sample's first point
       const uint32_t wlo = smp == 0 ? wloP : wloT, whi = smp == 0 ? whiP : whiT;
       const uint32_t sp0 = smp == 0 ? spP[0] : spT[0], sp1 = smp == 0 ? spP[1] : spT[1];
-      // acc[o][S]: this pair's points so far >= origin o in every dimension
-      // of S; snap[o][S]: acc at the origin's split.  A pair visits its
-      // groups in increasing order, so its groups before the split are
-      // wholly phase A, those after it wholly phase B.
-      uint32_t acc_r[2][NS], snap[2][NS];
+      // acc_r[o][S]: this pair's points so far >= origin o in every dimension
+      // of S.  A pair visits its groups in increasing order, so its groups
+      // before an origin's split are wholly phase A and those after it wholly
+      // phase B.  When the pair reaches the split it adds its phase-A count
+      // so far to the shared phase-A counter and takes it off the phase-B
+      // counter, which receives acc_r at the end.
+      uint32_t acc_r[2][NS];
       bool crossed[2];
 #pragma unroll
       for (int o = 0; o < 2; ++o) {
         crossed[o] = false;
 #pragma unroll
-        for (int S = 0; S < NS; ++S) acc_r[o][S] = snap[o][S] = 0u;
+        for (int S = 0; S < NS; ++S) acc_r[o][S] = 0u;
       }
       bool all_crossed = false;  // warp-uniform: past the block's window
+      auto snapshot = [&](int o, int S, uint32_t v) {
+        if (real[o] && v) {
+          const int slot = tp + 64 * o;
+          atomicAdd(&acc[(slot * 2 + 0) * NS + S], v);
+          atomicSub(&acc[(slot * 2 + 1) * NS + S], v);
+        }
+      };
       const int nb = (int)((pb - pa + kBG - 1) / kBG);
       // thread 0 of the pair: the ranks of batch i into stage st
       auto issue = [&](int i, uint32_t st) {
@@ -287,12 +294,16 @@ k_fused(const uint32_t* __restrict__ rankL, const uint2* __restrict__ tab, const
         uint32_t* pl_st = pbuf + st * (kBG * DS * 8);
         if (ok) {
           // x' of the batch's points, 32 per group, turned into bit planes:
-          // after the transpose lane 8m + k holds plane k of dimension m + 1
+          // after the transpose lane 8m + k holds plane k of dimension m + 1.
+          // Groups past the batch's end get zero planes (no point is >= a
+          // real origin there).
           const uint32_t* rb = rbuf + st * (DS * kBG * 32);
-          for (int j = half; j < n; j += 2) {
+          uint32_t keep[5];
+          transpose_masks(lane, keep);
+          for (int j = half; j < kBG; j += 2) {
             const int64_t pos = (g0 + j) * 32 + lane;  // sample-local position
             uint32_t w = 0;
-            if (pos < size) {
+            if (j < n && pos < size) {
 #pragma unroll
               for (int m = 0; m < DS; ++m)
                 w |= rerank(stab + (size_t)m * W, rb[m * (kBG * 32) + j * 32 + lane]) << (8 * m);
@@ -313,55 +324,24 @@ k_fused(const uint32_t* __restrict__ rankL, const uint2* __restrict__ tab, const
           break;
         }
         const uint4* P4 = reinterpret_cast<const uint4*>(pl_st);
-        for (int j = 0; j < n; ++j) {
-          const uint32_t gl = (uint32_t)(g0 + j);
-          uint32_t G[2][DS];
+        // G[o][m] = the group's points >= origin o in dimension m + 1
+        auto compare = [&](int j, uint32_t (&G)[2][DS]) {
 #pragma unroll
           for (int m = 0; m < DS; ++m) {
             const uint4 x0 = P4[(j * DS + m) * 2], x1 = P4[(j * DS + m) * 2 + 1];
             const uint32_t pl[kBits] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z};
 #pragma unroll
             for (int o = 0; o < 2; ++o) {
-              uint32_t r = 0xFFFFFFFFu;
+              uint32_t r = pl[0] | ~s[o][m][0];
 #pragma unroll
-              for (int k = 0; k < kBits; ++k) r = cmp_step(s[o][m][k], pl[k], r);
+              for (int k = 1; k < kBits; ++k) r = cmp_step(s[o][m][k], pl[k], r);
               G[o][m] = r;
             }
           }
-          if (!all_crossed && gl >= wlo) {
-            if (gl >= whi) {
-              // past every split of the block: the rest is phase B
-#pragma unroll
-              for (int o = 0; o < 2; ++o)
-                if (!crossed[o]) {
-#pragma unroll
-                  for (int S = 0; S < NS; ++S) snap[o][S] = acc_r[o][S];
-                  crossed[o] = true;
-                }
-              all_crossed = true;
-            } else {
-              // a group that may hold some origin's split
-#pragma unroll
-              for (int o = 0; o < 2; ++o) {
-                const uint32_t sp = o == 0 ? sp0 : sp1, pos0 = gl * 32u;
-                if (!crossed[o] && sp < pos0 + 32u) {
-                  const uint32_t pam = sp > pos0 ? (1u << (sp - pos0)) - 1u : 0u;  // phase-A points
-#pragma unroll
-                  for (int S = 1; S <= NS; ++S) {
-                    uint32_t Ms = pam;  // phase-A points >= the origin in every dimension of S
-#pragma unroll
-                    for (int m = 0; m < DS; ++m)
-                      if ((S >> m) & 1) Ms &= G[o][m];
-                    snap[o][S - 1] = acc_r[o][S - 1] + (uint32_t)__popc(Ms);
-                  }
-                  crossed[o] = true;
-                }
-              }
-            }
-          }
+        };
+        auto accumulate = [&](const uint32_t (&G)[2][DS]) {
 #pragma unroll
           for (int o = 0; o < 2; ++o) {
-            // M[S] = the group's points >= the origin in every dimension of S
             uint32_t M[NS + 1];
             M[0] = 0xFFFFFFFFu;
 #pragma unroll
@@ -372,29 +352,65 @@ k_fused(const uint32_t* __restrict__ rankL, const uint2* __restrict__ tab, const
 #pragma unroll
             for (int S = 1; S <= NS; ++S) acc_r[o][S - 1] += (uint32_t)__popc(M[S]);
           }
+        };
+        if (all_crossed || g0 + kBG <= (int64_t)wlo) {
+          // no split in this batch for any origin of the block
+#pragma unroll UNR
+          for (int j = 0; j < kBG; ++j) {
+            uint32_t G[2][DS];
+            compare(j, G);
+            accumulate(G);
+          }
+        } else {
+          for (int j = 0; j < n; ++j) {
+            const uint32_t gl = (uint32_t)(g0 + j);
+            uint32_t G[2][DS];
+            compare(j, G);
+            if (!all_crossed && gl >= wlo) {
+              if (gl >= whi) {
+                // past every split of the block: the rest is phase B
+#pragma unroll
+                for (int o = 0; o < 2; ++o)
+                  if (!crossed[o]) {
+#pragma unroll
+                    for (int S = 0; S < NS; ++S) snapshot(o, S, acc_r[o][S]);
+                    crossed[o] = true;
+                  }
+                all_crossed = true;
+              } else {
+                // a group that may hold some origin's split
+#pragma unroll
+                for (int o = 0; o < 2; ++o) {
+                  const uint32_t sp = o == 0 ? sp0 : sp1, pos0 = gl * 32u;
+                  if (!crossed[o] && sp < pos0 + 32u) {
+                    const uint32_t pam = sp > pos0 ? (1u << (sp - pos0)) - 1u : 0u;  // phase-A points
+#pragma unroll
+                    for (int S = 1; S <= NS; ++S) {
+                      uint32_t Ms = pam;
+#pragma unroll
+                      for (int m = 0; m < DS; ++m)
+                        if ((S >> m) & 1) Ms &= G[o][m];
+                      snapshot(o, S - 1, acc_r[o][S - 1] + (uint32_t)__popc(Ms));
+                    }
+                    crossed[o] = true;
+                  }
+                }
+              }
+            }
+            accumulate(G);
+          }
         }
       }
-      // phase A = the snapshot (all of acc if the pair never passed the
-      // split), phase B = the rest
-      uint32_t a[2][NS], b[2][NS];
-#pragma unroll
-      for (int o = 0; o < 2; ++o)
-#pragma unroll
-        for (int S = 0; S < NS; ++S) {
-          a[o][S] = crossed[o] ? snap[o][S] : acc_r[o][S];
-          b[o][S] = acc_r[o][S] - a[o][S];
-        }
       if (aborted) s_abort = 1u;
-      // the pairs' counters, summed in shared memory
+      // the pairs' counters, summed in shared memory: acc_r is phase A for
+      // an origin whose split this pair never reached, else phase B
 #pragma unroll
       for (int o = 0; o < 2; ++o) {
         if (!real[o]) continue;
         const int slot = tp + 64 * o;
 #pragma unroll
-        for (int S = 0; S < NS; ++S) {
-          if (a[o][S]) atomicAdd(&acc[(slot * 2 + 0) * NS + S], a[o][S]);
-          if (b[o][S]) atomicAdd(&acc[(slot * 2 + 1) * NS + S], b[o][S]);
-        }
+        for (int S = 0; S < NS; ++S)
+          if (acc_r[o][S]) atomicAdd(&acc[(slot * 2 + (crossed[o] ? 1 : 0)) * NS + S], acc_r[o][S]);
       }
       __syncthreads();
       const bool abort = s_abort != 0u;
@@ -427,14 +443,27 @@ k_fused(const uint32_t* __restrict__ rankL, const uint2* __restrict__ tab, const
   }
 }
 
+// Kernel shapes of the fused count (plan.fused): warp pairs per CTA,
+// resident CTAs per SM the registers are budgeted for, group-loop unroll.
+//   1: 4 pairs, 2 CTAs/SM (128 registers), no unroll
+//   2: 4 pairs, 1 CTA/SM (up to 255 registers), 16 groups unrolled
+//   3: 2 pairs, 3 CTAs/SM (up to 170 registers), 4 groups unrolled
+template <int DS>
+size_t fused_smem(int variant, int W) {
+  return variant == 3 ? FusedSmem<DS, 2>::total(W) : FusedSmem<DS, 4>::total(W);
+}
+
+size_t fused_smem_ds(int ds, int variant, int W) {
+  return ds == 1 ? fused_smem<1>(variant, W) : ds == 2 ? fused_smem<2>(variant, W) : fused_smem<3>(variant, W);
+}
+
 }  // namespace
 
-bool ddks_fused_supported(int ds, int64_t N) {
-  if (ds < 1 || ds > 3 || N < 2 || N > (1 << 24)) return false;
+bool ddks_fused_supported(int ds, int64_t N, int variant) {
+  if (ds < 1 || ds > 3 || N < 2 || N > (1 << 24) || variant < 1 || variant > 3) return false;
   const int W = (int)((N + 31) / 32);
-  const size_t smem = ds == 1 ? FusedSmem<1>::total(W) : ds == 2 ? FusedSmem<2>::total(W) : FusedSmem<3>::total(W);
   const size_t prep = (size_t)ds * W * 5;
-  return smem <= 220u * 1024u && prep <= 220u * 1024u;
+  return fused_smem_ds(ds, variant, W) <= 220u * 1024u && prep <= 220u * 1024u;
 }
 
 size_t ddks_fused_scratch_bytes(int ds, int64_t N, int64_t blocks) {
@@ -442,12 +471,12 @@ size_t ddks_fused_scratch_bytes(int ds, int64_t N, int64_t blocks) {
   return (size_t)blocks * tab_stride(ds, W) * 8 + (size_t)blocks * ds * kOC + 16;
 }
 
-cudaError_t ddks_fused_count(ddks_ctx* ctx, int ds, const uint32_t* rankL, const uint32_t* orank, const void* meta,
-                             int64_t no, int64_t N, int64_t NP, int64_t NT, int64_t NPpad, int64_t Lrow,
-                             uint32_t* gcnt, unsigned* done, unsigned long long* packed, uint64_t* best,
+cudaError_t ddks_fused_count(ddks_ctx* ctx, int ds, int variant, const uint32_t* rankL, const uint32_t* orank,
+                             const void* meta, int64_t no, int64_t N, int64_t NP, int64_t NT, int64_t NPpad,
+                             int64_t Lrow, uint32_t* gcnt, unsigned* done, unsigned long long* packed, uint64_t* best,
                              int32_t* bestj, int64_t ob, unsigned long long* out3, unsigned* flags,
                              void* scratch, cudaStream_t st, int* launches) {
-  if (!ddks_fused_supported(ds, N)) return cudaErrorInvalidValue;
+  if (!ddks_fused_supported(ds, N, variant)) return cudaErrorInvalidValue;
   const int W = (int)((N + 31) / 32);
   const int64_t blocks = (no + kOB - 1) / kOB;
   uint2* tab = reinterpret_cast<uint2*>(scratch);
@@ -455,9 +484,10 @@ cudaError_t ddks_fused_count(ddks_ctx* ctx, int ds, const uint32_t* rankL, const
   const int GP = (int)((NP + 31) / 32), GT = (int)((NT + 31) / 32);
   const int64_t units = blocks * (GP + GT);
   const size_t prep_smem = (size_t)ds * W * 5;
+  const size_t smem = fused_smem_ds(ds, variant, W);
   Final fin{out3, done, packed, best, bestj, ob, (int)blocks};
   const OriginMeta* mt = reinterpret_cast<const OriginMeta*>(meta);
-  auto go = [&](auto prep, auto kern, size_t smem) -> cudaError_t {
+  auto go = [&](auto prep, auto kern, int threads) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prep_smem);
     if (e != cudaSuccess) return e;
     prep<<<(unsigned)blocks, kPrepThreads, prep_smem, st>>>(orank, no, W, tab, oval);
@@ -465,7 +495,7 @@ cudaError_t ddks_fused_count(ddks_ctx* ctx, int ds, const uint32_t* rankL, const
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kFThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     // persistent: one wave of resident CTAs, each with at least a few batches
@@ -473,12 +503,17 @@ cudaError_t ddks_fused_count(ddks_ctx* ctx, int ds, const uint32_t* rankL, const
     const int64_t min_units = 4 * kBG;
     if (grid * min_units > units) grid = (units + min_units - 1) / min_units;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, kFThreads, smem, st>>>(rankL, tab, oval, mt, no, NP, NT, NPpad, Lrow, W, GP, GT, units,
-                                                  gcnt, flags, fin, ctx->dev_wait_ns);
+    kern<<<(unsigned)grid, threads, smem, st>>>(rankL, tab, oval, mt, no, NP, NT, NPpad, Lrow, W, GP, GT, units, gcnt,
+                                               flags, fin, ctx->dev_wait_ns);
     *launches += 2;
     return cudaGetLastError();
   };
-  if (ds == 1) return go(k_fused_tables<1>, k_fused<1>, FusedSmem<1>::total(W));
-  if (ds == 2) return go(k_fused_tables<2>, k_fused<2>, FusedSmem<2>::total(W));
-  return go(k_fused_tables<3>, k_fused<3>, FusedSmem<3>::total(W));
+  auto pick = [&](auto prep, auto k1, auto k2, auto k3) -> cudaError_t {
+    return variant == 1 ? go(prep, k1, 256) : variant == 2 ? go(prep, k2, 256) : go(prep, k3, 128);
+  };
+  if (ds == 1)
+    return pick(k_fused_tables<1>, k_fused<1, 4, 2, 1>, k_fused<1, 4, 1, 16>, k_fused<1, 2, 3, 4>);
+  if (ds == 2)
+    return pick(k_fused_tables<2>, k_fused<2, 4, 2, 1>, k_fused<2, 4, 1, 16>, k_fused<2, 2, 3, 4>);
+  return pick(k_fused_tables<3>, k_fused<3, 4, 2, 1>, k_fused<3, 4, 1, 16>, k_fused<3, 2, 3, 4>);
 }

@@ -485,7 +485,7 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   int rc = ctx->reg_meta.reserve(ctx, n_u32 * 4 + (size_t)no * sizeof(OriginMeta) + 64);
   if (rc) return cudaErrorMemoryAllocation;
   // group records [blocks][ngroups][ds][8] u32 and origin values [blocks][ds][128] u8
-  const bool fused = plan.fused && ddks_fused_supported(ds, N);
+  const bool fused = plan.fused && ddks_fused_supported(ds, N, plan.fused);
   const size_t rec_words = fused ? 0 : (size_t)blocks * ngroups * ds * 8;
   rc = ctx->reg_words.reserve(ctx, fused ? ddks_fused_scratch_bytes(ds, N, blocks)
                                          : rec_words * 4 + (size_t)blocks * ds * kOC);
@@ -532,7 +532,7 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   if (fused) {
     e = cudaMemsetAsync(gcnt, 0, ((size_t)no * kCnt + n_fin) * 4, st);
     if (e == cudaSuccess)
-      e = ddks_fused_count(ctx, ds, rankL, orank, meta, no, N, NP, NT, NPpad, Lrow, gcnt, done, packed, best, bestj,
+      e = ddks_fused_count(ctx, ds, plan.fused, rankL, orank, meta, no, N, NP, NT, NPpad, Lrow, gcnt, done, packed, best, bestj,
                            ob, out3, flags, ctx->reg_words.ptr, st, &n);
     if (e != cudaSuccess) return e;
     if (reduced) *reduced = out3 != nullptr;

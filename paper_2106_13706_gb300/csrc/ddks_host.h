@@ -30,7 +30,8 @@ struct ddks_plan {
   int threads = 256;  // lane path: threads per CTA (one origin each)
   int warps = 8;      // warp path: warps per CTA (one origin each)
   int reg_occ = 4;    // register path occupancy class: 4, 6, 8 (8, 12, 16 resident 64-thread CTAs per SM)
-  int fused = 1;      // register path: 1 = bit planes built in shared memory (count_fused.cu), 0 = pack kernel
+  int fused = 0;      // register path: 0 = bit planes staged by the pack kernel, 1..3 = built in shared
+                      // memory by the count kernel (count_fused.cu, kernel shapes listed there)
 };
 
 struct ServeState;  // serve.cu
@@ -129,11 +130,11 @@ bool ddks_register_supported(int d, int64_t NP, int64_t NT);
 
 // count_fused.cu: the register path's count with the bit planes built in
 // shared memory; the caller has zeroed gcnt, done and packed
-bool ddks_fused_supported(int ds, int64_t N);
+bool ddks_fused_supported(int ds, int64_t N, int variant);
 size_t ddks_fused_scratch_bytes(int ds, int64_t N, int64_t blocks);
-cudaError_t ddks_fused_count(ddks_ctx* ctx, int ds, const uint32_t* rankL, const uint32_t* orank, const void* meta,
-                             int64_t no, int64_t N, int64_t NP, int64_t NT, int64_t NPpad, int64_t Lrow,
-                             uint32_t* gcnt, unsigned* done, unsigned long long* packed, uint64_t* best,
+cudaError_t ddks_fused_count(ddks_ctx* ctx, int ds, int variant, const uint32_t* rankL, const uint32_t* orank,
+                             const void* meta, int64_t no, int64_t N, int64_t NP, int64_t NT, int64_t NPpad,
+                             int64_t Lrow, uint32_t* gcnt, unsigned* done, unsigned long long* packed, uint64_t* best,
                              int32_t* bestj, int64_t ob, unsigned long long* out3, unsigned* flags,
                              void* scratch, cudaStream_t st, int* launches);
 

@@ -81,7 +81,10 @@ int ddks_select_path(ddks_ctx* ctx, int64_t NP, int64_t NT, int32_t d, ddks_plan
     const int forced = ctx->cfg.path;
     p.path = forced;
     if (forced == DDKS_PATH_LANE) p.threads = d <= 4 ? 256 : (d <= 6 ? 128 : 64);
-    if (forced == DDKS_PATH_REGISTER) p.fused = ctx->cfg.register_variant == 1 ? 0 : 1;
+    if (forced == DDKS_PATH_REGISTER) {
+      const int rv = ctx->cfg.register_variant;
+      p.fused = rv >= 2 ? rv - 1 : 0;
+    }
     if (!plan_ok(p, NP, NT, d)) return DDKS_EUNSUPPORTED;
     *plan = p;
     return DDKS_OK;
@@ -136,7 +139,9 @@ int ddks_autotune(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64
   if ((rc = ctx->bestj.reserve(ctx, 4 * (size_t)N))) return rc;
   if ((rc = ctx->out3.reserve(ctx, 64 + ddks_reduce_scratch_bytes()))) return rc;
   std::vector<ddks_plan> cands;
-  { ddks_plan p; p.path = DDKS_PATH_REGISTER; p.fused = 1; cands.push_back(p); }
+  for (int v : {1, 2, 3}) {
+    ddks_plan p; p.path = DDKS_PATH_REGISTER; p.fused = v; cands.push_back(p);
+  }
   for (int occ : {4, 6, 8}) {
     ddks_plan p; p.path = DDKS_PATH_REGISTER; p.reg_occ = occ; p.fused = 0; cands.push_back(p);
   }

@@ -13,7 +13,7 @@ from paper_2106_13706_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [0, 1]  # 0: planes built by the count kernel, 1: staged by the pack kernel
+VARIANTS = [1, 2, 3, 4]  # 1: staged by the pack kernel; 2..4: built by the count kernel (three kernel shapes)
 
 
 @pytest.fixture(scope="module")
