@@ -42,7 +42,7 @@ class ddks_config(ctypes.Structure):
                 ("hbm_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_int32),
                 ("wait_limit_ms", ctypes.c_int32), ("tune_cache", ctypes.c_char_p),
                 ("graphs", ctypes.c_int32), ("radix_min_n", ctypes.c_int64),
-                ("register_variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("register_variant", ctypes.c_int32), ("rank_kernel", ctypes.c_int32)]
 
 
 class ddks_result(ctypes.Structure):
@@ -188,7 +188,7 @@ def _pair(P, T):
 
 # ------------------------------------------------------------------ entry points
 def ddks_ctx_create(device=-1, path=PATH_AUTO, hbm_budget_bytes=0, max_batch=0, wait_limit_ms=0,
-                    tune_cache=None, graphs=True, radix_min_n=0, register_variant=0):
+                    tune_cache=None, graphs=True, radix_min_n=0, register_variant=0, rank_kernel=0):
     lib = load()
     cfg = ddks_config()
     lib.ddks_config_default(ctypes.byref(cfg))
@@ -198,6 +198,7 @@ def ddks_ctx_create(device=-1, path=PATH_AUTO, hbm_budget_bytes=0, max_batch=0, 
     cfg.graphs = 1 if graphs else 0
     cfg.radix_min_n = radix_min_n
     cfg.register_variant = register_variant
+    cfg.rank_kernel = rank_kernel
     h = ctypes.c_void_p()
     _check(lib.ddks_ctx_create(ctypes.byref(cfg), ctypes.byref(h)), what="ddks_ctx_create")
     return h

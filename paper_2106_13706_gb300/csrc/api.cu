@@ -118,6 +118,7 @@ int ddks_ctx_create(const ddks_config* cfg, ddks_ctx** out) {
   if (cfg) ctx->cfg = *cfg; else ddks_config_default(&ctx->cfg);
   if (ctx->cfg.path < DDKS_PATH_AUTO || ctx->cfg.path > DDKS_PATH_DOMINANCE) { delete ctx; return DDKS_EINVAL; }
   if (ctx->cfg.register_variant < 0 || ctx->cfg.register_variant > 4) { delete ctx; return DDKS_EINVAL; }
+  if (ctx->cfg.rank_kernel < 0 || ctx->cfg.rank_kernel > 1) { delete ctx; return DDKS_EINVAL; }
   if (ctx->cfg.hbm_budget_bytes == 0) ctx->cfg.hbm_budget_bytes = 8ull << 30;
   if (ctx->cfg.max_batch <= 0) ctx->cfg.max_batch = 64;
   if (ctx->cfg.wait_limit_ms > 0)
@@ -245,6 +246,24 @@ int ddks_encode_problem(ddks_ctx* ctx, const void* dP, int64_t NP, const void* d
   const int64_t N = NP + NT;
   const size_t npad = ddks_rank_scratch_elems(N);
   int rc;
+  if (ctx->cfg.rank_kernel == 0 && ddks_rank_cluster_supported(N, dtype == DDKS_F64 ? 64 : 32)) {
+    // one launch: keys, ranks, every dimension's order, dimension 0's P prefix
+    if ((rc = ctx->rank.reserve(ctx, 4 * (size_t)N * d))) return rc;
+    if ((rc = ctx->sidx0.reserve(ctx, 4 * (size_t)N))) return rc;
+    if ((rc = ctx->pfx0.reserve(ctx, 4 * (size_t)N))) return rc;
+    if ((rc = ctx->ti1.reserve(ctx, 4 * (size_t)N * d))) return rc;
+    if ((rc = ctx->flags.reserve(ctx, 64))) return rc;
+    cudaError_t e = cudaMemsetAsync(ctx->flags.ptr, 0, 4, st);
+    if (e == cudaSuccess)
+      e = ddks_launch_rank_cluster(dP, dT, NP, NT, d, dtype == DDKS_F64, (uint32_t*)ctx->rank.ptr,
+                                   (uint32_t*)ctx->ti1.ptr, (uint32_t*)ctx->sidx0.ptr, (uint32_t*)ctx->pfx0.ptr,
+                                   (unsigned*)ctx->flags.ptr, st);
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "rank (cluster)");
+    ctx->launches += 1;
+    ctx->pfx0_valid = true;
+    ctx->sorted_rows = (const uint32_t*)ctx->ti1.ptr;
+    return DDKS_OK;
+  }
   if ((rc = ctx->keys.reserve(ctx, 8 * (size_t)N * d))) return rc;
   if ((rc = ctx->tk1.reserve(ctx, 8 * npad * d))) return rc;
   if ((rc = ctx->tk2.reserve(ctx, 8 * npad * d))) return rc;
@@ -386,6 +405,10 @@ static int distance_impl(ddks_ctx* ctx, const void* P, int64_t NP, const void* T
   const unsigned flags = (unsigned)(ctx->h_out[4] & 0xFFFFFFFFull);
   if (flags & ddks::kFlagNaN) return out->status = DDKS_ENAN;
   if (flags & ddks::kFlagTimeout) return out->status = DDKS_ETIMEOUT;
+  if (flags & ddks::kFlagBounds) {
+    ctx->last_err = "a kernel's bounds check failed";
+    return out->status = DDKS_ECUDA;
+  }
   out->num_max = ctx->h_out[0];
   out->denom = (uint64_t)NP * (uint64_t)NT;
   out->D = (double)out->num_max / (double)out->denom;

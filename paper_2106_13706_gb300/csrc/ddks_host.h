@@ -128,6 +128,14 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
                                  unsigned long long* out3 = nullptr, bool* reduced = nullptr);
 bool ddks_register_supported(int d, int64_t NP, int64_t NT);
 
+// rank_cluster.cu: K0 (order keys, min-ranks, dimension-0 order and P
+// prefix, every dimension's sorted order) in one launch of d thread-block
+// clusters, for samples whose rows fit a cluster's shared memory
+bool ddks_rank_cluster_supported(int64_t N, int key_bits);
+cudaError_t ddks_launch_rank_cluster(const void* P, const void* T, int64_t NP, int64_t NT, int d, bool f64,
+                                     uint32_t* rank, uint32_t* sorted, uint32_t* sidx0, uint32_t* pfx0,
+                                     unsigned* flags, cudaStream_t st);
+
 // count_fused.cu: the register path's count with the bit planes built in
 // shared memory; the caller has zeroed gcnt, done and packed
 bool ddks_fused_supported(int ds, int64_t N, int variant);

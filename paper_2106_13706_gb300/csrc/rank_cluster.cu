@@ -1,0 +1,295 @@
+// rank_cluster.cu -- K0 in one launch for pooled samples of up to ~88k
+// (float) or ~60k (double) points: order keys, per-dimension min-ranks, the
+// dimension-0 order and its P prefix.
+//
+// x_m >= o_m <=> rank_m(x) >= rank_m(o) with rank = the number of pooled
+// values strictly below (Eq. g only ever compares coordinates with ">="), so
+// the count kernels work on ranks.  Here one thread-block cluster of kC CTAs
+// ranks one dimension: CTA c holds positions [c*S, (c+1)*S) of the row in
+// shared memory, and a stable LSD radix sort with 8-bit digits runs entirely
+// in the cluster's distributed shared memory -- per pass each CTA ranks its
+// elements stably by digit (per-warp digit counters, lanes with equal digits
+// found by ballots), the cluster's digit counts are read across CTAs to give
+// every (digit, CTA) its first output position, and each element is stored
+// into the shared memory of the CTA that owns its new position.  A pass whose
+// digit is the same for every key is skipped.  After the last pass the
+// positions hold the keys in sorted order with ties in pooled-index order;
+// the min-rank of a position is its run's first position (a running maximum
+// of run heads within the CTA, carried across CTAs), and dimension 0 also
+// gets the count of P points (pooled index < NP) before each position.
+//
+// Replaces the encode kernel, the global radix passes and the rank kernels
+// (about a dozen latency-bound launches) by one launch of d clusters.
+#include <cooperative_groups.h>
+
+#include "ddks_host.h"
+#include "ddks_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int kC = 8;            // CTAs per cluster (portable maximum)
+constexpr int kKT = 512;         // threads per CTA
+constexpr int kKW = kKT / 32;    // warps per CTA
+constexpr size_t kSmemCap = 220u * 1024u;
+
+template <typename V> struct KeyOf;
+template <> struct KeyOf<float> { using K = uint32_t; static constexpr int kPasses = 4; };
+template <> struct KeyOf<double> { using K = uint64_t; static constexpr int kPasses = 8; };
+
+// shared memory of one CTA for a segment of S positions
+template <typename K>
+__host__ __device__ constexpr size_t cluster_smem(int64_t S) {
+  return (size_t)S * sizeof(K) * 2     // keys, two buffers
+         + (size_t)S * 4 * 2           // pooled indices, two buffers
+         + (size_t)S * 2               // rank of each element among its warp's equal digits
+         + (size_t)kKW * 256 * 4       // per-warp digit counters
+         + 16;
+}
+
+// lanes of the (fully active) warp whose 8-bit digit equals this lane's
+DDKS_DEV uint32_t same_digit(uint32_t dg) {
+  const uint32_t vary = __reduce_or_sync(0xffffffffu, dg) ^ __reduce_and_sync(0xffffffffu, dg);
+  uint32_t m = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    if ((vary >> b) & 1u) {
+      const bool bit = (dg >> b) & 1u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      m &= bit ? bal : ~bal;
+    }
+  }
+  return m;
+}
+
+// exclusive prefix over the CTA's threads (kKT of them) of one value each
+DDKS_DEV uint32_t cta_exscan(uint32_t v, uint32_t* ws) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += x;
+  }
+  if (lane == 31) ws[warp] = incl;
+  __syncthreads();
+  uint32_t carry = 0;
+  for (int q = 0; q < warp; ++q) carry += ws[q];
+  __syncthreads();
+  return carry + incl - v;
+}
+
+// Grid: d clusters of kC CTAs; cluster m ranks dimension m, CTA c of it holds
+// positions [c*S, c*S + S).  Outputs: rank[m*N + i] = min-rank of point i;
+// sorted[m*N + p] = pooled index at sorted position p; dimension 0 also
+// sidx0[p] = sorted[p] and pfx0[p] = P points before position p.
+template <typename V>
+__global__ void __launch_bounds__(kKT, 1)
+k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64_t NT, int d, int S,
+               uint32_t* __restrict__ rank, uint32_t* __restrict__ sorted, uint32_t* __restrict__ sidx0,
+               uint32_t* __restrict__ pfx0, unsigned* __restrict__ flags) {
+  using K = typename KeyOf<V>::K;
+  constexpr int kPasses = KeyOf<V>::kPasses;
+  cg::cluster_group cl = cg::this_cluster();
+  const int c = (int)cl.block_rank();
+  const int m = (int)(blockIdx.x / kC);
+  const int64_t N = NP + NT;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  extern __shared__ __align__(16) unsigned char kraw[];
+  K* keyA = reinterpret_cast<K*>(kraw);
+  K* keyB = keyA + S;
+  uint32_t* idxA = reinterpret_cast<uint32_t*>(keyB + S);
+  uint32_t* idxB = idxA + S;
+  uint16_t* rloc = reinterpret_cast<uint16_t*>(idxB + S);
+  uint32_t* wcnt = reinterpret_cast<uint32_t*>(rloc + S + (S & 1));  // [kKW][256]
+  __shared__ uint32_t hist[256], doff[256], ws[kKW], whead[kKW], wpc[kKW];
+  __shared__ uint32_t s_info[2];  // read by the other CTAs: last run head in the segment, its P points
+  __shared__ unsigned long long s_left;
+  __shared__ int s_skip;
+  const int64_t seg0 = (int64_t)c * S;
+  const int cnt = N - seg0 >= S ? S : (N > seg0 ? (int)(N - seg0) : 0);  // positions held
+  const int E = (S + kKT - 1) / kKT;  // warp w holds positions [w*32*E, (w+1)*32*E)
+
+  // order keys in pooled order (position = pooled index)
+  unsigned nan = 0;
+  for (int q = tid; q < cnt; q += kKT) {
+    const int64_t i = seg0 + q;
+    const V v = i < NP ? P[i * d + m] : T[(i - NP) * d + m];
+    nan |= v != v ? 1u : 0u;
+    keyA[q] = (K)ddks::order_key(v);
+    idxA[q] = (uint32_t)i;
+  }
+  if (__syncthreads_or(nan) && tid == 0) atomicOr(flags, ddks::kFlagNaN);
+
+  for (int pass = 0; pass < kPasses; ++pass) {
+    const int shift = 8 * pass;
+    // each warp ranks its positions stably by digit: rloc = rank among the
+    // warp's earlier elements of the same digit, wcnt = the warp's counts
+    for (int i = tid; i < kKW * 256; i += kKT) wcnt[i] = 0u;
+    __syncthreads();
+    for (int j = 0; j < E; ++j) {
+      const int q = w * 32 * E + j * 32 + lane;
+      const bool v = q < cnt;
+      const uint32_t vm = __ballot_sync(0xffffffffu, v);
+      if (vm == 0u) break;  // warp-uniform: positions only grow with j
+      const uint32_t dg = v ? (uint32_t)(keyA[q] >> shift) & 255u : 0u;
+      const uint32_t peers = same_digit(dg) & vm;
+      if (v) rloc[q] = (uint16_t)(wcnt[w * 256 + dg] + (uint32_t)__popc(peers & ((1u << lane) - 1u)));
+      __syncwarp();
+      if (v && (peers >> lane) == 1u) wcnt[w * 256 + dg] += (uint32_t)__popc(peers);  // the group's last lane
+      __syncwarp();
+    }
+    __syncthreads();
+    // thread t < 256 owns digit t: the warps' offsets within the digit, and
+    // the CTA's count of the digit
+    if (tid < 256) {
+      uint32_t s = 0;
+      for (int q = 0; q < kKW; ++q) {
+        const uint32_t x = wcnt[q * 256 + tid];
+        wcnt[q * 256 + tid] = s;
+        s += x;
+      }
+      hist[tid] = s;
+    }
+    if (tid == 0) s_skip = 0;
+    cl.sync();  // every CTA's counts are complete
+    uint32_t tot = 0, before = 0;
+    if (tid < 256) {
+      for (int r = 0; r < kC; ++r) {
+        const uint32_t h = cl.map_shared_rank(hist, (unsigned)r)[tid];
+        tot += h;
+        before += r < c ? h : 0u;
+      }
+    }
+    const uint32_t dbase = cta_exscan(tid < 256 ? tot : 0u, ws);
+    if (tid < 256) {
+      doff[tid] = dbase + before;  // first position of this CTA's elements with digit tid
+      if (tot == (uint32_t)N) s_skip = 1;  // every key has this digit: the pass keeps the order
+    }
+    __syncthreads();
+    const bool skip = s_skip != 0;
+    if (!skip) {
+      for (int j = 0; j < E; ++j) {
+        const int q = w * 32 * E + j * 32 + lane;
+        if (q >= cnt) break;
+        const K k = keyA[q];
+        const uint32_t dg = (uint32_t)(k >> shift) & 255u;
+        const uint32_t pos = doff[dg] + wcnt[w * 256 + dg] + rloc[q];
+        if (pos >= (uint64_t)N) {  // cannot happen when the counts are right; never store out of range
+          atomicOr(flags, ddks::kFlagBounds);
+          continue;
+        }
+        const uint32_t dst = pos / (uint32_t)S;
+        const uint32_t li = pos - dst * (uint32_t)S;
+        cl.map_shared_rank(keyB, dst)[li] = k;
+        cl.map_shared_rank(idxB, dst)[li] = idxA[q];
+      }
+    }
+    cl.sync();  // new positions complete everywhere; the counts may be reused
+    if (!skip) {
+      K* tk = keyA; keyA = keyB; keyB = tk;
+      uint32_t* ti = idxA; idxA = idxB; idxB = ti;
+    }
+  }
+
+  // run heads and P points, per warp chunk, then carried across the cluster
+  if (tid == 0) s_left = (c > 0 && cnt > 0) ? (unsigned long long)cl.map_shared_rank(keyA, (unsigned)(c - 1))[S - 1] : 0ull;
+  __syncthreads();
+  auto head_at = [&](int q) -> bool {
+    if (q >= cnt) return false;
+    if (seg0 + q == 0) return true;
+    const K left = q > 0 ? keyA[q - 1] : (K)s_left;
+    return keyA[q] != left;
+  };
+  {
+    uint32_t lh = 0, pc = 0;
+    for (int j = 0; j < E; ++j) {
+      const int q = w * 32 * E + j * 32 + lane;
+      const uint32_t hm = __ballot_sync(0xffffffffu, head_at(q));
+      if (hm) lh = (uint32_t)(seg0 + w * 32 * E + j * 32) + 31u - (uint32_t)__clz(hm);
+      pc += (uint32_t)__popc(__ballot_sync(0xffffffffu, q < cnt && idxA[q] < (uint64_t)NP));
+    }
+    if (lane == 0) { whead[w] = lh; wpc[w] = pc; }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t lh = 0, pc = 0;
+    for (int q = 0; q < kKW; ++q) { lh = whead[q] > lh ? whead[q] : lh; pc += wpc[q]; }
+    s_info[0] = lh;
+    s_info[1] = pc;
+  }
+  cl.sync();  // every CTA's summary is complete
+  uint32_t carry = 0, pbefore = 0;
+  for (int r = 0; r < c; ++r) {
+    const uint32_t* o = cl.map_shared_rank(s_info, (unsigned)r);
+    carry = o[0] > carry ? o[0] : carry;
+    pbefore += o[1];
+  }
+  for (int q = 0; q < w; ++q) {
+    carry = whead[q] > carry ? whead[q] : carry;
+    pbefore += wpc[q];
+  }
+  uint32_t* rk = rank + (int64_t)m * N;
+  uint32_t* so = sorted ? sorted + (int64_t)m * N : nullptr;
+  for (int j = 0; j < E; ++j) {
+    const int q = w * 32 * E + j * 32 + lane;
+    const uint32_t g0 = (uint32_t)(seg0 + w * 32 * E + j * 32);
+    const bool v = q < cnt;
+    const uint32_t hm = __ballot_sync(0xffffffffu, head_at(q));
+    const uint32_t upto = hm & (0xffffffffu >> (31 - lane));  // heads at lanes <= this one
+    const uint32_t run = upto ? g0 + 31u - (uint32_t)__clz(upto) : carry;
+    const uint32_t idx = v ? idxA[q] : 0u;
+    const bool isP = v && idx < (uint64_t)NP;
+    const uint32_t pm = __ballot_sync(0xffffffffu, isP);
+    if (v) {
+      rk[idx] = run;
+      if (so) so[g0 + lane] = idx;
+      if (m == 0) {
+        sidx0[g0 + lane] = idx;
+        pfx0[g0 + lane] = pbefore + (uint32_t)__popc(pm & ((1u << lane) - 1u));
+      }
+    }
+    if (hm) carry = g0 + 31u - (uint32_t)__clz(hm);
+    pbefore += (uint32_t)__popc(pm);
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+}  // namespace
+
+bool ddks_rank_cluster_supported(int64_t N, int key_bits) {
+  if (N < 1 || N >= ((int64_t)1 << 31)) return false;
+  const int64_t S = (N + kC - 1) / kC;
+  const size_t smem = key_bits == 64 ? cluster_smem<uint64_t>(S) : cluster_smem<uint32_t>(S);
+  return smem <= kSmemCap;
+}
+
+cudaError_t ddks_launch_rank_cluster(const void* P, const void* T, int64_t NP, int64_t NT, int d, bool f64,
+                                     uint32_t* rank, uint32_t* sorted, uint32_t* sidx0, uint32_t* pfx0,
+                                     unsigned* flags, cudaStream_t st) {
+  const int64_t N = NP + NT;
+  if (!ddks_rank_cluster_supported(N, f64 ? 64 : 32) || d < 1 || !rank || !sidx0 || !pfx0)
+    return cudaErrorInvalidValue;
+  const int S = (int)((N + kC - 1) / kC);
+  auto go = [&](auto kern, size_t smem, auto* p, auto* t) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(kC * d), 1, 1);
+    cfg.blockDim = dim3(kKT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kC;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p, t, NP, NT, d, S, rank, sorted, sidx0, pfx0, flags);
+  };
+  if (f64)
+    return go(k_rank_cluster<double>, cluster_smem<uint64_t>(S), (const double*)P, (const double*)T);
+  return go(k_rank_cluster<float>, cluster_smem<uint32_t>(S), (const float*)P, (const float*)T);
+}

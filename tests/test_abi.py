@@ -59,7 +59,7 @@ def test_config_defaults(lib):
     assert cfg.radix_min_n == 0 and cfg.graphs == 1 and cfg.device == -1 and cfg.register_variant == 0
     # the binding's struct matches the header's field order and size
     names = [n for n, _ in pkg.binding.ddks_config._fields_]
-    assert names[-3:] == ["radix_min_n", "register_variant", "reserved"]
+    assert names[-3:] == ["radix_min_n", "register_variant", "rank_kernel"]
     assert names.index("graphs") == len(names) - 4
     assert ctypes.sizeof(pkg.binding.ddks_config) == 56
 

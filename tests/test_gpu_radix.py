@@ -44,7 +44,7 @@ def test_distance_with_radix_ranks(torch, d, n_p, n_t, kind, path, dtype):
     P, T = wl.random_pair(31 * d + n_p, n_p, n_t, d, kind=kind, dtype=dtype)
     N = n_p + n_t
     ref = orc.ddks(P, T, origins=(0, N), per_origin=True)
-    with pkg.Context(device=0, path=path, radix_min_n=1) as c:
+    with pkg.Context(device=0, path=path, radix_min_n=1, rank_kernel=1) as c:
         got = c.distance_range(_dev(torch, P), _dev(torch, T), 0, N, per_origin=True)
     assert (got["num_max"], got["denom"]) == (ref["num_max"], ref["denom"])
     assert (got["argmax_origin"], got["argmax_orthant"]) == (ref["argmax_origin"], ref["argmax_orthant"])
@@ -59,7 +59,7 @@ def test_radix_and_merge_agree_d2_large(torch, kind, dtype):
     N = P.shape[0] + T.shape[0]
     res = []
     for m in (1, -1):
-        with pkg.Context(device=0, path=pkg.PATH_DOMINANCE, radix_min_n=m) as c:
+        with pkg.Context(device=0, path=pkg.PATH_DOMINANCE, radix_min_n=m, rank_kernel=1) as c:
             res.append(c.distance_range(Pd, Td, 0, N, per_origin=True))
     a, b = res
     assert (a["num_max"], a["argmax_origin"], a["argmax_orthant"]) == (b["num_max"], b["argmax_origin"],
@@ -79,7 +79,7 @@ def test_radix_and_merge_agree_d2_large(torch, kind, dtype):
 def test_rdks_with_radix_sort(torch, d, n_p, n_t, kind, dtype):
     P, T = wl.random_pair(400 + d, n_p, n_t, d, kind=kind, dtype=dtype)
     ref = orc.rdks(P, T)
-    with pkg.Context(device=0, radix_min_n=1) as c:
+    with pkg.Context(device=0, radix_min_n=1, rank_kernel=1) as c:
         got = c.rdks(_dev(torch, P), _dev(torch, T))
     assert (got["num_max"], got["denom"]) == (ref["num_max"], ref["denom"])
     assert np.array_equal(got["per_corner"], ref["per_corner"])
@@ -94,7 +94,7 @@ def test_rdks_radix_and_merge_agree_large(torch, n_p, n_t):
     Pd, Td = _dev(torch, P), _dev(torch, T)
     res = []
     for m in (1, -1):
-        with pkg.Context(device=0, radix_min_n=m) as c:
+        with pkg.Context(device=0, radix_min_n=m, rank_kernel=1) as c:
             res.append(c.rdks(Pd, Td))
     assert res[0]["num_max"] == res[1]["num_max"]
     assert np.array_equal(res[0]["per_corner"], res[1]["per_corner"])
@@ -104,7 +104,7 @@ def test_dominance_partial_ranges_with_radix(torch):
     # the whole range runs the queries in dimension-1 order; partial ranges in origin order
     P, T = wl.random_pair(13, 3000, 2600, 2, kind="int")
     N = 5600
-    with pkg.Context(device=0, path=pkg.PATH_DOMINANCE, radix_min_n=1) as c:
+    with pkg.Context(device=0, path=pkg.PATH_DOMINANCE, radix_min_n=1, rank_kernel=1) as c:
         for a, b in [(0, N), (0, 1), (2999, 3001), (4000, N), (1, N)]:
             got = c.distance_range(_dev(torch, P), _dev(torch, T), a, b, per_origin=True)
             ref = orc.ddks(P, T, origins=(a, b), per_origin=True)
@@ -122,7 +122,7 @@ def test_radix_special_values(torch, dtype):
     N = 5500
     ref = orc.ddks(P, T, origins=(0, N), per_origin=True)
     for path in (pkg.PATH_DOMINANCE, pkg.PATH_AUTO):
-        with pkg.Context(device=0, path=path, radix_min_n=1) as c:
+        with pkg.Context(device=0, path=path, radix_min_n=1, rank_kernel=1) as c:
             got = c.distance_range(_dev(torch, P), _dev(torch, T), 0, N, per_origin=True)
             assert (got["num_max"], got["argmax_origin"], got["argmax_orthant"]) == (
                 ref["num_max"], ref["argmax_origin"], ref["argmax_orthant"])
