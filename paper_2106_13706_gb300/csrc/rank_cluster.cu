@@ -4,7 +4,8 @@
 //
 // x_m >= o_m <=> rank_m(x) >= rank_m(o) with rank = the number of pooled
 // values strictly below (Eq. g only ever compares coordinates with ">="), so
-// the count kernels work on ranks.  Here one thread-block cluster of kC CTAs
+// the count kernels work on ranks.  Here one thread-block cluster of 16 CTAs
+// (8 where the GPU does not schedule clusters of 16)
 // ranks one dimension: CTA c holds positions [c*S, (c+1)*S) of the row in
 // shared memory, and a stable LSD radix sort with 8-bit digits runs entirely
 // in the cluster's distributed shared memory -- per pass each CTA ranks its
@@ -22,6 +23,8 @@
 // (about a dozen latency-bound launches) by one launch of d clusters.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "ddks_host.h"
 #include "ddks_internal.cuh"
 
@@ -29,8 +32,9 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int kC = 8;            // CTAs per cluster (portable maximum)
+constexpr int kCMax = 16;        // CTAs per cluster: 16 where the GPU allows it, else 8
 constexpr int kKT = 512;         // threads per CTA
+static_assert(kKT == 512, "the digit-count prefix splits the warps into two halves of 256 threads");
 constexpr int kKW = kKT / 32;    // warps per CTA
 constexpr size_t kSmemCap = 220u * 1024u;
 
@@ -48,21 +52,6 @@ __host__ __device__ constexpr size_t cluster_smem(int64_t S) {
          + 16;
 }
 
-// lanes of the (fully active) warp whose 8-bit digit equals this lane's
-DDKS_DEV uint32_t same_digit(uint32_t dg) {
-  const uint32_t vary = __reduce_or_sync(0xffffffffu, dg) ^ __reduce_and_sync(0xffffffffu, dg);
-  uint32_t m = 0xffffffffu;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    if ((vary >> b) & 1u) {
-      const bool bit = (dg >> b) & 1u;
-      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-      m &= bit ? bal : ~bal;
-    }
-  }
-  return m;
-}
-
 // exclusive prefix over the CTA's threads (kKT of them) of one value each
 DDKS_DEV uint32_t cta_exscan(uint32_t v, uint32_t* ws) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -74,8 +63,18 @@ DDKS_DEV uint32_t cta_exscan(uint32_t v, uint32_t* ws) {
   }
   if (lane == 31) ws[warp] = incl;
   __syncthreads();
-  uint32_t carry = 0;
-  for (int q = 0; q < warp; ++q) carry += ws[q];
+  if (warp == 0) {  // exclusive prefix of the warps' totals
+    const uint32_t t = lane < kKW ? ws[lane] : 0u;
+    uint32_t a = t;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, a, off);
+      if (lane >= off) a += x;
+    }
+    if (lane < kKW) ws[lane] = a - t;
+  }
+  __syncthreads();
+  const uint32_t carry = ws[warp];
   __syncthreads();
   return carry + incl - v;
 }
@@ -84,16 +83,16 @@ DDKS_DEV uint32_t cta_exscan(uint32_t v, uint32_t* ws) {
 // positions [c*S, c*S + S).  Outputs: rank[m*N + i] = min-rank of point i;
 // sorted[m*N + p] = pooled index at sorted position p; dimension 0 also
 // sidx0[p] = sorted[p] and pfx0[p] = P points before position p.
-template <typename V>
+template <typename V, int CL>
 __global__ void __launch_bounds__(kKT, 1)
 k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int64_t NT, int d, int S,
-               uint32_t* __restrict__ rank, uint32_t* __restrict__ sorted, uint32_t* __restrict__ sidx0,
+               uint32_t Smag, uint32_t* __restrict__ rank, uint32_t* __restrict__ sorted, uint32_t* __restrict__ sidx0,
                uint32_t* __restrict__ pfx0, unsigned* __restrict__ flags) {
   using K = typename KeyOf<V>::K;
   constexpr int kPasses = KeyOf<V>::kPasses;
   cg::cluster_group cl = cg::this_cluster();
   const int c = (int)cl.block_rank();
-  const int m = (int)(blockIdx.x / kC);
+  const int m = (int)(blockIdx.x / CL);
   const int64_t N = NP + NT;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   extern __shared__ __align__(16) unsigned char kraw[];
@@ -103,7 +102,7 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
   uint32_t* idxB = idxA + S;
   uint16_t* rloc = reinterpret_cast<uint16_t*>(idxB + S);
   uint32_t* wcnt = reinterpret_cast<uint32_t*>(rloc + S + (S & 1));  // [kKW][256]
-  __shared__ uint32_t hist[256], doff[256], ws[kKW], whead[kKW], wpc[kKW];
+  __shared__ uint32_t hist[256], doff[256], half_tot[256], ws[kKW], whead[kKW], wpc[kKW];
   __shared__ uint32_t s_info[2];  // read by the other CTAs: last run head in the segment, its P points
   __shared__ unsigned long long s_left;
   __shared__ int s_skip;
@@ -134,7 +133,8 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
       const uint32_t vm = __ballot_sync(0xffffffffu, v);
       if (vm == 0u) break;  // warp-uniform: positions only grow with j
       const uint32_t dg = v ? (uint32_t)(keyA[q] >> shift) & 255u : 0u;
-      const uint32_t peers = same_digit(dg) & vm;
+      // lanes with this lane's digit (past the end: a value no digit takes)
+      const uint32_t peers = __match_any_sync(0xffffffffu, v ? dg : 256u + (uint32_t)lane) & vm;
       if (v) rloc[q] = (uint16_t)(wcnt[w * 256 + dg] + (uint32_t)__popc(peers & ((1u << lane) - 1u)));
       __syncwarp();
       if (v && (peers >> lane) == 1u) wcnt[w * 256 + dg] += (uint32_t)__popc(peers);  // the group's last lane
@@ -143,20 +143,31 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
     __syncthreads();
     // thread t < 256 owns digit t: the warps' offsets within the digit, and
     // the CTA's count of the digit
-    if (tid < 256) {
+    {
+      // thread (h, t): digit t over warps [h * kKW / 2, (h + 1) * kKW / 2)
+      const int t = tid & 255, h = tid >> 8;
       uint32_t s = 0;
-      for (int q = 0; q < kKW; ++q) {
-        const uint32_t x = wcnt[q * 256 + tid];
-        wcnt[q * 256 + tid] = s;
+#pragma unroll
+      for (int q = h * (kKW / 2); q < (h + 1) * (kKW / 2); ++q) {
+        const uint32_t x = wcnt[q * 256 + t];
+        wcnt[q * 256 + t] = s;
         s += x;
       }
-      hist[tid] = s;
+      if (h == 0) half_tot[t] = s;
+      __syncthreads();
+      if (h == 1) {
+        const uint32_t lo = half_tot[t];
+#pragma unroll
+        for (int q = kKW / 2; q < kKW; ++q) wcnt[q * 256 + t] += lo;
+        hist[t] = lo + s;
+      }
     }
     if (tid == 0) s_skip = 0;
     cl.sync();  // every CTA's counts are complete
     uint32_t tot = 0, before = 0;
     if (tid < 256) {
-      for (int r = 0; r < kC; ++r) {
+#pragma unroll
+      for (int r = 0; r < CL; ++r) {
         const uint32_t h = cl.map_shared_rank(hist, (unsigned)r)[tid];
         tot += h;
         before += r < c ? h : 0u;
@@ -180,7 +191,8 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
           atomicOr(flags, ddks::kFlagBounds);
           continue;
         }
-        const uint32_t dst = pos / (uint32_t)S;
+        uint32_t dst = __umulhi(pos, Smag);  // pos / S or one more (Smag = ceil(2^32 / S), pos < 2^31)
+        if (dst * (uint32_t)S > pos) --dst;
         const uint32_t li = pos - dst * (uint32_t)S;
         cl.map_shared_rank(keyB, dst)[li] = k;
         cl.map_shared_rank(idxB, dst)[li] = idxA[q];
@@ -258,9 +270,47 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
 
 }  // namespace
 
+namespace {
+
+// Largest cluster size (16, else 8) that the device schedules with the most
+// shared memory this kernel asks for; looked up once per device.
+std::mutex g_cl_mu;
+int g_cl_size[128] = {};
+
+template <typename V>
+int cluster_size_for(int dev) {
+  std::lock_guard<std::mutex> g(g_cl_mu);
+  if (dev < 0 || dev >= 128) return 8;
+  if (g_cl_size[dev]) return g_cl_size[dev];
+  int best = 8;
+  auto kern = k_rank_cluster<V, 16>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16, 1, 1);
+    cfg.blockDim = dim3(kKT, 1, 1);
+    cfg.dynamicSmemBytes = kSmemCap;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) best = 16;
+  }
+  cudaGetLastError();
+  g_cl_size[dev] = best;
+  return best;
+}
+
+}  // namespace
+
 bool ddks_rank_cluster_supported(int64_t N, int key_bits) {
+  // sized for the portable cluster of 8; a cluster of 16 halves the segments
   if (N < 1 || N >= ((int64_t)1 << 31)) return false;
-  const int64_t S = (N + kC - 1) / kC;
+  const int64_t S = (N + 7) / 8;
   const size_t smem = key_bits == 64 ? cluster_smem<uint64_t>(S) : cluster_smem<uint32_t>(S);
   return smem <= kSmemCap;
 }
@@ -271,25 +321,38 @@ cudaError_t ddks_launch_rank_cluster(const void* P, const void* T, int64_t NP, i
   const int64_t N = NP + NT;
   if (!ddks_rank_cluster_supported(N, f64 ? 64 : 32) || d < 1 || !rank || !sidx0 || !pfx0)
     return cudaErrorInvalidValue;
-  const int S = (int)((N + kC - 1) / kC);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int CL = f64 ? cluster_size_for<double>(dev) : cluster_size_for<float>(dev);
+  const int S = (int)((N + CL - 1) / CL);
+  const uint32_t Smag = (uint32_t)((((uint64_t)1 << 32) + (uint64_t)S - 1) / (uint64_t)S);
   auto go = [&](auto kern, size_t smem, auto* p, auto* t) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (r != cudaSuccess) return r;
+    if (CL > 8 && (r = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+      return r;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(kC * d), 1, 1);
+    cfg.gridDim = dim3((unsigned)(CL * d), 1, 1);
     cfg.blockDim = dim3(kKT, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = kC;
+    at[0].val.clusterDim.x = (unsigned)CL;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, p, t, NP, NT, d, S, rank, sorted, sidx0, pfx0, flags);
+    return cudaLaunchKernelEx(&cfg, kern, p, t, NP, NT, d, S, Smag, rank, sorted, sidx0, pfx0, flags);
   };
+  const double* pd = (const double*)P;
+  const double* td = (const double*)T;
+  const float* pf = (const float*)P;
+  const float* tf = (const float*)T;
   if (f64)
-    return go(k_rank_cluster<double>, cluster_smem<uint64_t>(S), (const double*)P, (const double*)T);
-  return go(k_rank_cluster<float>, cluster_smem<uint32_t>(S), (const float*)P, (const float*)T);
+    return CL == 16 ? go(k_rank_cluster<double, 16>, cluster_smem<uint64_t>(S), pd, td)
+                    : go(k_rank_cluster<double, 8>, cluster_smem<uint64_t>(S), pd, td);
+  return CL == 16 ? go(k_rank_cluster<float, 16>, cluster_smem<uint32_t>(S), pf, tf)
+                  : go(k_rank_cluster<float, 8>, cluster_smem<uint32_t>(S), pf, tf);
 }
