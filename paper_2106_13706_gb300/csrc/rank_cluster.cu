@@ -191,9 +191,15 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
           atomicOr(flags, ddks::kFlagBounds);
           continue;
         }
-        uint32_t dst = __umulhi(pos, Smag);  // pos / S or one more (Smag = ceil(2^32 / S), pos < 2^31)
+        // dst = pos / S: Smag = ceil(2^32 / S) for S >= 2 gives the quotient
+        // or one more (pos < 2^31); S == 1 passes Smag = 0
+        uint32_t dst = S == 1 ? pos : __umulhi(pos, Smag);
         if (dst * (uint32_t)S > pos) --dst;
         const uint32_t li = pos - dst * (uint32_t)S;
+        if (dst >= (uint32_t)CL || li >= (uint32_t)S) {  // never store outside the cluster's buffers
+          atomicOr(flags, ddks::kFlagBounds);
+          continue;
+        }
         cl.map_shared_rank(keyB, dst)[li] = k;
         cl.map_shared_rank(idxB, dst)[li] = idxA[q];
       }
@@ -254,7 +260,9 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
     const uint32_t idx = v ? idxA[q] : 0u;
     const bool isP = v && idx < (uint64_t)NP;
     const uint32_t pm = __ballot_sync(0xffffffffu, isP);
-    if (v) {
+    if (v && idx >= (uint64_t)N) {  // an index that cannot come out of a correct sort: flag, skip
+      atomicOr(flags, ddks::kFlagBounds);
+    } else if (v) {
       rk[idx] = run;
       if (so) so[g0 + lane] = idx;
       if (m == 0) {
@@ -326,7 +334,8 @@ cudaError_t ddks_launch_rank_cluster(const void* P, const void* T, int64_t NP, i
   if (e != cudaSuccess) return e;
   const int CL = f64 ? cluster_size_for<double>(dev) : cluster_size_for<float>(dev);
   const int S = (int)((N + CL - 1) / CL);
-  const uint32_t Smag = (uint32_t)((((uint64_t)1 << 32) + (uint64_t)S - 1) / (uint64_t)S);
+  // ceil(2^32 / S) fits 32 bits for S >= 2; S == 1 divides by itself
+  const uint32_t Smag = S == 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + (uint64_t)S - 1) / (uint64_t)S);
   auto go = [&](auto kern, size_t smem, auto* p, auto* t) -> cudaError_t {
     cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (r != cudaSuccess) return r;
