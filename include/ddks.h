@@ -94,7 +94,7 @@ typedef struct {
                                  unrolled; 2 pairs at 3 CTAs/SM) */
   int32_t rank_kernel;        /* the per-dimension ranks of the exact paths: 0 = automatic (one launch of
                                  a thread-block cluster per dimension, sorting in distributed shared
-                                 memory, while N fits: about 88k float32 or 60k float64 points; else
+                                 memory, while N fits: about 125k float32 or 85k float64 points; else
                                  the multi-launch sorts), 1 = always the multi-launch sorts */
 } ddks_config;
 

@@ -246,7 +246,7 @@ int ddks_encode_problem(ddks_ctx* ctx, const void* dP, int64_t NP, const void* d
   const int64_t N = NP + NT;
   const size_t npad = ddks_rank_scratch_elems(N);
   int rc;
-  if (ctx->cfg.rank_kernel == 0 && ddks_rank_cluster_supported(N, dtype == DDKS_F64 ? 64 : 32)) {
+  if (ctx->cfg.rank_kernel == 0 && ddks_rank_cluster_supported(N, dtype == DDKS_F64 ? 64 : 32, ctx->device)) {
     // one launch: keys, ranks, every dimension's order, dimension 0's P prefix
     if ((rc = ctx->rank.reserve(ctx, 4 * (size_t)N * d))) return rc;
     if ((rc = ctx->sidx0.reserve(ctx, 4 * (size_t)N))) return rc;

@@ -131,7 +131,7 @@ bool ddks_register_supported(int d, int64_t NP, int64_t NT);
 // rank_cluster.cu: K0 (order keys, min-ranks, dimension-0 order and P
 // prefix, every dimension's sorted order) in one launch of d thread-block
 // clusters, for samples whose rows fit a cluster's shared memory
-bool ddks_rank_cluster_supported(int64_t N, int key_bits);
+bool ddks_rank_cluster_supported(int64_t N, int key_bits, int device);
 cudaError_t ddks_launch_rank_cluster(const void* P, const void* T, int64_t NP, int64_t NT, int d, bool f64,
                                      uint32_t* rank, uint32_t* sorted, uint32_t* sidx0, uint32_t* pfx0,
                                      unsigned* flags, cudaStream_t st);

@@ -1,6 +1,7 @@
-// rank_cluster.cu -- K0 in one launch for pooled samples of up to ~88k
-// (float) or ~60k (double) points: order keys, per-dimension min-ranks, the
-// dimension-0 order and its P prefix.
+// rank_cluster.cu -- K0 in one launch for pooled samples of up to about 125k
+// (float) or 85k (double) points (half that where clusters of 16 CTAs cannot
+// be scheduled): order keys, per-dimension min-ranks, every dimension's
+// sorted order, the dimension-0 P prefix.
 //
 // x_m >= o_m <=> rank_m(x) >= rank_m(o) with rank = the number of pooled
 // values strictly below (Eq. g only ever compares coordinates with ">="), so
@@ -10,10 +11,13 @@
 // shared memory, and a stable LSD radix sort with 8-bit digits runs entirely
 // in the cluster's distributed shared memory -- per pass each CTA ranks its
 // elements stably by digit (per-warp digit counters, lanes with equal digits
-// found by ballots), the cluster's digit counts are read across CTAs to give
-// every (digit, CTA) its first output position, and each element is stored
-// into the shared memory of the CTA that owns its new position.  A pass whose
-// digit is the same for every key is skipped.  After the last pass the
+// found by ballots) and reorders them locally into digit order, the cluster's
+// digit counts are read across CTAs to give every (digit, CTA) its first
+// output position, and each run of equal digits is copied, consecutive
+// threads to consecutive positions, into the shared memory of the CTAs that
+// own those positions.  Three buffers rotate (current, staging, destination),
+// so one cluster barrier after the counts and one after the copies suffice.
+// A pass whose digit is the same for every key is skipped.  After the last pass the
 // positions hold the keys in sorted order with ties in pooled-index order;
 // the min-rank of a position is its run's first position (a running maximum
 // of run heads within the CTA, carried across CTAs), and dimension 0 also
@@ -45,11 +49,28 @@ template <> struct KeyOf<double> { using K = uint64_t; static constexpr int kPas
 // shared memory of one CTA for a segment of S positions
 template <typename K>
 __host__ __device__ constexpr size_t cluster_smem(int64_t S) {
-  return (size_t)S * sizeof(K) * 2     // keys, two buffers
-         + (size_t)S * 4 * 2           // pooled indices, two buffers
+  return (size_t)S * sizeof(K) * 3     // keys: current, staging, destination
+         + (size_t)S * 4 * 3           // pooled indices, the same three
          + (size_t)S * 2               // rank of each element among its warp's equal digits
          + (size_t)kKW * 256 * 4       // per-warp digit counters
          + 16;
+}
+
+// Lanes of the (fully active) warp whose 8-bit digit equals this lane's: one
+// ballot per digit bit that differs somewhere in the warp (a fixed cost;
+// match.any slows down with the number of distinct values in the warp).
+DDKS_DEV uint32_t same_digit(uint32_t dg) {
+  const uint32_t vary = __reduce_or_sync(0xffffffffu, dg) ^ __reduce_and_sync(0xffffffffu, dg);
+  uint32_t m = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    if ((vary >> b) & 1u) {
+      const bool bit = (dg >> b) & 1u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      m &= bit ? bal : ~bal;
+    }
+  }
+  return m;
 }
 
 // exclusive prefix over the CTA's threads (kKT of them) of one value each
@@ -96,13 +117,16 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
   const int64_t N = NP + NT;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   extern __shared__ __align__(16) unsigned char kraw[];
+  // three key / index buffers: current (A), local staging (B), destination (C)
   K* keyA = reinterpret_cast<K*>(kraw);
   K* keyB = keyA + S;
-  uint32_t* idxA = reinterpret_cast<uint32_t*>(keyB + S);
+  K* keyC = keyB + S;
+  uint32_t* idxA = reinterpret_cast<uint32_t*>(keyC + S);
   uint32_t* idxB = idxA + S;
-  uint16_t* rloc = reinterpret_cast<uint16_t*>(idxB + S);
+  uint32_t* idxC = idxB + S;
+  uint16_t* rloc = reinterpret_cast<uint16_t*>(idxC + S);
   uint32_t* wcnt = reinterpret_cast<uint32_t*>(rloc + S + (S & 1));  // [kKW][256]
-  __shared__ uint32_t hist[256], doff[256], half_tot[256], ws[kKW], whead[kKW], wpc[kKW];
+  __shared__ uint32_t hist[256], doff[256], lstart[256], half_tot[256], ws[kKW], whead[kKW], wpc[kKW];
   __shared__ uint32_t s_info[2];  // read by the other CTAs: last run head in the segment, its P points
   __shared__ unsigned long long s_left;
   __shared__ int s_skip;
@@ -133,18 +157,16 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
       const uint32_t vm = __ballot_sync(0xffffffffu, v);
       if (vm == 0u) break;  // warp-uniform: positions only grow with j
       const uint32_t dg = v ? (uint32_t)(keyA[q] >> shift) & 255u : 0u;
-      // lanes with this lane's digit (past the end: a value no digit takes)
-      const uint32_t peers = __match_any_sync(0xffffffffu, v ? dg : 256u + (uint32_t)lane) & vm;
+      const uint32_t peers = same_digit(dg) & vm;
       if (v) rloc[q] = (uint16_t)(wcnt[w * 256 + dg] + (uint32_t)__popc(peers & ((1u << lane) - 1u)));
       __syncwarp();
       if (v && (peers >> lane) == 1u) wcnt[w * 256 + dg] += (uint32_t)__popc(peers);  // the group's last lane
       __syncwarp();
     }
     __syncthreads();
-    // thread t < 256 owns digit t: the warps' offsets within the digit, and
-    // the CTA's count of the digit
     {
-      // thread (h, t): digit t over warps [h * kKW / 2, (h + 1) * kKW / 2)
+      // thread (h, t): digit t over warps [h * kKW / 2, (h + 1) * kKW / 2):
+      // the warps' offsets within the digit, and the CTA's count of it
       const int t = tid & 255, h = tid >> 8;
       uint32_t s = 0;
 #pragma unroll
@@ -164,51 +186,62 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
     }
     if (tid == 0) s_skip = 0;
     cl.sync();  // every CTA's counts are complete
-    uint32_t tot = 0, before = 0;
+    uint32_t tot = 0, before = 0, mine = 0;
     if (tid < 256) {
 #pragma unroll
       for (int r = 0; r < CL; ++r) {
         const uint32_t h = cl.map_shared_rank(hist, (unsigned)r)[tid];
         tot += h;
         before += r < c ? h : 0u;
+        mine = r == c ? h : mine;
       }
     }
     const uint32_t dbase = cta_exscan(tid < 256 ? tot : 0u, ws);
+    const uint32_t lbase = cta_exscan(tid < 256 ? mine : 0u, ws);
     if (tid < 256) {
-      doff[tid] = dbase + before;  // first position of this CTA's elements with digit tid
+      doff[tid] = dbase + before;  // global position of this CTA's first element with digit tid
+      lstart[tid] = lbase;         // its local position in digit order
       if (tot == (uint32_t)N) s_skip = 1;  // every key has this digit: the pass keeps the order
     }
     __syncthreads();
-    const bool skip = s_skip != 0;
-    if (!skip) {
-      for (int j = 0; j < E; ++j) {
-        const int q = w * 32 * E + j * 32 + lane;
-        if (q >= cnt) break;
-        const K k = keyA[q];
-        const uint32_t dg = (uint32_t)(k >> shift) & 255u;
-        const uint32_t pos = doff[dg] + wcnt[w * 256 + dg] + rloc[q];
-        if (pos >= (uint64_t)N) {  // cannot happen when the counts are right; never store out of range
-          atomicOr(flags, ddks::kFlagBounds);
-          continue;
-        }
-        // dst = pos / S: Smag = ceil(2^32 / S) for S >= 2 gives the quotient
-        // or one more (pos < 2^31); S == 1 passes Smag = 0
-        uint32_t dst = S == 1 ? pos : __umulhi(pos, Smag);
-        if (dst * (uint32_t)S > pos) --dst;
-        const uint32_t li = pos - dst * (uint32_t)S;
-        if (dst >= (uint32_t)CL || li >= (uint32_t)S) {  // never store outside the cluster's buffers
-          atomicOr(flags, ddks::kFlagBounds);
-          continue;
-        }
-        cl.map_shared_rank(keyB, dst)[li] = k;
-        cl.map_shared_rank(idxB, dst)[li] = idxA[q];
+    if (s_skip) {  // CTA- and cluster-uniform (every CTA sees the same totals)
+      cl.sync();   // no CTA rewrites its counts while another still reads them
+      continue;
+    }
+    // local reorder into digit order (stable), in the staging buffer
+    for (int j = 0; j < E; ++j) {
+      const int q = w * 32 * E + j * 32 + lane;
+      if (q >= cnt) break;
+      const K k = keyA[q];
+      const uint32_t dg = (uint32_t)(k >> shift) & 255u;
+      const uint32_t lr = lstart[dg] + wcnt[w * 256 + dg] + rloc[q];
+      keyB[lr] = k;
+      idxB[lr] = idxA[q];
+    }
+    __syncthreads();
+    // runs of equal digits to the CTAs that own their positions: consecutive
+    // threads write consecutive positions of the destination buffer
+    for (int lr = tid; lr < cnt; lr += kKT) {
+      const K k = keyB[lr];
+      const uint32_t dg = (uint32_t)(k >> shift) & 255u;
+      const uint32_t pos = doff[dg] + ((uint32_t)lr - lstart[dg]);
+      // dst = pos / S: Smag = ceil(2^32 / S) for S >= 2 gives the quotient
+      // or one more (pos < 2^31); S == 1 passes Smag = 0
+      uint32_t dst = S == 1 ? pos : __umulhi(pos, Smag);
+      if (dst * (uint32_t)S > pos) --dst;
+      const uint32_t li = pos - dst * (uint32_t)S;
+      if (pos >= (uint64_t)N || dst >= (uint32_t)CL || li >= (uint32_t)S) {  // never store out of range
+        atomicOr(flags, ddks::kFlagBounds);
+        continue;
       }
+      cl.map_shared_rank(keyC, dst)[li] = k;
+      cl.map_shared_rank(idxC, dst)[li] = idxB[lr];
     }
-    cl.sync();  // new positions complete everywhere; the counts may be reused
-    if (!skip) {
-      K* tk = keyA; keyA = keyB; keyB = tk;
-      uint32_t* ti = idxA; idxA = idxB; idxB = ti;
-    }
+    cl.sync();  // the destination buffers are complete everywhere
+    // rotate: the destination becomes current; the old current (last read
+    // before this pass's first barrier) becomes the next destination
+    K* tk = keyA; keyA = keyC; keyC = tk;
+    uint32_t* ti = idxA; idxA = idxC; idxC = ti;
   }
 
   // run heads and P points, per warp chunk, then carried across the cluster
@@ -233,20 +266,32 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
   __syncthreads();
   if (tid == 0) {
     uint32_t lh = 0, pc = 0;
+#pragma unroll
     for (int q = 0; q < kKW; ++q) { lh = whead[q] > lh ? whead[q] : lh; pc += wpc[q]; }
     s_info[0] = lh;
     s_info[1] = pc;
   }
   cl.sync();  // every CTA's summary is complete
+  // the earlier CTAs' summaries (all loads issued together) and the earlier warps'
   uint32_t carry = 0, pbefore = 0;
-  for (int r = 0; r < c; ++r) {
-    const uint32_t* o = cl.map_shared_rank(s_info, (unsigned)r);
-    carry = o[0] > carry ? o[0] : carry;
-    pbefore += o[1];
+#pragma unroll
+  for (int r = 0; r < CL; ++r) {
+    if (r < c) {
+      const uint32_t* o = cl.map_shared_rank(s_info, (unsigned)r);
+      const uint32_t h = o[0], pc = o[1];
+      carry = h > carry ? h : carry;
+      pbefore += pc;
+    }
   }
-  for (int q = 0; q < w; ++q) {
-    carry = whead[q] > carry ? whead[q] : carry;
-    pbefore += wpc[q];
+  // the last read of another CTA's shared memory is done: arrive now, wait
+  // before exiting (a relaxed arrival, so the stores below need not drain)
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < kKW; ++q) {
+    if (q < w) {
+      carry = whead[q] > carry ? whead[q] : carry;
+      pbefore += wpc[q];
+    }
   }
   uint32_t* rk = rank + (int64_t)m * N;
   uint32_t* so = sorted ? sorted + (int64_t)m * N : nullptr;
@@ -273,7 +318,7 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
     if (hm) carry = g0 + 31u - (uint32_t)__clz(hm);
     pbefore += (uint32_t)__popc(pm);
   }
-  cl.sync();  // no CTA leaves while another may still read its shared memory
+  asm volatile("barrier.cluster.wait.aligned;" ::: "memory");  // no CTA leaves while another may still read it
 }
 
 }  // namespace
@@ -315,10 +360,10 @@ int cluster_size_for(int dev) {
 
 }  // namespace
 
-bool ddks_rank_cluster_supported(int64_t N, int key_bits) {
-  // sized for the portable cluster of 8; a cluster of 16 halves the segments
+bool ddks_rank_cluster_supported(int64_t N, int key_bits, int device) {
   if (N < 1 || N >= ((int64_t)1 << 31)) return false;
-  const int64_t S = (N + 7) / 8;
+  const int CL = key_bits == 64 ? cluster_size_for<double>(device) : cluster_size_for<float>(device);
+  const int64_t S = (N + CL - 1) / CL;
   const size_t smem = key_bits == 64 ? cluster_smem<uint64_t>(S) : cluster_smem<uint32_t>(S);
   return smem <= kSmemCap;
 }
@@ -327,11 +372,11 @@ cudaError_t ddks_launch_rank_cluster(const void* P, const void* T, int64_t NP, i
                                      uint32_t* rank, uint32_t* sorted, uint32_t* sidx0, uint32_t* pfx0,
                                      unsigned* flags, cudaStream_t st) {
   const int64_t N = NP + NT;
-  if (!ddks_rank_cluster_supported(N, f64 ? 64 : 32) || d < 1 || !rank || !sidx0 || !pfx0)
-    return cudaErrorInvalidValue;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  if (!ddks_rank_cluster_supported(N, f64 ? 64 : 32, dev) || d < 1 || !rank || !sidx0 || !pfx0)
+    return cudaErrorInvalidValue;
   const int CL = f64 ? cluster_size_for<double>(dev) : cluster_size_for<float>(dev);
   const int S = (int)((N + CL - 1) / CL);
   // ceil(2^32 / S) fits 32 bits for S >= 2; S == 1 divides by itself
