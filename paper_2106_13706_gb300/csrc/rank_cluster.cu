@@ -36,7 +36,7 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int kCMax = 16;        // CTAs per cluster: 16 where the GPU allows it, else 8
+constexpr int kEMax = 16;        // positions per thread at most (S <= kEMax * kKT)
 constexpr int kKT = 512;         // threads per CTA
 static_assert(kKT == 512, "the digit-count prefix splits the warps into two halves of 256 threads");
 constexpr int kKW = kKT / 32;    // warps per CTA
@@ -73,31 +73,34 @@ DDKS_DEV uint32_t same_digit(uint32_t dg) {
   return m;
 }
 
-// exclusive prefix over the CTA's threads (kKT of them) of one value each
-DDKS_DEV uint32_t cta_exscan(uint32_t v, uint32_t* ws) {
+// exclusive prefixes over the CTA's threads (kKT of them) of two values each;
+// ws2: 2 * kKW words
+DDKS_DEV void cta_exscan2(uint32_t v0, uint32_t v1, uint32_t* ws2, uint32_t& e0, uint32_t& e1) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t incl = v;
+  uint32_t a = v0, b = v1;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl += x;
+    const uint32_t x = __shfl_up_sync(0xffffffffu, a, off);
+    const uint32_t y = __shfl_up_sync(0xffffffffu, b, off);
+    if (lane >= off) { a += x; b += y; }
   }
-  if (lane == 31) ws[warp] = incl;
+  if (lane == 31) { ws2[warp] = a; ws2[kKW + warp] = b; }
   __syncthreads();
-  if (warp == 0) {  // exclusive prefix of the warps' totals
-    const uint32_t t = lane < kKW ? ws[lane] : 0u;
-    uint32_t a = t;
+  if (warp == 0) {
+    const uint32_t t0 = lane < kKW ? ws2[lane] : 0u, t1 = lane < kKW ? ws2[kKW + lane] : 0u;
+    uint32_t p0 = t0, p1 = t1;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t x = __shfl_up_sync(0xffffffffu, a, off);
-      if (lane >= off) a += x;
+      const uint32_t x = __shfl_up_sync(0xffffffffu, p0, off);
+      const uint32_t y = __shfl_up_sync(0xffffffffu, p1, off);
+      if (lane >= off) { p0 += x; p1 += y; }
     }
-    if (lane < kKW) ws[lane] = a - t;
+    if (lane < kKW) { ws2[lane] = p0 - t0; ws2[kKW + lane] = p1 - t1; }
   }
   __syncthreads();
-  const uint32_t carry = ws[warp];
+  e0 = ws2[warp] + a - v0;
+  e1 = ws2[kKW + warp] + b - v1;
   __syncthreads();
-  return carry + incl - v;
 }
 
 // Grid: d clusters of kC CTAs; cluster m ranks dimension m, CTA c of it holds
@@ -126,7 +129,7 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
   uint32_t* idxC = idxB + S;
   uint16_t* rloc = reinterpret_cast<uint16_t*>(idxC + S);
   uint32_t* wcnt = reinterpret_cast<uint32_t*>(rloc + S + (S & 1));  // [kKW][256]
-  __shared__ uint32_t hist[256], doff[256], lstart[256], half_tot[256], ws[kKW], whead[kKW], wpc[kKW];
+  __shared__ uint32_t hist[256], doff[256], lstart[256], half_tot[256], ws[2 * kKW], whead[kKW], wpc[kKW];
   __shared__ uint32_t s_info[2];  // read by the other CTAs: last run head in the segment, its P points
   __shared__ unsigned long long s_left;
   __shared__ int s_skip;
@@ -151,17 +154,37 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
     // warp's earlier elements of the same digit, wcnt = the warp's counts
     for (int i = tid; i < kKW * 256; i += kKT) wcnt[i] = 0u;
     __syncthreads();
-    for (int j = 0; j < E; ++j) {
-      const int q = w * 32 * E + j * 32 + lane;
-      const bool v = q < cnt;
-      const uint32_t vm = __ballot_sync(0xffffffffu, v);
-      if (vm == 0u) break;  // warp-uniform: positions only grow with j
-      const uint32_t dg = v ? (uint32_t)(keyA[q] >> shift) & 255u : 0u;
-      const uint32_t peers = same_digit(dg) & vm;
-      if (v) rloc[q] = (uint16_t)(wcnt[w * 256 + dg] + (uint32_t)__popc(peers & ((1u << lane) - 1u)));
-      __syncwarp();
-      if (v && (peers >> lane) == 1u) wcnt[w * 256 + dg] += (uint32_t)__popc(peers);  // the group's last lane
-      __syncwarp();
+    // Digits and groups of equal digits first (independent iterations), then
+    // each group takes its offset with one shared atomic add by its lowest
+    // lane: the returned value is the warp's count so far, and the shuffle
+    // that hands it to the group waits for it, so a warp's atomics on one
+    // address happen in program order (stable ranks).
+    uint32_t dgs[kEMax], prs[kEMax];
+#pragma unroll
+    for (int j = 0; j < kEMax; ++j) {
+      dgs[j] = 0u;
+      prs[j] = 0u;
+      if (j < E) {
+        const int q = w * 32 * E + j * 32 + lane;
+        const bool v = q < cnt;
+        const uint32_t vm = __ballot_sync(0xffffffffu, v);
+        if (vm != 0u) {  // warp-uniform
+          dgs[j] = v ? (uint32_t)(keyA[q] >> shift) & 255u : 0u;
+          const uint32_t pr = same_digit(dgs[j]) & vm;
+          prs[j] = v ? pr : 0u;  // nonzero exactly on the lanes that hold an element
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kEMax; ++j) {
+      if (j < E && __any_sync(0xffffffffu, prs[j] != 0u)) {  // warp-uniform
+        const int q = w * 32 * E + j * 32 + lane;
+        const int leader = __ffs(prs[j]) - 1;  // -1 exactly on lanes past the end
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&wcnt[w * 256 + dgs[j]], (uint32_t)__popc(prs[j]));
+        base = __shfl_sync(0xffffffffu, base, leader < 0 ? lane : leader);
+        if (leader >= 0 && q < cnt) rloc[q] = (uint16_t)(base + (uint32_t)__popc(prs[j] & ((1u << lane) - 1u)));
+      }
     }
     __syncthreads();
     {
@@ -196,8 +219,8 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
         mine = r == c ? h : mine;
       }
     }
-    const uint32_t dbase = cta_exscan(tid < 256 ? tot : 0u, ws);
-    const uint32_t lbase = cta_exscan(tid < 256 ? mine : 0u, ws);
+    uint32_t dbase, lbase;
+    cta_exscan2(tid < 256 ? tot : 0u, tid < 256 ? mine : 0u, ws, dbase, lbase);
     if (tid < 256) {
       doff[tid] = dbase + before;  // global position of this CTA's first element with digit tid
       lstart[tid] = lbase;         // its local position in digit order
@@ -365,7 +388,7 @@ bool ddks_rank_cluster_supported(int64_t N, int key_bits, int device) {
   const int CL = key_bits == 64 ? cluster_size_for<double>(device) : cluster_size_for<float>(device);
   const int64_t S = (N + CL - 1) / CL;
   const size_t smem = key_bits == 64 ? cluster_smem<uint64_t>(S) : cluster_smem<uint32_t>(S);
-  return smem <= kSmemCap;
+  return smem <= kSmemCap && S <= (int64_t)kEMax * kKT;
 }
 
 cudaError_t ddks_launch_rank_cluster(const void* P, const void* T, int64_t NP, int64_t NT, int d, bool f64,
