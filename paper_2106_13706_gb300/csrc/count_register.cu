@@ -48,7 +48,10 @@ using namespace ddks_reg;
 constexpr int kThreads = 64;          // threads per CTA of the count kernel
 constexpr int kOPL = 2;               // origin slots per thread
 static_assert(kThreads * kOPL == kOC, "one origin block per CTA");
-constexpr int kTG = 64;               // groups (of 32 points) per staged tile
+constexpr int kTG = 64;
+// ring stages of the count kernel (any occupancy class): two; four stages at
+// 8 CTAs per SM measured slower on 2 x 20,000 points (count 0.251 vs 0.205 ms)
+__host__ __device__ constexpr int reg_stages(int) { return 2; }               // groups (of 32 points) per staged tile
 constexpr int64_t kMaxRegN = 200000;
 constexpr int kPackThreads = 512;     // one origin block per CTA
 constexpr int kPack4Threads = 1024;   // four origin blocks per CTA
@@ -271,8 +274,9 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
   constexpr int RW = Rec<DS>::kWords;
   constexpr int NS = Rec<DS>::kNS;
   extern __shared__ __align__(16) uint32_t sm[];
-  uint32_t* tiles = sm;                                                  // [2][kTG][RW]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(tiles + 2 * kTG * RW);   // [2]
+  constexpr int NST = reg_stages(OCC);                                   // ring stages
+  uint32_t* tiles = sm;                                                  // [NST][kTG][RW]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tiles + NST * kTG * RW);  // [NST]
   const int tid = threadIdx.x;
   const int blk = (int)(blockIdx.x / C);
   const int ci = (int)(blockIdx.x % C);
@@ -289,23 +293,23 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
   const uint32_t tiles_s = (uint32_t)__cvta_generic_to_shared(tiles);
   const uint32_t bar_s = (uint32_t)__cvta_generic_to_shared(bars);
   const int ntiles = g1 > g0 ? (g1 - g0 + kTG - 1) / kTG : 0;
-  auto issue = [&](int t) {  // thread 0: tile t into stage t & 1
+  auto issue = [&](int t) {  // thread 0: tile t into stage t % NST
     const int base = g0 + t * kTG;
     const int n = (g1 - base) < kTG ? (g1 - base) : kTG;
     const uint32_t bytes = (uint32_t)(n * RW * 4);
-    const uint32_t bar = bar_s + 8u * (t & 1);
+    const uint32_t st = (uint32_t)(t % NST);
+    const uint32_t bar = bar_s + 8u * st;
     bk::fence_async();
     bk::mbar_expect(bar, bytes);
-    bk::load(tiles_s + (uint32_t)((t & 1) * kTG * RW * 4), rec + ((size_t)blk * ngroups + base) * RW, bytes,
-              bar);
+    bk::load(tiles_s + st * (uint32_t)(kTG * RW * 4), rec + ((size_t)blk * ngroups + base) * RW, bytes, bar);
   };
   if (tid == 0) {
-    bk::mbar_init(bar_s, 1);
-    bk::mbar_init(bar_s + 8, 1);
+    for (int k = 0; k < NST; ++k) bk::mbar_init(bar_s + 8u * k, 1);
     bk::mbar_init_fence();
   }
   __syncthreads();
-  if (tid == 0 && ntiles > 0) issue(0);
+  if (tid == 0)
+    for (int t = 0; t < NST - 1 && t < ntiles; ++t) issue(t);
 
   // this lane's origins: comparison masks s[o][m][k] = all ones where bit k
   // of o'_m is set, and the split (sample-local)
@@ -343,11 +347,11 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
   for (int t = 0; t < ntiles; ++t) {
     const int base = g0 + t * kTG;
     const int n = (g1 - base) < kTG ? (g1 - base) : kTG;
-    // stage (t + 1) & 1 was released by the barrier that ended tile t - 1
-    if (tid == 0 && t + 1 < ntiles) issue(t + 1);
-    const bool ok = bk::wait(bar_s + 8u * (t & 1), (uint32_t)((t >> 1) & 1), wait_ns);
+    // stage (t - 1) % NST was released by the barrier that ended tile t - 1
+    if (tid == 0 && t + NST - 1 < ntiles) issue(t + NST - 1);
+    const bool ok = bk::wait(bar_s + 8u * (uint32_t)(t % NST), (uint32_t)((t / NST) & 1), wait_ns);
     if (ok) {
-      const uint4* tile = reinterpret_cast<const uint4*>(tiles + (t & 1) * kTG * RW);
+      const uint4* tile = reinterpret_cast<const uint4*>(tiles + (t % NST) * kTG * RW);
       for (int gi = 0; gi < n; ++gi) {
         // compare the group's 32 points with both origins, dimension by dimension
         uint32_t G[kOPL][DS];
@@ -387,14 +391,14 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
         }
       }
     }
-    // every thread is done with stage t & 1; a timed-out wait ends the unit
+    // every thread is done with stage t % NST; a timed-out wait ends the unit
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(flags, ddks::kFlagTimeout);
-        // the copies of tiles t and t + 1 may still be in flight: wait for
-        // them (bounded) so that none lands after the CTA has exited
-        for (int k = t; k < t + 2 && k < ntiles; ++k)
-          bk::wait(bar_s + 8u * (k & 1), (uint32_t)((k >> 1) & 1), bk::kDrainNs);
+        // the copies of tiles t .. t + NST - 2 may still be in flight: wait
+        // for them (bounded) so that none lands after the CTA has exited
+        for (int k = t; k < t + NST - 1 && k < ntiles; ++k)
+          bk::wait(bar_s + 8u * (uint32_t)(k % NST), (uint32_t)((k / NST) & 1), bk::kDrainNs);
       }
       return;
     }
@@ -448,7 +452,7 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
   fin.out3[2] = (unsigned long long)(long long)__ldcg(&fin.bestj[pos]);
 }
 
-size_t reg_smem(int ds) { return (size_t)2 * kTG * 8 * ds * 4 + 16; }
+size_t reg_smem(int ds, int occ) { return (size_t)reg_stages(occ) * kTG * 8 * ds * 4 + 8 * 4 + 16; }
 size_t pack_smem(int NW, int G) { return (size_t)NW * 32 * G + (size_t)G * NW * 4 + 40 * 4; }
 constexpr size_t kPackSmemMax = 227u * 1024u;
 
@@ -568,10 +572,10 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   const int64_t C = CP + CT;
   e = cudaMemsetAsync(gcnt, 0, ((size_t)no * kCnt + n_fin) * 4, st);
   if (e != cudaSuccess) return e;
-  const size_t smem = reg_smem(ds);
   const unsigned ctas = (unsigned)(blocks * C);
   // resident 64-thread CTAs per SM the kernel is built for: 8, 12 or 16
   const int occ = plan.reg_occ == 4 ? 8 : plan.reg_occ == 8 ? 16 : 12;
+  const size_t smem = reg_smem(ds, occ);
   Final fin{out3, done, packed, best, bestj, ob, (int)blocks};
   auto go = [&](auto kern) -> cudaError_t {
     cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
