@@ -344,6 +344,19 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
 #pragma unroll
     for (int S = 0; S < NS; ++S) acc[o][S] = snap[o][S] = 0;
   }
+  // The block's origins are consecutive in dimension-0 order, so their splits
+  // lie between those of its first and last origin: only sample-local groups
+  // [wlo, whi) can hold a split (a split at 32k falls in group k).  Outside
+  // that window no origin changes phase (a warp-uniform test per group).
+  int wlo, whi;
+  {
+    const int64_t q0 = (int64_t)blk * kOB;
+    const int64_t qL = ((int64_t)(blk + 1) * kOB < no ? (int64_t)(blk + 1) * kOB : no) - 1;
+    const OriginMeta m0 = meta[q0], mL = meta[qL];
+    wlo = (int)((sample == 0 ? m0.sP : m0.sT) >> 5);
+    whi = (int)((sample == 0 ? mL.sP : mL.sT) >> 5) + 1;
+  }
+  bool all_crossed = g0 - gbase >= whi;
   for (int t = 0; t < ntiles; ++t) {
     const int base = g0 + t * kTG;
     const int n = (g1 - base) < kTG ? (g1 - base) : kTG;
@@ -352,6 +365,7 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
     const bool ok = bk::wait(bar_s + 8u * (uint32_t)(t % NST), (uint32_t)((t / NST) & 1), wait_ns);
     if (ok) {
       const uint4* tile = reinterpret_cast<const uint4*>(tiles + (t % NST) * kTG * RW);
+#pragma unroll 2
       for (int gi = 0; gi < n; ++gi) {
         // compare the group's 32 points with both origins, dimension by dimension
         uint32_t G[kOPL][DS];
@@ -368,7 +382,9 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
             G[o][m] = r;
           }
         }
-        const int pos0 = (base + gi - gbase) * 32;  // sample-local position of bit 0
+        const int gidx = base + gi - gbase;  // sample-local group
+        const int pos0 = gidx * 32;          // sample-local position of bit 0
+        const bool inwin = !all_crossed && gidx >= wlo;  // warp-uniform
 #pragma unroll
         for (int o = 0; o < kOPL; ++o) {
           uint32_t M[NS + 1];
@@ -379,7 +395,7 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
             const uint32_t gl = (S & 1) ? G[o][0] : ((S & 2) ? G[o][DS > 1 ? 1 : 0] : G[o][DS > 2 ? 2 : 0]);
             M[S] = M[S & (S - 1)] & gl;
           }
-          if (!crossed[o] && pos0 + 32 > split[o]) {
+          if (inwin && !crossed[o] && pos0 + 32 > split[o]) {
             // the group holds the origin's split, or begins phase B
             const uint32_t pa = pos0 < split[o] ? ~(0xFFFFFFFFu << (split[o] - pos0)) : 0u;  // phase-A points
 #pragma unroll
@@ -389,6 +405,7 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
 #pragma unroll
           for (int S = 1; S <= NS; ++S) acc[o][S - 1] += (uint32_t)__popc(M[S]);
         }
+        if (inwin && gidx + 1 >= whi) all_crossed = true;  // every split of the block is behind
       }
     }
     // every thread is done with stage t % NST; a timed-out wait ends the unit
