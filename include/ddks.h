@@ -162,6 +162,21 @@ int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* 
                           ddks_result* observed, uint64_t* perm_num_max, double* p_value);
 
 /*
+ * One shard of a permutation test split across GPUs by relabelling: the
+ * observed statistic and relabellings b in [b_begin, b_end) only, each drawn
+ * exactly as in ddks_permutation_test (relabelling b depends on seed and b
+ * alone), so the shards of one test reproduce its relabellings whatever the
+ * split.  perm_num_max (optional host array of b_end - b_begin) receives their
+ * num_max; count_ge (optional) the number with num_b >= num_obs.  Merge: sum
+ * count_ge over the shards; p = (1 + sum) / (1 + B) for B relabellings in all.
+ * 0 <= b_begin <= b_end, b_end - b_begin <= 2^20.
+ */
+int ddks_permutation_test_range(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT,
+                                int32_t d, int32_t dtype, int64_t b_begin, int64_t b_end, uint64_t seed,
+                                void* stream, ddks_result* observed, uint64_t* perm_num_max,
+                                uint64_t* count_ge);
+
+/*
  * Analytic significance (Sec. 3, Eq. ddks_significance) of a statistic
  * num_max for these samples: S = 1 - prod over every pooled origin k and
  * orthant j of p(delta <= D; lam_kj), where p(delta <= D; lam) sums

@@ -82,6 +82,8 @@ def load():
             "ddks_distance_range": (i32, [vp, vp, i64, vp, i64, i32, i32, i64, i64, vp, vp, R]),
             "ddks_permutation_test": (i32, [vp, vp, i64, vp, i64, i32, i32, i32, u64, vp, R, vp,
                                             ctypes.POINTER(ctypes.c_double)]),
+            "ddks_permutation_test_range": (i32, [vp, vp, i64, vp, i64, i32, i32, i64, i64, u64, vp, R, vp,
+                                                  ctypes.POINTER(u64)]),
             "ddks_significance": (i32, [vp, vp, i64, vp, i64, i32, i32, u64, i32, i32, vp,
                                         ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]),
@@ -293,6 +295,23 @@ def ddks_permutation_test(ctx, P, T, B, seed, stream=None, want_perm=True):
     return out
 
 
+def ddks_permutation_test_range(ctx, P, T, b_begin, b_end, seed, stream=None, want_perm=True):
+    """Relabellings [b_begin, b_end) of one permutation test: observed result,
+    their numerators and the count with num_b >= num_obs (merge: sum the counts)."""
+    p, NP, t, NT, d, dt, keep = _pair(P, T)
+    r = ddks_result()
+    n = int(b_end) - int(b_begin)
+    pm = np.zeros(max(n, 1), dtype=np.uint64) if want_perm else None
+    ge = ctypes.c_uint64(0)
+    _check(load().ddks_permutation_test_range(ctx, p, NP, t, NT, d, dt, int(b_begin), int(b_end), seed,
+                                              _stream(stream), ctypes.byref(r),
+                                              pm.ctypes.data if pm is not None else None, ctypes.byref(ge)), ctx)
+    out = dict(observed=r.as_dict(), count_ge=int(ge.value))
+    if want_perm:
+        out["perm_num_max"] = pm[:n]
+    return out
+
+
 def ddks_significance(ctx, P, T, num_max, estimator=1, model=0, stream=None):
     p, NP, t, NT, d, dt, keep = _pair(P, T)
     S = ctypes.c_double(0)
@@ -424,6 +443,9 @@ class Context:
 
     def permutation_test(self, P, T, B, seed, stream=None, want_perm=True):
         return ddks_permutation_test(self.h, P, T, B, seed, stream, want_perm)
+
+    def permutation_test_range(self, P, T, b_begin, b_end, seed, stream=None, want_perm=True):
+        return ddks_permutation_test_range(self.h, P, T, b_begin, b_end, seed, stream, want_perm)
 
     def significance(self, P, T, num_max, estimator=1, model=0, stream=None):
         return ddks_significance(self.h, P, T, num_max, estimator, model, stream)

@@ -61,7 +61,9 @@ k_perm_labels_warp(int64_t N, int64_t NP, int B, const unsigned long long* __res
   __shared__ uint32_t hist_all[kLabWarps][256];
   __shared__ unsigned long long ck_all[kLabWarps][kLabCand];
   __shared__ uint32_t ci_all[kLabWarps][kLabCand];
-  const uint64_t seed = *seedp;  // from device memory, so a captured graph serves every seed
+  // seed and the index of the first relabelling, from device memory so a
+  // captured graph serves every seed and every range of relabellings
+  const uint64_t seed = seedp[0], b_off = seedp[1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t* hist = hist_all[warp];
   unsigned long long* ck = ck_all[warp];
@@ -76,7 +78,7 @@ k_perm_labels_warp(int64_t N, int64_t NP, int B, const unsigned long long* __res
       for (int v = lane; v < 256; v += 32) hist[v] = 0;
       __syncwarp();
       for (int c = lane; c < nc; c += 32) {
-        uint64_t ctr[4] = {(uint64_t)c, (uint64_t)b, 0ull, 0ull};
+        uint64_t ctr[4] = {(uint64_t)c, b_off + (uint64_t)b, 0ull, 0ull};
         philox4x64_10(ctr, seed, 0ull);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -122,7 +124,7 @@ k_perm_labels_warp(int64_t N, int64_t NP, int B, const unsigned long long* __res
     uint32_t cnt = 0;
     for (int c0 = 0; c0 < nc; c0 += 32) {
       const int c = c0 + lane;
-      uint64_t ctr[4] = {(uint64_t)c, (uint64_t)b, 0ull, 0ull};
+      uint64_t ctr[4] = {(uint64_t)c, b_off + (uint64_t)b, 0ull, 0ull};
       if (c < nc) philox4x64_10(ctr, seed, 0ull);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -157,7 +159,7 @@ k_perm_labels_warp(int64_t N, int64_t NP, int B, const unsigned long long* __res
     ti = __shfl_sync(0xffffffffu, ti, src);
     // the NP smallest (key, index) pairs: (key, i) <= (tk, ti)
     for (int c = lane; c < nc; c += 32) {
-      uint64_t ctr[4] = {(uint64_t)c, (uint64_t)b, 0ull, 0ull};
+      uint64_t ctr[4] = {(uint64_t)c, b_off + (uint64_t)b, 0ull, 0ull};
       philox4x64_10(ctr, seed, 0ull);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -482,13 +484,14 @@ cudaError_t launch_count(const uint32_t* rank, int64_t N, int64_t NP, int B, int
 
 }  // namespace
 
-int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT,
-                          int32_t d, int32_t dtype, int32_t B, uint64_t seed, void* stream,
-                          ddks_result* observed, uint64_t* perm_num_max, double* p_value) {
+// Relabellings b_off .. b_off + B - 1; count_ge = #{b : num_b >= num_obs}.
+static int perm_impl(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT, int32_t d,
+                     int32_t dtype, uint64_t b_off, int32_t B, uint64_t seed, void* stream, ddks_result* observed,
+                     uint64_t* perm_num_max, uint64_t* count_ge, double* p_value) {
   if (!ctx || !observed) return DDKS_EINVAL;
   int rc = ddks_check_problem(P, NP, T, NT, d, dtype);
   if (rc) return observed->status = rc;
-  if (B < 0 || B > (1 << 20)) return observed->status = DDKS_EINVAL;
+  if (B < 0 || B > (1 << 20) || b_off > ((uint64_t)1 << 40)) return observed->status = DDKS_EINVAL;
   const int64_t N = NP + NT;
   if (N > kMaxPermN || d > 8) return observed->status = DDKS_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
@@ -500,9 +503,10 @@ int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* 
   if ((rc = ddks_select_path(ctx, NP, NT, d, &plan))) return observed->status = rc;
   if ((rc = ctx->out3.reserve(ctx, 64 + ddks_reduce_scratch_bytes()))) return observed->status = rc;
   unsigned long long* out3 = (unsigned long long*)ctx->out3.ptr;
-  // out3: [0..2] observed result, [4] #{b : num_b >= num_obs}, [6] seed
+  // out3: [0..2] observed result, [4] #{b : num_b >= num_obs}, [6] seed, [7] first relabelling
   ctx->h_out[16] = seed;
-  e = cudaMemcpyAsync(out3 + 6, ctx->h_out + 16, 8, cudaMemcpyHostToDevice, st);
+  ctx->h_out[17] = b_off;
+  e = cudaMemcpyAsync(out3 + 6, ctx->h_out + 16, 16, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return observed->status = ctx_cuda_fail(ctx, e, "seed upload");
   const int G = (B + 31) / 32;
   const int Bc = B > 0 ? B : 1;
@@ -615,6 +619,22 @@ int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* 
   observed->argmax_orthant = (int32_t)ctx->h_out[2];
   observed->status = DDKS_OK;
   const unsigned long long ge = B > 0 ? ctx->h_out[4] : 0ull;
+  if (count_ge) *count_ge = ge;
   if (p_value) *p_value = (double)(1 + ge) / (double)(1 + (int64_t)B);
   return DDKS_OK;
+}
+
+int ddks_permutation_test(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT,
+                          int32_t d, int32_t dtype, int32_t B, uint64_t seed, void* stream,
+                          ddks_result* observed, uint64_t* perm_num_max, double* p_value) {
+  return perm_impl(ctx, P, NP, T, NT, d, dtype, 0, B, seed, stream, observed, perm_num_max, nullptr, p_value);
+}
+
+int ddks_permutation_test_range(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT, int32_t d,
+                                int32_t dtype, int64_t b_begin, int64_t b_end, uint64_t seed, void* stream,
+                                ddks_result* observed, uint64_t* perm_num_max, uint64_t* count_ge) {
+  if (!observed) return DDKS_EINVAL;
+  if (b_begin < 0 || b_end < b_begin || b_end - b_begin > (1 << 20)) return observed->status = DDKS_EINVAL;
+  return perm_impl(ctx, P, NP, T, NT, d, dtype, (uint64_t)b_begin, (int32_t)(b_end - b_begin), seed, stream,
+                   observed, perm_num_max, count_ge, nullptr);
 }

@@ -63,3 +63,22 @@ def test_large_n_labels(torch):
     # before ranking its bucket; the lane-histogram counter takes N > 4096
     P, T = wl.random_pair(11, 5000, 4000, 2, kind="normal")
     _check(torch, P, T, 20, seed=123456789)
+
+
+@pytest.mark.parametrize("d,kind", [(3, "normal"), (5, "int"), (7, "normal")])
+def test_relabelling_ranges_reproduce_the_whole_test(torch, d, kind):
+    # shards by relabelling (one per GPU in a multi-GPU run): the ranges'
+    # numerators concatenate to the whole test's and their counts give its p
+    from paper_2106_13706_gb300 import sharding
+    P, T = wl.random_pair(70 + d, 600, 450, d, kind=kind)
+    B, seed = 250, 4242
+    ref = orc.permutation_test(P, T, B, seed)
+    with pkg.Context(device=0) as c:
+        Pd, Td = torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()
+        cuts = [0, 1, 97, 97, 200, 250]
+        parts = [c.permutation_test_range(Pd, Td, a, b, seed) for a, b in zip(cuts[:-1], cuts[1:])]
+        mid = c.permutation_test_range(Pd, Td, 120, 130, seed)
+    assert all(p["observed"]["num_max"] == ref["num_obs"] for p in parts)
+    assert np.array_equal(np.concatenate([p["perm_num_max"] for p in parts]), ref["perm_num_max"])
+    assert np.array_equal(mid["perm_num_max"], ref["perm_num_max"][120:130])
+    assert sharding.merge_perm_counts([p["count_ge"] for p in parts], B) == ref["p_value"]

@@ -71,3 +71,47 @@ def test_two_rank_gloo_merge_equals_whole():
     whole = orc.ddks(P, T)
     assert (merged["num_max"], merged["argmax_origin"], merged["argmax_orthant"]) == \
         (whole["num_max"], whole["argmax_origin"], whole["argmax_orthant"])
+
+
+def _perm_rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    from oracle import oracle as orc
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        P, T = wl.random_pair(12, 40, 50, 2, kind="normal", dtype=np.float64)
+        B = 23
+        a, b = sharding.shard_range(B, world, rank)
+        # this rank's relabellings, each drawn from (seed, b) alone
+        ref = orc.permutation_test(P, T, B, 99)
+        mine = ref["perm_num_max"][a:b]
+        count = int((mine >= ref["num_obs"]).sum())
+        p = sharding.all_merge_perm(count, B)
+        if rank == 0:
+            q.put(p)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_perm_count_merge():
+    assert sharding.merge_perm_counts([3, 4], 99) == 8 / 100
+    assert sharding.merge_perm_counts([], 0) == 1.0
+    with pytest.raises(ValueError):
+        sharding.merge_perm_counts([-1], 5)
+
+
+def test_two_rank_gloo_permutation_shards_equal_whole():
+    from oracle import oracle as orc
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_perm_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    p_merged = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    P, T = wl.random_pair(12, 40, 50, 2, kind="normal", dtype=np.float64)
+    assert p_merged == orc.permutation_test(P, T, 23, 99)["p_value"]
