@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-study", action="store_true", help="perm workload: skip the significance study")
+    ap.add_argument("--shard", choices=["origins", "replicas"], default="origins",
+                    help="N > 1: split one problem's origins across the ranks (strong scaling, exact max "
+                         "merge) or run one whole problem per rank (weak scaling)")
     return ap.parse_args()
 
 
@@ -213,13 +216,20 @@ def run_ours(args):
     Td = torch.from_numpy(T).cuda()
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device="cuda")
     ctx = pkg.Context(device=local, path=args.path)
+    from paper_2106_13706_gb300 import sharding
+    shard = args.shard if world > 1 else "none"
+    if shard == "origins":
+        o_begin, o_end = sharding.shard_range(N, world, rank)
+        call = lambda A, B: ctx.distance_range(A, B, o_begin, o_end)  # noqa: E731
+    else:
+        call = ctx.distance
     tuned = None
     if args.path == 0 and not args.no_autotune:
         tuned = ctx.autotune(Pd, Td)  # the project's autotuner picks the kernel shape
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
-        ref = ctx.distance(Pd, Td)  # repeated calls are replayed as one CUDA graph
+        ref = call(Pd, Td)  # repeated calls are replayed as one CUDA graph
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.2)
@@ -233,7 +243,7 @@ def run_ours(args):
     for s in range(args.steps):
         flush.zero_()
         ev[s][0].record(stream)
-        r = ctx.distance(Pd, Td)
+        r = call(Pd, Td)
         ev[s][1].record(stream)
         if r["num_max"] != ref["num_max"]:
             raise RuntimeError("result changed between steps")
@@ -249,7 +259,7 @@ def run_ours(args):
     ctx.set_stage_timing(True)
     for s in range(min(args.steps, 50)):
         flush.zero_()
-        ctx.distance(Pd, Td)
+        call(Pd, Td)
         st3 = ctx.stage_times()
         enc_ms.append(st3[0])
         count_ms.append(st3[1])
@@ -261,7 +271,10 @@ def run_ours(args):
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
-    value = units * args.steps * world / (total_ms * 1e-3)
+    mult = world if shard == "replicas" else 1  # origin shards make up one problem together
+    value = units * args.steps * mult / (total_ms * 1e-3)
+    if shard == "origins":
+        ref = sharding.all_merge(ref)  # the whole problem's result, on every rank
 
     # end to end through the same C call with pinned host inputs: the H2D copy
     # of P and T and the D2H copy of the result are inside each timed call
@@ -270,7 +283,7 @@ def run_ours(args):
         Ph = torch.from_numpy(P).pin_memory()
         Th = torch.from_numpy(T).pin_memory()
         for _ in range(3):
-            ctx.distance(Ph, Th)
+            call(Ph, Th)
         torch.cuda.synchronize()
     if not args.no_e2e:
         tot = 0.0
@@ -278,11 +291,16 @@ def run_ours(args):
             flush.zero_()
             torch.cuda.synchronize()
             a = time.perf_counter()
-            r2 = ctx.distance(Ph, Th)
+            r2 = call(Ph, Th)
             tot += time.perf_counter() - a
+        if shard == "origins":
+            r2 = sharding.all_merge(r2)
+            t2 = torch.tensor([tot], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t2, op=dist.ReduceOp.MAX)
+            tot = float(t2.item())
         if r2["num_max"] != ref["num_max"]:
             raise RuntimeError("host-input result differs")
-        e2e = {"value": units * args.steps * world / tot, "unit": UNIT,
+        e2e = {"value": units * args.steps * mult / tot, "unit": UNIT,
                "h2d_bytes_per_step": int(Ph.numel() * Ph.element_size() + Th.numel() * Th.element_size()),
                "d2h_bytes_per_step": 3 * 8 + 4}
 
@@ -296,7 +314,9 @@ def run_ours(args):
     cnt = statistics.mean(count_ms) if count_ms else None
     roof = None
     if cnt:
-        achieved = units / (cnt * 1e-3)
+        # this rank's compares: all points against its origins
+        units_rank = units * ((o_end - o_begin) / N if shard == "origins" else 1.0)
+        achieved = units_rank / (cnt * 1e-3)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
                 "frac": achieved / peak, "traffic": load_traffic({"cfg2": "count_d4_20k"}.get(args.workload, "")),
                 "kernel": "orthant count stage (re-rank pack + count + fused reduction)", "kernel_ms": cnt,
@@ -318,12 +338,15 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32 ranks (f32 input)" if P.dtype == np.float32 else "u32 ranks (f64 input)",
+        "scaling": "strong" if shard == "origins" else "weak", "vs_baseline": None,
+        "dtype": "u32 ranks (f32 input)" if P.dtype == np.float32 else "u32 ranks (f64 input)",
         "data": "synthetic (seeded numpy PCG64)",
         "config": {"workload": desc, "N": N, "d": d, "units_per_step": units,
                    "kernel_path": (["auto", "register", "lane", "warp", "sort"][tuned[0]] if tuned else
                                    ["auto", "register", "lane", "warp", "sort"][args.path]),
-                   "l2": f"flushed between steps ({args.flush_mb} MB write)", "replicas": world},
+                   "l2": f"flushed between steps ({args.flush_mb} MB write)",
+                   "parallelism": ("origin-sharded x%d (exact max merge)" % world if shard == "origins"
+                                   else "replicas x%d" % world)},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "num_max": ref["num_max"], "denom": ref["denom"], "parity": parity,
         "wall_s_timed": wall,
