@@ -31,7 +31,8 @@ struct BatchDesc {
 
 namespace {
 
-constexpr int kMaxBatchN = 16384;
+constexpr int kMaxBatchN = 16384;   // so NP, NT < 65536: P and T counts share one 32-bit bin
+constexpr int kMaxGroups = 16;      // dimensions 1..11 of the batched problems
 constexpr int kThreads = 256;
 constexpr int kOT = 64;        // origins per work unit
 constexpr int kTile = 512;     // points per staged tile
@@ -104,16 +105,14 @@ DDKS_DEV void unit_lane(const BatchDesc& D, const uint32_t* __restrict__ rk, int
   constexpr int S = kThreads / kOT;
   const int64_t N = D.NP + D.NT;
   const int tid = threadIdx.x, ol = tid / S, s = tid - ol * S;
-  const bool wide = D.NP > 65535 || D.NT > 65535;
-  uint32_t* histP = sm;                         // [NB][kThreads]
-  uint32_t* histT = sm + NB * kThreads;         // [NB][kThreads] (wide only)
-  uint32_t* tile = sm + 2 * NB * kThreads;      // [DD][kTile]
+  uint32_t* hist = sm;                          // [NB][kThreads]: P count | T count << 16
+  uint32_t* tile = sm + NB * kThreads;          // [DD][kTile]
   const int64_t k = o0 + ol;
   const bool active = k < N;
   uint32_t o[DD];
 #pragma unroll
   for (int m = 0; m < DD; ++m) o[m] = active ? rk[(int64_t)m * N + k] : 0u;
-  for (int j = 0; j < NB; ++j) { histP[j * kThreads + tid] = 0; histT[j * kThreads + tid] = 0; }
+  for (int j = 0; j < NB; ++j) hist[j * kThreads + tid] = 0;
   for (int64_t base = 0; base < N; base += kTile) {
     const int cnt = (int)((N - base) < kTile ? (N - base) : kTile);
     __syncthreads();
@@ -128,9 +127,7 @@ DDKS_DEV void unit_lane(const BatchDesc& D, const uint32_t* __restrict__ rk, int
       uint32_t c = 0;
 #pragma unroll
       for (int m = 0; m < DD; ++m) c |= (uint32_t)(tile[m * kTile + j] >= o[m]) << m;
-      if (j < pend) atomicAdd(&histP[c * kThreads + tid], 1u);
-      else if (wide) atomicAdd(&histT[c * kThreads + tid], 1u);
-      else atomicAdd(&histP[c * kThreads + tid], 1u << 16);
+      atomicAdd(&hist[c * kThreads + tid], j < pend ? 1u : (1u << 16));
     }
   }
   __syncthreads();
@@ -141,9 +138,9 @@ DDKS_DEV void unit_lane(const BatchDesc& D, const uint32_t* __restrict__ rk, int
       uint64_t a = 0, b = 0;
       for (int q = 0; q < S; ++q) {
         const int col = ol * S + q;
-        const uint32_t v = histP[j * kThreads + col];
-        if (wide) { a += v; b += histT[j * kThreads + col]; }
-        else { a += v & 0xFFFFu; b += v >> 16; }
+        const uint32_t v = hist[j * kThreads + col];
+        a += v & 0xFFFFu;
+        b += v >> 16;
       }
       const uint64_t num = ddks::numer(a, b, (uint64_t)D.NP, (uint64_t)D.NT);
       if (num > bv) { bv = num; bj = j; }
@@ -161,46 +158,80 @@ DDKS_DEV void unit_lane(const BatchDesc& D, const uint32_t* __restrict__ rk, int
   __syncthreads();
 }
 
-// one shared histogram per warp and origin (7 <= d <= 11), 8 warps x 8 origins
+// 7 <= d <= 11: the CTA's 8 warps take one origin each (8 rounds of 8 per
+// unit of 64), with one shared histogram per warp (P count | T count << 16).
+// Point tiles are staged in shared memory once for the 8 warps, ranks packed
+// as 16-bit pairs (N <= 16384): (x | 0x8000) - o keeps each half apart and its
+// bit 15 is [x >= o], so one subtract compares two dimensions.
 DDKS_DEV void unit_warp(const BatchDesc& D, const uint32_t* __restrict__ rk, int64_t o0,
                         uint32_t* sm, uint64_t* best, int32_t* bestj) {
-  const int d = D.d, nb = 1 << d;
+  const int d = D.d, nb = 1 << d, npair = (d + 1) >> 1;
   const int64_t N = D.NP + D.NT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool wide = D.NP > 65535 || D.NT > 65535;
-  uint32_t* hist = sm + (size_t)warp * nb * 2;
-  for (int it = 0; it < kOT / (kThreads / 32); ++it) {
-    const int64_t k = o0 + it * (kThreads / 32) + warp;
-    if (k >= N) break;
-    for (int j = lane; j < 2 * nb; j += 32) hist[j] = 0;
-    uint32_t o[ddks::kMaxD];
-    for (int m = 0; m < d; ++m) o[m] = rk[(int64_t)m * N + k];
-    __syncwarp();
-    for (int64_t i = lane; i < N; i += 32) {
-      uint32_t c = 0;
-      for (int m = 0; m < d; ++m) c |= (uint32_t)(rk[(int64_t)m * N + i] >= o[m]) << m;
-      const bool isP = i < D.NP;
-      if (wide) atomicAdd(&hist[isP ? c : nb + c], 1u);
-      else atomicAdd(&hist[c], isP ? 1u : (1u << 16));
+  constexpr int kW = kThreads / 32;
+  uint32_t* hist = sm + (size_t)warp * nb;              // [kW][nb]
+  uint32_t* tile = sm + (size_t)kW * nb;                // [npair][kTile] packed pairs
+  for (int round = 0; round < kOT / kW; ++round) {
+    const int64_t k = o0 + round * kW + warp;
+    const bool active = k < N;
+    // the origin's ranks as packed pairs; an odd last dimension is paired
+    // with a high half that every point passes
+    uint32_t op[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      uint32_t lo = 0, hi = 0;
+      if (active && q < npair) {
+        lo = rk[(int64_t)(2 * q) * N + k];
+        hi = 2 * q + 1 < d ? rk[(int64_t)(2 * q + 1) * N + k] : 0u;
+      }
+      op[q] = lo | (hi << 16);
+    }
+    for (int j = lane; j < nb; j += 32) hist[j] = 0;
+    for (int64_t base = 0; base < N; base += kTile) {
+      const int cnt = (int)((N - base) < kTile ? (N - base) : kTile);
+      __syncthreads();  // the previous tile is consumed (and the histograms are zeroed)
+      for (int e = threadIdx.x; e < npair * cnt; e += kThreads) {
+        const int q = e / cnt, j = e - q * cnt;
+        const uint32_t lo = rk[(int64_t)(2 * q) * N + base + j];
+        const uint32_t hi = 2 * q + 1 < d ? rk[(int64_t)(2 * q + 1) * N + base + j] : 0u;
+        tile[q * kTile + j] = (lo | (hi << 16)) | 0x80008000u;
+      }
+      __syncthreads();
+      if (active) {
+        const int pend = (int)(D.NP - base < 0 ? 0 : (D.NP - base > cnt ? cnt : D.NP - base));
+        for (int j = lane; j < cnt; j += 32) {
+          uint32_t c = 0;
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            if (q < npair) {
+              const uint32_t r = tile[q * kTile + j] - op[q];
+              c |= ((r >> 15) & 1u) << (2 * q);
+              c |= ((r >> 31) & 1u) << (2 * q + 1);
+            }
+          }
+          c &= (uint32_t)nb - 1u;  // an odd d's padding half is always >= and is dropped here
+          atomicAdd(&hist[c], j < pend ? 1u : (1u << 16));
+        }
+      }
     }
     __syncwarp();
-    uint64_t bv = 0;
-    int bj = 0;
-    for (int j = lane; j < nb; j += 32) {
-      uint64_t a, b;
-      if (wide) { a = hist[j]; b = hist[nb + j]; }
-      else { a = hist[j] & 0xFFFFu; b = hist[j] >> 16; }
-      const uint64_t num = ddks::numer(a, b, (uint64_t)D.NP, (uint64_t)D.NT);
-      if (num > bv) { bv = num; bj = j; }
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      const uint64_t v2 = __shfl_down_sync(0xffffffffu, bv, off);
-      const int j2 = __shfl_down_sync(0xffffffffu, bj, off);
-      if (v2 > bv || (v2 == bv && j2 < bj)) { bv = v2; bj = j2; }
-    }
-    if (lane == 0) {
-      best[D.off_pool + k] = bv;
-      bestj[D.off_pool + k] = bv ? bj : 0;
+    if (active) {
+      uint64_t bv = 0;
+      int bj = 0;
+      for (int j = lane; j < nb; j += 32) {
+        const uint32_t v = hist[j];
+        const uint64_t num = ddks::numer(v & 0xFFFFu, v >> 16, (uint64_t)D.NP, (uint64_t)D.NT);
+        if (num > bv) { bv = num; bj = j; }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const uint64_t v2 = __shfl_down_sync(0xffffffffu, bv, off);
+        const int j2 = __shfl_down_sync(0xffffffffu, bj, off);
+        if (v2 > bv || (v2 == bv && j2 < bj)) { bv = v2; bj = j2; }
+      }
+      if (lane == 0) {
+        best[D.off_pool + k] = bv;
+        bestj[D.off_pool + k] = bv ? bj : 0;
+      }
     }
     __syncwarp();
   }
@@ -284,8 +315,8 @@ k_batch_reduce(const BatchDesc* __restrict__ desc, const uint64_t* __restrict__ 
 }
 
 size_t unit_smem(int d) {
-  if (d <= 6) return (size_t)2 * (1u << d) * kThreads * 4 + (size_t)d * kTile * 4;
-  return (size_t)(kThreads / 32) * (1u << d) * 2 * 4;
+  if (d <= 6) return (size_t)(1u << d) * kThreads * 4 + (size_t)d * kTile * 4;
+  return (size_t)(kThreads / 32) * (1u << d) * 4 + (size_t)((d + 1) / 2) * kTile * 4;
 }
 
 }  // namespace
@@ -309,6 +340,9 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
   }
   int rc = DDKS_OK;
   if (!batched.empty()) {
+    // problems of one dimension form a group with its own persistent launch,
+    // its shared memory sized for that dimension
+    std::stable_sort(batched.begin(), batched.end(), [&](int a, int b) { return d[a] < d[b]; });
     const int nb = (int)batched.size();
     // stage host inputs into one device buffer
     size_t host_bytes = 0;
@@ -328,6 +362,8 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
     size_t hoff = 0;
     int64_t off_pool = 0, off_rank = 0, units = 0;
     size_t smem_rank = 0, smem_unit = 0;
+    struct Group { int d, first, count; int64_t units; double work; };
+    std::vector<Group> groups;
     for (int b = 0; b < nb; ++b) {
       const int i = batched[b];
       BatchDesc& D = hd[b];
@@ -354,10 +390,17 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
       const int64_t N = NP[i] + NT[i];
       D.off_pool = off_pool;
       D.off_rank = off_rank;
+      if (groups.empty() || groups.back().d != d[i]) {
+        groups.push_back(Group{d[i], b, 0, 0, 0.0});
+        units = 0;  // units are numbered within a group
+      }
       D.unit0 = units;
       off_pool += N;
       off_rank += N * d[i];
       units += (N + kOT - 1) / kOT;
+      groups.back().count += 1;
+      groups.back().units = units;
+      groups.back().work += (double)N * (double)N * d[i];
       for (int m = 0; m < d[i]; ++m) { cta_prob.push_back(b); cta_dim.push_back(m); }
       int P2 = 1;
       while (P2 < N) P2 <<= 1;
@@ -369,7 +412,7 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
     if ((rc = ctx->rank.reserve(ctx, 4 * (size_t)off_rank))) return rc;
     if ((rc = ctx->best.reserve(ctx, 8 * (size_t)off_pool))) return rc;
     if ((rc = ctx->bestj.reserve(ctx, 4 * (size_t)off_pool))) return rc;
-    if ((rc = ctx->batch_work.reserve(ctx, 8 * (3 * (size_t)nb + 4)))) return rc;
+    if ((rc = ctx->batch_work.reserve(ctx, 8 * (3 * (size_t)nb + 4 + kMaxGroups)))) return rc;
     if ((rc = ctx->flags.reserve(ctx, 64))) return rc;
     char* dd = (char*)ctx->batch_desc.ptr;
     BatchDesc* ddesc = (BatchDesc*)dd;
@@ -393,14 +436,19 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
     std::memcpy(hs + sizeof(BatchDesc) * nb + 4 * cta_prob.size(), cta_dim.data(), 4 * cta_dim.size());
     e = cudaMemcpyAsync(dd, hs, up, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "batch descriptors");
-    unsigned long long* work = (unsigned long long*)ctx->batch_work.ptr;
-    unsigned long long* res = work + 1;
+    unsigned long long* work = (unsigned long long*)ctx->batch_work.ptr;  // [kMaxGroups] unit counters
+    unsigned long long* res = work + kMaxGroups;
+    // the groups with the most work start first
+    std::vector<int> gorder(groups.size());
+    for (size_t g = 0; g < groups.size(); ++g) gorder[g] = (int)g;
+    std::stable_sort(gorder.begin(), gorder.end(),
+                     [&](int a, int b) { return groups[a].work > groups[b].work; });
     // the descriptors hold every shape and input address the kernels see
     GraphKey key;
     key.add(3).add((uint64_t)nb).add((uint64_t)units).add((uint64_t)smem_rank).add((uint64_t)smem_unit);
     key.add_bytes(hs, up);
     rc = ddks_graph_run(ctx, key.h, st, [&](cudaStream_t s) -> int {
-      cudaError_t ee = cudaMemsetAsync(work, 0, 8, s);
+      cudaError_t ee = cudaMemsetAsync(work, 0, 8 * kMaxGroups, s);
       if (ee == cudaSuccess) ee = cudaMemsetAsync(ctx->flags.ptr, 0, 4, s);
       if (ee == cudaSuccess)
         ee = cudaFuncSetAttribute(k_batch_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rank);
@@ -411,23 +459,26 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
       }
       if (ee == cudaSuccess)
         ee = cudaFuncSetAttribute(k_batch_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_unit);
-      if (ee == cudaSuccess) {
+      for (size_t gi = 0; gi < gorder.size() && ee == cudaSuccess; ++gi) {
+        const Group& G = groups[gorder[gi]];
+        const size_t sm_g = unit_smem(G.d);
         int blocks_per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_batch_count, kThreads, smem_unit);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_batch_count, kThreads, sm_g);
         if (blocks_per_sm < 1) blocks_per_sm = 1;
         int64_t grid = (int64_t)ctx->num_sms * blocks_per_sm;
-        if (grid > units) grid = units;
-        k_batch_count<<<(unsigned)grid, kThreads, smem_unit, s>>>(
-            ddesc, nb, units, (const uint32_t*)ctx->rank.ptr, work, (uint64_t*)ctx->best.ptr,
-            (int32_t*)ctx->bestj.ptr);
+        if (grid > G.units) grid = G.units;
+        k_batch_count<<<(unsigned)grid, kThreads, sm_g, s>>>(
+            ddesc + G.first, G.count, G.units, (const uint32_t*)ctx->rank.ptr, work + gorder[gi],
+            (uint64_t*)ctx->best.ptr, (int32_t*)ctx->bestj.ptr);
         ee = cudaGetLastError();
+        ctx->launches += 1;
       }
       if (ee == cudaSuccess) {
         k_batch_reduce<<<nb, 1024, 0, s>>>(ddesc, (const uint64_t*)ctx->best.ptr,
                                            (const int32_t*)ctx->bestj.ptr, res);
         ee = cudaGetLastError();
       }
-      ctx->launches += 3;
+      ctx->launches += 2;
       if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "batch");
       return DDKS_OK;
     });
