@@ -865,6 +865,10 @@ def run_batch(args):
     dev = [(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()) for P, T in probs]
     units = sum(float(len(P) + len(T)) ** 2 * P.shape[1] for P, T in probs)
     ctx = pkg.Context(device=0)
+    shapes = None
+    if not args.no_autotune:
+        tuned = ctx.autotune_batch(dev)  # the project's autotuner picks each dimension's tile shape
+        shapes = {str(d): list(tuned[d]) for d in sorted({P.shape[1] for P, _ in probs})}
     for _ in range(max(args.warmup, 3)):
         ref = ctx.batch_distance(dev)
     torch.cuda.synchronize()
@@ -894,7 +898,8 @@ def run_batch(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32 ranks (f32 input)",
         "data": "synthetic (seeded numpy PCG64)",
         "config": {"workload": "256 problems, NP,NT log-uniform [64,8192], d uniform 2..8, mixtures",
-                   "one_call_per_problem_tests_per_s": 256 / t1, "compares_per_s": units / tb},
+                   "one_call_per_problem_tests_per_s": 256 / t1, "compares_per_s": units / tb,
+                   "tile_shapes": shapes},
         "cpu_baseline": cpu}))
 
 

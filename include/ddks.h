@@ -192,15 +192,37 @@ int ddks_significance(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, i
                       int32_t model, void* stream, double* S, double* log_prod);
 
 /*
- * Many independent problems of different sizes and dimensions in one
- * persistent launch: CTAs pull (problem, origin tile) work units from a
- * device counter.  Arrays have count entries; P[i], T[i] follow the
- * conventions above (all of one dtype, all host or all device); out[i]
- * receives problem i's result.
+ * Many independent problems of different sizes and dimensions (Sec. 2.1's
+ * statistic for each) batched: problems of up to 16384 pooled points and
+ * d <= 11 are ranked in one launch and counted by one persistent launch per
+ * dimension present, whose CTAs pull (problem, origin tile) work units from a
+ * device counter; larger problems go through ddks_distance.  Arrays have
+ * count entries; P[i], T[i] follow the conventions above (all of one dtype,
+ * all host or all device); out[i] receives problem i's result.
  */
 int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, const int64_t* NP,
                         const void* const* T, const int64_t* NT, const int32_t* d,
                         int32_t dtype, void* stream, ddks_result* out);
+
+/*
+ * Tile shape of the batched units for problems of dimension d (1..11):
+ * origins per work unit (32, 64 or 128) and points per shared-memory tile
+ * (256, 512 or 1024); the default is 64 x 512.  DDKS_EINVAL otherwise.
+ * The results do not depend on the shape.  The paper has no counterpart.
+ */
+int ddks_set_batch_shape(ddks_ctx* ctx, int32_t d, int32_t origins_per_unit, int32_t points_per_tile);
+
+/*
+ * Autotuner of the batched launch: runs this batch with each of the nine tile
+ * shapes, times each dimension group's launch, keeps the fastest shape per
+ * dimension in the context, and checks that every shape gives identical
+ * results (DDKS_ECUDA if not).  shapes (optional host array of 12 x 2) gets
+ * (origins per unit, points per tile) per dimension.  The paper has no
+ * counterpart.
+ */
+int ddks_autotune_batch(ddks_ctx* ctx, int32_t count, const void* const* P, const int64_t* NP,
+                        const void* const* T, const int64_t* NT, const int32_t* d, int32_t dtype,
+                        void* stream, int32_t* shapes);
 
 /*
  * Serving: submit copies the inputs into library memory (the caller may free

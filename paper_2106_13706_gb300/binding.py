@@ -88,6 +88,8 @@ def load():
                                         ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]),
             "ddks_batch_distance": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp, R]),
+            "ddks_autotune_batch": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp, vp]),
+            "ddks_set_batch_shape": (i32, [vp, i32, i32, i32]),
             "ddks_submit": (i32, [vp, vp, i64, vp, i64, i32, i32, ctypes.POINTER(u64)]),
             "ddks_poll": (i32, [vp, u64, i32, R]),
             "ddks_ctx_stats": (i32, [vp, ctypes.POINTER(ddks_stats)]),
@@ -321,6 +323,38 @@ def ddks_significance(ctx, P, T, num_max, estimator=1, model=0, stream=None):
     return float(S.value), float(lp.value)
 
 
+def _batch_arrays(problems):
+    n = len(problems)
+    ps = (ctypes.c_void_p * n)()
+    ts = (ctypes.c_void_p * n)()
+    nps = (ctypes.c_int64 * n)()
+    nts = (ctypes.c_int64 * n)()
+    ds = (ctypes.c_int32 * n)()
+    keep = []
+    dtype = None
+    for i, (P, T) in enumerate(problems):
+        p, NP, t, NT, d, dt, k = _pair(P, T)
+        if dtype is None:
+            dtype = dt
+        elif dtype != dt:
+            raise ValueError("all problems of a batch must share one dtype")
+        ps[i], ts[i], nps[i], nts[i], ds[i] = p, t, NP, NT, d
+        keep.append(k)
+    return n, ps, nps, ts, nts, ds, dtype or 0, keep
+
+
+def ddks_autotune_batch(ctx, problems, stream=None):
+    """Tile shape per dimension ({d: (origins per unit, points per tile)}) chosen for this batch."""
+    n, ps, nps, ts, nts, ds, dtype, keep = _batch_arrays(problems)
+    shapes = (ctypes.c_int32 * 24)()
+    _check(load().ddks_autotune_batch(ctx, n, ps, nps, ts, nts, ds, dtype, _stream(stream), shapes), ctx)
+    return {k: (int(shapes[2 * k]), int(shapes[2 * k + 1])) for k in range(1, 12)}
+
+
+def ddks_set_batch_shape(ctx, d, origins_per_unit, points_per_tile):
+    _check(load().ddks_set_batch_shape(ctx, int(d), int(origins_per_unit), int(points_per_tile)), ctx)
+
+
 def ddks_batch_distance(ctx, problems, stream=None):
     n = len(problems)
     ps = (ctypes.c_void_p * n)()
@@ -452,6 +486,12 @@ class Context:
 
     def batch_distance(self, problems, stream=None):
         return ddks_batch_distance(self.h, problems, stream)
+
+    def autotune_batch(self, problems, stream=None):
+        return ddks_autotune_batch(self.h, problems, stream)
+
+    def set_batch_shape(self, d, origins_per_unit, points_per_tile):
+        ddks_set_batch_shape(self.h, d, origins_per_unit, points_per_tile)
 
     def submit(self, P, T):
         return ddks_submit(self.h, P, T)

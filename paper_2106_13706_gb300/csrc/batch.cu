@@ -34,8 +34,10 @@ namespace {
 constexpr int kMaxBatchN = 16384;   // so NP, NT < 65536: P and T counts share one 32-bit bin
 constexpr int kMaxGroups = 16;      // dimensions 1..11 of the batched problems
 constexpr int kThreads = 256;
-constexpr int kOT = 64;        // origins per work unit
-constexpr int kTile = 512;     // points per staged tile
+// tile shapes of the batched units, per dimension group (ddks_autotune_batch):
+// origins per work unit (32, 64 or 128) and points per staged tile
+constexpr int kOT = 64;        // default origins per work unit
+constexpr int kTile = 512;     // default points per staged tile
 
 DDKS_DEV bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
   return ka < kb || (ka == kb && ia < ib);
@@ -97,28 +99,42 @@ k_batch_rank(const BatchDesc* __restrict__ desc, const int* __restrict__ cta_pro
   }
 }
 
-// lane-private histograms: 64 origins x 4 slices
+// The two compare bits of a packed pair difference r (bit 15: low half,
+// bit 31: high half) as code bits 2q and 2q + 1: two shifts and one 3-input op.
+DDKS_DEV uint32_t pair_bits(uint32_t r, int q) {
+  return ((r >> (15 - 2 * q)) & (1u << (2 * q))) | ((r >> (30 - 2 * q)) & (2u << (2 * q)));
+}
+
+// lane-private histograms: OT origins x (kThreads / OT) slices of the points
 template <int DD>
 DDKS_DEV void unit_lane(const BatchDesc& D, const uint32_t* __restrict__ rk, int64_t o0,
-                        uint32_t* sm, uint64_t* best, int32_t* bestj) {
+                        uint32_t* sm, uint64_t* best, int32_t* bestj, int OT, int PT) {
   constexpr int NB = 1 << DD;
-  constexpr int S = kThreads / kOT;
+  const int S = kThreads / OT;
   const int64_t N = D.NP + D.NT;
   const int tid = threadIdx.x, ol = tid / S, s = tid - ol * S;
+  constexpr int NPR = (DD + 1) / 2;              // dimension pairs
   uint32_t* hist = sm;                          // [NB][kThreads]: P count | T count << 16
-  uint32_t* tile = sm + NB * kThreads;          // [DD][kTile]
+  uint32_t* tile = sm + NB * kThreads;          // [NPR][PT] packed 16-bit rank pairs | 0x80008000
   const int64_t k = o0 + ol;
   const bool active = k < N;
-  uint32_t o[DD];
+  // the origin's ranks as packed pairs (see unit_warp: one subtract, two compares)
+  uint32_t op[NPR];
 #pragma unroll
-  for (int m = 0; m < DD; ++m) o[m] = active ? rk[(int64_t)m * N + k] : 0u;
+  for (int q = 0; q < NPR; ++q) {
+    const uint32_t lo = active ? rk[(int64_t)(2 * q) * N + k] : 0u;
+    const uint32_t hi = (active && 2 * q + 1 < DD) ? rk[(int64_t)(2 * q + 1) * N + k] : 0u;
+    op[q] = lo | (hi << 16);
+  }
   for (int j = 0; j < NB; ++j) hist[j * kThreads + tid] = 0;
-  for (int64_t base = 0; base < N; base += kTile) {
-    const int cnt = (int)((N - base) < kTile ? (N - base) : kTile);
+  for (int64_t base = 0; base < N; base += PT) {
+    const int cnt = (int)((N - base) < PT ? (N - base) : PT);
     __syncthreads();
-    for (int e = tid; e < DD * cnt; e += kThreads) {
-      const int m = e / cnt, j = e - m * cnt;
-      tile[m * kTile + j] = rk[(int64_t)m * N + base + j];
+    for (int e = tid; e < NPR * cnt; e += kThreads) {
+      const int q = e / cnt, j = e - q * cnt;
+      const uint32_t lo = rk[(int64_t)(2 * q) * N + base + j];
+      const uint32_t hi = 2 * q + 1 < DD ? rk[(int64_t)(2 * q + 1) * N + base + j] : 0u;
+      tile[q * PT + j] = (lo | (hi << 16)) | 0x80008000u;
     }
     __syncthreads();
     int pend = (int)(D.NP - base);
@@ -126,7 +142,8 @@ DDKS_DEV void unit_lane(const BatchDesc& D, const uint32_t* __restrict__ rk, int
     for (int j = s; j < cnt; j += S) {
       uint32_t c = 0;
 #pragma unroll
-      for (int m = 0; m < DD; ++m) c |= (uint32_t)(tile[m * kTile + j] >= o[m]) << m;
+      for (int q = 0; q < NPR; ++q) c |= pair_bits(tile[q * PT + j] - op[q], q);
+      c &= (uint32_t)NB - 1u;  // an odd DD's padding half is dropped
       atomicAdd(&hist[c * kThreads + tid], j < pend ? 1u : (1u << 16));
     }
   }
@@ -163,38 +180,41 @@ DDKS_DEV void unit_lane(const BatchDesc& D, const uint32_t* __restrict__ rk, int
 // Point tiles are staged in shared memory once for the 8 warps, ranks packed
 // as 16-bit pairs (N <= 16384): (x | 0x8000) - o keeps each half apart and its
 // bit 15 is [x >= o], so one subtract compares two dimensions.
+template <int DD>
 DDKS_DEV void unit_warp(const BatchDesc& D, const uint32_t* __restrict__ rk, int64_t o0,
-                        uint32_t* sm, uint64_t* best, int32_t* bestj) {
-  const int d = D.d, nb = 1 << d, npair = (d + 1) >> 1;
+                        uint32_t* sm, uint64_t* best, int32_t* bestj, int OT, int PT) {
+  constexpr int d = DD, nb = 1 << DD, npair = (DD + 1) >> 1;
   const int64_t N = D.NP + D.NT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int kW = kThreads / 32;
-  uint32_t* hist = sm + (size_t)warp * nb;              // [kW][nb]
-  uint32_t* tile = sm + (size_t)kW * nb;                // [npair][kTile] packed pairs
-  for (int round = 0; round < kOT / kW; ++round) {
+  // two copies of the warp's histogram (even and odd lanes) halve the
+  // same-address collisions of its increments
+  uint32_t* hist = sm + (size_t)warp * 2 * nb;          // [kW][2][nb]
+  uint32_t* tile = sm + (size_t)kW * 2 * nb;            // [npair][PT] packed pairs
+  for (int round = 0; round < OT / kW; ++round) {
     const int64_t k = o0 + round * kW + warp;
     const bool active = k < N;
     // the origin's ranks as packed pairs; an odd last dimension is paired
     // with a high half that every point passes
-    uint32_t op[6];
+    uint32_t op[npair];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
+    for (int q = 0; q < npair; ++q) {
       uint32_t lo = 0, hi = 0;
-      if (active && q < npair) {
+      if (active) {
         lo = rk[(int64_t)(2 * q) * N + k];
         hi = 2 * q + 1 < d ? rk[(int64_t)(2 * q + 1) * N + k] : 0u;
       }
       op[q] = lo | (hi << 16);
     }
-    for (int j = lane; j < nb; j += 32) hist[j] = 0;
-    for (int64_t base = 0; base < N; base += kTile) {
-      const int cnt = (int)((N - base) < kTile ? (N - base) : kTile);
+    for (int j = lane; j < 2 * nb; j += 32) hist[j] = 0;
+    for (int64_t base = 0; base < N; base += PT) {
+      const int cnt = (int)((N - base) < PT ? (N - base) : PT);
       __syncthreads();  // the previous tile is consumed (and the histograms are zeroed)
       for (int e = threadIdx.x; e < npair * cnt; e += kThreads) {
         const int q = e / cnt, j = e - q * cnt;
         const uint32_t lo = rk[(int64_t)(2 * q) * N + base + j];
         const uint32_t hi = 2 * q + 1 < d ? rk[(int64_t)(2 * q + 1) * N + base + j] : 0u;
-        tile[q * kTile + j] = (lo | (hi << 16)) | 0x80008000u;
+        tile[q * PT + j] = (lo | (hi << 16)) | 0x80008000u;
       }
       __syncthreads();
       if (active) {
@@ -202,15 +222,10 @@ DDKS_DEV void unit_warp(const BatchDesc& D, const uint32_t* __restrict__ rk, int
         for (int j = lane; j < cnt; j += 32) {
           uint32_t c = 0;
 #pragma unroll
-          for (int q = 0; q < 6; ++q) {
-            if (q < npair) {
-              const uint32_t r = tile[q * kTile + j] - op[q];
-              c |= ((r >> 15) & 1u) << (2 * q);
-              c |= ((r >> 31) & 1u) << (2 * q + 1);
-            }
-          }
+          for (int q = 0; q < npair; ++q) c |= pair_bits(tile[q * PT + j] - op[q], q);
           c &= (uint32_t)nb - 1u;  // an odd d's padding half is always >= and is dropped here
-          atomicAdd(&hist[c], j < pend ? 1u : (1u << 16));
+          // (warp-aggregated increments by match.any measured slower: 13.1 vs 9.3 ms per batch)
+          atomicAdd(&hist[(lane & 1) * nb + c], j < pend ? 1u : (1u << 16));
         }
       }
     }
@@ -219,8 +234,9 @@ DDKS_DEV void unit_warp(const BatchDesc& D, const uint32_t* __restrict__ rk, int
       uint64_t bv = 0;
       int bj = 0;
       for (int j = lane; j < nb; j += 32) {
-        const uint32_t v = hist[j];
-        const uint64_t num = ddks::numer(v & 0xFFFFu, v >> 16, (uint64_t)D.NP, (uint64_t)D.NT);
+        const uint32_t v0 = hist[j], v1 = hist[nb + j];
+        const uint64_t num =
+            ddks::numer((v0 & 0xFFFFu) + (v1 & 0xFFFFu), (v0 >> 16) + (v1 >> 16), (uint64_t)D.NP, (uint64_t)D.NT);
         if (num > bv) { bv = num; bj = j; }
       }
       for (int off = 16; off > 0; off >>= 1) {
@@ -241,7 +257,7 @@ DDKS_DEV void unit_warp(const BatchDesc& D, const uint32_t* __restrict__ rk, int
 __global__ void __launch_bounds__(kThreads)
 k_batch_count(const BatchDesc* __restrict__ desc, int count, int64_t total_units,
               const uint32_t* __restrict__ rank, unsigned long long* __restrict__ next_unit,
-              uint64_t* __restrict__ best, int32_t* __restrict__ bestj) {
+              uint64_t* __restrict__ best, int32_t* __restrict__ bestj, int OT, int PT) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ long long unit;
   for (;;) {
@@ -257,16 +273,20 @@ k_batch_count(const BatchDesc* __restrict__ desc, int count, int64_t total_units
       if (desc[mid].unit0 <= u) lo = mid; else hi = mid - 1;
     }
     const BatchDesc D = desc[lo];
-    const int64_t o0 = (u - D.unit0) * kOT;
+    const int64_t o0 = (u - D.unit0) * OT;
     const uint32_t* rk = rank + D.off_rank;
     switch (D.d) {
-      case 1: unit_lane<1>(D, rk, o0, sm, best, bestj); break;
-      case 2: unit_lane<2>(D, rk, o0, sm, best, bestj); break;
-      case 3: unit_lane<3>(D, rk, o0, sm, best, bestj); break;
-      case 4: unit_lane<4>(D, rk, o0, sm, best, bestj); break;
-      case 5: unit_lane<5>(D, rk, o0, sm, best, bestj); break;
-      case 6: unit_lane<6>(D, rk, o0, sm, best, bestj); break;
-      default: unit_warp(D, rk, o0, sm, best, bestj); break;
+      case 1: unit_lane<1>(D, rk, o0, sm, best, bestj, OT, PT); break;
+      case 2: unit_lane<2>(D, rk, o0, sm, best, bestj, OT, PT); break;
+      case 3: unit_lane<3>(D, rk, o0, sm, best, bestj, OT, PT); break;
+      case 4: unit_lane<4>(D, rk, o0, sm, best, bestj, OT, PT); break;
+      case 5: unit_lane<5>(D, rk, o0, sm, best, bestj, OT, PT); break;
+      case 6: unit_lane<6>(D, rk, o0, sm, best, bestj, OT, PT); break;
+      case 7: unit_warp<7>(D, rk, o0, sm, best, bestj, OT, PT); break;
+      case 8: unit_warp<8>(D, rk, o0, sm, best, bestj, OT, PT); break;
+      case 9: unit_warp<9>(D, rk, o0, sm, best, bestj, OT, PT); break;
+      case 10: unit_warp<10>(D, rk, o0, sm, best, bestj, OT, PT); break;
+      default: unit_warp<11>(D, rk, o0, sm, best, bestj, OT, PT); break;
     }
   }
 }
@@ -314,9 +334,9 @@ k_batch_reduce(const BatchDesc* __restrict__ desc, const uint64_t* __restrict__ 
   }
 }
 
-size_t unit_smem(int d) {
-  if (d <= 6) return (size_t)(1u << d) * kThreads * 4 + (size_t)d * kTile * 4;
-  return (size_t)(kThreads / 32) * (1u << d) * 4 + (size_t)((d + 1) / 2) * kTile * 4;
+size_t unit_smem(int d, int PT) {
+  if (d <= 6) return (size_t)(1u << d) * kThreads * 4 + (size_t)((d + 1) / 2) * PT * 4;
+  return (size_t)(kThreads / 32) * 2 * (1u << d) * 4 + (size_t)((d + 1) / 2) * PT * 4;
 }
 
 }  // namespace
@@ -397,7 +417,8 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
       D.unit0 = units;
       off_pool += N;
       off_rank += N * d[i];
-      units += (N + kOT - 1) / kOT;
+      const int OT = ctx->batch_ot[d[i]];
+      units += (N + OT - 1) / OT;
       groups.back().count += 1;
       groups.back().units = units;
       groups.back().work += (double)N * (double)N * d[i];
@@ -405,7 +426,7 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
       int P2 = 1;
       while (P2 < N) P2 <<= 1;
       smem_rank = std::max(smem_rank, (size_t)P2 * 12);
-      smem_unit = std::max(smem_unit, unit_smem(d[i]));
+      smem_unit = std::max(smem_unit, unit_smem(d[i], ctx->batch_pt[d[i]]));
     }
     const size_t desc_bytes = sizeof(BatchDesc) * nb + 8 * cta_prob.size() + 64;
     if ((rc = ctx->batch_desc.reserve(ctx, desc_bytes))) return rc;
@@ -446,7 +467,8 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
     // the descriptors hold every shape and input address the kernels see
     GraphKey key;
     key.add(3).add((uint64_t)nb).add((uint64_t)units).add((uint64_t)smem_rank).add((uint64_t)smem_unit);
-    key.add_bytes(hs, up);
+    key.add_bytes(hs, up).add_bytes(ctx->batch_ot, sizeof ctx->batch_ot).add_bytes(ctx->batch_pt, sizeof ctx->batch_pt);
+    if (ctx->batch_timing) key.add(0xB7);  // tuning runs directly (events between the launches)
     rc = ddks_graph_run(ctx, key.h, st, [&](cudaStream_t s) -> int {
       cudaError_t ee = cudaMemsetAsync(work, 0, 8 * kMaxGroups, s);
       if (ee == cudaSuccess) ee = cudaMemsetAsync(ctx->flags.ptr, 0, 4, s);
@@ -461,7 +483,14 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
         ee = cudaFuncSetAttribute(k_batch_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_unit);
       for (size_t gi = 0; gi < gorder.size() && ee == cudaSuccess; ++gi) {
         const Group& G = groups[gorder[gi]];
-        const size_t sm_g = unit_smem(G.d);
+        const int OT = ctx->batch_ot[G.d], PT = ctx->batch_pt[G.d];
+        const size_t sm_g = unit_smem(G.d, PT);
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        if (ctx->batch_timing) {
+          cudaEventCreate(&ev0);
+          cudaEventCreate(&ev1);
+          cudaEventRecord(ev0, s);
+        }
         int blocks_per_sm = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_batch_count, kThreads, sm_g);
         if (blocks_per_sm < 1) blocks_per_sm = 1;
@@ -469,9 +498,18 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
         if (grid > G.units) grid = G.units;
         k_batch_count<<<(unsigned)grid, kThreads, sm_g, s>>>(
             ddesc + G.first, G.count, G.units, (const uint32_t*)ctx->rank.ptr, work + gorder[gi],
-            (uint64_t*)ctx->best.ptr, (int32_t*)ctx->bestj.ptr);
+            (uint64_t*)ctx->best.ptr, (int32_t*)ctx->bestj.ptr, OT, PT);
         ee = cudaGetLastError();
         ctx->launches += 1;
+        if (ctx->batch_timing) {
+          cudaEventRecord(ev1, s);
+          cudaEventSynchronize(ev1);
+          float ms = 0;
+          cudaEventElapsedTime(&ms, ev0, ev1);
+          ctx->batch_group_ms[G.d] = ms;
+          cudaEventDestroy(ev0);
+          cudaEventDestroy(ev1);
+        }
       }
       if (ee == cudaSuccess) {
         k_batch_reduce<<<nb, 1024, 0, s>>>(ddesc, (const uint64_t*)ctx->best.ptr,
@@ -508,5 +546,70 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
     rc = ddks_distance(ctx, P[i], NP[i], T[i], NT[i], d[i], dtype, stream, &out[i]);
     if (rc) return rc;
   }
+  return DDKS_OK;
+}
+
+int ddks_set_batch_shape(ddks_ctx* ctx, int32_t d, int32_t origins_per_unit, int32_t points_per_tile) {
+  if (!ctx || d < 1 || d > 11) return DDKS_EINVAL;
+  if (origins_per_unit != 32 && origins_per_unit != 64 && origins_per_unit != 128) return DDKS_EINVAL;
+  if (points_per_tile != 256 && points_per_tile != 512 && points_per_tile != 1024) return DDKS_EINVAL;
+  ctx->batch_ot[d] = origins_per_unit;
+  ctx->batch_pt[d] = points_per_tile;
+  return DDKS_OK;
+}
+
+// Times every tile shape on this batch, per dimension group, keeps the fastest
+// for each dimension present and checks that every shape gives the same
+// results.  shapes (optional): [12][2] (origins per unit, points per tile).
+int ddks_autotune_batch(ddks_ctx* ctx, int32_t count, const void* const* P, const int64_t* NP,
+                        const void* const* T, const int64_t* NT, const int32_t* d, int32_t dtype, void* stream,
+                        int32_t* shapes) {
+  if (!ctx || count < 1 || !d) return DDKS_EINVAL;
+  int ot0[12], pt0[12];
+  std::memcpy(ot0, ctx->batch_ot, sizeof ot0);
+  std::memcpy(pt0, ctx->batch_pt, sizeof pt0);
+  float best_ms[12];
+  int best_ot[12], best_pt[12];
+  for (int k = 0; k < 12; ++k) { best_ms[k] = 3.0e38f; best_ot[k] = ot0[k]; best_pt[k] = pt0[k]; }
+  std::vector<ddks_result> ref((size_t)count), got((size_t)count);
+  bool have_ref = false;
+  int rc = DDKS_OK;
+  ctx->batch_timing = true;
+  for (int ot : {32, 64, 128}) {
+    for (int pt : {256, 512, 1024}) {
+      for (int k = 1; k < 12; ++k) { ctx->batch_ot[k] = ot; ctx->batch_pt[k] = pt; }
+      for (int rep = 0; rep < 2 && rc == DDKS_OK; ++rep)  // the second run is timed warm
+        rc = ddks_batch_distance(ctx, count, P, NP, T, NT, d, dtype, stream, got.data());
+      if (rc) break;
+      if (!have_ref) {
+        ref = got;
+        have_ref = true;
+      } else {
+        for (int i = 0; i < count; ++i)
+          if (got[i].num_max != ref[i].num_max || got[i].argmax_origin != ref[i].argmax_origin ||
+              got[i].argmax_orthant != ref[i].argmax_orthant) {
+            ctx->last_err = "batch autotune: tile shapes disagree";
+            rc = DDKS_ECUDA;
+          }
+      }
+      if (rc) break;
+      for (int k = 1; k < 12; ++k) {
+        const float ms = ctx->batch_group_ms[k];
+        if (ms > 0.0f && ms < best_ms[k]) { best_ms[k] = ms; best_ot[k] = ot; best_pt[k] = pt; }
+        ctx->batch_group_ms[k] = 0.0f;
+      }
+    }
+    if (rc) break;
+  }
+  ctx->batch_timing = false;
+  if (rc) {
+    std::memcpy(ctx->batch_ot, ot0, sizeof ot0);
+    std::memcpy(ctx->batch_pt, pt0, sizeof pt0);
+    return rc;
+  }
+  std::memcpy(ctx->batch_ot, best_ot, sizeof best_ot);
+  std::memcpy(ctx->batch_pt, best_pt, sizeof best_pt);
+  if (shapes)
+    for (int k = 0; k < 12; ++k) { shapes[2 * k] = ctx->batch_ot[k]; shapes[2 * k + 1] = ctx->batch_pt[k]; }
   return DDKS_OK;
 }

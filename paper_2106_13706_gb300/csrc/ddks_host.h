@@ -80,6 +80,12 @@ struct ddks_ctx {
   std::string tune_cache_path;
   std::map<std::string, ddks_plan> tune;
   std::mutex tune_mu;
+  // batched launch: tile shapes per dimension (origins per work unit, points
+  // per staged tile), set by ddks_autotune_batch; per-group kernel times when tuning
+  int batch_ot[12] = {64, 64, 64, 64, 64, 64, 64, 64, 64, 64, 64, 64};
+  int batch_pt[12] = {512, 512, 512, 512, 512, 512, 512, 512, 512, 512, 512, 512};
+  bool batch_timing = false;
+  float batch_group_ms[12] = {};
   // serving
   ServeState* serve = nullptr;  // owned; freed by ddks_serve_shutdown
   // graph replay (graph.cu); buf_gen counts scratch reallocations

@@ -30,7 +30,7 @@ void drop_exec(GraphEntry& g) {
 int ddks_graph_begin(ddks_ctx* ctx, uint64_t key, cudaStream_t st, cudaStream_t* run_st, int* mode) {
   *mode = 0;
   *run_st = st;
-  if (!ctx->cfg.graphs || ctx->stage_timing) return DDKS_OK;
+  if (!ctx->cfg.graphs || ctx->stage_timing || ctx->batch_timing) return DDKS_OK;
   const uint64_t tick = ++ctx->graph_tick;
   GraphEntry* g = find(ctx, key);
   if (g && g->exec && g->gen == ctx->buf_gen) {

@@ -53,3 +53,36 @@ def test_config4_256_uneven(torch):
     for i in rng.choice(256, size=24, replace=False):
         P, T = probs[i]
         assert _key(got[i]) == _key(orc.ddks(P, T))
+
+
+SHAPES = [(ot, pt) for ot in (32, 64, 128) for pt in (256, 512, 1024)]
+
+
+def test_every_tile_shape_matches_oracle(torch):
+    # the batched units' tile shapes (origins per unit, points per staged
+    # tile) change the work split, never the result; ragged tails everywhere
+    probs = wl.uneven_problems(seed=5, count=22, n_lo=20, n_hi=1300, dims=tuple(range(1, 12)))
+    refs = [orc.ddks(P, T) for P, T in probs]
+    dev = [(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()) for P, T in probs]
+    with pkg.Context(device=0) as c:
+        for ot, pt in SHAPES:
+            for d in range(1, 12):
+                c.set_batch_shape(d, ot, pt)
+            got = c.batch_distance(dev)
+            for g, r in zip(got, refs):
+                assert _key(g) == _key(r), (ot, pt)
+        with pytest.raises(pkg.DdksError):
+            c.set_batch_shape(3, 48, 512)
+
+
+def test_autotuned_shapes_and_results(torch):
+    probs = wl.uneven_problems(seed=6, count=40, n_lo=64, n_hi=3000, dims=(2, 3, 5, 8))
+    refs = [orc.ddks(P, T) for P, T in probs]
+    dev = [(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()) for P, T in probs]
+    with pkg.Context(device=0) as c:
+        shapes = c.autotune_batch(dev)
+        for d in (2, 3, 5, 8):
+            assert shapes[d][0] in (32, 64, 128) and shapes[d][1] in (256, 512, 1024)
+        for _ in range(2):  # direct, then captured
+            got = c.batch_distance(dev)
+            assert [_key(g) for g in got] == [_key(r) for r in refs]
