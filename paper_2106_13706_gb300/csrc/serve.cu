@@ -1,13 +1,14 @@
 // serve.cu -- continuous batching of two-sample ddKS requests.
 //
-// ddks_submit copies a request's points into library-owned host memory and
-// queues it.  Worker threads (two, each with its own internal context and
+// ddks_submit copies a request's points into library-owned device memory
+// (stream-ordered allocations from the device's memory pool) and queues it.  Worker threads (two, each with its own internal context and
 // stream) repeatedly admit queued requests in arrival order while the sum of
 // the admitted requests' device footprints stays within the HBM budget and the
 // batch stays within max_batch, run the admitted requests as one batched
 // launch (batch.cu: one persistent kernel over all their work units), and
 // publish the results.  Requests that arrive while a batch is on the GPU join
-// the next one; with two workers two batches overlap on the device.  A
+// the next one; with two workers two batches overlap on the device.  A batch
+// of one request runs through the single-problem path (ddks_distance).  A
 // request whose footprint alone exceeds the budget is refused at submit with
 // DDKS_ENOMEM.  ddks_poll reads a result, optionally waiting a bounded time.
 // No device code waits on the host: the only waits are host condition
@@ -29,7 +30,8 @@ namespace {
 
 struct Request {
   uint64_t ticket = 0;
-  std::vector<char> P, T;
+  void* P = nullptr;  // device copies of the inputs, freed by the worker that served them
+  void* T = nullptr;
   int64_t NP = 0, NT = 0;
   int32_t d = 0, dtype = 0;
   uint64_t footprint = 0;
@@ -53,6 +55,8 @@ struct ServeState {
   std::vector<std::thread> workers;
   std::vector<ddks_ctx*> wctx;
   std::vector<cudaStream_t> streams;
+  cudaStream_t sub_st = nullptr;  // input copies of ddks_submit
+  std::mutex sub_mu;
 };
 
 static uint64_t request_footprint(int64_t NP, int64_t NT, int32_t d, int32_t dtype) {
@@ -97,8 +101,8 @@ static void worker_loop(ddks_ctx* owner, int w) {
       std::vector<std::shared_ptr<Request>> members;
       for (auto& r : batch)
         if (r->dtype == dt) {
-          Ps.push_back(r->P.data());
-          Ts.push_back(r->T.data());
+          Ps.push_back(r->P);
+          Ts.push_back(r->T);
           NPs.push_back(r->NP);
           NTs.push_back(r->NT);
           ds.push_back(r->d);
@@ -106,8 +110,11 @@ static void worker_loop(ddks_ctx* owner, int w) {
         }
       if (members.empty()) continue;
       std::vector<ddks_result> out(members.size());
-      int rc = ddks_batch_distance(ctx, (int32_t)members.size(), Ps.data(), NPs.data(), Ts.data(),
-                                   NTs.data(), ds.data(), dt, st, out.data());
+      // one request: the single-problem path; several: one batched launch
+      int rc = members.size() == 1
+                   ? ddks_distance(ctx, Ps[0], NPs[0], Ts[0], NTs[0], ds[0], dt, st, out.data())
+                   : ddks_batch_distance(ctx, (int32_t)members.size(), Ps.data(), NPs.data(), Ts.data(),
+                                         NTs.data(), ds.data(), dt, st, out.data());
       if (rc != DDKS_OK) {
         // find the failing members one by one so one bad request does not fail the rest
         for (size_t i = 0; i < members.size(); ++i) {
@@ -117,14 +124,16 @@ static void worker_loop(ddks_ctx* owner, int w) {
           out[i].status = r1;
         }
       }
+      // the calls above synchronised st: the inputs can go back to the pool
+      for (auto& m : members) {
+        cudaFreeAsync(m->P, st);
+        cudaFreeAsync(m->T, st);
+      }
       std::lock_guard<std::mutex> g(S->mu);
       for (size_t i = 0; i < members.size(); ++i) {
         members[i]->res = out[i];
         members[i]->status = out[i].status;
-        members[i]->P.clear();
-        members[i]->P.shrink_to_fit();
-        members[i]->T.clear();
-        members[i]->T.shrink_to_fit();
+        members[i]->P = members[i]->T = nullptr;
       }
     }
     {
@@ -163,6 +172,15 @@ static int serve_start(ddks_ctx* ctx) {
     S->wctx.push_back(c);
     S->streams.push_back(st);
   }
+  cudaError_t e = cudaStreamCreateWithFlags(&S->sub_st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    for (size_t i = 0; i < S->wctx.size(); ++i) {
+      cudaStreamDestroy(S->streams[i]);
+      ddks_ctx_destroy(S->wctx[i]);
+    }
+    delete S;
+    return ctx_cuda_fail(ctx, e, "cudaStreamCreate");
+  }
   ctx->serve = S;
   for (int w = 0; w < kWorkers; ++w) S->workers.emplace_back(worker_loop, ctx, w);
   return DDKS_OK;
@@ -178,6 +196,12 @@ void ddks_serve_shutdown(ddks_ctx* ctx) {
   S->cv_work.notify_all();
   S->cv_done.notify_all();
   for (auto& t : S->workers) t.join();
+  for (auto& r : S->pending) {  // never admitted: their inputs go back to the pool
+    cudaFreeAsync(r->P, S->sub_st);
+    cudaFreeAsync(r->T, S->sub_st);
+  }
+  cudaStreamSynchronize(S->sub_st);
+  cudaStreamDestroy(S->sub_st);
   for (size_t i = 0; i < S->wctx.size(); ++i) {
     cudaStreamDestroy(S->streams[i]);
     ddks_ctx_destroy(S->wctx[i]);
@@ -222,12 +246,24 @@ int ddks_submit(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t
     return DDKS_ENOMEM;
   }
   const size_t es = dtype == DDKS_F64 ? 8 : 4;
-  // copy the inputs (host or device) so the caller may free them on return
-  r->P.resize(es * (size_t)NP * d);
-  r->T.resize(es * (size_t)NT * d);
-  cudaError_t e = cudaMemcpy(r->P.data(), P, r->P.size(), cudaMemcpyDefault);
-  if (e == cudaSuccess) e = cudaMemcpy(r->T.data(), T, r->T.size(), cudaMemcpyDefault);
-  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "submit copy");
+  const size_t bP = es * (size_t)NP * d, bT = es * (size_t)NT * d;
+  // copy the inputs (host or device) to the device so the caller may free
+  // them on return; the copies are complete when submit returns
+  {
+    std::lock_guard<std::mutex> g(S->sub_mu);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = cudaMallocAsync(&r->P, bP, S->sub_st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&r->T, bT, S->sub_st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r->P, P, bP, cudaMemcpyDefault, S->sub_st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r->T, T, bT, cudaMemcpyDefault, S->sub_st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->sub_st);
+    if (e != cudaSuccess) {
+      if (r->P) cudaFreeAsync(r->P, S->sub_st);
+      if (r->T) cudaFreeAsync(r->T, S->sub_st);
+      cudaStreamSynchronize(S->sub_st);
+      return ctx_cuda_fail(ctx, e, "submit copy");
+    }
+  }
   {
     std::lock_guard<std::mutex> g(S->mu);
     r->ticket = S->next_ticket++;
