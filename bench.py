@@ -155,6 +155,38 @@ def peak_lane_ops(torch, dev, sm_max_mhz):
     return sms * 128 * mhz * 1e6, sms, mhz
 
 
+def pipe_mix(torch, dev, sm_max_mhz, path, d, NP, NT, origins, count_ms):
+    """Instruction-mix roofline of the bit-sliced count kernel (register path,
+    d = 2..4): its algorithmic operations per launch on each pipe against the
+    pipe's rate, and the count stage's time against the slowest pipe.
+
+    Per origin and group of 32 points: 7 (d - 1) three-input logic ops for the
+    compares and one AND per subset of two or more of dimensions 1..d-1 (ALU
+    pipe, 64 lanes/clk/SM), one popcount (XU pipe, 32 lanes/clk/SM, measured)
+    and one add (FMA pipe, 64 lanes/clk/SM) per non-empty subset; the shared
+    group loads add 2 (d - 1) 16-byte broadcast loads per 2 origins.  Issue:
+    one warp instruction per clock per scheduler (4 per SM)."""
+    if path != "register" or not 2 <= d <= 4:
+        return None
+    p = torch.cuda.get_device_properties(dev)
+    f = (sm_max_mhz or 2070.0) * 1e6
+    sms = p.multi_processor_count
+    ds = d - 1
+    subsets = (1 << ds) - 1
+    og = float(origins) * ((NP + 31) // 32 + (NT + 31) // 32)  # origin x group-of-32 units
+    alu = og * (7 * ds + (subsets - ds))
+    xu = og * subsets
+    fma = og * subsets
+    lds = og * ds  # two 16-byte loads per dimension, shared by two origins
+    t = {"alu": alu / (sms * 64 * f), "xu": xu / (sms * 32 * f), "fma": fma / (sms * 64 * f),
+         "issue": (alu + xu + fma + lds) / 32 / (sms * 4 * f)}
+    bound = max(t, key=t.get)
+    return {"lane_ops_per_launch": {"alu": alu, "xu": xu, "fma": fma},
+            "pipe_ms": {k: v * 1e3 for k, v in t.items()}, "bound_pipe": bound,
+            "frac_of_bound": t[bound] * 1e3 / count_ms,
+            "note": "count stage (re-rank pack + count kernel) time against the count kernel's slowest pipe"}
+
+
 def peak_compares(torch, dev, sm_max_mhz, path, d):
     """Compare-rate roofline of the count kernel's path, in compares/s.
 
@@ -321,6 +353,8 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": load_traffic({"cfg2": "count_d4_20k"}.get(args.workload, "")),
                 "kernel": "orthant count stage (re-rank pack + count + fused reduction)", "kernel_ms": cnt,
                 "peak_basis": basis, "compares_per_lane_op": achieved / lane_peak,
+                "pipe_mix": pipe_mix(torch, local, clocks.get("sm_max_mhz"), path_name, d, NP, NT,
+                                     (o_end - o_begin) if shard == "origins" else N, cnt),
                 "stage_ms": {"encode": statistics.mean(enc_ms), "count": cnt, "reduce": statistics.mean(red_ms)}}
 
     cpu = None

@@ -106,6 +106,41 @@ __global__ void k_reg_lists(const uint32_t* __restrict__ sidx0, const uint32_t* 
   }
 }
 
+// Both of the above in one pass when every point is an origin (the q-th
+// origin is the point at sorted position q): list-ordered ranks, meta and
+// orank.
+__global__ void k_reg_lists_meta(const uint32_t* __restrict__ sidx0, const uint32_t* __restrict__ rank,
+                                 int64_t N, int64_t NP, int64_t NPpad, int64_t Lrow, int ds,
+                                 const uint32_t* __restrict__ pprefix, uint32_t* __restrict__ rankL,
+                                 OriginMeta* __restrict__ meta, uint32_t* __restrict__ orank) {
+  const int64_t NT = N - NP;
+  if (blockIdx.x == 0 && threadIdx.x < 32) {  // at most 31 padding positions per sample
+    for (int m = 0; m < ds; ++m) {
+      if (NP + threadIdx.x < NPpad) rankL[(int64_t)m * Lrow + NP + threadIdx.x] = 0;
+      if (NPpad + NT + threadIdx.x < Lrow) rankL[(int64_t)m * Lrow + NPpad + NT + threadIdx.x] = 0;
+    }
+  }
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = sidx0[p];
+    const uint32_t pp = pprefix[p];
+    const int64_t pos = i < (uint64_t)NP ? (int64_t)pp : NPpad + (p - pp);
+    const uint32_t r0 = rank[i];
+    const uint32_t sp = pprefix[r0];  // P points with a smaller dimension-0 value
+    OriginMeta mt;
+    mt.sP = sp;
+    mt.sT = r0 - sp;
+    mt.k = i;
+    mt.pad = 0;
+    meta[p] = mt;
+    for (int m = 0; m < ds; ++m) {
+      const uint32_t r = rank[(int64_t)(m + 1) * N + i];
+      rankL[(int64_t)m * Lrow + pos] = r;
+      orank[(int64_t)m * N + p] = r;
+    }
+  }
+}
+
 // meta[q] for the q-th origin, and orank[m'][q] = its rank in dimension m'+1
 __global__ void k_reg_meta(const uint32_t* __restrict__ rank, const uint32_t* __restrict__ olist,
                            const uint32_t* __restrict__ pprefix, int64_t N, int64_t no, int ds,
@@ -544,10 +579,15 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
     if (e == cudaSuccess) e = ddks_scan_rows(exO, exO, 1, N, true, stmp, st, &n);
     if (e != cudaSuccess) return e;
   }
-  k_reg_lists<<<grid(N), 256, 0, st>>>(sidx0, rank, N, NP, NPpad, Lrow, ds, ob, oe, pprefix, exO, rankL,
-                                       olist);
-  k_reg_meta<<<grid(no), 256, 0, st>>>(rank, olist, pprefix, N, no, ds, meta, orank);
-  n += 2;
+  if (exO == nullptr) {  // every point an origin, q = sorted position
+    k_reg_lists_meta<<<grid(N), 256, 0, st>>>(sidx0, rank, N, NP, NPpad, Lrow, ds, pprefix, rankL, meta, orank);
+    n += 1;
+  } else {
+    k_reg_lists<<<grid(N), 256, 0, st>>>(sidx0, rank, N, NP, NPpad, Lrow, ds, ob, oe, pprefix, exO, rankL,
+                                         olist);
+    k_reg_meta<<<grid(no), 256, 0, st>>>(rank, olist, pprefix, N, no, ds, meta, orank);
+    n += 2;
+  }
   // stage timing: the count stage (re-rank packing included) starts here
   ddks_stage_mark(ctx, 1, st);
   if (fused) {
