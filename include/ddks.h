@@ -70,7 +70,9 @@ typedef enum {
   DDKS_PATH_LANE = 2,      /* lane-private shared-memory histograms (d <= 8) */
   DDKS_PATH_WARP = 3,      /* one shared-memory histogram per warp and origin (d <= 13) */
   DDKS_PATH_SORT = 4,      /* per-origin sort of codes and segmented counts (any d) */
-  DDKS_PATH_DOMINANCE = 5  /* d = 2 only: quadrant counts by range queries, O(N log N) work */
+  DDKS_PATH_DOMINANCE = 5, /* d = 2 only: quadrant counts by range queries, O(N log N) work */
+  DDKS_PATH_BYTE = 6       /* byte re-ranks, four dimensions per 32-bit compare, per-origin histograms
+                              (2 <= d <= 15, N <= 32768) */
 } ddks_path;
 
 typedef struct {

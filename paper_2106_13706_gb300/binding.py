@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libddks.so")
 DDKS_OK = 0
 DDKS_PENDING = 1
 DDKS_F32, DDKS_F64 = 0, 1
-PATH_AUTO, PATH_REGISTER, PATH_LANE, PATH_WARP, PATH_SORT, PATH_DOMINANCE = 0, 1, 2, 3, 4, 5
+PATH_AUTO, PATH_REGISTER, PATH_LANE, PATH_WARP, PATH_SORT, PATH_DOMINANCE, PATH_BYTE = 0, 1, 2, 3, 4, 5, 6
 MAX_D = 30
 VDKS_MAX_D = 10
 RDKS_MAX_D = 4096

@@ -116,7 +116,7 @@ int ddks_ctx_create(const ddks_config* cfg, ddks_ctx** out) {
   ddks_ctx* ctx = new (std::nothrow) ddks_ctx();
   if (!ctx) return DDKS_ENOMEM;
   if (cfg) ctx->cfg = *cfg; else ddks_config_default(&ctx->cfg);
-  if (ctx->cfg.path < DDKS_PATH_AUTO || ctx->cfg.path > DDKS_PATH_DOMINANCE) { delete ctx; return DDKS_EINVAL; }
+  if (ctx->cfg.path < DDKS_PATH_AUTO || ctx->cfg.path > DDKS_PATH_BYTE) { delete ctx; return DDKS_EINVAL; }
   if (ctx->cfg.register_variant < 0 || ctx->cfg.register_variant > 4) { delete ctx; return DDKS_EINVAL; }
   if (ctx->cfg.rank_kernel < 0 || ctx->cfg.rank_kernel > 1) { delete ctx; return DDKS_EINVAL; }
   if (ctx->cfg.hbm_budget_bytes == 0) ctx->cfg.hbm_budget_bytes = 8ull << 30;
@@ -333,6 +333,12 @@ int ddks_count_origins_plan(ddks_ctx* ctx, const ddks_plan& plan, int64_t NP, in
       e = ddks_launch_sort(rank, N, NP, NT, d, ob, oe, best, bestj, st);
       ctx->launches += 1;
       break;
+    case DDKS_PATH_BYTE: {
+      int nl = 0;
+      e = ddks_launch_byte(ctx, rank, N, NP, NT, d, ob, oe, best, bestj, st, &nl);
+      ctx->launches += nl;
+      break;
+    }
     case DDKS_PATH_DOMINANCE: {
       if (!ctx->pfx0_valid) return DDKS_EUNSUPPORTED;  // needs K0's dimension-0 order and P prefix
       int n = 0;

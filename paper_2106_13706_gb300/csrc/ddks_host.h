@@ -202,6 +202,12 @@ cudaError_t ddks_launch_dominance(ddks_ctx* ctx, const uint32_t* rank, int64_t N
                                   int64_t ob, int64_t oe, uint64_t* best, int32_t* bestj, cudaStream_t st,
                                   int* launches);
 
+// count_byte.cu
+bool ddks_byte_supported(int d, int64_t NP, int64_t NT);
+cudaError_t ddks_launch_byte(ddks_ctx* ctx, const uint32_t* rank, int64_t N, int64_t NP, int64_t NT, int d,
+                             int64_t ob, int64_t oe, uint64_t* best, int32_t* bestj, cudaStream_t st,
+                             int* launches);
+
 // count_warp.cu
 bool ddks_warp16_supported(int d, int64_t NP, int64_t NT);
 cudaError_t ddks_launch_warp16(ddks_ctx* ctx, const uint32_t* rank, int64_t N, int64_t NP, int64_t NT,

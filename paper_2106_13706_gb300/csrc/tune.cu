@@ -49,6 +49,7 @@ static bool plan_ok(const ddks_plan& p, int64_t NP, int64_t NT, int32_t d) {
     case DDKS_PATH_WARP: return ddks_warp_supported(d, NP, NT);
     case DDKS_PATH_SORT: return ddks_sort_supported(d, NP + NT);
     case DDKS_PATH_DOMINANCE: return ddks_dominance_supported(d, NP, NT);
+    case DDKS_PATH_BYTE: return ddks_byte_supported(d, NP, NT);
     default: return false;
   }
 }
@@ -151,6 +152,7 @@ int ddks_autotune(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64
   { ddks_plan p; p.path = DDKS_PATH_WARP; p.warps = 8; cands.push_back(p); }
   { ddks_plan p; p.path = DDKS_PATH_SORT; cands.push_back(p); }
   { ddks_plan p; p.path = DDKS_PATH_DOMINANCE; cands.push_back(p); }
+  { ddks_plan p; p.path = DDKS_PATH_BYTE; cands.push_back(p); }
   cudaEvent_t a, b;
   if ((e = cudaEventCreate(&a)) != cudaSuccess) return ctx_cuda_fail(ctx, e, "cudaEventCreate");
   if ((e = cudaEventCreate(&b)) != cudaSuccess) { cudaEventDestroy(a); return ctx_cuda_fail(ctx, e, "cudaEventCreate"); }
