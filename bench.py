@@ -30,6 +30,9 @@ METRIC = "ddks_compares_per_s"
 UNIT = "compares/s"
 
 
+PATH_NAMES = ["auto", "register", "lane", "warp", "sort", "dominance", "byte"]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -337,8 +340,8 @@ def run_ours(args):
                "d2h_bytes_per_step": 3 * 8 + 4}
 
     clocks = sampler.summary()
-    path_name = (["auto", "register", "lane", "warp", "sort"][tuned[0]] if tuned else
-                 ["auto", "register", "lane", "warp", "sort"][args.path])
+    path_name = (PATH_NAMES[tuned[0]] if tuned else
+                 PATH_NAMES[args.path])
     if path_name == "auto":
         path_name = "register" if 2 <= d <= 4 else ("warp" if d <= 13 else "sort")
     peak, basis = peak_compares(torch, local, clocks.get("sm_max_mhz"), path_name, d)
@@ -376,8 +379,8 @@ def run_ours(args):
         "dtype": "u32 ranks (f32 input)" if P.dtype == np.float32 else "u32 ranks (f64 input)",
         "data": "synthetic (seeded numpy PCG64)",
         "config": {"workload": desc, "N": N, "d": d, "units_per_step": units,
-                   "kernel_path": (["auto", "register", "lane", "warp", "sort"][tuned[0]] if tuned else
-                                   ["auto", "register", "lane", "warp", "sort"][args.path]),
+                   "kernel_path": (PATH_NAMES[tuned[0]] if tuned else
+                                   PATH_NAMES[args.path]),
                    "l2": f"flushed between steps ({args.flush_mb} MB write)",
                    "parallelism": ("origin-sharded x%d (exact max merge)" % world if shard == "origins"
                                    else "replicas x%d" % world)},
