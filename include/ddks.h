@@ -94,10 +94,11 @@ typedef struct {
                                  memory by the count kernel itself (where the re-rank tables fit) with count
                                  kernel shape 1..3 (4 warp pairs at 2 CTAs/SM; 4 pairs at 1 CTA/SM,
                                  unrolled; 2 pairs at 3 CTAs/SM) */
-  int32_t rank_kernel;        /* the per-dimension ranks of the exact paths: 0 = automatic (one launch of
-                                 a thread-block cluster per dimension, sorting in distributed shared
-                                 memory, while N fits: about 125k float32 or 85k float64 points; else
-                                 the multi-launch sorts), 1 = always the multi-launch sorts */
+  int32_t rank_kernel;        /* the per-dimension ranks of the exact paths: 0 = automatic (float32
+                                 inputs: one launch of a thread-block cluster per dimension, sorting in
+                                 distributed shared memory, up to about 125k points; otherwise the
+                                 multi-launch sorts), 1 = always the multi-launch sorts, 2 = the cluster
+                                 launch wherever it fits (float64 too) */
 } ddks_config;
 
 typedef struct {

@@ -44,7 +44,7 @@ def test_small_shapes_all_paths(torch, dtype, kind):
         P, T = wl.random_pair(300 + i, n_p, n_t, d, kind=kind, dtype=dtype)
         ref = orc.ddks(P, T, per_origin=True)
         for path in (pkg.PATH_REGISTER, pkg.PATH_LANE, pkg.PATH_WARP):
-            with pkg.Context(device=0, path=path) as c:
+            with pkg.Context(device=0, path=path, rank_kernel=2) as c:
                 got = c.distance_range(_dev(torch, P), _dev(torch, T), 0, n_p + n_t, per_origin=True)
             assert np.array_equal(got["per_origin"], ref["per_origin"]), (n_p, n_t, path)
             _same(got, ref)
@@ -60,7 +60,7 @@ def test_special_values(torch):
     T[40:45, 1] = -np.inf
     T[100:300, 2] = P[100:300, 2]  # ties across samples
     ref = orc.ddks(P, T)
-    for rk in (0, 1):
+    for rk in (0, 1, 2):
         with pkg.Context(device=0, rank_kernel=rk) as c:
             _same(c.distance(_dev(torch, P), _dev(torch, T)), ref)
     P[7, 2] = np.nan
@@ -81,7 +81,7 @@ def test_largest_cluster_sizes_sampled(torch, dtype, n_p, n_t, d):
     T = (rng.integers(0, 5000, size=(n_t, d)) + (rng.random((n_t, d)) < 0.2)).astype(dtype)
     N = n_p + n_t
     ranges = [(0, 100), (n_p - 50, n_p + 50), (N - 100, N)]
-    for rk in (0, 1):
+    for rk in (2, 1):
         with pkg.Context(device=0, rank_kernel=rk) as c:
             Pd, Td = _dev(torch, P), _dev(torch, T)
             for a, b in ranges:
