@@ -208,16 +208,20 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
                         int32_t dtype, void* stream, ddks_result* out);
 
 /*
- * Tile shape of the batched units for problems of dimension d (1..11):
- * origins per work unit (32, 64 or 128) and points per shared-memory tile
- * (256, 512 or 1024); the default is 64 x 512.  DDKS_EINVAL otherwise.
- * The results do not depend on the shape.  The paper has no counterpart.
+ * Tile shape of the batched units for problems of dimension d (1..11).
+ * Histogram units: origins per work unit (32, 64 or 128) and points per
+ * shared-memory tile (256, 512 or 1024).  Bit-sliced unit (2 <= d <= 6 only):
+ * origins_per_unit = 127 (the unit's origins re-rank every point to 7 bits;
+ * Sec. 2.2.1, Eq. g) and points per tile 256, 512, 1024 or 2048, rounded to
+ * groups of 32.  DDKS_EINVAL otherwise.  The default is 64 x 512.  The
+ * results do not depend on the shape.  The paper has no counterpart.
  */
 int ddks_set_batch_shape(ddks_ctx* ctx, int32_t d, int32_t origins_per_unit, int32_t points_per_tile);
 
 /*
- * Autotuner of the batched launch: runs this batch with each of the nine tile
- * shapes, times each dimension group's launch, keeps the fastest shape per
+ * Autotuner of the batched launch: runs this batch with each tile shape (the
+ * nine histogram shapes, and three bit-sliced shapes for the dimensions that
+ * take them), times each dimension group's launch, keeps the fastest shape per
  * dimension in the context, and checks that every shape gives identical
  * results (DDKS_ECUDA if not).  shapes (optional host array of 12 x 2) gets
  * (origins per unit, points per tile) per dimension.  The paper has no

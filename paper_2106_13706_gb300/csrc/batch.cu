@@ -3,19 +3,28 @@
 //
 // K0b (k_batch_rank): one CTA per (problem, dimension) maps the coordinates to
 //   order-preserving keys, sorts (key, index) in shared memory and writes each
-//   point's min-rank, so x_m >= o_m <=> rank_m(x) >= rank_m(o) (Eq. g).
+//   point's min-rank, so x_m >= o_m <=> rank_m(x) >= rank_m(o) (Eq. g).  The
+//   dimension-0 CTA also writes the sorted order, the number of P points
+//   before each sorted position and the two samples' lists in dimension-0
+//   order; k_batch_lists then writes every dimension's ranks in list order.
 // K5 (k_batch_count): a persistent kernel.  Work units are (problem, tile of
-//   64 origins); CTAs take units from a device counter until none are left, so
+//   OT origins); CTAs take units from a device counter until none are left, so
 //   problems of very different sizes share the GPU without a launch each.  A
-//   unit with d <= 6 keeps lane-private shared histograms (4 threads per
-//   origin), one with 7 <= d <= 11 one shared histogram per warp and origin.
-//   Each origin's max |cP*NT - cT*NP| (Eq. d1) and lowest orthant go to the
-//   problem's slice of best/bestj.
+//   unit with d <= 6 keeps lane-private shared histograms (256 / OT threads
+//   per origin), one with 7 <= d <= 11 one shared histogram per warp and
+//   origin.  Each origin's max |cP*NT - cT*NP| (Eq. d1) and lowest orthant go
+//   to the problem's slice of best/bestj.
+// K5b (k_batch_bits, 2 <= d <= 6, tile shape "127 origins"): the same work
+//   units counted bit-sliced, as the single-problem register path does:
+//   dimension 0 by list position, dimensions 1..d-1 by 7-bit re-ranks
+//   against the unit's 127 origins compared 32 points per logic op, orthant
+//   counts from subset popcounts by inclusion-exclusion.
 // K_r (k_batch_reduce): one CTA per problem: max over origins, lowest origin.
 #include <algorithm>
 #include <cstring>
 #include <vector>
 
+#include "count_register.cuh"
 #include "ddks_host.h"
 #include "ddks_internal.cuh"
 
@@ -38,15 +47,31 @@ constexpr int kThreads = 256;
 // origins per work unit (32, 64 or 128) and points per staged tile
 constexpr int kOT = 64;        // default origins per work unit
 constexpr int kTile = 512;     // default points per staged tile
+constexpr int kBitsOT = 127;   // origins per bit-sliced unit (re-ranked values fit 7 bits)
+constexpr int kBitsThreads = 128;
+
+// Layout of the rank buffer (u32): [ranks: sum of N*d][ranks in list order:
+// sum of N*d][sorted order: sum of N][lists: sum of N][P prefix: sum of N].
+struct RankAreas {
+  uint32_t* rank;
+  uint32_t* rankL;
+  uint32_t* ord;
+  uint32_t* lst;
+  uint32_t* pfx;
+};
 
 DDKS_DEV bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
   return ka < kb || (ka == kb && ia < ib);
 }
 
-__global__ void __launch_bounds__(1024)
+constexpr int kRankThreads = 1024;
+
+__global__ void __launch_bounds__(kRankThreads)
 k_batch_rank(const BatchDesc* __restrict__ desc, const int* __restrict__ cta_prob,
-             const int* __restrict__ cta_dim, uint32_t* __restrict__ rank, unsigned* __restrict__ flags) {
+             const int* __restrict__ cta_dim, const RankAreas ra, unsigned* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ uint32_t tmp[40];
+  uint32_t* rank = ra.rank;
   const BatchDesc D = desc[cta_prob[blockIdx.x]];
   const int m = cta_dim[blockIdx.x];
   const int64_t N = D.NP + D.NT;
@@ -96,6 +121,44 @@ k_batch_rank(const BatchDesc* __restrict__ desc, const int* __restrict__ cta_pro
       if (sk[mid] < key) lo = mid + 1; else hi = mid;
     }
     R[si[p]] = (uint32_t)lo;
+  }
+  if (m != 0) return;
+  // dimension 0: ord[p] = point at sorted position p, pfx[p] = #P points at
+  // positions < p, and the lists: P points in sorted order at [0, NP), T
+  // points in sorted order at [NP, N).  Points with x_0 < o_0 are exactly
+  // the positions < rank_0(o), so a sample's first pfx-many list entries are
+  // the origin's phase A (Eq. g for dimension 0).
+  const int NP = (int)D.NP;
+  const int seg = (int)((N + kRankThreads - 1) / kRankThreads);
+  const int pa = (int)threadIdx.x * seg < N ? (int)threadIdx.x * seg : (int)N;
+  const int pb = pa + seg < N ? pa + seg : (int)N;
+  uint32_t c = 0;
+  for (int p = pa; p < pb; ++p) c += si[p] < (uint32_t)NP ? 1u : 0u;
+  uint32_t run = ddks_reg::block_exscan<kRankThreads>(c, tmp);
+  uint32_t* od = ra.ord + D.off_pool;
+  uint32_t* ls = ra.lst + D.off_pool;
+  uint32_t* pf = ra.pfx + D.off_pool;
+  for (int p = pa; p < pb; ++p) {
+    const uint32_t i = si[p];
+    od[p] = i;
+    pf[p] = run;
+    if (i < (uint32_t)NP) ls[run++] = i;
+    else ls[NP + p - (int)run] = i;
+  }
+}
+
+// rankL[m][pos] = rank_m of the point at list position pos (one CTA per
+// problem; the bit-sliced units read their points' ranks in list order).
+__global__ void __launch_bounds__(512)
+k_batch_lists(const BatchDesc* __restrict__ desc, const RankAreas ra) {
+  const BatchDesc D = desc[blockIdx.x];
+  const int64_t N = D.NP + D.NT;
+  const uint32_t* ls = ra.lst + D.off_pool;
+  const uint32_t* rk = ra.rank + D.off_rank;
+  uint32_t* rl = ra.rankL + D.off_rank;
+  for (int64_t p = threadIdx.x; p < N; p += blockDim.x) {
+    const uint32_t i = ls[p];
+    for (int m = 1; m < D.d; ++m) rl[m * N + p] = rk[m * N + i];
   }
 }
 
@@ -291,6 +354,248 @@ k_batch_count(const BatchDesc* __restrict__ desc, int count, int64_t total_units
   }
 }
 
+// Index of the lowest dimension in subset S (S != 0), folded at compile time.
+__host__ __device__ constexpr int low_dim(int S) {
+  return (S & 1) ? 0 : (S & 2) ? 1 : (S & 4) ? 2 : (S & 8) ? 3 : 4;
+}
+
+// In place: n[S] = #points >= the origin in every dimension of S  ->  n[B] =
+// #points >= the origin in exactly the dimensions of B (inclusion-exclusion
+// over supersets, one dimension at a time; every intermediate value is a
+// count, so none goes negative).
+template <int DS>
+DDKS_DEV void exact_counts(uint32_t (&n)[1 << DS]) {
+#pragma unroll
+  for (int b = 0; b < DS; ++b)
+#pragma unroll
+    for (int S = 0; S < (1 << DS); ++S)
+      if (!(S & (1 << b))) n[S] -= n[S | (1 << b)];
+}
+
+// Bit-sliced units (K5b).  Shared memory, in this order:
+//   tab    uint2 [DS][NWmax]   per dimension, bitmap of the unit's origin ranks
+//                              over [0, N) with the exclusive prefix count of
+//                              each word: x'(r) = #distinct origin ranks <= r
+//   planes u32 [TG][DS][8]     7 bit planes (+1 pad) per group of 32 list positions
+//   cnt    u32 [4][NS][128]    per origin slot: P phase A, P all, T phase A, T all
+__host__ __device__ constexpr size_t bits_smem(int ds, int TG, int NWmax) {
+  return (size_t)ds * NWmax * 8 + (size_t)TG * ds * 32 + (size_t)4 * ((1 << ds) - 1) * kBitsThreads * 4;
+}
+
+// One unit: origins at sorted positions [b * 127, b * 127 + 127) of one
+// problem (consecutive in dimension-0 order), one per thread; every point of
+// both samples in groups of 32 list positions, TG groups per tile.  A tile is
+// built by the four warps (lane = point: x' by the bitmap table, then one
+// ballot per bit plane) and then compared by every thread with its origin:
+// G_m = [x'_m >= o'_m] for 32 points by 7 three-input logic ops, and for
+// every non-empty subset S of the DS dimensions the popcount of the AND of
+// its G_m.  Phase A of an origin (points before its dimension-0 split) is
+// the first split-many positions of a sample's list: the counters are copied
+// to shared memory when a thread passes its split.
+template <int DS>
+__global__ void __launch_bounds__(kBitsThreads)
+k_batch_bits(const BatchDesc* __restrict__ desc, int count, int64_t total_units, const RankAreas ra,
+             unsigned long long* __restrict__ next_unit, uint64_t* __restrict__ best,
+             int32_t* __restrict__ bestj, int TG, int NWmax) {
+  using namespace ddks_reg;
+  constexpr int NS = (1 << DS) - 1;
+  extern __shared__ __align__(16) uint32_t sm[];
+  uint2* tab = reinterpret_cast<uint2*>(sm);
+  uint32_t* planes = sm + 2 * DS * NWmax;
+  uint32_t* cnt = planes + TG * DS * 8;
+  __shared__ long long unit;
+  __shared__ uint32_t tmp[40];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarps = kBitsThreads / 32;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) unit = (long long)atomicAdd(next_unit, 1ull);
+    __syncthreads();
+    const long long u = unit;
+    if (u >= total_units) break;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (desc[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+    }
+    const BatchDesc D = desc[lo];
+    const int N = (int)(D.NP + D.NT), NP = (int)D.NP, NT = (int)D.NT;
+    const int NW = (N + 31) >> 5;
+    const uint32_t* rk = ra.rank + D.off_rank;
+    const uint32_t* rl = ra.rankL + D.off_rank;
+    const int pos = (int)(u - D.unit0) * kBitsOT + tid;
+    const bool real = tid < kBitsOT && pos < N;
+    const uint32_t k = real ? ra.ord[D.off_pool + pos] : 0u;
+    // the block's origin ranks as bitmaps, then the words' prefix counts
+    // (all dimensions in one scan, a byte each: at most 127 distinct values)
+    for (int i = tid; i < DS * NWmax; i += kBitsThreads) tab[i] = make_uint2(0u, 0u);
+    __syncthreads();
+    uint32_t orr[DS];
+#pragma unroll
+    for (int m = 0; m < DS; ++m) {
+      orr[m] = real ? rk[(int64_t)(m + 1) * N + k] : 0u;
+      if (real) atomicOr(&tab[m * NWmax + (orr[m] >> 5)].x, 1u << (orr[m] & 31));
+    }
+    __syncthreads();
+    {
+      const int seg = (NW + kBitsThreads - 1) / kBitsThreads;
+      const int wa = tid * seg < NW ? tid * seg : NW;
+      const int wb = wa + seg < NW ? wa + seg : NW;
+#pragma unroll
+      for (int m0 = 0; m0 < DS; m0 += 4) {
+        uint32_t c = 0;
+        for (int w = wa; w < wb; ++w)
+#pragma unroll
+          for (int mm = 0; mm < 4; ++mm)
+            if (m0 + mm < DS) c += (uint32_t)__popc(tab[(m0 + mm) * NWmax + w].x) << (8 * mm);
+        uint32_t run = block_exscan<kBitsThreads>(c, tmp);
+        for (int w = wa; w < wb; ++w)
+#pragma unroll
+          for (int mm = 0; mm < 4; ++mm)
+            if (m0 + mm < DS) {
+              uint2& e = tab[(m0 + mm) * NWmax + w];
+              e.y = (run >> (8 * mm)) & 0xFFu;
+              run += (uint32_t)__popc(e.x) << (8 * mm);
+            }
+      }
+    }
+    __syncthreads();
+    // the origin's re-ranked values as compare masks, and its splits
+    uint32_t sgn[DS][kBits];
+#pragma unroll
+    for (int m = 0; m < DS; ++m) {
+      uint32_t t = 0;
+      if (real) {
+        const uint2 e = tab[m * NWmax + (orr[m] >> 5)];
+        t = e.y + (uint32_t)__popc(e.x & (0xFFFFFFFFu >> (31 - (orr[m] & 31))));
+      }
+#pragma unroll
+      for (int kk = 0; kk < kBits; ++kk) sgn[m][kk] = 0u - ((t >> kk) & 1u);
+    }
+    const uint32_t r0 = real ? rk[k] : 0u;
+    const int sP = real ? (int)ra.pfx[D.off_pool + r0] : 0;
+    const int sT = (int)r0 - sP;
+    const int GP = (NP + 31) >> 5, GT = (NT + 31) >> 5, Gall = GP + GT;
+    uint32_t acc[NS];
+#pragma unroll
+    for (int S = 0; S < NS; ++S) acc[S] = 0;
+    int split = sP;
+    bool crossed = false;
+    int smp = 0;
+    for (int g0 = 0; g0 < Gall; g0 += TG) {
+      const int ng = Gall - g0 < TG ? Gall - g0 : TG;
+      __syncthreads();  // the previous tile is consumed
+      for (int i = warp; i < ng; i += kWarps) {
+        const int g = g0 + i;
+        int lp;
+        bool valid;
+        if (g < GP) {
+          lp = g * 32 + lane;
+          valid = lp < NP;
+        } else {
+          const int q = (g - GP) * 32 + lane;
+          lp = NP + q;
+          valid = q < NT;
+        }
+#pragma unroll
+        for (int m = 0; m < DS; ++m) {
+          uint32_t x = 0;
+          if (valid) {
+            const uint32_t r = rl[(int64_t)(m + 1) * N + lp];
+            const uint2 e = tab[m * NWmax + (r >> 5)];
+            x = e.y + (uint32_t)__popc(e.x & (0xFFFFFFFFu >> (31 - (r & 31))));
+          }
+          uint32_t pl[kBits];
+#pragma unroll
+          for (int kk = 0; kk < kBits; ++kk) pl[kk] = __ballot_sync(0xffffffffu, (x >> kk) & 1u);
+          if (lane == 0) {
+            uint4* dst = reinterpret_cast<uint4*>(planes + (i * DS + m) * 8);
+            dst[0] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+            dst[1] = make_uint4(pl[4], pl[5], pl[6], 0u);
+          }
+        }
+      }
+      __syncthreads();
+      for (int i = 0; i < ng; ++i) {
+        const int g = g0 + i;
+        if (g == GP) {  // the P list is done: keep its counters, start on T
+#pragma unroll
+          for (int S = 0; S < NS; ++S) {
+            if (!crossed) cnt[(0 * NS + S) * kBitsThreads + tid] = acc[S];
+            cnt[(1 * NS + S) * kBitsThreads + tid] = acc[S];
+            acc[S] = 0;
+          }
+          crossed = false;
+          split = sT;
+          smp = 1;
+        }
+        uint32_t Gm[DS];
+        const uint4* pr = reinterpret_cast<const uint4*>(planes + i * DS * 8);
+#pragma unroll
+        for (int m = 0; m < DS; ++m) {
+          const uint4 a = pr[2 * m], b = pr[2 * m + 1];
+          const uint32_t pl[kBits] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z};
+          uint32_t r = 0xFFFFFFFFu;
+#pragma unroll
+          for (int kk = 0; kk < kBits; ++kk) r = cmp_step(sgn[m][kk], pl[kk], r);
+          Gm[m] = r;
+        }
+        uint32_t M[NS + 1];
+        M[0] = 0xFFFFFFFFu;
+#pragma unroll
+        for (int S = 1; S <= NS; ++S) M[S] = M[S & (S - 1)] & Gm[low_dim(S)];
+        const int pos0 = (smp == 0 ? g : g - GP) * 32;
+        if (!crossed && pos0 + 32 > split) {
+          // the group holds the origin's split, or begins phase B
+          const uint32_t pa = pos0 < split ? ~(0xFFFFFFFFu << (split - pos0)) : 0u;
+#pragma unroll
+          for (int S = 1; S <= NS; ++S)
+            cnt[((2 * smp) * NS + S - 1) * kBitsThreads + tid] = acc[S - 1] + (uint32_t)__popc(M[S] & pa);
+          crossed = true;
+        }
+#pragma unroll
+        for (int S = 1; S <= NS; ++S) acc[S - 1] += (uint32_t)__popc(M[S]);
+      }
+    }
+    // the last sample (T; P when there are no T groups) ends here
+#pragma unroll
+    for (int S = 0; S < NS; ++S) {
+      if (!crossed) cnt[((2 * smp) * NS + S) * kBitsThreads + tid] = acc[S];
+      cnt[((2 * smp + 1) * NS + S) * kBitsThreads + tid] = acc[S];
+    }
+    if (real) {
+      uint64_t bv = 0;
+      int bj = 0;
+      // code = bin << 1 | phase (bit 0 is dimension 0); the lowest code of the maximum
+#pragma unroll
+      for (int ph = 0; ph < 2; ++ph) {
+        uint32_t nP[1 << DS], nT[1 << DS];
+        nP[0] = ph == 0 ? (uint32_t)sP : (uint32_t)(NP - sP);
+        nT[0] = ph == 0 ? (uint32_t)sT : (uint32_t)(NT - sT);
+#pragma unroll
+        for (int S = 1; S <= NS; ++S) {
+          const uint32_t aP = cnt[(0 * NS + S - 1) * kBitsThreads + tid];
+          const uint32_t wP = cnt[(1 * NS + S - 1) * kBitsThreads + tid];
+          const uint32_t aT = cnt[(2 * NS + S - 1) * kBitsThreads + tid];
+          const uint32_t wT = cnt[(3 * NS + S - 1) * kBitsThreads + tid];
+          nP[S] = ph == 0 ? aP : wP - aP;
+          nT[S] = ph == 0 ? aT : wT - aT;
+        }
+        exact_counts<DS>(nP);
+        exact_counts<DS>(nT);
+#pragma unroll
+        for (int bin = 0; bin < (1 << DS); ++bin) {
+          const uint64_t num = ddks::numer(nP[bin], nT[bin], (uint64_t)NP, (uint64_t)NT);
+          const int code = (bin << 1) | ph;
+          if (num > bv || (num == bv && num != 0 && code < bj)) { bv = num; bj = code; }
+        }
+      }
+      best[D.off_pool + k] = bv;
+      bestj[D.off_pool + k] = bj;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(1024)
 k_batch_reduce(const BatchDesc* __restrict__ desc, const uint64_t* __restrict__ best,
                const int32_t* __restrict__ bestj, unsigned long long* __restrict__ out) {
@@ -334,12 +639,50 @@ k_batch_reduce(const BatchDesc* __restrict__ desc, const uint64_t* __restrict__ 
   }
 }
 
+template <int DS>
+cudaError_t launch_bits_ds(int sms, const BatchDesc* desc, int count, int64_t units, const RankAreas& ra,
+                           unsigned long long* next, uint64_t* best, int32_t* bestj, int TG, int nw_max,
+                           cudaStream_t s) {
+  const size_t smem = bits_smem(DS, TG, nw_max);
+  cudaError_t e = cudaFuncSetAttribute(k_batch_bits<DS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_bits<DS>, kBitsThreads, smem);
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)sms * per_sm;
+  if (grid > units) grid = units;
+  k_batch_bits<DS><<<(unsigned)grid, kBitsThreads, smem, s>>>(desc, count, units, ra, next, best, bestj, TG,
+                                                               nw_max);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bits(int ds, int sms, const BatchDesc* desc, int count, int64_t units, const RankAreas& ra,
+                        unsigned long long* next, uint64_t* best, int32_t* bestj, int TG, int nw_max,
+                        cudaStream_t s) {
+  switch (ds) {
+    case 1: return launch_bits_ds<1>(sms, desc, count, units, ra, next, best, bestj, TG, nw_max, s);
+    case 2: return launch_bits_ds<2>(sms, desc, count, units, ra, next, best, bestj, TG, nw_max, s);
+    case 3: return launch_bits_ds<3>(sms, desc, count, units, ra, next, best, bestj, TG, nw_max, s);
+    case 4: return launch_bits_ds<4>(sms, desc, count, units, ra, next, best, bestj, TG, nw_max, s);
+    case 5: return launch_bits_ds<5>(sms, desc, count, units, ra, next, best, bestj, TG, nw_max, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 size_t unit_smem(int d, int PT) {
   if (d <= 6) return (size_t)(1u << d) * kThreads * 4 + (size_t)((d + 1) / 2) * PT * 4;
   return (size_t)(kThreads / 32) * 2 * (1u << d) * 4 + (size_t)((d + 1) / 2) * PT * 4;
 }
 
 }  // namespace
+
+// Tile shapes of the batched units: (32 | 64 | 128 origins per unit, 256 |
+// 512 | 1024 points per staged tile) for the histogram units, and (127, 256 |
+// 512 | 1024 | 2048) for the bit-sliced unit of 2 <= d <= 6.
+static bool shape_valid(int d, int ot, int pt) {
+  if (ot == kBitsOT) return d >= 2 && d <= 6 && (pt == 256 || pt == 512 || pt == 1024 || pt == 2048);
+  return (ot == 32 || ot == 64 || ot == 128) && (pt == 256 || pt == 512 || pt == 1024);
+}
 
 // Batched distances for problems that fit the batch kernels (N <= 16384, d <= 11);
 // the others go through the single-problem path.  Synchronous.
@@ -382,7 +725,7 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
     size_t hoff = 0;
     int64_t off_pool = 0, off_rank = 0, units = 0;
     size_t smem_rank = 0, smem_unit = 0;
-    struct Group { int d, first, count; int64_t units; double work; };
+    struct Group { int d, first, count; int64_t units; double work; int nw_max; };
     std::vector<Group> groups;
     for (int b = 0; b < nb; ++b) {
       const int i = batched[b];
@@ -411,7 +754,7 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
       D.off_pool = off_pool;
       D.off_rank = off_rank;
       if (groups.empty() || groups.back().d != d[i]) {
-        groups.push_back(Group{d[i], b, 0, 0, 0.0});
+        groups.push_back(Group{d[i], b, 0, 0, 0.0, 4});
         units = 0;  // units are numbered within a group
       }
       D.unit0 = units;
@@ -422,15 +765,23 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
       groups.back().count += 1;
       groups.back().units = units;
       groups.back().work += (double)N * (double)N * d[i];
+      const int nw = (int)(((N + 31) / 32 + 3) & ~(int64_t)3);  // a multiple of 4 words
+      if (nw > groups.back().nw_max) groups.back().nw_max = nw;
       for (int m = 0; m < d[i]; ++m) { cta_prob.push_back(b); cta_dim.push_back(m); }
       int P2 = 1;
       while (P2 < N) P2 <<= 1;
       smem_rank = std::max(smem_rank, (size_t)P2 * 12);
-      smem_unit = std::max(smem_unit, unit_smem(d[i], ctx->batch_pt[d[i]]));
+      if (OT != kBitsOT) smem_unit = std::max(smem_unit, unit_smem(d[i], ctx->batch_pt[d[i]]));
     }
     const size_t desc_bytes = sizeof(BatchDesc) * nb + 8 * cta_prob.size() + 64;
     if ((rc = ctx->batch_desc.reserve(ctx, desc_bytes))) return rc;
-    if ((rc = ctx->rank.reserve(ctx, 4 * (size_t)off_rank))) return rc;
+    if ((rc = ctx->rank.reserve(ctx, 4 * (2 * (size_t)off_rank + 3 * (size_t)off_pool)))) return rc;
+    RankAreas ra;
+    ra.rank = (uint32_t*)ctx->rank.ptr;
+    ra.rankL = ra.rank + off_rank;
+    ra.ord = ra.rankL + off_rank;
+    ra.lst = ra.ord + off_pool;
+    ra.pfx = ra.lst + off_pool;
     if ((rc = ctx->best.reserve(ctx, 8 * (size_t)off_pool))) return rc;
     if ((rc = ctx->bestj.reserve(ctx, 4 * (size_t)off_pool))) return rc;
     if ((rc = ctx->batch_work.reserve(ctx, 8 * (3 * (size_t)nb + 4 + kMaxGroups)))) return rc;
@@ -475,11 +826,15 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
       if (ee == cudaSuccess)
         ee = cudaFuncSetAttribute(k_batch_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rank);
       if (ee == cudaSuccess) {
-        k_batch_rank<<<(unsigned)cta_prob.size(), 1024, smem_rank, s>>>(
-            ddesc, dprob, ddim, (uint32_t*)ctx->rank.ptr, (unsigned*)ctx->flags.ptr);
+        k_batch_rank<<<(unsigned)cta_prob.size(), kRankThreads, smem_rank, s>>>(ddesc, dprob, ddim, ra,
+                                                                                (unsigned*)ctx->flags.ptr);
         ee = cudaGetLastError();
       }
-      if (ee == cudaSuccess)
+      if (ee == cudaSuccess) {
+        k_batch_lists<<<nb, 512, 0, s>>>(ddesc, ra);
+        ee = cudaGetLastError();
+      }
+      if (ee == cudaSuccess && smem_unit)
         ee = cudaFuncSetAttribute(k_batch_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_unit);
       for (size_t gi = 0; gi < gorder.size() && ee == cudaSuccess; ++gi) {
         const Group& G = groups[gorder[gi]];
@@ -491,15 +846,20 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
           cudaEventCreate(&ev1);
           cudaEventRecord(ev0, s);
         }
-        int blocks_per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_batch_count, kThreads, sm_g);
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
-        int64_t grid = (int64_t)ctx->num_sms * blocks_per_sm;
-        if (grid > G.units) grid = G.units;
-        k_batch_count<<<(unsigned)grid, kThreads, sm_g, s>>>(
-            ddesc + G.first, G.count, G.units, (const uint32_t*)ctx->rank.ptr, work + gorder[gi],
-            (uint64_t*)ctx->best.ptr, (int32_t*)ctx->bestj.ptr, OT, PT);
-        ee = cudaGetLastError();
+        if (OT == kBitsOT && G.d >= 2 && G.d <= 6) {
+          ee = launch_bits(G.d - 1, ctx->num_sms, ddesc + G.first, G.count, G.units, ra, work + gorder[gi],
+                           (uint64_t*)ctx->best.ptr, (int32_t*)ctx->bestj.ptr, PT / 32, G.nw_max, s);
+        } else {
+          int blocks_per_sm = 1;
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_batch_count, kThreads, sm_g);
+          if (blocks_per_sm < 1) blocks_per_sm = 1;
+          int64_t grid = (int64_t)ctx->num_sms * blocks_per_sm;
+          if (grid > G.units) grid = G.units;
+          k_batch_count<<<(unsigned)grid, kThreads, sm_g, s>>>(ddesc + G.first, G.count, G.units, ra.rank,
+                                                               work + gorder[gi], (uint64_t*)ctx->best.ptr,
+                                                               (int32_t*)ctx->bestj.ptr, OT, PT);
+          ee = cudaGetLastError();
+        }
         ctx->launches += 1;
         if (ctx->batch_timing) {
           cudaEventRecord(ev1, s);
@@ -516,7 +876,7 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
                                            (const int32_t*)ctx->bestj.ptr, res);
         ee = cudaGetLastError();
       }
-      ctx->launches += 2;
+      ctx->launches += 3;
       if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "batch");
       return DDKS_OK;
     });
@@ -551,8 +911,7 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
 
 int ddks_set_batch_shape(ddks_ctx* ctx, int32_t d, int32_t origins_per_unit, int32_t points_per_tile) {
   if (!ctx || d < 1 || d > 11) return DDKS_EINVAL;
-  if (origins_per_unit != 32 && origins_per_unit != 64 && origins_per_unit != 128) return DDKS_EINVAL;
-  if (points_per_tile != 256 && points_per_tile != 512 && points_per_tile != 1024) return DDKS_EINVAL;
+  if (!shape_valid(d, origins_per_unit, points_per_tile)) return DDKS_EINVAL;
   ctx->batch_ot[d] = origins_per_unit;
   ctx->batch_pt[d] = points_per_tile;
   return DDKS_OK;
@@ -575,9 +934,17 @@ int ddks_autotune_batch(ddks_ctx* ctx, int32_t count, const void* const* P, cons
   bool have_ref = false;
   int rc = DDKS_OK;
   ctx->batch_timing = true;
-  for (int ot : {32, 64, 128}) {
-    for (int pt : {256, 512, 1024}) {
-      for (int k = 1; k < 12; ++k) { ctx->batch_ot[k] = ot; ctx->batch_pt[k] = pt; }
+  static const int kShapes[][2] = {{32, 256},  {32, 512},  {32, 1024},  {64, 256},   {64, 512},  {64, 1024},
+                                   {128, 256}, {128, 512}, {128, 1024}, {127, 512}, {127, 1024}, {127, 2048}};
+  for (const auto& sh : kShapes) {
+    const int ot = sh[0], pt = sh[1];
+    {
+      // a shape a dimension cannot take leaves that dimension at its starting shape, untimed
+      for (int k = 1; k < 12; ++k) {
+        const bool ok = shape_valid(k, ot, pt);
+        ctx->batch_ot[k] = ok ? ot : ot0[k];
+        ctx->batch_pt[k] = ok ? pt : pt0[k];
+      }
       for (int rep = 0; rep < 2 && rc == DDKS_OK; ++rep)  // the second run is timed warm
         rc = ddks_batch_distance(ctx, count, P, NP, T, NT, d, dtype, stream, got.data());
       if (rc) break;
@@ -595,7 +962,7 @@ int ddks_autotune_batch(ddks_ctx* ctx, int32_t count, const void* const* P, cons
       if (rc) break;
       for (int k = 1; k < 12; ++k) {
         const float ms = ctx->batch_group_ms[k];
-        if (ms > 0.0f && ms < best_ms[k]) { best_ms[k] = ms; best_ot[k] = ot; best_pt[k] = pt; }
+        if (shape_valid(k, ot, pt) && ms > 0.0f && ms < best_ms[k]) { best_ms[k] = ms; best_ot[k] = ot; best_pt[k] = pt; }
         ctx->batch_group_ms[k] = 0.0f;
       }
     }

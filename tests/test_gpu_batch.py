@@ -56,6 +56,7 @@ def test_config4_256_uneven(torch):
 
 
 SHAPES = [(ot, pt) for ot in (32, 64, 128) for pt in (256, 512, 1024)]
+BITS_SHAPES = [(127, pt) for pt in (256, 512, 1024, 2048)]  # bit-sliced unit, 2 <= d <= 6
 
 
 def test_every_tile_shape_matches_oracle(torch):
@@ -65,14 +66,48 @@ def test_every_tile_shape_matches_oracle(torch):
     refs = [orc.ddks(P, T) for P, T in probs]
     dev = [(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()) for P, T in probs]
     with pkg.Context(device=0) as c:
-        for ot, pt in SHAPES:
+        for ot, pt in SHAPES + BITS_SHAPES:
             for d in range(1, 12):
-                c.set_batch_shape(d, ot, pt)
+                if ot != 127 or 2 <= d <= 6:
+                    c.set_batch_shape(d, ot, pt)
             got = c.batch_distance(dev)
             for g, r in zip(got, refs):
                 assert _key(g) == _key(r), (ot, pt)
-        with pytest.raises(pkg.DdksError):
-            c.set_batch_shape(3, 48, 512)
+        for d, ot, pt in [(3, 48, 512), (7, 127, 1024), (1, 127, 1024), (3, 64, 2048), (4, 127, 128)]:
+            with pytest.raises(pkg.DdksError):
+                c.set_batch_shape(d, ot, pt)
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 5, 6])
+def test_bit_sliced_unit_edges(torch, d):
+    # the bit-sliced unit against the oracle: one-point samples, samples of
+    # exactly 32k points, ragged tails, heavy ties (integer grids, so origins
+    # share values inside a block and splits land on group boundaries), and
+    # the largest batched size (16,384 pooled points)
+    rng = np.random.default_rng(40 + d)
+    shapes = [(1, 1), (1, 40), (33, 1), (32, 64), (127, 128), (200, 55), (700, 901), (64, 4000)]
+    probs = []
+    for i, (n_p, n_t) in enumerate(shapes):
+        kind = "int" if i % 2 else "normal"
+        probs.append(wl.random_pair(500 + 10 * d + i, n_p, n_t, d, kind=kind))
+    P = rng.integers(0, 6, size=(300, d)).astype(np.float32)  # very few distinct values
+    T = rng.integers(0, 6, size=(260, d)).astype(np.float32)
+    probs.append((P, T))
+    refs = [orc.ddks(P, T) for P, T in probs]
+    big = wl.random_pair(77 + d, 8192, 8192, d, kind="int")
+    dev = [(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()) for P, T in probs + [big]]
+    with pkg.Context(device=0) as c:
+        for pt in (256, 2048):
+            c.set_batch_shape(d, 127, pt)
+            got = c.batch_distance(dev)
+            for g, r in zip(got, refs):
+                assert _key(g) == _key(r), (pt, g, r)
+            # the largest problem: against the histogram unit and the
+            # single-problem path (the oracle over 16,384^2 pairs takes too long)
+            c.set_batch_shape(d, 64, 512)
+            hist = c.batch_distance(dev[-1:])[0]
+            alone = c.distance(*dev[-1])
+            assert _key(got[-1]) == _key(hist) == _key(alone)
 
 
 def test_autotuned_shapes_and_results(torch):
@@ -82,7 +117,11 @@ def test_autotuned_shapes_and_results(torch):
     with pkg.Context(device=0) as c:
         shapes = c.autotune_batch(dev)
         for d in (2, 3, 5, 8):
-            assert shapes[d][0] in (32, 64, 128) and shapes[d][1] in (256, 512, 1024)
+            ot, pt = shapes[d]
+            if ot == 127:
+                assert 2 <= d <= 6 and pt in (256, 512, 1024, 2048)
+            else:
+                assert ot in (32, 64, 128) and pt in (256, 512, 1024)
         for _ in range(2):  # direct, then captured
             got = c.batch_distance(dev)
             assert [_key(g) for g in got] == [_key(r) for r in refs]
