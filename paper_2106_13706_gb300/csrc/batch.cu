@@ -1,12 +1,12 @@
 // batch.cu -- many independent ddKS problems of different N and d in one
 // persistent launch (the batched form of Sec. 2.1's statistic).
 //
-// K0b (k_batch_rank): one CTA per (problem, dimension) maps the coordinates to
-//   order-preserving keys, sorts (key, index) in shared memory and writes each
-//   point's min-rank, so x_m >= o_m <=> rank_m(x) >= rank_m(o) (Eq. g).  The
-//   dimension-0 CTA also writes the sorted order, the number of P points
-//   before each sorted position and the two samples' lists in dimension-0
-//   order; k_batch_lists then writes every dimension's ranks in list order.
+// K0b (batch_rank.cu): one CTA per (problem, dimension) sorts the coordinate
+//   in shared memory and writes each point's min-rank, so x_m >= o_m <=>
+//   rank_m(x) >= rank_m(o) (Eq. g); the dimension-0 CTA also writes the
+//   sorted order, the number of P points before each sorted position and the
+//   two samples' lists in dimension-0 order.  k_batch_lists then writes every
+//   dimension's ranks in list order.
 // K5 (k_batch_count): a persistent kernel.  Work units are (problem, tile of
 //   OT origins); CTAs take units from a device counter until none are left, so
 //   problems of very different sizes share the GPU without a launch each.  A
@@ -24,23 +24,15 @@
 #include <cstring>
 #include <vector>
 
+#include "batch_internal.cuh"
 #include "count_register.cuh"
 #include "ddks_host.h"
 #include "ddks_internal.cuh"
 
-struct BatchDesc {
-  const void* P;
-  const void* T;
-  int64_t NP, NT;
-  int64_t off_pool;  // offset of the problem in best/bestj (pooled points)
-  int64_t off_rank;  // offset of the problem's [d][N] ranks
-  int64_t unit0;     // first work unit of the problem
-  int32_t d, is_f64;
-};
 
 namespace {
 
-constexpr int kMaxBatchN = 16384;   // so NP, NT < 65536: P and T counts share one 32-bit bin
+constexpr int kMaxBatchN = kBatchMaxN;  // so NP, NT < 65536: P and T counts share one 32-bit bin
 constexpr int kMaxGroups = 16;      // dimensions 1..11 of the batched problems
 constexpr int kThreads = 256;
 // tile shapes of the batched units, per dimension group (ddks_autotune_batch):
@@ -50,102 +42,6 @@ constexpr int kTile = 512;     // default points per staged tile
 constexpr int kBitsOT = 127;   // origins per bit-sliced unit (re-ranked values fit 7 bits)
 constexpr int kBitsThreads = 128;
 
-// Layout of the rank buffer (u32): [ranks: sum of N*d][ranks in list order:
-// sum of N*d][sorted order: sum of N][lists: sum of N][P prefix: sum of N].
-struct RankAreas {
-  uint32_t* rank;
-  uint32_t* rankL;
-  uint32_t* ord;
-  uint32_t* lst;
-  uint32_t* pfx;
-};
-
-DDKS_DEV bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
-  return ka < kb || (ka == kb && ia < ib);
-}
-
-constexpr int kRankThreads = 1024;
-
-__global__ void __launch_bounds__(kRankThreads)
-k_batch_rank(const BatchDesc* __restrict__ desc, const int* __restrict__ cta_prob,
-             const int* __restrict__ cta_dim, const RankAreas ra, unsigned* __restrict__ flags) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ uint32_t tmp[40];
-  uint32_t* rank = ra.rank;
-  const BatchDesc D = desc[cta_prob[blockIdx.x]];
-  const int m = cta_dim[blockIdx.x];
-  const int64_t N = D.NP + D.NT;
-  int P2 = 1;
-  while (P2 < N) P2 <<= 1;
-  uint64_t* sk = reinterpret_cast<uint64_t*>(smraw);
-  uint32_t* si = reinterpret_cast<uint32_t*>(sk + P2);
-  for (int i = threadIdx.x; i < P2; i += blockDim.x) {
-    uint64_t key = ~0ull;
-    if (i < N) {
-      if (D.is_f64) {
-        const double v = i < D.NP ? ((const double*)D.P)[(int64_t)i * D.d + m]
-                                  : ((const double*)D.T)[(int64_t)(i - D.NP) * D.d + m];
-        if (v != v) atomicOr(flags, ddks::kFlagNaN);
-        key = ddks::order_key(v);
-      } else {
-        const float v = i < D.NP ? ((const float*)D.P)[(int64_t)i * D.d + m]
-                                 : ((const float*)D.T)[(int64_t)(i - D.NP) * D.d + m];
-        if (v != v) atomicOr(flags, ddks::kFlagNaN);
-        key = ddks::order_key(v);
-      }
-    }
-    sk[i] = key;
-    si[i] = (uint32_t)i;
-  }
-  __syncthreads();
-  for (int size = 2; size <= P2; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = threadIdx.x; t < P2 / 2; t += blockDim.x) {
-        const int lo = 2 * t - (t & (stride - 1));
-        const int hi = lo + stride;
-        const bool asc = ((lo & size) == 0);
-        const uint64_t ka = sk[lo], kb = sk[hi];
-        const uint32_t ia = si[lo], ib = si[hi];
-        const bool swap = asc ? pair_less(kb, ib, ka, ia) : pair_less(ka, ia, kb, ib);
-        if (swap) { sk[lo] = kb; sk[hi] = ka; si[lo] = ib; si[hi] = ia; }
-      }
-      __syncthreads();
-    }
-  }
-  uint32_t* R = rank + D.off_rank + (int64_t)m * N;
-  for (int p = threadIdx.x; p < N; p += blockDim.x) {
-    const uint64_t key = sk[p];
-    int lo = 0, hi = p;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (sk[mid] < key) lo = mid + 1; else hi = mid;
-    }
-    R[si[p]] = (uint32_t)lo;
-  }
-  if (m != 0) return;
-  // dimension 0: ord[p] = point at sorted position p, pfx[p] = #P points at
-  // positions < p, and the lists: P points in sorted order at [0, NP), T
-  // points in sorted order at [NP, N).  Points with x_0 < o_0 are exactly
-  // the positions < rank_0(o), so a sample's first pfx-many list entries are
-  // the origin's phase A (Eq. g for dimension 0).
-  const int NP = (int)D.NP;
-  const int seg = (int)((N + kRankThreads - 1) / kRankThreads);
-  const int pa = (int)threadIdx.x * seg < N ? (int)threadIdx.x * seg : (int)N;
-  const int pb = pa + seg < N ? pa + seg : (int)N;
-  uint32_t c = 0;
-  for (int p = pa; p < pb; ++p) c += si[p] < (uint32_t)NP ? 1u : 0u;
-  uint32_t run = ddks_reg::block_exscan<kRankThreads>(c, tmp);
-  uint32_t* od = ra.ord + D.off_pool;
-  uint32_t* ls = ra.lst + D.off_pool;
-  uint32_t* pf = ra.pfx + D.off_pool;
-  for (int p = pa; p < pb; ++p) {
-    const uint32_t i = si[p];
-    od[p] = i;
-    pf[p] = run;
-    if (i < (uint32_t)NP) ls[run++] = i;
-    else ls[NP + p - (int)run] = i;
-  }
-}
 
 // rankL[m][pos] = rank_m of the point at list position pos (one CTA per
 // problem; the bit-sliced units read their points' ranks in list order).
@@ -724,7 +620,10 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
     std::vector<int> cta_prob, cta_dim;
     size_t hoff = 0;
     int64_t off_pool = 0, off_rank = 0, units = 0;
-    size_t smem_rank = 0, smem_unit = 0;
+    size_t smem_unit = 0;
+    // K0 entries (problem, dimension) by size class: above 4,096 points, then the rest
+    std::vector<int> wide_prob, wide_dim;
+    BatchRankClass rcls[2] = {{0, 0, 0, true}, {0, 0, 0, false}};
     struct Group { int d, first, count; int64_t units; double work; int nw_max; };
     std::vector<Group> groups;
     for (int b = 0; b < nb; ++b) {
@@ -767,12 +666,19 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
       groups.back().work += (double)N * (double)N * d[i];
       const int nw = (int)(((N + 31) / 32 + 3) & ~(int64_t)3);  // a multiple of 4 words
       if (nw > groups.back().nw_max) groups.back().nw_max = nw;
-      for (int m = 0; m < d[i]; ++m) { cta_prob.push_back(b); cta_dim.push_back(m); }
-      int P2 = 1;
-      while (P2 < N) P2 <<= 1;
-      smem_rank = std::max(smem_rank, (size_t)P2 * 12);
+      const bool wide = N > 4096;
+      BatchRankClass& rc_ = rcls[wide ? 0 : 1];
+      rc_.count += d[i];
+      if ((int)N > rc_.cap) rc_.cap = (int)N;
+      for (int m = 0; m < d[i]; ++m) {
+        (wide ? wide_prob : cta_prob).push_back(b);
+        (wide ? wide_dim : cta_dim).push_back(m);
+      }
       if (OT != kBitsOT) smem_unit = std::max(smem_unit, unit_smem(d[i], ctx->batch_pt[d[i]]));
     }
+    cta_prob.insert(cta_prob.begin(), wide_prob.begin(), wide_prob.end());
+    cta_dim.insert(cta_dim.begin(), wide_dim.begin(), wide_dim.end());
+    rcls[1].first = rcls[0].count;
     const size_t desc_bytes = sizeof(BatchDesc) * nb + 8 * cta_prob.size() + 64;
     if ((rc = ctx->batch_desc.reserve(ctx, desc_bytes))) return rc;
     if ((rc = ctx->rank.reserve(ctx, 4 * (2 * (size_t)off_rank + 3 * (size_t)off_pool)))) return rc;
@@ -817,19 +723,15 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
                      [&](int a, int b) { return groups[a].work > groups[b].work; });
     // the descriptors hold every shape and input address the kernels see
     GraphKey key;
-    key.add(3).add((uint64_t)nb).add((uint64_t)units).add((uint64_t)smem_rank).add((uint64_t)smem_unit);
+    key.add(3).add((uint64_t)nb).add((uint64_t)units).add((uint64_t)smem_unit);
+    key.add_bytes(rcls, sizeof rcls);
     key.add_bytes(hs, up).add_bytes(ctx->batch_ot, sizeof ctx->batch_ot).add_bytes(ctx->batch_pt, sizeof ctx->batch_pt);
     if (ctx->batch_timing) key.add(0xB7);  // tuning runs directly (events between the launches)
     rc = ddks_graph_run(ctx, key.h, st, [&](cudaStream_t s) -> int {
       cudaError_t ee = cudaMemsetAsync(work, 0, 8 * kMaxGroups, s);
       if (ee == cudaSuccess) ee = cudaMemsetAsync(ctx->flags.ptr, 0, 4, s);
       if (ee == cudaSuccess)
-        ee = cudaFuncSetAttribute(k_batch_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rank);
-      if (ee == cudaSuccess) {
-        k_batch_rank<<<(unsigned)cta_prob.size(), kRankThreads, smem_rank, s>>>(ddesc, dprob, ddim, ra,
-                                                                                (unsigned*)ctx->flags.ptr);
-        ee = cudaGetLastError();
-      }
+        ee = ddks_batch_rank(ddesc, dprob, ddim, rcls, 2, dtype == DDKS_F64, ra, (unsigned*)ctx->flags.ptr, s);
       if (ee == cudaSuccess) {
         k_batch_lists<<<nb, 512, 0, s>>>(ddesc, ra);
         ee = cudaGetLastError();
@@ -876,7 +778,7 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
                                            (const int32_t*)ctx->bestj.ptr, res);
         ee = cudaGetLastError();
       }
-      ctx->launches += 3;
+      ctx->launches += 2 + (rcls[0].count > 0) + (rcls[1].count > 0);
       if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "batch");
       return DDKS_OK;
     });
@@ -888,6 +790,11 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hflags, ctx->flags.ptr, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "batch");
+    if (hflags & ddks::kFlagBounds) {  // a kernel's own range check refused a store
+      ctx->last_err = "batch: index out of range";
+      for (int b = 0; b < nb; ++b) out[batched[b]].status = DDKS_ECUDA;
+      return DDKS_ECUDA;
+    }
     if (hflags & ddks::kFlagNaN) {
       for (int b = 0; b < nb; ++b) out[batched[b]].status = DDKS_ENAN;
       return DDKS_ENAN;

@@ -36,6 +36,23 @@ DDKS_DEV uint64_t order_key(double v) {
   return u;
 }
 
+// Lanes of the (fully active) warp whose 8-bit digit equals this lane's: one
+// ballot per digit bit that differs somewhere in the warp (a fixed cost;
+// match.any slows down with the number of distinct values in the warp).
+DDKS_DEV uint32_t same_digit(uint32_t dg) {
+  const uint32_t vary = __reduce_or_sync(0xffffffffu, dg) ^ __reduce_and_sync(0xffffffffu, dg);
+  uint32_t m = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    if ((vary >> b) & 1u) {
+      const bool bit = (dg >> b) & 1u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      m &= bit ? bal : ~bal;
+    }
+  }
+  return m;
+}
+
 // |a*NT - b*NP| for counts a <= NP, b <= NT with NP*NT < 2^62 (no overflow).
 DDKS_DEV uint64_t numer(uint64_t a, uint64_t b, uint64_t NP, uint64_t NT) {
   uint64_t x = a * NT, y = b * NP;

@@ -33,24 +33,6 @@ constexpr int64_t kSelfScanTiles = 128;  // up to here the scatter CTAs sum the 
 
 DDKS_DEV uint32_t digit_of(uint64_t k, int shift) { return (uint32_t)(k >> shift) & 255u; }
 
-// Lanes of the (fully active) warp whose 8-bit digit equals this lane's:
-// one ballot per digit bit that differs somewhere in the warp (found by an
-// OR and an AND reduction; high key bytes often take only a few values, so
-// most bits are skipped).  Cheaper than match.any here.
-DDKS_DEV uint32_t same_digit_lanes(uint32_t dg) {
-  const uint32_t vary = __reduce_or_sync(0xffffffffu, dg) ^ __reduce_and_sync(0xffffffffu, dg);
-  uint32_t m = 0xffffffffu;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    if ((vary >> b) & 1u) {  // warp-uniform
-      const bool bit = (dg >> b) & 1u;
-      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-      m &= bit ? bal : ~bal;
-    }
-  }
-  return m;
-}
-
 // exclusive prefix sum over the CTA's threads; ws: kRW words
 DDKS_DEV uint32_t block_exscan(uint32_t v, uint32_t* ws) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -98,7 +80,7 @@ k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int64_t stride, int s
       if (v) atomicAdd(&h[dg], 1u);
     } else {  // few distinct digits: one add per group of equal digits
       const uint32_t vm = __ballot_sync(0xffffffffu, v);
-      const uint32_t peers = same_digit_lanes(dg) & vm;
+      const uint32_t peers = ddks::same_digit(dg) & vm;
       if (v && (peers >> lane) == 1u) atomicAdd(&h[dg], (uint32_t)__popc(peers));
     }
   }
@@ -193,7 +175,7 @@ k_radix_scatter(const uint64_t* __restrict__ in_k, const uint32_t* __restrict__ 
 #pragma unroll
   for (int j = 0; j < RI; ++j) {
     const uint32_t dg = digit_of(k[j], shift);
-    const uint32_t peers = same_digit_lanes(dg);
+    const uint32_t peers = ddks::same_digit(dg);
     r[j] = wcnt[w][dg] + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     __syncwarp();
     if ((peers >> lane) == 1u) wcnt[w][dg] += (uint32_t)__popc(peers);  // the group's highest lane

@@ -56,23 +56,6 @@ __host__ __device__ constexpr size_t cluster_smem(int64_t S) {
          + 16;
 }
 
-// Lanes of the (fully active) warp whose 8-bit digit equals this lane's: one
-// ballot per digit bit that differs somewhere in the warp (a fixed cost;
-// match.any slows down with the number of distinct values in the warp).
-DDKS_DEV uint32_t same_digit(uint32_t dg) {
-  const uint32_t vary = __reduce_or_sync(0xffffffffu, dg) ^ __reduce_and_sync(0xffffffffu, dg);
-  uint32_t m = 0xffffffffu;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    if ((vary >> b) & 1u) {
-      const bool bit = (dg >> b) & 1u;
-      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-      m &= bit ? bal : ~bal;
-    }
-  }
-  return m;
-}
-
 // exclusive prefixes over the CTA's threads (kKT of them) of two values each;
 // ws2: 2 * kKW words
 DDKS_DEV void cta_exscan2(uint32_t v0, uint32_t v1, uint32_t* ws2, uint32_t& e0, uint32_t& e1) {
@@ -170,7 +153,7 @@ k_rank_cluster(const V* __restrict__ P, const V* __restrict__ T, int64_t NP, int
         const uint32_t vm = __ballot_sync(0xffffffffu, v);
         if (vm != 0u) {  // warp-uniform
           dgs[j] = v ? (uint32_t)(keyA[q] >> shift) & 255u : 0u;
-          const uint32_t pr = same_digit(dgs[j]) & vm;
+          const uint32_t pr = ddks::same_digit(dgs[j]) & vm;
           prs[j] = v ? pr : 0u;  // nonzero exactly on the lanes that hold an element
         }
       }

@@ -125,3 +125,36 @@ def test_autotuned_shapes_and_results(torch):
         for _ in range(2):  # direct, then captured
             got = c.batch_distance(dev)
             assert [_key(g) for g in got] == [_key(r) for r in refs]
+
+
+def test_float64_both_rank_classes(torch):
+    # K0 of the batch sorts each (problem, dimension) in one CTA; problems
+    # above 4,096 pooled points take the 1,024-thread class, up to the
+    # 16,384-point limit where a float64 row fills the CTA's shared memory
+    rng = np.random.default_rng(12)
+    probs = [wl.random_pair(81, 8192, 8192, 3, kind="int", dtype=np.float64),
+             wl.random_pair(82, 3000, 2100, 2, kind="normal", dtype=np.float64),
+             wl.random_pair(83, 40, 9, 5, kind="int", dtype=np.float64),
+             wl.random_pair(84, 1, 1, 4, kind="normal", dtype=np.float64)]
+    P = rng.standard_normal((700, 6))
+    P[:100, 1] = -0.0  # signed zeros tie with +0.0
+    T = rng.standard_normal((650, 6))
+    T[:50, 1] = 0.0
+    T[60:70, 2] = np.inf
+    probs.append((P, T))
+    dev = [(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()) for P, T in probs]
+    with pkg.Context(device=0) as c:
+        for shapes in ((64, 512), (127, 1024)):
+            for d in range(2, 7):
+                c.set_batch_shape(d, *shapes)
+            got = c.batch_distance(dev)
+            for i, ((P, T), g) in enumerate(zip(probs, got)):
+                if i == 0:  # 16,384 points: against the single-problem path
+                    assert _key(g) == _key(c.distance(*dev[0]))
+                else:
+                    assert _key(g) == _key(orc.ddks(P, T)), (i, shapes)
+        bad = [(x.clone(), y.clone()) for x, y in dev[1:3]]
+        bad[1][1][3, 0] = float("nan")
+        with pytest.raises(pkg.DdksError) as e:
+            c.batch_distance(bad)
+        assert e.value.code == -2
