@@ -213,15 +213,17 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
  * shared-memory tile (256, 512 or 1024).  Bit-sliced unit (2 <= d <= 6 only):
  * origins_per_unit = 127 (the unit's origins re-rank every point to 7 bits;
  * Sec. 2.2.1, Eq. g) and points per tile 256, 512, 1024 or 2048, rounded to
- * groups of 32.  DDKS_EINVAL otherwise.  The default is 64 x 512.  The
+ * groups of 32.  Byte unit (d = 7 or 8 only): origins_per_unit = 31 or 63
+ * (one origin per thread, each point re-ranked to a byte per dimension) and
+ * points per tile 256, 512, 1024 or 2048.  DDKS_EINVAL otherwise.  The default is 64 x 512.  The
  * results do not depend on the shape.  The paper has no counterpart.
  */
 int ddks_set_batch_shape(ddks_ctx* ctx, int32_t d, int32_t origins_per_unit, int32_t points_per_tile);
 
 /*
  * Autotuner of the batched launch: runs this batch with each tile shape (the
- * nine histogram shapes, and three bit-sliced shapes for the dimensions that
- * take them), times each dimension group's launch, keeps the fastest shape per
+ * nine histogram shapes, three bit-sliced shapes for 2 <= d <= 6 and four
+ * byte shapes for d = 7, 8), times each dimension group's launch, keeps the fastest shape per
  * dimension in the context, and checks that every shape gives identical
  * results (DDKS_ECUDA if not).  shapes (optional host array of 12 x 2) gets
  * (origins per unit, points per tile) per dimension.  The paper has no

@@ -41,6 +41,8 @@ constexpr int kOT = 64;        // default origins per work unit
 constexpr int kTile = 512;     // default points per staged tile
 constexpr int kBitsOT = 127;   // origins per bit-sliced unit (re-ranked values fit 7 bits)
 constexpr int kBitsThreads = 128;
+// origins per byte unit (one warp or two, one origin slot left over)
+constexpr bool is_bytes_ot(int ot) { return ot == 31 || ot == 63; }
 
 
 // rankL[m][pos] = rank_m of the point at list position pos (one CTA per
@@ -268,6 +270,54 @@ DDKS_DEV void exact_counts(uint32_t (&n)[1 << DS]) {
       if (!(S & (1 << b))) n[S] -= n[S | (1 << b)];
 }
 
+// Re-rank tables of a unit's origins (Sec. 2.2.1, Eq. g: only x >= o
+// matters): for dimensions [0, DD), tab[m][w] = {bitmap of the origins' ranks
+// over word w of [0, N), #set bits in the words before w}, so that
+//   x'(r) = #distinct origin ranks <= r = tab.y + popc(tab.x & bits <= r)
+// and x >= o <=> x'(rank x) >= x'(rank o) for every origin of the unit
+// (at most 127 origins: x' fits 7 bits).  orr[m]: this thread's origin rank
+// in dimension m (real: the thread holds an origin).  Every thread of the
+// CTA calls this; it ends with a barrier.
+template <int DD, int THREADS>
+DDKS_DEV void build_tables(uint2* __restrict__ tab, int NWmax, int NW, const uint32_t (&orr)[DD], bool real,
+                           uint32_t* tmp) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < DD * NWmax; i += THREADS) tab[i] = make_uint2(0u, 0u);
+  __syncthreads();
+  if (real) {
+#pragma unroll
+    for (int m = 0; m < DD; ++m) atomicOr(&tab[m * NWmax + (orr[m] >> 5)].x, 1u << (orr[m] & 31));
+  }
+  __syncthreads();
+  // exclusive prefix counts of the words, four dimensions per scan (a byte each)
+  const int seg = (NW + THREADS - 1) / THREADS;
+  const int wa = tid * seg < NW ? tid * seg : NW;
+  const int wb = wa + seg < NW ? wa + seg : NW;
+#pragma unroll
+  for (int m0 = 0; m0 < DD; m0 += 4) {
+    uint32_t c = 0;
+    for (int w = wa; w < wb; ++w)
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm)
+        if (m0 + mm < DD) c += (uint32_t)__popc(tab[(m0 + mm) * NWmax + w].x) << (8 * mm);
+    uint32_t run = ddks_reg::block_exscan<THREADS>(c, tmp);
+    for (int w = wa; w < wb; ++w)
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm)
+        if (m0 + mm < DD) {
+          uint2& e = tab[(m0 + mm) * NWmax + w];
+          e.y = (run >> (8 * mm)) & 0xFFu;
+          run += (uint32_t)__popc(e.x) << (8 * mm);
+        }
+  }
+  __syncthreads();
+}
+
+DDKS_DEV uint32_t xrank(const uint2* __restrict__ tab, int m, int NWmax, uint32_t r) {
+  const uint2 e = tab[m * NWmax + (r >> 5)];
+  return e.y + (uint32_t)__popc(e.x & (0xFFFFFFFFu >> (31 - (r & 31))));
+}
+
 // Bit-sliced units (K5b).  Shared memory, in this order:
 //   tab    uint2 [DS][NWmax]   per dimension, bitmap of the unit's origin ranks
 //                              over [0, N) with the exclusive prefix count of
@@ -322,49 +372,15 @@ k_batch_bits(const BatchDesc* __restrict__ desc, int count, int64_t total_units,
     const int pos = (int)(u - D.unit0) * kBitsOT + tid;
     const bool real = tid < kBitsOT && pos < N;
     const uint32_t k = real ? ra.ord[D.off_pool + pos] : 0u;
-    // the block's origin ranks as bitmaps, then the words' prefix counts
-    // (all dimensions in one scan, a byte each: at most 127 distinct values)
-    for (int i = tid; i < DS * NWmax; i += kBitsThreads) tab[i] = make_uint2(0u, 0u);
-    __syncthreads();
     uint32_t orr[DS];
 #pragma unroll
-    for (int m = 0; m < DS; ++m) {
-      orr[m] = real ? rk[(int64_t)(m + 1) * N + k] : 0u;
-      if (real) atomicOr(&tab[m * NWmax + (orr[m] >> 5)].x, 1u << (orr[m] & 31));
-    }
-    __syncthreads();
-    {
-      const int seg = (NW + kBitsThreads - 1) / kBitsThreads;
-      const int wa = tid * seg < NW ? tid * seg : NW;
-      const int wb = wa + seg < NW ? wa + seg : NW;
-#pragma unroll
-      for (int m0 = 0; m0 < DS; m0 += 4) {
-        uint32_t c = 0;
-        for (int w = wa; w < wb; ++w)
-#pragma unroll
-          for (int mm = 0; mm < 4; ++mm)
-            if (m0 + mm < DS) c += (uint32_t)__popc(tab[(m0 + mm) * NWmax + w].x) << (8 * mm);
-        uint32_t run = block_exscan<kBitsThreads>(c, tmp);
-        for (int w = wa; w < wb; ++w)
-#pragma unroll
-          for (int mm = 0; mm < 4; ++mm)
-            if (m0 + mm < DS) {
-              uint2& e = tab[(m0 + mm) * NWmax + w];
-              e.y = (run >> (8 * mm)) & 0xFFu;
-              run += (uint32_t)__popc(e.x) << (8 * mm);
-            }
-      }
-    }
-    __syncthreads();
+    for (int m = 0; m < DS; ++m) orr[m] = real ? rk[(int64_t)(m + 1) * N + k] : 0u;
+    build_tables<DS, kBitsThreads>(tab, NWmax, NW, orr, real, tmp);
     // the origin's re-ranked values as compare masks, and its splits
     uint32_t sgn[DS][kBits];
 #pragma unroll
     for (int m = 0; m < DS; ++m) {
-      uint32_t t = 0;
-      if (real) {
-        const uint2 e = tab[m * NWmax + (orr[m] >> 5)];
-        t = e.y + (uint32_t)__popc(e.x & (0xFFFFFFFFu >> (31 - (orr[m] & 31))));
-      }
+      const uint32_t t = real ? xrank(tab, m, NWmax, orr[m]) : 0u;
 #pragma unroll
       for (int kk = 0; kk < kBits; ++kk) sgn[m][kk] = 0u - ((t >> kk) & 1u);
     }
@@ -395,12 +411,7 @@ k_batch_bits(const BatchDesc* __restrict__ desc, int count, int64_t total_units,
         }
 #pragma unroll
         for (int m = 0; m < DS; ++m) {
-          uint32_t x = 0;
-          if (valid) {
-            const uint32_t r = rl[(int64_t)(m + 1) * N + lp];
-            const uint2 e = tab[m * NWmax + (r >> 5)];
-            x = e.y + (uint32_t)__popc(e.x & (0xFFFFFFFFu >> (31 - (r & 31))));
-          }
+          const uint32_t x = valid ? xrank(tab, m, NWmax, rl[(int64_t)(m + 1) * N + lp]) : 0u;
           uint32_t pl[kBits];
 #pragma unroll
           for (int kk = 0; kk < kBits; ++kk) pl[kk] = __ballot_sync(0xffffffffu, (x >> kk) & 1u);
@@ -492,6 +503,141 @@ k_batch_bits(const BatchDesc* __restrict__ desc, int count, int64_t total_units,
   }
 }
 
+// Byte units (K5c, d = 7, 8; tile shape "63 origins" or "31 origins").  One
+// origin per thread, THREADS - 1 origins per unit (consecutive pooled
+// indices), every point of the problem in tiles of PT.  Each point is
+// re-ranked against the unit's origins (x' <= 63, build_tables) and stored as
+// two words of bytes, x'_m | 0x80 in byte m % 4 of word m / 4 (bytes past d
+// are 0).  For an origin with bytes o'_m, (x'|0x80) - o' keeps every byte
+// apart (no borrow: x'|0x80 >= 128 > o') and its bit 7 is [x'_m >= o'_m] =
+// [x_m >= o_m]: two subtracts compare all d dimensions.  One multiply
+// gathers the eight compare bits into the orthant's index g (bit 2k = dim k,
+// bit 2k+1 = dim 4+k; for d = 7 bit 7 stays 0), and the thread adds the
+// point to its own histogram column (P count | T count << 16), so the shared
+// adds of a warp never meet on one address or bank.
+//   hist  u32 [2^d][THREADS]
+//   tab   uint2 [d][NWmax]
+//   tile  uint2 [PT], tinc u32 [PT] (1 for a P point, 1 << 16 for a T point)
+constexpr int kByteBatch = 8;  // points per batch of the byte unit's inner loop
+
+template <int DD, int THREADS>
+__host__ __device__ constexpr size_t bytes_smem(int PT, int NWmax) {
+  return (size_t)(1u << DD) * THREADS * 4 + (size_t)DD * NWmax * 8 + (size_t)PT * 12;
+}
+
+// orthant index g of the canonical code c (bit m = [x_m >= o_m])
+DDKS_DEV uint32_t byte_index(uint32_t c) {
+  uint32_t lo = c & 15u, hi = (c >> 4) & 15u;
+  lo = (lo | (lo << 2)) & 0x33u;
+  lo = (lo | (lo << 1)) & 0x55u;
+  hi = (hi | (hi << 2)) & 0x33u;
+  hi = (hi | (hi << 1)) & 0x55u;
+  return lo | (hi << 1);
+}
+
+template <int DD, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+k_batch_bytes(const BatchDesc* __restrict__ desc, int count, int64_t total_units, const RankAreas ra,
+              unsigned long long* __restrict__ next_unit, uint64_t* __restrict__ best,
+              int32_t* __restrict__ bestj, int PT, int NWmax) {
+  static_assert(DD >= 5 && DD <= 8, "two words of bytes");
+  constexpr int OB = THREADS - 1;
+  constexpr int NB = 1 << DD;
+  extern __shared__ __align__(16) uint32_t sm[];
+  uint32_t* hist = sm;
+  uint2* tab = reinterpret_cast<uint2*>(hist + NB * THREADS);
+  uint2* tile = tab + DD * NWmax;
+  uint32_t* tinc = reinterpret_cast<uint32_t*>(tile + PT);
+  __shared__ long long unit;
+  __shared__ uint32_t tmp[40];
+  const int tid = threadIdx.x;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) unit = (long long)atomicAdd(next_unit, 1ull);
+    __syncthreads();
+    const long long u = unit;
+    if (u >= total_units) break;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (desc[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+    }
+    const BatchDesc D = desc[lo];
+    const int N = (int)(D.NP + D.NT), NP = (int)D.NP, NT = (int)D.NT;
+    const uint32_t* rk = ra.rank + D.off_rank;
+    const int k = (int)(u - D.unit0) * OB + tid;  // this thread's origin (pooled index)
+    const bool real = tid < OB && k < N;
+    uint32_t orr[DD];
+#pragma unroll
+    for (int m = 0; m < DD; ++m) orr[m] = real ? rk[(int64_t)m * N + k] : 0u;
+    build_tables<DD, THREADS>(tab, NWmax, (N + 31) >> 5, orr, real, tmp);
+    uint32_t o0 = 0, o1 = 0;  // the origin's bytes
+#pragma unroll
+    for (int m = 0; m < DD; ++m) {
+      const uint32_t t = real ? xrank(tab, m, NWmax, orr[m]) : 0u;
+      if (m < 4) o0 |= t << (8 * m);
+      else o1 |= t << (8 * (m - 4));
+    }
+    for (int i = tid; i < NB * THREADS; i += THREADS) hist[i] = 0u;
+    for (int base = 0; base < N; base += PT) {
+      const int cnt = N - base < PT ? N - base : PT;
+      __syncthreads();  // the previous tile is consumed (and the tables and counters are ready)
+      const int cnt8 = (cnt + kByteBatch - 1) & ~(kByteBatch - 1);  // <= PT (a multiple of 256)
+      for (int p = tid; p < cnt8; p += THREADS) {
+        const int i = base + p;
+        // past the end: a point with x' = 0 in every dimension (bytes 0x80),
+        // so that no byte borrows and g stays below 2^d; it adds nothing
+        uint32_t w0 = 0, w1 = 0;
+#pragma unroll
+        for (int m = 0; m < DD; ++m) {
+          const uint32_t x = (p < cnt ? xrank(tab, m, NWmax, rk[(int64_t)m * N + i]) : 0u) | 0x80u;
+          if (m < 4) w0 |= x << (8 * m);
+          else w1 |= x << (8 * (m - 4));
+        }
+        tile[p] = make_uint2(w0, w1);
+        tinc[p] = p >= cnt ? 0u : (i < NP ? 1u : (1u << 16));  // past the end: adds nothing
+      }
+      __syncthreads();
+      uint32_t* col = hist + tid;
+      for (int p0 = 0; p0 < cnt8; p0 += kByteBatch) {
+        // a batch of points: every load first, then the indices, then the adds
+        // (the adds and the loads share the shared-memory window, so the
+        // compiler keeps their order)
+        uint2 w[kByteBatch];
+        uint32_t inc[kByteBatch];
+#pragma unroll
+        for (int q = 0; q < kByteBatch; ++q) {
+          w[q] = tile[p0 + q];
+          inc[q] = tinc[p0 + q];
+        }
+        uint32_t g[kByteBatch];
+#pragma unroll
+        for (int q = 0; q < kByteBatch; ++q) {
+          const uint32_t a = (w[q].x - o0) & 0x80808080u;  // dims 0..3 at bit 7 of each byte
+          const uint32_t b = (w[q].y - o1) & 0x80808080u;  // dims 4..7
+          // a >> 1 | b: byte k holds dim k at bit 6 and dim 4+k at bit 7; the
+          // multiply moves byte k's two bits to bits 24 + 2k, 25 + 2k (all other
+          // partial products land on distinct bits below 24 or above 31)
+          g[q] = (((a >> 1) | b) * 0x00041041u) >> 24;
+        }
+#pragma unroll
+        for (int q = 0; q < kByteBatch; ++q) atomicAdd(col + g[q] * THREADS, inc[q]);
+      }
+    }
+    if (real) {
+      uint64_t bv = 0;
+      int bj = 0;
+      for (int c = 0; c < NB; ++c) {  // lowest canonical code of the maximum
+        const uint32_t v = hist[byte_index((uint32_t)c) * THREADS + tid];
+        const uint64_t num = ddks::numer(v & 0xFFFFu, v >> 16, (uint64_t)NP, (uint64_t)NT);
+        if (num > bv) { bv = num; bj = c; }
+      }
+      best[D.off_pool + k] = bv;
+      bestj[D.off_pool + k] = bj;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(1024)
 k_batch_reduce(const BatchDesc* __restrict__ desc, const uint64_t* __restrict__ best,
                const int32_t* __restrict__ bestj, unsigned long long* __restrict__ out) {
@@ -552,6 +698,34 @@ cudaError_t launch_bits_ds(int sms, const BatchDesc* desc, int count, int64_t un
   return cudaGetLastError();
 }
 
+template <int DD, int THREADS>
+cudaError_t launch_bytes_dt(int sms, const BatchDesc* desc, int count, int64_t units, const RankAreas& ra,
+                            unsigned long long* next, uint64_t* best, int32_t* bestj, int PT, int nw_max,
+                            cudaStream_t s) {
+  const size_t smem = bytes_smem<DD, THREADS>(PT, nw_max);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_batch_bytes<DD, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_bytes<DD, THREADS>, THREADS, smem);
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)sms * per_sm;
+  if (grid > units) grid = units;
+  k_batch_bytes<DD, THREADS><<<(unsigned)grid, THREADS, smem, s>>>(desc, count, units, ra, next, best, bestj, PT,
+                                                                   nw_max);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bytes(int d, int ot, int sms, const BatchDesc* desc, int count, int64_t units,
+                         const RankAreas& ra, unsigned long long* next, uint64_t* best, int32_t* bestj, int PT,
+                         int nw_max, cudaStream_t s) {
+  if (d == 7 && ot == 63) return launch_bytes_dt<7, 64>(sms, desc, count, units, ra, next, best, bestj, PT, nw_max, s);
+  if (d == 7 && ot == 31) return launch_bytes_dt<7, 32>(sms, desc, count, units, ra, next, best, bestj, PT, nw_max, s);
+  if (d == 8 && ot == 63) return launch_bytes_dt<8, 64>(sms, desc, count, units, ra, next, best, bestj, PT, nw_max, s);
+  if (d == 8 && ot == 31) return launch_bytes_dt<8, 32>(sms, desc, count, units, ra, next, best, bestj, PT, nw_max, s);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_bits(int ds, int sms, const BatchDesc* desc, int count, int64_t units, const RankAreas& ra,
                         unsigned long long* next, uint64_t* best, int32_t* bestj, int TG, int nw_max,
                         cudaStream_t s) {
@@ -573,10 +747,12 @@ size_t unit_smem(int d, int PT) {
 }  // namespace
 
 // Tile shapes of the batched units: (32 | 64 | 128 origins per unit, 256 |
-// 512 | 1024 points per staged tile) for the histogram units, and (127, 256 |
-// 512 | 1024 | 2048) for the bit-sliced unit of 2 <= d <= 6.
+// 512 | 1024 points per staged tile) for the histogram units, (127, 256 |
+// 512 | 1024 | 2048) for the bit-sliced unit of 2 <= d <= 6 and (31 | 63,
+// 256 | 512 | 1024 | 2048) for the byte unit of d = 7, 8.
 static bool shape_valid(int d, int ot, int pt) {
   if (ot == kBitsOT) return d >= 2 && d <= 6 && (pt == 256 || pt == 512 || pt == 1024 || pt == 2048);
+  if (is_bytes_ot(ot)) return (d == 7 || d == 8) && (pt == 256 || pt == 512 || pt == 1024 || pt == 2048);
   return (ot == 32 || ot == 64 || ot == 128) && (pt == 256 || pt == 512 || pt == 1024);
 }
 
@@ -600,8 +776,12 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
   int rc = DDKS_OK;
   if (!batched.empty()) {
     // problems of one dimension form a group with its own persistent launch,
-    // its shared memory sized for that dimension
-    std::stable_sort(batched.begin(), batched.end(), [&](int a, int b) { return d[a] < d[b]; });
+    // its shared memory sized for that dimension; within a group the largest
+    // problems come first, so their long units start early and the small ones
+    // fill the end of the launch
+    std::stable_sort(batched.begin(), batched.end(), [&](int a, int b) {
+      return d[a] != d[b] ? d[a] < d[b] : NP[a] + NT[a] > NP[b] + NT[b];
+    });
     const int nb = (int)batched.size();
     // stage host inputs into one device buffer
     size_t host_bytes = 0;
@@ -674,7 +854,7 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
         (wide ? wide_prob : cta_prob).push_back(b);
         (wide ? wide_dim : cta_dim).push_back(m);
       }
-      if (OT != kBitsOT) smem_unit = std::max(smem_unit, unit_smem(d[i], ctx->batch_pt[d[i]]));
+      if (OT != kBitsOT && !is_bytes_ot(OT)) smem_unit = std::max(smem_unit, unit_smem(d[i], ctx->batch_pt[d[i]]));
     }
     cta_prob.insert(cta_prob.begin(), wide_prob.begin(), wide_prob.end());
     cta_dim.insert(cta_dim.begin(), wide_dim.begin(), wide_dim.end());
@@ -751,6 +931,9 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
         if (OT == kBitsOT && G.d >= 2 && G.d <= 6) {
           ee = launch_bits(G.d - 1, ctx->num_sms, ddesc + G.first, G.count, G.units, ra, work + gorder[gi],
                            (uint64_t*)ctx->best.ptr, (int32_t*)ctx->bestj.ptr, PT / 32, G.nw_max, s);
+        } else if (is_bytes_ot(OT)) {
+          ee = launch_bytes(G.d, OT, ctx->num_sms, ddesc + G.first, G.count, G.units, ra, work + gorder[gi],
+                            (uint64_t*)ctx->best.ptr, (int32_t*)ctx->bestj.ptr, PT, G.nw_max, s);
         } else {
           int blocks_per_sm = 1;
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_batch_count, kThreads, sm_g);
@@ -842,7 +1025,8 @@ int ddks_autotune_batch(ddks_ctx* ctx, int32_t count, const void* const* P, cons
   int rc = DDKS_OK;
   ctx->batch_timing = true;
   static const int kShapes[][2] = {{32, 256},  {32, 512},  {32, 1024},  {64, 256},   {64, 512},  {64, 1024},
-                                   {128, 256}, {128, 512}, {128, 1024}, {127, 512}, {127, 1024}, {127, 2048}};
+                                   {128, 256}, {128, 512}, {128, 1024}, {127, 512}, {127, 1024}, {127, 2048},
+                                   {63, 512},  {63, 1024}, {63, 2048},  {31, 1024}};
   for (const auto& sh : kShapes) {
     const int ot = sh[0], pt = sh[1];
     {

@@ -57,6 +57,15 @@ def test_config4_256_uneven(torch):
 
 SHAPES = [(ot, pt) for ot in (32, 64, 128) for pt in (256, 512, 1024)]
 BITS_SHAPES = [(127, pt) for pt in (256, 512, 1024, 2048)]  # bit-sliced unit, 2 <= d <= 6
+BYTE_SHAPES = [(ot, pt) for ot in (31, 63) for pt in (256, 2048)]  # byte unit, d = 7, 8
+
+
+def _shape_ok(d, ot, pt):
+    if ot == 127:
+        return 2 <= d <= 6
+    if ot in (31, 63):
+        return d in (7, 8)
+    return True
 
 
 def test_every_tile_shape_matches_oracle(torch):
@@ -66,14 +75,15 @@ def test_every_tile_shape_matches_oracle(torch):
     refs = [orc.ddks(P, T) for P, T in probs]
     dev = [(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()) for P, T in probs]
     with pkg.Context(device=0) as c:
-        for ot, pt in SHAPES + BITS_SHAPES:
+        for ot, pt in SHAPES + BITS_SHAPES + BYTE_SHAPES:
             for d in range(1, 12):
-                if ot != 127 or 2 <= d <= 6:
+                if _shape_ok(d, ot, pt):
                     c.set_batch_shape(d, ot, pt)
             got = c.batch_distance(dev)
             for g, r in zip(got, refs):
                 assert _key(g) == _key(r), (ot, pt)
-        for d, ot, pt in [(3, 48, 512), (7, 127, 1024), (1, 127, 1024), (3, 64, 2048), (4, 127, 128)]:
+        for d, ot, pt in [(3, 48, 512), (7, 127, 1024), (1, 127, 1024), (3, 64, 2048), (4, 127, 128),
+                          (6, 63, 1024), (9, 31, 512), (8, 63, 128)]:
             with pytest.raises(pkg.DdksError):
                 c.set_batch_shape(d, ot, pt)
 
@@ -120,11 +130,41 @@ def test_autotuned_shapes_and_results(torch):
             ot, pt = shapes[d]
             if ot == 127:
                 assert 2 <= d <= 6 and pt in (256, 512, 1024, 2048)
+            elif ot in (31, 63):
+                assert d in (7, 8) and pt in (256, 512, 1024, 2048)
             else:
                 assert ot in (32, 64, 128) and pt in (256, 512, 1024)
         for _ in range(2):  # direct, then captured
             got = c.batch_distance(dev)
             assert [_key(g) for g in got] == [_key(r) for r in refs]
+
+
+@pytest.mark.parametrize("d", [7, 8])
+def test_byte_unit_edges(torch, d):
+    # the byte unit against the oracle: one-point samples, ragged tails, unit
+    # boundaries (31 and 63 origins), heavy ties, and 16,384 pooled points
+    rng = np.random.default_rng(60 + d)
+    shapes = [(1, 1), (1, 40), (33, 1), (31, 32), (63, 64), (200, 55), (700, 901), (64, 3000)]
+    probs = []
+    for i, (n_p, n_t) in enumerate(shapes):
+        probs.append(wl.random_pair(600 + 10 * d + i, n_p, n_t, d, kind="int" if i % 2 else "normal"))
+    P = rng.integers(0, 3, size=(300, d)).astype(np.float32)  # three values per dimension
+    T = rng.integers(0, 3, size=(260, d)).astype(np.float32)
+    probs.append((P, T))
+    refs = [orc.ddks(P, T) for P, T in probs]
+    big = wl.random_pair(88 + d, 8192, 8192, d, kind="int")
+    dev = [(torch.from_numpy(P).cuda(), torch.from_numpy(T).cuda()) for P, T in probs + [big]]
+    with pkg.Context(device=0) as c:
+        c.set_batch_shape(d, 64, 512)
+        hist = c.batch_distance(dev[-1:])[0]
+        alone = c.distance(*dev[-1])
+        assert _key(hist) == _key(alone)
+        for ot, pt in [(31, 256), (63, 2048), (63, 512)]:
+            c.set_batch_shape(d, ot, pt)
+            got = c.batch_distance(dev)
+            for g, r in zip(got, refs):
+                assert _key(g) == _key(r), (ot, pt, g, r)
+            assert _key(got[-1]) == _key(hist)
 
 
 def test_float64_both_rank_classes(torch):
