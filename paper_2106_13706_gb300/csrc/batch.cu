@@ -41,6 +41,7 @@ constexpr int kOT = 64;        // default origins per work unit
 constexpr int kTile = 512;     // default points per staged tile
 constexpr int kBitsOT = 127;   // origins per bit-sliced unit (re-ranked values fit 7 bits)
 constexpr int kBitsThreads = 128;
+constexpr int kBuildPts = 4;  // points (groups) per thread (warp) whose rank loads are issued together
 // origins per byte unit (one warp or two, one origin slot left over)
 constexpr bool is_bytes_ot(int ot) { return ot == 31 || ot == 63; }
 
@@ -397,28 +398,43 @@ k_batch_bits(const BatchDesc* __restrict__ desc, int count, int64_t total_units,
     for (int g0 = 0; g0 < Gall; g0 += TG) {
       const int ng = Gall - g0 < TG ? Gall - g0 : TG;
       __syncthreads();  // the previous tile is consumed
-      for (int i = warp; i < ng; i += kWarps) {
-        const int g = g0 + i;
-        int lp;
-        bool valid;
-        if (g < GP) {
-          lp = g * 32 + lane;
-          valid = lp < NP;
-        } else {
-          const int q = (g - GP) * 32 + lane;
-          lp = NP + q;
-          valid = q < NT;
+      for (int i0 = warp; i0 < ng; i0 += kWarps * kBuildPts) {
+        // kBuildPts groups per warp at a time: all their rank loads first
+        uint32_t rr[kBuildPts][DS];
+        bool vv[kBuildPts];
+#pragma unroll
+        for (int u = 0; u < kBuildPts; ++u) {
+          const int g = g0 + i0 + u * kWarps;
+          int lp;
+          bool valid;
+          if (g < GP) {
+            lp = g * 32 + lane;
+            valid = lp < NP;
+          } else {
+            const int q = (g - GP) * 32 + lane;
+            lp = NP + q;
+            valid = q < NT;
+          }
+          valid = valid && i0 + u * kWarps < ng;
+          vv[u] = valid;
+#pragma unroll
+          for (int m = 0; m < DS; ++m) rr[u][m] = valid ? rl[(int64_t)(m + 1) * N + lp] : 0u;
         }
 #pragma unroll
-        for (int m = 0; m < DS; ++m) {
-          const uint32_t x = valid ? xrank(tab, m, NWmax, rl[(int64_t)(m + 1) * N + lp]) : 0u;
-          uint32_t pl[kBits];
+        for (int u = 0; u < kBuildPts; ++u) {
+          const int i = i0 + u * kWarps;
+          if (i >= ng) break;  // warp-uniform
 #pragma unroll
-          for (int kk = 0; kk < kBits; ++kk) pl[kk] = __ballot_sync(0xffffffffu, (x >> kk) & 1u);
-          if (lane == 0) {
-            uint4* dst = reinterpret_cast<uint4*>(planes + (i * DS + m) * 8);
-            dst[0] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-            dst[1] = make_uint4(pl[4], pl[5], pl[6], 0u);
+          for (int m = 0; m < DS; ++m) {
+            const uint32_t x = vv[u] ? xrank(tab, m, NWmax, rr[u][m]) : 0u;
+            uint32_t pl[kBits];
+#pragma unroll
+            for (int kk = 0; kk < kBits; ++kk) pl[kk] = __ballot_sync(0xffffffffu, (x >> kk) & 1u);
+            if (lane == 0) {
+              uint4* dst = reinterpret_cast<uint4*>(planes + (i * DS + m) * 8);
+              dst[0] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+              dst[1] = make_uint4(pl[4], pl[5], pl[6], 0u);
+            }
           }
         }
       }
@@ -583,19 +599,31 @@ k_batch_bytes(const BatchDesc* __restrict__ desc, int count, int64_t total_units
       const int cnt = N - base < PT ? N - base : PT;
       __syncthreads();  // the previous tile is consumed (and the tables and counters are ready)
       const int cnt8 = (cnt + kByteBatch - 1) & ~(kByteBatch - 1);  // <= PT (a multiple of 256)
-      for (int p = tid; p < cnt8; p += THREADS) {
-        const int i = base + p;
-        // past the end: a point with x' = 0 in every dimension (bytes 0x80),
-        // so that no byte borrows and g stays below 2^d; it adds nothing
-        uint32_t w0 = 0, w1 = 0;
+      // kBuildPts points per thread at a time: all their rank loads first
+      for (int p0 = tid; p0 < cnt8; p0 += THREADS * kBuildPts) {
+        uint32_t rr[kBuildPts][DD];
 #pragma unroll
-        for (int m = 0; m < DD; ++m) {
-          const uint32_t x = (p < cnt ? xrank(tab, m, NWmax, rk[(int64_t)m * N + i]) : 0u) | 0x80u;
-          if (m < 4) w0 |= x << (8 * m);
-          else w1 |= x << (8 * (m - 4));
+        for (int u = 0; u < kBuildPts; ++u) {
+          const int p = p0 + u * THREADS;
+#pragma unroll
+          for (int m = 0; m < DD; ++m) rr[u][m] = p < cnt ? rk[(int64_t)m * N + base + p] : 0u;
         }
-        tile[p] = make_uint2(w0, w1);
-        tinc[p] = p >= cnt ? 0u : (i < NP ? 1u : (1u << 16));  // past the end: adds nothing
+#pragma unroll
+        for (int u = 0; u < kBuildPts; ++u) {
+          const int p = p0 + u * THREADS;
+          if (p >= cnt8) break;
+          // past the end: a point with x' = 0 in every dimension (bytes 0x80),
+          // so that no byte borrows and g stays below 2^d; it adds nothing
+          uint32_t w0 = 0, w1 = 0;
+#pragma unroll
+          for (int m = 0; m < DD; ++m) {
+            const uint32_t x = (p < cnt ? xrank(tab, m, NWmax, rr[u][m]) : 0u) | 0x80u;
+            if (m < 4) w0 |= x << (8 * m);
+            else w1 |= x << (8 * (m - 4));
+          }
+          tile[p] = make_uint2(w0, w1);
+          tinc[p] = p >= cnt ? 0u : (base + p < NP ? 1u : (1u << 16));  // past the end: adds nothing
+        }
       }
       __syncthreads();
       uint32_t* col = hist + tid;

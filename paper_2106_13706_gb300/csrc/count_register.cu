@@ -34,6 +34,8 @@
 // an mbarrier, and every lane reads the same record (broadcast loads).  The
 // last unit of a block turns the block's counters into per-origin maxima and
 // the last block writes the result.
+#include <type_traits>
+
 #include "bulk_copy.cuh"
 #include "count_register.cuh"
 #include "ddks_host.h"
@@ -391,7 +393,49 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
     wlo = (int)((sample == 0 ? m0.sP : m0.sT) >> 5);
     whi = (int)((sample == 0 ? mL.sP : mL.sT) >> 5) + 1;
   }
-  bool all_crossed = g0 - gbase >= whi;
+  // one group of 32 points against both origins; CHECK: the group lies in
+  // the window, so an origin may pass its split here
+  auto group = [&](const uint4* __restrict__ tile, int gi, int gidx, auto check) {
+    constexpr bool CHECK = decltype(check)::value;
+    // compare the group's 32 points with both origins, dimension by dimension
+    uint32_t G[kOPL][DS];
+#pragma unroll
+    for (int m = 0; m < DS; ++m) {
+      const uint4 a = tile[(gi * RW + m * 8) / 4];
+      const uint4 b = tile[(gi * RW + m * 8) / 4 + 1];
+      const uint32_t pl[kBits] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z};
+#pragma unroll
+      for (int o = 0; o < kOPL; ++o) {
+        uint32_t r = 0xFFFFFFFFu;
+#pragma unroll
+        for (int k = 0; k < kBits; ++k) r = cmp_step(s[o][m][k], pl[k], r);
+        G[o][m] = r;
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < kOPL; ++o) {
+      uint32_t M[NS + 1];
+      M[0] = 0xFFFFFFFFu;
+#pragma unroll
+      for (int S = 1; S <= NS; ++S) {
+        // G of the lowest dimension in S; every index folds in the unrolled loop
+        const uint32_t gl = (S & 1) ? G[o][0] : ((S & 2) ? G[o][DS > 1 ? 1 : 0] : G[o][DS > 2 ? 2 : 0]);
+        M[S] = M[S & (S - 1)] & gl;
+      }
+      if (CHECK) {
+        const int pos0 = gidx * 32;  // sample-local position of bit 0
+        if (!crossed[o] && pos0 + 32 > split[o]) {
+          // the group holds the origin's split, or begins phase B
+          const uint32_t pa = pos0 < split[o] ? ~(0xFFFFFFFFu << (split[o] - pos0)) : 0u;  // phase-A points
+#pragma unroll
+          for (int S = 1; S <= NS; ++S) snap[o][S - 1] = acc[o][S - 1] + (uint32_t)__popc(M[S] & pa);
+          crossed[o] = true;
+        }
+      }
+#pragma unroll
+      for (int S = 1; S <= NS; ++S) acc[o][S - 1] += (uint32_t)__popc(M[S]);
+    }
+  };
   for (int t = 0; t < ntiles; ++t) {
     const int base = g0 + t * kTG;
     const int n = (g1 - base) < kTG ? (g1 - base) : kTG;
@@ -400,48 +444,16 @@ k_register(const uint32_t* __restrict__ rec, const uint8_t* __restrict__ oplanes
     const bool ok = bk::wait(bar_s + 8u * (uint32_t)(t % NST), (uint32_t)((t / NST) & 1), wait_ns);
     if (ok) {
       const uint4* tile = reinterpret_cast<const uint4*>(tiles + (t % NST) * kTG * RW);
+      // tile-local groups [wa, wb) lie in the window; before it no split is
+      // reached, after it every split is behind
+      const int off = base - gbase;  // sample-local group of gi = 0
+      const int wa = wlo - off < 0 ? 0 : (wlo - off > n ? n : wlo - off);
+      const int wb = whi - off < wa ? wa : (whi - off > n ? n : whi - off);
 #pragma unroll 2
-      for (int gi = 0; gi < n; ++gi) {
-        // compare the group's 32 points with both origins, dimension by dimension
-        uint32_t G[kOPL][DS];
-#pragma unroll
-        for (int m = 0; m < DS; ++m) {
-          const uint4 a = tile[(gi * RW + m * 8) / 4];
-          const uint4 b = tile[(gi * RW + m * 8) / 4 + 1];
-          const uint32_t pl[kBits] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z};
-#pragma unroll
-          for (int o = 0; o < kOPL; ++o) {
-            uint32_t r = 0xFFFFFFFFu;
-#pragma unroll
-            for (int k = 0; k < kBits; ++k) r = cmp_step(s[o][m][k], pl[k], r);
-            G[o][m] = r;
-          }
-        }
-        const int gidx = base + gi - gbase;  // sample-local group
-        const int pos0 = gidx * 32;          // sample-local position of bit 0
-        const bool inwin = !all_crossed && gidx >= wlo;  // warp-uniform
-#pragma unroll
-        for (int o = 0; o < kOPL; ++o) {
-          uint32_t M[NS + 1];
-          M[0] = 0xFFFFFFFFu;
-#pragma unroll
-          for (int S = 1; S <= NS; ++S) {
-            // G of the lowest dimension in S; every index folds in the unrolled loop
-            const uint32_t gl = (S & 1) ? G[o][0] : ((S & 2) ? G[o][DS > 1 ? 1 : 0] : G[o][DS > 2 ? 2 : 0]);
-            M[S] = M[S & (S - 1)] & gl;
-          }
-          if (inwin && !crossed[o] && pos0 + 32 > split[o]) {
-            // the group holds the origin's split, or begins phase B
-            const uint32_t pa = pos0 < split[o] ? ~(0xFFFFFFFFu << (split[o] - pos0)) : 0u;  // phase-A points
-#pragma unroll
-            for (int S = 1; S <= NS; ++S) snap[o][S - 1] = acc[o][S - 1] + (uint32_t)__popc(M[S] & pa);
-            crossed[o] = true;
-          }
-#pragma unroll
-          for (int S = 1; S <= NS; ++S) acc[o][S - 1] += (uint32_t)__popc(M[S]);
-        }
-        if (inwin && gidx + 1 >= whi) all_crossed = true;  // every split of the block is behind
-      }
+      for (int gi = 0; gi < wa; ++gi) group(tile, gi, off + gi, std::false_type{});
+      for (int gi = wa; gi < wb; ++gi) group(tile, gi, off + gi, std::true_type{});
+#pragma unroll 2
+      for (int gi = wb; gi < n; ++gi) group(tile, gi, off + gi, std::false_type{});
     }
     // every thread is done with stage t % NST; a timed-out wait ends the unit
     if (__syncthreads_or(!ok)) {
