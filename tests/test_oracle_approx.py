@@ -276,3 +276,64 @@ def test_pins_hold_for_the_oracle(tmp_path):
 @pytest.mark.parametrize("name,old,new", APPROX_MUTATIONS, ids=[m[0] for m in APPROX_MUTATIONS])
 def test_planted_mistake_is_caught(tmp_path, name, old, new):
     assert not _pins_hold(_mutant(tmp_path, name, old, new))
+
+
+def _ks_num_sorted(dp, dt):
+    """sup over r of |#P(dist <= r)*NT - #T(dist <= r)*NP| by one sorted sweep."""
+    NP, NT = len(dp), len(dt)
+    allv = np.concatenate([dp, dt])
+    is_p = np.concatenate([np.ones(NP, dtype=np.int64), np.zeros(NT, dtype=np.int64)])
+    order = np.argsort(allv, kind="stable")
+    v = allv[order]
+    cp = np.cumsum(is_p[order])
+    ct = np.cumsum(1 - is_p[order])
+    last = np.r_[v[1:] != v[:-1], True]  # evaluate after every distance equal to r
+    return int(np.abs(cp[last] * NT - ct[last] * NP).max())
+
+
+def test_rdks_expanded_distance_agrees_with_euclidean():
+    # The oracle (and the kernel) compute the squared distance to e_m as
+    # (|x'|^2 - 2 x'_m) + 1 (rdKS linear in d, Sec. 2.2 / Sec. 4) instead of
+    # sum_j (x'_j - e_j)^2.  Over many seeds and value structures -- continuous
+    # data, heavy tails, and dyadic grids whose distances tie exactly -- the two
+    # forms give the same per-corner statistic, and the pairs of distances the
+    # two forms put in a different order are rare (near-ties within rounding).
+    rng = np.random.default_rng(2024)
+    inversions = pairs = 0
+    for case in range(60):
+        d = int(rng.integers(2, 11))
+        n_p, n_t = int(rng.integers(20, 300)), int(rng.integers(20, 300))
+        kind = case % 4
+        if kind == 0:
+            P, T = rng.random((n_p, d)), rng.random((n_t, d)) ** 1.3
+        elif kind == 1:
+            P, T = rng.standard_cauchy((n_p, d)), rng.standard_cauchy((n_t, d)) + 0.2
+        elif kind == 2:  # dyadic grid: normalised coordinates k/16, exact ties
+            P = rng.integers(0, 17, size=(n_p, d)) / 16.0
+            T = rng.integers(0, 17, size=(n_t, d)) / 16.0
+            P[0], T[0] = 0.0, 1.0  # the range is exactly [0, 1]
+        else:
+            P, T = rng.standard_normal((n_p, d)), rng.standard_normal((n_t, d)) * 1.1
+        r = orc.rdks(P, T)
+        X = np.concatenate([P, T]).astype(np.float64)
+        lo, hi = X.min(axis=0), X.max(axis=0)
+        span = np.where(hi > lo, hi - lo, 1.0)
+        Xn = np.where(hi > lo, (X - lo) / span, 0.0)
+        s = np.zeros(len(Xn))
+        for j in range(d):  # the oracle's order: dimension by dimension
+            s = s + Xn[:, j] * Xn[:, j]
+        for c in range(d + 1):
+            e = np.zeros(d)
+            if c > 0:
+                e[c - 1] = 1.0
+            euclid = ((Xn - e) ** 2).sum(axis=1)
+            expanded = s if c == 0 else (s - 2.0 * Xn[:, c - 1]) + 1.0
+            assert int(r["per_corner"][c]) == _ks_num_sorted(euclid[:n_p], euclid[n_p:]), (case, c)
+            assert _ks_num_sorted(expanded[:n_p], expanded[n_p:]) == int(r["per_corner"][c]), (case, c)
+            if case % 6 == 0 and c < 3:
+                a = np.sign(euclid[:, None] - euclid[None, :])
+                b = np.sign(expanded[:, None] - expanded[None, :])
+                inversions += int((a != b).sum()) // 2
+                pairs += len(euclid) * (len(euclid) - 1) // 2
+    assert pairs > 100000
+    assert inversions <= pairs * 1e-4, (inversions, pairs)
