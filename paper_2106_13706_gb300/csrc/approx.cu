@@ -1059,6 +1059,400 @@ k_rdks_final(const ull* __restrict__ per_corner, int S, ull* __restrict__ out3) 
   }
 }
 
+// ------------------------------------------------------------------ rdKS by histogram
+//
+// GetDFromCornerLists without a full sort.  The statistic of a corner is
+// sup over run ends r of |D(r)|, D(r) = #P(dist <= r) * NT - #T(dist <= r) * NP
+// (exact integers).  The corner's keys are counted into 2^15 buckets of equal
+// width in key space between the row's smallest and largest key (one pass:
+// shared-memory counts per chunk of keys, then a sum over the chunks, P and
+// T counts in one 64-bit word).  Equal keys share a
+// bucket, so every bucket end is a run end and D there is exact; inside a
+// bucket D moves by +NT per P point and -NP per T point, so a bucket holding
+// one sample only has its extremes at its ends, and a mixed bucket can exceed
+// the best bucket end LB only if max(|D_start + nP*NT|, |D_start - nT*NP|) >
+// LB.  Only those candidate buckets are gathered and sorted (in shared
+// memory, one CTA each) and walked from D_start.  A row with more than
+// kMaxCand candidates, or a candidate with more than kRefineCap points, sets
+// kFlagRedo and the host reruns the call on the sorting path.
+constexpr int kHistBits = 15;
+constexpr int kHistB = 1 << kHistBits;
+constexpr int kMaxCand = 1024;
+constexpr int kRefineCap = 8192;
+constexpr int kCandThreads = 1024;
+
+constexpr size_t kRefineSmem = (size_t)kRefineCap * 9;
+constexpr int kWarpRefineMax = 512;  // candidates of up to this many points: one warp each, no sort
+
+struct RdksCand {
+  long long dstart;   // D before the bucket's first point
+  uint32_t off;       // first slot of the bucket's points in the gather buffer (row-local)
+  uint32_t n;         // points in the bucket
+};
+
+DDKS_DEV int hist_shift(ull kmin, ull kmax) {
+  const ull range = kmax - kmin;
+  if (range == 0) return 0;
+  const int bits = 64 - __clzll((long long)range);
+  return bits > kHistBits ? bits - kHistBits : 0;
+}
+
+// per corner: the smallest and largest key
+__global__ void __launch_bounds__(kThreads)
+k_rdks_krange(const ull* __restrict__ keys, int64_t N, ull* __restrict__ kmin, ull* __restrict__ kmax) {
+  const int s = blockIdx.y;
+  const ull* row = keys + (int64_t)s * N;
+  ull lo = ~0ull, hi = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < N; i += 4 * stride) {  // four loads in flight
+    ull k[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) k[u] = row[i + u * stride];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      lo = k[u] < lo ? k[u] : lo;
+      hi = k[u] > hi ? k[u] : hi;
+    }
+  }
+  for (; i < N; i += stride) {
+    const ull k = row[i];
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const ull a = __shfl_xor_sync(0xffffffffu, lo, off), b = __shfl_xor_sync(0xffffffffu, hi, off);
+    lo = a < lo ? a : lo;
+    hi = b > hi ? b : hi;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&kmin[s], lo);
+    atomicMax(&kmax[s], hi);
+  }
+}
+
+// Per chunk of kHistChunk keys of a corner (grid (chunks, S)), the bucket
+// counts in shared memory, P | T << 16 (a chunk has fewer than 2^16 keys),
+// written out whole: part[s][chunk][b].
+constexpr int kHistChunk = 65535;
+constexpr int kHistThreads = 1024;
+
+__global__ void __launch_bounds__(kHistThreads)
+k_rdks_hist(const ull* __restrict__ keys, int64_t N, int64_t NP, const ull* __restrict__ kmin,
+            const ull* __restrict__ kmax, uint32_t* __restrict__ part) {
+  extern __shared__ __align__(16) uint32_t hsm[];  // [kHistB]
+  const int s = blockIdx.y;
+  const ull* row = keys + (int64_t)s * N;
+  const ull k0 = kmin[s];
+  const int sh = hist_shift(k0, kmax[s]);
+  for (int b = threadIdx.x; b < kHistB; b += kHistThreads) hsm[b] = 0u;
+  __syncthreads();
+  const int64_t i0 = (int64_t)blockIdx.x * kHistChunk;
+  const int64_t i1 = i0 + kHistChunk < N ? i0 + kHistChunk : N;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += kHistThreads) {
+    const uint32_t b = (uint32_t)((row[i] - k0) >> sh);
+    atomicAdd(&hsm[b], i < NP ? 1u : (1u << 16));
+  }
+  __syncthreads();
+  uint32_t* out = part + ((int64_t)s * gridDim.x + blockIdx.x) * kHistB;
+  for (int b = threadIdx.x; b < kHistB; b += kHistThreads) out[b] = hsm[b];
+}
+
+// H[s][b] = sum over the chunks, as P | T << 32
+__global__ void __launch_bounds__(kThreads)
+k_rdks_hist_sum(const uint32_t* __restrict__ part, int chunks, ull* __restrict__ H) {
+  const int s = blockIdx.y;
+  for (int b = blockIdx.x * kThreads + threadIdx.x; b < kHistB; b += gridDim.x * kThreads) {
+    ull p = 0, t = 0;
+    for (int c = 0; c < chunks; ++c) {
+      const uint32_t v = part[((int64_t)s * chunks + c) * kHistB + b];
+      p += v & 0xFFFFu;
+      t += v >> 16;
+    }
+    H[(int64_t)s * kHistB + b] = p | (t << 32);
+  }
+}
+
+// One CTA per corner: D at every bucket end (LB = their maximum, the row's
+// statistic so far), then the candidate buckets with their D_start and
+// places in the gather buffer (taken in any order); slot[s][b] = candidate
+// index or -1.  Warp w walks buckets [w * kPerW, (w + 1) * kPerW), 32 at a time.
+__global__ void __launch_bounds__(kCandThreads)
+k_rdks_cands(const ull* __restrict__ H, int64_t NP, int64_t NT, ull* __restrict__ pc, int* __restrict__ slot,
+             RdksCand* __restrict__ cand, int* __restrict__ ccount, unsigned* __restrict__ fill,
+             unsigned* __restrict__ flags) {
+  constexpr int kW = kCandThreads / 32;
+  constexpr int kPerW = kHistB / kW;
+  __shared__ unsigned long long ws[kW];
+  __shared__ unsigned long long s_lb;
+  __shared__ unsigned s_nc, s_np;
+  const int s = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const ull* h = H + (int64_t)s * kHistB + warp * kPerW;
+  const long long nt = (long long)NT, np = (long long)NP;
+  auto D = [&](ull c) { return (long long)(c & 0xFFFFFFFFull) * nt - (long long)(c >> 32) * np; };
+  auto ab = [](long long v) { return (ull)(v < 0 ? -v : v); };
+  // inclusive scan of the packed (P, T) counts over the warp's lanes (the
+  // halves cannot carry: NP, NT < 2^32)
+  auto wscan = [&](ull v) {
+    for (int off = 1; off < 32; off <<= 1) {
+      const ull y = __shfl_up_sync(0xffffffffu, v, off);
+      if (lane >= off) v += y;
+    }
+    return v;
+  };
+  ull sum = 0;
+#pragma unroll 8
+  for (int j = lane; j < kPerW; j += 32) sum += h[j];
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+  if (lane == 0) ws[warp] = sum;
+  if (tid == 0) { s_nc = 0; s_np = 0; }
+  __syncthreads();
+  ull base = 0;
+  for (int w = 0; w < warp; ++w) base += ws[w];
+  // LB: the largest |D| at a bucket end
+  ull lb = 0, carry = base;
+  for (int j0 = 0; j0 < kPerW; j0 += 32 * 8) {
+    ull hv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) hv[u] = h[j0 + 32 * u + lane];  // eight loads in flight
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const ull inc = wscan(hv[u]);
+      const ull v = ab(D(carry + inc));
+      lb = v > lb ? v : lb;
+      carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const ull y = __shfl_xor_sync(0xffffffffu, lb, off);
+    lb = y > lb ? y : lb;
+  }
+  __syncthreads();  // ws is reused
+  if (lane == 0) ws[warp] = lb;
+  __syncthreads();
+  if (tid == 0) {
+    ull m = 0;
+    for (int w = 0; w < kW; ++w) m = ws[w] > m ? ws[w] : m;
+    s_lb = m;
+    pc[s] = m;
+  }
+  __syncthreads();
+  lb = s_lb;
+  // candidates: mixed buckets whose reachable extreme beats LB
+  static_assert(kPerW % 256 == 0, "eight chunks of 32 buckets per step");
+  carry = base;
+  for (int j0 = 0; j0 < kPerW; j0 += 32) {
+    const ull hb = h[j0 + lane];
+    const ull inc = wscan(hb);
+    const long long ds = D(carry + inc - hb);
+    const ull nP = hb & 0xFFFFFFFFull, nT = hb >> 32;
+    int sl = -1;
+    if (nP && nT && (ab(ds + (long long)nP * nt) > lb || ab(ds - (long long)nT * np) > lb)) {
+      const unsigned k = atomicAdd(&s_nc, 1u);
+      const unsigned off = atomicAdd(&s_np, (unsigned)(nP + nT));
+      if (k < (unsigned)kMaxCand) {
+        sl = (int)k;
+        RdksCand cd;
+        cd.dstart = ds;
+        cd.off = off;
+        cd.n = (unsigned)(nP + nT);
+        cand[(int64_t)s * kMaxCand + k] = cd;
+        fill[(int64_t)s * kMaxCand + k] = 0u;
+        if (cd.n > (unsigned)kRefineCap) atomicOr(flags, ddks::kFlagRedo);
+      }
+    }
+    slot[(int64_t)s * kHistB + warp * kPerW + j0 + lane] = sl;
+    carry += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    ccount[s] = s_nc < (unsigned)kMaxCand ? (int)s_nc : kMaxCand;
+    if (s_nc > (unsigned)kMaxCand) atomicOr(flags, ddks::kFlagRedo);
+  }
+}
+
+// the points of the candidate buckets, with their sample (1 = P)
+__global__ void __launch_bounds__(kThreads)
+k_rdks_gather(const ull* __restrict__ keys, int64_t N, int64_t NP, const ull* __restrict__ kmin,
+              const ull* __restrict__ kmax, const int* __restrict__ slot, const RdksCand* __restrict__ cand,
+              unsigned* __restrict__ fill, ull* __restrict__ gk, uint8_t* __restrict__ gl) {
+  const int s = blockIdx.y;
+  const ull* row = keys + (int64_t)s * N;
+  const ull k0 = kmin[s];
+  const int sh = hist_shift(k0, kmax[s]);
+  const int* sl = slot + (int64_t)s * kHistB;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < N; i0 += 4 * stride) {
+    // four keys at a time: their loads, then their buckets' slots, in flight together
+    ull k[4];
+    int c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) k[u] = i0 + u * stride < N ? row[i0 + u * stride] : k0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) c[u] = i0 + u * stride < N ? sl[(k[u] - k0) >> sh] : -1;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (c[u] < 0) continue;
+      const int64_t i = i0 + u * stride;
+      const RdksCand cd = cand[(int64_t)s * kMaxCand + c[u]];
+      const unsigned pos = atomicAdd(&fill[(int64_t)s * kMaxCand + c[u]], 1u);
+      if (pos >= cd.n || cd.n > (unsigned)kRefineCap) continue;  // never past the bucket's places
+      gk[(int64_t)s * N + cd.off + pos] = k[u];
+      gl[(int64_t)s * N + cd.off + pos] = i < NP ? 1 : 0;
+    }
+  }
+}
+
+// One warp per candidate of at most kWarpRefineMax points (E per lane): no
+// sort -- for each point, the points of each sample whose key is <= its key
+// give D at the end of its run (equal keys give the same value).
+template <int E>
+DDKS_DEV ull warp_refine(const ull* __restrict__ sk, const uint8_t* __restrict__ sp, int n, long long dstart,
+                         long long nt, long long np, int lane) {
+  ull mine[E];
+  unsigned cpn[E], cnn[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    mine[e] = e * 32 + lane < n ? sk[e * 32 + lane] : 0ull;
+    cpn[e] = cnn[e] = 0;
+  }
+  for (int j = 0; j < n; ++j) {
+    const ull kj = sk[j];
+    const unsigned pj = sp[j];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const unsigned le = kj <= mine[e] ? 1u : 0u;
+      cpn[e] += le & pj;
+      cnn[e] += le;
+    }
+  }
+  ull best = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (e * 32 + lane >= n) break;
+    const long long dv = dstart + (long long)cpn[e] * nt - (long long)(cnn[e] - cpn[e]) * np;
+    const ull v = (ull)(dv < 0 ? -dv : dv);
+    best = v > best ? v : best;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const ull y = __shfl_xor_sync(0xffffffffu, best, off);
+    best = y > best ? y : best;
+  }
+  return best;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_rdks_refine_warp(const ull* __restrict__ gk, const uint8_t* __restrict__ gl, int64_t N, int64_t NP, int64_t NT,
+                   const RdksCand* __restrict__ cand, const int* __restrict__ ccount, ull* __restrict__ pc) {
+  constexpr int kW = kThreads / 32;
+  __shared__ ull sk_all[kW][kWarpRefineMax];
+  __shared__ uint8_t sp_all[kW][kWarpRefineMax];
+  const int s = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ull* sk = sk_all[warp];
+  uint8_t* sp = sp_all[warp];
+  const long long nt = (long long)NT, np = (long long)NP;
+  // candidate ci goes to CTA ci % gridDim.x, so the work spreads over the SMs
+  for (int ci = blockIdx.x + gridDim.x * warp; ci < ccount[s]; ci += gridDim.x * kW) {
+    const RdksCand cd = cand[(int64_t)s * kMaxCand + ci];
+    const int n = (int)cd.n;
+    if (n > kWarpRefineMax) continue;  // the CTA kernel's
+    for (int i = lane; i < n; i += 32) {
+      sk[i] = gk[(int64_t)s * N + cd.off + i];
+      sp[i] = gl[(int64_t)s * N + cd.off + i];
+    }
+    __syncwarp();
+    const ull best = n <= 128   ? warp_refine<4>(sk, sp, n, cd.dstart, nt, np, lane)
+                     : n <= 256 ? warp_refine<8>(sk, sp, n, cd.dstart, nt, np, lane)
+                     : n <= 384 ? warp_refine<12>(sk, sp, n, cd.dstart, nt, np, lane)
+                                : warp_refine<16>(sk, sp, n, cd.dstart, nt, np, lane);
+    if (lane == 0) atomicMax(&pc[s], best);
+    __syncwarp();  // the warp's buffer is free for its next candidate
+  }
+}
+
+// One CTA per candidate bucket (a grid-stride over them): sort its points
+// in shared memory and walk its run ends from D_start; the row's statistic
+// is the maximum with LB.
+__global__ void __launch_bounds__(kThreads)
+k_rdks_refine(const ull* __restrict__ gk, const uint8_t* __restrict__ gl, int64_t N, int64_t NP, int64_t NT,
+              const RdksCand* __restrict__ cand, const int* __restrict__ ccount, ull* __restrict__ pc) {
+  extern __shared__ __align__(16) unsigned char rsm[];
+  ull* sk = reinterpret_cast<ull*>(rsm);                     // [kRefineCap]
+  uint8_t* sp = reinterpret_cast<uint8_t*>(sk + kRefineCap);  // [kRefineCap]
+  __shared__ unsigned long long wsum[kThreads / 32], wmax[kThreads / 32];
+  const int s = blockIdx.y;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kW = kThreads / 32;
+  const long long nt = (long long)NT, np = (long long)NP;
+  for (int ci = blockIdx.x; ci < ccount[s]; ci += gridDim.x) {
+    const RdksCand cd = cand[(int64_t)s * kMaxCand + ci];
+    const int n = (int)cd.n;
+    if (n > kRefineCap) continue;  // flagged: the host reruns on the sorting path
+    if (n <= kWarpRefineMax) continue;  // refined by k_rdks_refine_warp
+    int P2 = 1;
+    while (P2 < n) P2 <<= 1;
+    __syncthreads();
+    for (int i = tid; i < P2; i += kThreads) {
+      sk[i] = i < n ? gk[(int64_t)s * N + cd.off + i] : ~0ull;
+      sp[i] = i < n ? gl[(int64_t)s * N + cd.off + i] : 0;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P2; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int t = tid; t < P2 / 2; t += kThreads) {
+          const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+          const bool asc = (lo & size) == 0;
+          const ull a = sk[lo], b = sk[hi];
+          if (asc ? b < a : a < b) {
+            sk[lo] = b;
+            sk[hi] = a;
+            const uint8_t x = sp[lo];
+            sp[lo] = sp[hi];
+            sp[hi] = x;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // inclusive prefix of P points over the sorted positions, chunk per thread
+    const int seg = (n + kThreads - 1) / kThreads;
+    const int a0 = tid * seg < n ? tid * seg : n, a1 = a0 + seg < n ? a0 + seg : n;
+    unsigned long long cp = 0;
+    for (int i = a0; i < a1; ++i) cp += sp[i];
+    unsigned long long inc = cp;
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    unsigned long long run = inc - cp;
+    for (int w = 0; w < warp; ++w) run += wsum[w];
+    ull best = 0;
+    for (int i = a0; i < a1; ++i) {
+      run += sp[i];
+      if (i + 1 == n || sk[i + 1] != sk[i]) {  // a run end
+        const long long dv = cd.dstart + (long long)run * nt - (long long)(i + 1 - (long long)run) * np;
+        const ull v = (ull)(dv < 0 ? -dv : dv);
+        best = v > best ? v : best;
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const ull y = __shfl_xor_sync(0xffffffffu, best, off);
+      best = y > best ? y : best;
+    }
+    if (lane == 0) wmax[warp] = best;
+    __syncthreads();
+    if (tid == 0) {
+      ull m = 0;
+      for (int w = 0; w < kW; ++w) m = wmax[w] > m ? wmax[w] : m;
+      atomicMax(&pc[s], m);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ host
 
 int grid_cap(int64_t work, int per_block, int cap) {
@@ -1369,8 +1763,26 @@ int ddks_rescale(ddks_ctx* ctx, const double* v, int64_t n, double lo, double sp
   return DDKS_OK;
 }
 
+// pooled sizes from which rdKS takes the histogram path (below: sort and walk),
+// for up to kRdksHistMaxS corners (its buckets take 12 bytes x 2^16 per corner)
+constexpr int64_t kRdksHistMinN = 8192;
+constexpr int kRdksHistMaxS = 64;
+
+static int rdks_run(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT, int32_t d, int32_t dtype,
+                    void* stream, ddks_result* out, uint64_t* per_corner, bool allow_hist, bool* redo);
+
 int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT, int32_t d,
               int32_t dtype, void* stream, ddks_result* out, uint64_t* per_corner) {
+  bool redo = false;
+  int rc = rdks_run(ctx, P, NP, T, NT, d, dtype, stream, out, per_corner, true, &redo);
+  if (rc == DDKS_OK && redo)  // the histogram path met a bucket it does not refine: sort instead
+    rc = rdks_run(ctx, P, NP, T, NT, d, dtype, stream, out, per_corner, false, &redo);
+  return rc;
+}
+
+static int rdks_run(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT, int32_t d, int32_t dtype,
+                    void* stream, ddks_result* out, uint64_t* per_corner, bool allow_hist, bool* redo) {
+  *redo = false;
   if (!ctx || !out) return DDKS_EINVAL;
   if (d < 1 || d > DDKS_RDKS_MAX_D) return out->status = DDKS_EINVAL;
   int rc = ddks_check_problem(P, NP, T, NT, 1, dtype);
@@ -1394,14 +1806,25 @@ int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
   if ((rc = ctx->ti2.reserve(ctx, 4 * segs))) return out->status = rc;
   if ((rc = ctx->apx_cnt.reserve(ctx, 4 * segs))) return out->status = rc;  // P prefixes
   if ((rc = ctx->apx_U.reserve(ctx, 4 * segs))) return out->status = rc;
-  const bool radix = N > 1024 && ddks_use_radix(ctx, N, 64);
+  const bool hist = allow_hist && N >= kRdksHistMinN && S <= kRdksHistMaxS;
+  const bool radix = !hist && N > 1024 && ddks_use_radix(ctx, N, 64);
   if (radix && (rc = ctx->radix.reserve(ctx, 4 * ddks_radix_scratch_words(N, S, 0)))) return out->status = rc;
+  // histogram path scratch: partial histograms [S][chunks][B] u32, H [S][B]
+  // u64, slot [S][B] i32, cand [S][kMaxCand], fill [S][kMaxCand] u32, kmin
+  // [S], kmax [S], ccount [S]
+  const int hchunks = (int)((N + kHistChunk - 1) / kHistChunk);
+  const size_t a_part = 0, a_H = a_part + 4 * (size_t)S * hchunks * kHistB;
+  const size_t a_slot = a_H + 8 * (size_t)S * kHistB, a_cand = a_slot + 4 * (size_t)S * kHistB;
+  const size_t a_fill = a_cand + sizeof(RdksCand) * (size_t)S * kMaxCand;
+  const size_t a_kmin = (a_fill + 4 * (size_t)S * kMaxCand + 15) & ~(size_t)15;
+  const size_t a_kmax = a_kmin + 8 * (size_t)S, a_cc = a_kmax + 8 * (size_t)S, a_end = a_cc + 4 * (size_t)S;
+  if (hist && (rc = ctx->rdks_aux.reserve(ctx, a_end))) return out->status = rc;
   // warp kernel: shared memory of 2 * d doubles per warp
   int nwb = (int)((96 * 1024) / (16 * (size_t)d));
   nwb = nwb < 1 ? 1 : (nwb > 2 ? 2 : nwb);
   GraphKey key;
   key.add(8).add((uint64_t)NP).add((uint64_t)NT).add((uint64_t)d).add((uint64_t)dtype);
-  key.add_ptr(dP).add_ptr(dT).add((uint64_t)ctx->stage_timing);
+  key.add_ptr(dP).add_ptr(dT).add((uint64_t)ctx->stage_timing).add((uint64_t)hist);
   rc = ddks_graph_run(ctx, key.h, st, [&](cudaStream_t s) -> int {
     char* sm = (char*)ctx->apx_small.ptr;
     ull* gmin = (ull*)(sm + L.gmin);
@@ -1465,6 +1888,45 @@ int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
       ddks_stage_mark(ctx, 3, s);
       return DDKS_OK;
     }
+    if (hist) {
+      char* ax = (char*)ctx->rdks_aux.ptr;
+      ull* H = (ull*)(ax + a_H);
+      uint32_t* part = (uint32_t*)(ax + a_part);
+      int* slot = (int*)(ax + a_slot);
+      RdksCand* cand = (RdksCand*)(ax + a_cand);
+      unsigned* fill = (unsigned*)(ax + a_fill);
+      ull* kmin = (ull*)(ax + a_kmin);
+      ull* kmax = (ull*)(ax + a_kmax);
+      int* ccount = (int*)(ax + a_cc);
+      ull* gk = (ull*)ctx->tk1.ptr;
+      uint8_t* gl = (uint8_t*)ctx->ti1.ptr;
+      ee = cudaMemsetAsync(kmin, 0xFF, 8 * (size_t)S, s);
+      if (ee == cudaSuccess) ee = cudaFuncSetAttribute(k_rdks_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)(4 * kHistB));
+      if (ee == cudaSuccess) ee = cudaMemsetAsync(kmax, 0, 8 * (size_t)S, s);
+      if (ee == cudaSuccess) ee = cudaFuncSetAttribute(k_rdks_refine, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)kRefineSmem);
+      if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "rdks histogram setup");
+      int gx = grid_cap(N, kThreads, ctx->num_sms * 8);
+      const int per = (ctx->num_sms * 8 + S - 1) / S;
+      if (gx > per) gx = per < 1 ? 1 : per;
+      const dim3 g2((unsigned)gx, (unsigned)S);
+      k_rdks_krange<<<g2, kThreads, 0, s>>>(keys, N, kmin, kmax);
+      k_rdks_hist<<<dim3((unsigned)hchunks, (unsigned)S), kHistThreads, 4 * kHistB, s>>>(keys, N, NP, kmin, kmax,
+                                                                                        part);
+      k_rdks_hist_sum<<<dim3((kHistB + kThreads - 1) / kThreads, (unsigned)S), kThreads, 0, s>>>(part, hchunks, H);
+      ddks_stage_mark(ctx, 2, s);
+      k_rdks_cands<<<S, kCandThreads, 0, s>>>(H, NP, NT, pc, slot, cand, ccount, fill, flags);
+      k_rdks_gather<<<g2, kThreads, 0, s>>>(keys, N, NP, kmin, kmax, slot, cand, fill, gk, gl);
+      k_rdks_refine_warp<<<dim3(kMaxCand / 8, (unsigned)S), kThreads, 0, s>>>(gk, gl, N, NP, NT, cand, ccount, pc);
+      k_rdks_refine<<<dim3(16, (unsigned)S), kThreads, kRefineSmem, s>>>(gk, gl, N, NP, NT, cand, ccount, pc);
+      k_rdks_final<<<1, kThreads, 0, s>>>(pc, S, (ull*)sm);
+      ctx->launches += 8;
+      ee = cudaGetLastError();
+      if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "rdks histogram kernels");
+      ddks_stage_mark(ctx, 3, s);
+      return DDKS_OK;
+    }
     const uint64_t* sk;
     const uint32_t *si, *sp;
     int n = 0;
@@ -1508,5 +1970,6 @@ int ddks_rdks(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t N
   if (rc) return out->status = rc;
   rc = finish(ctx, st, L, NP, NT, out, per_corner, (char*)ctx->apx_small.ptr + L.tail, 8 * (size_t)S);
   if (rc == DDKS_OK) out->argmax_orthant = 0;
+  if (rc == DDKS_OK && (ctx->h_out[4] & ddks::kFlagRedo)) *redo = true;
   return rc;
 }

@@ -67,6 +67,7 @@ struct ddks_ctx {
   DevBuf sig_cells, sig_logp;                   // significance
   DevBuf batch_desc, batch_work;                // batched launch
   DevBuf apx_small, apx_cnt, apx_U, apx_hist;   // vdKS / rdKS (approx.cu)
+  DevBuf rdks_aux;                              // rdKS by histogram: buckets, candidates
   DevBuf dom_work;                              // d = 2 range-query path (dominance.cu)
   DevBuf radix;                                 // radix sort counts / offsets / flags (radix.cu)
   unsigned long long* h_out = nullptr;          // pinned, 64 entries
@@ -99,7 +100,7 @@ struct ddks_ctx {
     return {&inP, &inT, &keys, &tk1, &tk2, &ti1, &ti2, &rank, &sidx0, &pfx0, &best, &bestj, &out3,
             &flags, &reg_words, &reg_meta, &warp_words, &perm_keys, &perm_labels, &perm_best, &perm_codes,
             &sig_cells, &sig_logp, &batch_desc, &batch_work, &apx_small, &apx_cnt, &apx_U, &apx_hist, &dom_work,
-            &radix};
+            &radix, &rdks_aux};
   }
 };
 

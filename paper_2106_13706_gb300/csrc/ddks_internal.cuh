@@ -19,8 +19,10 @@ constexpr int kMaxD = 30;
 
 // error flags raised by kernels and read back by the host
 // (kFlagRange: a coordinate range that cannot be rescaled to [0, 1], the
-// normalisation of the vdKS / rdKS approximations)
-enum : unsigned { kFlagNaN = 1u, kFlagTimeout = 2u, kFlagBounds = 4u, kFlagRange = 8u };
+// normalisation of the vdKS / rdKS approximations; kFlagRedo: not an error,
+// a fast path met data it does not take and the host reruns the call on the
+// general path)
+enum : unsigned { kFlagNaN = 1u, kFlagTimeout = 2u, kFlagBounds = 4u, kFlagRange = 8u, kFlagRedo = 16u };
 
 // Order-preserving image of a float as an unsigned integer: x <= y (IEEE, no
 // NaN) <=> key(x) <= key(y).  -0.0 is mapped like +0.0 so the two compare equal.

@@ -247,3 +247,27 @@ def test_rescale_random_operands(torch, ctx):
         ref = _ieee_rescale(v, 0.0, span)
         got = ctx.rescale(_dev(torch, v), 0.0, span).cpu().numpy()
         assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_rdks_histogram_path(torch, ctx, dtype):
+    # N >= 8192 takes the histogram path: bucket ends exact, mixed buckets
+    # that could beat them sorted in shared memory.  Heavy ties (integer
+    # grids: buckets of equal keys), continuous data, and shapes whose
+    # buckets force the rerun on the sorting path: P = T (every bucket end
+    # is 0, more than 1,024 candidates), one tight cluster plus two outliers
+    # (more than 8,192 points in one candidate bucket), all points equal.
+    rng = np.random.default_rng(77)
+    cases = [wl.random_pair(301, 6000, 5000, 3, kind="int", dtype=dtype),
+             wl.random_pair(302, 9000, 8000, 2, kind="int", dtype=dtype),
+             wl.random_pair(303, 7000, 9000, 5, kind="normal", dtype=dtype)]
+    X = rng.standard_normal((20000, 3)).astype(dtype)
+    cases.append((X, X.copy()))
+    C = (rng.standard_normal((12000, 2)) * 1e-6).astype(dtype)
+    C[0], C[1] = -1.0, 1.0
+    cases.append((C[:6000], C[6000:]))
+    Z = np.ones((5000, 4), dtype=dtype)
+    cases.append((Z, Z[:4000].copy()))
+    for P, T in cases:
+        ref = orc.rdks(P, T)
+        _rdks_same(ctx.rdks(_dev(torch, P), _dev(torch, T)), ref)
