@@ -970,31 +970,66 @@ def run_serve(args):
 
     ctx = pkg.Context(device=0, max_batch=64)
     nums = [None] * len(reqs)  # num_max of each request as served
+    import queue
+    # a pool of client threads started beforehand waits for the tickets (a
+    # thread started per request would put its start-up into the latency)
+    tq = queue.Queue()
+
+    errors = []
+
+    def poller():
+        while True:
+            item = tq.get()
+            if item is None:
+                return
+            try:
+                i, tk, t0, lat = item
+                while True:
+                    rc, r = ctx.poll(tk, 200000)
+                    if rc != pkg.DDKS_PENDING:
+                        if rc == pkg.DDKS_OK:
+                            lat[i] = time.perf_counter() - t0
+                            nums[i] = r["num_max"]
+                        break
+            except Exception as ex:  # a failed request fails the run, it must not hang it
+                errors.append(repr(ex))
+            finally:
+                tq.task_done()
+
+    def drain_tickets(limit_s=300.0):
+        end = time.perf_counter() + limit_s
+        while tq.unfinished_tasks and not errors:
+            if time.perf_counter() > end:
+                raise RuntimeError("served requests still pending after %.0f s" % limit_s)
+            time.sleep(0.0005)
+        if errors:
+            raise RuntimeError("served request failed: " + errors[0])
+
+    pollers = [threading.Thread(target=poller, daemon=True) for _ in range(8)]
+    for th in pollers:
+        th.start()
 
     def submit_fn(i, P, T, lat):
         t0 = time.perf_counter()
-        tk = ctx.submit(P, T)
-
-        def waiter():
-            while True:
-                rc, r = ctx.poll(tk, 200000)
-                if rc != pkg.DDKS_PENDING:
-                    if rc == pkg.DDKS_OK:
-                        lat[i] = time.perf_counter() - t0
-                        nums[i] = r["num_max"]
-                    return
-        th = threading.Thread(target=waiter, daemon=True)
-        th.start()
-        return th
+        tq.put((i, ctx.submit(P, T), t0, lat))
+        return None
 
     lat_b, wall_b = replay(submit_fn)
+    drain_tickets()
+    wall_b = max(wall_b, max(a + l for (a, _, _), l in zip(reqs, lat_b)))
     st = ctx.stats()
     # saturated: every request submitted at once, throughput of the batching loop
-    _, wall_bs = replay(submit_fn, saturated=True)
+    t_sat = time.perf_counter()
+    replay(submit_fn, saturated=True)
+    drain_tickets()
+    wall_bs = time.perf_counter() - t_sat
+    for _ in pollers:
+        tq.put(None)
+    for th in pollers:
+        th.join()
     ctx.close()
     # one request per call, FIFO on one worker thread
     ctx1 = pkg.Context(device=0)
-    import queue
     qq = queue.Queue()
 
     def worker():

@@ -1492,7 +1492,7 @@ cudaError_t launch_minmax(const void* P, const void* T, int64_t NP, int64_t NT, 
   const int64_t S = ((int64_t)g * kThreads * VEC / L) * L;
   const size_t smem = 2 * sizeof(typename NativeKey<V>::K) * (size_t)d;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_minmax<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ddks_smem_attr(k_minmax<V>, (int)smem);
     if (e != cudaSuccess) return e;
   }
   k_minmax<V><<<g, kThreads, smem, st>>>((const V*)P, (const V*)T, NP, NT, d, S, gmin, gmax, flags);
@@ -1506,7 +1506,7 @@ cudaError_t launch_voxel_smem(const void* P, const void* T, int64_t NP, int64_t 
   using K = typename NativeKey<V>::K;
   constexpr int U4 = sizeof(V) == 4 ? 4 : 2;
   auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ddks_smem_attr(kern, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<nb, kVoxThreads, smem, st>>>((const V*)P, (const V*)T, NP, NT, d, Vd, gmin, gmax, (const K*)thr,
                                        use_thr ? 1 : 0, cells, bP, hall, flags);
@@ -1550,7 +1550,7 @@ cudaError_t launch_voxel_bulk(const void* P, const void* T, int64_t NP, int64_t 
                               unsigned long long wait_ns) {
   using K = typename NativeKey<V>::K;
   auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bp.smem);
+    cudaError_t e = ddks_smem_attr(kern, (int)bp.smem);
     if (e != cudaSuccess) return e;
     kern<<<nb, kVoxBulkThreads, bp.smem, st>>>((const V*)P, (const V*)T, NP, NT, d, Vd, gmin, gmax, (const K*)thr,
                                               use_thr ? 1 : 0, cells, bP, bp.r0, bp.rc, bp.thr_off, bp.stage_off,
@@ -1854,12 +1854,12 @@ static int rdks_run(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int
       const size_t smem = (size_t)nwb * 16 * (size_t)d;
       const int g = grid_cap(N, nwb, ctx->num_sms * 16);
       if (f64) {
-        ee = cudaFuncSetAttribute(k_rdks_dist_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ee = ddks_smem_attr(k_rdks_dist_warp<double>, (int)smem);
         if (ee == cudaSuccess)
           k_rdks_dist_warp<double><<<g, 32 * nwb, smem, s>>>((const double*)dP, (const double*)dT, NP, NT, d,
                                                              gmin, gmax, keys, flags);
       } else {
-        ee = cudaFuncSetAttribute(k_rdks_dist_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ee = ddks_smem_attr(k_rdks_dist_warp<float>, (int)smem);
         if (ee == cudaSuccess)
           k_rdks_dist_warp<float><<<g, 32 * nwb, smem, s>>>((const float*)dP, (const float*)dT, NP, NT, d,
                                                             gmin, gmax, keys, flags);
@@ -1901,11 +1901,9 @@ static int rdks_run(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int
       ull* gk = (ull*)ctx->tk1.ptr;
       uint8_t* gl = (uint8_t*)ctx->ti1.ptr;
       ee = cudaMemsetAsync(kmin, 0xFF, 8 * (size_t)S, s);
-      if (ee == cudaSuccess) ee = cudaFuncSetAttribute(k_rdks_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)(4 * kHistB));
+      if (ee == cudaSuccess) ee = ddks_smem_attr(k_rdks_hist, (int)(4 * kHistB));
       if (ee == cudaSuccess) ee = cudaMemsetAsync(kmax, 0, 8 * (size_t)S, s);
-      if (ee == cudaSuccess) ee = cudaFuncSetAttribute(k_rdks_refine, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)kRefineSmem);
+      if (ee == cudaSuccess) ee = ddks_smem_attr(k_rdks_refine, (int)kRefineSmem);
       if (ee != cudaSuccess) return ctx_cuda_fail(ctx, ee, "rdks histogram setup");
       int gx = grid_cap(N, kThreads, ctx->num_sms * 8);
       const int per = (ctx->num_sms * 8 + S - 1) / S;

@@ -714,7 +714,7 @@ cudaError_t launch_bits_ds(int sms, const BatchDesc* desc, int count, int64_t un
                            unsigned long long* next, uint64_t* best, int32_t* bestj, int TG, int nw_max,
                            cudaStream_t s) {
   const size_t smem = bits_smem(DS, TG, nw_max);
-  cudaError_t e = cudaFuncSetAttribute(k_batch_bits<DS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ddks_smem_attr(k_batch_bits<DS>, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_bits<DS>, kBitsThreads, smem);
@@ -732,7 +732,7 @@ cudaError_t launch_bytes_dt(int sms, const BatchDesc* desc, int count, int64_t u
                             cudaStream_t s) {
   const size_t smem = bytes_smem<DD, THREADS>(PT, nw_max);
   cudaError_t e =
-      cudaFuncSetAttribute(k_batch_bytes<DD, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      ddks_smem_attr(k_batch_bytes<DD, THREADS>, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_bytes<DD, THREADS>, THREADS, smem);
@@ -945,7 +945,7 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
         ee = cudaGetLastError();
       }
       if (ee == cudaSuccess && smem_unit)
-        ee = cudaFuncSetAttribute(k_batch_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_unit);
+        ee = ddks_smem_attr(k_batch_count, (int)smem_unit);
       for (size_t gi = 0; gi < gorder.size() && ee == cudaSuccess; ++gi) {
         const Group& G = groups[gorder[gi]];
         const int OT = ctx->batch_ot[G.d], PT = ctx->batch_pt[G.d];

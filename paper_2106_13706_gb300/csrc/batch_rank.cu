@@ -203,12 +203,12 @@ cudaError_t launch_class(const BatchDesc* desc, const int* dprob, const int* ddi
   cudaError_t e;
   if (c.wide) {
     const size_t smem = radix_smem<V>(cap, 1024);
-    e = cudaFuncSetAttribute(k_batch_radix<V, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ddks_smem_attr(k_batch_radix<V, 1024>, (int)smem);
     if (e != cudaSuccess) return e;
     k_batch_radix<V, 1024><<<c.count, 1024, smem, st>>>(desc, dprob + c.first, ddim + c.first, cap, ra, flags);
   } else {
     const size_t smem = radix_smem<V>(cap, 256);
-    e = cudaFuncSetAttribute(k_batch_radix<V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ddks_smem_attr(k_batch_radix<V, 256>, (int)smem);
     if (e != cudaSuccess) return e;
     k_batch_radix<V, 256><<<c.count, 256, smem, st>>>(desc, dprob + c.first, ddim + c.first, cap, ra, flags);
   }

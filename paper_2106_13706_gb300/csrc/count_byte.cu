@@ -231,7 +231,7 @@ cudaError_t ddks_launch_byte(ddks_ctx* ctx, const uint32_t* rank, int64_t N, int
   if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, 8, st);
   if (e != cudaSuccess) return e;
   const size_t psmem = (size_t)W * 5;
-  e = cudaFuncSetAttribute(k_byte_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+  e = ddks_smem_attr(k_byte_pack, (int)psmem);
   if (e != cudaSuccess) return e;
   k_byte_pack<<<dim3((unsigned)blocks, (unsigned)d), kBPrep, psmem, st>>>(rank, N, d, NQ, ob, no, W, (uint8_t*)X8,
                                                                          (uint8_t*)OW);
@@ -244,7 +244,7 @@ cudaError_t ddks_launch_byte(ddks_ctx* ctx, const uint32_t* rank, int64_t N, int
   const int rpb = (kBO + H - 1) / H;
   const size_t smem = byte_smem(d, NQ, H);
   auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t r = ddks_smem_attr(kern, (int)smem);
     if (r != cudaSuccess) return r;
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBThreads, smem);

@@ -488,11 +488,11 @@ cudaError_t ddks_fused_count(ddks_ctx* ctx, int ds, int variant, const uint32_t*
   Final fin{out3, done, packed, best, bestj, ob, (int)blocks};
   const OriginMeta* mt = reinterpret_cast<const OriginMeta*>(meta);
   auto go = [&](auto prep, auto kern, int threads) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prep_smem);
+    cudaError_t e = ddks_smem_attr(prep, (int)prep_smem);
     if (e != cudaSuccess) return e;
     prep<<<(unsigned)blocks, kPrepThreads, prep_smem, st>>>(orank, no, W, tab, oval);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ddks_smem_attr(kern, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);

@@ -115,8 +115,7 @@ cudaError_t launch_t(const uint32_t* rank, int64_t N, int64_t NP, int64_t NT, in
                      int64_t oe, uint64_t* best, int32_t* bestj, cudaStream_t st, int threads,
                      int S) {
   const size_t sm = lane_smem(D, WIDE, threads);
-  cudaError_t e = cudaFuncSetAttribute(k_lane<D, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
+  cudaError_t e = ddks_smem_attr(k_lane<D, WIDE>, (int)sm);
   if (e != cudaSuccess) return e;
   const int64_t no = oe - ob;
   const int TO = threads / S;

@@ -614,15 +614,13 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   }
   if (pack_smem(NW, 4) <= kPackSmemMax) {
     const size_t psmem = pack_smem(NW, 4);
-    e = cudaFuncSetAttribute(k_reg_pack<4, kPack4Threads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)psmem);
+    e = ddks_smem_attr(k_reg_pack<4, kPack4Threads>, (int)psmem);
     if (e != cudaSuccess) return e;
     k_reg_pack<4, kPack4Threads><<<dim3((unsigned)((blocks + 3) / 4), (unsigned)ds), kPack4Threads, psmem, st>>>(
         rankL, orank, no, blocks, NP, NT, NPpad, Lrow, NW, ds, rec, oplanes);
   } else {
     const size_t psmem = pack_smem(NW, 1);
-    e = cudaFuncSetAttribute(k_reg_pack<1, kPackThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)psmem);
+    e = ddks_smem_attr(k_reg_pack<1, kPackThreads>, (int)psmem);
     if (e != cudaSuccess) return e;
     k_reg_pack<1, kPackThreads><<<dim3((unsigned)blocks, (unsigned)ds), kPackThreads, psmem, st>>>(
         rankL, orank, no, blocks, NP, NT, NPpad, Lrow, NW, ds, rec, oplanes);
@@ -647,7 +645,7 @@ cudaError_t ddks_launch_register(ddks_ctx* ctx, const uint32_t* rank, int64_t N,
   const size_t smem = reg_smem(ds, occ);
   Final fin{out3, done, packed, best, bestj, ob, (int)blocks};
   auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t r = ddks_smem_attr(kern, (int)smem);
     if (r != cudaSuccess) return r;
     kern<<<ctas, kThreads, smem, st>>>(rec, oplanes, meta, no, NP, NT, ngroups, (int)C, (int)CP, GP, GT, CGP,
                                         CGT, gcnt, flags, fin, ctx->dev_wait_ns);

@@ -111,7 +111,7 @@ cudaError_t ddks_launch_sort(const uint32_t* rank, int64_t N, int64_t NP, int64_
   int P2 = 1;
   while (P2 < N) P2 <<= 1;
   const size_t sm = (size_t)P2 * 4u;
-  cudaError_t e = cudaFuncSetAttribute(k_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = ddks_smem_attr(k_sort, (int)sm);
   if (e != cudaSuccess) return e;
   const int64_t no = o_end - o_begin;
   if (no <= 0) return cudaSuccess;

@@ -229,11 +229,11 @@ cudaError_t ddks_launch_warp(const uint32_t* rank, int64_t N, int64_t NP, int64_
   if (grid == 0) return cudaSuccess;
   cudaError_t e;
   if (wide) {
-    e = cudaFuncSetAttribute(k_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = ddks_smem_attr(k_warp<true>, (int)sm);
     if (e != cudaSuccess) return e;
     k_warp<true><<<grid, warps * 32, sm, st>>>(rank, N, NP, NT, d, o_begin, o_end, best, bestj);
   } else {
-    e = cudaFuncSetAttribute(k_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = ddks_smem_attr(k_warp<false>, (int)sm);
     if (e != cudaSuccess) return e;
     k_warp<false><<<grid, warps * 32, sm, st>>>(rank, N, NP, NT, d, o_begin, o_end, best, bestj);
   }
@@ -271,7 +271,7 @@ cudaError_t ddks_launch_warp16(ddks_ctx* ctx, const uint32_t* rank, int64_t N, i
   if ((int64_t)H > no) H = (int)no;
   const size_t sm = per_hist * H + 16 + (size_t)H * 8 * 4 + (size_t)W * 8;
   auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t r = ddks_smem_attr(kern, (int)sm);
     if (r != cudaSuccess) return r;
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kW16Threads, sm);

@@ -108,6 +108,9 @@ int ctx_cuda_fail(ddks_ctx* ctx, cudaError_t e, const char* where);
 // 1: device memory of `device` or managed memory (read in place); 0: host
 // memory (copied by the call); DDKS_EINVAL: device memory of another GPU.
 int ddks_pointer_kind(const void* p, int device);
+// true for host memory CUDA does not know (pageable): a copy from it is staged
+// by the driver before the copy call returns
+bool ddks_is_pageable(const void* p);
 int ddks_check_problem(const void* P, int64_t NP, const void* T, int64_t NT, int32_t d, int32_t dtype);
 int ddks_stage_inputs(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t NT,
                       int32_t d, int32_t dtype, cudaStream_t st, const void** dP, const void** dT);

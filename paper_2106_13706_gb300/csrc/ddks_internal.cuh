@@ -63,6 +63,16 @@ DDKS_DEV uint64_t numer(uint64_t a, uint64_t b, uint64_t NP, uint64_t NT) {
 
 }  // namespace ddks
 
+// The dynamic shared-memory limit of a kernel, raised to at least `bytes`
+// (never lowered: contexts on several threads launch the same kernels with
+// different sizes, and a lowered limit would fail another thread's launch
+// between its own set and launch).  Per device; thread-safe.
+cudaError_t ddks_smem_attr_raw(const void* func, size_t bytes);
+template <class F>
+inline cudaError_t ddks_smem_attr(F* func, size_t bytes) {
+  return ddks_smem_attr_raw(reinterpret_cast<const void*>(func), bytes);
+}
+
 // Launch wrappers implemented in the .cu files (all enqueue on `st`).
 struct DdksProblemDev {
   const uint32_t* rank;  // [d][N]

@@ -158,11 +158,11 @@ int ddks_distance_noalloc(const void* P, int64_t NP, const void* T, int64_t NT, 
   while (P2 < N) P2 <<= 1;
   const size_t smem = (size_t)P2 * 12;
   if (dtype == DDKS_F64) {
-    e = cudaFuncSetAttribute(k_noalloc_rank<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ddks_smem_attr(k_noalloc_rank<double>, (int)smem);
     if (e == cudaSuccess)
       k_noalloc_rank<double><<<d, 1024, smem, st>>>((const double*)P, (const double*)T, NP, NT, d, rank, flags);
   } else {
-    e = cudaFuncSetAttribute(k_noalloc_rank<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ddks_smem_attr(k_noalloc_rank<float>, (int)smem);
     if (e == cudaSuccess)
       k_noalloc_rank<float><<<d, 1024, smem, st>>>((const float*)P, (const float*)T, NP, NT, d, rank, flags);
   }

@@ -474,8 +474,7 @@ cudaError_t launch_count(const uint32_t* rank, int64_t N, int64_t NP, int B, int
   if (R > 16) R = 16;
   const size_t smem = (size_t)NB * 4 + (size_t)R * NW * kCountThreads * 4 +
                       (size_t)kPtsTile * WARPS * R * 4 + (size_t)N;
-  cudaError_t e = cudaFuncSetAttribute(k_perm_count<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = ddks_smem_attr(k_perm_count<D>, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = (int)(N < (int64_t)num_sms * 4 ? N : (int64_t)num_sms * 4);
   k_perm_count<D><<<grid, kCountThreads, smem, st>>>(rank, N, NP, B, G, labels, R, perm_best);
@@ -558,11 +557,11 @@ static int perm_impl(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, in
           uint16_t* boff = sidx + (size_t)N * N;
           const size_t smem1 = (size_t)kSortWarps * (1 << d) * 4 + (size_t)kSortWarps * ((N + 15) & ~15);
           auto go = [&](auto sortk, auto bitsk) -> cudaError_t {
-            cudaError_t q = cudaFuncSetAttribute(sortk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+            cudaError_t q = ddks_smem_attr(sortk, (int)smem1);
             if (q != cudaSuccess) return q;
             int g1 = (int)((N + kSortWarps - 1) / kSortWarps);
             sortk<<<g1, kSortWarps * 32, smem1, s>>>(rank, (int)N, sidx, boff);
-            q = cudaFuncSetAttribute(bitsk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+            q = ddks_smem_attr(bitsk, (int)smem2);
             if (q != cudaSuccess) return q;
             const int npass = (B + kPassPerms - 1) / kPassPerms;
             for (int pass = 0; pass < npass && q == cudaSuccess; ++pass) {

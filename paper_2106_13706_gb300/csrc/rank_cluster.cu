@@ -344,7 +344,7 @@ int cluster_size_for(int dev) {
   int best = 8;
   auto kern = k_rank_cluster<V, 16>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap) == cudaSuccess) {
+      ddks_smem_attr(kern, kSmemCap) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16, 1, 1);
     cfg.blockDim = dim3(kKT, 1, 1);
@@ -388,7 +388,7 @@ cudaError_t ddks_launch_rank_cluster(const void* P, const void* T, int64_t NP, i
   // ceil(2^32 / S) fits 32 bits for S >= 2; S == 1 divides by itself
   const uint32_t Smag = S == 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + (uint64_t)S - 1) / (uint64_t)S);
   auto go = [&](auto kern, size_t smem, auto* p, auto* t) -> cudaError_t {
-    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t r = ddks_smem_attr(kern, (int)smem);
     if (r != cudaSuccess) return r;
     if (CL > 8 && (r = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
       return r;

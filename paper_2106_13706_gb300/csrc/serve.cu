@@ -1,18 +1,22 @@
 // serve.cu -- continuous batching of two-sample ddKS requests.
 //
 // ddks_submit copies a request's points into library-owned device memory
-// (stream-ordered allocations from the device's memory pool) and queues it.  Worker threads (two, each with its own internal context and
-// stream) repeatedly admit queued requests in arrival order while the sum of
-// the admitted requests' device footprints stays within the HBM budget and the
-// batch stays within max_batch, run the admitted requests as one batched
-// launch (batch.cu: one persistent kernel over all their work units), and
-// publish the results.  Requests that arrive while a batch is on the GPU join
-// the next one; with two workers two batches overlap on the device.  A batch
-// of one request runs through the single-problem path (ddks_distance).  A
-// request whose footprint alone exceeds the budget is refused at submit with
-// DDKS_ENOMEM.  ddks_poll reads a result, optionally waiting a bounded time.
-// No device code waits on the host: the only waits are host condition
-// variables with timeouts.
+// (stream-ordered allocations from the device's memory pool; from pageable
+// host memory the worker's stream waits on an event for the copy, otherwise
+// submit waits for it) and queues it.  Worker threads (two, each with its own
+// internal context and stream) repeatedly admit queued requests in arrival
+// order while the sum of the admitted requests' device footprints stays
+// within the HBM budget and the batch stays within max_batch, run the admitted
+// requests as one batched launch (batch.cu: one persistent launch per
+// dimension over all their work units), and publish the results.  Requests
+// that arrive while a batch is on the GPU join the next one; with two workers
+// two batches overlap on the device.  A request above the batched kernels'
+// size (16,384 pooled points) fills the GPU by itself: it runs alone, one at
+// a time, through the single-problem path (ddks_distance), and small requests
+// behind a waiting large one may go first.  A request whose footprint alone
+// exceeds the budget is refused at submit with DDKS_ENOMEM.  ddks_poll reads
+// a result, optionally waiting a bounded time.  No device code waits on the
+// host: the only waits are host condition variables with timeouts.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -37,7 +41,11 @@ struct Request {
   uint64_t footprint = 0;
   int status = DDKS_PENDING;
   ddks_result res{};
+  cudaEvent_t ready = nullptr;  // input copies still in flight (pageable host inputs)
+  bool big = false;             // above the batched kernels' size: runs alone
 };
+
+constexpr int64_t kBigN = 16384;  // pooled points above which a request runs alone
 
 constexpr int kWorkers = 2;
 
@@ -50,6 +58,7 @@ struct ServeState {
   std::unordered_map<uint64_t, std::shared_ptr<Request>> reqs;
   uint64_t next_ticket = 1;
   uint64_t resident = 0, resident_peak = 0;
+  int big_running = 0;  // large requests on the GPU (at most one)
   uint64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, batches = 0;
   bool stop = false;
   std::vector<std::thread> workers;
@@ -75,17 +84,39 @@ static void worker_loop(ddks_ctx* owner, int w) {
   const int max_batch = owner->cfg.max_batch;
   for (;;) {
     std::vector<std::shared_ptr<Request>> batch;
+    bool big = false;
     {
       std::unique_lock<std::mutex> lk(S->mu);
+      // A large request fills the GPU by itself: it runs alone and one at a
+      // time (two at once would each take twice as long); small requests
+      // behind a waiting large one may go first.  Otherwise arrival order.
+      auto admissible = [&](const std::shared_ptr<Request>& r) {
+        return S->resident + r->footprint <= budget && (!r->big || S->big_running == 0);
+      };
       S->cv_work.wait(lk, [&] {
         if (S->stop) return true;
-        return !S->pending.empty() && S->resident + S->pending.front()->footprint <= budget;
+        for (auto& r : S->pending)
+          if (admissible(r)) return true;
+        return false;
       });
       if (S->stop) return;
-      while (!S->pending.empty() && (int)batch.size() < max_batch &&
-             S->resident + S->pending.front()->footprint <= budget) {
-        auto r = S->pending.front();
-        S->pending.pop_front();
+      for (auto it = S->pending.begin(); it != S->pending.end() && (int)batch.size() < max_batch;) {
+        auto r = *it;
+        if (r->big) {
+          if (batch.empty() && admissible(r)) {  // alone
+            it = S->pending.erase(it);
+            S->resident += r->footprint;
+            S->admitted += 1;
+            S->big_running += 1;
+            batch.push_back(r);
+            big = true;
+            break;
+          }
+          ++it;  // small requests behind it may go first
+          continue;
+        }
+        if (S->resident + r->footprint > budget) break;  // arrival order within the budget
+        it = S->pending.erase(it);
         S->resident += r->footprint;
         S->admitted += 1;
         batch.push_back(r);
@@ -93,6 +124,13 @@ static void worker_loop(ddks_ctx* owner, int w) {
       if (S->resident > S->resident_peak) S->resident_peak = S->resident;
       S->batches += 1;
     }
+    // the batch's input copies, where submit did not wait for them
+    for (auto& r : batch)
+      if (r->ready) {
+        cudaStreamWaitEvent(st, r->ready, 0);
+        cudaEventDestroy(r->ready);
+        r->ready = nullptr;
+      }
     // group by dtype (one batched launch per dtype)
     for (int dt = 0; dt < 2; ++dt) {
       std::vector<const void*> Ps, Ts;
@@ -142,6 +180,7 @@ static void worker_loop(ddks_ctx* owner, int w) {
         S->resident -= r->footprint;
         S->completed += 1;
       }
+      if (big) S->big_running -= 1;
     }
     S->cv_done.notify_all();
     S->cv_work.notify_all();
@@ -199,6 +238,7 @@ void ddks_serve_shutdown(ddks_ctx* ctx) {
   for (auto& r : S->pending) {  // never admitted: their inputs go back to the pool
     cudaFreeAsync(r->P, S->sub_st);
     cudaFreeAsync(r->T, S->sub_st);
+    if (r->ready) cudaEventDestroy(r->ready);
   }
   cudaStreamSynchronize(S->sub_st);
   cudaStreamDestroy(S->sub_st);
@@ -240,6 +280,7 @@ int ddks_submit(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t
   r->d = d;
   r->dtype = dtype;
   r->footprint = request_footprint(NP, NT, d, dtype);
+  r->big = NP + NT > kBigN;
   if (r->footprint > ctx->cfg.hbm_budget_bytes) {
     std::lock_guard<std::mutex> g(S->mu);
     S->rejected += 1;
@@ -248,19 +289,28 @@ int ddks_submit(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int64_t
   const size_t es = dtype == DDKS_F64 ? 8 : 4;
   const size_t bP = es * (size_t)NP * d, bT = es * (size_t)NT * d;
   // copy the inputs (host or device) to the device so the caller may free
-  // them on return; the copies are complete when submit returns
+  // them on return.  From pageable host memory the driver has staged the
+  // data by the time the copy call returns, so the worker's stream waits on
+  // an event instead; device and page-locked inputs are waited for here.
   {
     std::lock_guard<std::mutex> g(S->sub_mu);
     cudaError_t e = cudaSetDevice(ctx->device);
+    const bool pageable = ddks_is_pageable(P) && ddks_is_pageable(T);
     if (e == cudaSuccess) e = cudaMallocAsync(&r->P, bP, S->sub_st);
     if (e == cudaSuccess) e = cudaMallocAsync(&r->T, bT, S->sub_st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(r->P, P, bP, cudaMemcpyDefault, S->sub_st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(r->T, T, bT, cudaMemcpyDefault, S->sub_st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->sub_st);
+    if (e == cudaSuccess && pageable) {
+      e = cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(r->ready, S->sub_st);
+    } else if (e == cudaSuccess) {
+      e = cudaStreamSynchronize(S->sub_st);
+    }
     if (e != cudaSuccess) {
       if (r->P) cudaFreeAsync(r->P, S->sub_st);
       if (r->T) cudaFreeAsync(r->T, S->sub_st);
       cudaStreamSynchronize(S->sub_st);
+      if (r->ready) cudaEventDestroy(r->ready);
       return ctx_cuda_fail(ctx, e, "submit copy");
     }
   }

@@ -222,7 +222,7 @@ int ddks_significance(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, i
     int warps = 8;
     while (warps > 1 && (size_t)warps * ((size_t)(1u << d) + ddks::kMaxD) * 4 > 160u * 1024u) --warps;
     const size_t smem = (size_t)warps * ((size_t)(1u << d) + ddks::kMaxD) * 4;
-    e = cudaFuncSetAttribute(k_sig_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ddks_smem_attr(k_sig_cells, (int)smem);
     if (e == cudaSuccess) {
       int64_t g = (N + warps - 1) / warps;
       if (g > (int64_t)ctx->num_sms * 8) g = (int64_t)ctx->num_sms * 8;

@@ -119,3 +119,26 @@ def test_poll_without_wait_and_shutdown_with_queue(torch):
     rc, r = c.poll(tks[-1], 0)
     assert rc in (pkg.DDKS_OK, pkg.DDKS_PENDING)
     c.close()  # joins the workers with requests possibly still queued
+
+
+def test_submit_inputs_reusable_on_return(torch):
+    # submit returns before the device copy of pageable host inputs has
+    # landed (the worker waits on an event); the caller may still overwrite
+    # its buffers at once: every result must be that of the original data
+    rng = np.random.default_rng(12)
+    probs = [wl.random_pair(70 + i, int(rng.integers(50, 3000)), int(rng.integers(50, 3000)), 2 + i % 3)
+             for i in range(12)]
+    refs = [orc.ddks(P, T) for P, T in probs]
+    with pkg.Context(device=0, max_batch=8) as c:
+        tickets = []
+        for P, T in probs:
+            Pb, Tb = P.copy(), T.copy()
+            tickets.append(c.submit(Pb, Tb))
+            Pb[:] = 1e6  # reused by the caller right after submit
+            Tb[:] = -1e6
+            del Pb, Tb
+        for tk, ref in zip(tickets, refs):
+            rc, r = c.poll(tk, 10_000_000)
+            assert rc == pkg.DDKS_OK
+            assert (r["num_max"], r["argmax_origin"], r["argmax_orthant"]) == (
+                ref["num_max"], ref["argmax_origin"], ref["argmax_orthant"])
