@@ -1180,7 +1180,7 @@ k_rdks_hist_sum(const uint32_t* __restrict__ part, int chunks, ull* __restrict__
 __global__ void __launch_bounds__(kCandThreads)
 k_rdks_cands(const ull* __restrict__ H, int64_t NP, int64_t NT, ull* __restrict__ pc, int* __restrict__ slot,
              RdksCand* __restrict__ cand, int* __restrict__ ccount, unsigned* __restrict__ fill,
-             unsigned* __restrict__ flags) {
+             uint32_t* __restrict__ cbits, unsigned* __restrict__ flags) {
   constexpr int kW = kCandThreads / 32;
   constexpr int kPerW = kHistB / kW;
   __shared__ unsigned long long ws[kW];
@@ -1263,6 +1263,8 @@ k_rdks_cands(const ull* __restrict__ H, int64_t NP, int64_t NT, ull* __restrict_
       }
     }
     slot[(int64_t)s * kHistB + warp * kPerW + j0 + lane] = sl;
+    const uint32_t bm = __ballot_sync(0xffffffffu, sl >= 0);  // 32 buckets, one word of the bitmap
+    if (lane == 0) cbits[(int64_t)s * (kHistB / 32) + (warp * kPerW + j0) / 32] = bm;
     carry += __shfl_sync(0xffffffffu, inc, 31);
   }
   __syncthreads();
@@ -1276,8 +1278,14 @@ k_rdks_cands(const ull* __restrict__ H, int64_t NP, int64_t NT, ull* __restrict_
 __global__ void __launch_bounds__(kThreads)
 k_rdks_gather(const ull* __restrict__ keys, int64_t N, int64_t NP, const ull* __restrict__ kmin,
               const ull* __restrict__ kmax, const int* __restrict__ slot, const RdksCand* __restrict__ cand,
-              unsigned* __restrict__ fill, ull* __restrict__ gk, uint8_t* __restrict__ gl) {
+              const uint32_t* __restrict__ cbits, unsigned* __restrict__ fill, ull* __restrict__ gk,
+              uint8_t* __restrict__ gl) {
+  // the row's candidate buckets as a bitmap in shared memory: only keys in a
+  // candidate bucket read the slot table
+  __shared__ uint32_t sbits[kHistB / 32];
   const int s = blockIdx.y;
+  for (int w = threadIdx.x; w < kHistB / 32; w += blockDim.x) sbits[w] = cbits[(int64_t)s * (kHistB / 32) + w];
+  __syncthreads();
   const ull* row = keys + (int64_t)s * N;
   const ull k0 = kmin[s];
   const int sh = hist_shift(k0, kmax[s]);
@@ -1290,7 +1298,10 @@ k_rdks_gather(const ull* __restrict__ keys, int64_t N, int64_t NP, const ull* __
 #pragma unroll
     for (int u = 0; u < 4; ++u) k[u] = i0 + u * stride < N ? row[i0 + u * stride] : k0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) c[u] = i0 + u * stride < N ? sl[(k[u] - k0) >> sh] : -1;
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t b = (uint32_t)((k[u] - k0) >> sh);
+      c[u] = (i0 + u * stride < N && ((sbits[b >> 5] >> (b & 31)) & 1u)) ? sl[b] : -1;
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (c[u] < 0) continue;
@@ -1304,17 +1315,19 @@ k_rdks_gather(const ull* __restrict__ keys, int64_t N, int64_t NP, const ull* __
   }
 }
 
-// One warp per candidate of at most kWarpRefineMax points (E per lane): no
-// sort -- for each point, the points of each sample whose key is <= its key
-// give D at the end of its run (equal keys give the same value).
+// One CTA per candidate of at most kWarpRefineMax points: its 8 warps split
+// the candidate's points (warp w: points w * 32 * E .. ), each warp counting
+// against all of them.
+// This warp's points are [first, end) of the candidate's n points.
 template <int E>
-DDKS_DEV ull warp_refine(const ull* __restrict__ sk, const uint8_t* __restrict__ sp, int n, long long dstart,
-                         long long nt, long long np, int lane) {
+DDKS_DEV ull warp_refine_part(const ull* __restrict__ sk, const uint8_t* __restrict__ sp, int n, int first, int end,
+                              long long dstart, long long nt, long long np, int lane) {
   ull mine[E];
   unsigned cpn[E], cnn[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    mine[e] = e * 32 + lane < n ? sk[e * 32 + lane] : 0ull;
+    const int i = first + e * 32 + lane;
+    mine[e] = i < end ? sk[i] : 0ull;
     cpn[e] = cnn[e] = 0;
   }
   for (int j = 0; j < n; ++j) {
@@ -1330,14 +1343,10 @@ DDKS_DEV ull warp_refine(const ull* __restrict__ sk, const uint8_t* __restrict__
   ull best = 0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    if (e * 32 + lane >= n) break;
+    if (first + e * 32 + lane >= end) break;
     const long long dv = dstart + (long long)cpn[e] * nt - (long long)(cnn[e] - cpn[e]) * np;
     const ull v = (ull)(dv < 0 ? -dv : dv);
     best = v > best ? v : best;
-  }
-  for (int off = 16; off > 0; off >>= 1) {
-    const ull y = __shfl_xor_sync(0xffffffffu, best, off);
-    best = y > best ? y : best;
   }
   return best;
 }
@@ -1346,29 +1355,41 @@ __global__ void __launch_bounds__(kThreads)
 k_rdks_refine_warp(const ull* __restrict__ gk, const uint8_t* __restrict__ gl, int64_t N, int64_t NP, int64_t NT,
                    const RdksCand* __restrict__ cand, const int* __restrict__ ccount, ull* __restrict__ pc) {
   constexpr int kW = kThreads / 32;
-  __shared__ ull sk_all[kW][kWarpRefineMax];
-  __shared__ uint8_t sp_all[kW][kWarpRefineMax];
+  constexpr int kE = kWarpRefineMax / kThreads;  // points per lane at most
+  __shared__ ull sk[kWarpRefineMax];
+  __shared__ uint8_t sp[kWarpRefineMax];
+  __shared__ ull wbest[kW];
   const int s = blockIdx.y;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  ull* sk = sk_all[warp];
-  uint8_t* sp = sp_all[warp];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long nt = (long long)NT, np = (long long)NP;
-  // candidate ci goes to CTA ci % gridDim.x, so the work spreads over the SMs
-  for (int ci = blockIdx.x + gridDim.x * warp; ci < ccount[s]; ci += gridDim.x * kW) {
+  for (int ci = blockIdx.x; ci < ccount[s]; ci += gridDim.x) {
     const RdksCand cd = cand[(int64_t)s * kMaxCand + ci];
     const int n = (int)cd.n;
-    if (n > kWarpRefineMax) continue;  // the CTA kernel's
-    for (int i = lane; i < n; i += 32) {
+    if (n > kWarpRefineMax) continue;  // the sorting kernel's
+    __syncthreads();  // the buffers are free
+    for (int i = tid; i < n; i += kThreads) {
       sk[i] = gk[(int64_t)s * N + cd.off + i];
       sp[i] = gl[(int64_t)s * N + cd.off + i];
     }
-    __syncwarp();
-    const ull best = n <= 128   ? warp_refine<4>(sk, sp, n, cd.dstart, nt, np, lane)
-                     : n <= 256 ? warp_refine<8>(sk, sp, n, cd.dstart, nt, np, lane)
-                     : n <= 384 ? warp_refine<12>(sk, sp, n, cd.dstart, nt, np, lane)
-                                : warp_refine<16>(sk, sp, n, cd.dstart, nt, np, lane);
-    if (lane == 0) atomicMax(&pc[s], best);
-    __syncwarp();  // the warp's buffer is free for its next candidate
+    __syncthreads();
+    const int per = (n + kW - 1) / kW;  // points of each warp
+    const int first = warp * per, cnt = n - first < per ? (n - first > 0 ? n - first : 0) : per;
+    ull best = 0;
+    if (cnt > 0) {  // warp-uniform
+      best = cnt <= 32 ? warp_refine_part<1>(sk, sp, n, first, first + cnt, cd.dstart, nt, np, lane)
+                       : warp_refine_part<kE>(sk, sp, n, first, first + cnt, cd.dstart, nt, np, lane);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const ull y = __shfl_xor_sync(0xffffffffu, best, off);
+      best = y > best ? y : best;
+    }
+    if (lane == 0) wbest[warp] = best;
+    __syncthreads();
+    if (tid == 0) {
+      ull m = 0;
+      for (int w = 0; w < kW; ++w) m = wbest[w] > m ? wbest[w] : m;
+      atomicMax(&pc[s], m);
+    }
   }
 }
 
@@ -1817,7 +1838,8 @@ static int rdks_run(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int
   const size_t a_slot = a_H + 8 * (size_t)S * kHistB, a_cand = a_slot + 4 * (size_t)S * kHistB;
   const size_t a_fill = a_cand + sizeof(RdksCand) * (size_t)S * kMaxCand;
   const size_t a_kmin = (a_fill + 4 * (size_t)S * kMaxCand + 15) & ~(size_t)15;
-  const size_t a_kmax = a_kmin + 8 * (size_t)S, a_cc = a_kmax + 8 * (size_t)S, a_end = a_cc + 4 * (size_t)S;
+  const size_t a_kmax = a_kmin + 8 * (size_t)S, a_cc = a_kmax + 8 * (size_t)S;
+  const size_t a_bits = (a_cc + 4 * (size_t)S + 15) & ~(size_t)15, a_end = a_bits + 4 * (size_t)S * (kHistB / 32);
   if (hist && (rc = ctx->rdks_aux.reserve(ctx, a_end))) return out->status = rc;
   // warp kernel: shared memory of 2 * d doubles per warp
   int nwb = (int)((96 * 1024) / (16 * (size_t)d));
@@ -1898,6 +1920,7 @@ static int rdks_run(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int
       ull* kmin = (ull*)(ax + a_kmin);
       ull* kmax = (ull*)(ax + a_kmax);
       int* ccount = (int*)(ax + a_cc);
+      uint32_t* cbits = (uint32_t*)(ax + a_bits);
       ull* gk = (ull*)ctx->tk1.ptr;
       uint8_t* gl = (uint8_t*)ctx->ti1.ptr;
       ee = cudaMemsetAsync(kmin, 0xFF, 8 * (size_t)S, s);
@@ -1914,9 +1937,9 @@ static int rdks_run(ddks_ctx* ctx, const void* P, int64_t NP, const void* T, int
                                                                                         part);
       k_rdks_hist_sum<<<dim3((kHistB + kThreads - 1) / kThreads, (unsigned)S), kThreads, 0, s>>>(part, hchunks, H);
       ddks_stage_mark(ctx, 2, s);
-      k_rdks_cands<<<S, kCandThreads, 0, s>>>(H, NP, NT, pc, slot, cand, ccount, fill, flags);
-      k_rdks_gather<<<g2, kThreads, 0, s>>>(keys, N, NP, kmin, kmax, slot, cand, fill, gk, gl);
-      k_rdks_refine_warp<<<dim3(kMaxCand / 8, (unsigned)S), kThreads, 0, s>>>(gk, gl, N, NP, NT, cand, ccount, pc);
+      k_rdks_cands<<<S, kCandThreads, 0, s>>>(H, NP, NT, pc, slot, cand, ccount, fill, cbits, flags);
+      k_rdks_gather<<<g2, kThreads, 0, s>>>(keys, N, NP, kmin, kmax, slot, cand, cbits, fill, gk, gl);
+      k_rdks_refine_warp<<<dim3(kMaxCand / 2, (unsigned)S), kThreads, 0, s>>>(gk, gl, N, NP, NT, cand, ccount, pc);
       k_rdks_refine<<<dim3(16, (unsigned)S), kThreads, kRefineSmem, s>>>(gk, gl, N, NP, NT, cand, ccount, pc);
       k_rdks_final<<<1, kThreads, 0, s>>>(pc, S, (ull*)sm);
       ctx->launches += 8;
