@@ -213,11 +213,11 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
  * shared-memory tile (256, 512 or 1024).  Bit-sliced unit (2 <= d <= 6 only):
  * origins_per_unit = 127 (the unit's origins re-rank every point to 7 bits;
  * Sec. 2.2.1, Eq. g) and points per tile 256, 512, 1024 or 2048, rounded to
- * groups of 32.  Byte unit (d = 7 or 8 only): origins_per_unit = 31 or 63
- * (one origin per thread, each point re-ranked to a byte per dimension) and
- * points per tile 256, 512, 1024 or 2048.  DDKS_EINVAL otherwise.  The
- * defaults: 127 x 512 for 2 <= d <= 6, 63 x 512 for d = 7, 8, 64 x 512
- * otherwise.  The results do not depend on the shape.  The paper has no counterpart.
+ * groups of 32.  Byte unit (d = 7 or 8 only): origins_per_unit = 31, 63 or
+ * 127 (one origin per thread, each point re-ranked to a byte per dimension)
+ * and points per tile 256, 512, 1024 or 2048.  DDKS_EINVAL otherwise.  The
+ * defaults: 127 x 512 for 2 <= d <= 8 (bit-sliced up to d = 6, bytes for
+ * d = 7, 8), 64 x 512 otherwise.  The results do not depend on the shape.  The paper has no counterpart.
  */
 int ddks_set_batch_shape(ddks_ctx* ctx, int32_t d, int32_t origins_per_unit, int32_t points_per_tile);
 

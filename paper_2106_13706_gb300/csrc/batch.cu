@@ -42,8 +42,9 @@ constexpr int kTile = 512;     // default points per staged tile
 constexpr int kBitsOT = 127;   // origins per bit-sliced unit (re-ranked values fit 7 bits)
 constexpr int kBitsThreads = 128;
 constexpr int kBuildPts = 4;  // points (groups) per thread (warp) whose rank loads are issued together
-// origins per byte unit (one warp or two, one origin slot left over)
-constexpr bool is_bytes_ot(int ot) { return ot == 31 || ot == 63; }
+// origins per byte unit (one, two or four warps, one origin slot left over;
+// 127 means the byte unit for d = 7, 8 and the bit-sliced unit below)
+constexpr bool is_bytes_ot(int ot, int d) { return (d == 7 || d == 8) && (ot == 31 || ot == 63 || ot == 127); }
 
 
 // rankL[m][pos] = rank_m of the point at list position pos (one CTA per
@@ -751,6 +752,8 @@ cudaError_t launch_bytes(int d, int ot, int sms, const BatchDesc* desc, int coun
   if (d == 7 && ot == 31) return launch_bytes_dt<7, 32>(sms, desc, count, units, ra, next, best, bestj, PT, nw_max, s);
   if (d == 8 && ot == 63) return launch_bytes_dt<8, 64>(sms, desc, count, units, ra, next, best, bestj, PT, nw_max, s);
   if (d == 8 && ot == 31) return launch_bytes_dt<8, 32>(sms, desc, count, units, ra, next, best, bestj, PT, nw_max, s);
+  if (d == 7 && ot == 127) return launch_bytes_dt<7, 128>(sms, desc, count, units, ra, next, best, bestj, PT, nw_max, s);
+  if (d == 8 && ot == 127) return launch_bytes_dt<8, 128>(sms, desc, count, units, ra, next, best, bestj, PT, nw_max, s);
   return cudaErrorInvalidValue;
 }
 
@@ -776,11 +779,11 @@ size_t unit_smem(int d, int PT) {
 
 // Tile shapes of the batched units: (32 | 64 | 128 origins per unit, 256 |
 // 512 | 1024 points per staged tile) for the histogram units, (127, 256 |
-// 512 | 1024 | 2048) for the bit-sliced unit of 2 <= d <= 6 and (31 | 63,
-// 256 | 512 | 1024 | 2048) for the byte unit of d = 7, 8.
+// 512 | 1024 | 2048) for the bit-sliced unit of 2 <= d <= 6 and (31 | 63 |
+// 127, 256 | 512 | 1024 | 2048) for the byte unit of d = 7, 8.
 static bool shape_valid(int d, int ot, int pt) {
+  if (is_bytes_ot(ot, d)) return pt == 256 || pt == 512 || pt == 1024 || pt == 2048;
   if (ot == kBitsOT) return d >= 2 && d <= 6 && (pt == 256 || pt == 512 || pt == 1024 || pt == 2048);
-  if (is_bytes_ot(ot)) return (d == 7 || d == 8) && (pt == 256 || pt == 512 || pt == 1024 || pt == 2048);
   return (ot == 32 || ot == 64 || ot == 128) && (pt == 256 || pt == 512 || pt == 1024);
 }
 
@@ -882,7 +885,7 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
         (wide ? wide_prob : cta_prob).push_back(b);
         (wide ? wide_dim : cta_dim).push_back(m);
       }
-      if (OT != kBitsOT && !is_bytes_ot(OT)) smem_unit = std::max(smem_unit, unit_smem(d[i], ctx->batch_pt[d[i]]));
+      if (OT != kBitsOT && !is_bytes_ot(OT, d[i])) smem_unit = std::max(smem_unit, unit_smem(d[i], ctx->batch_pt[d[i]]));
     }
     cta_prob.insert(cta_prob.begin(), wide_prob.begin(), wide_prob.end());
     cta_dim.insert(cta_dim.begin(), wide_dim.begin(), wide_dim.end());
@@ -959,7 +962,7 @@ int ddks_batch_distance(ddks_ctx* ctx, int32_t count, const void* const* P, cons
         if (OT == kBitsOT && G.d >= 2 && G.d <= 6) {
           ee = launch_bits(G.d - 1, ctx->num_sms, ddesc + G.first, G.count, G.units, ra, work + gorder[gi],
                            (uint64_t*)ctx->best.ptr, (int32_t*)ctx->bestj.ptr, PT / 32, G.nw_max, s);
-        } else if (is_bytes_ot(OT)) {
+        } else if (is_bytes_ot(OT, G.d)) {
           ee = launch_bytes(G.d, OT, ctx->num_sms, ddesc + G.first, G.count, G.units, ra, work + gorder[gi],
                             (uint64_t*)ctx->best.ptr, (int32_t*)ctx->bestj.ptr, PT, G.nw_max, s);
         } else {
@@ -1055,6 +1058,7 @@ int ddks_autotune_batch(ddks_ctx* ctx, int32_t count, const void* const* P, cons
   static const int kShapes[][2] = {{32, 256},  {32, 512},  {32, 1024},  {64, 256},   {64, 512},  {64, 1024},
                                    {128, 256}, {128, 512}, {128, 1024}, {127, 512}, {127, 1024}, {127, 2048},
                                    {63, 512},  {63, 1024}, {63, 2048},  {31, 1024}};
+  // (127, pt) above is the bit-sliced unit for d <= 6 and the byte unit for d = 7, 8
   for (const auto& sh : kShapes) {
     const int ot = sh[0], pt = sh[1];
     {

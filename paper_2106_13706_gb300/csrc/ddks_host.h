@@ -83,8 +83,8 @@ struct ddks_ctx {
   std::mutex tune_mu;
   // batched launch: tile shapes per dimension (origins per work unit, points
   // per staged tile), set by ddks_autotune_batch; per-group kernel times when tuning
-  // per dimension: bit-sliced units (127) for 2..6, byte units (63) for 7, 8
-  int batch_ot[12] = {64, 64, 127, 127, 127, 127, 127, 63, 63, 64, 64, 64};
+  // per dimension: bit-sliced units (127) for 2..6, byte units (127) for 7, 8
+  int batch_ot[12] = {64, 64, 127, 127, 127, 127, 127, 127, 127, 64, 64, 64};
   int batch_pt[12] = {512, 512, 512, 512, 512, 512, 512, 512, 512, 512, 512, 512};
   bool batch_timing = false;
   float batch_group_ms[12] = {};

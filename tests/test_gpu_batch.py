@@ -57,12 +57,12 @@ def test_config4_256_uneven(torch):
 
 SHAPES = [(ot, pt) for ot in (32, 64, 128) for pt in (256, 512, 1024)]
 BITS_SHAPES = [(127, pt) for pt in (256, 512, 1024, 2048)]  # bit-sliced unit, 2 <= d <= 6
-BYTE_SHAPES = [(ot, pt) for ot in (31, 63) for pt in (256, 2048)]  # byte unit, d = 7, 8
+BYTE_SHAPES = [(ot, pt) for ot in (31, 63, 127) for pt in (256, 2048)]  # byte unit, d = 7, 8
 
 
 def _shape_ok(d, ot, pt):
-    if ot == 127:
-        return 2 <= d <= 6
+    if ot == 127:  # the bit-sliced unit for d <= 6, the byte unit for d = 7, 8
+        return 2 <= d <= 8
     if ot in (31, 63):
         return d in (7, 8)
     return True
@@ -82,7 +82,7 @@ def test_every_tile_shape_matches_oracle(torch):
             got = c.batch_distance(dev)
             for g, r in zip(got, refs):
                 assert _key(g) == _key(r), (ot, pt)
-        for d, ot, pt in [(3, 48, 512), (7, 127, 1024), (1, 127, 1024), (3, 64, 2048), (4, 127, 128),
+        for d, ot, pt in [(3, 48, 512), (9, 127, 1024), (1, 127, 1024), (3, 64, 2048), (4, 127, 128),
                           (6, 63, 1024), (9, 31, 512), (8, 63, 128)]:
             with pytest.raises(pkg.DdksError):
                 c.set_batch_shape(d, ot, pt)
@@ -129,7 +129,7 @@ def test_autotuned_shapes_and_results(torch):
         for d in (2, 3, 5, 8):
             ot, pt = shapes[d]
             if ot == 127:
-                assert 2 <= d <= 6 and pt in (256, 512, 1024, 2048)
+                assert 2 <= d <= 8 and pt in (256, 512, 1024, 2048)
             elif ot in (31, 63):
                 assert d in (7, 8) and pt in (256, 512, 1024, 2048)
             else:
@@ -159,7 +159,7 @@ def test_byte_unit_edges(torch, d):
         hist = c.batch_distance(dev[-1:])[0]
         alone = c.distance(*dev[-1])
         assert _key(hist) == _key(alone)
-        for ot, pt in [(31, 256), (63, 2048), (63, 512)]:
+        for ot, pt in [(31, 256), (63, 2048), (63, 512), (127, 512), (127, 2048)]:
             c.set_batch_shape(d, ot, pt)
             got = c.batch_distance(dev)
             for g, r in zip(got, refs):
