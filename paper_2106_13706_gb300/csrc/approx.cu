@@ -1071,10 +1071,14 @@ k_rdks_final(const ull* __restrict__ per_corner, int S, ull* __restrict__ out3) 
 // bucket D moves by +NT per P point and -NP per T point, so a bucket holding
 // one sample only has its extremes at its ends, and a mixed bucket can exceed
 // the best bucket end LB only if max(|D_start + nP*NT|, |D_start - nT*NP|) >
-// LB.  Only those candidate buckets are gathered and sorted (in shared
-// memory, one CTA each) and walked from D_start.  A row with more than
-// kMaxCand candidates, or a candidate with more than kRefineCap points, sets
-// kFlagRedo and the host reruns the call on the sorting path.
+// LB.  Only those candidate buckets are gathered (a bitmap of them lets the
+// other keys skip the slot table) and refined from D_start, one CTA each: up
+// to kWarpRefineMax points without a sort (each point counts the points of
+// each sample with a key <= its own, the warps splitting the points), larger
+// ones by a bitonic sort in shared memory and a walk of the run ends.  A row
+// with more than kMaxCand candidates, or a candidate with more than
+// kRefineCap points, sets kFlagRedo and the host reruns the call on the
+// sorting path.
 constexpr int kHistBits = 15;
 constexpr int kHistB = 1 << kHistBits;
 constexpr int kMaxCand = 1024;
